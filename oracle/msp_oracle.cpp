@@ -1,0 +1,756 @@
+// Oracle for the non-nested multilevel smoothed Schwarz method (arXiv 2412.08981).
+//
+// TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously correct FP64 CPU
+// restatement of what the GPU library computes.  It shares no code with the
+// library (no headers, helpers or tables) and is only ever loaded by the tests,
+// by __graft_entry__.smoke() and by the CPU-baseline leg of bench.py.
+//
+// Every function follows the paper's statement step by step, in its order:
+//   * discretisation J u = b of a linear PDE on a mesh (Section 2.1, Eq. (2)-(4)),
+//     realised as P1 finite elements for -div(k(x;mu) grad u) = f;
+//   * one-level restricted additive Schwarz (Section 2.2, Eq. (5)-(7));
+//   * the V-cycle of Algorithm 2 (Section 3.3), with the readings listed below;
+//   * right-preconditioned (flexible) GMRES (Section 2.1, Eq. (4); Section 4).
+// Readings where the paper is silent (shared with the library by specification,
+// not by code):
+//   * fine->coarse transfer is P^T and coarse->fine is P, P the P1 barycentric
+//     interpolation of coarse fields at fine nodes (replaces the MLS operator of
+//     Eq. (16)); the coarsest level is solved directly, not smoothed;
+//   * the smoothing loops of Algorithm 2 run exactly `its` times;
+//   * subdomain solvers are unpivoted LU of each (SPD) subdomain block;
+//   * Dirichlet rows are identity rows, Dirichlet columns are zeroed;
+//   * k(x;mu) is evaluated at the tet centroid, f at the vertices (vertex rule).
+// Compiled with -O2 -ffp-contract=off, OpenMP over subdomains and rows only.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+namespace {
+
+struct Csr {
+  std::vector<int> rowptr, col;
+  std::vector<double> val;
+};
+
+struct Subdomain {
+  std::vector<int> dofs;           // sorted global DoF ids (non-Dirichlet)
+  std::vector<unsigned char> own;  // 1 where the DoF is owned (R^0 rows)
+  std::vector<double> lu;          // dense n x n row-major, Doolittle LU in place
+};
+
+struct Level {
+  int n = 0, m = 0;
+  std::vector<double> xyz;
+  std::vector<int> tets;
+  std::vector<unsigned char> dir;
+  std::vector<int> owner;
+  Csr A;                  // assembled operator (pattern + values)
+  std::vector<double> b;  // load vector
+  std::vector<Subdomain> subs;
+  Subdomain coarse;       // used on the coarsest level: all interior DoFs
+  Csr P;                  // interpolation from level+1 (coarse) to this level
+  Csr PT;                 // its transpose
+};
+
+struct Oracle {
+  std::vector<Level> lv;
+  int delta = 1, nu_pre = 2, nu_post = 2;
+  int coef_kind = 0;  // 0: k = 1; 1: exp(s * sum_j mu_j * 0.5 * cos(pi a_j . x))
+  int wave[24] = {0};
+  double coef_scale = 1.0;
+  int load_kind = 0;  // 0: f = 1; 1: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+  std::vector<double> mu;
+  std::string err;
+};
+
+const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- geometry
+// Barycentric gradients of a tet: lambda = J^{-1} (x - x0) with
+// J = [x1-x0, x2-x0, x3-x0]; rows of J^{-1} are (e2 x e3, e3 x e1, e1 x e2)/det.
+void cross(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// grad[4][3], returns det (signed); volume = |det| / 6.
+double tet_gradients(const double* x0, const double* x1, const double* x2, const double* x3,
+                     double grad[4][3]) {
+  double e1[3], e2[3], e3[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = x1[d] - x0[d];
+    e2[d] = x2[d] - x0[d];
+    e3[d] = x3[d] - x0[d];
+  }
+  double c23[3], c31[3], c12[3];
+  cross(e2, e3, c23);
+  cross(e3, e1, c31);
+  cross(e1, e2, c12);
+  double det = dot3(e1, c23);
+  for (int d = 0; d < 3; ++d) {
+    grad[1][d] = c23[d] / det;
+    grad[2][d] = c31[d] / det;
+    grad[3][d] = c12[d] / det;
+    grad[0][d] = -(grad[1][d] + grad[2][d] + grad[3][d]);
+  }
+  return det;
+}
+
+// ------------------------------------------------------ coefficient and load
+double coefficient(const Oracle& o, const double* x) {
+  if (o.coef_kind == 0) return 1.0;
+  double s = 0.0;
+  for (int j = 0; j < 8; ++j) {
+    double ax = o.wave[3 * j] * x[0] + o.wave[3 * j + 1] * x[1] + o.wave[3 * j + 2] * x[2];
+    s += o.mu[j] * 0.5 * std::cos(kPi * ax);
+  }
+  return std::exp(o.coef_scale * s);
+}
+
+double load_f(const Oracle& o, const double* x) {
+  if (o.load_kind == 0) return 1.0;
+  return 3.0 * kPi * kPi * std::sin(kPi * x[0]) * std::sin(kPi * x[1]) * std::sin(kPi * x[2]);
+}
+
+// ------------------------------------------------------------- CSR pattern
+// Row i: the sorted distinct vertices that share a tet with i (i included).
+void build_pattern(Level& L) {
+  std::vector<std::set<int>> nb(L.n);
+  for (int e = 0; e < L.m; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nb[L.tets[4 * e + a]].insert(L.tets[4 * e + b]);
+  L.A.rowptr.assign(L.n + 1, 0);
+  L.A.col.clear();
+  for (int i = 0; i < L.n; ++i) {
+    for (int j : nb[i]) L.A.col.push_back(j);
+    L.A.rowptr[i + 1] = (int)L.A.col.size();
+  }
+  L.A.val.assign(L.A.col.size(), 0.0);
+}
+
+long csr_find(const Csr& A, int i, int j) {
+  auto b = A.col.begin() + A.rowptr[i], e = A.col.begin() + A.rowptr[i + 1];
+  auto it = std::lower_bound(b, e, j);
+  if (it == e || *it != j) return -1;
+  return it - A.col.begin();
+}
+
+// --------------------------------------------------------------- assembly
+// J(i,j) = sum over tets T (ascending id) of int_T k grad phi_j . grad phi_i
+// (Eq. (3) for the P1 Galerkin scheme), k at the centroid; then Dirichlet rows
+// become identity rows and Dirichlet columns are zeroed.
+// b(a) = sum over tets T containing a of f(x_a) |T| / 4 (vertex rule), 0 on
+// Dirichlet nodes.
+int assemble_level(const Oracle& o, Level& L) {
+  std::fill(L.A.val.begin(), L.A.val.end(), 0.0);
+  L.b.assign(L.n, 0.0);
+  for (int e = 0; e < L.m; ++e) {
+    const int* t = &L.tets[4 * e];
+    const double* x[4];
+    for (int a = 0; a < 4; ++a) x[a] = &L.xyz[3 * t[a]];
+    double g[4][3];
+    double det = tet_gradients(x[0], x[1], x[2], x[3], g);
+    double vol = std::fabs(det) / 6.0;
+    if (!(vol > 0.0)) return -1;
+    double xc[3];
+    for (int d = 0; d < 3; ++d) xc[d] = (x[0][d] + x[1][d] + x[2][d] + x[3][d]) / 4.0;
+    double k = coefficient(o, xc);
+    for (int a = 0; a < 4; ++a) {
+      for (int b = 0; b < 4; ++b) {
+        long nz = csr_find(L.A, t[a], t[b]);
+        L.A.val[nz] += k * vol * dot3(g[a], g[b]);
+      }
+      L.b[t[a]] += load_f(o, x[a]) * vol / 4.0;
+    }
+  }
+  for (int i = 0; i < L.n; ++i) {
+    for (int p = L.A.rowptr[i]; p < L.A.rowptr[i + 1]; ++p) {
+      int j = L.A.col[p];
+      if (L.dir[i]) L.A.val[p] = (i == j) ? 1.0 : 0.0;
+      else if (L.dir[j]) L.A.val[p] = 0.0;
+    }
+    if (L.dir[i]) L.b[i] = 0.0;
+  }
+  return 0;
+}
+
+void spmv(const Csr& A, const double* x, double* y) {
+  int n = (int)A.rowptr.size() - 1;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
+    y[i] = s;
+  }
+}
+
+// ------------------------------------------------------- subdomains (2.2)
+// Owners come from the vertex partition; a subdomain exists for every owner id
+// that owns at least one non-Dirichlet vertex, in ascending owner id.  The
+// overlap adds delta layers: V^{k+1} = vertices of tets touching V^k.
+void build_subdomains(const Oracle& o, Level& L) {
+  L.subs.clear();
+  std::set<int> ids;
+  for (int i = 0; i < L.n; ++i)
+    if (!L.dir[i]) ids.insert(L.owner[i]);
+  for (int id : ids) {
+    std::vector<unsigned char> in(L.n, 0);
+    for (int i = 0; i < L.n; ++i)
+      if (L.owner[i] == id) in[i] = 1;
+    for (int layer = 0; layer < o.delta; ++layer) {
+      std::vector<unsigned char> nxt = in;
+      for (int i = 0; i < L.n; ++i)
+        if (in[i])
+          for (int p = L.A.rowptr[i]; p < L.A.rowptr[i + 1]; ++p) nxt[L.A.col[p]] = 1;
+      in.swap(nxt);
+    }
+    Subdomain S;
+    for (int i = 0; i < L.n; ++i)
+      if (in[i] && !L.dir[i]) {
+        S.dofs.push_back(i);
+        S.own.push_back(L.owner[i] == id ? 1 : 0);
+      }
+    L.subs.push_back(std::move(S));
+  }
+}
+
+void build_coarse(Level& L) {
+  L.coarse = Subdomain();
+  for (int i = 0; i < L.n; ++i)
+    if (!L.dir[i]) {
+      L.coarse.dofs.push_back(i);
+      L.coarse.own.push_back(1);
+    }
+}
+
+// ------------------------------------------------------------ dense LU
+// Doolittle LU without pivoting, k-i-j order, in place (unit L below the
+// diagonal, U on and above it).  Returns -1 on a zero pivot.
+int lu_factor(int n, double* A) {
+  for (int k = 0; k < n; ++k) {
+    double piv = A[(size_t)k * n + k];
+    if (piv == 0.0 || !std::isfinite(piv)) return -1;
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[(size_t)i * n + k] / piv;
+      A[(size_t)i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+    }
+  }
+  return 0;
+}
+
+void lu_solve(int n, const double* LU, double* x) {
+  for (int i = 0; i < n; ++i) {
+    double s = x[i];
+    for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * x[j];
+    x[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * x[j];
+    x[i] = s / LU[(size_t)i * n + i];
+  }
+}
+
+// A_p = R_p A R_p^T as a dense block (Eq. (5)).
+void extract_dense(const Csr& A, const Subdomain& S, std::vector<double>& D) {
+  int n = (int)S.dofs.size();
+  D.assign((size_t)n * n, 0.0);
+  for (int li = 0; li < n; ++li) {
+    int i = S.dofs[li];
+    for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
+      auto it = std::lower_bound(S.dofs.begin(), S.dofs.end(), A.col[p]);
+      if (it != S.dofs.end() && *it == A.col[p]) D[(size_t)li * n + (it - S.dofs.begin())] = A.val[p];
+    }
+  }
+}
+
+int factor_sub(const Csr& A, Subdomain& S) {
+  extract_dense(A, S, S.lu);
+  return lu_factor((int)S.dofs.size(), S.lu.data());
+}
+
+// ------------------------------------------------------------- RAS (2.2)
+// z = sum_p (R^0_p)^T (A_p)^{-1} R^delta_p r  on non-Dirichlet DoFs, z_i = r_i
+// on Dirichlet DoFs (identity rows).
+void ras_apply(const Level& L, const double* r, double* z) {
+  for (int i = 0; i < L.n; ++i) z[i] = L.dir[i] ? r[i] : 0.0;
+  int np = (int)L.subs.size();
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int p = 0; p < np; ++p) {
+    const Subdomain& S = L.subs[p];
+    int n = (int)S.dofs.size();
+    std::vector<double> t(n);
+    for (int li = 0; li < n; ++li) t[li] = r[S.dofs[li]];
+    lu_solve(n, S.lu.data(), t.data());
+    for (int li = 0; li < n; ++li)
+      if (S.own[li]) z[S.dofs[li]] += t[li];  // each DoF is owned once: no race
+  }
+}
+
+void coarse_solve(const Level& L, const double* r, double* z) {
+  for (int i = 0; i < L.n; ++i) z[i] = L.dir[i] ? r[i] : 0.0;
+  const Subdomain& S = L.coarse;
+  int n = (int)S.dofs.size();
+  std::vector<double> t(n);
+  for (int li = 0; li < n; ++li) t[li] = r[S.dofs[li]];
+  lu_solve(n, S.lu.data(), t.data());
+  for (int li = 0; li < n; ++li) z[S.dofs[li]] = t[li];
+}
+
+// ---------------------------------------------------- interpolation P
+// For each fine non-Dirichlet node x, the coarse tet that contains it (all
+// barycentric coordinates >= -1e-12; the lowest tet id if several; the tet
+// maximising the smallest coordinate if none) gives the row: the raw
+// barycentric weights on that tet's vertices, columns sorted.  With
+// drop_dirichlet the columns of Dirichlet coarse vertices are left out and the
+// rows of Dirichlet fine nodes are empty.
+void barycentric(const double* xyz, const int* t, const double* x, double lam[4]) {
+  double g[4][3];
+  tet_gradients(&xyz[3 * t[0]], &xyz[3 * t[1]], &xyz[3 * t[2]], &xyz[3 * t[3]], g);
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = x[k] - xyz[3 * t[0] + k];
+  lam[1] = dot3(g[1], d);
+  lam[2] = dot3(g[2], d);
+  lam[3] = dot3(g[3], d);
+  lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+}
+
+void build_interp(int nc, const double* cxyz, int mc, const int* ctets, const unsigned char* cdir,
+                  int nf, const double* fxyz, const unsigned char* fdir, int drop_dirichlet,
+                  Csr& P) {
+  // bucket grid over the coarse bounding box; each tet goes into every bucket
+  // its (slightly enlarged) bounding box overlaps.  Candidates are then tested
+  // exactly, so the grid only prunes.
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < nc; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], cxyz[3 * i + d]);
+      hi[d] = std::max(hi[d], cxyz[3 * i + d]);
+    }
+  int G = std::max(1, (int)std::cbrt((double)mc / 6.0));
+  double ext[3];
+  for (int d = 0; d < 3; ++d) ext[d] = std::max(hi[d] - lo[d], 1e-300);
+  auto cell = [&](double v, int d) {
+    int c = (int)std::floor((v - lo[d]) / ext[d] * G);
+    return std::min(std::max(c, 0), G - 1);
+  };
+  std::vector<std::vector<int>> bucket((size_t)G * G * G);
+  for (int e = 0; e < mc; ++e) {
+    double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+    for (int a = 0; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) {
+        blo[d] = std::min(blo[d], cxyz[3 * ctets[4 * e + a] + d]);
+        bhi[d] = std::max(bhi[d], cxyz[3 * ctets[4 * e + a] + d]);
+      }
+    int c0[3], c1[3];
+    for (int d = 0; d < 3; ++d) {
+      double pad = 1e-9 * ext[d];
+      c0[d] = cell(blo[d] - pad, d);
+      c1[d] = cell(bhi[d] + pad, d);
+    }
+    for (int k = c0[2]; k <= c1[2]; ++k)
+      for (int j = c0[1]; j <= c1[1]; ++j)
+        for (int i = c0[0]; i <= c1[0]; ++i) bucket[(size_t)i + G * ((size_t)j + G * k)].push_back(e);
+  }
+  P.rowptr.assign(nf + 1, 0);
+  P.col.clear();
+  P.val.clear();
+  for (int f = 0; f < nf; ++f) {
+    if (!fdir[f] || !drop_dirichlet) {
+      const double* x = &fxyz[3 * f];
+      int best = -1;
+      double lam_best[4];
+      const auto& cand = bucket[(size_t)cell(x[0], 0) + G * ((size_t)cell(x[1], 1) + G * cell(x[2], 2))];
+      for (int e : cand) {  // candidates are in ascending tet id
+        double lam[4];
+        barycentric(cxyz, &ctets[4 * e], x, lam);
+        if (std::min(std::min(lam[0], lam[1]), std::min(lam[2], lam[3])) >= -1e-12) {
+          best = e;
+          std::copy(lam, lam + 4, lam_best);
+          break;
+        }
+      }
+      if (best < 0) {  // outside every tet: take the least-violating one (all tets)
+        double bm = -1e300;
+        for (int e = 0; e < mc; ++e) {
+          double lam[4];
+          barycentric(cxyz, &ctets[4 * e], x, lam);
+          double mn = std::min(std::min(lam[0], lam[1]), std::min(lam[2], lam[3]));
+          if (mn > bm) {
+            bm = mn;
+            best = e;
+            std::copy(lam, lam + 4, lam_best);
+          }
+        }
+      }
+      std::vector<std::pair<int, double>> row;
+      for (int a = 0; a < 4; ++a) {
+        int c = ctets[4 * best + a];
+        if (drop_dirichlet && cdir[c]) continue;
+        row.push_back({c, lam_best[a]});
+      }
+      std::sort(row.begin(), row.end());
+      for (auto& pr : row) {
+        P.col.push_back(pr.first);
+        P.val.push_back(pr.second);
+      }
+    }
+    P.rowptr[f + 1] = (int)P.col.size();
+  }
+}
+
+void transpose(const Csr& P, int ncols, Csr& T) {
+  int nr = (int)P.rowptr.size() - 1;
+  T.rowptr.assign(ncols + 1, 0);
+  for (int c : P.col) T.rowptr[c + 1]++;
+  for (int i = 0; i < ncols; ++i) T.rowptr[i + 1] += T.rowptr[i];
+  T.col.assign(P.col.size(), 0);
+  T.val.assign(P.col.size(), 0.0);
+  std::vector<int> pos(T.rowptr.begin(), T.rowptr.end() - 1);
+  for (int i = 0; i < nr; ++i)  // rows visited in ascending order: columns of T sorted
+    for (int p = P.rowptr[i]; p < P.rowptr[i + 1]; ++p) {
+      int q = pos[P.col[p]]++;
+      T.col[q] = i;
+      T.val[q] = P.val[p];
+    }
+}
+
+// ------------------------------------------------------ V-cycle (Alg. 2)
+void residual(const Level& L, const double* r, const double* z, double* t) {
+  spmv(L.A, z, t);
+  for (int i = 0; i < L.n; ++i) t[i] = r[i] - t[i];
+}
+
+// z += B^{-1} (r - A z), `its` times, starting from the given z.
+void smooth(const Level& L, const double* r, double* z, int its) {
+  std::vector<double> t(L.n), y(L.n);
+  for (int s = 0; s < its; ++s) {
+    residual(L, r, z, t.data());
+    ras_apply(L, t.data(), y.data());
+    for (int i = 0; i < L.n; ++i) z[i] += y[i];
+  }
+}
+
+void vcycle(const Oracle& o, const double* r0, double* z0) {
+  int Lc = (int)o.lv.size() - 1;
+  std::vector<std::vector<double>> r(o.lv.size()), z(o.lv.size());
+  for (int l = 0; l <= Lc; ++l) {
+    r[l].assign(o.lv[l].n, 0.0);
+    z[l].assign(o.lv[l].n, 0.0);
+  }
+  std::copy(r0, r0 + o.lv[0].n, r[0].begin());
+  for (int l = 0; l < Lc; ++l) {  // down: pre-smooth from z = 0, restrict residual
+    const Level& L = o.lv[l];
+    smooth(L, r[l].data(), z[l].data(), o.nu_pre);
+    std::vector<double> t(L.n);
+    residual(L, r[l].data(), z[l].data(), t.data());
+    spmv(L.PT, t.data(), r[l + 1].data());
+  }
+  coarse_solve(o.lv[Lc], r[Lc].data(), z[Lc].data());
+  for (int l = Lc - 1; l >= 0; --l) {  // up: prolongate correction, post-smooth
+    const Level& L = o.lv[l];
+    std::vector<double> pz(L.n);
+    spmv(L.P, z[l + 1].data(), pz.data());
+    for (int i = 0; i < L.n; ++i) z[l][i] += pz[i];
+    smooth(L, r[l].data(), z[l].data(), o.nu_post);
+  }
+  std::copy(z[0].begin(), z[0].end(), z0);
+}
+
+// ------------------------------------------------------------- FGMRES(m)
+// Right-preconditioned flexible GMRES with modified Gram-Schmidt and Givens
+// rotations; stops when the estimated residual |g_{j+1}| <= rtol ||b||, then
+// confirms with the true residual at every restart.
+double nrm2(const std::vector<double>& v) {
+  double s = 0.0;
+  for (double a : v) s += a * a;
+  return std::sqrt(s);
+}
+double dotv(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+int fgmres(const Oracle& o, const double* bptr, double* xptr, double rtol, int m, int maxit,
+           int precond, int* iters_out, double* relres_out) {
+  const Level& L = o.lv[0];
+  int n = L.n;
+  std::vector<double> b(bptr, bptr + n), x(n, 0.0), r(n), w(n);
+  double bnorm = nrm2(b);
+  *iters_out = 0;
+  if (bnorm == 0.0) {
+    std::copy(x.begin(), x.end(), xptr);
+    *relres_out = 0.0;
+    return 0;
+  }
+  int it = 0, status = -3;
+  std::vector<std::vector<double>> V(m + 1, std::vector<double>(n)), Z(m, std::vector<double>(n));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
+  r = b;
+  double rnorm = bnorm;
+  while (true) {
+    if (rnorm <= rtol * bnorm) {
+      status = 0;
+      break;
+    }
+    if (it >= maxit) break;
+    for (int i = 0; i < n; ++i) V[0][i] = r[i] / rnorm;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = rnorm;
+    int j = 0;
+    bool breakdown = false;
+    for (; j < m && it < maxit; ++j) {
+      if (precond) vcycle(o, V[j].data(), Z[j].data());
+      else Z[j] = V[j];
+      spmv(L.A, Z[j].data(), w.data());
+      for (int i = 0; i <= j; ++i) {
+        double h = dotv(w, V[i]);
+        H[(size_t)i * m + j] = h;
+        for (int k = 0; k < n; ++k) w[k] -= h * V[i][k];
+      }
+      double hn = nrm2(w);
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      double den = std::hypot(a, c);
+      cs[j] = (den == 0.0) ? 1.0 : a / den;
+      sn[j] = (den == 0.0) ? 0.0 : c / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      if (hn <= 1e-300) {
+        breakdown = true;
+        ++j;
+        break;
+      }
+      for (int k = 0; k < n; ++k) V[j + 1][k] = w[k] / hn;
+      if (std::fabs(g[j + 1]) <= rtol * bnorm) {
+        ++j;
+        break;
+      }
+    }
+    // y = H(0:j,0:j)^{-1} g(0:j); x += Z y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < j; ++i)
+      for (int k = 0; k < n; ++k) x[k] += y[i] * Z[i][k];
+    spmv(L.A, x.data(), w.data());
+    for (int k = 0; k < n; ++k) r[k] = b[k] - w[k];
+    rnorm = nrm2(r);
+    if (breakdown && rnorm > rtol * bnorm) break;
+  }
+  std::copy(x.begin(), x.end(), xptr);
+  *iters_out = it;
+  *relres_out = rnorm / bnorm;
+  return (rnorm <= rtol * bnorm) ? 0 : status;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+typedef struct {
+  int n_nodes;
+  const double* xyz;
+  int n_tets;
+  const int* tets;
+  const unsigned char* dirichlet;
+  const int* owner;  // may be NULL on the coarsest level
+} orc_level;
+
+void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
+                 int coef_kind, const int* wave, double coef_scale, int load_kind) {
+  if (nlevels < 1) return nullptr;
+  Oracle* o = new Oracle();
+  o->delta = delta;
+  o->nu_pre = nu_pre;
+  o->nu_post = nu_post;
+  o->coef_kind = coef_kind;
+  if (wave) std::copy(wave, wave + 24, o->wave);
+  o->coef_scale = coef_scale;
+  o->load_kind = load_kind;
+  o->lv.resize(nlevels);
+  for (int l = 0; l < nlevels; ++l) {
+    Level& L = o->lv[l];
+    L.n = lv[l].n_nodes;
+    L.m = lv[l].n_tets;
+    L.xyz.assign(lv[l].xyz, lv[l].xyz + 3 * (size_t)L.n);
+    L.tets.assign(lv[l].tets, lv[l].tets + 4 * (size_t)L.m);
+    L.dir.assign(lv[l].dirichlet, lv[l].dirichlet + L.n);
+    if (lv[l].owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
+    build_pattern(L);
+    if (l + 1 < nlevels) {
+      if (L.owner.empty()) {
+        delete o;
+        return nullptr;
+      }
+      build_subdomains(*o, L);
+    } else {
+      build_coarse(L);
+    }
+  }
+  for (int l = 0; l + 1 < nlevels; ++l) {
+    Level& F = o->lv[l];
+    Level& C = o->lv[l + 1];
+    build_interp(C.n, C.xyz.data(), C.m, C.tets.data(), C.dir.data(), F.n, F.xyz.data(),
+                 F.dir.data(), 1, F.P);
+    transpose(F.P, C.n, F.PT);
+  }
+  return o;
+}
+
+void orc_destroy(void* h) { delete static_cast<Oracle*>(h); }
+
+int orc_assemble(void* h, const double* mu) {
+  Oracle* o = static_cast<Oracle*>(h);
+  o->mu.assign(mu, mu + 8);
+  for (auto& L : o->lv)
+    if (assemble_level(*o, L)) return -1;
+  return 0;
+}
+
+int orc_factor(void* h) {
+  Oracle* o = static_cast<Oracle*>(h);
+  int bad = 0;
+  for (size_t l = 0; l < o->lv.size(); ++l) {
+    Level& L = o->lv[l];
+    if (l + 1 < o->lv.size()) {
+      int np = (int)L.subs.size();
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+      for (int p = 0; p < np; ++p) bad += factor_sub(L.A, L.subs[p]) ? 1 : 0;
+    } else {
+      bad += factor_sub(L.A, L.coarse) ? 1 : 0;
+    }
+  }
+  return bad ? -1 : 0;
+}
+
+// Factor only the subdomains [p0, p1) of one level (used to time a sample).
+int orc_factor_range(void* h, int level, int p0, int p1) {
+  Oracle* o = static_cast<Oracle*>(h);
+  Level& L = o->lv[level];
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+  for (int p = p0; p < p1; ++p) bad += factor_sub(L.A, L.subs[p]) ? 1 : 0;
+  return bad ? -1 : 0;
+}
+
+int orc_spmv(void* h, int level, const double* x, double* y) {
+  spmv(static_cast<Oracle*>(h)->lv[level].A, x, y);
+  return 0;
+}
+int orc_interp(void* h, int level, const double* xc, double* yf) {  // y_l = P x_{l+1}
+  spmv(static_cast<Oracle*>(h)->lv[level].P, xc, yf);
+  return 0;
+}
+int orc_restrict(void* h, int level, const double* yf, double* xc) {  // x_{l+1} = P^T y_l
+  spmv(static_cast<Oracle*>(h)->lv[level].PT, yf, xc);
+  return 0;
+}
+int orc_ras_apply(void* h, int level, const double* r, double* z) {
+  ras_apply(static_cast<Oracle*>(h)->lv[level], r, z);
+  return 0;
+}
+int orc_coarse_solve(void* h, const double* r, double* z) {
+  Oracle* o = static_cast<Oracle*>(h);
+  coarse_solve(o->lv.back(), r, z);
+  return 0;
+}
+int orc_vcycle(void* h, const double* r, double* z) {
+  vcycle(*static_cast<Oracle*>(h), r, z);
+  return 0;
+}
+int orc_fgmres(void* h, const double* b, double* x, double rtol, int restart, int maxit,
+               int precond, int* iters, double* relres) {
+  return fgmres(*static_cast<Oracle*>(h), b, x, rtol, restart, maxit, precond, iters, relres);
+}
+
+// Accessors into the oracle's state; they return the element count and set *ptr.
+long orc_get(void* h, const char* what, int level, int sub, const void** ptr) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (level < 0 || level >= (int)o->lv.size()) return -1;
+  Level& L = o->lv[level];
+  std::string w(what);
+  auto ret = [&](const auto& v) {
+    *ptr = v.data();
+    return (long)v.size();
+  };
+  if (w == "rowptr") return ret(L.A.rowptr);
+  if (w == "col") return ret(L.A.col);
+  if (w == "val") return ret(L.A.val);
+  if (w == "b") return ret(L.b);
+  if (w == "P_rowptr") return ret(L.P.rowptr);
+  if (w == "P_col") return ret(L.P.col);
+  if (w == "P_val") return ret(L.P.val);
+  if (w == "PT_rowptr") return ret(L.PT.rowptr);
+  if (w == "PT_col") return ret(L.PT.col);
+  if (w == "PT_val") return ret(L.PT.val);
+  if (w == "n_subs") {
+    *ptr = nullptr;
+    return (long)L.subs.size();
+  }
+  const Subdomain* S = nullptr;
+  if (sub < 0) S = &L.coarse;
+  else if (sub < (int)L.subs.size()) S = &L.subs[sub];
+  if (!S) return -1;
+  if (w == "sub_dofs") return ret(S->dofs);
+  if (w == "sub_own") return ret(S->own);
+  if (w == "sub_lu") return ret(S->lu);
+  return -1;
+}
+
+// ---- standalone pieces used by the pins ----
+double orc_tet_stiffness(const double* x4, double k, double* K16) {
+  double g[4][3];
+  double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);
+  double vol = std::fabs(det) / 6.0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) K16[4 * a + b] = k * vol * dot3(g[a], g[b]);
+  return vol;
+}
+
+int orc_lu_factor(int n, double* A) { return lu_factor(n, A); }
+void orc_lu_solve(int n, const double* LU, double* x) { lu_solve(n, LU, x); }
+
+// Interpolation between two arbitrary meshes (returns nnz; arrays are
+// allocated by the oracle and freed with orc_free_csr).
+long orc_build_interp(int nc, const double* cxyz, int mc, const int* ctets, const unsigned char* cdir,
+                      int nf, const double* fxyz, const unsigned char* fdir, int drop_dirichlet,
+                      int** rowptr, int** col, double** val) {
+  Csr P;
+  build_interp(nc, cxyz, mc, ctets, cdir, nf, fxyz, fdir, drop_dirichlet, P);
+  *rowptr = new int[P.rowptr.size()];
+  *col = new int[P.col.size() + 1];
+  *val = new double[P.val.size() + 1];
+  std::copy(P.rowptr.begin(), P.rowptr.end(), *rowptr);
+  std::copy(P.col.begin(), P.col.end(), *col);
+  std::copy(P.val.begin(), P.val.end(), *val);
+  return (long)P.col.size();
+}
+void orc_free_csr(int* rowptr, int* col, double* val) {
+  delete[] rowptr;
+  delete[] col;
+  delete[] val;
+}
+
+}  // extern "C"

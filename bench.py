@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Preconditioned solves/s (+ p50/p99 latency) of the multilevel smoothed
+Schwarz FGMRES solver on one GB300 per rank.
+
+A step is one whole solve for one parameter vector mu: assembly of J(mu) on
+every level, the subdomain and coarsest factorisations, and FGMRES(30) with the
+V-cycle preconditioner to rtol 1e-8.  Ranks solve independent parameters
+(replicas, weak scaling); there is no data-path collective.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl msp|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "preconditioned solves/s + p50/p99 latency at rtol 1e-8: mixed/batched vs FP64"
+UNIT = "solves/s"
+# FP64 on GB300 runs on the SIMT pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 SIMT: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+DESCR = {
+    "cube64_3lvl": "64^3/32^3/16^3 independently jittered Kuhn tet meshes (274,625 fine nodes, "
+                   "1.57M tets), k(x;mu)=exp(sum_j mu_j 0.5 cos(pi a_j.x)), 512 subdomains per "
+                   "smoothed level, overlap 2, nu=2, coarsest direct, FGMRES(30) rtol 1e-8, "
+                   "one mu per step (16 sequential)",
+    "cube16_3lvl": "16^3/8^3/4^3 jittered Kuhn meshes, 64/8 subdomains, overlap 2",
+    "cube8_2lvl": "8^3/4^3 jittered Kuhn meshes, k=1, 8 subdomains, overlap 1",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
+    ap.add_argument("--workload", default="cube64_3lvl")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=24,
+                    help="fine subdomains factored/solved by the CPU baseline sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- CPU baseline
+def cpu_baseline(levels, w, mu, iters, sample, rtol):
+    """The oracle, as it stands, on a bounded sample of one solve of the workload.
+
+    Timed: assembly of every level (full), LU of `sample` fine subdomains and of
+    every coarser-level block (full), one V-cycle in which the fine-level RAS
+    solves run for the sampled subdomains only, and the rest of one FGMRES
+    iteration (SpMVs, transfers, coarser levels, coarsest solve: full).  The
+    fine-level factor and solve times are scaled by n_sub / sample; a solve
+    costs assembly + factor + iterations x (V-cycle + SpMV + Gram-Schmidt), with
+    the iteration count of the GPU run of the same solve.
+    """
+    import oracle
+    o = oracle.Oracle(levels, delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], coef=w["coef"],
+                      wave=__import__("synthetic").wave_vectors(), scale=w["scale"], load=w["load"])
+    L = len(levels)
+    nsub0 = o.get("n_subs", 0)
+    sample = max(1, min(sample, nsub0))
+    t0 = time.perf_counter()
+    o.assemble(mu)
+    t_asm = time.perf_counter() - t0
+    # factor: sampled fine subdomains (scaled), coarser levels in full
+    t0 = time.perf_counter()
+    o.factor_range(0, 0, sample)
+    t_f0 = (time.perf_counter() - t0) * nsub0 / sample
+    t0 = time.perf_counter()
+    for l in range(1, L - 1):
+        o.factor_range(l, 0, o.get("n_subs", l))
+    t_rest_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.factor_coarsest()
+    t_fc = time.perf_counter() - t0
+    t_factor = t_f0 + t_rest_f + t_fc
+    # one iteration: fine RAS applications (sampled, scaled) + everything else
+    n0 = levels[0].n_nodes
+    r = np.random.default_rng(0).normal(size=n0)
+    t0 = time.perf_counter()
+    o.ras_apply_range(r, 0, 0, sample)
+    t_ras0 = (time.perf_counter() - t0) * nsub0 / sample
+    t0 = time.perf_counter()
+    nu = w["nu"]
+    # the remainder of a V-cycle: fine SpMVs and transfers, coarser levels
+    for _ in range(2 * nu + 1):
+        o.spmv(r, 0)
+    if L > 1:
+        rc = o.restrict(r, 0)
+        o.interp(rc, 0)
+        for l in range(1, L - 1):
+            for _ in range(2 * nu):
+                o.ras_apply(rc, l)
+                o.spmv(rc, l)
+            rc = o.restrict(rc, l)
+        o.coarse_solve(rc)
+    t_rest = time.perf_counter() - t0
+    # the outer SpMV of one iteration (the oracle's Gram-Schmidt, a few vector
+    # passes, is left out: well under 1% of an iteration here)
+    t0 = time.perf_counter()
+    o.spmv(r, 0)
+    t_gs = time.perf_counter() - t0
+    t_iter = 2 * nu * t_ras0 + t_rest + t_gs
+    t_solve = t_asm + t_factor + iters * t_iter
+    cores = os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    if omp:
+        cores = int(omp)
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "seconds_per_solve": t_solve,
+            "sample": (f"one solve of the workload: assembly + coarser-level and coarsest LU in "
+                       f"full; LU and RAS solves of {sample} of {nsub0} fine subdomains scaled "
+                       f"x{nsub0 / sample:.1f}; {iters} iterations (GPU count) x (V-cycle + "
+                       f"SpMV; Gram-Schmidt left out)"),
+            "parts_s": {"assemble": t_asm, "factor": t_factor, "iteration": t_iter}}
+
+
+# ------------------------------------------------------------- msp arm
+def run_msp(args):
+    import torch
+    import torch.distributed as dist
+
+    import synthetic as syn
+    import paper_2412_08981_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.load()
+    levels, w = syn.workload(args.workload)
+    kw = dict(delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], restart=w["restart"],
+              coef=w["coef"], wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
+    stream = torch.cuda.Stream()
+
+    def mu_of(i):
+        return syn.mu_draw(rank * 100000 + i)
+
+    def measure(precision, steps, warmup, profile_all=False):
+        h = P.Hierarchy(levels, precision=precision, **kw)
+        inst = h.assemble(mu_of(0), stream=stream)
+        n = levels[0].n_nodes
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        iters = []
+
+        def step(i):
+            inst.reassemble(mu_of(i))
+            inst.factor()
+            st = inst.solve(x, rtol=args.rtol)
+            iters.append(st["iterations"])
+            return st
+
+        # warm-up, with every kernel class timed to find the dominant one
+        inst.profile_enable(P.msp.KERNEL_CLASSES)
+        inst.profile_reset()
+        for i in range(warmup):
+            step(1000 + i)
+        prof = inst.profile()
+        dominant = max(prof, key=lambda k: prof[k]["ms"])
+        shares = {k: v["ms"] for k, v in prof.items()}
+        tot = sum(shares.values()) or 1.0
+        shares = {k: round(v / tot, 4) for k, v in shares.items() if v > 0}
+        inst.profile_enable([dominant])
+        inst.profile_reset()
+        iters.clear()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        clk = Clocks(local)
+        clk.start()
+        evs[0].record(stream)
+        for i in range(steps):
+            step(i)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        if world > 1:
+            dist.barrier()
+        ms = evs[0].elapsed_time(evs[-1])
+        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        prof = inst.profile()
+        launches = int(sum(v["launches"] for v in prof.values()))
+        out = dict(ms=ms, lat=lat, iters=list(iters), prof=prof, dominant=dominant,
+                   shares=shares, launches=launches, clocks=clocks, x=x.cpu().numpy())
+        # end to end through the host-buffer entry point
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        xnp = xh.numpy()
+        inst.solve_host(mu_of(0), xnp, rtol=args.rtol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(steps, 8))
+        for i in range(e2e_steps):
+            inst.solve_host(mu_of(i), xnp, rtol=args.rtol)
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * 8,
+                      "d2h_bytes_per_step": 8 * n}
+        inst.close()
+        h.close()
+        return out
+
+    res = measure(args.precision, args.steps, args.warmup)
+    ms = res["ms"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1e3)
+    mixed = None
+    if not args.no_mixed and args.precision == "f64":
+        mres = measure("f32", args.steps, args.warmup)
+        mms = mres["ms"]
+        if world > 1:
+            t = torch.tensor([mms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mms = float(t.item())
+        mval = args.steps * world / (mms / 1e3)
+        err = float(np.linalg.norm(mres["x"] - res["x"]) / np.linalg.norm(res["x"]))
+        mixed = {"precision": "f32 subdomain factors, FP64 outer loop/SpMV/coarsest",
+                 "value": mval, "unit": UNIT, "speedup_vs_f64": mval / value,
+                 "latency_ms": {"p50": float(np.percentile(mres["lat"], 50)),
+                                "p99": float(np.percentile(mres["lat"], 99))},
+                 "iterations_mean": float(np.mean(mres["iters"])),
+                 "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"]}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    prof = res["prof"][res["dominant"]]
+    is_flop = res["dominant"].startswith("ldlt")
+    dom_ms = prof["ms"] / max(1, prof["timed"])
+    if is_flop:
+        peak = FP64_PEAK_TFLOPS if args.precision == "f64" else FP32_PEAK_TFLOPS
+        achieved = prof["flops"] / max(1, prof["launches"]) / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": res["dominant"], "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x FMA/clk x 2 x 2.07 GHz (FP64 SIMT, no fast "
+                               "FP64 tensor path on GB300); probe measured 1.19 TFLOP/s FP64",
+                "traffic": traffic_for(res["dominant"], prof)}
+    else:
+        peak = measured_peak("hbm_gbs", 6755.1)
+        achieved = prof["bytes"] / max(1, prof["launches"]) / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": res["dominant"], "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": "MEASURED_PEAKS hbm_gbs",
+                "traffic": traffic_for(res["dominant"], prof)}
+    roof["avg_launch_ms"] = dom_ms
+    roof["time_shares_warmup"] = res["shares"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "description": DESCR.get(args.workload, ""),
+                   "parallelism": f"replicas x{world} (independent mu per rank)",
+                   "factor_precision": args.precision, "rtol": args.rtol,
+                   "l2": "inputs larger than L2 (subdomain factors of several GB)"},
+        "latency_ms": {"p50": float(np.percentile(res["lat"], 50)),
+                       "p99": float(np.percentile(res["lat"], 99))},
+        "iterations_mean": float(np.mean(res["iters"])),
+        "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"],
+        "roofline": roof,
+    }
+    if mixed:
+        line["mixed"] = mixed
+    if world == 1 and not args.no_cpu_baseline:
+        levels_, w_ = syn.workload(args.workload)
+        line["cpu_baseline"] = cpu_baseline(levels_, w_, mu_of(0),
+                                            int(round(np.mean(res["iters"]))), args.cpu_sample,
+                                            args.rtol)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2412_08981_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith("k_") and f.endswith(".cu"):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, prof):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else null)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("kernel_sources") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# -------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle timed on the host cores, on this arm's workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synthetic as syn
+    levels, w = syn.workload(args.workload)
+    iters = 10  # representative iteration count of the workload (GPU runs: 9-11)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(levels, w, syn.mu_draw(i), iters, max(4, args.cpu_sample // 3), args.rtol)
+        if i >= args.warmup:
+            vals.append(cb["seconds_per_solve"])
+    s = float(np.sum(vals))
+    value = len(vals) / s
+    cb["value"] = value
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * s / len(vals), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "description": DESCR.get(args.workload, "")},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_msp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * msp.h - C ABI of the GB300 library for the non-nested multilevel smoothed
+ * Schwarz preconditioner of arXiv 2412.08981, applied inside right-
+ * preconditioned FGMRES for P1 tetrahedral finite-element systems whose
+ * coefficient k(x; mu) changes with a parameter vector mu while the mesh
+ * hierarchy is reused.
+ *
+ * Conventions for every call:
+ *   - Return value: an msp_status; MSP_OK (0) on success.  On failure the
+ *     outputs are left untouched (msp_stats is always filled) and
+ *     msp_last_error() returns a message for the calling thread.
+ *   - Host pointers are caller-owned and only read during the call (they are
+ *     copied).  "device" pointers are caller-owned CUDA device memory on the
+ *     current device; the library never frees them.
+ *   - Library-owned device memory (hierarchy, per-parameter instance) comes
+ *     from msp_options.alloc / .free when given (the Python binding routes it
+ *     to PyTorch's caching allocator), else from cudaMalloc / cudaFree.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued on it; calls that return results to the host
+ *     (msp_solve, msp_solve_host) synchronise it.
+ *   - Vectors on a level hold one FP64 entry per mesh node (Dirichlet nodes
+ *     included), in the node order of that level's msp_level_desc.
+ *   - Level 0 is the finest mesh M_0; level L-1 is the coarsest.
+ */
+#ifndef MSP_H_
+#define MSP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSP_API __attribute__((visibility("default")))
+#else
+#define MSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum msp_status {
+  MSP_OK = 0,
+  MSP_PENDING = 1,             /* request still running (msp_poll) */
+  MSP_ERR_INVALID = -1,        /* bad argument or mesh; nothing was changed */
+  MSP_ERR_OOM = -2,            /* allocation failed or memory budget exceeded */
+  MSP_ERR_NOT_CONVERGED = -3,  /* FGMRES hit max_it or broke down; x holds the last iterate */
+  MSP_ERR_TIMEOUT = -4,        /* a bounded wait gave up */
+  MSP_ERR_CUDA = -5,           /* a CUDA runtime call failed */
+  MSP_ERR_INTERNAL = -6        /* a zero/non-finite pivot or a device-side check failed */
+} msp_status;
+
+/* Precision of the subdomain LU factors and their triangular solves.  The
+ * outer FGMRES, every SpMV, the transfers and the coarsest level stay FP64. */
+typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1 } msp_precision;
+
+/* Coefficient family k(x; mu), evaluated at each tet centroid x_c:
+ *   MSP_K_CONST : k = 1
+ *   MSP_K_COSEXP: k = exp(s * sum_{j=1..8} mu_j * 0.5 * cos(pi * a_j . x_c)),
+ *                 a_j integer wave vectors (msp_options.wave), s = coef_scale. */
+typedef enum msp_coef { MSP_K_CONST = 0, MSP_K_COSEXP = 1 } msp_coef;
+
+/* Right-hand side f of -div(k grad u) = f, integrated with the vertex rule
+ * b_a = sum_{T containing a} f(x_a) |T| / 4 (0 on Dirichlet nodes):
+ *   MSP_F_ONE  : f = 1
+ *   MSP_F_SINES: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) */
+typedef enum msp_load { MSP_F_ONE = 0, MSP_F_SINES = 1 } msp_load;
+
+/* One mesh level (Section 2.1: the mesh perspective M = (K, N) with one DoF
+ * per vertex, N = (1,0,0,0)).  All arrays are host memory, copied. */
+typedef struct msp_level_desc {
+  int32_t n_nodes;            /* number of vertices (= DoFs) */
+  const double* xyz;          /* [n_nodes][3] coordinates */
+  int32_t n_tets;             /* number of tetrahedra */
+  const int32_t* tets;        /* [n_tets][4] vertex ids, any orientation */
+  const uint8_t* dirichlet;   /* [n_nodes] 1 = homogeneous Dirichlet node */
+  const int32_t* owner;       /* [n_nodes] partition id of every vertex (Section 2.2:
+                                 the non-overlapping subdomains); required on every
+                                 level but the coarsest, ignored there */
+} msp_level_desc;
+
+typedef void* (*msp_alloc_fn)(void* ctx, size_t bytes, void* stream);
+typedef void (*msp_free_fn)(void* ctx, void* ptr, void* stream);
+
+typedef struct msp_options {
+  int32_t delta;              /* overlap: element layers added to each subdomain (>= 0) */
+  int32_t nu_pre, nu_post;    /* RAS smoothing steps before / after the coarse correction */
+  int32_t restart;            /* FGMRES restart length m (1..256) */
+  int32_t max_it;             /* FGMRES iteration cap */
+  int32_t factor_precision;   /* msp_precision */
+  int32_t coef_kind;          /* msp_coef */
+  int32_t wave[8][3];         /* a_j for MSP_K_COSEXP */
+  double coef_scale;          /* s for MSP_K_COSEXP */
+  int32_t load_kind;          /* msp_load */
+  int32_t host_only;          /* 1: build the host-side structures only (no device use);
+                                 only msp_hierarchy_copy / info work on such a handle */
+  size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
+  msp_alloc_fn alloc;         /* optional device allocator (NULL: cudaMalloc) */
+  msp_free_fn free;
+  void* alloc_ctx;
+} msp_options;
+
+/* Fills *o with the defaults: delta 1, nu 2/2, restart 30, max_it 1000, FP64
+ * factors, k = 1, f = 1, no budget, cudaMalloc. */
+MSP_API void msp_default_options(msp_options* o);
+
+typedef struct msp_hierarchy msp_hierarchy;
+typedef struct msp_instance msp_instance;
+
+typedef struct msp_stats {
+  int32_t status;             /* msp_status of the call */
+  int32_t iterations;         /* FGMRES iterations (V-cycles) */
+  double rel_residual;        /* ||b - A x|| / ||b||, true residual, FP64 */
+  double ms_assemble, ms_factor, ms_solve;  /* device time of each stage */
+} msp_stats;
+
+/* ---- set-up, once per hierarchy (Algorithm 2, lines "construct the hierarchy
+ * and provide J per level"; reuse across parameters, Sections 1 and 4.1) ----
+ * lv[0..nlevels-1], finest first, nlevels >= 1.  Builds on the host: the CSR
+ * pattern of every level, the element-to-nonzero contribution map, the
+ * delta-overlapping subdomains (Section 2.2), the dense-block extraction maps,
+ * point location and the barycentric interpolation P (coarse l+1 -> fine l)
+ * with its transpose; then uploads them and computes the per-tet geometry and
+ * the load vector on the device.  Errors: MSP_ERR_INVALID (degenerate tet,
+ * index out of range, missing owner array, bad option), MSP_ERR_OOM. */
+MSP_API int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_options* o,
+                       msp_hierarchy** out);
+MSP_API void msp_free_hierarchy(msp_hierarchy* h);
+
+/* Sizes of level `level`: n_nodes, nnz, number of subdomains (0 on the
+ * coarsest level), sum over subdomains of n_p (DoFs), and factor elements. */
+typedef struct msp_level_info {
+  int32_t n_nodes, n_tets;
+  int64_t nnz;
+  int32_t n_sub;
+  int64_t sub_dofs;           /* sum_p n_p (coarsest: interior DoFs) */
+  int64_t factor_elems;       /* elements of the tiled factor storage of this level */
+  int64_t P_nnz;              /* nnz of P from level+1 (0 on the coarsest) */
+} msp_level_info;
+MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
+
+/* ---- per parameter (Eq. (2)-(3) on every level) ----
+ * Creates an instance bound to `stream` and assembles J(mu) (CSR values) on
+ * every level.  mu: host array of n_mu doubles (n_mu == 8 for MSP_K_COSEXP,
+ * ignored for MSP_K_CONST).  Errors: MSP_ERR_INVALID (non-finite mu, wrong
+ * n_mu), MSP_ERR_OOM (allocation or budget). */
+MSP_API int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream,
+                 msp_instance** out);
+/* Re-assembles an existing instance for a new mu (no allocation). */
+MSP_API int msp_reassemble(msp_instance* inst, const double* mu, int n_mu);
+MSP_API void msp_free_instance(msp_instance* inst);
+
+/* Subdomain blocks J^delta_p = R J R^T of every smoothed level (Eq. (5)) and
+ * their unpivoted LU factors in symmetric form (unit lower L, D; U = D L^T),
+ * plus the FP64 factor of the coarsest level's interior block. */
+MSP_API int msp_factor(msp_instance* inst);
+
+/* One application of the V-cycle preconditioner of Algorithm 2 (z = B^{-1} r)
+ * with the fine->coarse transfer P^T, coarse->fine P and a direct coarsest
+ * solve.  r_dev, z_dev: device arrays of n_nodes(level 0) doubles; they must
+ * not overlap.  Requires msp_factor. */
+MSP_API int msp_apply(msp_instance* inst, const double* r_dev, double* z_dev, void* stream);
+
+/* Right-preconditioned FGMRES(restart) on J(mu) x = b (Eq. (4)), x_0 = 0,
+ * stopping when ||b - J x|| <= rtol ||b|| (true residual).  b_dev: device
+ * right-hand side, or NULL for the assembled load vector.  x_dev: device
+ * output.  Synchronises the instance stream.  MSP_ERR_NOT_CONVERGED leaves the
+ * last iterate in x_dev. */
+MSP_API int msp_solve(msp_instance* inst, const double* b_dev, double* x_dev, double rtol,
+              msp_stats* st);
+
+/* The whole per-parameter path from host memory: re-assemble for mu, factor,
+ * solve, copy the solution back.  b_host: NULL for the load vector, else
+ * n_nodes doubles; x_host: n_nodes doubles. */
+MSP_API int msp_solve_host(msp_instance* inst, const double* mu, int n_mu, const double* b_host,
+                   double* x_host, double rtol, msp_stats* st);
+
+/* ---- single operators of the path, for parity checks and composition ----
+ * y = op(x) on level `level`, device arrays, enqueued on `stream`:
+ *   MSP_OP_SPMV     y = J_l x                     (n_l -> n_l)
+ *   MSP_OP_RESIDUAL y = y - J_l x  (y holds r on entry)
+ *   MSP_OP_INTERP   y = P_l x      (n_{l+1} -> n_l), l < L-1
+ *   MSP_OP_RESTRICT y = P_l^T x    (n_l -> n_{l+1}), l < L-1
+ *   MSP_OP_RAS      y = B_l^{-1} x (Eq. (6)), l < L-1, needs msp_factor
+ *   MSP_OP_COARSE   y = J_{L-1}^{-1} x, l = L-1, needs msp_factor */
+typedef enum msp_op {
+  MSP_OP_SPMV = 0, MSP_OP_RESIDUAL = 1, MSP_OP_INTERP = 2, MSP_OP_RESTRICT = 3,
+  MSP_OP_RAS = 4, MSP_OP_COARSE = 5
+} msp_op;
+MSP_API int msp_apply_op(msp_instance* inst, int op, int level, const double* x_dev, double* y_dev,
+                 void* stream);
+
+/* ---- introspection: copy a named array into host memory ----
+ * Hierarchy arrays (index structures, host-resident):
+ *   MSP_ARR_ROWPTR, MSP_ARR_COL (int32), MSP_ARR_SUB_PTR, MSP_ARR_SUB_DOFS (int32),
+ *   MSP_ARR_SUB_OWN (uint8), MSP_ARR_P_ROWPTR, MSP_ARR_P_COL (int32),
+ *   MSP_ARR_P_VAL (double), MSP_ARR_PT_ROWPTR, MSP_ARR_PT_COL (int32),
+ *   MSP_ARR_PT_VAL (double), MSP_ARR_LOAD (double, device-resident b)
+ * Instance arrays (device-resident, copied back):
+ *   MSP_ARR_VAL (double CSR values), MSP_ARR_FACTOR (the tiled factor of
+ *   subdomain `sub` of `level`, sub = -1 for the coarsest level, in the
+ *   precision of that level's factors).
+ * bytes_out receives the array size; with dst == NULL only the size is
+ * returned.  MSP_ERR_INVALID if cap is too small. */
+typedef enum msp_array {
+  MSP_ARR_ROWPTR = 0, MSP_ARR_COL = 1, MSP_ARR_SUB_PTR = 2, MSP_ARR_SUB_DOFS = 3,
+  MSP_ARR_SUB_OWN = 4, MSP_ARR_P_ROWPTR = 5, MSP_ARR_P_COL = 6, MSP_ARR_P_VAL = 7,
+  MSP_ARR_PT_ROWPTR = 8, MSP_ARR_PT_COL = 9, MSP_ARR_PT_VAL = 10, MSP_ARR_LOAD = 11,
+  MSP_ARR_VAL = 12, MSP_ARR_FACTOR = 13
+} msp_array;
+MSP_API int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, size_t cap,
+                       size_t* bytes_out);
+MSP_API int msp_instance_copy(const msp_instance* inst, int level, int what, int sub, void* dst,
+                      size_t cap, size_t* bytes_out);
+
+/* Tile edge of the factor storage: every subdomain block of n_p DoFs is padded
+ * to NT = ceil(n_p / 64) tiles per side (padding is an identity block) and
+ * stored as its lower tile triangle, tile (I, J), J <= I, at index
+ * I (I + 1) / 2 + J, each tile 64 x 64 row-major.  In a diagonal tile the
+ * strict lower part holds L, the diagonal holds D and the strict upper part
+ * holds the transpose of the inverse of the unit lower diagonal block. */
+#define MSP_TILE 64
+
+/* ---- per-kernel accounting ----
+ * Every launch is counted per kernel class with its algorithmic bytes and
+ * flops (bytes the operation must move at least once, flops it must do).
+ * Classes in `class_mask` (bit = 1 << class) are also timed with CUDA events
+ * recorded around each launch on the launching stream. */
+typedef enum msp_kernel_class {
+  MSP_PK_ASSEMBLE = 0,     /* coefficient + assembly of J(mu), every level */
+  MSP_PK_EXTRACT = 1,      /* dense subdomain blocks from CSR */
+  MSP_PK_LDLT_DIAG = 2,    /* diagonal tile factorisation */
+  MSP_PK_LDLT_PANEL = 3,   /* panel solves */
+  MSP_PK_LDLT_TRAIL = 4,   /* trailing (Schur complement) updates */
+  MSP_PK_RAS = 5,          /* RAS application on level 0 */
+  MSP_PK_RAS_COARSER = 6,  /* RAS application on levels 1..L-2 */
+  MSP_PK_COARSE = 7,       /* coarsest-level direct solve */
+  MSP_PK_SPMV = 8,         /* J x and residuals */
+  MSP_PK_TRANSFER = 9,     /* P and P^T */
+  MSP_PK_VEC = 10,         /* Krylov dots, axpys, copies */
+  MSP_PK_COUNT = 11
+} msp_kernel_class;
+
+typedef struct msp_kernel_profile {
+  int64_t launches;        /* kernels launched */
+  double bytes;            /* algorithmic bytes of those launches */
+  double flops;            /* algorithmic flops of those launches */
+  int64_t timed;           /* launches covered by ms */
+  double ms;               /* summed CUDA-event duration of the timed launches */
+} msp_kernel_profile;
+
+MSP_API int msp_profile_enable(msp_instance* inst, uint32_t class_mask);
+MSP_API int msp_profile_reset(msp_instance* inst);
+MSP_API int msp_profile_read(msp_instance* inst, int kclass, msp_kernel_profile* out);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+MSP_API const char* msp_last_error(void);
+/* Library version string. */
+MSP_API const char* msp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSP_H_ */

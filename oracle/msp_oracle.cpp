@@ -237,6 +237,8 @@ int lu_factor(int n, double* A) {
   for (int k = 0; k < n; ++k) {
     double piv = A[(size_t)k * n + k];
     if (piv == 0.0 || !std::isfinite(piv)) return -1;
+    // rows are independent at fixed k (large blocks only; nested regions stay serial)
+#pragma omp parallel for schedule(static) if (n > 1024)
     for (int i = k + 1; i < n; ++i) {
       double l = A[(size_t)i * n + k] / piv;
       A[(size_t)i * n + k] = l;
@@ -645,6 +647,13 @@ int orc_factor(void* h) {
   return bad ? -1 : 0;
 }
 
+// Factor only the coarsest block.
+int orc_factor_coarsest(void* h) {
+  Oracle* o = static_cast<Oracle*>(h);
+  Level& L = o->lv.back();
+  return factor_sub(L.A, L.coarse) ? -1 : 0;
+}
+
 // Factor only the subdomains [p0, p1) of one level (used to time a sample).
 int orc_factor_range(void* h, int level, int p0, int p1) {
   Oracle* o = static_cast<Oracle*>(h);
@@ -671,11 +680,42 @@ int orc_ras_apply(void* h, int level, const double* r, double* z) {
   ras_apply(static_cast<Oracle*>(h)->lv[level], r, z);
   return 0;
 }
+// RAS contributions of the subdomains [p0, p1) only: z[owned] = A_p^{-1} r
+// (used to time a sample of the subdomain solves).
+int orc_ras_apply_range(void* h, int level, int p0, int p1, const double* r, double* z) {
+  Oracle* o = static_cast<Oracle*>(h);
+  const Level& L = o->lv[level];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int p = p0; p < p1; ++p) {
+    const Subdomain& S = L.subs[p];
+    int n = (int)S.dofs.size();
+    std::vector<double> t(n);
+    for (int li = 0; li < n; ++li) t[li] = r[S.dofs[li]];
+    lu_solve(n, S.lu.data(), t.data());
+    for (int li = 0; li < n; ++li)
+      if (S.own[li]) z[S.dofs[li]] = t[li];
+  }
+  return 0;
+}
+
 int orc_coarse_solve(void* h, const double* r, double* z) {
   Oracle* o = static_cast<Oracle*>(h);
   coarse_solve(o->lv.back(), r, z);
   return 0;
 }
+// Solve one subdomain block: y = A_p^{-1} r[V_p] (level `level`, subdomain p;
+// p = -1 for the coarsest block).  y has n_p entries.
+int orc_sub_solve(void* h, int level, int p, const double* r, double* y) {
+  Oracle* o = static_cast<Oracle*>(h);
+  const Level& L = o->lv[level];
+  const Subdomain& S = (p < 0) ? L.coarse : L.subs[p];
+  int n = (int)S.dofs.size();
+  if (S.lu.size() != (size_t)n * n) return -1;
+  for (int li = 0; li < n; ++li) y[li] = r[S.dofs[li]];
+  lu_solve(n, S.lu.data(), y);
+  return 0;
+}
+
 int orc_vcycle(void* h, const double* r, double* z) {
   vcycle(*static_cast<Oracle*>(h), r, z);
   return 0;

@@ -45,10 +45,13 @@ def lib():
                 getattr(L, name).argtypes = [vp, vp]
             L.orc_factor.argtypes = [vp]
             L.orc_factor_range.argtypes = [vp, ip, ip, ip]
+            L.orc_factor_coarsest.argtypes = [vp]
             for name in ("orc_spmv", "orc_interp", "orc_restrict", "orc_ras_apply"):
                 getattr(L, name).argtypes = [vp, ip, vp, vp]
             L.orc_coarse_solve.argtypes = [vp, vp, vp]
+            L.orc_ras_apply_range.argtypes = [vp, ip, ip, ip, vp, vp]
             L.orc_vcycle.argtypes = [vp, vp, vp]
+            L.orc_sub_solve.argtypes = [vp, ip, ip, vp, vp]
             L.orc_fgmres.argtypes = [vp, vp, vp, dp, ip, ip, ip, vp, vp]
             L.orc_get.restype = C.c_long
             L.orc_get.argtypes = [vp, C.c_char_p, ip, ip, C.POINTER(C.c_void_p)]
@@ -145,6 +148,10 @@ class Oracle:
         if lib().orc_factor(self.h):
             raise ValueError("oracle: zero pivot")
 
+    def factor_coarsest(self):
+        if lib().orc_factor_coarsest(self.h):
+            raise ValueError("oracle: zero pivot")
+
     def factor_range(self, level, p0, p1):
         return lib().orc_factor_range(self.h, level, p0, p1)
 
@@ -166,11 +173,26 @@ class Oracle:
     def ras_apply(self, r, level=0):
         return self._vec_op(lib().orc_ras_apply, level, r, self.n[level])
 
+    def ras_apply_range(self, r, level, p0, p1):
+        r = np.ascontiguousarray(r, np.float64)
+        z = np.zeros(self.n[level])
+        lib().orc_ras_apply_range(self.h, int(level), int(p0), int(p1), _p(r), _p(z))
+        return z
+
     def coarse_solve(self, r):
         r = np.ascontiguousarray(r, np.float64)
         z = np.zeros(self.n[-1])
         lib().orc_coarse_solve(self.h, _p(r), _p(z))
         return z
+
+    def sub_solve(self, r, level, p):
+        """y = A_p^{-1} r[V_p] for one factored subdomain (p = -1: coarsest block)."""
+        r = np.ascontiguousarray(r, np.float64)
+        n = (self.get("sub_dofs", level, p)).size
+        y = np.zeros(n)
+        if lib().orc_sub_solve(self.h, int(level), int(p), _p(r), _p(y)):
+            raise ValueError("subdomain not factored")
+        return y
 
     def vcycle(self, r):
         r = np.ascontiguousarray(r, np.float64)

@@ -1,0 +1,435 @@
+// Dense subdomain kernels of the msp library (Section 2.2, Eq. (5)-(6)):
+//   * extraction of the blocks J^delta_p = R J R^T into tiled storage,
+//   * batched, blocked, right-looking unpivoted LU of every block in its
+//     symmetric form J_p = L D L^T (U = D L^T; the blocks are SPD, so no
+//     pivoting is needed and half of the LU work is skipped),
+//   * the RAS application z = sum_p R0_p^T (L D L^T)^{-1} R_p t.
+//
+// Tile layout (see msp.h): 64 x 64 row-major tiles, lower tile triangle of
+// each block, tile (I, J) at index I (I + 1) / 2 + J.  Diagonal tiles hold L
+// below the diagonal, D on it and X^T above it, X = inverse of the unit lower
+// diagonal block of L; the triangular solves use X, so every step is a dense
+// product and the only sequential dependency is between tile rows.
+//
+// On GB300 FP64 runs on the SIMT pipe at ~1/64 of the FP32 rate (there is no
+// fast FP64 tensor path), so the FP64 kernels are ALU-bound: their design
+// keeps the FMA pipe fed from shared memory and avoids idle lanes.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "msp_kernels.h"
+
+namespace msp {
+namespace {
+
+constexpr int T64 = 64;
+constexpr int TE = T64 * T64;
+
+__device__ inline int64_t tri(int i) { return (int64_t)i * (i + 1) / 2; }
+
+template <typename T> struct Acc { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+// ------------------------------------------------------------ extraction
+template <typename T>
+__global__ void k_zero(T* __restrict__ p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __restrict__ nz,
+                          const double* __restrict__ val, int64_t nent, T* __restrict__ fac) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  int q = nz[e];
+  fac[pos[e]] = (T)(q >= 0 ? val[q] : 1.0);
+}
+
+// ---------------------------------------------------- diagonal tile LDL^T
+// One block per active subdomain.  Factors tile (k, k) in FP64 shared memory
+// (column by column: scale the column by 1/d, then update the trailing lower
+// triangle with l_r d l_s), then forms X = L^{-1} one column per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac,
+                                                   const int64_t* __restrict__ fac_off,
+                                                   const int32_t* __restrict__ order, int k,
+                                                   int* __restrict__ info) {
+  extern __shared__ double sm[];
+  double* A = sm;               // [64][65]
+  double* X = sm + 64 * 65;     // [64][65]
+  const int p = order[blockIdx.x];
+  T* tile = fac + fac_off[p] + (tri(k) + k) * TE;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TE; e += blockDim.x) {
+    int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (c <= r) ? (double)tile[e] : 0.0;
+  }
+  __syncthreads();
+  const int row = tid >> 2, sub = tid & 3;
+  for (int c = 0; c < T64; ++c) {
+    const double d = A[c * 65 + c];
+    if (tid == 0 && !(d > 0.0 && d < 1e300)) atomicOr(info, 1);
+    const double dinv = 1.0 / d;
+    __syncthreads();
+    if (row > c && sub == 0) A[row * 65 + c] *= dinv;
+    __syncthreads();
+    if (row > c) {
+      const double lr = A[row * 65 + c] * d;
+      for (int s = c + 1 + sub; s <= row; s += 4) A[row * 65 + s] -= lr * A[s * 65 + c];
+    }
+    __syncthreads();
+  }
+  // X = L^{-1}, unit lower: X[i][j] = -sum_{m=j}^{i-1} L[i][m] X[m][j]
+  if (tid < T64) {
+    const int j = tid;
+    for (int i = 0; i < T64; ++i) X[i * 65 + j] = (i == j) ? 1.0 : 0.0;
+    for (int i = j + 1; i < T64; ++i) {
+      double s = 0.0;
+      for (int m = j; m < i; ++m) s -= A[i * 65 + m] * X[m * 65 + j];
+      X[i * 65 + j] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < TE; e += blockDim.x) {
+    int r = e >> 6, c = e & 63;
+    double v = (c <= r) ? A[r * 65 + c] : X[c * 65 + r];
+    tile[e] = (T)v;
+  }
+}
+
+// ----------------------------------------------------------- panel solve
+// L_ik = A_ik X^T D^{-1} for the tiles below the diagonal tile of step k.
+// Warp w owns the 8 columns 8w..8w+7 (X^T is upper triangular, so its loop
+// stops at 8w+7); each lane owns 2 rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac,
+                                                    const int64_t* __restrict__ fac_off,
+                                                    const int32_t* __restrict__ nt,
+                                                    const int32_t* __restrict__ order, int k) {
+  using AT = typename Acc<T>::type;
+  const int p = order[blockIdx.y];
+  const int NT = nt[p];
+  const int i = k + 1 + blockIdx.x;
+  if (i >= NT) return;
+  extern __shared__ unsigned char smraw[];
+  AT* A = reinterpret_cast<AT*>(smraw);   // [64][65] panel tile
+  AT* Xt = A + 64 * 65;                   // [64][64] X^T (upper, unit diagonal)
+  AT* Dinv = Xt + 64 * 64;                // [64]
+  T* base = fac + fac_off[p];
+  const T* dtile = base + (tri(k) + k) * TE;
+  T* ptile = base + (tri(i) + k) * TE;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TE; e += blockDim.x) {
+    int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (AT)ptile[e];
+    AT xv = (r < c) ? (AT)dtile[e] : (r == c ? AT(1) : AT(0));
+    Xt[e] = xv;
+    if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const int c0 = warp * 8;
+  const int r0 = lane, r1 = lane + 32;
+  AT w0[8], w1[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { w0[q] = 0; w1[q] = 0; }
+  const int mend = c0 + 8;
+  for (int m = 0; m < mend; ++m) {
+    AT a0 = A[r0 * 65 + m], a1 = A[r1 * 65 + m];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      AT x = Xt[m * 64 + c0 + q];
+      w0[q] += a0 * x;
+      w1[q] += a1 * x;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    ptile[r0 * 64 + c0 + q] = (T)(w0[q] * Dinv[c0 + q]);
+    ptile[r1 * 64 + c0 + q] = (T)(w1[q] * Dinv[c0 + q]);
+  }
+}
+
+// -------------------------------------------------------- trailing update
+// A_ij -= (L_ik D_k) L_jk^T for k < j <= i < NT.  One block per (i, j) pair;
+// each thread accumulates a 4x4 register block from k-major shared tiles.
+__device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
+  int x = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((x + 1) * (x + 2) / 2 <= t) ++x;
+  while (x * (x + 1) / 2 > t) --x;
+  a = x;
+  b = t - x * (x + 1) / 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac,
+                                                    const int64_t* __restrict__ fac_off,
+                                                    const int32_t* __restrict__ nt,
+                                                    const int32_t* __restrict__ order, int k) {
+  using AT = typename Acc<T>::type;
+  const int p = order[blockIdx.y];
+  const int NT = nt[p];
+  const int rem = NT - k - 1;
+  if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
+  int a, b;
+  pair_of(blockIdx.x, a, b);
+  const int i = k + 1 + a, j = k + 1 + b;
+  extern __shared__ unsigned char smraw[];
+  constexpr int LD = 68;
+  AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][LD] = L_ik[r][m] * d_m
+  AT* Lt = Wt + 64 * LD;                  // [64 m][LD] = L_jk[c][m]
+  T* base = fac + fac_off[p];
+  const T* dt = base + (tri(k) + k) * TE;
+  const T* li = base + (tri(i) + k) * TE;
+  const T* lj = base + (tri(j) + k) * TE;
+  T* out = base + (tri(i) + j) * TE;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TE; e += blockDim.x) {
+    int r = e >> 6, m = e & 63;
+    AT d = (AT)dt[m * 65];
+    Wt[m * LD + r] = (AT)li[e] * d;
+    Lt[m * LD + r] = (AT)lj[e];
+  }
+  __syncthreads();
+  const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;
+  if (i == j && c0 > r0 + 3) return;  // strictly above the diagonal of a diagonal tile
+  AT acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+#pragma unroll 4
+  for (int m = 0; m < T64; ++m) {
+    AT av[4], bv[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      av[x] = Wt[m * LD + r0 + x];
+      bv[x] = Lt[m * LD + c0 + x];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * bv[y];
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      int r = r0 + x, c = c0 + y;
+      if (i != j || c <= r) {
+        T* o = out + r * 64 + c;
+        *o = (T)((AT)*o - acc[x][y]);
+      }
+    }
+}
+
+// -------------------------------------------------------------- RAS solve
+// One block (8 warps) per subdomain; extra blocks copy t into z on the
+// Dirichlet nodes.  Gather t[dofs] -> y; forward sweep over tile rows
+// (y_I = X_II (t_I - sum_{J<I} L_IJ y_J)); y /= D; backward sweep
+// (x_I = X_II^T (y_I - sum_{J>I} L_JI^T x_J)); scatter the owned entries.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ras_solve(
+    const T* __restrict__ fac, const int64_t* __restrict__ fac_off, const int32_t* __restrict__ nt,
+    const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ dofs,
+    const uint8_t* __restrict__ own, int nsub, const int32_t* __restrict__ dir_list, int ndir,
+    const double* __restrict__ t, double* __restrict__ z, int add) {
+  using AT = typename Acc<T>::type;
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x >= nsub) {
+    int d = (blockIdx.x - nsub) * blockDim.x + tid;
+    if (d < ndir) {
+      int g = dir_list[d];
+      z[g] = add ? z[g] + t[g] : t[g];
+    }
+    return;
+  }
+  const int p = blockIdx.x;
+  const int NT = nt[p];
+  const int off = sub_ptr[p];
+  const int np_ = sub_ptr[p + 1] - off;
+  extern __shared__ unsigned char smraw[];
+  AT* y = reinterpret_cast<AT*>(smraw);   // [NT*64]
+  AT* acc = y + NT * 64;                  // [64]
+  AT* part = acc + 64;                    // [8][64]
+  const T* base = fac + fac_off[p];
+  for (int li = tid; li < NT * 64; li += blockDim.x)
+    y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  // forward
+  for (int I = 0; I < NT; ++I) {
+    AT s[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = 0;
+    const T* rowt = base + tri(I) * TE;
+    for (int J = 0; J < I; ++J) {
+      const T* tl = rowt + (int64_t)J * TE;
+      AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int r = warp * 8 + q;
+        s[q] += (AT)tl[r * 64 + lane] * y0 + (AT)tl[r * 64 + lane + 32] * y1;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      AT v = s[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) acc[warp * 8 + q] = y[I * 64 + warp * 8 + q] - v;
+    }
+    __syncthreads();
+    // y_I = X acc, X[b][a] = dtile[a][b] for a < b (upper part of the diagonal tile)
+    const T* dtl = rowt + (int64_t)I * TE;
+    {
+      const int bcol = tid & 63, pr = tid >> 6;  // 4 parts over a
+      AT v = 0;
+      for (int a = pr * 16; a < pr * 16 + 16; ++a)
+        if (a < bcol) v += (AT)dtl[a * 64 + bcol] * acc[a];
+      part[pr * 64 + bcol] = v;
+    }
+    __syncthreads();
+    if (tid < 64) y[I * 64 + tid] = acc[tid] + part[tid] + part[64 + tid] + part[128 + tid] + part[192 + tid];
+    __syncthreads();
+  }
+  // diagonal scaling
+  for (int li = tid; li < NT * 64; li += blockDim.x) {
+    int I = li >> 6, r = li & 63;
+    y[li] = y[li] / (AT)base[(tri(I) + I) * TE + r * 65];
+  }
+  __syncthreads();
+  // backward
+  for (int I = NT - 1; I >= 0; --I) {
+    AT s0 = 0, s1 = 0;
+    for (int J = I + 1; J < NT; ++J) {
+      const T* tl = base + (tri(J) + I) * TE;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int r = warp * 8 + q;
+        AT xr = y[J * 64 + r];
+        s0 += (AT)tl[r * 64 + lane] * xr;
+        s1 += (AT)tl[r * 64 + lane + 32] * xr;
+      }
+    }
+    part[warp * 64 + lane] = s0;
+    part[warp * 64 + lane + 32] = s1;
+    __syncthreads();
+    if (tid < 64) {
+      AT v = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += part[w * 64 + tid];
+      acc[tid] = y[I * 64 + tid] - v;
+    }
+    __syncthreads();
+    // x_I[a] = acc[a] + sum_{b>a} X[b][a] acc[b] = acc[a] + sum_{b>a} dtile[a][b] acc[b]
+    const T* dtl = base + (tri(I) + I) * TE;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int a = warp * 8 + q;
+      AT v = 0;
+      if (lane > a) v += (AT)dtl[a * 64 + lane] * acc[lane];
+      if (lane + 32 > a) v += (AT)dtl[a * 64 + lane + 32] * acc[lane + 32];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) y[I * 64 + a] = acc[a] + v;
+    }
+    __syncthreads();
+  }
+  for (int li = tid; li < np_; li += blockDim.x) {
+    if (own[off + li]) {
+      int g = dofs[off + li];
+      z[g] = add ? z[g] + (double)y[li] : (double)y[li];
+    }
+  }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+template <typename T>
+void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
+                    const double* val, int64_t fac_elems, T* fac, cudaStream_t s) {
+  if (fac_elems > 0) k_zero<T><<<152 * 8, 256, 0, s>>>(fac, fac_elems);
+  if (nent > 0) k_scatter<T><<<nblk(nent, 256), 256, 0, s>>>(ext_pos, ext_nz, val, nent, fac);
+}
+
+template <typename T>
+void launch_ldlt_diag(T* fac, const int64_t* fac_off, const int32_t* order, int nactive, int k,
+                      int* info, cudaStream_t s) {
+  if (nactive <= 0) return;
+  size_t smem = 2 * 64 * 65 * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_ldlt_diag<T><<<nactive, 256, smem, s>>>(fac, fac_off, order, k, info);
+}
+
+template <typename T>
+void launch_ldlt_panel(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
+                       int nactive, int k, int max_rows, cudaStream_t s) {
+  if (nactive <= 0 || max_rows <= 0) return;
+  using AT = typename Acc<T>::type;
+  size_t smem = (64 * 65 + 64 * 64 + 64) * sizeof(AT);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_ldlt_panel<T><<<dim3(max_rows, nactive), 256, smem, s>>>(fac, fac_off, nt, order, k);
+}
+
+template <typename T>
+void launch_ldlt_trail(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
+                       int nactive, int k, int max_pairs, cudaStream_t s) {
+  if (nactive <= 0 || max_pairs <= 0) return;
+  using AT = typename Acc<T>::type;
+  size_t smem = 2 * 64 * 68 * sizeof(AT);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_ldlt_trail<T><<<dim3(max_pairs, nactive), 256, smem, s>>>(fac, fac_off, nt, order, k);
+}
+
+template <typename T>
+void launch_ras_solve(const T* fac, const int64_t* fac_off, const int32_t* nt,
+                      const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int nsub,
+                      int max_nt, const int32_t* dir_list, int ndir, const double* t, double* z,
+                      int add, cudaStream_t s) {
+  using AT = typename Acc<T>::type;
+  size_t smem = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  unsigned nb = (unsigned)nsub + nblk(ndir, 256);
+  if (nb == 0) return;
+  k_ras_solve<T><<<nb, 256, smem, s>>>(fac, fac_off, nt, sub_ptr, dofs, own, nsub, dir_list, ndir,
+                                       t, z, add);
+}
+
+#define MSP_INST(T)                                                                              \
+  template void launch_extract<T>(const int64_t*, const int32_t*, int64_t, const double*,        \
+                                  int64_t, T*, cudaStream_t);                                    \
+  template void launch_ldlt_diag<T>(T*, const int64_t*, const int32_t*, int, int, int*,          \
+                                    cudaStream_t);                                               \
+  template void launch_ldlt_panel<T>(T*, const int64_t*, const int32_t*, const int32_t*, int,    \
+                                     int, int, cudaStream_t);                                    \
+  template void launch_ldlt_trail<T>(T*, const int64_t*, const int32_t*, const int32_t*, int,    \
+                                     int, int, cudaStream_t);                                    \
+  template void launch_ras_solve<T>(const T*, const int64_t*, const int32_t*, const int32_t*,    \
+                                    const int32_t*, const uint8_t*, int, int, const int32_t*,    \
+                                    int, const double*, double*, int, cudaStream_t);
+MSP_INST(double)
+MSP_INST(float)
+
+}  // namespace msp

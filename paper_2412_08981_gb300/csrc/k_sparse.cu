@@ -1,0 +1,302 @@
+// Sparse and vector kernels of the msp library: per-tet geometry, load vector,
+// coefficient, assembly of J(mu) into CSR, CSR SpMV (J, P, P^T) and the
+// Krylov reductions.  All FP64; every reduction has a fixed order, so results
+// are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "msp_kernels.h"
+
+namespace msp {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------- geometry
+// lambda = J^{-1}(x - x0), J = [x1-x0 | x2-x0 | x3-x0]; the rows of J^{-1} are
+// the gradients of lambda_1..3 (cofactors / det), grad lambda_0 = -sum.
+__global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
+                               int m, double* __restrict__ S, double* __restrict__ vol,
+                               double* __restrict__ cen, int* bad) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  int4 t = reinterpret_cast<const int4*>(tets)[e];
+  double p[4][3];
+  const int v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p[a][d] = xyz[3 * (int64_t)v[a] + d];
+  double u[3], w[3], q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    u[d] = p[1][d] - p[0][d];
+    w[d] = p[2][d] - p[0][d];
+    q[d] = p[3][d] - p[0][d];
+  }
+  // cofactor rows
+  double g[4][3];
+  g[1][0] = w[1] * q[2] - w[2] * q[1];
+  g[1][1] = w[2] * q[0] - w[0] * q[2];
+  g[1][2] = w[0] * q[1] - w[1] * q[0];
+  g[2][0] = q[1] * u[2] - q[2] * u[1];
+  g[2][1] = q[2] * u[0] - q[0] * u[2];
+  g[2][2] = q[0] * u[1] - q[1] * u[0];
+  g[3][0] = u[1] * w[2] - u[2] * w[1];
+  g[3][1] = u[2] * w[0] - u[0] * w[2];
+  g[3][2] = u[0] * w[1] - u[1] * w[0];
+  double det = u[0] * g[1][0] + u[1] * g[1][1] + u[2] * g[1][2];
+  double vv = fabs(det) / 6.0;
+  if (!(vv > 0.0)) atomicOr(bad, 1);
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g[a][d] /= det;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+  int s = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      double dd = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+      S[(int64_t)e * 10 + s] = vv * dd;
+      ++s;
+    }
+  vol[e] = vv;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cen[3 * (int64_t)e + d] = (p[0][d] + p[1][d] + p[2][d] + p[3][d]) / 4.0;
+}
+
+__device__ inline double load_f(int kind, double x, double y, double z) {
+  if (kind == 0) return 1.0;
+  return 3.0 * kPi * kPi * sin(kPi * x) * sin(kPi * y) * sin(kPi * z);
+}
+
+// The incident tets of node i are exactly the contributions to its diagonal
+// nonzero (ascending e), so the load sums over that list.
+__global__ void k_load_vector(const double* __restrict__ xyz, const uint8_t* __restrict__ dir,
+                              const int32_t* __restrict__ diag, const int32_t* __restrict__ cptr,
+                              const int32_t* __restrict__ contrib, const double* __restrict__ vol,
+                              int n, int kind, double* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (dir[i]) {
+    b[i] = 0.0;
+    return;
+  }
+  double f = load_f(kind, xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2]);
+  int q = diag[i];
+  double s = 0.0;
+  for (int c = cptr[q]; c < cptr[q + 1]; ++c) s += f * vol[contrib[c] / 10] / 4.0;
+  b[i] = s;
+}
+
+__global__ void k_coefficient(const double* __restrict__ cen, int m, int kind,
+                              const double* __restrict__ mu, const int32_t* __restrict__ wave,
+                              double scale, double* __restrict__ k) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  if (kind == 0) {
+    k[e] = 1.0;
+    return;
+  }
+  double x = cen[3 * (int64_t)e], y = cen[3 * (int64_t)e + 1], z = cen[3 * (int64_t)e + 2];
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    double ax = wave[3 * j] * x + wave[3 * j + 1] * y + wave[3 * j + 2] * z;
+    s += mu[j] * 0.5 * cos(kPi * ax);
+  }
+  k[e] = exp(scale * s);
+}
+
+__global__ void k_assemble(const int32_t* __restrict__ cptr, const int32_t* __restrict__ contrib,
+                           const uint8_t* __restrict__ flag, const double* __restrict__ k,
+                           const double* __restrict__ S, int64_t nnz, double* __restrict__ val) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  uint8_t f = flag[q];
+  double s = 0.0;
+  if (f == 0) {
+    for (int c = cptr[q]; c < cptr[q + 1]; ++c) {
+      int id = contrib[c];
+      s += k[id / 10] * S[id];
+    }
+  } else if (f == 1) {
+    s = 1.0;
+  }
+  val[q] = s;
+}
+
+// ---------------------------------------------------------------- SpMV
+// LPR lanes per row, rows packed into warps; each row's partial sums are
+// combined by a fixed butterfly over its lane group.
+template <int LPR>
+__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, int nrows, const double* __restrict__ x,
+                       double* __restrict__ y, const double* __restrict__ r, int mode) {
+  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t row = gt / LPR;
+  int lane = threadIdx.x % LPR;
+  const bool valid = row < nrows;  // no early exit: every lane joins the shuffles
+  double s = 0.0;
+  if (valid) {
+    int b = rowptr[row], e = rowptr[row + 1];
+    for (int q = b + lane; q < e; q += LPR) s += val[q] * x[col[q]];
+  }
+#pragma unroll
+  for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LPR);
+  if (valid && lane == 0) {
+    switch (mode) {
+      case SPMV_SET: y[row] = s; break;
+      case SPMV_SUB_FROM: y[row] = y[row] - s; break;
+      case SPMV_ADD: y[row] = y[row] + s; break;
+      default: y[row] = r[row] - s; break;
+    }
+  }
+}
+
+// ------------------------------------------------------------- vectors
+// Stage 1: block b of vector i sums a strided slice of V_i . w.
+__global__ void k_multidot_part(const double* __restrict__ V, int64_t ld,
+                                const double* __restrict__ w, int64_t n,
+                                double* __restrict__ part) {
+  int i = blockIdx.y;
+  const double* v = V + ld * i;
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    s += v[k] * w[k];
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int nw = blockDim.x >> 5;
+    s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Stage 2: one warp per vector sums its kDotBlocks partials in a fixed order.
+__global__ void k_multidot_final(const double* __restrict__ part, int nparts,
+                                 double* __restrict__ out) {
+  int i = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += 32) s += part[(int64_t)i * nparts + b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) out[i] = s;
+}
+
+__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int nv,
+                             const double* __restrict__ h, double* __restrict__ w, int64_t n,
+                             double sign) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < nv; ++i) s += h[i] * V[ld * i + k];
+  w[k] += sign * s;
+}
+
+__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) y[k] = a * x[k];
+}
+
+__global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) y[k] += a * x[k];
+}
+
+__global__ void k_fill(double* __restrict__ y, double v, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) y[k] = v;
+}
+
+__global__ void k_copy(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) y[k] = x[k];
+}
+
+__global__ void k_add(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) b[k] += a[k];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, double* S, double* vol,
+                         double* cen, int* bad, cudaStream_t s) {
+  if (m > 0) k_tet_geometry<<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, S, vol, cen, bad);
+}
+
+void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,
+                        const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
+                        int load_kind, double* b, cudaStream_t s) {
+  if (n > 0)
+    k_load_vector<<<nblk(n, 256), 256, 0, s>>>(xyz, dir, diag, cptr, contrib, vol, n, load_kind, b);
+}
+
+void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
+                        const int32_t* wave24, double scale, double* k, cudaStream_t s) {
+  if (m > 0) k_coefficient<<<nblk(m, 256), 256, 0, s>>>(cen, m, coef_kind, mu8, wave24, scale, k);
+}
+
+void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,
+                     const double* k, const double* S, int64_t nnz, double* val, cudaStream_t s) {
+  if (nnz > 0) k_assemble<<<nblk(nnz, 256), 256, 0, s>>>(cptr, contrib, nzflag, k, S, nnz, val);
+}
+
+void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
+                 const double* x, double* y, const double* r, int mode, int avg_row_nnz,
+                 cudaStream_t s) {
+  if (nrows <= 0) return;
+  if (avg_row_nnz <= 5)
+    k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+  else if (avg_row_nnz <= 20)
+    k_spmv<8><<<nblk((int64_t)nrows * 8, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+  else
+    k_spmv<16><<<nblk((int64_t)nrows * 16, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+}
+
+void launch_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n,
+                     double* part, double* out, cudaStream_t s) {
+  if (nv <= 0) return;
+  k_multidot_part<<<dim3(kDotBlocks, nv), 256, 0, s>>>(V, ld, w, n, part);
+  k_multidot_final<<<nv, 32, 0, s>>>(part, kDotBlocks, out);
+}
+
+void launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w,
+                       int64_t n, double sign, cudaStream_t s) {
+  if (nv > 0 && n > 0) k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(V, ld, nv, h, w, n, sign);
+}
+
+void launch_scale(const double* x, double alpha, double* y, int64_t n, cudaStream_t s) {
+  if (n > 0) k_scale<<<nblk(n, 256), 256, 0, s>>>(x, alpha, y, n);
+}
+
+void launch_axpy(double alpha, const double* x, double* y, int64_t n, cudaStream_t s) {
+  if (n > 0) k_axpy<<<nblk(n, 256), 256, 0, s>>>(alpha, x, y, n);
+}
+
+void launch_add_vec(const double* a, double* b, int64_t n, cudaStream_t s) {
+  if (n > 0) k_add<<<nblk(n, 256), 256, 0, s>>>(a, b, n);
+}
+
+void launch_fill(double* y, double v, int64_t n, cudaStream_t s) {
+  if (n > 0) k_fill<<<nblk(n, 256), 256, 0, s>>>(y, v, n);
+}
+
+void launch_copy(const double* x, double* y, int64_t n, cudaStream_t s) {
+  if (n > 0) k_copy<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
+}
+
+}  // namespace msp

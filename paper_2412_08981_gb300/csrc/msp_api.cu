@@ -1,0 +1,985 @@
+// C ABI of the msp library: device state, per-parameter assembly and
+// factorisation, the V-cycle of Algorithm 2 and right-preconditioned FGMRES
+// (Eq. (4)).  Every arithmetic step runs in the kernels of k_sparse.cu and
+// k_dense.cu; this file only allocates, uploads, orders launches on the
+// instance stream and runs the small Hessenberg least-squares update of
+// FGMRES on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "msp.h"
+#include "msp_internal.h"
+#include "msp_kernels.h"
+#include "msp_profile.h"
+
+namespace msp {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define MSP_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(MSP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+// ------------------------------------------------------- device memory
+struct Allocator {
+  msp_alloc_fn a = nullptr;
+  msp_free_fn f = nullptr;
+  void* ctx = nullptr;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (a) return a(ctx, bytes, nullptr);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    if (f) f(ctx, p, nullptr);
+    else cudaFree(p);
+  }
+};
+
+// Owns a list of device allocations made through one Allocator.
+struct DevArena {
+  Allocator al;
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  bool ok = true;
+  template <typename T>
+  T* alloc(size_t n) {
+    size_t b = n * sizeof(T);
+    void* p = al.get(b);
+    if (!p) {
+      ok = false;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (p && !v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      ok = false;
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) al.put(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+struct DevLevel {
+  int n = 0, m = 0;
+  int64_t nnz = 0;
+  int avg_A = 15, avg_P = 4, avg_PT = 32;
+  int32_t *rowptr = nullptr, *col = nullptr, *diag = nullptr, *cptr = nullptr, *contrib = nullptr;
+  uint8_t *nzflag = nullptr, *dir = nullptr;
+  int32_t* dir_list = nullptr;
+  int ndir = 0;
+  double *xyz = nullptr, *S = nullptr, *vol = nullptr, *cen = nullptr;
+  int32_t* tets = nullptr;
+  double* b = nullptr;  // load vector
+  // subdomains
+  int nsub = 0, max_nt = 0;
+  int32_t *sub_ptr = nullptr, *sub_dofs = nullptr, *sub_nt = nullptr, *sub_order = nullptr;
+  uint8_t* sub_own = nullptr;
+  int64_t* fac_off = nullptr;
+  int64_t fac_elems = 0;
+  int64_t* ext_pos = nullptr;
+  int32_t* ext_nz = nullptr;
+  int64_t next = 0;
+  std::vector<int> active;        // active[k] = #subdomains with NT > k
+  std::vector<double> trail_flops;  // algorithmic flops of trailing step k
+  double ldlt_flops = 0;          // sum_p n_p^3 / 3
+  int64_t sum_np = 0, sum_np2 = 0, sum_owned = 0;
+  // transfer from level+1
+  int64_t P_nnz = 0;
+  int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
+  double *P_val = nullptr, *PT_val = nullptr;
+};
+
+}  // namespace msp
+
+using namespace msp;
+
+struct msp_hierarchy {
+  msp_options opt{};
+  std::vector<HostLevel> host;
+  std::vector<DevLevel> dev;
+  DevArena arena;
+  int32_t* wave = nullptr;
+  int device = 0;
+  bool host_only = false;
+  std::mutex mu;
+  size_t instance_bytes = 0;  // bytes held by live instances (budget)
+};
+
+struct msp_instance {
+  msp_hierarchy* h = nullptr;
+  cudaStream_t stream = nullptr;
+  DevArena arena;
+  size_t charged = 0;
+  double* mu = nullptr;
+  std::vector<double*> k, val, r, z, t;
+  std::vector<void*> fac;  // per level, T = double or float
+  int* info = nullptr;
+  int m = 30;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
+  double* xb = nullptr;  // device buffers used by msp_solve_host
+  double* hpin = nullptr;  // pinned host staging
+  bool assembled = false, factored = false;
+  Profile prof;
+};
+
+namespace msp {
+namespace {
+
+bool level_f32(const msp_hierarchy* h, int l) {
+  return h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->dev.size();
+}
+
+void finish_level_stats(const HostLevel& H, DevLevel& D) {
+  D.max_nt = 0;
+  for (int p = 0; p < H.nsub; ++p) D.max_nt = std::max(D.max_nt, H.sub_nt[p]);
+  D.active.assign(D.max_nt + 1, 0);
+  D.trail_flops.assign(D.max_nt + 1, 0.0);
+  D.ldlt_flops = 0;
+  D.sum_np = D.sum_np2 = D.sum_owned = 0;
+  for (int p = 0; p < H.nsub; ++p) {
+    int nt = H.sub_nt[p];
+    double np_ = H.sub_ptr[p + 1] - H.sub_ptr[p];
+    D.sum_np += (int64_t)np_;
+    D.sum_np2 += (int64_t)np_ * (int64_t)np_;
+    D.ldlt_flops += np_ * np_ * np_ / 3.0;
+    for (int k = 0; k < nt; ++k) {
+      D.active[k]++;
+      int rem = nt - k - 1;
+      double off = (double)rem * (rem - 1) / 2, dg = rem;
+      D.trail_flops[k] += off * 2.0 * 64 * 64 * 64 + dg * 64.0 * (64 * 65 / 2) * 2.0;
+    }
+  }
+  for (uint8_t o : H.sub_own) D.sum_owned += o;
+}
+
+int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
+  HostLevel& H = h->host[l];
+  DevLevel& D = h->dev[l];
+  DevArena& A = h->arena;
+  D.n = H.n;
+  D.m = H.m;
+  D.nnz = (int64_t)H.col.size();
+  D.avg_A = (int)std::max<int64_t>(1, D.nnz / std::max(1, H.n));
+  D.xyz = A.upload(H.xyz);
+  D.tets = A.upload(H.tets);
+  D.dir = A.upload(H.dir);
+  D.dir_list = A.upload(H.dir_list);
+  D.ndir = (int)H.dir_list.size();
+  D.rowptr = A.upload(H.rowptr);
+  D.col = A.upload(H.col);
+  D.diag = A.upload(H.diag);
+  D.cptr = A.upload(H.cptr);
+  D.contrib = A.upload(H.contrib);
+  D.nzflag = A.upload(H.nzflag);
+  D.S = A.alloc<double>((size_t)H.m * 10);
+  D.vol = A.alloc<double>(H.m);
+  D.cen = A.alloc<double>((size_t)H.m * 3);
+  D.b = A.alloc<double>(H.n);
+  D.nsub = H.nsub;
+  D.sub_ptr = A.upload(H.sub_ptr);
+  D.sub_dofs = A.upload(H.sub_dofs);
+  D.sub_own = A.upload(H.sub_own);
+  D.sub_nt = A.upload(H.sub_nt);
+  D.sub_order = A.upload(H.sub_order);
+  D.fac_off = A.upload(H.sub_fac_off);
+  D.fac_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
+  D.ext_pos = A.upload(H.ext_pos);
+  D.ext_nz = A.upload(H.ext_nz);
+  D.next = (int64_t)H.ext_pos.size();
+  finish_level_stats(H, D);
+  if (l + 1 < (int)h->host.size()) {
+    D.P_nnz = (int64_t)H.P_col.size();
+    D.P_rowptr = A.upload(H.P_rowptr);
+    D.P_col = A.upload(H.P_col);
+    D.P_val = A.upload(H.P_val);
+    D.PT_rowptr = A.upload(H.PT_rowptr);
+    D.PT_col = A.upload(H.PT_col);
+    D.PT_val = A.upload(H.PT_val);
+    D.avg_P = (int)std::max<int64_t>(1, D.P_nnz / std::max(1, H.n));
+    D.avg_PT = (int)std::max<int64_t>(1, D.P_nnz / std::max(1, h->host[l + 1].n));
+  }
+  if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
+  int* bad = A.alloc<int>(1);
+  if (!bad) return fail(MSP_ERR_OOM, "device allocation failed");
+  MSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  launch_tet_geometry(D.xyz, D.tets, D.m, D.S, D.vol, D.cen, bad, s);
+  launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, D.b, s);
+  int hbad = 0;
+  MSP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA(cudaStreamSynchronize(s));
+  MSP_CUDA(cudaGetLastError());
+  if (hbad) return fail(MSP_ERR_INVALID, "degenerate tet on level " + std::to_string(l));
+  return MSP_OK;
+}
+
+int check_options(const msp_options& o) {
+  if (o.delta < 0 || o.delta > 64) return fail(MSP_ERR_INVALID, "delta out of range");
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 64 || o.nu_post > 64)
+    return fail(MSP_ERR_INVALID, "nu out of range");
+  if (o.restart < 1 || o.restart > 256) return fail(MSP_ERR_INVALID, "restart out of range");
+  if (o.max_it < 1) return fail(MSP_ERR_INVALID, "max_it must be >= 1");
+  if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32)
+    return fail(MSP_ERR_INVALID, "unknown factor precision");
+  if (o.coef_kind != MSP_K_CONST && o.coef_kind != MSP_K_COSEXP)
+    return fail(MSP_ERR_INVALID, "unknown coefficient family");
+  if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
+    return fail(MSP_ERR_INVALID, "unknown load");
+  if (!std::isfinite(o.coef_scale)) return fail(MSP_ERR_INVALID, "non-finite coef_scale");
+  if ((o.alloc == nullptr) != (o.free == nullptr))
+    return fail(MSP_ERR_INVALID, "alloc and free must be given together");
+  return MSP_OK;
+}
+
+// ------------------------------------------------------------ launches
+int assemble_all(msp_instance* I) {
+  msp_hierarchy* h = I->h;
+  cudaStream_t s = I->stream;
+  for (size_t l = 0; l < h->dev.size(); ++l) {
+    DevLevel& D = h->dev[l];
+    ProfScope ps(I->prof, PK_ASSEMBLE, s, 2);
+    launch_coefficient(D.cen, D.m, h->opt.coef_kind, I->mu, h->wave, h->opt.coef_scale, I->k[l], s);
+    launch_assemble(D.cptr, D.contrib, D.nzflag, I->k[l], D.S, D.nnz, I->val[l], s);
+    ps.account((double)D.nnz * 8 + (double)D.nnz * 5 + (double)h->host[l].contrib.size() * 12 +
+                   (double)D.m * 32,
+               (double)h->host[l].contrib.size() * 2);
+  }
+  MSP_CUDA(cudaGetLastError());
+  return MSP_OK;
+}
+
+template <typename T>
+void factor_level(msp_instance* I, int l, T* fac) {
+  msp_hierarchy* h = I->h;
+  DevLevel& D = h->dev[l];
+  cudaStream_t s = I->stream;
+  {
+    ProfScope ps(I->prof, PK_EXTRACT, s, 2);
+    launch_extract<T>(D.ext_pos, D.ext_nz, D.next, I->val[l], D.fac_elems, fac, s);
+    ps.account((double)D.fac_elems * sizeof(T) + (double)D.next * (12 + sizeof(T) + 8), 0);
+  }
+  for (int k = 0; k < D.max_nt; ++k) {
+    int na = D.active[k];
+    int na1 = (k + 1 <= D.max_nt) ? D.active[k + 1] : 0;
+    {
+      ProfScope ps(I->prof, PK_LDLT_DIAG, s);
+      launch_ldlt_diag<T>(fac, D.fac_off, D.sub_order, na, k, I->info, s);
+      ps.account((double)na * 2 * 4096 * sizeof(T), (double)na * (64.0 * 64 * 64 / 3 + 64.0 * 64 * 64 / 3));
+    }
+    if (na1 > 0) {
+      int rows = D.max_nt - k - 1;
+      {
+        ProfScope ps(I->prof, PK_LDLT_PANEL, s);
+        launch_ldlt_panel<T>(fac, D.fac_off, D.sub_nt, D.sub_order, na1, k, rows, s);
+        ps.account(0, 0);
+      }
+      {
+        ProfScope ps(I->prof, PK_LDLT_TRAIL, s);
+        launch_ldlt_trail<T>(fac, D.fac_off, D.sub_nt, D.sub_order, na1, k, rows * (rows + 1) / 2, s);
+        ps.account(0, D.trail_flops[k]);
+      }
+    }
+  }
+}
+
+int factor_all(msp_instance* I) {
+  msp_hierarchy* h = I->h;
+  MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
+  for (size_t l = 0; l < h->dev.size(); ++l) {
+    if (level_f32(h, (int)l)) factor_level<float>(I, (int)l, static_cast<float*>(I->fac[l]));
+    else factor_level<double>(I, (int)l, static_cast<double*>(I->fac[l]));
+  }
+  MSP_CUDA(cudaGetLastError());
+  int hinfo = 0;
+  MSP_CUDA(cudaMemcpyAsync(&hinfo, I->info, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  I->prof.harvest();
+  if (hinfo) return fail(MSP_ERR_INTERNAL, "non-positive or non-finite pivot in a subdomain factor");
+  I->factored = true;
+  return MSP_OK;
+}
+
+void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream_t s) {
+  msp_hierarchy* h = I->h;
+  DevLevel& D = h->dev[l];
+  bool coarse = (l + 1 == (int)h->dev.size());
+  int kind = coarse ? PK_COARSE : (l == 0 ? PK_RAS : PK_RAS_COARSER);
+  ProfScope ps(I->prof, kind, s);
+  size_t es = level_f32(h, l) ? 4 : 8;
+  if (level_f32(h, l))
+    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.fac_off, D.sub_nt, D.sub_ptr,
+                            D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+  else
+    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.fac_off, D.sub_nt, D.sub_ptr,
+                             D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+  // algorithmic: every factor element read once per sweep pair (n_p^2 as in
+  // an L and U pair), gather + scatter of the DoF vectors
+  ps.account((double)D.sum_np2 * es + (double)D.sum_np * 13 + (double)D.sum_owned * (add ? 16 : 8),
+             2.0 * (double)D.sum_np2);
+}
+
+void spmv(msp_instance* I, int l, const double* x, double* y, const double* r, int mode,
+          cudaStream_t s) {
+  DevLevel& D = I->h->dev[l];
+  ProfScope ps(I->prof, PK_SPMV, s);
+  launch_spmv(D.rowptr, D.col, I->val[l], D.n, x, y, r, mode, D.avg_A, s);
+  ps.account((double)D.nnz * 12 + (double)(D.n + 1) * 4 + (double)D.n * (mode == SPMV_SET ? 16 : 24),
+             2.0 * (double)D.nnz);
+}
+
+void transfer(msp_instance* I, int l, bool restrict_, const double* x, double* y, int mode,
+              cudaStream_t s) {
+  DevLevel& D = I->h->dev[l];
+  int nc = I->h->dev[l + 1].n;
+  ProfScope ps(I->prof, PK_TRANSFER, s);
+  if (restrict_)
+    launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, D.avg_PT, s);
+  else
+    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, D.avg_P, s);
+  double rows = restrict_ ? nc : D.n, cols = restrict_ ? D.n : nc;
+  ps.account((double)D.P_nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16),
+             2.0 * (double)D.P_nnz);
+}
+
+// z += B^{-1}(r - A z), `its` times; when `from_zero`, z is not read first
+// (the first step is z = B^{-1} r).
+void smooth(msp_instance* I, int l, const double* r, double* z, int its, bool from_zero,
+            cudaStream_t s) {
+  int n = I->h->dev[l].n;
+  for (int it = 0; it < its; ++it) {
+    if (from_zero && it == 0) {
+      ras(I, l, r, z, 0, s);
+    } else {
+      spmv(I, l, z, I->t[l], r, SPMV_RESIDUAL, s);
+      ras(I, l, I->t[l], z, 1, s);
+    }
+  }
+  if (from_zero && its == 0) {
+    ProfScope ps(I->prof, PK_VEC, s);
+    launch_fill(z, 0.0, n, s);
+    ps.account((double)n * 8, 0);
+  }
+}
+
+// Algorithm 2 with P^T / P transfers and a direct solve on the coarsest level.
+void vcycle(msp_instance* I, const double* r0, double* z0, cudaStream_t s) {
+  msp_hierarchy* h = I->h;
+  const int L = (int)h->dev.size();
+  std::vector<const double*> r(L);
+  std::vector<double*> z(L);
+  r[0] = r0;
+  z[0] = z0;
+  for (int l = 1; l < L; ++l) {
+    r[l] = I->r[l];
+    z[l] = I->z[l];
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    smooth(I, l, r[l], z[l], h->opt.nu_pre, true, s);
+    spmv(I, l, z[l], I->t[l], r[l], SPMV_RESIDUAL, s);
+    transfer(I, l, true, I->t[l], I->r[l + 1], SPMV_SET, s);
+  }
+  ras(I, L - 1, r[L - 1], z[L - 1], 0, s);
+  for (int l = L - 2; l >= 0; --l) {
+    transfer(I, l, false, z[l + 1], z[l], SPMV_ADD, s);
+    smooth(I, l, r[l], z[l], h->opt.nu_post, false, s);
+  }
+}
+
+// ---------------------------------------------------------------- FGMRES
+struct Dot {
+  msp_instance* I;
+  // out[0..nv) = V_i . w on the device, then copied to the pinned staging
+  void run(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out_dev) {
+    ProfScope ps(I->prof, PK_VEC, I->stream, 2);
+    launch_multidot(V, ld, nv, w, n, I->part, out_dev, I->stream);
+    ps.account((double)(nv + 1) * n * 8, 2.0 * nv * n);
+  }
+};
+
+int fgmres(msp_instance* I, const double* b, double* x, double rtol, msp_stats* st) {
+  msp_hierarchy* h = I->h;
+  cudaStream_t s = I->stream;
+  const int64_t n = h->dev[0].n;
+  const int m = I->m;
+  const int maxit = h->opt.max_it;
+  double* V = I->V;
+  double* Z = I->Z;
+  double* w = I->w;
+  double* rr = I->res;
+  double* hd = I->hdev;   // device: [0..m] h1, [m+1..2m+1] h2, [2m+2] norm^2
+  double* hp = I->hpin;   // pinned host copy
+  Dot dot{I};
+  auto vec = [&](int i) { return V + (int64_t)i * n; };
+  auto zvec = [&](int i) { return Z + (int64_t)i * n; };
+  // ||b||
+  dot.run(b, 0, 1, b, n, hd);
+  MSP_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(hp[0]);
+  {
+    ProfScope ps(I->prof, PK_VEC, s);
+    launch_fill(x, 0.0, n, s);
+    ps.account((double)n * 8, 0);
+  }
+  st->iterations = 0;
+  st->rel_residual = 0.0;
+  if (!(bnorm > 0.0)) {
+    MSP_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(bnorm)) return fail(MSP_ERR_INVALID, "non-finite right-hand side");
+    return MSP_OK;
+  }
+  {
+    ProfScope ps(I->prof, PK_VEC, s);
+    launch_copy(b, rr, n, s);
+    ps.account((double)n * 16, 0);
+  }
+  double rnorm = bnorm;
+  int it = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  int status = MSP_ERR_NOT_CONVERGED;
+  while (true) {
+    if (rnorm <= rtol * bnorm) {
+      status = MSP_OK;
+      break;
+    }
+    if (it >= maxit) break;
+    {
+      ProfScope ps(I->prof, PK_VEC, s);
+      launch_scale(rr, 1.0 / rnorm, vec(0), n, s);
+      ps.account((double)n * 16, (double)n);
+    }
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = rnorm;
+    int j = 0;
+    bool breakdown = false;
+    for (; j < m && it < maxit; ++j) {
+      vcycle(I, vec(j), zvec(j), s);
+      spmv(I, 0, zvec(j), w, nullptr, SPMV_SET, s);
+      // classical Gram-Schmidt, twice (CGS2)
+      dot.run(V, n, j + 1, w, n, hd);
+      {
+        ProfScope ps(I->prof, PK_VEC, s);
+        launch_multi_axpy(V, n, j + 1, hd, w, n, -1.0, s);
+        ps.account((double)(j + 3) * n * 8, 2.0 * (j + 1) * n);
+      }
+      dot.run(V, n, j + 1, w, n, hd + (m + 1));
+      {
+        ProfScope ps(I->prof, PK_VEC, s);
+        launch_multi_axpy(V, n, j + 1, hd + (m + 1), w, n, -1.0, s);
+        ps.account((double)(j + 3) * n * 8, 2.0 * (j + 1) * n);
+      }
+      dot.run(w, 0, 1, w, n, hd + 2 * (m + 1));
+      MSP_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      MSP_CUDA(cudaStreamSynchronize(s));
+      I->prof.harvest();
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hp[i] + hp[m + 1 + i];
+      double hn = std::sqrt(std::max(hp[2 * (m + 1)], 0.0));
+      if (!std::isfinite(hn)) {
+        st->iterations = it;
+        return fail(MSP_ERR_NOT_CONVERGED, "non-finite Arnoldi vector");
+      }
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      double den = std::hypot(a, c);
+      cs[j] = den == 0.0 ? 1.0 : a / den;
+      sn[j] = den == 0.0 ? 0.0 : c / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      if (hn <= 1e-300) {
+        breakdown = true;
+        ++j;
+        break;
+      }
+      {
+        ProfScope ps(I->prof, PK_VEC, s);
+        launch_scale(w, 1.0 / hn, vec(j + 1), n, s);
+        ps.account((double)n * 16, (double)n);
+      }
+      if (std::fabs(g[j + 1]) <= rtol * bnorm) {
+        ++j;
+        break;
+      }
+    }
+    for (int i = j - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int k = i + 1; k < j; ++k) sum -= H[(size_t)i * m + k] * y[k];
+      y[i] = sum / H[(size_t)i * m + i];
+    }
+    // x += Z y (y staged through pinned memory, then used on the device)
+    for (int i = 0; i < j; ++i) hp[2 * (m + 1) + 1 + i] = y[i];
+    MSP_CUDA(cudaMemcpyAsync(hd + 2 * (m + 1) + 1, hp + 2 * (m + 1) + 1, sizeof(double) * j,
+                             cudaMemcpyHostToDevice, s));
+    {
+      ProfScope ps(I->prof, PK_VEC, s);
+      launch_multi_axpy(Z, n, j, hd + 2 * (m + 1) + 1, x, n, 1.0, s);
+      ps.account((double)(j + 2) * n * 8, 2.0 * j * n);
+    }
+    spmv(I, 0, x, rr, b, SPMV_RESIDUAL, s);
+    dot.run(rr, 0, 1, rr, n, hd);
+    MSP_CUDA(cudaMemcpyAsync(hp, hd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    rnorm = std::sqrt(std::max(hp[0], 0.0));
+    if (!std::isfinite(rnorm)) break;
+    if (breakdown && rnorm > rtol * bnorm) break;
+  }
+  MSP_CUDA(cudaGetLastError());
+  st->iterations = it;
+  st->rel_residual = rnorm / bnorm;
+  if (status != MSP_OK)
+    return fail(MSP_ERR_NOT_CONVERGED, "FGMRES did not reach rtol within max_it (or broke down)");
+  return MSP_OK;
+}
+
+int alloc_instance(msp_hierarchy* h, msp_instance* I) {
+  DevArena& A = I->arena;
+  A.al = h->arena.al;
+  const int L = (int)h->dev.size();
+  I->mu = A.alloc<double>(8);
+  I->info = A.alloc<int>(1);
+  I->k.resize(L);
+  I->val.resize(L);
+  I->r.resize(L);
+  I->z.resize(L);
+  I->t.resize(L);
+  I->fac.resize(L);
+  for (int l = 0; l < L; ++l) {
+    DevLevel& D = h->dev[l];
+    I->k[l] = A.alloc<double>(D.m);
+    I->val[l] = A.alloc<double>(D.nnz);
+    I->r[l] = A.alloc<double>(D.n);
+    I->z[l] = A.alloc<double>(D.n);
+    I->t[l] = A.alloc<double>(D.n);
+    if (level_f32(h, l)) I->fac[l] = A.alloc<float>(D.fac_elems);
+    else I->fac[l] = A.alloc<double>(D.fac_elems);
+  }
+  I->m = h->opt.restart;
+  const int64_t n = h->dev[0].n;
+  I->V = A.alloc<double>((size_t)(I->m + 1) * n);
+  I->Z = A.alloc<double>((size_t)I->m * n);
+  I->w = A.alloc<double>(n);
+  I->res = A.alloc<double>(n);
+  I->xb = A.alloc<double>(2 * n);
+  I->part = A.alloc<double>((size_t)(I->m + 1) * kDotBlocks);
+  I->hdev = A.alloc<double>(4 * (size_t)(I->m + 1) + 8);
+  if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
+  if (cudaMallocHost(&I->hpin, sizeof(double) * (4 * (size_t)(I->m + 1) + 8)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MSP_ERR_OOM, "pinned host allocation failed");
+  }
+  return MSP_OK;
+}
+
+int set_mu(msp_instance* I, const double* mu, int n_mu) {
+  msp_hierarchy* h = I->h;
+  double m8[8] = {0};
+  if (h->opt.coef_kind == MSP_K_COSEXP) {
+    if (n_mu != 8 || !mu) return fail(MSP_ERR_INVALID, "MSP_K_COSEXP needs n_mu == 8");
+    for (int j = 0; j < 8; ++j) {
+      if (!std::isfinite(mu[j])) return fail(MSP_ERR_INVALID, "non-finite mu");
+      m8[j] = mu[j];
+    }
+  }
+  std::copy(m8, m8 + 8, I->hpin);
+  MSP_CUDA(cudaMemcpyAsync(I->mu, I->hpin, sizeof(m8), cudaMemcpyHostToDevice, I->stream));
+  int rc = assemble_all(I);
+  if (rc) return rc;
+  MSP_CUDA(cudaStreamSynchronize(I->stream));  // the staging buffer is reused next
+  I->assembled = true;
+  I->factored = false;
+  return MSP_OK;
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+}  // namespace msp
+
+// =============================================================== C ABI
+extern "C" {
+
+void msp_default_options(msp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->delta = 1;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->restart = 30;
+  o->max_it = 1000;
+  o->factor_precision = MSP_F64;
+  o->coef_kind = MSP_K_CONST;
+  o->coef_scale = 1.0;
+  o->load_kind = MSP_F_ONE;
+}
+
+const char* msp_last_error(void) { return msp::g_last_error.c_str(); }
+const char* msp_version(void) { return "msp 0.1 (sm_103a)"; }
+
+int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_options* o,
+                       msp_hierarchy** out) {
+  msp::g_last_error.clear();
+  if (!lv || !o || !out || nlevels < 1) return fail(MSP_ERR_INVALID, "NULL argument or nlevels < 1");
+  int rc = check_options(*o);
+  if (rc) return rc;
+  std::unique_ptr<msp_hierarchy> h(new (std::nothrow) msp_hierarchy());
+  if (!h) return fail(MSP_ERR_OOM, "host allocation failed");
+  h->opt = *o;
+  h->host_only = o->host_only != 0;
+  try {
+    std::string err = build_host_levels(lv, nlevels, *o, h->host);
+    if (!err.empty()) return fail(MSP_ERR_INVALID, err);
+  } catch (const std::bad_alloc&) {
+    return fail(MSP_ERR_OOM, "host allocation failed during set-up");
+  }
+  if (!h->host_only) {
+    MSP_CUDA(cudaGetDevice(&h->device));
+    h->arena.al.a = o->alloc;
+    h->arena.al.f = o->free;
+    h->arena.al.ctx = o->alloc_ctx;
+    h->dev.resize(nlevels);
+    std::vector<int32_t> wave(24);
+    for (int j = 0; j < 8; ++j)
+      for (int d = 0; d < 3; ++d) wave[3 * j + d] = o->wave[j][d];
+    h->wave = h->arena.upload(wave);
+    cudaStream_t s;
+    MSP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (int l = 0; l < nlevels; ++l) {
+      rc = upload_level(h.get(), l, s);
+      if (rc) {
+        cudaStreamDestroy(s);
+        h->arena.release();
+        return rc;
+      }
+    }
+    cudaStreamDestroy(s);
+  }
+  *out = h.release();
+  return MSP_OK;
+}
+
+void msp_free_hierarchy(msp_hierarchy* h) {
+  if (!h) return;
+  if (!h->host_only) cudaDeviceSynchronize();
+  h->arena.release();
+  delete h;
+}
+
+int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) {
+  if (!h || !info || level < 0 || level >= (int)h->host.size())
+    return fail(MSP_ERR_INVALID, "bad hierarchy, level or info pointer");
+  const HostLevel& H = h->host[level];
+  info->n_nodes = H.n;
+  info->n_tets = H.m;
+  info->nnz = (int64_t)H.col.size();
+  info->n_sub = H.coarsest ? 0 : H.nsub;
+  info->sub_dofs = H.sub_ptr.empty() ? 0 : H.sub_ptr.back();
+  info->factor_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
+  info->P_nnz = (int64_t)H.P_col.size();
+  return MSP_OK;
+}
+
+int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream, msp_instance** out) {
+  msp::g_last_error.clear();
+  if (!h || !out) return fail(MSP_ERR_INVALID, "NULL argument");
+  if (h->host_only) return fail(MSP_ERR_INVALID, "host-only hierarchy");
+  std::unique_ptr<msp_instance> I(new (std::nothrow) msp_instance());
+  if (!I) return fail(MSP_ERR_OOM, "host allocation failed");
+  I->h = h;
+  I->stream = static_cast<cudaStream_t>(stream);
+  // budget check before allocating
+  size_t need = 0;
+  for (size_t l = 0; l < h->dev.size(); ++l) {
+    const DevLevel& D = h->dev[l];
+    need += (size_t)D.m * 8 + (size_t)D.nnz * 8 + (size_t)D.n * 24 +
+            (size_t)D.fac_elems * (level_f32(h, (int)l) ? 4 : 8);
+  }
+  need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (h->opt.mem_budget_bytes && h->arena.bytes + h->instance_bytes + need > h->opt.mem_budget_bytes)
+      return fail(MSP_ERR_OOM, "memory budget exceeded: instance needs " + std::to_string(need) + " bytes");
+    h->instance_bytes += need;
+  }
+  I->charged = need;
+  auto undo = [&](int rc) {
+    I->arena.release();
+    if (I->hpin) cudaFreeHost(I->hpin);
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->instance_bytes -= need;
+    return rc;
+  };
+  int rc = alloc_instance(h, I.get());
+  if (rc) return undo(rc);
+  I->prof.init(I->stream);
+  rc = set_mu(I.get(), mu, n_mu);
+  if (rc) return undo(rc);
+  *out = I.release();
+  return MSP_OK;
+}
+
+int msp_reassemble(msp_instance* I, const double* mu, int n_mu) {
+  msp::g_last_error.clear();
+  if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
+  return set_mu(I, mu, n_mu);
+}
+
+void msp_free_instance(msp_instance* I) {
+  if (!I) return;
+  cudaStreamSynchronize(I->stream);
+  I->prof.destroy();
+  I->arena.release();
+  if (I->hpin) cudaFreeHost(I->hpin);
+  {
+    std::lock_guard<std::mutex> lk(I->h->mu);
+    I->h->instance_bytes -= I->charged;
+  }
+  delete I;
+}
+
+int msp_factor(msp_instance* I) {
+  msp::g_last_error.clear();
+  if (!I || !I->assembled) return fail(MSP_ERR_INVALID, "instance not assembled");
+  return factor_all(I);
+}
+
+int msp_apply(msp_instance* I, const double* r, double* z, void* stream) {
+  msp::g_last_error.clear();
+  if (!I || !r || !z) return fail(MSP_ERR_INVALID, "NULL argument");
+  if (!I->factored) return fail(MSP_ERR_INVALID, "instance not factored");
+  if (r == z) return fail(MSP_ERR_INVALID, "r and z must not alias");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : I->stream;
+  vcycle(I, r, z, s);
+  MSP_CUDA(cudaGetLastError());
+  return MSP_OK;
+}
+
+int msp_apply_op(msp_instance* I, int op, int level, const double* x, double* y, void* stream) {
+  msp::g_last_error.clear();
+  if (!I || !x || !y) return fail(MSP_ERR_INVALID, "NULL argument");
+  msp_hierarchy* h = I->h;
+  const int L = (int)h->dev.size();
+  if (level < 0 || level >= L) return fail(MSP_ERR_INVALID, "level out of range");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : I->stream;
+  switch (op) {
+    case MSP_OP_SPMV: spmv(I, level, x, y, nullptr, SPMV_SET, s); break;
+    case MSP_OP_RESIDUAL: spmv(I, level, x, y, nullptr, SPMV_SUB_FROM, s); break;
+    case MSP_OP_INTERP:
+      if (level + 1 >= L) return fail(MSP_ERR_INVALID, "no coarser level");
+      transfer(I, level, false, x, y, SPMV_SET, s);
+      break;
+    case MSP_OP_RESTRICT:
+      if (level + 1 >= L) return fail(MSP_ERR_INVALID, "no coarser level");
+      transfer(I, level, true, x, y, SPMV_SET, s);
+      break;
+    case MSP_OP_RAS:
+      if (level + 1 >= L) return fail(MSP_ERR_INVALID, "the coarsest level is solved, not smoothed");
+      if (!I->factored) return fail(MSP_ERR_INVALID, "instance not factored");
+      ras(I, level, x, y, 0, s);
+      break;
+    case MSP_OP_COARSE:
+      if (level != L - 1) return fail(MSP_ERR_INVALID, "MSP_OP_COARSE needs the coarsest level");
+      if (!I->factored) return fail(MSP_ERR_INVALID, "instance not factored");
+      ras(I, level, x, y, 0, s);
+      break;
+    default: return fail(MSP_ERR_INVALID, "unknown op");
+  }
+  MSP_CUDA(cudaGetLastError());
+  return MSP_OK;
+}
+
+int msp_solve(msp_instance* I, const double* b, double* x, double rtol, msp_stats* st) {
+  msp::g_last_error.clear();
+  msp_stats dummy;
+  if (!st) st = &dummy;
+  std::memset(st, 0, sizeof(*st));
+  int rc;
+  if (!I || !x) rc = fail(MSP_ERR_INVALID, "NULL argument");
+  else if (!I->factored) rc = fail(MSP_ERR_INVALID, "instance not factored");
+  else if (!(rtol > 0.0) || !std::isfinite(rtol)) rc = fail(MSP_ERR_INVALID, "rtol must be > 0");
+  else {
+    Timer tm;
+    rc = fgmres(I, b ? b : I->h->dev[0].b, x, rtol, st);
+    I->prof.harvest();
+    st->ms_solve = tm.ms();
+  }
+  st->status = rc;
+  return rc;
+}
+
+int msp_solve_host(msp_instance* I, const double* mu, int n_mu, const double* b_host,
+                   double* x_host, double rtol, msp_stats* st) {
+  msp::g_last_error.clear();
+  msp_stats dummy;
+  if (!st) st = &dummy;
+  std::memset(st, 0, sizeof(*st));
+  if (!I || !x_host) return st->status = fail(MSP_ERR_INVALID, "NULL argument");
+  const int64_t n = I->h->dev[0].n;
+  Timer t0;
+  int rc = set_mu(I, mu, n_mu);
+  st->ms_assemble = t0.ms();
+  if (rc) return st->status = rc;
+  Timer t1;
+  rc = factor_all(I);
+  st->ms_factor = t1.ms();
+  if (rc) return st->status = rc;
+  const double* b = nullptr;
+  if (b_host) {
+    if (cudaMemcpyAsync(I->xb + n, b_host, n * sizeof(double), cudaMemcpyHostToDevice, I->stream) != cudaSuccess)
+      return st->status = fail(MSP_ERR_CUDA, "copy of b failed");
+    b = I->xb + n;
+  }
+  double a = st->ms_assemble, f = st->ms_factor;
+  rc = msp_solve(I, b, I->xb, rtol, st);
+  st->ms_assemble = a;
+  st->ms_factor = f;
+  if (rc && rc != MSP_ERR_NOT_CONVERGED) return rc;
+  int rc2 = rc;
+  if (cudaMemcpyAsync(x_host, I->xb, n * sizeof(double), cudaMemcpyDeviceToHost, I->stream) != cudaSuccess ||
+      cudaStreamSynchronize(I->stream) != cudaSuccess)
+    return st->status = fail(MSP_ERR_CUDA, "copy of x failed");
+  st->status = rc2;
+  return rc2;
+}
+
+int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, size_t cap,
+                       size_t* bytes_out) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(MSP_ERR_INVALID, "bad hierarchy or level");
+  const HostLevel& H = h->host[level];
+  const void* src = nullptr;
+  size_t bytes = 0;
+  bool on_device = false;
+  auto pick = [&](const auto& v) {
+    src = v.data();
+    bytes = v.size() * sizeof(v[0]);
+  };
+  switch (what) {
+    case MSP_ARR_ROWPTR: pick(H.rowptr); break;
+    case MSP_ARR_COL: pick(H.col); break;
+    case MSP_ARR_SUB_PTR: pick(H.sub_ptr); break;
+    case MSP_ARR_SUB_DOFS: pick(H.sub_dofs); break;
+    case MSP_ARR_SUB_OWN: pick(H.sub_own); break;
+    case MSP_ARR_P_ROWPTR: pick(H.P_rowptr); break;
+    case MSP_ARR_P_COL: pick(H.P_col); break;
+    case MSP_ARR_P_VAL: pick(H.P_val); break;
+    case MSP_ARR_PT_ROWPTR: pick(H.PT_rowptr); break;
+    case MSP_ARR_PT_COL: pick(H.PT_col); break;
+    case MSP_ARR_PT_VAL: pick(H.PT_val); break;
+    case MSP_ARR_LOAD:
+      if (h->host_only) return fail(MSP_ERR_INVALID, "host-only hierarchy has no load vector");
+      src = h->dev[level].b;
+      bytes = (size_t)H.n * sizeof(double);
+      on_device = true;
+      break;
+    default: return fail(MSP_ERR_INVALID, "unknown hierarchy array");
+  }
+  if (bytes_out) *bytes_out = bytes;
+  if (!dst) return MSP_OK;
+  if (cap < bytes) return fail(MSP_ERR_INVALID, "destination too small");
+  if (bytes == 0) return MSP_OK;
+  if (on_device) MSP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  else std::memcpy(dst, src, bytes);
+  return MSP_OK;
+}
+
+int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void* dst, size_t cap,
+                      size_t* bytes_out) {
+  if (!I || level < 0 || level >= (int)I->h->dev.size()) return fail(MSP_ERR_INVALID, "bad instance or level");
+  const msp_hierarchy* h = I->h;
+  const DevLevel& D = h->dev[level];
+  const HostLevel& H = h->host[level];
+  const void* src = nullptr;
+  size_t bytes = 0;
+  if (what == MSP_ARR_VAL) {
+    src = I->val[level];
+    bytes = (size_t)D.nnz * sizeof(double);
+  } else if (what == MSP_ARR_FACTOR) {
+    bool coarse = level + 1 == (int)h->dev.size();
+    int p = coarse ? 0 : sub;
+    if (p < 0 || p >= H.nsub || (coarse && sub != -1 && sub != 0))
+      return fail(MSP_ERR_INVALID, "subdomain out of range");
+    size_t es = level_f32(h, level) ? 4 : 8;
+    src = static_cast<const char*>(I->fac[level]) + (size_t)H.sub_fac_off[p] * es;
+    bytes = (size_t)(H.sub_fac_off[p + 1] - H.sub_fac_off[p]) * es;
+  } else {
+    return fail(MSP_ERR_INVALID, "unknown instance array");
+  }
+  if (bytes_out) *bytes_out = bytes;
+  if (!dst) return MSP_OK;
+  if (cap < bytes) return fail(MSP_ERR_INVALID, "destination too small");
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  MSP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  return MSP_OK;
+}
+
+// ---- per-kernel accounting (launch counts, algorithmic bytes/flops, and
+// CUDA-event durations while profiling is on)
+int msp_profile_enable(msp_instance* I, uint32_t class_mask) {
+  if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  I->prof.harvest();
+  I->prof.mask = class_mask;
+  return MSP_OK;
+}
+
+int msp_profile_reset(msp_instance* I) {
+  if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  I->prof.harvest();
+  I->prof.reset();
+  return MSP_OK;
+}
+
+int msp_profile_read(msp_instance* I, int kclass, msp_kernel_profile* out) {
+  if (!I || !out || kclass < 0 || kclass >= PK_COUNT) return fail(MSP_ERR_INVALID, "bad argument");
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  I->prof.harvest();
+  *out = I->prof.c[kclass];
+  return MSP_OK;
+}
+
+}  // extern "C"

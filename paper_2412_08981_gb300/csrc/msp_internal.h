@@ -1,0 +1,72 @@
+// Internal data structures of the msp library (host set-up + device state).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "msp.h"
+
+namespace msp {
+
+constexpr int kTile = MSP_TILE;             // factor tile edge
+constexpr int kTileElems = kTile * kTile;   // elements per tile
+
+// Pair slot of the symmetric 4x4 element matrix: (a,b), a <= b, row-major
+// over the upper triangle: (0,0)=0 (0,1)=1 (0,2)=2 (0,3)=3 (1,1)=4 (1,2)=5
+// (1,3)=6 (2,2)=7 (2,3)=8 (3,3)=9.
+inline int pair_slot(int a, int b) {
+  if (a > b) { int t = a; a = b; b = t; }
+  static const int base[4] = {0, 4, 7, 9};
+  return base[a] + (b - a);
+}
+
+inline int64_t tri_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+
+// Host-side structures of one level, built once per hierarchy.
+struct HostLevel {
+  int n = 0, m = 0;
+  std::vector<double> xyz;
+  std::vector<int32_t> tets;
+  std::vector<uint8_t> dir;
+  std::vector<int32_t> owner;
+  std::vector<int32_t> dir_list;       // Dirichlet node ids, ascending
+
+  // CSR pattern of J (Section 2.1): vertices sharing a tet
+  std::vector<int32_t> rowptr, col, diag;
+  // element -> nonzero contributions: for nonzero q, contrib[cptr[q]..cptr[q+1])
+  // are e*10+slot in ascending e; nzflag[q]: 0 assemble, 1 Dirichlet diagonal
+  // (value 1), 2 Dirichlet-coupled (value 0)
+  std::vector<int32_t> cptr, contrib;
+  std::vector<uint8_t> nzflag;
+
+  // subdomains (Section 2.2) on smoothed levels; one block of all interior
+  // DoFs on the coarsest level
+  bool coarsest = false;
+  int nsub = 0;
+  std::vector<int32_t> sub_ptr;         // [nsub+1] offsets into sub_dofs
+  std::vector<int32_t> sub_dofs;        // sorted DoFs of each subdomain
+  std::vector<uint8_t> sub_own;         // owned flag (R^0) per entry of sub_dofs
+  std::vector<int32_t> sub_nt;          // tiles per side
+  std::vector<int64_t> sub_fac_off;     // [nsub+1] element offsets of each factor
+  // dense extraction map: for subdomain p, entries ext_ptr[p]..ext_ptr[p+1]
+  // give (absolute position in the level's factor storage, CSR nonzero index,
+  // or -1 for a padding diagonal that is set to 1)
+  std::vector<int64_t> ext_ptr;
+  std::vector<int64_t> ext_pos;
+  std::vector<int32_t> ext_nz;
+  // work list of the factorisation: subdomains sorted by descending NT
+  std::vector<int32_t> sub_order;
+
+  // interpolation from level+1 to this level, and its transpose
+  std::vector<int32_t> P_rowptr, P_col, PT_rowptr, PT_col;
+  std::vector<double> P_val, PT_val;
+};
+
+// Builds every host structure of a hierarchy; returns an empty string or an
+// error message.
+std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_options& o,
+                              std::vector<HostLevel>& out);
+
+}  // namespace msp

@@ -1,0 +1,71 @@
+// Host-callable launchers of the msp CUDA kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace msp {
+
+// ---- per-tet geometry (set-up) and per-parameter coefficient / assembly
+// S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b); vol[e] = |T|; cen[e*3] centroid
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, double* S, double* vol,
+                         double* cen, int* bad, cudaStream_t s);
+// b_i = f(x_i) * sum_{e containing i} |T_e| / 4 (ascending e), 0 on Dirichlet nodes
+void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,
+                        const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
+                        int load_kind, double* b, cudaStream_t s);
+// k_e = exp(s * sum_j mu_j 0.5 cos(pi a_j . c_e))  (or 1)
+void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
+                        const int32_t* wave24, double scale, double* k, cudaStream_t s);
+// val[q] = sum_{c in contrib(q)} k[c/10] * S[c]  (ascending e), Dirichlet flags
+void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,
+                     const double* k, const double* S, int64_t nnz, double* val, cudaStream_t s);
+
+// ---- CSR SpMV family (FP64)
+enum SpmvMode { SPMV_SET = 0, SPMV_SUB_FROM = 1, SPMV_ADD = 2, SPMV_RESIDUAL = 3 };
+// SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x
+void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
+                 const double* x, double* y, const double* r, int mode, int avg_row_nnz,
+                 cudaStream_t s);
+
+// ---- dense subdomain blocks (templated on the factor type T = double | float)
+// zero the level's factor storage, then scatter the CSR values (or 1 on the
+// padding diagonals, nz == -1) to their absolute positions
+template <typename T>
+void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
+                    const double* val, int64_t fac_elems, T* fac, cudaStream_t s);
+// step k of the blocked L D L^T over the first `nactive` subdomains of `order`
+// (sorted by descending tile count, so those are exactly the ones with NT > k)
+template <typename T>
+void launch_ldlt_diag(T* fac, const int64_t* fac_off, const int32_t* order, int nactive, int k,
+                      int* info, cudaStream_t s);
+template <typename T>
+void launch_ldlt_panel(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
+                       int nactive, int k, int max_rows, cudaStream_t s);
+template <typename T>
+void launch_ldlt_trail(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
+                       int nactive, int k, int max_pairs, cudaStream_t s);
+// z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
+// entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
+template <typename T>
+void launch_ras_solve(const T* fac, const int64_t* fac_off, const int32_t* nt,
+                      const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int nsub,
+                      int max_nt, const int32_t* dir_list, int ndir, const double* t, double* z,
+                      int add, cudaStream_t s);
+
+// ---- Krylov helpers (deterministic two-stage reductions)
+// out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles
+constexpr int kDotBlocks = 296;
+void launch_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n,
+                     double* part, double* out, cudaStream_t s);
+// w -= sum_i h[i] V_i  (h on the device)
+void launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w,
+                       int64_t n, double sign, cudaStream_t s);
+// y = alpha * x (alpha read from the host argument)
+void launch_scale(const double* x, double alpha, double* y, int64_t n, cudaStream_t s);
+void launch_axpy(double alpha, const double* x, double* y, int64_t n, cudaStream_t s);
+void launch_add_vec(const double* a, double* b, int64_t n, cudaStream_t s);  // b += a
+void launch_fill(double* y, double v, int64_t n, cudaStream_t s);
+void launch_copy(const double* x, double* y, int64_t n, cudaStream_t s);
+
+}  // namespace msp

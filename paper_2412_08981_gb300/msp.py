@@ -1,0 +1,356 @@
+"""Python binding of the msp C ABI (include/msp.h): argument marshalling only.
+
+Every computation runs in libmsp.so (CUDA kernels for sm_103a).  PyTorch only
+provides device memory (through the allocator hooks) and streams.  There is
+no fallback: if the library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmsp.so")
+
+# ---------------------------------------------------------------- constants
+MSP_OK, MSP_PENDING = 0, 1
+MSP_ERR_INVALID, MSP_ERR_OOM, MSP_ERR_NOT_CONVERGED = -1, -2, -3
+MSP_ERR_TIMEOUT, MSP_ERR_CUDA, MSP_ERR_INTERNAL = -4, -5, -6
+MSP_F64, MSP_F32 = 0, 1
+MSP_K_CONST, MSP_K_COSEXP = 0, 1
+MSP_F_ONE, MSP_F_SINES = 0, 1
+MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
+ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
+          "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
+          "val": 12, "factor": 13}
+_ARRAY_DTYPE = {"rowptr": np.int32, "col": np.int32, "sub_ptr": np.int32, "sub_dofs": np.int32,
+                "sub_own": np.uint8, "P_rowptr": np.int32, "P_col": np.int32,
+                "P_val": np.float64, "PT_rowptr": np.int32, "PT_col": np.int32,
+                "PT_val": np.float64, "load": np.float64, "val": np.float64}
+KERNEL_CLASSES = ["assemble", "extract", "ldlt_diag", "ldlt_panel", "ldlt_trail", "ras",
+                  "ras_coarser", "coarse", "spmv", "transfer", "vec"]
+MSP_TILE = 64
+
+ERR_NAMES = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_ERR_INVALID", -2: "MSP_ERR_OOM",
+             -3: "MSP_ERR_NOT_CONVERGED", -4: "MSP_ERR_TIMEOUT", -5: "MSP_ERR_CUDA",
+             -6: "MSP_ERR_INTERNAL"}
+
+
+class MspError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ------------------------------------------------------------------ structs
+class msp_level_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("xyz", C.c_void_p), ("n_tets", C.c_int32),
+                ("tets", C.c_void_p), ("dirichlet", C.c_void_p), ("owner", C.c_void_p)]
+
+
+msp_alloc_fn = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+msp_free_fn = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class msp_options(C.Structure):
+    _fields_ = [("delta", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
+                ("restart", C.c_int32), ("max_it", C.c_int32), ("factor_precision", C.c_int32),
+                ("coef_kind", C.c_int32), ("wave", (C.c_int32 * 3) * 8),
+                ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("host_only", C.c_int32),
+                ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
+                ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
+
+
+class msp_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("ms_assemble", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double)]
+
+
+class msp_level_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("nnz", C.c_int64),
+                ("n_sub", C.c_int32), ("sub_dofs", C.c_int64), ("factor_elems", C.c_int64),
+                ("P_nnz", C.c_int64)]
+
+
+class msp_kernel_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("bytes", C.c_double), ("flops", C.c_double),
+                ("timed", C.c_int64), ("ms", C.c_double)]
+
+
+# ------------------------------------------------------------------ library
+_lib = None
+
+EXPORTS = {
+    "msp_default_options": (None, [C.POINTER(msp_options)]),
+    "msp_last_error": (C.c_char_p, []),
+    "msp_version": (C.c_char_p, []),
+    "msp_load_hierarchy": (C.c_int, [C.POINTER(msp_level_desc), C.c_int, C.POINTER(msp_options),
+                                     C.POINTER(C.c_void_p)]),
+    "msp_free_hierarchy": (None, [C.c_void_p]),
+    "msp_hierarchy_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_level_info)]),
+    "msp_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "msp_reassemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "msp_free_instance": (None, [C.c_void_p]),
+    "msp_factor": (C.c_int, [C.c_void_p]),
+    "msp_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "msp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(msp_stats)]),
+    "msp_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_double, C.POINTER(msp_stats)]),
+    "msp_apply_op": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "msp_hierarchy_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                     C.POINTER(C.c_size_t)]),
+    "msp_instance_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                    C.c_size_t, C.POINTER(C.c_size_t)]),
+    "msp_profile_enable": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "msp_profile_reset": (C.c_int, [C.c_void_p]),
+    "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libmsp.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libmsp.so not built: {path} (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+_load_library = load
+
+
+def _check(rc):
+    if rc != MSP_OK:
+        raise MspError(rc, load().msp_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# -------------------------------------------------- torch device allocator
+_torch_alloc_refs = []
+
+
+def _torch_allocator():
+    import torch
+
+    @msp_alloc_fn
+    def _alloc(ctx, nbytes, stream):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:  # reported to the library as a failed allocation
+            return None
+
+    @msp_free_fn
+    def _free(ctx, ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _torch_alloc_refs.append((_alloc, _free))
+    return _alloc, _free
+
+
+# ------------------------------------------------------------- high level
+def default_options(**kw) -> msp_options:
+    o = msp_options()
+    load().msp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "wave":
+            w = np.asarray(v, np.int32).reshape(8, 3)
+            for j in range(8):
+                for d in range(3):
+                    o.wave[j][d] = int(w[j, d])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Hierarchy:
+    """msp_load_hierarchy / msp_free_hierarchy.
+
+    levels: sequence of objects with xyz [n,3] f64, tets [m,4] i32,
+    dirichlet [n] u8 and owner [n] i32 (or None on the coarsest level).
+    """
+
+    def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
+                 max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
+                 load="one", host_only=False, budget_bytes=0, torch_alloc=True):
+        lib = _load_library()
+        self._keep = []
+        arr = (msp_level_desc * len(levels))()
+        for i, lv in enumerate(levels):
+            xyz = np.ascontiguousarray(lv.xyz, np.float64)
+            tets = np.ascontiguousarray(lv.tets, np.int32)
+            dr = np.ascontiguousarray(lv.dirichlet, np.uint8)
+            ow = None if lv.owner is None else np.ascontiguousarray(lv.owner, np.int32)
+            self._keep += [xyz, tets, dr, ow]
+            arr[i] = msp_level_desc(xyz.shape[0], xyz.ctypes.data, tets.shape[0], tets.ctypes.data,
+                                    dr.ctypes.data, None if ow is None else ow.ctypes.data)
+        o = default_options(delta=int(delta), nu_pre=int(nu_pre), nu_post=int(nu_post),
+                            restart=int(restart), max_it=int(max_it),
+                            factor_precision={"f64": MSP_F64, "f32": MSP_F32}[precision],
+                            coef_kind={"const": MSP_K_CONST, "cosexp": MSP_K_COSEXP}[coef],
+                            coef_scale=float(scale),
+                            load_kind={"one": MSP_F_ONE, "sines": MSP_F_SINES}[load],
+                            host_only=1 if host_only else 0,
+                            mem_budget_bytes=int(budget_bytes))
+        if wave is not None:
+            w = np.asarray(wave, np.int32).reshape(8, 3)
+            for j in range(8):
+                for d in range(3):
+                    o.wave[j][d] = int(w[j, d])
+        if torch_alloc and not host_only:
+            a, f = _torch_allocator()
+            o.alloc, o.free = a, f
+            self._keep.append((a, f))
+        self.options = o
+        h = C.c_void_p()
+        _check(lib.msp_load_hierarchy(arr, len(levels), C.byref(o), C.byref(h)))
+        self.h = h
+        self.nlevels = len(levels)
+        self.coef = coef
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().msp_free_hierarchy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def info(self, level=0) -> dict:
+        inf = msp_level_info()
+        _check(load().msp_hierarchy_info(self.h, level, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in msp_level_info._fields_}
+
+    def array(self, level, name) -> np.ndarray:
+        lib = load()
+        what = ARRAYS[name]
+        nb = C.c_size_t(0)
+        _check(lib.msp_hierarchy_copy(self.h, level, what, None, 0, C.byref(nb)))
+        out = np.empty(nb.value // np.dtype(_ARRAY_DTYPE[name]).itemsize, _ARRAY_DTYPE[name])
+        _check(lib.msp_hierarchy_copy(self.h, level, what, _ptr(out), out.nbytes, C.byref(nb)))
+        return out
+
+    def assemble(self, mu=None, stream=None) -> "Instance":
+        return Instance(self, mu, stream)
+
+
+class Instance:
+    """msp_assemble ... msp_free_instance for one parameter vector."""
+
+    def __init__(self, h: Hierarchy, mu=None, stream=None):
+        self.hier = h
+        self._mu = np.zeros(8) if mu is None else np.ascontiguousarray(mu, np.float64)
+        self.stream = _stream_ptr(stream)
+        inst = C.c_void_p()
+        _check(load().msp_assemble(h.h, _ptr(self._mu), 8, self.stream, C.byref(inst)))
+        self.inst = inst
+
+    def close(self):
+        if getattr(self, "inst", None):
+            load().msp_free_instance(self.inst)
+            self.inst = None
+
+    def __del__(self):
+        self.close()
+
+    def reassemble(self, mu):
+        self._mu = np.ascontiguousarray(mu, np.float64)
+        _check(load().msp_reassemble(self.inst, _ptr(self._mu), 8))
+
+    def factor(self):
+        _check(load().msp_factor(self.inst))
+
+    def apply(self, r, z, stream=None):
+        _check(load().msp_apply(self.inst, _ptr(r), _ptr(z),
+                                self.stream if stream is None else _stream_ptr(stream)))
+
+    def apply_op(self, op, level, x, y, stream=None):
+        _check(load().msp_apply_op(self.inst, int(op), int(level), _ptr(x), _ptr(y),
+                                   self.stream if stream is None else _stream_ptr(stream)))
+
+    def solve(self, x, b=None, rtol=1e-8, raise_on_fail=True) -> dict:
+        st = msp_stats()
+        rc = load().msp_solve(self.inst, _ptr(b), _ptr(x), float(rtol), C.byref(st))
+        if rc not in (MSP_OK, MSP_ERR_NOT_CONVERGED) or (raise_on_fail and rc != MSP_OK):
+            _check(rc)
+        return {k: getattr(st, k) for k, _ in msp_stats._fields_}
+
+    def solve_host(self, mu, x_host, b_host=None, rtol=1e-8, raise_on_fail=True) -> dict:
+        st = msp_stats()
+        mu = np.ascontiguousarray(mu, np.float64)
+        rc = load().msp_solve_host(self.inst, _ptr(mu), 8, _ptr(b_host), _ptr(x_host),
+                                   float(rtol), C.byref(st))
+        if rc not in (MSP_OK, MSP_ERR_NOT_CONVERGED) or (raise_on_fail and rc != MSP_OK):
+            _check(rc)
+        return {k: getattr(st, k) for k, _ in msp_stats._fields_}
+
+    def array(self, level, name, sub=0, dtype=np.float64) -> np.ndarray:
+        lib = load()
+        nb = C.c_size_t(0)
+        _check(lib.msp_instance_copy(self.inst, level, ARRAYS[name], sub, None, 0, C.byref(nb)))
+        out = np.empty(nb.value // np.dtype(dtype).itemsize, dtype)
+        _check(lib.msp_instance_copy(self.inst, level, ARRAYS[name], sub, _ptr(out), out.nbytes,
+                                     C.byref(nb)))
+        return out
+
+    def profile_enable(self, classes=()):
+        mask = 0
+        for c in classes:
+            mask |= 1 << KERNEL_CLASSES.index(c)
+        _check(load().msp_profile_enable(self.inst, mask))
+
+    def profile_reset(self):
+        _check(load().msp_profile_reset(self.inst))
+
+    def profile(self) -> dict:
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            p = msp_kernel_profile()
+            _check(load().msp_profile_read(self.inst, i, C.byref(p)))
+            out[name] = {k: getattr(p, k) for k, _ in msp_kernel_profile._fields_}
+        return out
+
+
+def unpack_factor(flat: np.ndarray, n: int):
+    """Dense (L, D) of one subdomain from its tiled factor storage (test helper).
+
+    Returns L (unit lower, n x n) and d (n,), reading tiles (I, J), J <= I,
+    at I (I+1)/2 + J as described in msp.h.
+    """
+    T = MSP_TILE
+    nt = (n + T - 1) // T
+    N = nt * T
+    full = np.zeros((N, N), dtype=np.float64)
+    for I in range(nt):
+        for J in range(I + 1):
+            t = I * (I + 1) // 2 + J
+            full[I * T:(I + 1) * T, J * T:(J + 1) * T] = flat[t * T * T:(t + 1) * T * T].reshape(T, T)
+    d = np.diag(full).copy()
+    L = np.tril(full, -1) + np.eye(N)
+    return L[:n, :n], d[:n]

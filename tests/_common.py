@@ -1,0 +1,35 @@
+"""Shared helpers of the test suite: the same seeded workload is handed to the
+oracle and to the library, each through its own entry points."""
+import numpy as np
+
+import synthetic as syn
+
+# small parity workloads (oracle finishes in seconds, several tiles + a ragged tail)
+PARITY = ["cube8_2lvl", "cube16_3lvl", "cube20_3lvl"]
+
+syn.WORKLOADS.setdefault("cube20_3lvl", dict(ns=(20, 10, 5), parts=((3, 3, 3), (2, 2, 2)),
+                                              delta=2, nu=2, coef="cosexp", scale=1.0,
+                                              load="one", rtol=1e-10, restart=30))
+
+
+def workload(name, hierarchy_id=0):
+    return syn.workload(name, hierarchy_id)
+
+
+def make_oracle(levels, w, orc):
+    return orc.Oracle(levels, delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], coef=w["coef"],
+                      wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
+
+
+def make_hierarchy(levels, w, P, **kw):
+    args = dict(delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], restart=w["restart"],
+                coef=w["coef"], wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
+    args.update(kw)
+    return P.Hierarchy(levels, **args)
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)

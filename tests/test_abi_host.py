@@ -1,0 +1,116 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol that
+include/msp.h declares, and its host-side set-up (CSR pattern, subdomains,
+interpolation P and P^T) matches the oracle bit-exactly on the index
+structures (values of P to 1e-13)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from _common import make_hierarchy, make_oracle, workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2412_08981_gb300 import build as b
+    b.build()
+    import paper_2412_08981_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "msp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(msp_\w+)\s*\(", src))
+    # drop typedef'd function-pointer types
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_library_exports_every_declared_symbol(P):
+    lib = P.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", P.msp.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+    assert set(P.msp.EXPORTS) <= set(names)
+    assert lib.msp_version().startswith(b"msp")
+
+
+@pytest.mark.parametrize("name", ["cube8_2lvl", "cube16_3lvl", "cube20_3lvl"])
+def test_host_structures_match_oracle(P, orc, name):
+    levels, w = workload(name)
+    h = make_hierarchy(levels, w, P, host_only=True)
+    o = make_oracle(levels, w, orc)
+    L = len(levels)
+    for l in range(L):
+        np.testing.assert_array_equal(h.array(l, "rowptr"), o.get("rowptr", l))
+        np.testing.assert_array_equal(h.array(l, "col"), o.get("col", l))
+    for l in range(L - 1):
+        subs = o.subdomains(l)
+        sp, sd, so = h.array(l, "sub_ptr"), h.array(l, "sub_dofs"), h.array(l, "sub_own")
+        assert sp.size - 1 == len(subs)
+        for p, (d, ow) in enumerate(subs):
+            np.testing.assert_array_equal(sd[sp[p]:sp[p + 1]], d)
+            np.testing.assert_array_equal(so[sp[p]:sp[p + 1]], ow)
+        for a in ("P_rowptr", "P_col", "PT_rowptr", "PT_col"):
+            np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+        np.testing.assert_allclose(h.array(l, "P_val"), o.get("P_val", l), atol=1e-13)
+        np.testing.assert_allclose(h.array(l, "PT_val"), o.get("PT_val", l), atol=1e-13)
+    # coarsest block = all interior DoFs
+    sd = h.array(L - 1, "sub_dofs")
+    np.testing.assert_array_equal(sd, np.where(levels[-1].dirichlet == 0)[0])
+    info = h.info(0)
+    assert info["nnz"] == o.get("col", 0).size
+    assert info["n_sub"] == o.get("n_subs", 0)
+
+
+def test_odd_partition_and_empty_boxes(P, orc):
+    """Partition ids that skip values and boxes with only Dirichlet nodes."""
+    fine = syn.cube_level(9, 3, parts=(5, 3, 2))
+    fine.owner = (fine.owner * 7 + 3).astype(np.int32)  # sparse, non-contiguous ids
+    coarse = syn.cube_level(4, 4)
+    w = dict(delta=1, nu=1, coef="const", scale=1.0, load="one", restart=10)
+    h = make_hierarchy([fine, coarse], w, P, host_only=True)
+    o = make_oracle([fine, coarse], w, orc)
+    subs = o.subdomains(0)
+    sp, sd = h.array(0, "sub_ptr"), h.array(0, "sub_dofs")
+    assert sp.size - 1 == len(subs)
+    for p, (d, _) in enumerate(subs):
+        np.testing.assert_array_equal(sd[sp[p]:sp[p + 1]], d)
+
+
+def test_invalid_inputs_are_rejected(P):
+    lv = syn.cube_level(3, 1, parts=(1, 1, 1))
+    co = syn.cube_level(2, 2)
+    bad = syn.cube_level(3, 1, parts=(1, 1, 1))
+    bad.tets = bad.tets.copy()
+    bad.tets[5, 3] = bad.tets[5, 2]  # degenerate tet
+    with pytest.raises(P.MspError) as e:
+        P.Hierarchy([bad, co], host_only=True)
+    assert e.value.code == P.msp.MSP_ERR_INVALID
+    bad2 = syn.cube_level(3, 1, parts=(1, 1, 1))
+    bad2.tets = bad2.tets.copy()
+    bad2.tets[0, 0] = 10 ** 6  # out of range
+    with pytest.raises(P.MspError):
+        P.Hierarchy([bad2, co], host_only=True)
+    nown = syn.cube_level(3, 1)  # no owner on a smoothed level
+    with pytest.raises(P.MspError):
+        P.Hierarchy([nown, co], host_only=True)
+    with pytest.raises(P.MspError):
+        P.Hierarchy([lv, co], restart=0, host_only=True)
+    with pytest.raises(P.MspError):
+        P.Hierarchy([lv, co], delta=-1, host_only=True)
+    h = P.Hierarchy([lv, co], host_only=True)
+    with pytest.raises(P.MspError):  # no device state on a host-only handle
+        h.assemble(np.zeros(8), stream=0)

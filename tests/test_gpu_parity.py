@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every operator of the hot path is compared element by element on the same
+seeded inputs: assembly, load vector, SpMV, P and P^T, subdomain factors, the
+RAS application, the coarsest solve, the whole V-cycle and the FGMRES
+solution.  Tolerances: FP64 operators <= 1e-12 relative (norm-wise, the per
+operator bound of the method's FP64 path), solution <= 1e-7 relative at
+rtol 1e-10.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from _common import PARITY, make_hierarchy, make_oracle, rel, workload
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2412_08981_gb300 import build as b
+    b.build()
+    import paper_2412_08981_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+class Case:
+    def __init__(self, name, P, orc, torch, mu_req=0, **kw):
+        self.levels, self.w = workload(name)
+        self.mu = syn.mu_draw(mu_req)
+        self.o = make_oracle(self.levels, self.w, orc)
+        self.o.assemble(self.mu)
+        self.o.factor()
+        self.h = make_hierarchy(self.levels, self.w, P, **kw)
+        self.inst = self.h.assemble(self.mu, stream=torch.cuda.current_stream())
+        self.inst.factor()
+        self.torch = torch
+        self.n = [lv.n_nodes for lv in self.levels]
+
+    def dev(self, x):
+        return self.torch.tensor(np.asarray(x, np.float64), device="cuda")
+
+    def zeros(self, n):
+        return self.torch.zeros(n, dtype=self.torch.float64, device="cuda")
+
+    def host(self, t):
+        self.torch.cuda.synchronize()
+        return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=PARITY)
+def case(request, P, orc, torch):
+    return Case(request.param, P, orc, torch)
+
+
+def test_assembly_and_load(case):
+    for l in range(len(case.levels)):
+        vg = case.inst.array(l, "val")
+        vo = case.o.get("val", l)
+        assert np.max(np.abs(vg - vo)) <= 1e-13 * np.max(np.abs(vo))
+    bg = case.h.array(0, "load")
+    assert rel(bg, case.o.get("b", 0)) <= 1e-14
+
+
+def test_spmv_and_transfers(case, P):
+    rng = np.random.default_rng(1)
+    m = P.msp
+    for l in range(len(case.levels)):
+        x = rng.normal(size=case.n[l])
+        y = case.zeros(case.n[l])
+        case.inst.apply_op(m.MSP_OP_SPMV, l, case.dev(x), y)
+        assert rel(case.host(y), case.o.spmv(x, l)) <= 1e-14
+        # residual form: y = r - A x
+        r = rng.normal(size=case.n[l])
+        yr = case.dev(r)
+        case.inst.apply_op(m.MSP_OP_RESIDUAL, l, case.dev(x), yr)
+        assert rel(case.host(yr), r - case.o.spmv(x, l)) <= 1e-13
+    for l in range(len(case.levels) - 1):
+        xc = rng.normal(size=case.n[l + 1])
+        yf = case.zeros(case.n[l])
+        case.inst.apply_op(m.MSP_OP_INTERP, l, case.dev(xc), yf)
+        assert rel(case.host(yf), case.o.interp(xc, l)) <= 1e-14
+        xf = rng.normal(size=case.n[l])
+        yc = case.zeros(case.n[l + 1])
+        case.inst.apply_op(m.MSP_OP_RESTRICT, l, case.dev(xf), yc)
+        assert rel(case.host(yc), case.o.restrict(xf, l)) <= 1e-14
+
+
+def test_subdomain_factors(case, P):
+    """L and D of sampled blocks vs the oracle's Doolittle LU (U = D L^T)."""
+    for l in range(len(case.levels)):
+        coarse = l == len(case.levels) - 1
+        ns = 1 if coarse else case.o.get("n_subs", l)
+        for p in sorted(set([0, ns // 2, ns - 1])):
+            sub = -1 if coarse else p
+            dofs = case.o.get("sub_dofs", l, sub)
+            n = dofs.size
+            LU = case.o.get("sub_lu", l, sub).reshape(n, n)
+            Lo = np.tril(LU, -1) + np.eye(n)
+            do = np.diag(LU)
+            Lg, dg = P.msp.unpack_factor(case.inst.array(l, "factor", sub), n)
+            assert np.max(np.abs(Lg - Lo)) <= 1e-10 * max(1.0, np.max(np.abs(Lo)))
+            assert rel(dg, do) <= 1e-12
+            # the symmetric factors reproduce the block: L D L^T = A_p
+            A = case.o.csr(l).toarray()[np.ix_(dofs, dofs)]
+            assert np.linalg.norm(Lg @ np.diag(dg) @ Lg.T - A) <= 1e-13 * np.linalg.norm(A)
+
+
+def test_ras_and_coarse_solve(case, P):
+    rng = np.random.default_rng(2)
+    m = P.msp
+    L = len(case.levels)
+    for l in range(L - 1):
+        r = rng.normal(size=case.n[l])
+        z = case.zeros(case.n[l])
+        case.inst.apply_op(m.MSP_OP_RAS, l, case.dev(r), z)
+        assert rel(case.host(z), case.o.ras_apply(r, l)) <= OP_TOL
+    r = rng.normal(size=case.n[-1])
+    z = case.zeros(case.n[-1])
+    case.inst.apply_op(m.MSP_OP_COARSE, L - 1, case.dev(r), z)
+    assert rel(case.host(z), case.o.coarse_solve(r)) <= OP_TOL
+
+
+def test_vcycle(case):
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        r = rng.normal(size=case.n[0])
+        z = case.zeros(case.n[0])
+        case.inst.apply(case.dev(r), z)
+        assert rel(case.host(z), case.o.vcycle(r)) <= OP_TOL
+
+
+def test_fgmres_solution(case):
+    rtol = 1e-10
+    xo, so = case.o.fgmres(rtol=rtol, restart=case.w["restart"])
+    x = case.zeros(case.n[0])
+    st = case.inst.solve(x, rtol=rtol)
+    assert st["status"] == 0 and st["rel_residual"] <= rtol
+    assert abs(st["iterations"] - so["iters"]) <= 1
+    assert rel(case.host(x), xo) <= 1e-7
+    # user right-hand side through the same call
+    b = np.random.default_rng(4).normal(size=case.n[0])
+    b[case.levels[0].dirichlet == 1] = 0.0
+    xb = case.zeros(case.n[0])
+    st = case.inst.solve(xb, b=case.dev(b), rtol=rtol)
+    xob, _ = case.o.fgmres(b, rtol=rtol, restart=case.w["restart"])
+    assert st["status"] == 0 and rel(case.host(xb), xob) <= 1e-7
+
+
+def test_solve_host_end_to_end(case):
+    """The host-buffer entry point: re-assemble, factor, solve, copy back."""
+    x = np.zeros(case.n[0])
+    mu2 = syn.mu_draw(17)
+    st = case.inst.solve_host(mu2, x, rtol=1e-10)
+    case.o.assemble(mu2)
+    case.o.factor()
+    xo, _ = case.o.fgmres(rtol=1e-10, restart=case.w["restart"])
+    assert st["status"] == 0 and rel(x, xo) <= 1e-7
+    # back to the fixture's parameter for the other tests of this module
+    case.o.assemble(case.mu)
+    case.o.factor()
+    case.inst.reassemble(case.mu)
+    case.inst.factor()
+
+
+# ------------------------------------------------------------- edge cases
+def test_single_level_is_a_direct_solve(P, orc, torch):
+    lv = syn.cube_level(6, 9)
+    w = dict(delta=1, nu=2, coef="cosexp", scale=1.0, load="one", restart=30)
+    h = make_hierarchy([lv], w, P)
+    mu = syn.mu_draw(3)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(lv.n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-12)
+    assert st["iterations"] == 1
+    o = make_oracle([lv], w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, _ = o.fgmres(rtol=1e-12)
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
+
+
+@pytest.mark.parametrize("delta,nu", [(0, 1), (1, 0), (3, 3)])
+def test_overlap_and_smoothing_variants(P, orc, torch, delta, nu):
+    levels = syn.hierarchy((10, 5), ((3, 2, 2),))
+    w = dict(delta=delta, nu=nu, coef="cosexp", scale=1.0, load="one", restart=20)
+    o = make_oracle(levels, w, orc)
+    mu = syn.mu_draw(8)
+    o.assemble(mu)
+    o.factor()
+    h = make_hierarchy(levels, w, P)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    r = np.random.default_rng(5).normal(size=levels[0].n_nodes)
+    z = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    inst.apply(torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), o.vcycle(r)) <= OP_TOL
+    x = torch.zeros_like(z)
+    st = inst.solve(x, rtol=1e-10)
+    xo, so = o.fgmres(rtol=1e-10, restart=20)
+    assert st["status"] == 0 and rel(x.cpu().numpy(), xo) <= 1e-7
+
+
+def test_zero_rhs_and_bad_inputs(P, torch):
+    levels, w = workload("cube8_2lvl")
+    h = make_hierarchy(levels, w, P)
+    inst = h.assemble(np.zeros(8), stream=torch.cuda.current_stream())
+    n = levels[0].n_nodes
+    x = torch.ones(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.MspError):  # not factored yet
+        inst.solve(x)
+    inst.factor()
+    st = inst.solve(x, b=torch.zeros_like(x))
+    assert st["status"] == 0 and st["iterations"] == 0 and not x.any()
+    h2 = make_hierarchy(*workload("cube16_3lvl"), P)
+    with pytest.raises(P.MspError) as e:
+        h2.assemble(np.array([np.nan] + [0.0] * 7), stream=torch.cuda.current_stream())
+    assert e.value.code == P.msp.MSP_ERR_INVALID
+    with pytest.raises(P.MspError):  # aliasing input and output
+        inst.apply(x, x)
+
+
+def test_memory_budget_refuses_instances(P, torch):
+    levels, w = workload("cube8_2lvl")
+    h = make_hierarchy(levels, w, P, budget_bytes=1)
+    with pytest.raises(P.MspError) as e:
+        h.assemble(np.zeros(8), stream=torch.cuda.current_stream())
+    assert e.value.code == P.msp.MSP_ERR_OOM
+
+
+def test_not_converged_reports_partial_stats(P, torch):
+    levels, w = workload("cube16_3lvl")
+    h = make_hierarchy(levels, w, P, max_it=2)
+    inst = h.assemble(syn.mu_draw(1), stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-14, raise_on_fail=False)
+    assert st["status"] == P.msp.MSP_ERR_NOT_CONVERGED and st["iterations"] == 2
+    assert 0 < st["rel_residual"] < 1
+
+
+def test_fp32_factors_reach_fp64_accuracy(P, orc, torch):
+    """FP32 subdomain factors under the FP64 outer loop: same tolerance on x."""
+    levels, w = workload("cube16_3lvl")
+    mu = syn.mu_draw(2)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10)
+    h = make_hierarchy(levels, w, P, precision="f32")
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= so["iters"] + 3
+
+
+def test_results_reproducible_bitwise(P, torch):
+    levels, w = workload("cube16_3lvl")
+    h = make_hierarchy(levels, w, P)
+    inst = h.assemble(syn.mu_draw(5), stream=torch.cuda.current_stream())
+    inst.factor()
+    n = levels[0].n_nodes
+    xs = []
+    for _ in range(2):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        inst.solve(x, rtol=1e-10)
+        xs.append(x.cpu().numpy())
+    np.testing.assert_array_equal(xs[0], xs[1])

@@ -205,13 +205,14 @@ def run_msp(args):
         inst = h.assemble(mu_of(0), stream=stream)
         n = levels[0].n_nodes
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        iters = []
+        iters, relres = [], []
 
         def step(i):
             inst.reassemble(mu_of(i))
             inst.factor()
             st = inst.solve(x, rtol=args.rtol)
             iters.append(st["iterations"])
+            relres.append(st["rel_residual"])
             return st
 
         # warm-up, with every kernel class timed to find the dominant one
@@ -245,7 +246,7 @@ def run_msp(args):
         lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
         prof = inst.profile()
         launches = int(sum(v["launches"] for v in prof.values()))
-        out = dict(ms=ms, lat=lat, iters=list(iters), prof=prof, dominant=dominant,
+        out = dict(ms=ms, lat=lat, iters=list(iters), relres=list(relres), prof=prof, dominant=dominant,
                    shares=shares, launches=launches, clocks=clocks, x=x.cpu().numpy())
         # end to end through the host-buffer entry point
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -285,7 +286,9 @@ def run_msp(args):
                  "latency_ms": {"p50": float(np.percentile(mres["lat"], 50)),
                                 "p99": float(np.percentile(mres["lat"], 99))},
                  "iterations_mean": float(np.mean(mres["iters"])),
-                 "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"]}
+                 "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"],
+                 "final_rel_residual_max": float(np.max(mres["relres"])),
+                 "kernel_time_shares_warmup": mres["shares"]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -320,6 +323,7 @@ def run_msp(args):
         "latency_ms": {"p50": float(np.percentile(res["lat"], 50)),
                        "p99": float(np.percentile(res["lat"], 99))},
         "iterations_mean": float(np.mean(res["iters"])),
+        "final_rel_residual_max": float(np.max(res["relres"])),
         "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"],
         "roofline": roof,
     }

@@ -192,15 +192,17 @@ def test_single_level_is_a_direct_solve(P, orc, torch):
     assert rel(x.cpu().numpy(), xo) <= 1e-10
 
 
-@pytest.mark.parametrize("delta,nu", [(0, 1), (1, 0), (3, 3)])
-def test_overlap_and_smoothing_variants(P, orc, torch, delta, nu):
+@pytest.mark.parametrize("delta,nu_pre,nu_post", [(0, 1, 1), (1, 0, 2), (3, 3, 1)])
+def test_overlap_and_smoothing_variants(P, orc, torch, delta, nu_pre, nu_post):
+    """No overlap (block Jacobi smoother), no pre-smoothing, asymmetric counts."""
     levels = syn.hierarchy((10, 5), ((3, 2, 2),))
-    w = dict(delta=delta, nu=nu, coef="cosexp", scale=1.0, load="one", restart=20)
-    o = make_oracle(levels, w, orc)
+    w = dict(delta=delta, nu=1, coef="cosexp", scale=1.0, load="one", restart=20)
+    o = orc.Oracle(levels, delta=delta, nu_pre=nu_pre, nu_post=nu_post, coef="cosexp",
+                   wave=syn.wave_vectors(), load="one")
     mu = syn.mu_draw(8)
     o.assemble(mu)
     o.factor()
-    h = make_hierarchy(levels, w, P)
+    h = make_hierarchy(levels, w, P, nu_pre=nu_pre, nu_post=nu_post)
     inst = h.assemble(mu, stream=torch.cuda.current_stream())
     inst.factor()
     r = np.random.default_rng(5).normal(size=levels[0].n_nodes)
@@ -211,7 +213,8 @@ def test_overlap_and_smoothing_variants(P, orc, torch, delta, nu):
     x = torch.zeros_like(z)
     st = inst.solve(x, rtol=1e-10)
     xo, so = o.fgmres(rtol=1e-10, restart=20)
-    assert st["status"] == 0 and rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
 
 
 def test_zero_rhs_and_bad_inputs(P, torch):
@@ -268,6 +271,19 @@ def test_fp32_factors_reach_fp64_accuracy(P, orc, torch):
     assert st["status"] == 0 and st["rel_residual"] <= 1e-10
     assert rel(x.cpu().numpy(), xo) <= 1e-7
     assert st["iterations"] <= so["iters"] + 3
+    # the smoother really runs in FP32: one RAS application differs from the
+    # FP64 one at single-precision level, not at double-precision level
+    r = np.random.default_rng(6).normal(size=levels[0].n_nodes)
+    z = torch.zeros_like(x)
+    inst.apply_op(P.msp.MSP_OP_RAS, 0, torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    d = rel(z.cpu().numpy(), o.ras_apply(r, 0))
+    assert 1e-10 < d < 1e-4, d
+    fac = inst.array(0, "factor", 0, dtype=np.float32)
+    Lg, dg = P.msp.unpack_factor(fac.astype(np.float64), o.get("sub_dofs", 0, 0).size)
+    n0 = o.get("sub_dofs", 0, 0).size
+    do = np.diag(o.get("sub_lu", 0, 0).reshape(n0, n0))
+    assert 1e-12 < rel(dg, do) < 1e-5
 
 
 def test_results_reproducible_bitwise(P, torch):

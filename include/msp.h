@@ -192,6 +192,8 @@ MSP_API int msp_apply_op(msp_instance* inst, int op, int level, const double* x_
 /* ---- introspection: copy a named array into host memory ----
  * Hierarchy arrays (index structures, host-resident):
  *   MSP_ARR_ROWPTR, MSP_ARR_COL (int32), MSP_ARR_SUB_PTR, MSP_ARR_SUB_DOFS (int32),
+ *   MSP_ARR_SUB_NT (int32 tiles per side of each block), MSP_ARR_TILE_FIRST (int32
+ *   F_I of every tile row, blocks concatenated; see MSP_TILE),
  *   MSP_ARR_SUB_OWN (uint8), MSP_ARR_P_ROWPTR, MSP_ARR_P_COL (int32),
  *   MSP_ARR_P_VAL (double), MSP_ARR_PT_ROWPTR, MSP_ARR_PT_COL (int32),
  *   MSP_ARR_PT_VAL (double), MSP_ARR_LOAD (double, device-resident b)
@@ -205,19 +207,22 @@ typedef enum msp_array {
   MSP_ARR_ROWPTR = 0, MSP_ARR_COL = 1, MSP_ARR_SUB_PTR = 2, MSP_ARR_SUB_DOFS = 3,
   MSP_ARR_SUB_OWN = 4, MSP_ARR_P_ROWPTR = 5, MSP_ARR_P_COL = 6, MSP_ARR_P_VAL = 7,
   MSP_ARR_PT_ROWPTR = 8, MSP_ARR_PT_COL = 9, MSP_ARR_PT_VAL = 10, MSP_ARR_LOAD = 11,
-  MSP_ARR_VAL = 12, MSP_ARR_FACTOR = 13
+  MSP_ARR_VAL = 12, MSP_ARR_FACTOR = 13, MSP_ARR_SUB_NT = 14, MSP_ARR_TILE_FIRST = 15
 } msp_array;
 MSP_API int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, size_t cap,
                        size_t* bytes_out);
 MSP_API int msp_instance_copy(const msp_instance* inst, int level, int what, int sub, void* dst,
                       size_t cap, size_t* bytes_out);
 
-/* Tile edge of the factor storage: every subdomain block of n_p DoFs is padded
- * to NT = ceil(n_p / 64) tiles per side (padding is an identity block) and
- * stored as its lower tile triangle, tile (I, J), J <= I, at index
- * I (I + 1) / 2 + J, each tile 64 x 64 row-major.  In a diagonal tile the
- * strict lower part holds L, the diagonal holds D and the strict upper part
- * holds the transpose of the inverse of the unit lower diagonal block. */
+/* Tile edge of the factor storage.  Every block of n_p DoFs (ascending global
+ * ids) is padded to NT = ceil(n_p / 64) tiles per side (the padding is an
+ * identity block).  Only its tile envelope is stored: tile row I holds the
+ * tiles (I, F_I) .. (I, I), 64 x 64 row-major each, rows one after another,
+ * where F_I (nondecreasing) is the first tile column with a nonzero in tile
+ * rows >= I.  Without pivoting the factors stay inside that envelope.  In a
+ * diagonal tile the strict lower part holds L, the diagonal holds D and the
+ * strict upper part holds the transpose of the inverse of the unit lower
+ * diagonal block of L. */
 #define MSP_TILE 64
 
 /* ---- per-kernel accounting ----

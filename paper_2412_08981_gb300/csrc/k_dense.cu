@@ -5,11 +5,15 @@
 //     pivoting is needed and half of the LU work is skipped),
 //   * the RAS application z = sum_p R0_p^T (L D L^T)^{-1} R_p t.
 //
-// Tile layout (see msp.h): 64 x 64 row-major tiles, lower tile triangle of
-// each block, tile (I, J) at index I (I + 1) / 2 + J.  Diagonal tiles hold L
-// below the diagonal, D on it and X^T above it, X = inverse of the unit lower
-// diagonal block of L; the triangular solves use X, so every step is a dense
-// product and the only sequential dependency is between tile rows.
+// Tile layout (see msp.h): 64 x 64 row-major tiles over the tile envelope of
+// each block; tile row I holds the tiles (I, F_I) .. (I, I) contiguously.  The
+// blocks are banded (DoFs in ascending global order), fill stays inside the
+// envelope, so the tiles left of F_I are never stored, read or updated: the
+// arithmetic on every stored entry is that of the full dense factorisation.
+// Diagonal tiles hold L below the diagonal, D on it and X^T above it, X =
+// inverse of the unit lower diagonal block of L; the triangular solves use X,
+// so every step is a dense product and the only sequential dependency is
+// between tile rows.
 //
 // On GB300 FP64 runs on the SIMT pipe at ~1/64 of the FP32 rate (there is no
 // fast FP64 tensor path), so the FP64 kernels are ALU-bound: their design
@@ -26,10 +30,14 @@ namespace {
 constexpr int T64 = 64;
 constexpr int TE = T64 * T64;
 
-__device__ inline int64_t tri(int i) { return (int64_t)i * (i + 1) / 2; }
-
 template <typename T> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = float; };
+
+// element offset of tile (I, J), J >= F_I, of subdomain p
+__device__ inline int64_t tile_at(const EnvDev& E, int p, int I, int J) {
+  const int rb = E.trow[p] + I;
+  return E.fac_off[p] + (int64_t)(E.toff[rb] + (J - E.first[rb])) * TE;
+}
 
 // ------------------------------------------------------------ extraction
 template <typename T>
@@ -53,15 +61,14 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 // (column by column: scale the column by 1/d, then update the trailing lower
 // triangle with l_r d l_s), then forms X = L^{-1} one column per thread.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac,
-                                                   const int64_t* __restrict__ fac_off,
+__global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
                                                    const int32_t* __restrict__ order, int k,
                                                    int* __restrict__ info) {
   extern __shared__ double sm[];
   double* A = sm;               // [64][65]
   double* X = sm + 64 * 65;     // [64][65]
   const int p = order[blockIdx.x];
-  T* tile = fac + fac_off[p] + (tri(k) + k) * TE;
+  T* tile = fac + tile_at(E, p, k, k);
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
@@ -101,26 +108,22 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac,
 }
 
 // ----------------------------------------------------------- panel solve
-// L_ik = A_ik X^T D^{-1} for the tiles below the diagonal tile of step k.
-// Warp w owns the 8 columns 8w..8w+7 (X^T is upper triangular, so its loop
-// stops at 8w+7); each lane owns 2 rows.
+// L_ik = A_ik X^T D^{-1} for the tiles below the diagonal tile of step k,
+// k < i <= R_k.  Warp w owns the 8 columns 8w..8w+7 (X^T is upper
+// triangular, so its loop stops at 8w+7); each lane owns 2 rows.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac,
-                                                    const int64_t* __restrict__ fac_off,
-                                                    const int32_t* __restrict__ nt,
+__global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
-  const int NT = nt[p];
   const int i = k + 1 + blockIdx.x;
-  if (i >= NT) return;
+  if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
   AT* A = reinterpret_cast<AT*>(smraw);   // [64][65] panel tile
   AT* Xt = A + 64 * 65;                   // [64][64] X^T (upper, unit diagonal)
   AT* Dinv = Xt + 64 * 64;                // [64]
-  T* base = fac + fac_off[p];
-  const T* dtile = base + (tri(k) + k) * TE;
-  T* ptile = base + (tri(i) + k) * TE;
+  const T* dtile = fac + tile_at(E, p, k, k);
+  T* ptile = fac + tile_at(E, p, i, k);
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac,
 }
 
 // -------------------------------------------------------- trailing update
-// A_ij -= (L_ik D_k) L_jk^T for k < j <= i < NT.  One block per (i, j) pair;
-// each thread accumulates a 4x4 register block from k-major shared tiles.
+// A_ij -= (L_ik D_k) L_jk^T for k < j <= i <= R_k.  One block per (i, j)
+// pair; each thread accumulates a 4x4 register block from k-major tiles.
 __device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
   int x = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((x + 1) * (x + 2) / 2 <= t) ++x;
@@ -165,14 +168,11 @@ __device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac,
-                                                    const int64_t* __restrict__ fac_off,
-                                                    const int32_t* __restrict__ nt,
+__global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
-  const int NT = nt[p];
-  const int rem = NT - k - 1;
+  const int rem = E.last[E.trow[p] + k] - k;
   if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
   int a, b;
   pair_of(blockIdx.x, a, b);
@@ -181,11 +181,10 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac,
   constexpr int LD = 68;
   AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][LD] = L_ik[r][m] * d_m
   AT* Lt = Wt + 64 * LD;                  // [64 m][LD] = L_jk[c][m]
-  T* base = fac + fac_off[p];
-  const T* dt = base + (tri(k) + k) * TE;
-  const T* li = base + (tri(i) + k) * TE;
-  const T* lj = base + (tri(j) + k) * TE;
-  T* out = base + (tri(i) + j) * TE;
+  const T* dt = fac + tile_at(E, p, k, k);
+  const T* li = fac + tile_at(E, p, i, k);
+  const T* lj = fac + tile_at(E, p, j, k);
+  T* out = fac + tile_at(E, p, i, j);
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, m = e & 63;
@@ -229,14 +228,15 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac,
 // -------------------------------------------------------------- RAS solve
 // One block (8 warps) per subdomain; extra blocks copy t into z on the
 // Dirichlet nodes.  Gather t[dofs] -> y; forward sweep over tile rows
-// (y_I = X_II (t_I - sum_{J<I} L_IJ y_J)); y /= D; backward sweep
-// (x_I = X_II^T (y_I - sum_{J>I} L_JI^T x_J)); scatter the owned entries.
+// (y_I = X_II (t_I - sum_{F_I <= J < I} L_IJ y_J)); y /= D; backward sweep
+// (x_I = X_II^T (y_I - sum_{I < J <= R_I} L_JI^T x_J)); scatter the owned
+// entries.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ras_solve(
-    const T* __restrict__ fac, const int64_t* __restrict__ fac_off, const int32_t* __restrict__ nt,
-    const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ dofs,
-    const uint8_t* __restrict__ own, int nsub, const int32_t* __restrict__ dir_list, int ndir,
-    const double* __restrict__ t, double* __restrict__ z, int add) {
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own, int nsub,
+    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
+    double* __restrict__ z, int add) {
   using AT = typename Acc<T>::type;
   const int tid = threadIdx.x;
   if ((int)blockIdx.x >= nsub) {
@@ -248,14 +248,15 @@ __global__ void __launch_bounds__(256) k_ras_solve(
     return;
   }
   const int p = blockIdx.x;
-  const int NT = nt[p];
+  const int NT = E.nt[p];
+  const int rb = E.trow[p];
   const int off = sub_ptr[p];
   const int np_ = sub_ptr[p + 1] - off;
   extern __shared__ unsigned char smraw[];
   AT* y = reinterpret_cast<AT*>(smraw);   // [NT*64]
   AT* acc = y + NT * 64;                  // [64]
   AT* part = acc + 64;                    // [8][64]
-  const T* base = fac + fac_off[p];
+  const T* base = fac + E.fac_off[p];
   for (int li = tid; li < NT * 64; li += blockDim.x)
     y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
   __syncthreads();
@@ -265,9 +266,10 @@ __global__ void __launch_bounds__(256) k_ras_solve(
     AT s[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) s[q] = 0;
-    const T* rowt = base + tri(I) * TE;
-    for (int J = 0; J < I; ++J) {
-      const T* tl = rowt + (int64_t)J * TE;
+    const int F = E.first[rb + I];
+    const T* rowt = base + (int64_t)E.toff[rb + I] * TE;  // tile (I, F)
+    for (int J = F; J < I; ++J) {
+      const T* tl = rowt + (int64_t)(J - F) * TE;
       AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(256) k_ras_solve(
     }
     __syncthreads();
     // y_I = X acc, X[b][a] = dtile[a][b] for a < b (upper part of the diagonal tile)
-    const T* dtl = rowt + (int64_t)I * TE;
+    const T* dtl = rowt + (int64_t)(I - F) * TE;
     {
       const int bcol = tid & 63, pr = tid >> 6;  // 4 parts over a
       AT v = 0;
@@ -299,14 +301,16 @@ __global__ void __launch_bounds__(256) k_ras_solve(
   // diagonal scaling
   for (int li = tid; li < NT * 64; li += blockDim.x) {
     int I = li >> 6, r = li & 63;
-    y[li] = y[li] / (AT)base[(tri(I) + I) * TE + r * 65];
+    const int F = E.first[rb + I];
+    y[li] = y[li] / (AT)base[(int64_t)(E.toff[rb + I] + (I - F)) * TE + r * 65];
   }
   __syncthreads();
   // backward
   for (int I = NT - 1; I >= 0; --I) {
     AT s0 = 0, s1 = 0;
-    for (int J = I + 1; J < NT; ++J) {
-      const T* tl = base + (tri(J) + I) * TE;
+    const int R = E.last[rb + I];
+    for (int J = I + 1; J <= R; ++J) {
+      const T* tl = base + (int64_t)(E.toff[rb + J] + (I - E.first[rb + J])) * TE;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int r = warp * 8 + q;
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(256) k_ras_solve(
     }
     __syncthreads();
     // x_I[a] = acc[a] + sum_{b>a} X[b][a] acc[b] = acc[a] + sum_{b>a} dtile[a][b] acc[b]
-    const T* dtl = base + (tri(I) + I) * TE;
+    const T* dtl = base + (int64_t)(E.toff[rb + I] + (I - E.first[rb + I])) * TE;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int a = warp * 8 + q;
@@ -359,7 +363,7 @@ void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
 }
 
 template <typename T>
-void launch_ldlt_diag(T* fac, const int64_t* fac_off, const int32_t* order, int nactive, int k,
+void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                       int* info, cudaStream_t s) {
   if (nactive <= 0) return;
   size_t smem = 2 * 64 * 65 * sizeof(double);
@@ -368,12 +372,12 @@ void launch_ldlt_diag(T* fac, const int64_t* fac_off, const int32_t* order, int 
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ldlt_diag<T><<<nactive, 256, smem, s>>>(fac, fac_off, order, k, info);
+  k_ldlt_diag<T><<<nactive, 256, smem, s>>>(fac, E, order, k, info);
 }
 
 template <typename T>
-void launch_ldlt_panel(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
-                       int nactive, int k, int max_rows, cudaStream_t s) {
+void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
+                       int max_rows, cudaStream_t s) {
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = (64 * 65 + 64 * 64 + 64) * sizeof(AT);
@@ -382,12 +386,12 @@ void launch_ldlt_panel(T* fac, const int64_t* fac_off, const int32_t* nt, const 
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ldlt_panel<T><<<dim3(max_rows, nactive), 256, smem, s>>>(fac, fac_off, nt, order, k);
+  k_ldlt_panel<T><<<dim3(max_rows, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
 template <typename T>
-void launch_ldlt_trail(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
-                       int nactive, int k, int max_pairs, cudaStream_t s) {
+void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
+                       int max_pairs, cudaStream_t s) {
   if (nactive <= 0 || max_pairs <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = 2 * 64 * 68 * sizeof(AT);
@@ -396,14 +400,13 @@ void launch_ldlt_trail(T* fac, const int64_t* fac_off, const int32_t* nt, const 
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ldlt_trail<T><<<dim3(max_pairs, nactive), 256, smem, s>>>(fac, fac_off, nt, order, k);
+  k_ldlt_trail<T><<<dim3(max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
 template <typename T>
-void launch_ras_solve(const T* fac, const int64_t* fac_off, const int32_t* nt,
-                      const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int nsub,
-                      int max_nt, const int32_t* dir_list, int ndir, const double* t, double* z,
-                      int add, cudaStream_t s) {
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* sub_ptr, const int32_t* dofs,
+                      const uint8_t* own, int nsub, int max_nt, const int32_t* dir_list, int ndir,
+                      const double* t, double* z, int add, cudaStream_t s) {
   using AT = typename Acc<T>::type;
   size_t smem = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
   static bool attr = false;
@@ -413,22 +416,21 @@ void launch_ras_solve(const T* fac, const int64_t* fac_off, const int32_t* nt,
   }
   unsigned nb = (unsigned)nsub + nblk(ndir, 256);
   if (nb == 0) return;
-  k_ras_solve<T><<<nb, 256, smem, s>>>(fac, fac_off, nt, sub_ptr, dofs, own, nsub, dir_list, ndir,
-                                       t, z, add);
+  k_ras_solve<T><<<nb, 256, smem, s>>>(fac, E, sub_ptr, dofs, own, nsub, dir_list, ndir, t, z, add);
 }
 
 #define MSP_INST(T)                                                                              \
   template void launch_extract<T>(const int64_t*, const int32_t*, int64_t, const double*,        \
                                   int64_t, T*, cudaStream_t);                                    \
-  template void launch_ldlt_diag<T>(T*, const int64_t*, const int32_t*, int, int, int*,          \
+  template void launch_ldlt_diag<T>(T*, const EnvDev&, const int32_t*, int, int, int*,           \
                                     cudaStream_t);                                               \
-  template void launch_ldlt_panel<T>(T*, const int64_t*, const int32_t*, const int32_t*, int,    \
-                                     int, int, cudaStream_t);                                    \
-  template void launch_ldlt_trail<T>(T*, const int64_t*, const int32_t*, const int32_t*, int,    \
-                                     int, int, cudaStream_t);                                    \
-  template void launch_ras_solve<T>(const T*, const int64_t*, const int32_t*, const int32_t*,    \
-                                    const int32_t*, const uint8_t*, int, int, const int32_t*,    \
-                                    int, const double*, double*, int, cudaStream_t);
+  template void launch_ldlt_panel<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
+                                     cudaStream_t);                                              \
+  template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
+                                     cudaStream_t);                                              \
+  template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*,     \
+                                    const uint8_t*, int, int, const int32_t*, int,               \
+                                    const double*, double*, int, cudaStream_t);
 MSP_INST(double)
 MSP_INST(float)
 

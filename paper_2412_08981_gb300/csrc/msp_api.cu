@@ -110,13 +110,15 @@ struct DevLevel {
   uint8_t* sub_own = nullptr;
   int64_t* fac_off = nullptr;
   int64_t fac_elems = 0;
+  EnvDev env{};
   int64_t* ext_pos = nullptr;
   int32_t* ext_nz = nullptr;
   int64_t next = 0;
   std::vector<int> active;        // active[k] = #subdomains with NT > k
-  std::vector<double> trail_flops;  // algorithmic flops of trailing step k
-  double ldlt_flops = 0;          // sum_p n_p^3 / 3
-  int64_t sum_np = 0, sum_np2 = 0, sum_owned = 0;
+  std::vector<int> max_rows;      // max_p (R_k - k) at step k
+  std::vector<double> trail_flops;  // flops of trailing step k (tile envelope)
+  std::vector<double> panel_flops;  // flops of panel step k
+  int64_t sum_np = 0, env_elems = 0, sum_owned = 0;
   // transfer from level+1
   int64_t P_nnz = 0;
   int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
@@ -167,20 +169,22 @@ void finish_level_stats(const HostLevel& H, DevLevel& D) {
   D.max_nt = 0;
   for (int p = 0; p < H.nsub; ++p) D.max_nt = std::max(D.max_nt, H.sub_nt[p]);
   D.active.assign(D.max_nt + 1, 0);
+  D.max_rows.assign(D.max_nt + 1, 0);
   D.trail_flops.assign(D.max_nt + 1, 0.0);
-  D.ldlt_flops = 0;
-  D.sum_np = D.sum_np2 = D.sum_owned = 0;
+  D.panel_flops.assign(D.max_nt + 1, 0.0);
+  D.sum_np = D.sum_owned = 0;
+  D.env_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
+  const double tile_gemm = 2.0 * 64 * 64 * 64, tile_syrk = 2.0 * 64 * (64 * 65 / 2);
   for (int p = 0; p < H.nsub; ++p) {
     int nt = H.sub_nt[p];
-    double np_ = H.sub_ptr[p + 1] - H.sub_ptr[p];
-    D.sum_np += (int64_t)np_;
-    D.sum_np2 += (int64_t)np_ * (int64_t)np_;
-    D.ldlt_flops += np_ * np_ * np_ / 3.0;
+    D.sum_np += H.sub_ptr[p + 1] - H.sub_ptr[p];
+    const int32_t* R = &H.tile_last[H.sub_trow[p]];
     for (int k = 0; k < nt; ++k) {
       D.active[k]++;
-      int rem = nt - k - 1;
-      double off = (double)rem * (rem - 1) / 2, dg = rem;
-      D.trail_flops[k] += off * 2.0 * 64 * 64 * 64 + dg * 64.0 * (64 * 65 / 2) * 2.0;
+      int rem = R[k] - k;
+      D.max_rows[k] = std::max(D.max_rows[k], rem);
+      D.trail_flops[k] += (double)rem * (rem - 1) / 2 * tile_gemm + rem * tile_syrk;
+      D.panel_flops[k] += rem * (64.0 * 64 * 65);  // triangular X^T product + scaling
     }
   }
   for (uint8_t o : H.sub_own) D.sum_owned += o;
@@ -217,6 +221,12 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.sub_order = A.upload(H.sub_order);
   D.fac_off = A.upload(H.sub_fac_off);
   D.fac_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
+  D.env.fac_off = D.fac_off;
+  D.env.trow = A.upload(H.sub_trow);
+  D.env.first = A.upload(H.tile_first);
+  D.env.last = A.upload(H.tile_last);
+  D.env.toff = A.upload(H.tile_off);
+  D.env.nt = D.sub_nt;
   D.ext_pos = A.upload(H.ext_pos);
   D.ext_nz = A.upload(H.ext_nz);
   D.next = (int64_t)H.ext_pos.size();
@@ -293,22 +303,21 @@ void factor_level(msp_instance* I, int l, T* fac) {
   }
   for (int k = 0; k < D.max_nt; ++k) {
     int na = D.active[k];
-    int na1 = (k + 1 <= D.max_nt) ? D.active[k + 1] : 0;
     {
       ProfScope ps(I->prof, PK_LDLT_DIAG, s);
-      launch_ldlt_diag<T>(fac, D.fac_off, D.sub_order, na, k, I->info, s);
-      ps.account((double)na * 2 * 4096 * sizeof(T), (double)na * (64.0 * 64 * 64 / 3 + 64.0 * 64 * 64 / 3));
+      launch_ldlt_diag<T>(fac, D.env, D.sub_order, na, k, I->info, s);
+      ps.account((double)na * 2 * 4096 * sizeof(T), (double)na * (2.0 * 64 * 64 * 64 / 3));
     }
-    if (na1 > 0) {
-      int rows = D.max_nt - k - 1;
+    int rows = D.max_rows[k];
+    if (rows > 0) {
       {
         ProfScope ps(I->prof, PK_LDLT_PANEL, s);
-        launch_ldlt_panel<T>(fac, D.fac_off, D.sub_nt, D.sub_order, na1, k, rows, s);
-        ps.account(0, 0);
+        launch_ldlt_panel<T>(fac, D.env, D.sub_order, na, k, rows, s);
+        ps.account(0, D.panel_flops[k]);
       }
       {
         ProfScope ps(I->prof, PK_LDLT_TRAIL, s);
-        launch_ldlt_trail<T>(fac, D.fac_off, D.sub_nt, D.sub_order, na1, k, rows * (rows + 1) / 2, s);
+        launch_ldlt_trail<T>(fac, D.env, D.sub_order, na, k, rows * (rows + 1) / 2, s);
         ps.account(0, D.trail_flops[k]);
       }
     }
@@ -340,15 +349,16 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   ProfScope ps(I->prof, kind, s);
   size_t es = level_f32(h, l) ? 4 : 8;
   if (level_f32(h, l))
-    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.fac_off, D.sub_nt, D.sub_ptr,
-                            D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.sub_ptr, D.sub_dofs,
+                            D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
   else
-    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.fac_off, D.sub_nt, D.sub_ptr,
-                             D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
-  // algorithmic: every factor element read once per sweep pair (n_p^2 as in
-  // an L and U pair), gather + scatter of the DoF vectors
-  ps.account((double)D.sum_np2 * es + (double)D.sum_np * 13 + (double)D.sum_owned * (add ? 16 : 8),
-             2.0 * (double)D.sum_np2);
+    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr, D.sub_dofs,
+                             D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+  // algorithmic: the stored envelope of L read by each of the two sweeps
+  // (the element count of an L and U pair), gather + scatter of the vectors
+  ps.account(2.0 * (double)D.env_elems * es + (double)D.sum_np * 13 +
+                 (double)D.sum_owned * (add ? 16 : 8),
+             4.0 * (double)D.env_elems);
 }
 
 void spmv(msp_instance* I, int l, const double* x, double* y, const double* r, int mode,
@@ -909,6 +919,8 @@ int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, s
     case MSP_ARR_PT_ROWPTR: pick(H.PT_rowptr); break;
     case MSP_ARR_PT_COL: pick(H.PT_col); break;
     case MSP_ARR_PT_VAL: pick(H.PT_val); break;
+    case MSP_ARR_SUB_NT: pick(H.sub_nt); break;
+    case MSP_ARR_TILE_FIRST: pick(H.tile_first); break;
     case MSP_ARR_LOAD:
       if (h->host_only) return fail(MSP_ERR_INVALID, "host-only hierarchy has no load vector");
       src = h->dev[level].b;

@@ -48,7 +48,16 @@ struct HostLevel {
   std::vector<int32_t> sub_ptr;         // [nsub+1] offsets into sub_dofs
   std::vector<int32_t> sub_dofs;        // sorted DoFs of each subdomain
   std::vector<uint8_t> sub_own;         // owned flag (R^0) per entry of sub_dofs
-  std::vector<int32_t> sub_nt;          // tiles per side
+  std::vector<int32_t> sub_nt;          // tiles per side NT_p
+  // Tile envelope of every block (the blocks are ordered by ascending global
+  // DoF id, which makes them banded): tile row I of subdomain p holds the
+  // tiles (I, F_I) .. (I, I) contiguously; entries left of F_I are zero and
+  // stay zero through the factorisation (fill stays inside the envelope).
+  // Per-tile-row arrays are indexed by sub_trow[p] + I.
+  std::vector<int32_t> sub_trow;        // [nsub+1] offsets into the per-tile-row arrays
+  std::vector<int32_t> tile_first;      // F_I, nondecreasing in I
+  std::vector<int32_t> tile_last;       // R_I = last tile row J with F_J <= I
+  std::vector<int32_t> tile_off;        // index of tile (I, F_I) inside the subdomain storage
   std::vector<int64_t> sub_fac_off;     // [nsub+1] element offsets of each factor
   // dense extraction map: for subdomain p, entries ext_ptr[p]..ext_ptr[p+1]
   // give (absolute position in the level's factor storage, CSR nonzero index,

@@ -29,6 +29,15 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
                  cudaStream_t s);
 
 // ---- dense subdomain blocks (templated on the factor type T = double | float)
+// Device view of a level's tile envelopes (see msp_internal.h).
+struct EnvDev {
+  const int64_t* fac_off;  // [nsub+1] element offset of each subdomain's tiles
+  const int32_t* trow;     // [nsub+1] offset of subdomain p's tile rows
+  const int32_t* first;    // F_I per tile row
+  const int32_t* last;     // R_I per tile row
+  const int32_t* toff;     // tile index of (I, F_I) in the subdomain's storage
+  const int32_t* nt;       // NT_p
+};
 // zero the level's factor storage, then scatter the CSR values (or 1 on the
 // padding diagonals, nz == -1) to their absolute positions
 template <typename T>
@@ -37,21 +46,20 @@ void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
 // step k of the blocked L D L^T over the first `nactive` subdomains of `order`
 // (sorted by descending tile count, so those are exactly the ones with NT > k)
 template <typename T>
-void launch_ldlt_diag(T* fac, const int64_t* fac_off, const int32_t* order, int nactive, int k,
+void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                       int* info, cudaStream_t s);
 template <typename T>
-void launch_ldlt_panel(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
-                       int nactive, int k, int max_rows, cudaStream_t s);
+void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
+                       int max_rows, cudaStream_t s);
 template <typename T>
-void launch_ldlt_trail(T* fac, const int64_t* fac_off, const int32_t* nt, const int32_t* order,
-                       int nactive, int k, int max_pairs, cudaStream_t s);
+void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
+                       int max_pairs, cudaStream_t s);
 // z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
 // entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
 template <typename T>
-void launch_ras_solve(const T* fac, const int64_t* fac_off, const int32_t* nt,
-                      const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int nsub,
-                      int max_nt, const int32_t* dir_list, int ndir, const double* t, double* z,
-                      int add, cudaStream_t s);
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* sub_ptr, const int32_t* dofs,
+                      const uint8_t* own, int nsub, int max_nt, const int32_t* dir_list, int ndir,
+                      const double* t, double* z, int add, cudaStream_t s);
 
 // ---- Krylov helpers (deterministic two-stage reductions)
 // out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles

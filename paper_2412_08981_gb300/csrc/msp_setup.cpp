@@ -182,41 +182,77 @@ void build_coarsest_block(HostLevel& L) {
   L.sub_own.assign(L.sub_dofs.size(), 1);
 }
 
-// Tiled factor layout and the CSR -> dense-block extraction map.  Only the
+// Tiled envelope layout and the CSR -> dense-block extraction map.  Only the
 // lower triangle (li >= lj) is extracted: the blocks are symmetric.
 void build_factor_layout(HostLevel& L) {
   L.sub_nt.resize(L.nsub);
-  L.sub_fac_off.assign(L.nsub + 1, 0);
+  L.sub_trow.assign(L.nsub + 1, 0);
   for (int p = 0; p < L.nsub; ++p) {
     int np_ = L.sub_ptr[p + 1] - L.sub_ptr[p];
-    int nt = (np_ + kTile - 1) / kTile;
-    L.sub_nt[p] = nt;
-    L.sub_fac_off[p + 1] = L.sub_fac_off[p] + tri_tiles(nt) * kTileElems;
+    L.sub_nt[p] = (np_ + kTile - 1) / kTile;
+    L.sub_trow[p + 1] = L.sub_trow[p] + L.sub_nt[p];
   }
-  L.ext_ptr.assign(L.nsub + 1, 0);
+  const int ntr = L.sub_trow[L.nsub];
+  L.tile_first.assign(ntr, 0);
+  L.tile_last.assign(ntr, 0);
+  L.tile_off.assign(ntr, 0);
+  L.sub_fac_off.assign(L.nsub + 1, 0);
   std::vector<int32_t> loc(L.n, -1);
+  // pass 1: envelope of every block
+  for (int p = 0; p < L.nsub; ++p) {
+    const int32_t* d = &L.sub_dofs[L.sub_ptr[p]];
+    const int np_ = L.sub_ptr[p + 1] - L.sub_ptr[p];
+    const int nt = L.sub_nt[p];
+    int32_t* F = &L.tile_first[L.sub_trow[p]];
+    for (int I = 0; I < nt; ++I) F[I] = I;
+    for (int li = 0; li < np_; ++li) loc[d[li]] = li;
+    for (int li = 0; li < np_; ++li) {
+      int i = d[li];
+      for (int q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
+        int lj = loc[L.col[q]];
+        if (lj >= 0 && lj <= li) F[li / kTile] = std::min(F[li / kTile], lj / kTile);
+      }
+    }
+    for (int li = 0; li < np_; ++li) loc[d[li]] = -1;
+    for (int I = nt - 2; I >= 0; --I) F[I] = std::min(F[I], F[I + 1]);  // monotone
+    int32_t* R = &L.tile_last[L.sub_trow[p]];
+    int32_t* O = &L.tile_off[L.sub_trow[p]];
+    int64_t ntiles = 0;
+    for (int I = 0; I < nt; ++I) {
+      O[I] = (int32_t)ntiles;
+      ntiles += I - F[I] + 1;
+      int J = I;
+      while (J + 1 < nt && F[J + 1] <= I) ++J;
+      R[I] = J;
+    }
+    L.sub_fac_off[p + 1] = L.sub_fac_off[p] + ntiles * kTileElems;
+  }
+  // pass 2: extraction positions
+  L.ext_ptr.assign(L.nsub + 1, 0);
   std::vector<int64_t> pos;
   std::vector<int32_t> nz;
   for (int p = 0; p < L.nsub; ++p) {
     const int64_t base = L.sub_fac_off[p];
     const int32_t* d = &L.sub_dofs[L.sub_ptr[p]];
-    int np_ = L.sub_ptr[p + 1] - L.sub_ptr[p];
+    const int np_ = L.sub_ptr[p + 1] - L.sub_ptr[p];
+    const int32_t* F = &L.tile_first[L.sub_trow[p]];
+    const int32_t* O = &L.tile_off[L.sub_trow[p]];
+    auto at = [&](int li, int lj) {
+      int I = li / kTile, J = lj / kTile;
+      return base + (int64_t)(O[I] + (J - F[I])) * kTileElems + (li % kTile) * kTile + (lj % kTile);
+    };
     for (int li = 0; li < np_; ++li) loc[d[li]] = li;
     for (int li = 0; li < np_; ++li) {
       int i = d[li];
       for (int q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
         int lj = loc[L.col[q]];
         if (lj < 0 || lj > li) continue;
-        int I = li / kTile, J = lj / kTile;
-        int64_t off = (tri_tiles(I) + J) * kTileElems + (li % kTile) * kTile + (lj % kTile);
-        pos.push_back(base + off);
+        pos.push_back(at(li, lj));
         nz.push_back(q);
       }
     }
     for (int li = np_; li < L.sub_nt[p] * kTile; ++li) {  // identity padding
-      int I = li / kTile;
-      int64_t off = (tri_tiles(I) + I) * kTileElems + (li % kTile) * (kTile + 1);
-      pos.push_back(base + off);
+      pos.push_back(at(li, li));
       nz.push_back(-1);
     }
     for (int li = 0; li < np_; ++li) loc[d[li]] = -1;

@@ -25,11 +25,12 @@ MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
-          "val": 12, "factor": 13}
+          "val": 12, "factor": 13, "sub_nt": 14, "tile_first": 15}
 _ARRAY_DTYPE = {"rowptr": np.int32, "col": np.int32, "sub_ptr": np.int32, "sub_dofs": np.int32,
                 "sub_own": np.uint8, "P_rowptr": np.int32, "P_col": np.int32,
                 "P_val": np.float64, "PT_rowptr": np.int32, "PT_col": np.int32,
-                "PT_val": np.float64, "load": np.float64, "val": np.float64}
+                "PT_val": np.float64, "load": np.float64, "val": np.float64,
+                "sub_nt": np.int32, "tile_first": np.int32}
 KERNEL_CLASSES = ["assemble", "extract", "ldlt_diag", "ldlt_panel", "ldlt_trail", "ras",
                   "ras_coarser", "coarse", "spmv", "transfer", "vec"]
 MSP_TILE = 64
@@ -337,20 +338,31 @@ class Instance:
         return out
 
 
-def unpack_factor(flat: np.ndarray, n: int):
-    """Dense (L, D) of one subdomain from its tiled factor storage (test helper).
+def tile_first_of(h: "Hierarchy", level: int, sub: int) -> np.ndarray:
+    """F_I of the tile rows of one block (sub = -1 or 0 for the coarsest)."""
+    nt = h.array(level, "sub_nt")
+    first = h.array(level, "tile_first")
+    p = max(sub, 0)
+    b = int(np.sum(nt[:p]))
+    return first[b:b + int(nt[p])]
 
-    Returns L (unit lower, n x n) and d (n,), reading tiles (I, J), J <= I,
-    at I (I+1)/2 + J as described in msp.h.
+
+def unpack_factor(flat: np.ndarray, n: int, first: np.ndarray):
+    """Dense (L, D) of one block from its tiled envelope storage (test helper).
+
+    Tile row I holds tiles (I, first[I]) .. (I, I), 64 x 64 row-major each, as
+    described in msp.h.  Returns L (unit lower, n x n) and d (n,).
     """
     T = MSP_TILE
-    nt = (n + T - 1) // T
+    nt = len(first)
     N = nt * T
     full = np.zeros((N, N), dtype=np.float64)
+    t = 0
     for I in range(nt):
-        for J in range(I + 1):
-            t = I * (I + 1) // 2 + J
+        for J in range(int(first[I]), I + 1):
             full[I * T:(I + 1) * T, J * T:(J + 1) * T] = flat[t * T * T:(t + 1) * T * T].reshape(T, T)
+            t += 1
+    assert t * T * T == flat.size
     d = np.diag(full).copy()
     L = np.tril(full, -1) + np.eye(N)
     return L[:n, :n], d[:n]

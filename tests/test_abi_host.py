@@ -114,3 +114,33 @@ def test_invalid_inputs_are_rejected(P):
     h = P.Hierarchy([lv, co], host_only=True)
     with pytest.raises(P.MspError):  # no device state on a host-only handle
         h.assemble(np.zeros(8), stream=0)
+
+
+@pytest.mark.parametrize("name", ["cube16_3lvl", "cube20_3lvl"])
+def test_tile_envelope_holds_the_full_dense_lu(P, orc, name):
+    """The library stores only the tile envelope of each block.  The oracle's
+    full dense LU (no skipping) must be exactly zero outside it, in L and U."""
+    levels, w = workload(name)
+    h = make_hierarchy(levels, w, P, host_only=True)
+    o = make_oracle(levels, w, orc)
+    o.assemble(syn.mu_draw(0))
+    o.factor()
+    T = P.msp.MSP_TILE
+    for l in range(len(levels)):
+        coarse = l == len(levels) - 1
+        ns = 1 if coarse else o.get("n_subs", l)
+        for p in range(ns):
+            sub = -1 if coarse else p
+            first = P.msp.tile_first_of(h, l, sub)
+            n = o.get("sub_dofs", l, sub).size
+            LU = o.get("sub_lu", l, sub).reshape(n, n)
+            assert np.all(np.diff(first) >= 0) and np.all(first <= np.arange(first.size))
+            for I in range(first.size):
+                c0 = int(first[I]) * T
+                rows = slice(I * T, min(n, (I + 1) * T))
+                assert not LU[rows, :c0].any()   # L outside the envelope
+                assert not LU[:c0, rows].any()   # U = D L^T, mirrored
+    # the envelope is much smaller than the full lower triangle of tiles
+    info = h.info(0)
+    nt = h.array(0, "sub_nt").astype(np.int64)
+    assert info["factor_elems"] < 0.8 * np.sum(nt * (nt + 1) // 2) * T * T

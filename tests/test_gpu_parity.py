@@ -109,7 +109,8 @@ def test_subdomain_factors(case, P):
             LU = case.o.get("sub_lu", l, sub).reshape(n, n)
             Lo = np.tril(LU, -1) + np.eye(n)
             do = np.diag(LU)
-            Lg, dg = P.msp.unpack_factor(case.inst.array(l, "factor", sub), n)
+            Lg, dg = P.msp.unpack_factor(case.inst.array(l, "factor", sub), n,
+                                         P.msp.tile_first_of(case.h, l, sub))
             assert np.max(np.abs(Lg - Lo)) <= 1e-10 * max(1.0, np.max(np.abs(Lo)))
             assert rel(dg, do) <= 1e-12
             # the symmetric factors reproduce the block: L D L^T = A_p
@@ -280,7 +281,8 @@ def test_fp32_factors_reach_fp64_accuracy(P, orc, torch):
     d = rel(z.cpu().numpy(), o.ras_apply(r, 0))
     assert 1e-10 < d < 1e-4, d
     fac = inst.array(0, "factor", 0, dtype=np.float32)
-    Lg, dg = P.msp.unpack_factor(fac.astype(np.float64), o.get("sub_dofs", 0, 0).size)
+    Lg, dg = P.msp.unpack_factor(fac.astype(np.float64), o.get("sub_dofs", 0, 0).size,
+                                 P.msp.tile_first_of(h, 0, 0))
     n0 = o.get("sub_dofs", 0, 0).size
     do = np.diag(o.get("sub_lu", 0, 0).reshape(n0, n0))
     assert 1e-12 < rel(dg, do) < 1e-5

@@ -57,54 +57,62 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 }
 
 // ---------------------------------------------------- diagonal tile LDL^T
-// One block per active subdomain.  Factors tile (k, k) in FP64 shared memory
-// (column by column: scale the column by 1/d, then update the trailing lower
-// triangle with l_r d l_s), then forms X = L^{-1} one column per thread.
+// One block per active subdomain, computing in the factor's precision.
+// Column c: d = A[c][c]; every row r > c subtracts (a_rc / d) a_sc from its
+// entries s in (c, r] (a_sc, the still unscaled column, is final since step
+// c-1), one barrier per column; then the columns are scaled by 1/d.  The
+// inverse X = L^{-1} of the unit lower factor is built row by row (row i needs
+// rows < i only), four lanes per entry, one barrier per row, and stored
+// transposed in the strict upper part.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
                                                    const int32_t* __restrict__ order, int k,
                                                    int* __restrict__ info) {
-  extern __shared__ double sm[];
-  double* A = sm;               // [64][65]
-  double* X = sm + 64 * 65;     // [64][65]
+  using AT = typename Acc<T>::type;
+  extern __shared__ unsigned char smraw[];
+  AT* A = reinterpret_cast<AT*>(smraw);   // [64][65]: L (lower), D (diag), X^T (upper)
   const int p = order[blockIdx.x];
   T* tile = fac + tile_at(E, p, k, k);
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (c <= r) ? (double)tile[e] : 0.0;
+    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
   const int row = tid >> 2, sub = tid & 3;
   for (int c = 0; c < T64; ++c) {
-    const double d = A[c * 65 + c];
-    if (tid == 0 && !(d > 0.0 && d < 1e300)) atomicOr(info, 1);
-    const double dinv = 1.0 / d;
-    __syncthreads();
-    if (row > c && sub == 0) A[row * 65 + c] *= dinv;
-    __syncthreads();
+    const AT d = A[c * 65 + c];
     if (row > c) {
-      const double lr = A[row * 65 + c] * d;
-      for (int s = c + 1 + sub; s <= row; s += 4) A[row * 65 + s] -= lr * A[s * 65 + c];
+      const AT f = A[row * 65 + c] / d;
+      for (int s = c + 1 + sub; s <= row; s += 4) A[row * 65 + s] -= f * A[s * 65 + c];
     }
     __syncthreads();
   }
-  // X = L^{-1}, unit lower: X[i][j] = -sum_{m=j}^{i-1} L[i][m] X[m][j]
-  if (tid < T64) {
-    const int j = tid;
-    for (int i = 0; i < T64; ++i) X[i * 65 + j] = (i == j) ? 1.0 : 0.0;
-    for (int i = j + 1; i < T64; ++i) {
-      double s = 0.0;
-      for (int m = j; m < i; ++m) s -= A[i * 65 + m] * X[m * 65 + j];
-      X[i * 65 + j] = s;
+  if (tid == 0) {
+    for (int c = 0; c < T64; ++c) {
+      const AT d = A[c * 65 + c];
+      if (!(d > AT(0)) || !(d < AT(1e300))) atomicOr(info, 1);
     }
+  }
+  for (int e = tid; e < TE; e += blockDim.x) {  // L = W D^{-1}; clear the upper part
+    int r = e >> 6, c = e & 63;
+    if (c < r) A[r * 65 + c] /= A[c * 65 + c];
+    else if (c > r) A[r * 65 + c] = AT(0);
   }
   __syncthreads();
-  for (int e = tid; e < TE; e += blockDim.x) {
-    int r = e >> 6, c = e & 63;
-    double v = (c <= r) ? A[r * 65 + c] : X[c * 65 + r];
-    tile[e] = (T)v;
+  // X[i][j] = -(L[i][j] + sum_{j<m<i} L[i][m] X[m][j]); X[m][j] lives at A[j][m]
+  const int jcol = tid >> 2, part = tid & 3;
+  for (int i = 1; i < T64; ++i) {
+    AT v = 0;
+    if (jcol < i) {
+      for (int m = jcol + 1 + part; m < i; m += 4) v += A[i * 65 + m] * A[jcol * 65 + m];
+    }
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    if (jcol < i && part == 0) A[jcol * 65 + i] = -(A[i * 65 + jcol] + v);
+    __syncthreads();
   }
+  for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
 // ----------------------------------------------------------- panel solve
@@ -366,7 +374,8 @@ template <typename T>
 void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                       int* info, cudaStream_t s) {
   if (nactive <= 0) return;
-  size_t smem = 2 * 64 * 65 * sizeof(double);
+  using AT = typename Acc<T>::type;
+  size_t smem = 64 * 65 * sizeof(AT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -154,6 +154,8 @@ struct msp_instance {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
   double* xb = nullptr;  // device buffers used by msp_solve_host
   double* hpin = nullptr;  // pinned host staging
+  cudaStream_t aux[2] = {nullptr, nullptr};  // coarser levels factor concurrently
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   bool assembled = false, factored = false;
   Profile prof;
 };
@@ -292,10 +294,9 @@ int assemble_all(msp_instance* I) {
 }
 
 template <typename T>
-void factor_level(msp_instance* I, int l, T* fac) {
+void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
   msp_hierarchy* h = I->h;
   DevLevel& D = h->dev[l];
-  cudaStream_t s = I->stream;
   {
     ProfScope ps(I->prof, PK_EXTRACT, s, 2);
     launch_extract<T>(D.ext_pos, D.ext_nz, D.next, I->val[l], D.fac_elems, fac, s);
@@ -327,9 +328,19 @@ void factor_level(msp_instance* I, int l, T* fac) {
 int factor_all(msp_instance* I) {
   msp_hierarchy* h = I->h;
   MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
-  for (size_t l = 0; l < h->dev.size(); ++l) {
-    if (level_f32(h, (int)l)) factor_level<float>(I, (int)l, static_cast<float*>(I->fac[l]));
-    else factor_level<double>(I, (int)l, static_cast<double*>(I->fac[l]));
+  // level 0 on the instance stream, the coarser (independent) levels on two
+  // auxiliary streams forked from it and joined back
+  const int L = (int)h->dev.size();
+  MSP_CUDA(cudaEventRecord(I->fork, I->stream));
+  for (int a = 0; a < 2; ++a) MSP_CUDA(cudaStreamWaitEvent(I->aux[a], I->fork, 0));
+  for (int l = 0; l < L; ++l) {
+    cudaStream_t s = (l == 0) ? I->stream : I->aux[(l - 1) % 2];
+    if (level_f32(h, l)) factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
+    else factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
+  }
+  for (int a = 0; a < 2; ++a) {
+    MSP_CUDA(cudaEventRecord(I->join[a], I->aux[a]));
+    MSP_CUDA(cudaStreamWaitEvent(I->stream, I->join[a], 0));
   }
   MSP_CUDA(cudaGetLastError());
   int hinfo = 0;
@@ -617,6 +628,11 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     cudaGetLastError();
     return fail(MSP_ERR_OOM, "pinned host allocation failed");
   }
+  for (int a = 0; a < 2; ++a) {
+    MSP_CUDA(cudaStreamCreateWithFlags(&I->aux[a], cudaStreamNonBlocking));
+    MSP_CUDA(cudaEventCreateWithFlags(&I->join[a], cudaEventDisableTiming));
+  }
+  MSP_CUDA(cudaEventCreateWithFlags(&I->fork, cudaEventDisableTiming));
   return MSP_OK;
 }
 
@@ -759,6 +775,11 @@ int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream, msp
   auto undo = [&](int rc) {
     I->arena.release();
     if (I->hpin) cudaFreeHost(I->hpin);
+    for (int a = 0; a < 2; ++a) {
+      if (I->aux[a]) cudaStreamDestroy(I->aux[a]);
+      if (I->join[a]) cudaEventDestroy(I->join[a]);
+    }
+    if (I->fork) cudaEventDestroy(I->fork);
     std::lock_guard<std::mutex> lk(h->mu);
     h->instance_bytes -= need;
     return rc;
@@ -781,6 +802,11 @@ int msp_reassemble(msp_instance* I, const double* mu, int n_mu) {
 void msp_free_instance(msp_instance* I) {
   if (!I) return;
   cudaStreamSynchronize(I->stream);
+  for (int a = 0; a < 2; ++a) {
+    if (I->aux[a]) cudaStreamDestroy(I->aux[a]);
+    if (I->join[a]) cudaEventDestroy(I->join[a]);
+  }
+  if (I->fork) cudaEventDestroy(I->fork);
   I->prof.destroy();
   I->arena.release();
   if (I->hpin) cudaFreeHost(I->hpin);

@@ -138,7 +138,7 @@ typedef struct msp_level_info {
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
 
-/* ---- per parameter (Eq. (2)-(3) on every level) ----
+/* ---- per parameter (Eq. 2-4 on every level) ----
  * Creates an instance bound to `stream` and assembles J(mu) (CSR values) on
  * every level.  mu: host array of n_mu doubles (n_mu == 8 for MSP_K_COSEXP,
  * ignored for MSP_K_CONST).  Errors: MSP_ERR_INVALID (non-finite mu, wrong
@@ -149,7 +149,7 @@ MSP_API int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* str
 MSP_API int msp_reassemble(msp_instance* inst, const double* mu, int n_mu);
 MSP_API void msp_free_instance(msp_instance* inst);
 
-/* Subdomain blocks J^delta_p = R J R^T of every smoothed level (Eq. (5)) and
+/* Subdomain blocks J^delta_p = R J R^T of every smoothed level (Eq. 6) and
  * their unpivoted LU factors in symmetric form (unit lower L, D; U = D L^T),
  * plus the FP64 factor of the coarsest level's interior block. */
 MSP_API int msp_factor(msp_instance* inst);
@@ -160,7 +160,7 @@ MSP_API int msp_factor(msp_instance* inst);
  * not overlap.  Requires msp_factor. */
 MSP_API int msp_apply(msp_instance* inst, const double* r_dev, double* z_dev, void* stream);
 
-/* Right-preconditioned FGMRES(restart) on J(mu) x = b (Eq. (4)), x_0 = 0,
+/* Right-preconditioned FGMRES(restart) on J(mu) x = b (Eq. 5), x_0 = 0,
  * stopping when ||b - J x|| <= rtol ||b|| (true residual).  b_dev: device
  * right-hand side, or NULL for the assembled load vector.  x_dev: device
  * output.  Synchronises the instance stream.  MSP_ERR_NOT_CONVERGED leaves the
@@ -180,7 +180,7 @@ MSP_API int msp_solve_host(msp_instance* inst, const double* mu, int n_mu, const
  *   MSP_OP_RESIDUAL y = y - J_l x  (y holds r on entry)
  *   MSP_OP_INTERP   y = P_l x      (n_{l+1} -> n_l), l < L-1
  *   MSP_OP_RESTRICT y = P_l^T x    (n_l -> n_{l+1}), l < L-1
- *   MSP_OP_RAS      y = B_l^{-1} x (Eq. (6)), l < L-1, needs msp_factor
+ *   MSP_OP_RAS      y = B_l^{-1} x (Eq. 7), l < L-1, needs msp_factor
  *   MSP_OP_COARSE   y = J_{L-1}^{-1} x, l = L-1, needs msp_factor */
 typedef enum msp_op {
   MSP_OP_SPMV = 0, MSP_OP_RESIDUAL = 1, MSP_OP_INTERP = 2, MSP_OP_RESTRICT = 3,

@@ -6,16 +6,16 @@
 // by __graft_entry__.smoke() and by the CPU-baseline leg of bench.py.
 //
 // Every function follows the paper's statement step by step, in its order:
-//   * discretisation J u = b of a linear PDE on a mesh (Section 2.1, Eq. (2)-(4)),
+//   * discretisation J u = b of a linear PDE on a mesh (Section 2.1, Eq. 2-4),
 //     realised as P1 finite elements for -div(k(x;mu) grad u) = f;
-//   * one-level restricted additive Schwarz (Section 2.2, Eq. (5)-(7));
+//   * one-level restricted additive Schwarz (Section 2.2, Eq. 6-8);
 //   * the V-cycle of Algorithm 2 (Section 3.3), with the readings listed below;
-//   * right-preconditioned (flexible) GMRES (Section 2.1, Eq. (4); Section 4).
+//   * right-preconditioned (flexible) GMRES (Section 2.1, Eq. 5; Section 4).
 // Readings where the paper is silent (shared with the library by specification,
 // not by code):
 //   * fine->coarse transfer is P^T and coarse->fine is P, P the P1 barycentric
 //     interpolation of coarse fields at fine nodes (replaces the MLS operator of
-//     Eq. (16)); the coarsest level is solved directly, not smoothed;
+//     Eq. 24); the coarsest level is solved directly, not smoothed;
 //   * the smoothing loops of Algorithm 2 run exactly `its` times;
 //   * subdomain solvers are unpivoted LU of each (SPD) subdomain block;
 //   * Dirichlet rows are identity rows, Dirichlet columns are zeroed;
@@ -144,7 +144,7 @@ long csr_find(const Csr& A, int i, int j) {
 
 // --------------------------------------------------------------- assembly
 // J(i,j) = sum over tets T (ascending id) of int_T k grad phi_j . grad phi_i
-// (Eq. (3) for the P1 Galerkin scheme), k at the centroid; then Dirichlet rows
+// (Eq. 4 for the P1 Galerkin scheme), k at the centroid; then Dirichlet rows
 // become identity rows and Dirichlet columns are zeroed.
 // b(a) = sum over tets T containing a of f(x_a) |T| / 4 (vertex rule), 0 on
 // Dirichlet nodes.
@@ -261,7 +261,7 @@ void lu_solve(int n, const double* LU, double* x) {
   }
 }
 
-// A_p = R_p A R_p^T as a dense block (Eq. (5)).
+// A_p = R_p A R_p^T as a dense block (Eq. 6).
 void extract_dense(const Csr& A, const Subdomain& S, std::vector<double>& D) {
   int n = (int)S.dofs.size();
   D.assign((size_t)n * n, 0.0);

@@ -1,4 +1,4 @@
-// Dense subdomain kernels of the msp library (Section 2.2, Eq. (5)-(6)):
+// Dense subdomain kernels of the msp library (Section 2.2, Eq. 6-7):
 //   * extraction of the blocks J^delta_p = R J R^T into tiled storage,
 //   * batched, blocked, right-looking unpivoted LU of every block in its
 //     symmetric form J_p = L D L^T (U = D L^T; the blocks are SPD, so no

@@ -1,6 +1,6 @@
 // C ABI of the msp library: device state, per-parameter assembly and
 // factorisation, the V-cycle of Algorithm 2 and right-preconditioned FGMRES
-// (Eq. (4)).  Every arithmetic step runs in the kernels of k_sparse.cu and
+// (Eq. 5).  Every arithmetic step runs in the kernels of k_sparse.cu and
 // k_dense.cu; this file only allocates, uploads, orders launches on the
 // instance stream and runs the small Hessenberg least-squares update of
 // FGMRES on the host.

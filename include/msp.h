@@ -257,6 +257,27 @@ MSP_API int msp_profile_enable(msp_instance* inst, uint32_t class_mask);
 MSP_API int msp_profile_reset(msp_instance* inst);
 MSP_API int msp_profile_read(msp_instance* inst, int kclass, msp_kernel_profile* out);
 
+/* ---- allocation-free multi-vector dot product ----
+ * No counterpart in the paper: a library convenience for callers that may not
+ * allocate device memory when they need the result (code running while a
+ * stream is captured into a CUDA graph, code under a memory manager that owns
+ * all device memory, real-time loops that cannot risk an allocation failing).
+ * out_dev[i] = sum_{k<n} V_dev[i*ld + k] * w_dev[k] for i < nv, with the same
+ * fixed-order two-stage reduction FGMRES uses, so results are bitwise
+ * reproducible.  All pointers are caller-owned device memory; `stream` as
+ * above.  The partial sums live in one fixed device array of
+ * MSP_NOALLOC_MAX_VECTORS x 296 doubles (148 KiB) that every GPU loading the
+ * library holds until exit; the call allocates nothing.  The first call on a
+ * device looks up that array's device address with the device current (make
+ * that first call before any stream capture).  Every call reuses the array,
+ * so calls that overlap on the GPU race; each call overwrites every entry it
+ * reads, so nothing needs clearing.  Errors: MSP_ERR_INVALID for nv outside
+ * 1..MSP_NOALLOC_MAX_VECTORS, n < 0, ld < n (nv > 1) or NULL pointers;
+ * MSP_ERR_CUDA if the launch fails. */
+#define MSP_NOALLOC_MAX_VECTORS 64
+MSP_API int msp_multidot_noalloc(const double* V_dev, int64_t ld, int nv, const double* w_dev,
+                                 int64_t n, double* out_dev, void* stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 MSP_API const char* msp_last_error(void);
 /* Library version string. */

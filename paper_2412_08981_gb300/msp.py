@@ -108,7 +108,10 @@ EXPORTS = {
     "msp_profile_enable": (C.c_int, [C.c_void_p, C.c_uint32]),
     "msp_profile_reset": (C.c_int, [C.c_void_p]),
     "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
+    "msp_multidot_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_void_p]),
 }
+MSP_NOALLOC_MAX_VECTORS = 64
 
 
 def load(path: str = LIB_PATH):
@@ -336,6 +339,19 @@ class Instance:
             _check(load().msp_profile_read(self.inst, i, C.byref(p)))
             out[name] = {k: getattr(p, k) for k, _ in msp_kernel_profile._fields_}
         return out
+
+
+def multidot_noalloc(V, w, out, nv=None, ld=None, n=None, stream=None):
+    """msp_multidot_noalloc: out[i] = V_i . w with no device allocation.
+
+    V: device tensor (nv rows of length >= n, row stride ld), w: device
+    vector, out: device tensor of nv doubles (caller-owned).
+    """
+    n = int(w.numel()) if n is None else int(n)
+    nv = (1 if V.dim() == 1 else int(V.shape[0])) if nv is None else int(nv)
+    ld = (n if V.dim() == 1 else int(V.stride(0))) if ld is None else int(ld)
+    _check(load().msp_multidot_noalloc(_ptr(V), ld, nv, _ptr(w), n, _ptr(out),
+                                       _stream_ptr(stream)))
 
 
 def tile_first_of(h: "Hierarchy", level: int, sub: int) -> np.ndarray:

@@ -58,12 +58,13 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 
 // ---------------------------------------------------- diagonal tile LDL^T
 // One block per active subdomain, computing in the factor's precision.
-// Column c: d = A[c][c]; every row r > c subtracts (a_rc / d) a_sc from its
-// entries s in (c, r] (a_sc, the still unscaled column, is final since step
-// c-1), one barrier per column; then the columns are scaled by 1/d.  The
-// inverse X = L^{-1} of the unit lower factor is built row by row (row i needs
-// rows < i only), four lanes per entry, one barrier per row, and stored
-// transposed in the strict upper part.
+// Column c: every row r > c subtracts (a_rc / d_c) a_sc from its entries s in
+// (c, r] (a_sc, the still unscaled column, is final since step c-1), one
+// barrier per column.  1/d_c is formed once, by the thread that finishes the
+// pivot d_c (the update of entry (c, c) at step c-1), so each column costs a
+// single division.  Then L = W D^{-1}, and the inverse X = L^{-1} of the unit
+// lower factor is built row by row (row i needs rows < i only), four lanes
+// per entry, one barrier per row, stored transposed in the strict upper part.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
                                                    const int32_t* __restrict__ order, int k,
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   AT* A = reinterpret_cast<AT*>(smraw);   // [64][65]: L (lower), D (diag), X^T (upper)
+  AT* dinv = A + 64 * 65;                 // [64] reciprocals of the pivots
   const int p = order[blockIdx.x];
   T* tile = fac + tile_at(E, p, k, k);
   const int tid = threadIdx.x;
@@ -79,24 +81,27 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
+  if (tid == 0) dinv[0] = AT(1) / A[0];
+  __syncthreads();
   const int row = tid >> 2, sub = tid & 3;
   for (int c = 0; c < T64; ++c) {
-    const AT d = A[c * 65 + c];
     if (row > c) {
-      const AT f = A[row * 65 + c] / d;
-      for (int s = c + 1 + sub; s <= row; s += 4) A[row * 65 + s] -= f * A[s * 65 + c];
+      const AT f = A[row * 65 + c] * dinv[c];
+      for (int s = c + 1 + sub; s <= row; s += 4) {
+        const AT v = A[row * 65 + s] - f * A[s * 65 + c];
+        A[row * 65 + s] = v;
+        if (s == c + 1 && row == c + 1) dinv[c + 1] = AT(1) / v;  // pivot c+1 is final
+      }
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    for (int c = 0; c < T64; ++c) {
-      const AT d = A[c * 65 + c];
-      if (!(d > AT(0)) || !(d < AT(1e300))) atomicOr(info, 1);
-    }
+  if (tid < T64) {
+    const AT d = A[tid * 65 + tid];
+    if (!(d > AT(0)) || !(d < AT(1e300))) atomicOr(info, 1);
   }
   for (int e = tid; e < TE; e += blockDim.x) {  // L = W D^{-1}; clear the upper part
     int r = e >> 6, c = e & 63;
-    if (c < r) A[r * 65 + c] /= A[c * 65 + c];
+    if (c < r) A[r * 65 + c] *= dinv[c];
     else if (c > r) A[r * 65 + c] = AT(0);
   }
   __syncthreads();
@@ -117,8 +122,9 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
 
 // ----------------------------------------------------------- panel solve
 // L_ik = A_ik X^T D^{-1} for the tiles below the diagonal tile of step k,
-// k < i <= R_k.  Warp w owns the 8 columns 8w..8w+7 (X^T is upper
-// triangular, so its loop stops at 8w+7); each lane owns 2 rows.
+// k < i <= R_k.  Column c needs the products over m <= c (X^T is upper
+// triangular), so warp w takes the 4 columns 4w..4w+3 and the 4 columns
+// 60-4w..63-4w: every warp does the same work.  Each lane owns 2 rows.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k) {
@@ -142,25 +148,28 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  const int c0 = warp * 8;
   const int r0 = lane, r1 = lane + 32;
-  AT w0[8], w1[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { w0[q] = 0; w1[q] = 0; }
-  const int mend = c0 + 8;
-  for (int m = 0; m < mend; ++m) {
-    AT a0 = A[r0 * 65 + m], a1 = A[r1 * 65 + m];
+  for (int half = 0; half < 2; ++half) {
+    const int c0 = half == 0 ? warp * 4 : 60 - warp * 4;
+    AT w0[4], w1[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      AT x = Xt[m * 64 + c0 + q];
-      w0[q] += a0 * x;
-      w1[q] += a1 * x;
+    for (int q = 0; q < 4; ++q) { w0[q] = 0; w1[q] = 0; }
+    const int mend = c0 + 4;
+    for (int m = 0; m < mend; ++m) {
+      AT a0 = A[r0 * 65 + m], a1 = A[r1 * 65 + m];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        AT x = Xt[m * 64 + c0 + q];
+        w0[q] += a0 * x;
+        w1[q] += a1 * x;
+      }
     }
-  }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    ptile[r0 * 64 + c0 + q] = (T)(w0[q] * Dinv[c0 + q]);
-    ptile[r1 * 64 + c0 + q] = (T)(w1[q] * Dinv[c0 + q]);
+    for (int q = 0; q < 4; ++q) {
+      ptile[r0 * 64 + c0 + q] = (T)(w0[q] * Dinv[c0 + q]);
+      ptile[r1 * 64 + c0 + q] = (T)(w1[q] * Dinv[c0 + q]);
+    }
   }
 }
 
@@ -375,7 +384,7 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
                       int* info, cudaStream_t s) {
   if (nactive <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = 64 * 65 * sizeof(AT);
+  size_t smem = (64 * 65 + 64) * sizeof(AT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -20,6 +20,7 @@
 // keeps the FMA pipe fed from shared memory and avoids idle lanes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "msp_kernels.h"
@@ -243,128 +244,240 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
 }
 
 // -------------------------------------------------------------- RAS solve
-// One block (8 warps) per subdomain; extra blocks copy t into z on the
-// Dirichlet nodes.  Gather t[dofs] -> y; forward sweep over tile rows
-// (y_I = X_II (t_I - sum_{F_I <= J < I} L_IJ y_J)); y /= D; backward sweep
-// (x_I = X_II^T (y_I - sum_{I < J <= R_I} L_JI^T x_J)); scatter the owned
-// entries.
+// Persistent and warp-specialised.  Each CTA (one per SM) takes the
+// subdomains order[b], order[b + G], ... (largest first).  Warp 8 is the
+// producer: one lane streams the factor tiles of every subdomain, in the
+// order the sweeps consume them, into a ring of shared-memory slots with
+// cp.async.bulk, each slot guarded by a "full" mbarrier (transaction count)
+// and an "empty" mbarrier (one arrival per consumer warp).  Warps 0-7 are the
+// consumers: gather t[dofs] -> y; forward sweep over tile rows
+// (y_I = X_II (y_I - sum_{F_I <= J < I} L_IJ y_J)); backward sweep, diagonal
+// tile first (x_I = X_II^T (y_I / D_I - sum_{I < J <= R_I} L_JI^T x_J));
+// scatter the owned entries.  Every mbarrier wait is bounded: on expiry it
+// records an error bit and goes on (the results are then garbage and the
+// host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
+// own copies, so none is in flight when the CTA exits.
+constexpr int kConsumers = 8;
+constexpr long kWaitLimit = 1L << 20;
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete.  After a first expiry
+// (flag set) later waits give up almost at once.
+__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, volatile int* sflag, int* err) {
+  const long limit = *sflag ? 64 : kWaitLimit;
+  for (long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return;
+  *sflag = 1;
+  atomicOr(err, 4);
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// The tile sequence of one subdomain, shared by producer and consumers.
+struct TileSeq {
+  const EnvDev& E;
+  int p, rb, NT;
+  __device__ TileSeq(const EnvDev& e, int pp) : E(e), p(pp), rb(e.trow[pp]), NT(e.nt[pp]) {}
+  __device__ int first(int I) const { return E.first[rb + I]; }
+  __device__ int last(int I) const { return E.last[rb + I]; }
+  __device__ int64_t at(int I, int J) const {  // element offset of tile (I, J)
+    return E.fac_off[p] + (int64_t)(E.toff[rb + I] + (J - E.first[rb + I])) * TE;
+  }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_ras_solve(
-    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ sub_ptr,
-    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own, int nsub,
-    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
-    double* __restrict__ z, int add) {
+__global__ void __launch_bounds__(288, 1) k_ras_solve(
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ order,
+    const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ dofs,
+    const uint8_t* __restrict__ own, int nsub, const int32_t* __restrict__ dir_list, int ndir,
+    const double* __restrict__ t, double* __restrict__ z, int add, int max_nt, int nslot,
+    int* __restrict__ err) {
   using AT = typename Acc<T>::type;
+  constexpr uint32_t kTileBytes = TE * sizeof(T);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* ring = reinterpret_cast<T*>(smraw);                                        // [nslot][TE]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)nslot * kTileBytes);  // [nslot]
+  uint64_t* empty = full + nslot;                                               // [nslot]
+  AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
+  AT* acc = y + max_nt * 64;                                                    // [64]
+  AT* part = acc + 64;                                                          // [8][64]
+  __shared__ int sflag;
   const int tid = threadIdx.x;
-  if ((int)blockIdx.x >= nsub) {
-    int d = (blockIdx.x - nsub) * blockDim.x + tid;
-    if (d < ndir) {
-      int g = dir_list[d];
-      z[g] = add ? z[g] + t[g] : t[g];
+  const int warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  if (tid == 0) {
+    sflag = 0;
+    for (int s = 0; s < nslot; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers);
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kConsumers) {  // ------------------------------------ producer
+    if (lane != 0) return;
+    long seq = 0;
+    auto issue = [&](const T* src) {
+      const int slot = (int)(seq % nslot);
+      if (seq >= nslot) mbar_wait(&empty[slot], (uint32_t)(((seq / nslot) - 1) & 1), &sflag, err);
+      mbar_expect_tx(&full[slot], kTileBytes);
+      bulk_g2s(ring + (size_t)slot * TE, src, kTileBytes, &full[slot]);
+      ++seq;
+    };
+    for (int q = blockIdx.x; q < nsub; q += G) {
+      TileSeq S(E, order[q]);
+      for (int I = 0; I < S.NT; ++I)
+        for (int J = S.first(I); J <= I; ++J) issue(fac + S.at(I, J));
+      for (int I = S.NT - 1; I >= 0; --I) {
+        issue(fac + S.at(I, I));
+        for (int J = I + 1; J <= S.last(I); ++J) issue(fac + S.at(J, I));
+      }
+    }
+    // drain: the last copy of every slot has landed before the CTA may exit
+    for (long k = (seq > nslot ? seq - nslot : 0); k < seq; ++k)
+      mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err);
     return;
   }
-  const int p = blockIdx.x;
-  const int NT = E.nt[p];
-  const int rb = E.trow[p];
-  const int off = sub_ptr[p];
-  const int np_ = sub_ptr[p + 1] - off;
-  extern __shared__ unsigned char smraw[];
-  AT* y = reinterpret_cast<AT*>(smraw);   // [NT*64]
-  AT* acc = y + NT * 64;                  // [64]
-  AT* part = acc + 64;                    // [8][64]
-  const T* base = fac + E.fac_off[p];
-  for (int li = tid; li < NT * 64; li += blockDim.x)
-    y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  // forward
-  for (int I = 0; I < NT; ++I) {
-    AT s[8];
+
+  // ------------------------------------------------------------ consumers
+  for (int d = blockIdx.x * 256 + tid; d < ndir; d += G * 256) {
+    const int g = dir_list[d];
+    z[g] = add ? z[g] + t[g] : t[g];
+  }
+  long seq = 0;
+  auto acquire = [&]() -> const T* {
+    const int slot = (int)(seq % nslot);
+    mbar_wait(&full[slot], (uint32_t)((seq / nslot) & 1), &sflag, err);
+    return ring + (size_t)slot * TE;
+  };
+  auto release = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[seq % nslot]);
+    ++seq;
+  };
+  for (int q = blockIdx.x; q < nsub; q += G) {
+    const int p = order[q];
+    TileSeq S(E, p);
+    const int NT = S.NT;
+    const int off = sub_ptr[p];
+    const int np_ = sub_ptr[p + 1] - off;
+    for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+    consumers_sync();
+    // forward sweep
+    for (int I = 0; I < NT; ++I) {
+      AT s8[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[q] = 0;
-    const int F = E.first[rb + I];
-    const T* rowt = base + (int64_t)E.toff[rb + I] * TE;  // tile (I, F)
-    for (int J = F; J < I; ++J) {
-      const T* tl = rowt + (int64_t)(J - F) * TE;
-      AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
+      for (int k = 0; k < 8; ++k) s8[k] = 0;
+      for (int J = S.first(I); J < I; ++J) {
+        const T* tl = acquire();
+        const AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        int r = warp * 8 + q;
-        s[q] += (AT)tl[r * 64 + lane] * y0 + (AT)tl[r * 64 + lane + 32] * y1;
+        for (int k = 0; k < 8; ++k) {
+          const int r = warp * 8 + k;
+          s8[k] += (AT)tl[r * 64 + lane] * y0 + (AT)tl[r * 64 + lane + 32] * y1;
+        }
+        release();
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        AT v = s8[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) acc[warp * 8 + k] = y[I * 64 + warp * 8 + k] - v;
+      }
+      consumers_sync();
+      {  // y_I = X acc, X[b][a] = tile[a][b] for a < b
+        const T* dt = acquire();
+        const int bcol = tid & 63, pr = tid >> 6;
+        AT v = 0;
+        for (int a = pr * 16; a < pr * 16 + 16; ++a)
+          if (a < bcol) v += (AT)dt[a * 64 + bcol] * acc[a];
+        part[pr * 64 + bcol] = v;
+        release();
+      }
+      consumers_sync();
+      if (tid < 64) y[I * 64 + tid] = acc[tid] + part[tid] + part[64 + tid] + part[128 + tid] + part[192 + tid];
+      consumers_sync();
+    }
+    // backward sweep
+    for (int I = NT - 1; I >= 0; --I) {
+      const T* dt = acquire();  // held until the end of the row
+      const long dseq = seq;
+      ++seq;
+      AT s0 = 0, s1 = 0;
+      for (int J = I + 1; J <= S.last(I); ++J) {
+        const T* tl = acquire();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = warp * 8 + k;
+          const AT xr = y[J * 64 + r];
+          s0 += (AT)tl[r * 64 + lane] * xr;
+          s1 += (AT)tl[r * 64 + lane + 32] * xr;
+        }
+        release();
+      }
+      part[warp * 64 + lane] = s0;
+      part[warp * 64 + lane + 32] = s1;
+      consumers_sync();
+      if (tid < 64) {
+        AT v = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v += part[w * 64 + tid];
+        acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - v;
+      }
+      consumers_sync();
+      // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int a = warp * 8 + k;
+        AT v = 0;
+        if (lane > a) v += (AT)dt[a * 64 + lane] * acc[lane];
+        if (lane + 32 > a) v += (AT)dt[a * 64 + lane + 32] * acc[lane + 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[I * 64 + a] = acc[a] + v;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
+      consumers_sync();
+    }
+    for (int li = tid; li < np_; li += 256) {
+      if (own[off + li]) {
+        const int g = dofs[off + li];
+        z[g] = add ? z[g] + (double)y[li] : (double)y[li];
       }
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      AT v = s[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) acc[warp * 8 + q] = y[I * 64 + warp * 8 + q] - v;
-    }
-    __syncthreads();
-    // y_I = X acc, X[b][a] = dtile[a][b] for a < b (upper part of the diagonal tile)
-    const T* dtl = rowt + (int64_t)(I - F) * TE;
-    {
-      const int bcol = tid & 63, pr = tid >> 6;  // 4 parts over a
-      AT v = 0;
-      for (int a = pr * 16; a < pr * 16 + 16; ++a)
-        if (a < bcol) v += (AT)dtl[a * 64 + bcol] * acc[a];
-      part[pr * 64 + bcol] = v;
-    }
-    __syncthreads();
-    if (tid < 64) y[I * 64 + tid] = acc[tid] + part[tid] + part[64 + tid] + part[128 + tid] + part[192 + tid];
-    __syncthreads();
-  }
-  // diagonal scaling
-  for (int li = tid; li < NT * 64; li += blockDim.x) {
-    int I = li >> 6, r = li & 63;
-    const int F = E.first[rb + I];
-    y[li] = y[li] / (AT)base[(int64_t)(E.toff[rb + I] + (I - F)) * TE + r * 65];
-  }
-  __syncthreads();
-  // backward
-  for (int I = NT - 1; I >= 0; --I) {
-    AT s0 = 0, s1 = 0;
-    const int R = E.last[rb + I];
-    for (int J = I + 1; J <= R; ++J) {
-      const T* tl = base + (int64_t)(E.toff[rb + J] + (I - E.first[rb + J])) * TE;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        int r = warp * 8 + q;
-        AT xr = y[J * 64 + r];
-        s0 += (AT)tl[r * 64 + lane] * xr;
-        s1 += (AT)tl[r * 64 + lane + 32] * xr;
-      }
-    }
-    part[warp * 64 + lane] = s0;
-    part[warp * 64 + lane + 32] = s1;
-    __syncthreads();
-    if (tid < 64) {
-      AT v = 0;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) v += part[w * 64 + tid];
-      acc[tid] = y[I * 64 + tid] - v;
-    }
-    __syncthreads();
-    // x_I[a] = acc[a] + sum_{b>a} X[b][a] acc[b] = acc[a] + sum_{b>a} dtile[a][b] acc[b]
-    const T* dtl = base + (int64_t)(E.toff[rb + I] + (I - E.first[rb + I])) * TE;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int a = warp * 8 + q;
-      AT v = 0;
-      if (lane > a) v += (AT)dtl[a * 64 + lane] * acc[lane];
-      if (lane + 32 > a) v += (AT)dtl[a * 64 + lane + 32] * acc[lane + 32];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) y[I * 64 + a] = acc[a] + v;
-    }
-    __syncthreads();
-  }
-  for (int li = tid; li < np_; li += blockDim.x) {
-    if (own[off + li]) {
-      int g = dofs[off + li];
-      z[g] = add ? z[g] + (double)y[li] : (double)y[li];
-    }
+    consumers_sync();
   }
 }
 
@@ -421,20 +534,51 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   k_ldlt_trail<T><<<dim3(max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
+namespace {
+struct DevLimits {
+  int nsm = 0, smem = 0;
+};
+DevLimits& limits() {
+  static DevLimits L;
+  if (L.nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&L.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    L.smem -= 1024;  // static shared memory and slack
+  }
+  return L;
+}
+}  // namespace
+
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* sub_ptr, const int32_t* dofs,
-                      const uint8_t* own, int nsub, int max_nt, const int32_t* dir_list, int ndir,
-                      const double* t, double* z, int add, cudaStream_t s) {
+int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
-  size_t smem = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+  const size_t fixed = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+  const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
+  const size_t smem = (size_t)limits().smem;
+  if (smem <= fixed) return 0;
+  return (int)std::min<size_t>(8, (smem - fixed) / per_slot);
+}
+
+template <typename T>
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, int nsub, int max_nt,
+                      const int32_t* dir_list, int ndir, const double* t, double* z, int add,
+                      int* err, cudaStream_t s) {
+  using AT = typename Acc<T>::type;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limits().smem);
     attr = true;
   }
-  unsigned nb = (unsigned)nsub + nblk(ndir, 256);
-  if (nb == 0) return;
-  k_ras_solve<T><<<nb, 256, smem, s>>>(fac, E, sub_ptr, dofs, own, nsub, dir_list, ndir, t, z, add);
+  const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
+  const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
+                      ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+  int grid = std::min(nsub, limits().nsm);
+  if (grid < 1) grid = std::max(1, std::min(limits().nsm, (ndir + 255) / 256));
+  k_ras_solve<T><<<grid, 288, smem, s>>>(fac, E, order, sub_ptr, dofs, own, nsub, dir_list, ndir, t, z,
+                                         add, max_nt, nslot, err);
 }
 
 #define MSP_INST(T)                                                                              \
@@ -447,8 +591,9 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* sub_ptr, con
   template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
                                      cudaStream_t);                                              \
   template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*,     \
-                                    const uint8_t*, int, int, const int32_t*, int,               \
-                                    const double*, double*, int, cudaStream_t);
+                                    const int32_t*, const uint8_t*, int, int, const int32_t*,    \
+                                    int, const double*, double*, int, int*, cudaStream_t);    \
+  template int ras_slots<T>(int);
 MSP_INST(double)
 MSP_INST(float)
 

@@ -119,6 +119,7 @@ struct DevLevel {
   std::vector<double> trail_flops;  // flops of trailing step k (tile envelope)
   std::vector<double> panel_flops;  // flops of panel step k
   int64_t sum_np = 0, env_elems = 0, sum_owned = 0;
+  int max_band = 0;               // max over tile rows of 1 + (R_I - I)
   // transfer from level+1
   int64_t P_nnz = 0;
   int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
@@ -150,6 +151,7 @@ struct msp_instance {
   std::vector<double*> k, val, r, z, t;
   std::vector<void*> fac;  // per level, T = double or float
   int* info = nullptr;
+  int* ras_err = nullptr;  // bit 4: a bounded wait of the staged RAS solve expired
   int m = 30;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
   double* xb = nullptr;  // device buffers used by msp_solve_host
@@ -181,6 +183,7 @@ void finish_level_stats(const HostLevel& H, DevLevel& D) {
     int nt = H.sub_nt[p];
     D.sum_np += H.sub_ptr[p + 1] - H.sub_ptr[p];
     const int32_t* R = &H.tile_last[H.sub_trow[p]];
+    for (int k = 0; k < nt; ++k) D.max_band = std::max(D.max_band, 1 + R[k] - k);
     for (int k = 0; k < nt; ++k) {
       D.active[k]++;
       int rem = R[k] - k;
@@ -233,6 +236,15 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.ext_nz = A.upload(H.ext_nz);
   D.next = (int64_t)H.ext_pos.size();
   finish_level_stats(H, D);
+  {
+    const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
+    const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
+    if (slots < D.max_band + 1 || slots < 2)
+      return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large or " +
+                                       "too wide for the staged triangular solve (" +
+                                       std::to_string(D.max_nt) + " tiles, band " +
+                                       std::to_string(D.max_band) + ")");
+  }
   if (l + 1 < (int)h->host.size()) {
     D.P_nnz = (int64_t)H.P_col.size();
     D.P_rowptr = A.upload(H.P_rowptr);
@@ -360,11 +372,13 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   ProfScope ps(I->prof, kind, s);
   size_t es = level_f32(h, l) ? 4 : 8;
   if (level_f32(h, l))
-    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.sub_ptr, D.sub_dofs,
-                            D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.sub_order, D.sub_ptr,
+                            D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add,
+                            I->ras_err, s);
   else
-    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr, D.sub_dofs,
-                             D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_order, D.sub_ptr,
+                             D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add,
+                             I->ras_err, s);
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
   ps.account(2.0 * (double)D.env_elems * es + (double)D.sum_np * 13 +
@@ -587,6 +601,15 @@ int fgmres(msp_instance* I, const double* b, double* x, double rtol, msp_stats* 
   MSP_CUDA(cudaGetLastError());
   st->iterations = it;
   st->rel_residual = rnorm / bnorm;
+  {
+    int e = 0;
+    MSP_CUDA(cudaMemcpyAsync(&e, I->ras_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+      MSP_CUDA(cudaMemsetAsync(I->ras_err, 0, sizeof(int), s));
+      return fail(MSP_ERR_TIMEOUT, "a bounded wait in the staged RAS solve expired");
+    }
+  }
   if (status != MSP_OK)
     return fail(MSP_ERR_NOT_CONVERGED, "FGMRES did not reach rtol within max_it (or broke down)");
   return MSP_OK;
@@ -598,6 +621,7 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
   const int L = (int)h->dev.size();
   I->mu = A.alloc<double>(8);
   I->info = A.alloc<int>(1);
+  I->ras_err = A.alloc<int>(1);
   I->k.resize(L);
   I->val.resize(L);
   I->r.resize(L);
@@ -633,6 +657,7 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     MSP_CUDA(cudaEventCreateWithFlags(&I->join[a], cudaEventDisableTiming));
   }
   MSP_CUDA(cudaEventCreateWithFlags(&I->fork, cudaEventDisableTiming));
+  MSP_CUDA(cudaMemset(I->ras_err, 0, sizeof(int)));
   return MSP_OK;
 }
 

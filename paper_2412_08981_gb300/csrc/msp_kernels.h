@@ -56,10 +56,18 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int max_pairs, cudaStream_t s);
 // z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
 // entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
+// Subdomains are taken in the order `order` (largest first); a bounded mbarrier
+// wait that expires sets bit 4 of *err.  The factor tiles stream through
+// ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
+// diagonal tile while it reads that tile column, so the slots must exceed the
+// largest 1 + (R_I - I) of the level (checked on the host at set-up).
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* sub_ptr, const int32_t* dofs,
-                      const uint8_t* own, int nsub, int max_nt, const int32_t* dir_list, int ndir,
-                      const double* t, double* z, int add, cudaStream_t s);
+int ras_slots(int max_nt);
+template <typename T>
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, int nsub, int max_nt,
+                      const int32_t* dir_list, int ndir, const double* t, double* z, int add,
+                      int* err, cudaStream_t s);
 
 // ---- Krylov helpers (deterministic two-stage reductions)
 // out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles

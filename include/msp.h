@@ -242,7 +242,8 @@ typedef enum msp_kernel_class {
   MSP_PK_SPMV = 8,         /* J x and residuals */
   MSP_PK_TRANSFER = 9,     /* P and P^T */
   MSP_PK_VEC = 10,         /* Krylov dots, axpys, copies */
-  MSP_PK_COUNT = 11
+  MSP_PK_LDLT_BLOCKS = 11, /* whole-block factorisation, one persistent launch per level */
+  MSP_PK_COUNT = 12
 } msp_kernel_class;
 
 typedef struct msp_kernel_profile {

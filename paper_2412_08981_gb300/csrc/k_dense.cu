@@ -58,25 +58,20 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 }
 
 // ---------------------------------------------------- diagonal tile LDL^T
-// One block per active subdomain, computing in the factor's precision.
-// Column c: every row r > c subtracts (a_rc / d_c) a_sc from its entries s in
-// (c, r] (a_sc, the still unscaled column, is final since step c-1), one
-// barrier per column.  1/d_c is formed once, by the thread that finishes the
-// pivot d_c (the update of entry (c, c) at step c-1), so each column costs a
-// single division.  Then L = W D^{-1}, and the inverse X = L^{-1} of the unit
-// lower factor is built row by row (row i needs rows < i only), four lanes
-// per entry, one barrier per row, stored transposed in the strict upper part.
-template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
-                                                   const int32_t* __restrict__ order, int k,
-                                                   int* __restrict__ info) {
-  using AT = typename Acc<T>::type;
-  extern __shared__ unsigned char smraw[];
-  AT* A = reinterpret_cast<AT*>(smraw);   // [64][65]: L (lower), D (diag), X^T (upper)
-  AT* dinv = A + 64 * 65;                 // [64] reciprocals of the pivots
-  const int p = order[blockIdx.x];
-  T* tile = fac + tile_at(E, p, k, k);
+// Factors one diagonal tile in shared memory, computing in the factor's
+// precision.  Column c: every row r > c subtracts (a_rc / d_c) a_sc from its
+// entries s in (c, r] (a_sc, the still unscaled column, is final since step
+// c-1), one barrier per column.  1/d_c is formed once, by the thread that
+// finishes the pivot d_c (the update of entry (c, c) at step c-1), so each
+// column costs a single division.  Then L = W D^{-1}, and the inverse
+// X = L^{-1} of the unit lower factor is built row by row (row i needs rows
+// < i only), four lanes per entry, one barrier per row, stored transposed in
+// the strict upper part.  smem: (64*65 + 64) elements of AT.
+template <typename T, typename AT>
+__device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
+  AT* dinv = A + 64 * 65;  // reciprocals of the pivots
   const int tid = threadIdx.x;
+  __syncthreads();  // the shared buffer may still be read by a previous phase
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
@@ -111,7 +106,7 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   for (int i = 1; i < T64; ++i) {
     AT v = 0;
     if (jcol < i) {
-      for (int m = jcol + 1 + part; m < i; m += 4) v += A[i * 65 + m] * A[jcol * 65 + m];
+      for (int m = jcol + 1 + part; m < i; m += 4) v = fma(A[i * 65 + m], A[jcol * 65 + m], v);
     }
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -121,25 +116,27 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
-// ----------------------------------------------------------- panel solve
-// L_ik = A_ik X^T D^{-1} for the tiles below the diagonal tile of step k,
-// k < i <= R_k.  Column c needs the products over m <= c (X^T is upper
-// triangular), so warp w takes the 4 columns 4w..4w+3 and the 4 columns
-// 60-4w..63-4w: every warp does the same work.  Each lane owns 2 rows.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
-                                                    const int32_t* __restrict__ order, int k) {
+__global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
+                                                   const int32_t* __restrict__ order, int k,
+                                                   int* __restrict__ info) {
   using AT = typename Acc<T>::type;
-  const int p = order[blockIdx.y];
-  const int i = k + 1 + blockIdx.x;
-  if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
-  AT* A = reinterpret_cast<AT*>(smraw);   // [64][65] panel tile
-  AT* Xt = A + 64 * 65;                   // [64][64] X^T (upper, unit diagonal)
-  AT* Dinv = Xt + 64 * 64;                // [64]
-  const T* dtile = fac + tile_at(E, p, k, k);
-  T* ptile = fac + tile_at(E, p, i, k);
+  const int p = order[blockIdx.x];
+  diag_tile<T, AT>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
+}
+
+// ----------------------------------------------------------- panel solve
+// L_ik = A_ik X^T D^{-1} for a tile below the diagonal tile of step k.
+// Column c needs the products over m <= c (X^T is upper triangular), so warp
+// w takes the 4 columns 4w..4w+3 and the 4 columns 60-4w..63-4w: every warp
+// does the same work.  Each lane owns 2 rows.  smem: (64*65 + 64*64 + 64) AT.
+template <typename T, typename AT>
+__device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, AT* __restrict__ A) {
+  AT* Xt = A + 64 * 65;     // [64][64] X^T (upper, unit diagonal)
+  AT* Dinv = Xt + 64 * 64;  // [64]
   const int tid = threadIdx.x;
+  __syncthreads();
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     A[r * 65 + c] = (AT)ptile[e];
@@ -162,8 +159,8 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         AT x = Xt[m * 64 + c0 + q];
-        w0[q] += a0 * x;
-        w1[q] += a1 * x;
+        w0[q] = fma(a0, x, w0[q]);
+        w1[q] = fma(a1, x, w1[q]);
       }
     }
 #pragma unroll
@@ -174,9 +171,20 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
+                                                    const int32_t* __restrict__ order, int k) {
+  using AT = typename Acc<T>::type;
+  const int p = order[blockIdx.y];
+  const int i = k + 1 + blockIdx.x;
+  if (i > E.last[E.trow[p] + k]) return;
+  extern __shared__ unsigned char smraw[];
+  panel_tile<T, AT>(fac + tile_at(E, p, k, k), fac + tile_at(E, p, i, k), reinterpret_cast<AT*>(smraw));
+}
+
 // -------------------------------------------------------- trailing update
-// A_ij -= (L_ik D_k) L_jk^T for k < j <= i <= R_k.  One block per (i, j)
-// pair; each thread accumulates a 4x4 register block from k-major tiles.
+// A_ij -= (L_ik D_k) L_jk^T for one pair k < j <= i; each thread accumulates a
+// 4x4 register block from k-major tiles.  smem: 2*64*68 AT.
 __device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
   int x = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((x + 1) * (x + 2) / 2 <= t) ++x;
@@ -185,25 +193,15 @@ __device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
   b = t - x * (x + 1) / 2;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
-                                                    const int32_t* __restrict__ order, int k) {
-  using AT = typename Acc<T>::type;
-  const int p = order[blockIdx.y];
-  const int rem = E.last[E.trow[p] + k] - k;
-  if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
-  int a, b;
-  pair_of(blockIdx.x, a, b);
-  const int i = k + 1 + a, j = k + 1 + b;
-  extern __shared__ unsigned char smraw[];
+template <typename T, typename AT>
+__device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
+                           const T* __restrict__ lj, T* __restrict__ out, bool diagonal,
+                           AT* __restrict__ smem) {
   constexpr int LD = 68;
-  AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][LD] = L_ik[r][m] * d_m
-  AT* Lt = Wt + 64 * LD;                  // [64 m][LD] = L_jk[c][m]
-  const T* dt = fac + tile_at(E, p, k, k);
-  const T* li = fac + tile_at(E, p, i, k);
-  const T* lj = fac + tile_at(E, p, j, k);
-  T* out = fac + tile_at(E, p, i, j);
+  AT* Wt = smem;         // [64 m][LD] = L_ik[r][m] * d_m
+  AT* Lt = Wt + 64 * LD; // [64 m][LD] = L_jk[c][m]
   const int tid = threadIdx.x;
+  __syncthreads();
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, m = e & 63;
     AT d = (AT)dt[m * 65];
@@ -212,7 +210,7 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
   }
   __syncthreads();
   const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;
-  if (i == j && c0 > r0 + 3) return;  // strictly above the diagonal of a diagonal tile
+  if (diagonal && c0 > r0 + 3) return;  // strictly above the diagonal of a diagonal tile
   AT acc[4][4];
 #pragma unroll
   for (int x = 0; x < 4; ++x)
@@ -229,18 +227,64 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * bv[y];
+      for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       int r = r0 + x, c = c0 + y;
-      if (i != j || c <= r) {
+      if (!diagonal || c <= r) {
         T* o = out + r * 64 + c;
         *o = (T)((AT)*o - acc[x][y]);
       }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
+                                                    const int32_t* __restrict__ order, int k) {
+  using AT = typename Acc<T>::type;
+  const int p = order[blockIdx.y];
+  const int rem = E.last[E.trow[p] + k] - k;
+  if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
+  int a, b;
+  pair_of(blockIdx.x, a, b);
+  const int i = k + 1 + a, j = k + 1 + b;
+  extern __shared__ unsigned char smraw[];
+  trail_pair<T, AT>(fac + tile_at(E, p, k, k), fac + tile_at(E, p, i, k), fac + tile_at(E, p, j, k),
+                    fac + tile_at(E, p, i, j), i == j, reinterpret_cast<AT*>(smraw));
+}
+
+// ------------------------------------------------- whole-block factorisation
+// Persistent: CTA b factors the blocks cta_list[cta_ptr[b] .. cta_ptr[b+1])
+// (a longest-first balanced assignment built on the host), every tile step
+// in turn -- diagonal tile, its panel, the trailing pairs -- with the phases
+// separated by block barriers (global writes of one phase are visible to the
+// whole block in the next).  Used on levels with many blocks, where one launch
+// replaces three launches per tile step.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev E,
+                                                     const int32_t* __restrict__ cta_ptr,
+                                                     const int32_t* __restrict__ cta_list,
+                                                     int* __restrict__ info) {
+  using AT = typename Acc<T>::type;
+  extern __shared__ unsigned char smraw[];
+  AT* sm = reinterpret_cast<AT*>(smraw);
+  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+    const int p = cta_list[q];
+    const int NT = E.nt[p];
+    for (int k = 0; k < NT; ++k) {
+      const int R = E.last[E.trow[p] + k];
+      T* dt = fac + tile_at(E, p, k, k);
+      diag_tile<T, AT>(dt, sm, info);
+      for (int i = k + 1; i <= R; ++i) panel_tile<T, AT>(dt, fac + tile_at(E, p, i, k), sm);
+      for (int i = k + 1; i <= R; ++i)
+        for (int j = k + 1; j <= i; ++j)
+          trail_pair<T, AT>(dt, fac + tile_at(E, p, i, k), fac + tile_at(E, p, j, k),
+                            fac + tile_at(E, p, i, j), i == j, sm);
+    }
+  }
 }
 
 // -------------------------------------------------------------- RAS solve
@@ -316,11 +360,11 @@ struct TileSeq {
 
 template <typename T>
 __global__ void __launch_bounds__(288, 1) k_ras_solve(
-    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ order,
-    const int32_t* __restrict__ sub_ptr, const int32_t* __restrict__ dofs,
-    const uint8_t* __restrict__ own, int nsub, const int32_t* __restrict__ dir_list, int ndir,
-    const double* __restrict__ t, double* __restrict__ z, int add, int max_nt, int nslot,
-    int* __restrict__ err) {
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
+    const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
+    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
+    double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err) {
   using AT = typename Acc<T>::type;
   constexpr uint32_t kTileBytes = TE * sizeof(T);
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -354,8 +398,8 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       bulk_g2s(ring + (size_t)slot * TE, src, kTileBytes, &full[slot]);
       ++seq;
     };
-    for (int q = blockIdx.x; q < nsub; q += G) {
-      TileSeq S(E, order[q]);
+    for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+      TileSeq S(E, cta_list[q]);
       for (int I = 0; I < S.NT; ++I)
         for (int J = S.first(I); J <= I; ++J) issue(fac + S.at(I, J));
       for (int I = S.NT - 1; I >= 0; --I) {
@@ -385,8 +429,8 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
     if (lane == 0) mbar_arrive(&empty[seq % nslot]);
     ++seq;
   };
-  for (int q = blockIdx.x; q < nsub; q += G) {
-    const int p = order[q];
+  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+    const int p = cta_list[q];
     TileSeq S(E, p);
     const int NT = S.NT;
     const int off = sub_ptr[p];
@@ -404,7 +448,8 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int r = warp * 8 + k;
-          s8[k] += (AT)tl[r * 64 + lane] * y0 + (AT)tl[r * 64 + lane + 32] * y1;
+          s8[k] = fma((AT)tl[r * 64 + lane], y0, s8[k]);
+          s8[k] = fma((AT)tl[r * 64 + lane + 32], y1, s8[k]);
         }
         release();
       }
@@ -420,9 +465,12 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
         const T* dt = acquire();
         const int bcol = tid & 63, pr = tid >> 6;
         AT v = 0;
-        for (int a = pr * 16; a < pr * 16 + 16; ++a)
-          if (a < bcol) v += (AT)dt[a * 64 + bcol] * acc[a];
-        part[pr * 64 + bcol] = v;
+        AT v2 = 0;  // two independent chains
+        for (int a = pr * 16; a < pr * 16 + 16; a += 2) {
+          if (a < bcol) v = fma((AT)dt[a * 64 + bcol], acc[a], v);
+          if (a + 1 < bcol) v2 = fma((AT)dt[(a + 1) * 64 + bcol], acc[a + 1], v2);
+        }
+        part[pr * 64 + bcol] = v + v2;
         release();
       }
       consumers_sync();
@@ -441,8 +489,8 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
         for (int k = 0; k < 8; ++k) {
           const int r = warp * 8 + k;
           const AT xr = y[J * 64 + r];
-          s0 += (AT)tl[r * 64 + lane] * xr;
-          s1 += (AT)tl[r * 64 + lane + 32] * xr;
+          s0 = fma((AT)tl[r * 64 + lane], xr, s0);
+          s1 = fma((AT)tl[r * 64 + lane + 32], xr, s1);
         }
         release();
       }
@@ -562,8 +610,9 @@ int ras_slots(int max_nt) {
 }
 
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, int nsub, int max_nt,
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
+                      const int32_t* cta_list, int grid, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
                       int* err, cudaStream_t s) {
   using AT = typename Acc<T>::type;
@@ -575,10 +624,30 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
                       ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
-  int grid = std::min(nsub, limits().nsm);
-  if (grid < 1) grid = std::max(1, std::min(limits().nsm, (ndir + 255) / 256));
-  k_ras_solve<T><<<grid, 288, smem, s>>>(fac, E, order, sub_ptr, dofs, own, nsub, dir_list, ndir, t, z,
-                                         add, max_nt, nslot, err);
+  if (grid < 1) return;
+  k_ras_solve<T><<<grid, 288, smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
+                                         ndir, t, z, add, max_nt, nslot, err);
+}
+
+template <typename T>
+void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                        int grid, int* info, cudaStream_t s) {
+  using AT = typename Acc<T>::type;
+  if (grid < 1) return;
+  const size_t smem = (size_t)(2 * 64 * 68) * sizeof(AT);  // the largest phase (trailing pair)
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ldlt_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_ldlt_blocks<T><<<grid, 256, smem, s>>>(fac, E, cta_ptr, cta_list, info);
+}
+
+template <typename T>
+int ldlt_blocks_per_sm() {
+  using AT = typename Acc<T>::type;
+  const size_t smem = (size_t)(2 * 64 * 68) * sizeof(AT) + 1024;
+  return (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(limits().smem + 1024) / smem));
 }
 
 #define MSP_INST(T)                                                                              \
@@ -590,10 +659,14 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const
                                      cudaStream_t);                                              \
   template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
                                      cudaStream_t);                                              \
-  template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*,     \
-                                    const int32_t*, const uint8_t*, int, int, const int32_t*,    \
-                                    int, const double*, double*, int, int*, cudaStream_t);    \
-  template int ras_slots<T>(int);
+  template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
+                                    const int32_t*, const int32_t*, const uint8_t*, int,         \
+                                    const int32_t*, int, const double*, double*, int, int*,      \
+                                    cudaStream_t);                                               \
+  template int ras_slots<T>(int);                                                                \
+  template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
+                                      int*, cudaStream_t);                                       \
+  template int ldlt_blocks_per_sm<T>();
 MSP_INST(double)
 MSP_INST(float)
 

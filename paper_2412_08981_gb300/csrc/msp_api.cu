@@ -120,6 +120,11 @@ struct DevLevel {
   std::vector<double> panel_flops;  // flops of panel step k
   int64_t sum_np = 0, env_elems = 0, sum_owned = 0;
   int max_band = 0;               // max over tile rows of 1 + (R_I - I)
+  int ras_grid = 0;               // CTAs of the RAS solve and their subdomain lists
+  int32_t *ras_cta_ptr = nullptr, *ras_cta_list = nullptr;
+  bool fac_blocks = false;        // whole-block persistent factorisation on this level
+  int32_t *fac_cta_ptr = nullptr; // one block per CTA, largest first
+  double fac_flops = 0;           // all tile steps of the level
   // transfer from level+1
   int64_t P_nnz = 0;
   int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
@@ -177,6 +182,7 @@ void finish_level_stats(const HostLevel& H, DevLevel& D) {
   D.trail_flops.assign(D.max_nt + 1, 0.0);
   D.panel_flops.assign(D.max_nt + 1, 0.0);
   D.sum_np = D.sum_owned = 0;
+  D.fac_flops = 0;
   D.env_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
   const double tile_gemm = 2.0 * 64 * 64 * 64, tile_syrk = 2.0 * 64 * (64 * 65 / 2);
   for (int p = 0; p < H.nsub; ++p) {
@@ -190,6 +196,8 @@ void finish_level_stats(const HostLevel& H, DevLevel& D) {
       D.max_rows[k] = std::max(D.max_rows[k], rem);
       D.trail_flops[k] += (double)rem * (rem - 1) / 2 * tile_gemm + rem * tile_syrk;
       D.panel_flops[k] += rem * (64.0 * 64 * 65);  // triangular X^T product + scaling
+      D.fac_flops += (double)rem * (rem - 1) / 2 * tile_gemm + rem * tile_syrk +
+                     rem * (64.0 * 64 * 65) + 2.0 * 64 * 64 * 64 / 3;
     }
   }
   for (uint8_t o : H.sub_own) D.sum_owned += o;
@@ -236,6 +244,44 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.ext_nz = A.upload(H.ext_nz);
   D.next = (int64_t)H.ext_pos.size();
   finish_level_stats(H, D);
+  {
+    // longest-first assignment of subdomains to the persistent RAS CTAs, cost
+    // = stored envelope tiles (both sweeps read each once)
+    int nsm = 0;
+    MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int G = std::max(1, std::min(H.nsub, nsm));
+    std::vector<int32_t> ids(H.nsub);
+    std::vector<int64_t> cost(H.nsub);
+    for (int p = 0; p < H.nsub; ++p) {
+      ids[p] = p;
+      cost[p] = (H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems;
+    }
+    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int64_t> load(G, 0);
+    std::vector<std::vector<int32_t>> lists(G);
+    for (int p : ids) {
+      int best = 0;
+      for (int g = 1; g < G; ++g)
+        if (load[g] < load[best]) best = g;
+      load[best] += cost[p];
+      lists[best].push_back(p);
+    }
+    std::vector<int32_t> cptr(G + 1, 0), clist;
+    for (int g = 0; g < G; ++g) {
+      clist.insert(clist.end(), lists[g].begin(), lists[g].end());
+      cptr[g + 1] = (int32_t)clist.size();
+    }
+    D.ras_grid = G;
+    D.ras_cta_ptr = A.upload(cptr);
+    D.ras_cta_list = A.upload(clist);
+    // many blocks: factor them with one persistent launch, one block per CTA in
+    // descending tile count (the hardware hands out CTAs in that order)
+    D.fac_blocks = H.nsub >= std::max(2, nsm / 2);
+    std::vector<int32_t> iota(H.nsub + 1);
+    for (int p = 0; p <= H.nsub; ++p) iota[p] = p;
+    D.fac_cta_ptr = A.upload(iota);
+    if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
+  }
   {
     const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
     const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
@@ -314,6 +360,12 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
     launch_extract<T>(D.ext_pos, D.ext_nz, D.next, I->val[l], D.fac_elems, fac, s);
     ps.account((double)D.fac_elems * sizeof(T) + (double)D.next * (12 + sizeof(T) + 8), 0);
   }
+  if (D.fac_blocks) {
+    ProfScope ps(I->prof, PK_LDLT_BLOCKS, s);
+    launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.sub_order, D.nsub, I->info, s);
+    ps.account(0, D.fac_flops);
+    return;
+  }
   for (int k = 0; k < D.max_nt; ++k) {
     int na = D.active[k];
     {
@@ -372,13 +424,13 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   ProfScope ps(I->prof, kind, s);
   size_t es = level_f32(h, l) ? 4 : 8;
   if (level_f32(h, l))
-    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.sub_order, D.sub_ptr,
-                            D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add,
-                            I->ras_err, s);
+    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                            D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
+                            D.dir_list, D.ndir, t, z, add, I->ras_err, s);
   else
-    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_order, D.sub_ptr,
-                             D.sub_dofs, D.sub_own, D.nsub, D.max_nt, D.dir_list, D.ndir, t, z, add,
-                             I->ras_err, s);
+    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                             D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
+                             D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, s);
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
   ps.account(2.0 * (double)D.env_elems * es + (double)D.sum_np * 13 +

@@ -54,9 +54,17 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
 template <typename T>
 void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                        int max_pairs, cudaStream_t s);
+// The whole L D L^T of many blocks in one persistent launch: CTA b factors
+// cta_list[cta_ptr[b] .. cta_ptr[b+1]) through every tile step.
+template <typename T>
+void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                        int grid, int* info, cudaStream_t s);
+template <typename T>
+int ldlt_blocks_per_sm();
 // z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
 // entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
-// Subdomains are taken in the order `order` (largest first); a bounded mbarrier
+// CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
+// longest-first balanced assignment built on the host); a bounded mbarrier
 // wait that expires sets bit 4 of *err.  The factor tiles stream through
 // ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
 // diagonal tile while it reads that tile column, so the slots must exceed the
@@ -64,8 +72,9 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
 template <typename T>
 int ras_slots(int max_nt);
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* order, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, int nsub, int max_nt,
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
+                      const int32_t* cta_list, int grid, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
                       int* err, cudaStream_t s);
 

@@ -14,7 +14,8 @@ enum {
   PK_ASSEMBLE = MSP_PK_ASSEMBLE, PK_EXTRACT = MSP_PK_EXTRACT, PK_LDLT_DIAG = MSP_PK_LDLT_DIAG,
   PK_LDLT_PANEL = MSP_PK_LDLT_PANEL, PK_LDLT_TRAIL = MSP_PK_LDLT_TRAIL, PK_RAS = MSP_PK_RAS,
   PK_RAS_COARSER = MSP_PK_RAS_COARSER, PK_COARSE = MSP_PK_COARSE, PK_SPMV = MSP_PK_SPMV,
-  PK_TRANSFER = MSP_PK_TRANSFER, PK_VEC = MSP_PK_VEC, PK_COUNT = MSP_PK_COUNT
+  PK_TRANSFER = MSP_PK_TRANSFER, PK_VEC = MSP_PK_VEC, PK_LDLT_BLOCKS = MSP_PK_LDLT_BLOCKS,
+  PK_COUNT = MSP_PK_COUNT
 };
 
 struct Profile {

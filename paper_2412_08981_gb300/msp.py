@@ -32,7 +32,7 @@ _ARRAY_DTYPE = {"rowptr": np.int32, "col": np.int32, "sub_ptr": np.int32, "sub_d
                 "PT_val": np.float64, "load": np.float64, "val": np.float64,
                 "sub_nt": np.int32, "tile_first": np.int32}
 KERNEL_CLASSES = ["assemble", "extract", "ldlt_diag", "ldlt_panel", "ldlt_trail", "ras",
-                  "ras_coarser", "coarse", "spmv", "transfer", "vec"]
+                  "ras_coarser", "coarse", "spmv", "transfer", "vec", "ldlt_blocks"]
 MSP_TILE = 64
 
 ERR_NAMES = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_ERR_INVALID", -2: "MSP_ERR_OOM",

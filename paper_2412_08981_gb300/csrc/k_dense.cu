@@ -346,17 +346,24 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
 }
 __device__ inline void consumers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// The tile sequence of one subdomain, shared by producer and consumers.
-struct TileSeq {
-  const EnvDev& E;
-  int p, rb, NT;
-  __device__ TileSeq(const EnvDev& e, int pp) : E(e), p(pp), rb(e.trow[pp]), NT(e.nt[pp]) {}
-  __device__ int first(int I) const { return E.first[rb + I]; }
-  __device__ int last(int I) const { return E.last[rb + I]; }
-  __device__ int64_t at(int I, int J) const {  // element offset of tile (I, J)
-    return E.fac_off[p] + (int64_t)(E.toff[rb + I] + (J - E.first[rb + I])) * TE;
-  }
+// Per-subdomain envelope metadata staged in shared memory (one copy for the
+// producer, which runs ahead, one for the consumers): F_I, R_I and the tile
+// index of (I, F_I), so that no tile address needs a global-memory lookup.
+struct MetaSm {
+  int32_t* first;
+  int32_t* last;
+  int32_t* toff;
 };
+
+// All 32 lanes of the calling warp load the metadata of subdomain p.
+__device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int lane) {
+  const int rb = E.trow[p];
+  for (int I = lane; I < NT; I += 32) {
+    m.first[I] = E.first[rb + I];
+    m.last[I] = E.last[rb + I];
+    m.toff[I] = E.toff[rb + I];
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(288, 1) k_ras_solve(
@@ -374,6 +381,9 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
   AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
   AT* acc = y + max_nt * 64;                                                    // [64]
   AT* part = acc + 64;                                                          // [8][64]
+  int32_t* meta = reinterpret_cast<int32_t*>(part + 8 * 64);                    // [2][3][max_nt]
+  const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
+  const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
   __shared__ int sflag;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -389,7 +399,6 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
   __syncthreads();
 
   if (warp == kConsumers) {  // ------------------------------------ producer
-    if (lane != 0) return;
     long seq = 0;
     auto issue = [&](const T* src) {
       const int slot = (int)(seq % nslot);
@@ -399,17 +408,28 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       ++seq;
     };
     for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
-      TileSeq S(E, cta_list[q]);
-      for (int I = 0; I < S.NT; ++I)
-        for (int J = S.first(I); J <= I; ++J) issue(fac + S.at(I, J));
-      for (int I = S.NT - 1; I >= 0; --I) {
-        issue(fac + S.at(I, I));
-        for (int J = I + 1; J <= S.last(I); ++J) issue(fac + S.at(J, I));
+      const int p = cta_list[q];
+      const int NT = E.nt[p];
+      load_meta(E, p, NT, pm, lane);
+      __syncwarp();
+      if (lane == 0) {
+        const T* base = fac + E.fac_off[p];
+        for (int I = 0; I < NT; ++I) {
+          const T* row = base + (int64_t)pm.toff[I] * TE;
+          for (int J = pm.first[I]; J <= I; ++J) issue(row + (int64_t)(J - pm.first[I]) * TE);
+        }
+        for (int I = NT - 1; I >= 0; --I) {
+          issue(base + (int64_t)(pm.toff[I] + (I - pm.first[I])) * TE);
+          for (int J = I + 1; J <= pm.last[I]; ++J)
+            issue(base + (int64_t)(pm.toff[J] + (I - pm.first[J])) * TE);
+        }
       }
+      __syncwarp();
     }
     // drain: the last copy of every slot has landed before the CTA may exit
-    for (long k = (seq > nslot ? seq - nslot : 0); k < seq; ++k)
-      mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err);
+    if (lane == 0)
+      for (long k = (seq > nslot ? seq - nslot : 0); k < seq; ++k)
+        mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err);
     return;
   }
 
@@ -431,10 +451,10 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
   };
   for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
     const int p = cta_list[q];
-    TileSeq S(E, p);
-    const int NT = S.NT;
+    const int NT = E.nt[p];
     const int off = sub_ptr[p];
     const int np_ = sub_ptr[p + 1] - off;
+    if (warp == 0) load_meta(E, p, NT, cm, lane);
     for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
     consumers_sync();
     // forward sweep
@@ -442,7 +462,7 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       AT s8[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) s8[k] = 0;
-      for (int J = S.first(I); J < I; ++J) {
+      for (int J = cm.first[I]; J < I; ++J) {
         const T* tl = acquire();
         const AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
 #pragma unroll
@@ -483,7 +503,7 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       const long dseq = seq;
       ++seq;
       AT s0 = 0, s1 = 0;
-      for (int J = I + 1; J <= S.last(I); ++J) {
+      for (int J = I + 1; J <= cm.last[I]; ++J) {
         const T* tl = acquire();
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -509,8 +529,8 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       for (int k = 0; k < 8; ++k) {
         const int a = warp * 8 + k;
         AT v = 0;
-        if (lane > a) v += (AT)dt[a * 64 + lane] * acc[lane];
-        if (lane + 32 > a) v += (AT)dt[a * 64 + lane + 32] * acc[lane + 32];
+        if (lane > a) v = fma((AT)dt[a * 64 + lane], acc[lane], v);
+        if (lane + 32 > a) v = fma((AT)dt[a * 64 + lane + 32], acc[lane + 32], v);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) y[I * 64 + a] = acc[a] + v;
@@ -602,7 +622,7 @@ DevLimits& limits() {
 template <typename T>
 int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
-  const size_t fixed = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+  const size_t fixed = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
   const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
   const size_t smem = (size_t)limits().smem;
   if (smem <= fixed) return 0;
@@ -623,7 +643,7 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
   }
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
-                      ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT);
+                      ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
   if (grid < 1) return;
   k_ras_solve<T><<<grid, 288, smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
                                          ndir, t, z, add, max_nt, nslot, err);

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev
 // records an error bit and goes on (the results are then garbage and the
 // host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
 // own copies, so none is in flight when the CTA exits.
-constexpr int kConsumers = 8;
+constexpr int kConsumers = 16;
 constexpr long kWaitLimit = 1L << 20;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -344,7 +344,7 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ inline void consumers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory"); }
 
 // Per-subdomain envelope metadata staged in shared memory (one copy for the
 // producer, which runs ahead, one for the consumers): F_I, R_I and the tile
@@ -366,7 +366,7 @@ __device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int l
 }
 
 template <typename T>
-__global__ void __launch_bounds__(288, 1) k_ras_solve(
+__global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
     const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
     const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
@@ -374,14 +374,17 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
     double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err) {
   using AT = typename Acc<T>::type;
   constexpr uint32_t kTileBytes = TE * sizeof(T);
+  constexpr int NC = kConsumers * 32;       // consumer threads
+  constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
+  constexpr int NP = NC / 64;               // column parts of the forward diagonal product
   extern __shared__ __align__(128) unsigned char smraw[];
   T* ring = reinterpret_cast<T*>(smraw);                                        // [nslot][TE]
   uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)nslot * kTileBytes);  // [nslot]
   uint64_t* empty = full + nslot;                                               // [nslot]
   AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
   AT* acc = y + max_nt * 64;                                                    // [64]
-  AT* part = acc + 64;                                                          // [8][64]
-  int32_t* meta = reinterpret_cast<int32_t*>(part + 8 * 64);                    // [2][3][max_nt]
+  AT* part = acc + 64;                                                          // [kConsumers][64]
+  int32_t* meta = reinterpret_cast<int32_t*>(part + kConsumers * 64);           // [2][3][max_nt]
   const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
   const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
   __shared__ int sflag;
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
   }
 
   // ------------------------------------------------------------ consumers
-  for (int d = blockIdx.x * 256 + tid; d < ndir; d += G * 256) {
+  for (int d = blockIdx.x * NC + tid; d < ndir; d += G * NC) {
     const int g = dir_list[d];
     z[g] = add ? z[g] + t[g] : t[g];
   }
@@ -455,38 +458,42 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
     const int off = sub_ptr[p];
     const int np_ = sub_ptr[p + 1] - off;
     if (warp == 0) load_meta(E, p, NT, cm, lane);
-    for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+    for (int li = tid; li < NT * 64; li += NC) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
     consumers_sync();
     // forward sweep
     for (int I = 0; I < NT; ++I) {
-      AT s8[8];
+      AT sr[RW];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) s8[k] = 0;
+      for (int k = 0; k < RW; ++k) sr[k] = 0;
       for (int J = cm.first[I]; J < I; ++J) {
         const T* tl = acquire();
         const AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
+        AT a0[RW], a1[RW];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int r = warp * 8 + k;
-          s8[k] = fma((AT)tl[r * 64 + lane], y0, s8[k]);
-          s8[k] = fma((AT)tl[r * 64 + lane + 32], y1, s8[k]);
+        for (int k = 0; k < RW; ++k) {
+          const int r = warp * RW + k;
+          a0[k] = (AT)tl[r * 64 + lane];
+          a1[k] = (AT)tl[r * 64 + lane + 32];
         }
+#pragma unroll
+        for (int k = 0; k < RW; ++k) sr[k] = fma(a1[k], y1, fma(a0[k], y0, sr[k]));
         release();
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        AT v = s8[k];
+      for (int k = 0; k < RW; ++k) {
+        AT v = sr[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) acc[warp * 8 + k] = y[I * 64 + warp * 8 + k] - v;
+        if (lane == 0) acc[warp * RW + k] = y[I * 64 + warp * RW + k] - v;
       }
       consumers_sync();
       {  // y_I = X acc, X[b][a] = tile[a][b] for a < b
         const T* dt = acquire();
         const int bcol = tid & 63, pr = tid >> 6;
-        AT v = 0;
-        AT v2 = 0;  // two independent chains
-        for (int a = pr * 16; a < pr * 16 + 16; a += 2) {
+        constexpr int AW = 64 / NP;  // rows a of each part
+        AT v = 0, v2 = 0;            // two independent chains
+#pragma unroll
+        for (int a = pr * AW; a < pr * AW + AW; a += 2) {
           if (a < bcol) v = fma((AT)dt[a * 64 + bcol], acc[a], v);
           if (a + 1 < bcol) v2 = fma((AT)dt[(a + 1) * 64 + bcol], acc[a + 1], v2);
         }
@@ -494,7 +501,12 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
         release();
       }
       consumers_sync();
-      if (tid < 64) y[I * 64 + tid] = acc[tid] + part[tid] + part[64 + tid] + part[128 + tid] + part[192 + tid];
+      if (tid < 64) {
+        AT v = acc[tid];
+#pragma unroll
+        for (int q2 = 0; q2 < NP; ++q2) v += part[q2 * 64 + tid];
+        y[I * 64 + tid] = v;
+      }
       consumers_sync();
     }
     // backward sweep
@@ -505,12 +517,18 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       AT s0 = 0, s1 = 0;
       for (int J = I + 1; J <= cm.last[I]; ++J) {
         const T* tl = acquire();
+        AT a0[RW], a1[RW], xr[RW];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int r = warp * 8 + k;
-          const AT xr = y[J * 64 + r];
-          s0 = fma((AT)tl[r * 64 + lane], xr, s0);
-          s1 = fma((AT)tl[r * 64 + lane + 32], xr, s1);
+        for (int k = 0; k < RW; ++k) {
+          const int r = warp * RW + k;
+          xr[k] = y[J * 64 + r];
+          a0[k] = (AT)tl[r * 64 + lane];
+          a1[k] = (AT)tl[r * 64 + lane + 32];
+        }
+#pragma unroll
+        for (int k = 0; k < RW; ++k) {
+          s0 = fma(a0[k], xr[k], s0);
+          s1 = fma(a1[k], xr[k], s1);
         }
         release();
       }
@@ -520,14 +538,14 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       if (tid < 64) {
         AT v = 0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) v += part[w * 64 + tid];
+        for (int w = 0; w < kConsumers; ++w) v += part[w * 64 + tid];
         acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - v;
       }
       consumers_sync();
       // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int a = warp * 8 + k;
+      for (int k = 0; k < RW; ++k) {
+        const int a = warp * RW + k;
         AT v = 0;
         if (lane > a) v = fma((AT)dt[a * 64 + lane], acc[lane], v);
         if (lane + 32 > a) v = fma((AT)dt[a * 64 + lane + 32], acc[lane + 32], v);
@@ -539,7 +557,7 @@ __global__ void __launch_bounds__(288, 1) k_ras_solve(
       if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
       consumers_sync();
     }
-    for (int li = tid; li < np_; li += 256) {
+    for (int li = tid; li < np_; li += NC) {
       if (own[off + li]) {
         const int g = dofs[off + li];
         z[g] = add ? z[g] + (double)y[li] : (double)y[li];
@@ -622,7 +640,7 @@ DevLimits& limits() {
 template <typename T>
 int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
-  const size_t fixed = ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+  const size_t fixed = ((size_t)max_nt * 64 + 64 + kConsumers * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
   const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
   const size_t smem = (size_t)limits().smem;
   if (smem <= fixed) return 0;
@@ -643,9 +661,9 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
   }
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
-                      ((size_t)max_nt * 64 + 64 + 8 * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+                      ((size_t)max_nt * 64 + 64 + kConsumers * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
   if (grid < 1) return;
-  k_ras_solve<T><<<grid, 288, smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
+  k_ras_solve<T><<<grid, 32 * (kConsumers + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
                                          ndir, t, z, add, max_nt, nslot, err);
 }
 

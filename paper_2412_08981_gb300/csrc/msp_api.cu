@@ -285,7 +285,9 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   {
     const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
     const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
-    if (slots < D.max_band + 1 || slots < 2)
+    // the backward sweep holds a row's diagonal tile while the next R_I - I
+    // tiles stream in: max_band slots are enough, and never deadlock
+    if (slots < D.max_band || slots < 2)
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large or " +
                                        "too wide for the staged triangular solve (" +
                                        std::to_string(D.max_nt) + " tiles, band " +

@@ -67,8 +67,9 @@ int ldlt_blocks_per_sm();
 // longest-first balanced assignment built on the host); a bounded mbarrier
 // wait that expires sets bit 4 of *err.  The factor tiles stream through
 // ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
-// diagonal tile while it reads that tile column, so the slots must exceed the
-// largest 1 + (R_I - I) of the level (checked on the host at set-up).
+// diagonal tile while it reads that tile column, so there must be at least
+// 1 + (R_I - I) slots for every row I of the level (checked on the host at
+// set-up).
 template <typename T>
 int ras_slots(int max_nt);
 template <typename T>

@@ -209,8 +209,18 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
     Lt[m * LD + r] = (AT)lj[e];
   }
   __syncthreads();
-  const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;
-  if (diagonal && c0 > r0 + 3) return;  // strictly above the diagonal of a diagonal tile
+  // 4x4 output blocks: all 256 of a general pair; for a diagonal pair only the
+  // 136 blocks on or below the diagonal, numbered densely so that they fill
+  // whole warps (an idle lane costs as much FP64 issue time as a busy one)
+  int rb, cb;
+  if (!diagonal) {
+    rb = tid >> 4;
+    cb = tid & 15;
+  } else {
+    if (tid >= 136) return;
+    pair_of(tid, rb, cb);  // rb >= cb
+  }
+  const int r0 = rb * 4, c0 = cb * 4;
   AT acc[4][4];
 #pragma unroll
   for (int x = 0; x < 4; ++x)
@@ -384,7 +394,8 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
   AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
   AT* acc = y + max_nt * 64;                                                    // [64]
   AT* part = acc + 64;                                                          // [kConsumers][64]
-  int32_t* meta = reinterpret_cast<int32_t*>(part + kConsumers * 64);           // [2][3][max_nt]
+  AT* red = part + kConsumers * 64;                                             // [64][33] row partials
+  int32_t* meta = reinterpret_cast<int32_t*>(red + 64 * 33);                    // [2][3][max_nt]
   const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
   const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
   __shared__ int sflag;
@@ -479,12 +490,19 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         for (int k = 0; k < RW; ++k) sr[k] = fma(a1[k], y1, fma(a0[k], y0, sr[k]));
         release();
       }
+      // row sums: one thread per row adds the 32 lane partials (a shared-memory
+      // transpose costs far fewer FP64 instructions than warp shuffles)
 #pragma unroll
-      for (int k = 0; k < RW; ++k) {
-        AT v = sr[k];
+      for (int k = 0; k < RW; ++k) red[(warp * RW + k) * 33 + lane] = sr[k];
+      consumers_sync();
+      if (tid < 64) {
+        AT v0 = 0, v1 = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) acc[warp * RW + k] = y[I * 64 + warp * RW + k] - v;
+        for (int l = 0; l < 32; l += 2) {
+          v0 += red[tid * 33 + l];
+          v1 += red[tid * 33 + l + 1];
+        }
+        acc[tid] = y[I * 64 + tid] - (v0 + v1);
       }
       consumers_sync();
       {  // y_I = X acc, X[b][a] = tile[a][b] for a < b
@@ -549,12 +567,20 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         AT v = 0;
         if (lane > a) v = fma((AT)dt[a * 64 + lane], acc[lane], v);
         if (lane + 32 > a) v = fma((AT)dt[a * 64 + lane + 32], acc[lane + 32], v);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[I * 64 + a] = acc[a] + v;
+        red[a * 33 + lane] = v;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
+      consumers_sync();
+      if (tid < 64) {
+        AT v0 = 0, v1 = 0;
+#pragma unroll
+        for (int l = 0; l < 32; l += 2) {
+          v0 += red[tid * 33 + l];
+          v1 += red[tid * 33 + l + 1];
+        }
+        y[I * 64 + tid] = acc[tid] + (v0 + v1);
+      }
       consumers_sync();
     }
     for (int li = tid; li < np_; li += NC) {
@@ -640,7 +666,8 @@ DevLimits& limits() {
 template <typename T>
 int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
-  const size_t fixed = ((size_t)max_nt * 64 + 64 + kConsumers * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+  const size_t fixed = ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
+                       6 * (size_t)max_nt * 4;
   const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
   const size_t smem = (size_t)limits().smem;
   if (smem <= fixed) return 0;
@@ -661,7 +688,8 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
   }
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
-                      ((size_t)max_nt * 64 + 64 + kConsumers * 64) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+                      ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
+                      6 * (size_t)max_nt * 4;
   if (grid < 1) return;
   k_ras_solve<T><<<grid, 32 * (kConsumers + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
                                          ndir, t, z, add, max_nt, nslot, err);

@@ -123,7 +123,8 @@ struct DevLevel {
   int ras_grid = 0;               // CTAs of the RAS solve and their subdomain lists
   int32_t *ras_cta_ptr = nullptr, *ras_cta_list = nullptr;
   bool fac_blocks = false;        // whole-block persistent factorisation on this level
-  int32_t *fac_cta_ptr = nullptr; // one block per CTA, largest first
+  int fac_grid = 0;               // its CTAs and their block lists
+  int32_t *fac_cta_ptr = nullptr, *fac_cta_list = nullptr;
   double fac_flops = 0;           // all tile steps of the level
   // transfer from level+1
   int64_t P_nnz = 0;
@@ -203,6 +204,32 @@ void finish_level_stats(const HostLevel& H, DevLevel& D) {
   for (uint8_t o : H.sub_own) D.sum_owned += o;
 }
 
+// Longest-processing-time-first assignment of items (cost) to G bins: items
+// in descending cost, each to the least loaded bin; ptr/list in CSR form,
+// each bin's items in descending cost.
+void lpt_lists(const std::vector<int64_t>& cost, int G, std::vector<int32_t>& ptr,
+               std::vector<int32_t>& list) {
+  const int n = (int)cost.size();
+  std::vector<int32_t> ids(n);
+  for (int p = 0; p < n; ++p) ids[p] = p;
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int64_t> load(G, 0);
+  std::vector<std::vector<int32_t>> bins(G);
+  for (int p : ids) {
+    int best = 0;
+    for (int g = 1; g < G; ++g)
+      if (load[g] < load[best]) best = g;
+    load[best] += cost[p];
+    bins[best].push_back(p);
+  }
+  ptr.assign(G + 1, 0);
+  list.clear();
+  for (int g = 0; g < G; ++g) {
+    list.insert(list.end(), bins[g].begin(), bins[g].end());
+    ptr[g + 1] = (int32_t)list.size();
+  }
+}
+
 int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   HostLevel& H = h->host[l];
   DevLevel& D = h->dev[l];
@@ -245,41 +272,38 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.next = (int64_t)H.ext_pos.size();
   finish_level_stats(H, D);
   {
-    // longest-first assignment of subdomains to the persistent RAS CTAs, cost
-    // = stored envelope tiles (both sweeps read each once)
     int nsm = 0;
     MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int G = std::max(1, std::min(H.nsub, nsm));
-    std::vector<int32_t> ids(H.nsub);
+    // RAS solve: one persistent CTA per SM, cost = stored envelope tiles (both
+    // sweeps read each once)
     std::vector<int64_t> cost(H.nsub);
-    for (int p = 0; p < H.nsub; ++p) {
-      ids[p] = p;
-      cost[p] = (H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems;
-    }
-    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<int64_t> load(G, 0);
-    std::vector<std::vector<int32_t>> lists(G);
-    for (int p : ids) {
-      int best = 0;
-      for (int g = 1; g < G; ++g)
-        if (load[g] < load[best]) best = g;
-      load[best] += cost[p];
-      lists[best].push_back(p);
-    }
-    std::vector<int32_t> cptr(G + 1, 0), clist;
-    for (int g = 0; g < G; ++g) {
-      clist.insert(clist.end(), lists[g].begin(), lists[g].end());
-      cptr[g + 1] = (int32_t)clist.size();
-    }
-    D.ras_grid = G;
+    for (int p = 0; p < H.nsub; ++p) cost[p] = (H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems;
+    std::vector<int32_t> cptr, clist;
+    lpt_lists(cost, std::max(1, std::min(H.nsub, nsm)), cptr, clist);
+    D.ras_grid = (int)cptr.size() - 1;
     D.ras_cta_ptr = A.upload(cptr);
     D.ras_cta_list = A.upload(clist);
-    // many blocks: factor them with one persistent launch, one block per CTA in
-    // descending tile count (the hardware hands out CTAs in that order)
+    // factorisation: on levels with many blocks one persistent launch, as many
+    // CTAs as fit on the GPU at once, cost = tile operations of all steps
+    // (diagonal 1, panel 1, trailing pair 2, diagonal pair 1)
     D.fac_blocks = H.nsub >= std::max(2, nsm / 2);
-    std::vector<int32_t> iota(H.nsub + 1);
-    for (int p = 0; p <= H.nsub; ++p) iota[p] = p;
-    D.fac_cta_ptr = A.upload(iota);
+    if (D.fac_blocks) {
+      const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
+      const int per_sm = f32 ? ldlt_blocks_per_sm<float>() : ldlt_blocks_per_sm<double>();
+      for (int p = 0; p < H.nsub; ++p) {
+        const int32_t* R = &H.tile_last[H.sub_trow[p]];
+        int64_t c = 0;
+        for (int k = 0; k < H.sub_nt[p]; ++k) {
+          const int64_t rem = R[k] - k;
+          c += 1 + rem + rem * (rem - 1) + rem;
+        }
+        cost[p] = c;
+      }
+      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
+      D.fac_grid = (int)cptr.size() - 1;
+      D.fac_cta_ptr = A.upload(cptr);
+      D.fac_cta_list = A.upload(clist);
+    }
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   }
   {
@@ -364,7 +388,7 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
   }
   if (D.fac_blocks) {
     ProfScope ps(I->prof, PK_LDLT_BLOCKS, s);
-    launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.sub_order, D.nsub, I->info, s);
+    launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
     ps.account(0, D.fac_flops);
     return;
   }

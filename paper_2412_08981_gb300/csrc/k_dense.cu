@@ -59,34 +59,60 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 
 // ---------------------------------------------------- diagonal tile LDL^T
 // Factors one diagonal tile in shared memory, computing in the factor's
-// precision.  Column c: every row r > c subtracts (a_rc / d_c) a_sc from its
-// entries s in (c, r] (a_sc, the still unscaled column, is final since step
-// c-1), one barrier per column.  1/d_c is formed once, by the thread that
-// finishes the pivot d_c (the update of entry (c, c) at step c-1), so each
-// column costs a single division.  Then L = W D^{-1}, and the inverse
-// X = L^{-1} of the unit lower factor is built row by row (row i needs rows
-// < i only), four lanes per entry, one barrier per row, stored transposed in
-// the strict upper part.  smem: (64*65 + 64) elements of AT.
+// precision, blocked by 8 columns so that a tile costs ~34 block barriers:
+//   for each panel of 8 columns: warp 0 alone eliminates the 8 columns on the
+//   rows below (warp-synchronous; the entries of the panel hold W = L D while
+//   in progress), then all threads apply the rank-8 update
+//   A_rs -= sum_c W_rc W_sc / d_c to the trailing lower triangle;
+//   then L = W D^{-1}, and X = L^{-1} is formed by 8-row blocks:
+//   X_I = L_II^{-1} (E_I - sum_{K<I} L_IK X_K), stored transposed in the strict
+//   upper part of the tile.
+// smem: (64*65 + 64) elements of AT.
 template <typename T, typename AT>
 __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
   AT* dinv = A + 64 * 65;  // reciprocals of the pivots
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   __syncthreads();  // the shared buffer may still be read by a previous phase
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
-  if (tid == 0) dinv[0] = AT(1) / A[0];
-  __syncthreads();
-  const int row = tid >> 2, sub = tid & 3;
-  for (int c = 0; c < T64; ++c) {
-    if (row > c) {
-      const AT f = A[row * 65 + c] * dinv[c];
-      for (int s = c + 1 + sub; s <= row; s += 4) {
-        const AT v = A[row * 65 + s] - f * A[s * 65 + c];
-        A[row * 65 + s] = v;
-        if (s == c + 1 && row == c + 1) dinv[c + 1] = AT(1) / v;  // pivot c+1 is final
+  for (int c0 = 0; c0 < T64; c0 += 8) {
+    if (warp == 0) {  // panel: columns c0..c0+7, rows >= c0, two rows per lane
+      const int r0 = c0 + lane, r1 = c0 + lane + 32;
+      for (int c = c0; c < c0 + 8; ++c) {
+        const AT d = A[c * 65 + c];
+        const AT di = AT(1) / d;
+        if (lane == 0) dinv[c] = di;
+        // rows r > c: entries s in (c, c0+8), s <= r, lose W_rc W_sc / d_c
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = h ? r1 : r0;
+          if (r > c && r < T64) {
+            const AT f = A[r * 65 + c] * di;
+            for (int s2 = c + 1; s2 < c0 + 8 && s2 <= r; ++s2) A[r * 65 + s2] -= f * A[s2 * 65 + c];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // rank-8 update of the trailing lower triangle rows/cols >= c0+8
+    const int t0 = c0 + 8;
+    if (t0 < T64) {
+      const int m = T64 - t0;                 // trailing size
+      const int nent = m * (m + 1) / 2;       // lower triangle entries
+      for (int e = tid; e < nent; e += blockDim.x) {
+        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        while (rr * (rr + 1) / 2 > e) --rr;
+        const int r = t0 + rr, s2 = t0 + (e - rr * (rr + 1) / 2);
+        AT v = A[r * 65 + s2];
+#pragma unroll
+        for (int c = c0; c < c0 + 8; ++c) v -= A[r * 65 + c] * dinv[c] * A[s2 * 65 + c];
+        A[r * 65 + s2] = v;
       }
     }
     __syncthreads();
@@ -101,16 +127,30 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     else if (c > r) A[r * 65 + c] = AT(0);
   }
   __syncthreads();
-  // X[i][j] = -(L[i][j] + sum_{j<m<i} L[i][m] X[m][j]); X[m][j] lives at A[j][m]
-  const int jcol = tid >> 2, part = tid & 3;
-  for (int i = 1; i < T64; ++i) {
-    AT v = 0;
-    if (jcol < i) {
-      for (int m = jcol + 1 + part; m < i; m += 4) v = fma(A[i * 65 + m], A[jcol * 65 + m], v);
+  // X = L^{-1} by 8-row blocks; X[i][j] (j < i) lives at A[j][i].
+  for (int I = 0; I < 8; ++I) {
+    const int i0 = I * 8;
+    // T[i][j] = -(L[i][j] + sum_{j < m < i0} L[i][m] X[m][j]) for rows i in the
+    // block, columns j < i0 (one thread per entry)
+    for (int e = tid; e < 8 * i0; e += blockDim.x) {
+      const int i = i0 + e / i0, j = e % i0;
+      AT v = A[i * 65 + j];
+      for (int mm = j + 1; mm < i0; ++mm) v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
+      A[j * 65 + i] = -v;  // partial X[i][j], rows of the block not yet applied
     }
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    if (jcol < i && part == 0) A[jcol * 65 + i] = -(A[i * 65 + jcol] + v);
+    __syncthreads();
+    // apply the unit lower L_II^{-1} inside the block: rows i0..i0+7 in order,
+    // one thread per column j < i0 + 8 (columns of the diagonal block included)
+    if (tid < i0 + 8) {
+      const int j = tid;
+      for (int i = (j >= i0 ? j + 1 : i0); i < i0 + 8; ++i) {
+        // X[i][j] = T[i][j] - sum_{i0 <= m < i} L[i][m] X[m][j]  (j < i0), or for
+        // j in the block: X[i][j] = -(L[i][j] + sum_{j < m < i} L[i][m] X[m][j])
+        AT v = (j >= i0) ? -A[i * 65 + j] : A[j * 65 + i];
+        for (int mm = (j >= i0 ? j + 1 : i0); mm < i; ++mm) v -= A[i * 65 + mm] * A[j * 65 + mm];
+        A[j * 65 + i] = v;
+      }
+    }
     __syncthreads();
   }
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
@@ -171,15 +211,43 @@ __device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, A
   }
 }
 
+// Multi-launch form (levels with few, large blocks): every panel tile is
+// split into four CTAs of 16 rows each, so that a step spreads over more SMs.
+// Thread t owns row 16q + (t & 15) and the columns g, 31-g, 32+g, 63-g,
+// g = t >> 4 (column c needs the products over m <= c; this pairing gives
+// every lane nearly the same loop length).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
-  const int i = k + 1 + blockIdx.x;
+  const int i = k + 1 + (blockIdx.x >> 2), q = blockIdx.x & 3;
   if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
-  panel_tile<T, AT>(fac + tile_at(E, p, k, k), fac + tile_at(E, p, i, k), reinterpret_cast<AT*>(smraw));
+  AT* A = reinterpret_cast<AT*>(smraw);   // [16][65] rows of the panel tile
+  AT* Xt = A + 16 * 65;                   // [64][64] X^T (upper, unit diagonal)
+  AT* Dinv = Xt + 64 * 64;                // [64]
+  const T* dtile = fac + tile_at(E, p, k, k);
+  T* ptile = fac + tile_at(E, p, i, k) + q * 16 * 64;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TE; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    Xt[e] = (r < c) ? (AT)dtile[e] : (r == c ? AT(1) : AT(0));
+    if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
+    if (e < 16 * 64) A[r * 65 + c] = (AT)ptile[e];
+  }
+  __syncthreads();
+  const int r = tid & 15, g = tid >> 4;
+  const int cc[4] = {g, 31 - g, 32 + g, 63 - g};
+  AT w[4] = {0, 0, 0, 0};
+  for (int m = 0; m <= 63 - g; ++m) {
+    const AT a = A[r * 65 + m];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (m <= cc[u]) w[u] = fma(a, Xt[m * 64 + cc[u]], w[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) ptile[r * 64 + cc[u]] = (T)(w[u] * Dinv[cc[u]]);
 }
 
 // -------------------------------------------------------- trailing update
@@ -251,19 +319,54 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
     }
 }
 
+// Multi-launch form: every pair is split into four CTAs of 16 output rows;
+// thread t owns row 16q + (t >> 4) and the 4 columns 4 (t & 15) .. +3 (on a
+// diagonal pair only those on or below the diagonal).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
   const int rem = E.last[E.trow[p] + k] - k;
-  if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
+  const int pair = blockIdx.x >> 2, q = blockIdx.x & 3;
+  if (pair >= rem * (rem + 1) / 2) return;
   int a, b;
-  pair_of(blockIdx.x, a, b);
+  pair_of(pair, a, b);
   const int i = k + 1 + a, j = k + 1 + b;
+  const bool diagonal = (i == j);
   extern __shared__ unsigned char smraw[];
-  trail_pair<T, AT>(fac + tile_at(E, p, k, k), fac + tile_at(E, p, i, k), fac + tile_at(E, p, j, k),
-                    fac + tile_at(E, p, i, j), i == j, reinterpret_cast<AT*>(smraw));
+  constexpr int LD = 68;
+  AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][16] = L_ik[16q + r][m] * d_m
+  AT* Lt = Wt + 64 * 16;                  // [64 m][LD] = L_jk[c][m]
+  const T* dt = fac + tile_at(E, p, k, k);
+  const T* li = fac + tile_at(E, p, i, k) + q * 16 * 64;
+  const T* lj = fac + tile_at(E, p, j, k);
+  T* out = fac + tile_at(E, p, i, j) + q * 16 * 64;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TE; e += blockDim.x) {
+    const int r = e >> 6, m = e & 63;
+    Lt[m * LD + r] = (AT)lj[e];
+    if (e < 16 * 64) Wt[m * 16 + r] = (AT)li[e] * (AT)dt[m * 65];
+  }
+  __syncthreads();
+  const int r = tid >> 4, c0 = (tid & 15) * 4;
+  const int rg = 16 * q + r;  // row inside the tile
+  if (diagonal && c0 > rg) return;
+  AT acc[4] = {0, 0, 0, 0};
+#pragma unroll 8
+  for (int m = 0; m < T64; ++m) {
+    const AT av = Wt[m * 16 + r];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[y] = fma(av, Lt[m * LD + c0 + y], acc[y]);
+  }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int c = c0 + y;
+    if (!diagonal || c <= rg) {
+      T* o = out + r * 64 + c;
+      *o = (T)((AT)*o - acc[y]);
+    }
+  }
 }
 
 // ------------------------------------------------- whole-block factorisation
@@ -623,13 +726,13 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int max_rows, cudaStream_t s) {
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (64 * 65 + 64 * 64 + 64) * sizeof(AT);
+  size_t smem = (16 * 65 + 64 * 64 + 64) * sizeof(AT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ldlt_panel<T><<<dim3(max_rows, nactive), 256, smem, s>>>(fac, E, order, k);
+  k_ldlt_panel<T><<<dim3(4 * max_rows, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
 template <typename T>
@@ -637,13 +740,13 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int max_pairs, cudaStream_t s) {
   if (nactive <= 0 || max_pairs <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = 2 * 64 * 68 * sizeof(AT);
+  size_t smem = (64 * 16 + 64 * 68) * sizeof(AT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ldlt_trail<T><<<dim3(max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
+  k_ldlt_trail<T><<<dim3(4 * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
 namespace {

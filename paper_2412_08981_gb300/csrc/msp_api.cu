@@ -299,7 +299,9 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
         }
         cost[p] = c;
       }
-      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
+      // one CTA slot per SM stays free for the latency-bound factorisation
+      // chain of the coarsest block, which runs concurrently on its own stream
+      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * std::max(1, per_sm - 1))), cptr, clist);
       D.fac_grid = (int)cptr.size() - 1;
       D.fac_cta_ptr = A.upload(cptr);
       D.fac_cta_list = A.upload(clist);
@@ -418,13 +420,15 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
 int factor_all(msp_instance* I) {
   msp_hierarchy* h = I->h;
   MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
-  // level 0 on the instance stream, the coarser (independent) levels on two
-  // auxiliary streams forked from it and joined back
+  // The levels are independent: level 0 on the instance stream, the coarser
+  // ones on two auxiliary streams forked from it and joined back.  The
+  // coarsest block (a long chain of small dependent launches) goes first, on
+  // the high-priority stream.
   const int L = (int)h->dev.size();
   MSP_CUDA(cudaEventRecord(I->fork, I->stream));
   for (int a = 0; a < 2; ++a) MSP_CUDA(cudaStreamWaitEvent(I->aux[a], I->fork, 0));
-  for (int l = 0; l < L; ++l) {
-    cudaStream_t s = (l == 0) ? I->stream : I->aux[(l - 1) % 2];
+  for (int l = L - 1; l >= 0; --l) {
+    cudaStream_t s = (l == 0) ? I->stream : (l == L - 1 ? I->aux[0] : I->aux[1]);
     if (level_f32(h, l)) factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
     else factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
   }
@@ -730,8 +734,10 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     cudaGetLastError();
     return fail(MSP_ERR_OOM, "pinned host allocation failed");
   }
+  int prio_lo = 0, prio_hi = 0;
+  MSP_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
   for (int a = 0; a < 2; ++a) {
-    MSP_CUDA(cudaStreamCreateWithFlags(&I->aux[a], cudaStreamNonBlocking));
+    MSP_CUDA(cudaStreamCreateWithPriority(&I->aux[a], cudaStreamNonBlocking, a == 0 ? prio_hi : prio_lo));
     MSP_CUDA(cudaEventCreateWithFlags(&I->join[a], cudaEventDisableTiming));
   }
   MSP_CUDA(cudaEventCreateWithFlags(&I->fork, cudaEventDisableTiming));

@@ -299,9 +299,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
         }
         cost[p] = c;
       }
-      // one CTA slot per SM stays free for the latency-bound factorisation
-      // chain of the coarsest block, which runs concurrently on its own stream
-      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * std::max(1, per_sm - 1))), cptr, clist);
+      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
       D.fac_grid = (int)cptr.size() - 1;
       D.fac_cta_ptr = A.upload(cptr);
       D.fac_cta_list = A.upload(clist);

@@ -59,61 +59,40 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 
 // ---------------------------------------------------- diagonal tile LDL^T
 // Factors one diagonal tile in shared memory, computing in the factor's
-// precision, blocked by 8 columns so that a tile costs ~34 block barriers:
-//   for each panel of 8 columns: warp 0 alone eliminates the 8 columns on the
-//   rows below (warp-synchronous; the entries of the panel hold W = L D while
-//   in progress), then all threads apply the rank-8 update
-//   A_rs -= sum_c W_rc W_sc / d_c to the trailing lower triangle;
-//   then L = W D^{-1}, and X = L^{-1} is formed by 8-row blocks:
-//   X_I = L_II^{-1} (E_I - sum_{K<I} L_IK X_K), stored transposed in the strict
-//   upper part of the tile.
-// smem: (64*65 + 64) elements of AT.
+// precision.  Right-looking, column by column: the scaled column
+// l_r = W_rc / d_c is formed (64 threads), then the trailing lower triangle
+// entries (r, s), c < s <= r, are spread evenly over all threads (one FMA
+// each: A_rs -= l_r W_sc).  On GB300 FP64 issues one warp instruction per 16
+// SM cycles, so the work must fill every lane of every warp.  Then
+// L = W D^{-1}, and X = L^{-1} is formed by 8-row blocks
+// (X_I = L_II^{-1} (E_I - sum_{K<I} L_IK X_K)), stored transposed in the
+// strict upper part.  smem: (64*65 + 128) elements of AT.
 template <typename T, typename AT>
 __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
-  AT* dinv = A + 64 * 65;  // reciprocals of the pivots
+  AT* lcol = A + 64 * 65;  // [64] the scaled column of the current step
+  AT* dinv = lcol + 64;    // [64] 1/d_c, formed once each, by the thread finishing d_c
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
   __syncthreads();  // the shared buffer may still be read by a previous phase
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
-  for (int c0 = 0; c0 < T64; c0 += 8) {
-    if (warp == 0) {  // panel: columns c0..c0+7, rows >= c0, two rows per lane
-      const int r0 = c0 + lane, r1 = c0 + lane + 32;
-      for (int c = c0; c < c0 + 8; ++c) {
-        const AT d = A[c * 65 + c];
-        const AT di = AT(1) / d;
-        if (lane == 0) dinv[c] = di;
-        // rows r > c: entries s in (c, c0+8), s <= r, lose W_rc W_sc / d_c
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = h ? r1 : r0;
-          if (r > c && r < T64) {
-            const AT f = A[r * 65 + c] * di;
-            for (int s2 = c + 1; s2 < c0 + 8 && s2 <= r; ++s2) A[r * 65 + s2] -= f * A[s2 * 65 + c];
-          }
-        }
-        __syncwarp();
-      }
-    }
+  if (tid == 0) dinv[0] = AT(1) / A[0];
+  __syncthreads();
+  for (int c = 0; c < T64 - 1; ++c) {
+    if (tid > c && tid < T64) lcol[tid] = A[tid * 65 + c] * dinv[c];
     __syncthreads();
-    // rank-8 update of the trailing lower triangle rows/cols >= c0+8
-    const int t0 = c0 + 8;
-    if (t0 < T64) {
-      const int m = T64 - t0;                 // trailing size
-      const int nent = m * (m + 1) / 2;       // lower triangle entries
-      for (int e = tid; e < nent; e += blockDim.x) {
-        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-        while (rr * (rr + 1) / 2 > e) --rr;
-        const int r = t0 + rr, s2 = t0 + (e - rr * (rr + 1) / 2);
-        AT v = A[r * 65 + s2];
-#pragma unroll
-        for (int c = c0; c < c0 + 8; ++c) v -= A[r * 65 + c] * dinv[c] * A[s2 * 65 + c];
-        A[r * 65 + s2] = v;
-      }
+    const int m = T64 - 1 - c;            // trailing size
+    const int nent = m * (m + 1) / 2;
+    for (int e = tid; e < nent; e += blockDim.x) {
+      int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      rr += ((rr + 1) * (rr + 2) / 2 <= e);
+      rr -= (rr * (rr + 1) / 2 > e);
+      const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+      const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+      A[r * 65 + s2] = v;
+      if (e == 0) dinv[c + 1] = AT(1) / v;  // entry (c+1, c+1): the next pivot is final
     }
     __syncthreads();
   }
@@ -712,7 +691,7 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
                       int* info, cudaStream_t s) {
   if (nactive <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (64 * 65 + 64) * sizeof(AT);
+  size_t smem = (64 * 65 + 128) * sizeof(AT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

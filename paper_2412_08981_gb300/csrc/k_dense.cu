@@ -85,14 +85,34 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     __syncthreads();
     const int m = T64 - 1 - c;            // trailing size
     const int nent = m * (m + 1) / 2;
-    for (int e = tid; e < nent; e += blockDim.x) {
-      int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-      rr += ((rr + 1) * (rr + 2) / 2 <= e);
-      rr -= (rr * (rr + 1) / 2 > e);
-      const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-      const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
-      A[r * 65 + s2] = v;
-      if (e == 0) dinv[c + 1] = AT(1) / v;  // entry (c+1, c+1): the next pivot is final
+    // four entries per pass, all operands loaded before any store, so that the
+    // FMAs of a thread do not wait on each other through shared memory
+    for (int e0 = tid; e0 < nent; e0 += 4 * 256) {
+      int pos[4];
+      AT lv[4], wv[4], av[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * 256;
+        pos[u] = -1;
+        if (e < nent) {
+          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+          rr += ((rr + 1) * (rr + 2) / 2 <= e);
+          rr -= (rr * (rr + 1) / 2 > e);
+          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+          pos[u] = r * 65 + s2;
+          lv[u] = lcol[r];
+          wv[u] = A[s2 * 65 + c];
+          av[u] = A[pos[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (pos[u] >= 0) {
+          const AT v = fma(-lv[u], wv[u], av[u]);
+          A[pos[u]] = v;
+          if (e0 + u * 256 == 0) dinv[c + 1] = AT(1) / v;  // entry (c+1, c+1): next pivot final
+        }
+      }
     }
     __syncthreads();
   }
@@ -113,9 +133,16 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     // block, columns j < i0 (one thread per entry)
     for (int e = tid; e < 8 * i0; e += blockDim.x) {
       const int i = i0 + e / i0, j = e % i0;
-      AT v = A[i * 65 + j];
-      for (int mm = j + 1; mm < i0; ++mm) v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
-      A[j * 65 + i] = -v;  // partial X[i][j], rows of the block not yet applied
+      AT v0 = A[i * 65 + j], v1 = 0, v2 = 0, v3 = 0;  // four independent chains
+      int mm = j + 1;
+      for (; mm + 3 < i0; mm += 4) {
+        v0 = fma(A[i * 65 + mm], A[j * 65 + mm], v0);
+        v1 = fma(A[i * 65 + mm + 1], A[j * 65 + mm + 1], v1);
+        v2 = fma(A[i * 65 + mm + 2], A[j * 65 + mm + 2], v2);
+        v3 = fma(A[i * 65 + mm + 3], A[j * 65 + mm + 3], v3);
+      }
+      for (; mm < i0; ++mm) v0 = fma(A[i * 65 + mm], A[j * 65 + mm], v0);
+      A[j * 65 + i] = -((v0 + v1) + (v2 + v3));  // partial X[i][j], block rows not yet applied
     }
     __syncthreads();
     // apply the unit lower L_II^{-1} inside the block: rows i0..i0+7 in order,

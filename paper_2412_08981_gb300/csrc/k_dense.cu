@@ -34,6 +34,21 @@ constexpr int TE = T64 * T64;
 template <typename T> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = float; };
 
+// 1/d by Newton's method for the reciprocal (x <- x + x (1 - d x), which
+// doubles the correct bits per step) from a single-precision seed: two steps
+// take the seed's ~23 bits past double precision.  Shorter dependent chain
+// than a full-precision division on the pivot chain of the factorisation;
+// agrees with 1/d to within an ulp (checked in the GPU tests).  d must be a
+// normal number within the float range (pivots of SPD blocks are).
+__device__ inline double rcp_newton(double d) {
+  double x = (double)__frcp_rn((float)d);
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  return fma(x, e, x);
+}
+__device__ inline float rcp_newton(float d) { return 1.0f / d; }
+
 // element offset of tile (I, J), J >= F_I, of subdomain p
 __device__ inline int64_t tile_at(const EnvDev& E, int p, int I, int J) {
   const int rb = E.trow[p] + I;
@@ -78,41 +93,21 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
-  if (tid == 0) dinv[0] = AT(1) / A[0];
+  if (tid == 0) dinv[0] = rcp_newton(A[0]);
   __syncthreads();
   for (int c = 0; c < T64 - 1; ++c) {
     if (tid > c && tid < T64) lcol[tid] = A[tid * 65 + c] * dinv[c];
     __syncthreads();
     const int m = T64 - 1 - c;            // trailing size
     const int nent = m * (m + 1) / 2;
-    // four entries per pass, all operands loaded before any store, so that the
-    // FMAs of a thread do not wait on each other through shared memory
-    for (int e0 = tid; e0 < nent; e0 += 4 * 256) {
-      int pos[4];
-      AT lv[4], wv[4], av[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + u * 256;
-        pos[u] = -1;
-        if (e < nent) {
-          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-          rr += ((rr + 1) * (rr + 2) / 2 <= e);
-          rr -= (rr * (rr + 1) / 2 > e);
-          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-          pos[u] = r * 65 + s2;
-          lv[u] = lcol[r];
-          wv[u] = A[s2 * 65 + c];
-          av[u] = A[pos[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (pos[u] >= 0) {
-          const AT v = fma(-lv[u], wv[u], av[u]);
-          A[pos[u]] = v;
-          if (e0 + u * 256 == 0) dinv[c + 1] = AT(1) / v;  // entry (c+1, c+1): next pivot final
-        }
-      }
+    for (int e = tid; e < nent; e += blockDim.x) {
+      int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      rr += ((rr + 1) * (rr + 2) / 2 <= e);
+      rr -= (rr * (rr + 1) / 2 > e);
+      const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+      const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+      A[r * 65 + s2] = v;
+      if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
     }
     __syncthreads();
   }

@@ -160,6 +160,10 @@ WORKLOADS = {
     # profiling case of the same kernels: 64 subdomains of up to ~1700 DoFs
     "cube32_3lvl": dict(ns=(32, 16, 8), parts=((4, 4, 4), (4, 4, 4)), delta=2, nu=2,
                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
+    # mid-size profiling case (persistent factorisation path): 343 blocks of
+    # ~1300 DoFs, like the 64^3 case
+    "cube48_3lvl": dict(ns=(48, 24, 12), parts=((7, 7, 7), (7, 7, 7)), delta=2, nu=2,
+                        coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
     # three-level plain FP64, 64^3 -> 32^3 -> 16^3, 512 boxes per RAS level, overlap 2
     "cube64_3lvl": dict(ns=(64, 32, 16), parts=((8, 8, 8), (8, 8, 8)), delta=2, nu=2,
                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--batch", type=int, default=4,
+                    help="concurrent instances of the batched FP32-factor measurement")
     ap.add_argument("--cpu-sample", type=int, default=24,
                     help="fine subdomains factored/solved by the CPU baseline sample")
     return ap.parse_args()
@@ -270,6 +272,48 @@ def run_msp(args):
         h.close()
         return out
 
+    def measure_batched(precision, steps, warmup, B):
+        """B instances of the hierarchy solve different mu concurrently, each on
+        its own stream and host thread (the C calls release the GIL)."""
+        import threading
+        h = P.Hierarchy(levels, precision=precision, **kw)
+        streams = [torch.cuda.Stream() for _ in range(B)]
+        insts = [h.assemble(mu_of(0), stream=streams[b]) for b in range(B)]
+        n = levels[0].n_nodes
+        xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(B)]
+        lat, iters = [], []
+        lock = threading.Lock()
+
+        def worker(b, lo, hi, record):
+            for i in range(lo + b, hi, B):
+                t0 = time.perf_counter()
+                insts[b].reassemble(mu_of(i))
+                insts[b].factor()
+                st = insts[b].solve(xs[b], rtol=args.rtol)
+                dt = (time.perf_counter() - t0) * 1e3
+                if record:
+                    with lock:
+                        lat.append(dt)
+                        iters.append(st["iterations"])
+
+        def run(lo, hi, record):
+            th = [threading.Thread(target=worker, args=(b, lo, hi, record)) for b in range(B)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+
+        run(1000, 1000 + max(warmup, B), False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(0, steps, True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        for inst in insts:
+            inst.close()
+        h.close()
+        return dict(value=steps / wall, lat=lat, iters=iters, wall_s=wall)
+
     res = measure(args.precision, args.steps, args.warmup)
     ms = res["ms"]
     if world > 1:
@@ -295,6 +339,20 @@ def run_msp(args):
                  "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"],
                  "final_rel_residual_max": float(np.max(mres["relres"])),
                  "stage_ms_host": mres["stage_ms"], "kernel_ms_per_solve": mres["kernel_ms"]}
+        if args.batch > 1:
+            bres = measure_batched("f32", max(args.steps, 2 * args.batch), args.warmup, args.batch)
+            bval = bres["value"]
+            if world > 1:
+                t = torch.tensor([bres["wall_s"]], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                bval = max(args.steps, 2 * args.batch) * world / float(t.item())
+            mixed["batched"] = {
+                "instances": args.batch, "value": bval, "unit": UNIT,
+                "speedup_vs_f64": bval / value,
+                "latency_ms": {"p50": float(np.percentile(bres["lat"], 50)),
+                               "p99": float(np.percentile(bres["lat"], 99))},
+                "iterations_mean": float(np.mean(bres["iters"])),
+                "timing": "host wall clock over all instances, after a device synchronisation"}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "msp_kernels.h"
 
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
 
 // -------------------------------------------------------- trailing update
 // A_ij -= (L_ik D_k) L_jk^T for one pair k < j <= i; each thread accumulates a
-// 4x4 register block from k-major tiles.  smem: 2*64*68 AT.
+// 4x4 register block from k-major tiles.  smem: 2*64*65 AT.
 __device__ inline void pair_of(int t, int& a, int& b) {  // t -> (a, b), b <= a
   int x = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((x + 1) * (x + 2) / 2 <= t) ++x;
@@ -266,7 +267,7 @@ template <typename T, typename AT>
 __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
                            const T* __restrict__ lj, T* __restrict__ out, bool diagonal,
                            AT* __restrict__ smem) {
-  constexpr int LD = 68;
+  constexpr int LD = 65;  // odd stride: the transposed stores spread over the banks
   AT* Wt = smem;         // [64 m][LD] = L_ik[r][m] * d_m
   AT* Lt = Wt + 64 * LD; // [64 m][LD] = L_jk[c][m]
   const int tid = threadIdx.x;
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
   const int i = k + 1 + a, j = k + 1 + b;
   const bool diagonal = (i == j);
   extern __shared__ unsigned char smraw[];
-  constexpr int LD = 68;
+  constexpr int LD = 65;  // odd stride: the transposed stores spread over the banks
   AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][16] = L_ik[16q + r][m] * d_m
   AT* Lt = Wt + 64 * 16;                  // [64 m][LD] = L_jk[c][m]
   const T* dt = fac + tile_at(E, p, k, k);
@@ -714,11 +715,10 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
   if (nactive <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = (64 * 65 + 128) * sizeof(AT);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_ldlt_diag<T><<<nactive, 256, smem, s>>>(fac, E, order, k, info);
 }
 
@@ -728,11 +728,10 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = (16 * 65 + 64 * 64 + 64) * sizeof(AT);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_ldlt_panel<T><<<dim3(4 * max_rows, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
@@ -741,12 +740,11 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int max_pairs, cudaStream_t s) {
   if (nactive <= 0 || max_pairs <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (64 * 16 + 64 * 68) * sizeof(AT);
-  static bool attr = false;
-  if (!attr) {
+  size_t smem = (64 * 16 + 64 * 65) * sizeof(AT);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_ldlt_trail<T><<<dim3(4 * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
 }
 
@@ -755,14 +753,15 @@ struct DevLimits {
   int nsm = 0, smem = 0;
 };
 DevLimits& limits() {
-  static DevLimits L;
-  if (L.nsm == 0) {
+  static DevLimits L = [] {
+    DevLimits d;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&L.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    L.smem -= 1024;  // static shared memory and slack
-  }
+    cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    d.smem -= 1024;  // static shared memory and slack
+    return d;
+  }();
   return L;
 }
 }  // namespace
@@ -785,11 +784,10 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
                       int* err, cudaStream_t s) {
   using AT = typename Acc<T>::type;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limits().smem);
-    attr = true;
-  }
+  });
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
                       ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
@@ -804,19 +802,18 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
                         int grid, int* info, cudaStream_t s) {
   using AT = typename Acc<T>::type;
   if (grid < 1) return;
-  const size_t smem = (size_t)(2 * 64 * 68) * sizeof(AT);  // the largest phase (trailing pair)
-  static bool attr = false;
-  if (!attr) {
+  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_ldlt_blocks<T><<<grid, 256, smem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
 
 template <typename T>
 int ldlt_blocks_per_sm() {
   using AT = typename Acc<T>::type;
-  const size_t smem = (size_t)(2 * 64 * 68) * sizeof(AT) + 1024;
+  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT) + 1024;
   return (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(limits().smem + 1024) / smem));
 }
 

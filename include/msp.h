@@ -110,7 +110,8 @@ typedef struct msp_stats {
   int32_t status;             /* msp_status of the call */
   int32_t iterations;         /* FGMRES iterations (V-cycles) */
   double rel_residual;        /* ||b - A x|| / ||b||, true residual, FP64 */
-  double ms_assemble, ms_factor, ms_solve;  /* device time of each stage */
+  double ms_assemble, ms_factor, ms_solve;  /* host wall time of each stage */
+  double ms_queue, ms_total;  /* msp_poll only: time queued, and submit-to-done */
 } msp_stats;
 
 /* ---- set-up, once per hierarchy (Algorithm 2, lines "construct the hierarchy
@@ -173,6 +174,48 @@ MSP_API int msp_solve(msp_instance* inst, const double* b_dev, double* x_dev, do
  * n_nodes doubles; x_host: n_nodes doubles. */
 MSP_API int msp_solve_host(msp_instance* inst, const double* mu, int n_mu, const double* b_host,
                    double* x_host, double rtol, msp_stats* st);
+
+/* Device bytes one instance of `h` needs (CSR values, factors, level vectors,
+ * Krylov basis), for admission decisions. */
+MSP_API int msp_instance_bytes(const msp_hierarchy* h, size_t* bytes);
+
+/* ---- serving: continuous batching over resident hierarchies ----
+ * A server owns worker slots.  Each slot is one instance of one hierarchy
+ * with its own CUDA stream and host thread, running the whole per-parameter
+ * path (assemble, factor, FGMRES, copy back) for one request at a time.
+ * Slots are created on demand, up to slots_per_hierarchy per hierarchy, and
+ * only while the server's device-memory budget has room for another instance
+ * (admission by memory).  Requests that arrive while others are running go to
+ * any idle slot of their hierarchy at once, so their device work overlaps;
+ * otherwise they wait in a FIFO queue per hierarchy.  Every slot computes with
+ * fixed-order reductions, so a request's result does not depend on what else
+ * is running.  The caller keeps ownership of the hierarchies, which must
+ * outlive the server. */
+typedef struct msp_server msp_server;
+typedef struct msp_server_opts {
+  int32_t slots_per_hierarchy;  /* >= 1 */
+  size_t mem_budget_bytes;      /* device bytes for all slots' instances; 0 = unlimited */
+  double rtol_default;          /* used when msp_submit gets rtol <= 0 */
+} msp_server_opts;
+MSP_API void msp_server_default_options(msp_server_opts* o);
+MSP_API int msp_server_create(const msp_server_opts* o, msp_server** out);
+/* Registers a device-resident hierarchy; *id receives its handle (0, 1, ...). */
+MSP_API int msp_server_add_hierarchy(msp_server* srv, msp_hierarchy* h, int* id);
+/* Queues one solve of hierarchy `hierarchy_id` for parameter mu (host array,
+ * copied) to relative residual rtol with the hierarchy's load vector as
+ * right-hand side.  *req_id receives the request handle.  MSP_ERR_INVALID for
+ * a bad id or mu; MSP_ERR_OOM if the budget cannot hold even one instance of
+ * the hierarchy. */
+MSP_API int msp_submit(msp_server* srv, int hierarchy_id, const double* mu, int n_mu, double rtol,
+                       uint64_t* req_id);
+/* Waits up to timeout_ms (0: no wait, < 0: no limit) for a request.
+ * Returns MSP_PENDING if it has not finished (the request stays queued);
+ * otherwise the request's own status, copies the solution (n_nodes of level
+ * 0) into x_host when non-NULL, fills *st (ms_queue / ms_total included) and
+ * forgets the request.  MSP_ERR_INVALID for an unknown req_id. */
+MSP_API int msp_poll(msp_server* srv, uint64_t req_id, double* x_host, msp_stats* st, int timeout_ms);
+/* Stops the workers after their current request, frees every slot. */
+MSP_API void msp_server_free(msp_server* srv);
 
 /* ---- single operators of the path, for parity checks and composition ----
  * y = op(x) on level `level`, device arrays, enqueued on `stream`:

@@ -5,6 +5,6 @@ package holds its sources (csrc/), its in-tree build (build.py) and a thin
 ctypes binding with the C names (msp.py).
 """
 from . import msp  # noqa: F401
-from .msp import Hierarchy, Instance, MspError, load  # noqa: F401
+from .msp import Hierarchy, Instance, MspError, Server, load  # noqa: F401
 
-__all__ = ["msp", "Hierarchy", "Instance", "MspError", "load"]
+__all__ = ["msp", "Hierarchy", "Instance", "MspError", "Server", "load"]

@@ -763,6 +763,17 @@ int set_mu(msp_instance* I, const double* mu, int n_mu) {
   return MSP_OK;
 }
 
+size_t instance_need(const msp_hierarchy* h) {
+  size_t need = 0;
+  for (size_t l = 0; l < h->dev.size(); ++l) {
+    const DevLevel& D = h->dev[l];
+    need += (size_t)D.m * 8 + (size_t)D.nnz * 8 + (size_t)D.n * 24 +
+            (size_t)D.fac_elems * (level_f32(h, (int)l) ? 4 : 8);
+  }
+  need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
+  return need;
+}
+
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double ms() const {
@@ -842,6 +853,13 @@ void msp_free_hierarchy(msp_hierarchy* h) {
   delete h;
 }
 
+int msp_instance_bytes(const msp_hierarchy* h, size_t* bytes) {
+  if (!h || !bytes) return fail(MSP_ERR_INVALID, "NULL argument");
+  if (h->host_only) return fail(MSP_ERR_INVALID, "host-only hierarchy");
+  *bytes = instance_need(h);
+  return MSP_OK;
+}
+
 int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) {
   if (!h || !info || level < 0 || level >= (int)h->host.size())
     return fail(MSP_ERR_INVALID, "bad hierarchy, level or info pointer");
@@ -865,13 +883,7 @@ int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream, msp
   I->h = h;
   I->stream = static_cast<cudaStream_t>(stream);
   // budget check before allocating
-  size_t need = 0;
-  for (size_t l = 0; l < h->dev.size(); ++l) {
-    const DevLevel& D = h->dev[l];
-    need += (size_t)D.m * 8 + (size_t)D.nnz * 8 + (size_t)D.n * 24 +
-            (size_t)D.fac_elems * (level_f32(h, (int)l) ? 4 : 8);
-  }
-  need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
+  const size_t need = instance_need(h);
   {
     std::lock_guard<std::mutex> lk(h->mu);
     if (h->opt.mem_budget_bytes && h->arena.bytes + h->instance_bytes + need > h->opt.mem_budget_bytes)

@@ -67,7 +67,13 @@ class msp_options(C.Structure):
 
 class msp_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
-                ("ms_assemble", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double)]
+                ("ms_assemble", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("ms_queue", C.c_double), ("ms_total", C.c_double)]
+
+
+class msp_server_opts(C.Structure):
+    _fields_ = [("slots_per_hierarchy", C.c_int32), ("mem_budget_bytes", C.c_size_t),
+                ("rtol_default", C.c_double)]
 
 
 class msp_level_info(C.Structure):
@@ -110,6 +116,14 @@ EXPORTS = {
     "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
     "msp_multidot_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                        C.c_void_p, C.c_void_p]),
+    "msp_instance_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "msp_server_default_options": (None, [C.POINTER(msp_server_opts)]),
+    "msp_server_create": (C.c_int, [C.POINTER(msp_server_opts), C.POINTER(C.c_void_p)]),
+    "msp_server_add_hierarchy": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "msp_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                             C.POINTER(C.c_uint64)]),
+    "msp_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(msp_stats), C.c_int]),
+    "msp_server_free": (None, [C.c_void_p]),
 }
 MSP_NOALLOC_MAX_VECTORS = 64
 
@@ -263,6 +277,11 @@ class Hierarchy:
     def assemble(self, mu=None, stream=None) -> "Instance":
         return Instance(self, mu, stream)
 
+    def instance_bytes(self) -> int:
+        b = C.c_size_t(0)
+        _check(load().msp_instance_bytes(self.h, C.byref(b)))
+        return int(b.value)
+
 
 class Instance:
     """msp_assemble ... msp_free_instance for one parameter vector."""
@@ -339,6 +358,50 @@ class Instance:
             _check(load().msp_profile_read(self.inst, i, C.byref(p)))
             out[name] = {k: getattr(p, k) for k, _ in msp_kernel_profile._fields_}
         return out
+
+
+class Server:
+    """msp_server_*: continuous batching of solves over resident hierarchies."""
+
+    def __init__(self, slots_per_hierarchy=4, budget_bytes=0, rtol_default=1e-8):
+        o = msp_server_opts()
+        load().msp_server_default_options(C.byref(o))
+        o.slots_per_hierarchy = int(slots_per_hierarchy)
+        o.mem_budget_bytes = int(budget_bytes)
+        o.rtol_default = float(rtol_default)
+        srv = C.c_void_p()
+        _check(load().msp_server_create(C.byref(o), C.byref(srv)))
+        self.srv = srv
+        self._hier = []
+
+    def add(self, h: Hierarchy) -> int:
+        i = C.c_int(0)
+        _check(load().msp_server_add_hierarchy(self.srv, h.h, C.byref(i)))
+        self._hier.append(h)
+        return int(i.value)
+
+    def submit(self, hid, mu, rtol=0.0) -> int:
+        mu = np.ascontiguousarray(mu, np.float64)
+        rid = C.c_uint64(0)
+        _check(load().msp_submit(self.srv, int(hid), _ptr(mu), int(mu.size), float(rtol),
+                                 C.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, rid, x_host=None, timeout_ms=-1):
+        """Returns (status, stats dict); status MSP_PENDING if not finished."""
+        st = msp_stats()
+        rc = load().msp_poll(self.srv, C.c_uint64(rid), _ptr(x_host), C.byref(st), int(timeout_ms))
+        if rc == MSP_ERR_INVALID:
+            _check(rc)
+        return rc, {k: getattr(st, k) for k, _ in msp_stats._fields_}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            load().msp_server_free(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        self.close()
 
 
 def multidot_noalloc(V, w, out, nv=None, ld=None, n=None, stream=None):

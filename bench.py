@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--batch", type=int, default=4,
                     help="concurrent instances of the batched FP32-factor measurement")
+    ap.add_argument("--serve", type=int, default=48,
+                    help="requests of the serving trace (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrivals per second")
     ap.add_argument("--cpu-sample", type=int, default=24,
                     help="fine subdomains factored/solved by the CPU baseline sample")
     return ap.parse_args()
@@ -314,6 +317,63 @@ def run_msp(args):
         h.close()
         return dict(value=steps / wall, lat=lat, iters=iters, wall_s=wall)
 
+    def measure_serving(nreq, rate):
+        """Poisson arrivals of seeded mu over two resident hierarchies (32^3 and
+        64^3, FP32 subdomain factors), served by msp_submit/msp_poll."""
+        import threading
+        names, probs = ("cube32_3lvl", "cube64_3lvl"), (0.6, 0.4)
+        srv = P.Server(slots_per_hierarchy=4, budget_bytes=120 << 30)
+        hs, ids = [], []
+        for nm in names:
+            lv, ww = syn.workload(nm)
+            kk = dict(delta=ww["delta"], nu_pre=ww["nu"], nu_post=ww["nu"], restart=ww["restart"],
+                      coef=ww["coef"], wave=syn.wave_vectors(), scale=ww["scale"], load=ww["load"])
+            h = P.Hierarchy(lv, precision="f32", **kk)
+            hs.append(h)
+            ids.append(srv.add(h))
+        rng = np.random.default_rng(99)
+        gaps = rng.exponential(1.0 / rate, size=nreq)
+        which = rng.choice(len(names), size=nreq, p=probs)
+        # warm every slot's instance first (not timed)
+        warm = [srv.submit(ids[k], mu_of(900 + k)) for k in range(len(names)) for _ in range(4)]
+        for r in warm:
+            srv.poll(r, None, -1)
+        rids = [None] * nreq
+        t0 = time.perf_counter()
+
+        def submitter():
+            t = t0
+            for i in range(nreq):
+                t += gaps[i]
+                dt = t - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                rids[i] = srv.submit(ids[which[i]], mu_of(5000 + i), rtol=args.rtol)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, iters = [], []
+        for i in range(nreq):
+            while rids[i] is None:
+                time.sleep(0.0005)
+            rc, st = srv.poll(rids[i], None, -1)
+            lat.append(st["ms_total"])
+            iters.append(st["iterations"])
+        th.join()
+        wall = time.perf_counter() - t0
+        srv.close()
+        for h in hs:
+            h.close()
+        return {"requests": nreq, "arrival_rate_per_s": rate,
+                "hierarchies": {nm: int((which == k).sum()) for k, nm in enumerate(names)},
+                "factor_precision": "f32 (FP64 outer loop, SpMV, transfers, coarsest level)",
+                "slots_per_hierarchy": 4, "mem_budget_bytes": 120 << 30,
+                "value": nreq / wall, "unit": UNIT,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p99": float(np.percentile(lat, 99))},
+                "iterations_mean": float(np.mean(iters)),
+                "timing": "host wall clock from the first arrival to the last completion"}
+
     res = measure(args.precision, args.steps, args.warmup)
     ms = res["ms"]
     if world > 1:
@@ -353,6 +413,9 @@ def run_msp(args):
                                "p99": float(np.percentile(bres["lat"], 99))},
                 "iterations_mean": float(np.mean(bres["iters"])),
                 "timing": "host wall clock over all instances, after a device synchronisation"}
+    serving = None
+    if args.serve > 0 and world == 1:
+        serving = measure_serving(args.serve, args.serve_rate)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -394,6 +457,8 @@ def run_msp(args):
     }
     if mixed:
         line["mixed"] = mixed
+    if serving:
+        line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:
         levels_, w_ = syn.workload(args.workload)
         line["cpu_baseline"] = cpu_baseline(levels_, w_, mu_of(0),

@@ -18,6 +18,7 @@
 // On GB300 FP64 runs on the SIMT pipe at ~1/64 of the FP32 rate (there is no
 // fast FP64 tensor path), so the FP64 kernels are ALU-bound: their design
 // keeps the FMA pipe fed from shared memory and avoids idle lanes.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -698,6 +699,119 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
   }
 }
 
+// ------------------------------------------- single-block solve on a cluster
+// The coarsest level is one block (one CTA would use one SM's FP64 pipe), so
+// its sweeps run on a cluster of kCl CTAs.  Every CTA keeps the whole
+// right-hand side / solution vector in its shared memory.  Forward, tile row
+// I: CTA c owns rows 8c..8c+7; it sums its rows of the off-diagonal tiles,
+// sends its 8 results to every CTA (distributed shared memory), the cluster
+// synchronises, each CTA applies its rows of X_II, sends them, synchronises.
+// Backward, tile row I: CTA c owns the columns 8c..8c+7 of L_JI^T x_J and the
+// rows 8c..8c+7 of X_II^T, with the same two exchanges.
+constexpr int kCl = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_solve_cluster(
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const int32_t* __restrict__ dir_list, int ndir,
+    const double* __restrict__ t, double* __restrict__ z, int add) {
+  using AT = typename Acc<T>::type;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int me = (int)cl.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p = 0;
+  const int NT = E.nt[p], rb = E.trow[p];
+  const int off = sub_ptr[p], np_ = sub_ptr[p + 1] - off;
+  extern __shared__ unsigned char smraw[];
+  AT* y = reinterpret_cast<AT*>(smraw);  // [NT*64] the whole vector, in every CTA
+  AT* acc = y + NT * 64;                 // [64] exchanged partial results
+  AT* red = acc + 64;                    // [8][32] backward column partials
+  const T* base = fac + E.fac_off[p];
+  for (int d = me * 256 + tid; d < ndir; d += kCl * 256) {
+    const int g = dir_list[d];
+    z[g] = add ? z[g] + t[g] : t[g];
+  }
+  for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+  cl.sync();
+  const int r8 = 8 * me;  // this CTA's 8 rows (columns)
+  // sends v (this CTA's row/column r8 + k) to every CTA's array `dst`
+  auto send8 = [&](AT* dst, int k, AT v) {
+    for (int c = 0; c < kCl; ++c) cl.map_shared_rank(dst, c)[r8 + k] = v;
+  };
+  // ---- forward
+  for (int I = 0; I < NT; ++I) {
+    const int F = E.first[rb + I];
+    const T* rowt = base + (int64_t)E.toff[rb + I] * TE;
+    {  // warp w: row r8 + w of the off-diagonal tiles
+      const int r = r8 + warp;
+      AT s0 = 0, s1 = 0;
+      for (int J = F; J < I; ++J) {
+        const T* tl = rowt + (int64_t)(J - F) * TE;
+        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
+        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+      }
+      AT v = s0 + s1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(acc, lane)[r] = y[I * 64 + r] - v;
+    }
+    cl.sync();
+    {  // warp w: y_I[b], b = r8 + w: acc[b] + sum_{a<b} X[b][a] acc[a], X[b][a] = dt[a][b]
+      const T* dt = rowt + (int64_t)(I - F) * TE;
+      const int b = r8 + warp;
+      AT v = 0;
+      if (lane < b) v = fma((AT)dt[lane * 64 + b], acc[lane], v);
+      if (lane + 32 < b) v = fma((AT)dt[(lane + 32) * 64 + b], acc[lane + 32], v);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + b] = acc[b] + v;
+    }
+    cl.sync();
+  }
+  // ---- backward
+  for (int I = NT - 1; I >= 0; --I) {
+    const int R = E.last[rb + I];
+    const T* dt = base + (int64_t)(E.toff[rb + I] + (I - E.first[rb + I])) * TE;
+    {  // column col = r8 + (tid & 7); rows split over 32 groups of 2
+      const int col = r8 + (tid & 7), rg = tid >> 3;
+      AT v = 0;
+      for (int J = I + 1; J <= R; ++J) {
+        const T* tl = base + (int64_t)(E.toff[rb + J] + (I - E.first[rb + J])) * TE;
+        v = fma((AT)tl[(2 * rg) * 64 + col], y[J * 64 + 2 * rg], v);
+        v = fma((AT)tl[(2 * rg + 1) * 64 + col], y[J * 64 + 2 * rg + 1], v);
+      }
+      // the 4 row groups inside a warp share a column: lanes l, l^8, l^16, l^24
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      if (lane < 8) red[warp * 8 + lane] = v;
+      __syncthreads();
+      if (tid < 8) {
+        AT sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += red[w * 8 + tid];
+        const int c = r8 + tid;
+        send8(acc, tid, y[I * 64 + c] / (AT)dt[c * 65] - sum);
+      }
+    }
+    cl.sync();
+    {  // warp w: x_I[a], a = r8 + w: acc[a] + sum_{b>a} dt[a][b] acc[b]
+      const int a2 = r8 + warp;
+      AT v = 0;
+      if (lane > a2) v = fma((AT)dt[a2 * 64 + lane], acc[lane], v);
+      if (lane + 32 > a2) v = fma((AT)dt[a2 * 64 + lane + 32], acc[lane + 32], v);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + a2] = acc[a2] + v;
+    }
+    cl.sync();
+  }
+  for (int li = me * 256 + tid; li < np_; li += kCl * 256) {
+    const int g = dofs[off + li];
+    z[g] = add ? z[g] + (double)y[li] : (double)y[li];
+  }
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -817,6 +931,32 @@ int ldlt_blocks_per_sm() {
   return (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(limits().smem + 1024) / smem));
 }
 
+template <typename T>
+void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
+                                const int32_t* dofs, int max_nt, const int32_t* dir_list,
+                                int ndir, const double* t, double* z, int add, cudaStream_t s) {
+  using AT = typename Acc<T>::type;
+  const size_t smem = ((size_t)max_nt * 64 + 64 + 64) * sizeof(AT);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_block_solve_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         limits().smem);
+  });
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCl, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr1[1];
+  attr1[0].id = cudaLaunchAttributeClusterDimension;
+  attr1[0].val.clusterDim.x = kCl;
+  attr1[0].val.clusterDim.y = 1;
+  attr1[0].val.clusterDim.z = 1;
+  cfg.attrs = attr1;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_block_solve_cluster<T>, fac, E, sub_ptr, dofs, dir_list, ndir, t, z, add);
+}
+
 #define MSP_INST(T)                                                                              \
   template void launch_extract<T>(const int64_t*, const int32_t*, int64_t, const double*,        \
                                   int64_t, T*, cudaStream_t);                                    \
@@ -833,7 +973,10 @@ int ldlt_blocks_per_sm() {
   template int ras_slots<T>(int);                                                                \
   template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
                                       int*, cudaStream_t);                                       \
-  template int ldlt_blocks_per_sm<T>();
+  template int ldlt_blocks_per_sm<T>();                                                           \
+  template void launch_block_solve_cluster<T>(const T*, const EnvDev&, const int32_t*,            \
+                                              const int32_t*, int, const int32_t*, int,           \
+                                              const double*, double*, int, cudaStream_t);
 MSP_INST(double)
 MSP_INST(float)
 

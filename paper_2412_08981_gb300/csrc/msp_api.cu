@@ -311,7 +311,11 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
     // the backward sweep holds a row's diagonal tile while the next R_I - I
     // tiles stream in: max_band slots are enough, and never deadlock
-    if (slots < D.max_band || slots < 2)
+    const bool coarsest = l + 1 == (int)h->host.size();
+    if (coarsest && ((size_t)D.max_nt * 64 + 128) * sizeof(double) > 220u * 1024u)
+      return fail(MSP_ERR_INVALID, "coarsest level too large for the cluster block solve (" +
+                                       std::to_string(D.max_nt) + " tiles)");
+    if (!coarsest && (slots < D.max_band || slots < 2))
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large or " +
                                        "too wide for the staged triangular solve (" +
                                        std::to_string(D.max_nt) + " tiles, band " +
@@ -451,7 +455,10 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   int kind = coarse ? PK_COARSE : (l == 0 ? PK_RAS : PK_RAS_COARSER);
   ProfScope ps(I->prof, kind, s);
   size_t es = level_f32(h, l) ? 4 : 8;
-  if (level_f32(h, l))
+  if (coarse) {  // one block: both sweeps split over a cluster of CTAs
+    launch_block_solve_cluster<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr,
+                                       D.sub_dofs, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+  } else if (level_f32(h, l))
     launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
                             D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
                             D.dir_list, D.ndir, t, z, add, I->ras_err, s);

@@ -61,6 +61,14 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
                         int grid, int* info, cudaStream_t s);
 template <typename T>
 int ldlt_blocks_per_sm();
+// y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level),
+// on a cluster of 8 CTAs that split every tile row of both sweeps and
+// exchange partial results through distributed shared memory; Dirichlet
+// nodes get t.  Written (add = 0) or added (add = 1) to z.
+template <typename T>
+void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
+                                const int32_t* dofs, int max_nt, const int32_t* dir_list,
+                                int ndir, const double* t, double* z, int add, cudaStream_t s);
 // z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
 // entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
 // CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a

@@ -924,11 +924,22 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
   k_ldlt_blocks<T><<<grid, 256, smem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
 
+// CTAs of k_ldlt_blocks resident per SM at once (shared memory and registers
+// both counted), so that the persistent grid is exactly one wave.
 template <typename T>
 int ldlt_blocks_per_sm() {
   using AT = typename Acc<T>::type;
-  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT) + 1024;
-  return (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(limits().smem + 1024) / smem));
+  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_ldlt_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ldlt_blocks<T>, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return std::max(1, std::min(8, n));
 }
 
 template <typename T>

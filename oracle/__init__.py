@@ -17,11 +17,17 @@ Parity status per function (what pins it, tests/test_oracle_pins.py):
   RAS                one subdomain (or full overlap) gives A^{-1} exactly;
                      dense numpy formula sum R0^T (R A R^T)^{-1} R
   interpolation P    affine reproduction, unit row sums, identity on equal meshes
+  MLS transfer       every row against a brute-force weighted least-squares fit
+                     (numpy BFS neighbourhood, SVD rank, monomial basis, pinv);
+                     affine reproduction; Dirichlet handling; nodal-volume
+                     scaling (tests/test_oracle_mls_pins.py)
   V-cycle            dense numpy composition of the same operators on tiny meshes
   FGMRES             Krylov least-squares optimality (M = I), direct solve
 Iteration counts of the preconditioned solver: parity unpinned (the paper
 reports counts only for other PDEs and meshes).
 """
-from .oracle import Oracle, build, lib, tet_stiffness, lu_factor, lu_solve, build_interp
+from .oracle import (Oracle, build, lib, tet_stiffness, lu_factor, lu_solve, build_interp,
+                     build_mls, mesh_h)
 
-__all__ = ["Oracle", "build", "lib", "tet_stiffness", "lu_factor", "lu_solve", "build_interp"]
+__all__ = ["Oracle", "build", "lib", "tet_stiffness", "lu_factor", "lu_solve", "build_interp",
+           "build_mls", "mesh_h"]

@@ -13,9 +13,11 @@
 //   * right-preconditioned (flexible) GMRES (Section 2.1, Eq. 5; Section 4).
 // Readings where the paper is silent (shared with the library by specification,
 // not by code):
-//   * fine->coarse transfer is P^T and coarse->fine is P, P the P1 barycentric
-//     interpolation of coarse fields at fine nodes (replaces the MLS operator of
-//     Eq. 24); the coarsest level is solved directly, not smoothed;
+//   * the transfers are either P (coarse->fine) and P^T (fine->coarse), P the
+//     P1 barycentric interpolation of coarse fields at fine nodes, or the
+//     overlapping MLS operators of Section 3.2 (Eq. 13-15, 24) in both
+//     directions, with the readings stated at build_mls below; the coarsest
+//     level is solved directly, not smoothed;
 //   * the smoothing loops of Algorithm 2 run exactly `its` times;
 //   * subdomain solvers are unpivoted LU of each (SPD) subdomain block;
 //   * Dirichlet rows are identity rows, Dirichlet columns are zeroed;
@@ -54,7 +56,7 @@ struct Level {
   std::vector<Subdomain> subs;
   Subdomain coarse;       // used on the coarsest level: all interior DoFs
   Csr P;                  // interpolation from level+1 (coarse) to this level
-  Csr PT;                 // its transpose
+  Csr PT;                 // restriction to level+1: P^T, or the MLS operator
 };
 
 struct Oracle {
@@ -64,6 +66,8 @@ struct Oracle {
   int wave[24] = {0};
   double coef_scale = 1.0;
   int load_kind = 0;  // 0: f = 1; 1: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+  int transfer = 0;   // 0: P / P^T; 1: MLS both ways (Section 3.2)
+  int restrict_scaling = 1;  // MLS restriction: 1 nodal-volume scaled, 0 plain
   std::vector<double> mu;
   std::string err;
 };
@@ -425,6 +429,164 @@ void transpose(const Csr& P, int ncols, Csr& T) {
     }
 }
 
+// ------------------------------------- MLS transfer (Section 3.2, Eq. 13-15, 24)
+// Overlapping moving-least-squares interpolation from a source mesh S to the
+// nodes of a target mesh T.  For a target node x* with partition id q:
+//   N(x*) = the source vertices of Omega^delta_q (the S-vertices owned by q,
+//           Dirichlet ones included, grown by delta element layers as in
+//           Section 2.2) at distance < rho from x*;
+//   w     = 1 - 6 s^2 + 8 s^3 - 3 s^4, s = |x - x*| / rho        (Eq. 15);
+//   P1    = sum_n w_n p(x_n) p(x_n)^T,  P2[:, n] = w_n p(x_n)   (Theorem 3.2);
+//   row   = p(x*)^T P1^{-1} P2                                   (Eq. 24).
+// Readings of what the paper leaves open:
+//   * the polynomial space is linear, written in the basis
+//     p(x) = [1, (x - x*)/rho] (p(x*) = e_1); the fitted value is the same in
+//     every basis of the space;
+//   * rho = c h, h = cbrt(6 |bounding box| / tets) of the coarser mesh of the
+//     pair, c = 1.5 and then multiplied by 1.5 until rank(P) = 4, tested as:
+//     at least 4 neighbours and every pivot of the unpivoted elimination of
+//     P1 above 1e-9 P1[0][0];
+//   * subdomain q of S is subdomain q of T when both meshes are partitioned
+//     over the same set of ids (the paper keeps np subdomains on every level);
+//     when either mesh has no partition (the coarsest level) or the id sets
+//     differ, N(x*) is taken from all of S;
+//   * Dirichlet source vertices take part in the fit; with drop_dirichlet
+//     their columns are left out (the vectors transferred vanish there) and
+//     Dirichlet target nodes get empty rows;
+//   * with `scale` the row is multiplied by |w_t| / |w_n| (nodal volumes
+//     |w_i| = sum of |T|/4 over the tets at i): the fine->coarse transfer of a
+//     residual, whose entries are integrals, goes through the densities
+//     r_i / |w_i| so that its scale matches the coarse operator.
+double mls_weight(double s) { return 1.0 - 6.0 * s * s + 8.0 * s * s * s - 3.0 * s * s * s * s; }
+
+double mesh_h(const Level& C) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < C.n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], C.xyz[3 * i + d]);
+      hi[d] = std::max(hi[d], C.xyz[3 * i + d]);
+    }
+  double vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  return std::cbrt(6.0 * vol / C.m);
+}
+
+std::vector<double> nodal_volumes(const Level& L) {
+  std::vector<double> v(L.n, 0.0);
+  for (int e = 0; e < L.m; ++e) {
+    const int* t = &L.tets[4 * e];
+    double g[4][3];
+    double det = tet_gradients(&L.xyz[3 * t[0]], &L.xyz[3 * t[1]], &L.xyz[3 * t[2]], &L.xyz[3 * t[3]], g);
+    double vol = std::fabs(det) / 6.0;
+    for (int a = 0; a < 4; ++a) v[t[a]] += vol / 4.0;
+  }
+  return v;
+}
+
+// Omega^delta_q on S, ascending vertex ids.
+std::vector<int> overlap_vertices(const Level& S, int q, int delta) {
+  std::vector<unsigned char> in(S.n, 0);
+  for (int i = 0; i < S.n; ++i)
+    if (S.owner[i] == q) in[i] = 1;
+  for (int layer = 0; layer < delta; ++layer) {
+    std::vector<unsigned char> nxt = in;
+    for (int i = 0; i < S.n; ++i)
+      if (in[i])
+        for (int p = S.A.rowptr[i]; p < S.A.rowptr[i + 1]; ++p) nxt[S.A.col[p]] = 1;
+    in.swap(nxt);
+  }
+  std::vector<int> v;
+  for (int i = 0; i < S.n; ++i)
+    if (in[i]) v.push_back(i);
+  return v;
+}
+
+// One row of Eq. 24 at x* over the candidates (ascending ids); false when
+// rank(P) < 4 for this rho.
+bool mls_row(const double* xs, const std::vector<double>& sxyz, const std::vector<int>& cand,
+             double rho, std::vector<std::pair<int, double>>& row) {
+  std::vector<int> nb;
+  std::vector<double> w, p;
+  for (int n : cand) {
+    double d0 = sxyz[3 * n] - xs[0], d1 = sxyz[3 * n + 1] - xs[1], d2 = sxyz[3 * n + 2] - xs[2];
+    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    if (!(r2 < rho * rho)) continue;
+    nb.push_back(n);
+    w.push_back(mls_weight(std::sqrt(r2) / rho));
+    p.insert(p.end(), {1.0, d0 / rho, d1 / rho, d2 / rho});
+  }
+  const int N = (int)nb.size();
+  if (N < 4) return false;
+  double P1[16] = {0};
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) P1[4 * i + j] += w[k] * p[4 * k + i] * p[4 * k + j];
+  double LU[16];
+  std::copy(P1, P1 + 16, LU);
+  if (lu_factor(4, LU)) return false;
+  for (int i = 0; i < 4; ++i)
+    if (!(LU[5 * i] > 1e-9 * P1[0])) return false;
+  double y[4] = {1.0, 0.0, 0.0, 0.0};  // p(x*)
+  lu_solve(4, LU, y);                  // y = P1^{-1} p(x*), i.e. y^T = p(x*)^T P1^{-1}
+  row.clear();
+  for (int k = 0; k < N; ++k) {
+    double phi = 0.0;
+    for (int i = 0; i < 4; ++i) phi += y[i] * (w[k] * p[4 * k + i]);  // (.. P2)_k
+    row.push_back({nb[k], phi});
+  }
+  return true;
+}
+
+// The MLS operator from S to the nodes of T (rows: T nodes, columns: S nodes).
+// Returns -1 if some row never reaches rank 4.
+int build_mls(const Level& S, const Level& T, double h, int delta, int drop_dirichlet, int scale,
+              Csr& R) {
+  bool part = !S.owner.empty() && !T.owner.empty();
+  if (part) {
+    std::set<int> us(S.owner.begin(), S.owner.end()), ut(T.owner.begin(), T.owner.end());
+    part = (us == ut);
+  }
+  std::vector<double> vs, vt;
+  if (scale) {
+    vs = nodal_volumes(S);
+    vt = nodal_volumes(T);
+  }
+  std::vector<int> all(S.n);
+  for (int i = 0; i < S.n; ++i) all[i] = i;
+  std::vector<int> ids;
+  if (part) {
+    std::set<int> u(T.owner.begin(), T.owner.end());
+    ids.assign(u.begin(), u.end());
+  }
+  std::vector<std::vector<int>> sets(ids.size());
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int k = 0; k < (int)ids.size(); ++k) sets[k] = overlap_vertices(S, ids[k], delta);
+  std::vector<std::vector<std::pair<int, double>>> rows(T.n);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
+  for (int t = 0; t < T.n; ++t) {
+    if (drop_dirichlet && T.dir[t]) continue;
+    const std::vector<int>* cand = &all;
+    if (part) cand = &sets[std::lower_bound(ids.begin(), ids.end(), T.owner[t]) - ids.begin()];
+    double c = 1.5;
+    bool ok = false;
+    for (int it = 0; it < 16 && !ok; ++it, c *= 1.5) ok = mls_row(&T.xyz[3 * t], S.xyz, *cand, c * h, rows[t]);
+    if (!ok) ++bad;
+  }
+  if (bad) return -1;
+  R.rowptr.assign(T.n + 1, 0);
+  R.col.clear();
+  R.val.clear();
+  for (int t = 0; t < T.n; ++t) {
+    for (auto& e : rows[t]) {
+      if (drop_dirichlet && S.dir[e.first]) continue;
+      R.col.push_back(e.first);
+      R.val.push_back(scale ? vt[t] * e.second / vs[e.first] : e.second);
+    }
+    R.rowptr[t + 1] = (int)R.col.size();
+  }
+  return 0;
+}
+
 // ------------------------------------------------------ V-cycle (Alg. 2)
 void residual(const Level& L, const double* r, const double* z, double* t) {
   spmv(L.A, z, t);
@@ -581,9 +743,12 @@ typedef struct {
 } orc_level;
 
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
-                 int coef_kind, const int* wave, double coef_scale, int load_kind) {
-  if (nlevels < 1) return nullptr;
+                 int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
+                 int restrict_scaling) {
+  if (nlevels < 1 || transfer < 0 || transfer > 1) return nullptr;
   Oracle* o = new Oracle();
+  o->transfer = transfer;
+  o->restrict_scaling = restrict_scaling ? 1 : 0;
   o->delta = delta;
   o->nu_pre = nu_pre;
   o->nu_post = nu_post;
@@ -614,9 +779,17 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
   for (int l = 0; l + 1 < nlevels; ++l) {
     Level& F = o->lv[l];
     Level& C = o->lv[l + 1];
-    build_interp(C.n, C.xyz.data(), C.m, C.tets.data(), C.dir.data(), F.n, F.xyz.data(),
-                 F.dir.data(), 1, F.P);
-    transpose(F.P, C.n, F.PT);
+    if (o->transfer == 1) {
+      double h = mesh_h(C);
+      if (build_mls(C, F, h, o->delta, 1, 0, F.P) || build_mls(F, C, h, o->delta, 1, o->restrict_scaling, F.PT)) {
+        delete o;
+        return nullptr;
+      }
+    } else {
+      build_interp(C.n, C.xyz.data(), C.m, C.tets.data(), C.dir.data(), F.n, F.xyz.data(),
+                   F.dir.data(), 1, F.P);
+      transpose(F.P, C.n, F.PT);
+    }
   }
   return o;
 }
@@ -672,7 +845,7 @@ int orc_interp(void* h, int level, const double* xc, double* yf) {  // y_l = P x
   spmv(static_cast<Oracle*>(h)->lv[level].P, xc, yf);
   return 0;
 }
-int orc_restrict(void* h, int level, const double* yf, double* xc) {  // x_{l+1} = P^T y_l
+int orc_restrict(void* h, int level, const double* yf, double* xc) {  // x_{l+1} = R y_l
   spmv(static_cast<Oracle*>(h)->lv[level].PT, yf, xc);
   return 0;
 }
@@ -787,6 +960,42 @@ long orc_build_interp(int nc, const double* cxyz, int mc, const int* ctets, cons
   std::copy(P.val.begin(), P.val.end(), *val);
   return (long)P.col.size();
 }
+// MLS operator from mesh S to the nodes of mesh T (see build_mls).  owner may
+// be NULL on either mesh (no partition).  h <= 0 takes h from the coarser
+// (fewer tets) of the two.  Returns nnz, or -1 if a row never reaches rank 4.
+long orc_build_mls(const orc_level* src, const orc_level* dst, double h, int delta, int drop_dirichlet,
+                   int scale, int** rowptr, int** col, double** val) {
+  Level M[2];
+  const orc_level* d[2] = {src, dst};
+  for (int k = 0; k < 2; ++k) {
+    M[k].n = d[k]->n_nodes;
+    M[k].m = d[k]->n_tets;
+    M[k].xyz.assign(d[k]->xyz, d[k]->xyz + 3 * (size_t)M[k].n);
+    M[k].tets.assign(d[k]->tets, d[k]->tets + 4 * (size_t)M[k].m);
+    M[k].dir.assign(d[k]->dirichlet, d[k]->dirichlet + M[k].n);
+    if (d[k]->owner) M[k].owner.assign(d[k]->owner, d[k]->owner + M[k].n);
+    build_pattern(M[k]);
+  }
+  if (!(h > 0)) h = mesh_h(M[0].m <= M[1].m ? M[0] : M[1]);
+  Csr R;
+  if (build_mls(M[0], M[1], h, delta, drop_dirichlet, scale, R)) return -1;
+  *rowptr = new int[R.rowptr.size()];
+  *col = new int[R.col.size() + 1];
+  *val = new double[R.val.size() + 1];
+  std::copy(R.rowptr.begin(), R.rowptr.end(), *rowptr);
+  std::copy(R.col.begin(), R.col.end(), *col);
+  std::copy(R.val.begin(), R.val.end(), *val);
+  return (long)R.col.size();
+}
+
+double orc_mesh_h(const orc_level* c) {
+  Level L;
+  L.n = c->n_nodes;
+  L.m = c->n_tets;
+  L.xyz.assign(c->xyz, c->xyz + 3 * (size_t)L.n);
+  return mesh_h(L);
+}
+
 void orc_free_csr(int* rowptr, int* col, double* val) {
   delete[] rowptr;
   delete[] col;

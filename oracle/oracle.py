@@ -39,7 +39,7 @@ def lib():
             L = C.CDLL(build())
             vp, ip, dp = C.c_void_p, C.c_int, C.c_double
             L.orc_create.restype = vp
-            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip]
+            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip]
             L.orc_destroy.argtypes = [vp]
             for name in ("orc_assemble",):
                 getattr(L, name).argtypes = [vp, vp]
@@ -64,6 +64,13 @@ def lib():
                                            C.POINTER(C.POINTER(C.c_int)),
                                            C.POINTER(C.POINTER(C.c_int)),
                                            C.POINTER(C.POINTER(C.c_double))]
+            L.orc_build_mls.restype = C.c_long
+            L.orc_build_mls.argtypes = [C.POINTER(_Level), C.POINTER(_Level), dp, ip, ip, ip,
+                                        C.POINTER(C.POINTER(C.c_int)),
+                                        C.POINTER(C.POINTER(C.c_int)),
+                                        C.POINTER(C.POINTER(C.c_double))]
+            L.orc_mesh_h.restype = dp
+            L.orc_mesh_h.argtypes = [C.POINTER(_Level)]
             L.orc_free_csr.argtypes = [vp, vp, vp]
             _lib = L
     return _lib
@@ -75,13 +82,14 @@ def _p(a):
 
 _COEF = {"const": 0, "cosexp": 1}
 _LOAD = {"one": 0, "sines": 1}
+_TRANSFER = {"bary": 0, "mls": 1}
 
 
 class Oracle:
     """One hierarchy + one parameter vector, in the oracle's FP64 arithmetic."""
 
     def __init__(self, levels, delta=1, nu_pre=2, nu_post=2, coef="const", wave=None,
-                 scale=1.0, load="one"):
+                 scale=1.0, load="one", transfer="bary", restrict_scaling=True):
         L = lib()
         self._keep = []
         arr = (_Level * len(levels))()
@@ -95,7 +103,8 @@ class Oracle:
         w = None if wave is None else np.ascontiguousarray(wave, np.int32).ravel()
         self._keep.append(w)
         self.h = L.orc_create(arr, len(levels), int(delta), int(nu_pre), int(nu_post),
-                              _COEF[coef], _p(w), float(scale), _LOAD[load])
+                              _COEF[coef], _p(w), float(scale), _LOAD[load],
+                              _TRANSFER[transfer], 1 if restrict_scaling else 0)
         if not self.h:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels
@@ -248,3 +257,40 @@ def build_interp(coarse, fine_xyz, fine_dir, drop_dirichlet=True):
     V = np.ctypeslib.as_array(val, shape=(max(nnz, 1),))[:nnz].copy()
     lib().orc_free_csr(rp, col, val)
     return sp.csr_matrix((V, Cc, R), shape=(nf, cx.shape[0]))
+
+
+def _level_desc(lv, keep):
+    xyz = np.ascontiguousarray(lv.xyz, np.float64)
+    tets = np.ascontiguousarray(lv.tets, np.int32)
+    dr = np.ascontiguousarray(lv.dirichlet, np.uint8)
+    ow = None if getattr(lv, "owner", None) is None else np.ascontiguousarray(lv.owner, np.int32)
+    keep += [xyz, tets, dr, ow]
+    return _Level(xyz.shape[0], _p(xyz), tets.shape[0], _p(tets), _p(dr), _p(ow))
+
+
+def build_mls(src, dst, h=0.0, delta=1, drop_dirichlet=True, scale=False):
+    """The MLS operator from mesh `src` to the nodes of mesh `dst` (Section 3.2),
+    as a scipy CSR matrix of shape (dst nodes, src nodes).  `owner` may be None
+    on either mesh.  h <= 0: h of the mesh with fewer tets."""
+    import scipy.sparse as sp
+    keep = []
+    a, b = _level_desc(src, keep), _level_desc(dst, keep)
+    rp, col, val = C.POINTER(C.c_int)(), C.POINTER(C.c_int)(), C.POINTER(C.c_double)()
+    nnz = lib().orc_build_mls(C.byref(a), C.byref(b), float(h), int(delta),
+                              1 if drop_dirichlet else 0, 1 if scale else 0,
+                              C.byref(rp), C.byref(col), C.byref(val))
+    if nnz < 0:
+        raise ValueError("oracle: an MLS row never reached rank 4")
+    nt = b.n_nodes
+    R = np.ctypeslib.as_array(rp, shape=(nt + 1,)).copy()
+    Cc = np.ctypeslib.as_array(col, shape=(max(nnz, 1),))[:nnz].copy()
+    V = np.ctypeslib.as_array(val, shape=(max(nnz, 1),))[:nnz].copy()
+    lib().orc_free_csr(rp, col, val)
+    return sp.csr_matrix((V, Cc, R), shape=(nt, a.n_nodes))
+
+
+def mesh_h(lv):
+    """h = cbrt(6 |bounding box| / tets) of a mesh (the MLS radius unit)."""
+    keep = []
+    d = _level_desc(lv, keep)
+    return float(lib().orc_mesh_h(C.byref(d)))

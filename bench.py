@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mls", action="store_true",
+                    help="skip the MLS-transfer variant (Section 3.2) of the same workload")
     ap.add_argument("--batch", type=int, default=4,
                     help="concurrent instances of the batched FP32-factor measurement")
     ap.add_argument("--serve", type=int, default=48,
@@ -205,8 +207,8 @@ def run_msp(args):
     def mu_of(i):
         return syn.mu_draw(rank * 100000 + i)
 
-    def measure(precision, steps, warmup, profile_all=False):
-        h = P.Hierarchy(levels, precision=precision, **kw)
+    def measure(precision, steps, warmup, transfer="bary"):
+        h = P.Hierarchy(levels, precision=precision, transfer=transfer, **kw)
         inst = h.assemble(mu_of(0), stream=stream)
         n = levels[0].n_nodes
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -413,6 +415,21 @@ def run_msp(args):
                                "p99": float(np.percentile(bres["lat"], 99))},
                 "iterations_mean": float(np.mean(bres["iters"])),
                 "timing": "host wall clock over all instances, after a device synchronisation"}
+    mls = None
+    if not args.no_mls and args.precision == "f64":
+        mls = {"transfer": "overlapping MLS both ways (Section 3.2), restriction of residual "
+                           "densities scaled by nodal volumes"}
+        for prec in ("f64", "f32"):
+            k = args.steps  # same mu sequence as the barycentric runs
+            r = measure(prec, k, args.warmup, transfer="mls")
+            ref = res["x"] if prec == "f64" else (mres["x"] if mixed else res["x"])
+            mls[prec] = {"value": k / (r["ms"] / 1e3), "unit": UNIT, "steps": k,
+                         "iterations_mean": float(np.mean(r["iters"])),
+                         "final_rel_residual_max": float(np.max(r["relres"])),
+                         "rel_diff_vs_barycentric_solution":
+                             float(np.linalg.norm(r["x"] - ref) / np.linalg.norm(ref)),
+                         "stage_ms_host": r["stage_ms"],
+                         "transfer_ms_per_solve": r["kernel_ms"].get("transfer", 0.0)}
     serving = None
     if args.serve > 0 and world == 1:
         serving = measure_serving(args.serve, args.serve_rate)
@@ -457,6 +474,8 @@ def run_msp(args):
     }
     if mixed:
         line["mixed"] = mixed
+    if mls:
+        line["mls"] = mls
     if serving:
         line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:

@@ -81,6 +81,14 @@ typedef struct msp_level_desc {
 typedef void* (*msp_alloc_fn)(void* ctx, size_t bytes, void* stream);
 typedef void (*msp_free_fn)(void* ctx, void* ptr, void* stream);
 
+/* Transfers between consecutive levels (msp_options.transfer). */
+typedef enum msp_transfer {
+  MSP_TRANSFER_BARY = 0,  /* P = barycentric interpolation of level-(l+1) fields at the
+                             nodes of level l; restriction by P^T */
+  MSP_TRANSFER_MLS = 1    /* overlapping moving-least-squares interpolation in both
+                             directions (Section 3.2, Eq. 13-15, 24); see below */
+} msp_transfer;
+
 typedef struct msp_options {
   int32_t delta;              /* overlap: element layers added to each subdomain (>= 0) */
   int32_t nu_pre, nu_post;    /* RAS smoothing steps before / after the coarse correction */
@@ -91,6 +99,12 @@ typedef struct msp_options {
   int32_t wave[8][3];         /* a_j for MSP_K_COSEXP */
   double coef_scale;          /* s for MSP_K_COSEXP */
   int32_t load_kind;          /* msp_load */
+  int32_t transfer;           /* msp_transfer */
+  int32_t restrict_scaling;   /* MSP_TRANSFER_MLS only.  1 (default): the residual is
+                                 restricted as a density, r_i / |w_i| (|w_i| = sum of |T|/4
+                                 over the tets at node i), and the result multiplied by the
+                                 coarse |w|, so that its scale matches the coarse operator;
+                                 0: the plain interpolated residual of Algorithm 2 */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
@@ -100,7 +114,8 @@ typedef struct msp_options {
 } msp_options;
 
 /* Fills *o with the defaults: delta 1, nu 2/2, restart 30, max_it 1000, FP64
- * factors, k = 1, f = 1, no budget, cudaMalloc. */
+ * factors, k = 1, f = 1, barycentric transfers (MLS restriction scaling on),
+ * no budget, cudaMalloc. */
 MSP_API void msp_default_options(msp_options* o);
 
 typedef struct msp_hierarchy msp_hierarchy;
@@ -119,10 +134,23 @@ typedef struct msp_stats {
  * lv[0..nlevels-1], finest first, nlevels >= 1.  Builds on the host: the CSR
  * pattern of every level, the element-to-nonzero contribution map, the
  * delta-overlapping subdomains (Section 2.2), the dense-block extraction maps,
- * point location and the barycentric interpolation P (coarse l+1 -> fine l)
- * with its transpose; then uploads them and computes the per-tet geometry and
- * the load vector on the device.  Errors: MSP_ERR_INVALID (degenerate tet,
- * index out of range, missing owner array, bad option), MSP_ERR_OOM. */
+ * and the transfers: with MSP_TRANSFER_BARY point location and the barycentric
+ * interpolation P (coarse l+1 -> fine l) with its transpose; with
+ * MSP_TRANSFER_MLS the two MLS operators of Section 3.2.  MLS row at a target
+ * node x* owned by id q: the source nodes of Omega^delta_q (source vertices
+ * owned by q, Dirichlet ones included, grown by delta element layers) within
+ * rho of x*, weights w = 1 - 6s^2 + 8s^3 - 3s^4 (s = distance / rho, Eq. 15),
+ * row = p(x*)^T P1^{-1} P2 for the linear basis; rho = c h with h =
+ * cbrt(6 |bounding box| / tets) of level l+1 and c = 1.5, 1.5^2, ... until the
+ * neighbourhood has rank 4 (Theorem 3.2).  Subdomain q of one level is
+ * subdomain q of the other when both levels are partitioned over the same id
+ * set; otherwise (and for the coarsest level) the neighbourhood comes from the
+ * whole source level.  Dirichlet source nodes take part in the fit and are
+ * then dropped as columns; Dirichlet target nodes get empty rows.  Then it
+ * uploads everything and computes the per-tet geometry and the load vector on
+ * the device.  Errors: MSP_ERR_INVALID (degenerate tet, index out of range,
+ * missing owner array, bad option, an MLS neighbourhood that never reaches
+ * rank 4), MSP_ERR_OOM. */
 MSP_API int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_options* o,
                        msp_hierarchy** out);
 MSP_API void msp_free_hierarchy(msp_hierarchy* h);
@@ -136,6 +164,7 @@ typedef struct msp_level_info {
   int64_t sub_dofs;           /* sum_p n_p (coarsest: interior DoFs) */
   int64_t factor_elems;       /* elements of the tiled factor storage of this level */
   int64_t P_nnz;              /* nnz of P from level+1 (0 on the coarsest) */
+  int64_t R_nnz;              /* nnz of the restriction to level+1 (P^T or MLS) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
 
@@ -238,8 +267,9 @@ MSP_API int msp_apply_op(msp_instance* inst, int op, int level, const double* x_
  *   MSP_ARR_SUB_NT (int32 tiles per side of each block), MSP_ARR_TILE_FIRST (int32
  *   F_I of every tile row, blocks concatenated; see MSP_TILE),
  *   MSP_ARR_SUB_OWN (uint8), MSP_ARR_P_ROWPTR, MSP_ARR_P_COL (int32),
- *   MSP_ARR_P_VAL (double), MSP_ARR_PT_ROWPTR, MSP_ARR_PT_COL (int32),
- *   MSP_ARR_PT_VAL (double), MSP_ARR_LOAD (double, device-resident b)
+ *   MSP_ARR_P_VAL (double) of the prolongation from level+1 (P or MLS),
+ *   MSP_ARR_PT_ROWPTR, MSP_ARR_PT_COL (int32), MSP_ARR_PT_VAL (double) of the
+ *   restriction to level+1 (P^T or MLS), MSP_ARR_LOAD (double, device-resident b)
  * Instance arrays (device-resident, copied back):
  *   MSP_ARR_VAL (double CSR values), MSP_ARR_FACTOR (the tiled factor of
  *   subdomain `sub` of `level`, sub = -1 for the coarsest level, in the

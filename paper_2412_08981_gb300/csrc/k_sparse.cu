@@ -263,8 +263,10 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
     k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
   else if (avg_row_nnz <= 20)
     k_spmv<8><<<nblk((int64_t)nrows * 8, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
-  else
+  else if (avg_row_nnz <= 64)
     k_spmv<16><<<nblk((int64_t)nrows * 16, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+  else
+    k_spmv<32><<<nblk((int64_t)nrows * 32, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
 }
 
 void launch_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n,

@@ -126,8 +126,8 @@ struct DevLevel {
   int fac_grid = 0;               // its CTAs and their block lists
   int32_t *fac_cta_ptr = nullptr, *fac_cta_list = nullptr;
   double fac_flops = 0;           // all tile steps of the level
-  // transfer from level+1
-  int64_t P_nnz = 0;
+  // prolongation from level+1 (P_*) and restriction to it (PT_*)
+  int64_t P_nnz = 0, PT_nnz = 0;
   int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
   double *P_val = nullptr, *PT_val = nullptr;
 };
@@ -323,6 +323,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   }
   if (l + 1 < (int)h->host.size()) {
     D.P_nnz = (int64_t)H.P_col.size();
+    D.PT_nnz = (int64_t)H.PT_col.size();
     D.P_rowptr = A.upload(H.P_rowptr);
     D.P_col = A.upload(H.P_col);
     D.P_val = A.upload(H.P_val);
@@ -330,7 +331,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.PT_col = A.upload(H.PT_col);
     D.PT_val = A.upload(H.PT_val);
     D.avg_P = (int)std::max<int64_t>(1, D.P_nnz / std::max(1, H.n));
-    D.avg_PT = (int)std::max<int64_t>(1, D.P_nnz / std::max(1, h->host[l + 1].n));
+    D.avg_PT = (int)std::max<int64_t>(1, D.PT_nnz / std::max(1, h->host[l + 1].n));
   }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   int* bad = A.alloc<int>(1);
@@ -354,6 +355,8 @@ int check_options(const msp_options& o) {
   if (o.max_it < 1) return fail(MSP_ERR_INVALID, "max_it must be >= 1");
   if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32)
     return fail(MSP_ERR_INVALID, "unknown factor precision");
+  if (o.transfer != MSP_TRANSFER_BARY && o.transfer != MSP_TRANSFER_MLS)
+    return fail(MSP_ERR_INVALID, "unknown transfer");
   if (o.coef_kind != MSP_K_CONST && o.coef_kind != MSP_K_COSEXP)
     return fail(MSP_ERR_INVALID, "unknown coefficient family");
   if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
@@ -492,8 +495,8 @@ void transfer(msp_instance* I, int l, bool restrict_, const double* x, double* y
   else
     launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, D.avg_P, s);
   double rows = restrict_ ? nc : D.n, cols = restrict_ ? D.n : nc;
-  ps.account((double)D.P_nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16),
-             2.0 * (double)D.P_nnz);
+  double nnz = (double)(restrict_ ? D.PT_nnz : D.P_nnz);
+  ps.account(nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16), 2.0 * nnz);
 }
 
 // z += B^{-1}(r - A z), `its` times; when `from_zero`, z is not read first
@@ -516,7 +519,8 @@ void smooth(msp_instance* I, int l, const double* r, double* z, int its, bool fr
   }
 }
 
-// Algorithm 2 with P^T / P transfers and a direct solve on the coarsest level.
+// Algorithm 2 with the level transfers (P^T / P, or MLS both ways) and a
+// direct solve on the coarsest level.
 void vcycle(msp_instance* I, const double* r0, double* z0, cudaStream_t s) {
   msp_hierarchy* h = I->h;
   const int L = (int)h->dev.size();
@@ -806,6 +810,8 @@ void msp_default_options(msp_options* o) {
   o->coef_kind = MSP_K_CONST;
   o->coef_scale = 1.0;
   o->load_kind = MSP_F_ONE;
+  o->transfer = MSP_TRANSFER_BARY;
+  o->restrict_scaling = 1;
 }
 
 const char* msp_last_error(void) { return msp::g_last_error.c_str(); }
@@ -878,6 +884,7 @@ int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) 
   info->sub_dofs = H.sub_ptr.empty() ? 0 : H.sub_ptr.back();
   info->factor_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
   info->P_nnz = (int64_t)H.P_col.size();
+  info->R_nnz = (int64_t)H.PT_col.size();
   return MSP_OK;
 }
 

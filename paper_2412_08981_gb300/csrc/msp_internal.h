@@ -68,7 +68,8 @@ struct HostLevel {
   // work list of the factorisation: subdomains sorted by descending NT
   std::vector<int32_t> sub_order;
 
-  // interpolation from level+1 to this level, and its transpose
+  // prolongation from level+1 to this level (P or MLS) and restriction to
+  // level+1 (P^T or MLS)
   std::vector<int32_t> P_rowptr, P_col, PT_rowptr, PT_col;
   std::vector<double> P_val, PT_val;
 };

@@ -6,7 +6,9 @@
 //   * CSR pattern of J on every level and the element->nonzero map used by
 //     the device assembly kernel,
 //   * delta-overlapping subdomains and their dense extraction maps,
-//   * barycentric interpolation P between consecutive levels and P^T.
+//   * the transfers between consecutive levels: barycentric interpolation P
+//     and P^T, or the overlapping MLS operators of Section 3.2 (the weights
+//     are set-up; applying them is a sparse product on the device).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -431,6 +433,276 @@ void build_interp(const HostLevel& F, const HostLevel& C, HostLevel& out) {
     }
 }
 
+// --------------------------------------------- MLS transfer (Section 3.2)
+// Source nodes in uniform cubic cells over their bounding box (ids ascending
+// within a cell), for radius queries.
+struct NodeGrid {
+  double lo[3] = {0, 0, 0}, cell = 1;
+  int G[3] = {1, 1, 1};
+  std::vector<int32_t> ptr, ids;
+  int idx(double v, int d) const {
+    double c = std::floor((v - lo[d]) / cell);
+    return c < 0 ? 0 : (c >= G[d] ? G[d] - 1 : (int)c);
+  }
+};
+
+void build_node_grid(const HostLevel& S, double cell, NodeGrid& g) {
+  double hi[3] = {-1e300, -1e300, -1e300};
+  for (int d = 0; d < 3; ++d) g.lo[d] = 1e300;
+  for (int i = 0; i < S.n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      g.lo[d] = std::min(g.lo[d], S.xyz[3 * (int64_t)i + d]);
+      hi[d] = std::max(hi[d], S.xyz[3 * (int64_t)i + d]);
+    }
+  g.cell = cell;
+  for (int d = 0; d < 3; ++d) g.G[d] = std::max(1, std::min(1024, (int)((hi[d] - g.lo[d]) / cell) + 1));
+  const size_t nc = (size_t)g.G[0] * g.G[1] * g.G[2];
+  std::vector<int32_t> c_of(S.n);
+  g.ptr.assign(nc + 1, 0);
+  for (int i = 0; i < S.n; ++i) {
+    const double* x = &S.xyz[3 * (int64_t)i];
+    c_of[i] = g.idx(x[0], 0) + g.G[0] * (g.idx(x[1], 1) + g.G[1] * g.idx(x[2], 2));
+    g.ptr[c_of[i] + 1]++;
+  }
+  for (size_t c = 0; c < nc; ++c) g.ptr[c + 1] += g.ptr[c];
+  g.ids.resize(S.n);
+  std::vector<int32_t> fill(g.ptr.begin(), g.ptr.end() - 1);
+  for (int i = 0; i < S.n; ++i) g.ids[fill[c_of[i]]++] = i;
+}
+
+// h = cbrt(6 |bounding box| / tets): the edge of the cube cells that would
+// hold the mesh's tets (the Kuhn split puts 6 tets in each).
+double mls_unit(const HostLevel& C) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < C.n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], C.xyz[3 * (int64_t)i + d]);
+      hi[d] = std::max(hi[d], C.xyz[3 * (int64_t)i + d]);
+    }
+  double vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  return std::cbrt(6.0 * vol / C.m);
+}
+
+// Lumped nodal volumes |w_i| = sum over the tets at i of |T|/4 (ascending tet).
+std::vector<double> nodal_volume(const HostLevel& L) {
+  std::vector<double> v(L.n, 0.0);
+  for (int e = 0; e < L.m; ++e) {
+    const int32_t* t = &L.tets[4 * (int64_t)e];
+    const double* p0 = &L.xyz[3 * (int64_t)t[0]];
+    double c[3][3];
+    for (int a = 1; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) c[a - 1][k] = L.xyz[3 * (int64_t)t[a] + k] - p0[k];
+    const double q = std::fabs(det3(c[0], c[1], c[2])) / 6.0 / 4.0;
+    for (int a = 0; a < 4; ++a) v[t[a]] += q;
+  }
+  return v;
+}
+
+// y = M^{-1} e_1 for the symmetric 4x4 moment matrix M = L D L^T; false when a
+// pivot D_k is not above tol (rank < 4).
+bool moment_solve(const double* M, double tol, double y[4]) {
+  double Lm[4][4] = {{0}}, D[4];
+  for (int k = 0; k < 4; ++k) {
+    double d = M[5 * k];
+    for (int j = 0; j < k; ++j) d -= Lm[k][j] * Lm[k][j] * D[j];
+    if (!(d > tol)) return false;
+    D[k] = d;
+    for (int i = k + 1; i < 4; ++i) {
+      double v = M[4 * i + k];
+      for (int j = 0; j < k; ++j) v -= Lm[i][j] * Lm[k][j] * D[j];
+      Lm[i][k] = v / d;
+    }
+  }
+  double z[4] = {1.0, 0.0, 0.0, 0.0};
+  for (int i = 1; i < 4; ++i)
+    for (int j = 0; j < i; ++j) z[i] -= Lm[i][j] * z[j];
+  for (int i = 0; i < 4; ++i) z[i] /= D[i];
+  for (int i = 2; i >= 0; --i)
+    for (int j = i + 1; j < 4; ++j) z[i] -= Lm[j][i] * z[j];
+  std::copy(z, z + 4, y);
+  return true;
+}
+
+struct MlsRow {
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+
+// One MLS row at x: the admitted source nodes (stamp[n] == key, or all when
+// stamp is null) within rho = c h, c = 1.5, 1.5^2, ..., until the moment matrix
+// of the linear basis [1, (x_n - x)/rho] has rank 4; row_n = w_n [1, (x_n - x)/rho] . y
+// with y = M^{-1} p(x), p(x) = e_1 in this basis.
+bool mls_row(const HostLevel& S, const NodeGrid& g, const double* x, double h,
+             const int32_t* stamp, int32_t key, std::vector<int32_t>& cand, MlsRow& out) {
+  double c = 1.5;
+  for (int it = 0; it < 16; ++it, c *= 1.5) {
+    const double rho = c * h;
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = g.idx(x[d] - rho, d);
+      hi[d] = g.idx(x[d] + rho, d);
+    }
+    cand.clear();
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const int cc = i + g.G[0] * (j + g.G[1] * k);
+          for (int q = g.ptr[cc]; q < g.ptr[cc + 1]; ++q) {
+            const int32_t n = g.ids[q];
+            if (stamp && stamp[n] != key) continue;
+            const double* y = &S.xyz[3 * (int64_t)n];
+            const double d0 = y[0] - x[0], d1 = y[1] - x[1], d2 = y[2] - x[2];
+            if (d0 * d0 + d1 * d1 + d2 * d2 < rho * rho) cand.push_back(n);
+          }
+        }
+    if (cand.size() < 4) continue;
+    std::sort(cand.begin(), cand.end());
+    const size_t N = cand.size();
+    std::vector<double> wq(5 * N);  // per neighbour: w, then the basis values
+    double M[16] = {0};
+    for (size_t a = 0; a < N; ++a) {
+      const double* y = &S.xyz[3 * (int64_t)cand[a]];
+      const double d0 = y[0] - x[0], d1 = y[1] - x[1], d2 = y[2] - x[2];
+      const double s = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) / rho;
+      const double w = 1.0 - 6.0 * s * s + 8.0 * s * s * s - 3.0 * s * s * s * s;  // Eq. 15
+      const double q[4] = {1.0, d0 / rho, d1 / rho, d2 / rho};
+      wq[5 * a] = w;
+      for (int i = 0; i < 4; ++i) {
+        wq[5 * a + 1 + i] = q[i];
+        for (int j = 0; j < 4; ++j) M[4 * i + j] += w * q[i] * q[j];
+      }
+    }
+    double yv[4];
+    if (!moment_solve(M, 1e-9 * M[0], yv)) continue;
+    out.col.assign(cand.begin(), cand.end());
+    out.val.resize(N);
+    for (size_t a = 0; a < N; ++a) {
+      double t = 0.0;
+      for (int i = 0; i < 4; ++i) t += yv[i] * (wq[5 * a] * wq[5 * a + 1 + i]);
+      out.val[a] = t;
+    }
+    return true;
+  }
+  return false;
+}
+
+// The MLS operator from S to the nodes of T: rows of T's non-Dirichlet nodes,
+// columns of S's non-Dirichlet nodes (ascending).  With `scale` every entry is
+// multiplied by |w_t| / |w_n|.  Returns "" or an error message.
+std::string build_mls(const HostLevel& S, const HostLevel& T, double h, int delta, bool scale,
+                      std::vector<int32_t>& rowptr, std::vector<int32_t>& col,
+                      std::vector<double>& val) {
+  NodeGrid g;
+  build_node_grid(S, 1.5 * h, g);
+  // subdomain q of S pairs with subdomain q of T when both partitions use the
+  // same id set
+  std::vector<int32_t> ids_s, ids_t;
+  bool part = !S.owner.empty() && !T.owner.empty();
+  if (part) {
+    ids_s = S.owner;
+    ids_t = T.owner;
+    for (auto* v : {&ids_s, &ids_t}) {
+      std::sort(v->begin(), v->end());
+      v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    part = (ids_s == ids_t);
+  }
+  // work groups: target nodes by owner id (one group when unpaired)
+  std::vector<int32_t> gptr, gnodes;
+  std::vector<int32_t> gid;  // owner id of each group
+  if (part) {
+    gid = ids_t;
+    gptr.assign(gid.size() + 1, 0);
+    std::vector<int32_t> gi(T.n);
+    for (int t = 0; t < T.n; ++t) {
+      gi[t] = (int32_t)(std::lower_bound(gid.begin(), gid.end(), T.owner[t]) - gid.begin());
+      gptr[gi[t] + 1]++;
+    }
+    for (size_t k = 0; k < gid.size(); ++k) gptr[k + 1] += gptr[k];
+    gnodes.resize(T.n);
+    std::vector<int32_t> fill(gptr.begin(), gptr.end() - 1);
+    for (int t = 0; t < T.n; ++t) gnodes[fill[gi[t]]++] = t;
+  } else {
+    const int nchunk = 64;
+    gptr.resize(nchunk + 1);
+    for (int k = 0; k <= nchunk; ++k) gptr[k] = (int32_t)((int64_t)T.n * k / nchunk);
+    gnodes.resize(T.n);
+    std::iota(gnodes.begin(), gnodes.end(), 0);
+  }
+  // source vertices by owner id, for the overlap growth
+  std::vector<int32_t> sptr, snodes;
+  if (part) {
+    sptr.assign(ids_s.size() + 1, 0);
+    std::vector<int32_t> si(S.n);
+    for (int n = 0; n < S.n; ++n) {
+      si[n] = (int32_t)(std::lower_bound(ids_s.begin(), ids_s.end(), S.owner[n]) - ids_s.begin());
+      sptr[si[n] + 1]++;
+    }
+    for (size_t k = 0; k < ids_s.size(); ++k) sptr[k + 1] += sptr[k];
+    snodes.resize(S.n);
+    std::vector<int32_t> fill(sptr.begin(), sptr.end() - 1);
+    for (int n = 0; n < S.n; ++n) snodes[fill[si[n]]++] = n;
+  }
+  std::vector<MlsRow> rows(T.n);
+  const int ngroups = (int)gptr.size() - 1;
+  std::vector<int> failed(ngroups, -1);
+  auto work = [&](int g0, int g1) {
+    std::vector<int32_t> stamp(part ? S.n : 0, -1), frontier, next, cand;
+    for (int k = g0; k < g1; ++k) {
+      if (part) {  // Omega^delta_q: owned vertices, then delta layers over the mesh graph
+        frontier.assign(snodes.begin() + sptr[k], snodes.begin() + sptr[k + 1]);
+        for (int32_t v : frontier) stamp[v] = k;
+        for (int layer = 0; layer < delta; ++layer) {
+          next.clear();
+          for (int32_t v : frontier)
+            for (int q = S.rowptr[v]; q < S.rowptr[v + 1]; ++q)
+              if (stamp[S.col[q]] != k) {
+                stamp[S.col[q]] = k;
+                next.push_back(S.col[q]);
+              }
+          frontier.swap(next);
+        }
+      }
+      for (int q = gptr[k]; q < gptr[k + 1]; ++q) {
+        const int t = gnodes[q];
+        if (T.dir[t]) continue;
+        if (!mls_row(S, g, &T.xyz[3 * (int64_t)t], h, part ? stamp.data() : nullptr, k, cand, rows[t])) {
+          failed[k] = t;
+          break;
+        }
+      }
+    }
+  };
+  int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+  nth = std::min(nth, ngroups);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back(work, (int)((int64_t)ngroups * t / nth), (int)((int64_t)ngroups * (t + 1) / nth));
+  for (auto& t : th) t.join();
+  for (int k = 0; k < ngroups; ++k)
+    if (failed[k] >= 0)
+      return "MLS neighbourhood of node " + std::to_string(failed[k]) + " never reached rank 4";
+  std::vector<double> vs, vt;
+  if (scale) {
+    vs = nodal_volume(S);
+    vt = nodal_volume(T);
+  }
+  rowptr.assign(T.n + 1, 0);
+  col.clear();
+  val.clear();
+  for (int t = 0; t < T.n; ++t) {
+    const MlsRow& r = rows[t];
+    for (size_t a = 0; a < r.col.size(); ++a) {
+      const int32_t n = r.col[a];
+      if (S.dir[n]) continue;  // the transferred vectors vanish there
+      col.push_back(n);
+      val.push_back(scale ? vt[t] * r.val[a] / vs[n] : r.val[a]);
+    }
+    rowptr[t + 1] = (int32_t)col.size();
+  }
+  return "";
+}
+
 std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
   if (d.n_nodes <= 0 || d.n_tets <= 0 || !d.xyz || !d.tets || !d.dirichlet)
     return "level " + std::to_string(l) + ": empty mesh or NULL array";
@@ -484,7 +756,18 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
       return "internal: empty coarsest block";
     build_factor_layout(L);
   }
-  for (int l = 0; l + 1 < nlevels; ++l) build_interp(out[l], out[l + 1], out[l]);
+  for (int l = 0; l + 1 < nlevels; ++l) {
+    HostLevel& F = out[l];
+    const HostLevel& C = out[l + 1];
+    if (o.transfer == MSP_TRANSFER_MLS) {
+      const double h = mls_unit(C);
+      std::string e = build_mls(C, F, h, o.delta, false, F.P_rowptr, F.P_col, F.P_val);
+      if (e.empty()) e = build_mls(F, C, h, o.delta, o.restrict_scaling != 0, F.PT_rowptr, F.PT_col, F.PT_val);
+      if (!e.empty()) return "level " + std::to_string(l) + ": " + e;
+    } else {
+      build_interp(F, C, F);
+    }
+  }
   return "";
 }
 

@@ -22,6 +22,7 @@ MSP_ERR_TIMEOUT, MSP_ERR_CUDA, MSP_ERR_INTERNAL = -4, -5, -6
 MSP_F64, MSP_F32 = 0, 1
 MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
+MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
@@ -60,7 +61,8 @@ class msp_options(C.Structure):
     _fields_ = [("delta", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("restart", C.c_int32), ("max_it", C.c_int32), ("factor_precision", C.c_int32),
                 ("coef_kind", C.c_int32), ("wave", (C.c_int32 * 3) * 8),
-                ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("host_only", C.c_int32),
+                ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("transfer", C.c_int32),
+                ("restrict_scaling", C.c_int32), ("host_only", C.c_int32),
                 ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
                 ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
 
@@ -79,7 +81,7 @@ class msp_server_opts(C.Structure):
 class msp_level_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("nnz", C.c_int64),
                 ("n_sub", C.c_int32), ("sub_dofs", C.c_int64), ("factor_elems", C.c_int64),
-                ("P_nnz", C.c_int64)]
+                ("P_nnz", C.c_int64), ("R_nnz", C.c_int64)]
 
 
 class msp_kernel_profile(C.Structure):
@@ -216,7 +218,8 @@ class Hierarchy:
 
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
                  max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
-                 load="one", host_only=False, budget_bytes=0, torch_alloc=True):
+                 load="one", host_only=False, budget_bytes=0, torch_alloc=True,
+                 transfer="bary", restrict_scaling=True):
         lib = _load_library()
         self._keep = []
         arr = (msp_level_desc * len(levels))()
@@ -234,6 +237,8 @@ class Hierarchy:
                             coef_kind={"const": MSP_K_CONST, "cosexp": MSP_K_COSEXP}[coef],
                             coef_scale=float(scale),
                             load_kind={"one": MSP_F_ONE, "sines": MSP_F_SINES}[load],
+                            transfer={"bary": MSP_TRANSFER_BARY, "mls": MSP_TRANSFER_MLS}[transfer],
+                            restrict_scaling=1 if restrict_scaling else 0,
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))
         if wave is not None:

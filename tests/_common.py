@@ -11,14 +11,20 @@ syn.WORKLOADS.setdefault("cube20_3lvl", dict(ns=(20, 10, 5), parts=((3, 3, 3), (
                                               delta=2, nu=2, coef="cosexp", scale=1.0,
                                               load="one", rtol=1e-10, restart=30))
 
+# the same sizes with one box grid on both RAS levels, so that the MLS transfer
+# pairs subdomain q of one level with subdomain q of the other
+syn.WORKLOADS.setdefault("cube20m_3lvl", dict(ns=(20, 10, 5), parts=((3, 3, 3), (3, 3, 3)),
+                                               delta=2, nu=2, coef="cosexp", scale=1.0,
+                                               load="one", rtol=1e-10, restart=30))
+
 
 def workload(name, hierarchy_id=0):
     return syn.workload(name, hierarchy_id)
 
 
-def make_oracle(levels, w, orc):
+def make_oracle(levels, w, orc, **kw):
     return orc.Oracle(levels, delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], coef=w["coef"],
-                      wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
+                      wave=syn.wave_vectors(), scale=w["scale"], load=w["load"], **kw)
 
 
 def make_hierarchy(levels, w, P, **kw):

@@ -75,6 +75,24 @@ def test_host_structures_match_oracle(P, orc, name):
     assert info["n_sub"] == o.get("n_subs", 0)
 
 
+@pytest.mark.parametrize("name", ["cube8_2lvl", "cube16_3lvl", "cube20m_3lvl"])
+@pytest.mark.parametrize("scaling", [True, False])
+def test_host_mls_transfers_match_oracle(P, orc, name, scaling):
+    """MLS weights (Section 3.2): same neighbourhoods bit-exactly, values to
+    rounding; cube20m pairs subdomains across levels, the others do not."""
+    levels, w = workload(name)
+    h = make_hierarchy(levels, w, P, host_only=True, transfer="mls", restrict_scaling=scaling)
+    o = make_oracle(levels, w, orc, transfer="mls", restrict_scaling=scaling)
+    for l in range(len(levels) - 1):
+        for a in ("P_rowptr", "P_col", "PT_rowptr", "PT_col"):
+            np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+        for a in ("P_val", "PT_val"):
+            ref = o.get(a, l)
+            np.testing.assert_allclose(h.array(l, a), ref, rtol=1e-12, atol=1e-13 * abs(ref).max())
+        info = h.info(l)
+        assert info["P_nnz"] == o.get("P_col", l).size and info["R_nnz"] == o.get("PT_col", l).size
+
+
 def test_odd_partition_and_empty_boxes(P, orc):
     """Partition ids that skip values and boxes with only Dirichlet nodes."""
     fine = syn.cube_level(9, 3, parts=(5, 3, 2))
@@ -114,6 +132,21 @@ def test_invalid_inputs_are_rejected(P):
     h = P.Hierarchy([lv, co], host_only=True)
     with pytest.raises(P.MspError):  # no device state on a host-only handle
         h.assemble(np.zeros(8), stream=0)
+    # unknown transfer kind, straight through the C ABI
+    import ctypes as C
+    arr = (P.msp.msp_level_desc * 2)()
+    keep = []
+    for i, m in enumerate((lv, co)):
+        xyz = np.ascontiguousarray(m.xyz)
+        tets = np.ascontiguousarray(m.tets, np.int32)
+        dr = np.ascontiguousarray(m.dirichlet, np.uint8)
+        ow = None if m.owner is None else np.ascontiguousarray(m.owner, np.int32)
+        keep += [xyz, tets, dr, ow]
+        arr[i] = P.msp.msp_level_desc(xyz.shape[0], xyz.ctypes.data, tets.shape[0], tets.ctypes.data,
+                                      dr.ctypes.data, None if ow is None else ow.ctypes.data)
+    o = P.msp.default_options(host_only=1, transfer=7)
+    out = C.c_void_p()
+    assert P.load().msp_load_hierarchy(arr, 2, C.byref(o), C.byref(out)) == P.msp.MSP_ERR_INVALID
 
 
 @pytest.mark.parametrize("name", ["cube16_3lvl", "cube20_3lvl"])

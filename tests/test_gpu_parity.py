@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Every operator of the hot path is compared element by element on the same
-seeded inputs: assembly, load vector, SpMV, P and P^T, subdomain factors, the
+seeded inputs: assembly, load vector, SpMV, the transfers (P and P^T, or the
+MLS operators), subdomain factors, the
 RAS application, the coarsest solve, the whole V-cycle and the FGMRES
 solution.  Tolerances: FP64 operators <= 1e-12 relative (norm-wise, the per
 operator bound of the method's FP64 path), solution <= 1e-7 relative at
@@ -36,13 +37,13 @@ def P():
 
 
 class Case:
-    def __init__(self, name, P, orc, torch, mu_req=0, **kw):
+    def __init__(self, name, P, orc, torch, mu_req=0, transfer="bary", **kw):
         self.levels, self.w = workload(name)
         self.mu = syn.mu_draw(mu_req)
-        self.o = make_oracle(self.levels, self.w, orc)
+        self.o = make_oracle(self.levels, self.w, orc, transfer=transfer)
         self.o.assemble(self.mu)
         self.o.factor()
-        self.h = make_hierarchy(self.levels, self.w, P, **kw)
+        self.h = make_hierarchy(self.levels, self.w, P, transfer=transfer, **kw)
         self.inst = self.h.assemble(self.mu, stream=torch.cuda.current_stream())
         self.inst.factor()
         self.torch = torch
@@ -59,9 +60,15 @@ class Case:
         return t.cpu().numpy()
 
 
-@pytest.fixture(scope="module", params=PARITY)
+# every parity workload with P / P^T, and two with the MLS transfers of
+# Section 3.2 (cube20m pairs the subdomains of the two RAS levels)
+CASES = [(n, "bary") for n in PARITY] + [("cube16_3lvl", "mls"), ("cube20m_3lvl", "mls")]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-{c[1]}")
 def case(request, P, orc, torch):
-    return Case(request.param, P, orc, torch)
+    name, transfer = request.param
+    return Case(name, P, orc, torch, transfer=transfer)
 
 
 def test_assembly_and_load(case):
@@ -286,6 +293,26 @@ def test_fp32_factors_reach_fp64_accuracy(P, orc, torch):
     n0 = o.get("sub_dofs", 0, 0).size
     do = np.diag(o.get("sub_lu", 0, 0).reshape(n0, n0))
     assert 1e-12 < rel(dg, do) < 1e-5
+
+
+@pytest.mark.parametrize("scaling", [True, False])
+def test_mls_with_fp32_factors(P, orc, torch, scaling):
+    """MLS transfers (both restriction scalings) with FP32 subdomain factors:
+    the FP64 outer loop still reaches the FP64 oracle's solution."""
+    levels, w = workload("cube20m_3lvl")
+    mu = syn.mu_draw(6)
+    o = make_oracle(levels, w, orc, transfer="mls", restrict_scaling=scaling)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10)
+    h = make_hierarchy(levels, w, P, precision="f32", transfer="mls", restrict_scaling=scaling)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= so["iters"] + 3
 
 
 def test_results_reproducible_bitwise(P, torch):

@@ -21,7 +21,9 @@ Parity status per function (what pins it, tests/test_oracle_pins.py):
                      (numpy BFS neighbourhood, SVD rank, monomial basis, pinv);
                      affine reproduction; Dirichlet handling; nodal-volume
                      scaling (tests/test_oracle_mls_pins.py)
-  V-cycle            dense numpy composition of the same operators on tiny meshes
+  V-cycle            dense numpy composition of the same operators on tiny meshes,
+                     also with the coarsest level RAS-smoothed and for the
+                     one-level RAS preconditioner (tests/test_oracle_alg2_pins.py)
   FGMRES             Krylov least-squares optimality (M = I), direct solve
 Iteration counts of the preconditioned solver: parity unpinned (the paper
 reports counts only for other PDEs and meshes).

@@ -16,8 +16,10 @@
 //   * the transfers are either P (coarse->fine) and P^T (fine->coarse), P the
 //     P1 barycentric interpolation of coarse fields at fine nodes, or the
 //     overlapping MLS operators of Section 3.2 (Eq. 13-15, 24) in both
-//     directions, with the readings stated at build_mls below; the coarsest
-//     level is solved directly, not smoothed;
+//     directions, with the readings stated at build_mls below;
+//   * the coarsest level is solved directly, or (coarse_ras) smoothed like the
+//     others as Algorithm 2 states: nu_pre RAS steps from z = 0; with a single
+//     level that is the one-level RAS preconditioner;
 //   * the smoothing loops of Algorithm 2 run exactly `its` times;
 //   * subdomain solvers are unpivoted LU of each (SPD) subdomain block;
 //   * Dirichlet rows are identity rows, Dirichlet columns are zeroed;
@@ -68,6 +70,7 @@ struct Oracle {
   int load_kind = 0;  // 0: f = 1; 1: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
   int transfer = 0;   // 0: P / P^T; 1: MLS both ways (Section 3.2)
   int restrict_scaling = 1;  // MLS restriction: 1 nodal-volume scaled, 0 plain
+  int coarse_ras = 0;        // 1: the coarsest level is RAS-smoothed (Algorithm 2)
   std::vector<double> mu;
   std::string err;
 };
@@ -618,7 +621,8 @@ void vcycle(const Oracle& o, const double* r0, double* z0) {
     residual(L, r[l].data(), z[l].data(), t.data());
     spmv(L.PT, t.data(), r[l + 1].data());
   }
-  coarse_solve(o.lv[Lc], r[Lc].data(), z[Lc].data());
+  if (o.coarse_ras) smooth(o.lv[Lc], r[Lc].data(), z[Lc].data(), o.nu_pre);  // from z = 0
+  else coarse_solve(o.lv[Lc], r[Lc].data(), z[Lc].data());
   for (int l = Lc - 1; l >= 0; --l) {  // up: prolongate correction, post-smooth
     const Level& L = o.lv[l];
     std::vector<double> pz(L.n);
@@ -744,9 +748,10 @@ typedef struct {
 
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
                  int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
-                 int restrict_scaling) {
+                 int restrict_scaling, int coarse_ras) {
   if (nlevels < 1 || transfer < 0 || transfer > 1) return nullptr;
   Oracle* o = new Oracle();
+  o->coarse_ras = coarse_ras ? 1 : 0;
   o->transfer = transfer;
   o->restrict_scaling = restrict_scaling ? 1 : 0;
   o->delta = delta;
@@ -766,7 +771,7 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
     L.dir.assign(lv[l].dirichlet, lv[l].dirichlet + L.n);
     if (lv[l].owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
     build_pattern(L);
-    if (l + 1 < nlevels) {
+    if (l + 1 < nlevels || o->coarse_ras) {
       if (L.owner.empty()) {
         delete o;
         return nullptr;
@@ -809,7 +814,7 @@ int orc_factor(void* h) {
   int bad = 0;
   for (size_t l = 0; l < o->lv.size(); ++l) {
     Level& L = o->lv[l];
-    if (l + 1 < o->lv.size()) {
+    if (l + 1 < o->lv.size() || o->coarse_ras) {
       int np = (int)L.subs.size();
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
       for (int p = 0; p < np; ++p) bad += factor_sub(L.A, L.subs[p]) ? 1 : 0;
@@ -823,6 +828,7 @@ int orc_factor(void* h) {
 // Factor only the coarsest block.
 int orc_factor_coarsest(void* h) {
   Oracle* o = static_cast<Oracle*>(h);
+  if (o->coarse_ras) return -1;
   Level& L = o->lv.back();
   return factor_sub(L.A, L.coarse) ? -1 : 0;
 }
@@ -873,6 +879,7 @@ int orc_ras_apply_range(void* h, int level, int p0, int p1, const double* r, dou
 
 int orc_coarse_solve(void* h, const double* r, double* z) {
   Oracle* o = static_cast<Oracle*>(h);
+  if (o->coarse_ras) return -1;
   coarse_solve(o->lv.back(), r, z);
   return 0;
 }

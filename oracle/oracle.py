@@ -39,7 +39,7 @@ def lib():
             L = C.CDLL(build())
             vp, ip, dp = C.c_void_p, C.c_int, C.c_double
             L.orc_create.restype = vp
-            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip]
+            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip, ip]
             L.orc_destroy.argtypes = [vp]
             for name in ("orc_assemble",):
                 getattr(L, name).argtypes = [vp, vp]
@@ -89,7 +89,7 @@ class Oracle:
     """One hierarchy + one parameter vector, in the oracle's FP64 arithmetic."""
 
     def __init__(self, levels, delta=1, nu_pre=2, nu_post=2, coef="const", wave=None,
-                 scale=1.0, load="one", transfer="bary", restrict_scaling=True):
+                 scale=1.0, load="one", transfer="bary", restrict_scaling=True, coarse="direct"):
         L = lib()
         self._keep = []
         arr = (_Level * len(levels))()
@@ -104,7 +104,8 @@ class Oracle:
         self._keep.append(w)
         self.h = L.orc_create(arr, len(levels), int(delta), int(nu_pre), int(nu_post),
                               _COEF[coef], _p(w), float(scale), _LOAD[load],
-                              _TRANSFER[transfer], 1 if restrict_scaling else 0)
+                              _TRANSFER[transfer], 1 if restrict_scaling else 0,
+                              {"direct": 0, "ras": 1}[coarse])
         if not self.h:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-mls", action="store_true",
                     help="skip the MLS-transfer variant (Section 3.2) of the same workload")
+    ap.add_argument("--no-literal", action="store_true",
+                    help="skip the paper-literal Algorithm 2 and one-level RAS iteration study")
     ap.add_argument("--batch", type=int, default=4,
                     help="concurrent instances of the batched FP32-factor measurement")
     ap.add_argument("--serve", type=int, default=48,
@@ -207,8 +209,9 @@ def run_msp(args):
     def mu_of(i):
         return syn.mu_draw(rank * 100000 + i)
 
-    def measure(precision, steps, warmup, transfer="bary"):
-        h = P.Hierarchy(levels, precision=precision, transfer=transfer, **kw)
+    def measure(precision, steps, warmup, transfer="bary", lv=None, opts=None):
+        h = P.Hierarchy(levels if lv is None else lv, precision=precision,
+                        **(dict(kw, transfer=transfer) if opts is None else opts))
         inst = h.assemble(mu_of(0), stream=stream)
         n = levels[0].n_nodes
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -430,6 +433,26 @@ def run_msp(args):
                              float(np.linalg.norm(r["x"] - ref) / np.linalg.norm(ref)),
                          "stage_ms_host": r["stage_ms"],
                          "transfer_ms_per_solve": r["kernel_ms"].get("transfer", 0.0)}
+    literal = None
+    if not args.no_literal and args.precision == "f64":
+        # Algorithm 2 as printed: every level RAS-smoothed (the coarsest too,
+        # boxes of the same grid), its = 3, MLS both ways with the interpolated
+        # residual, delta = 1; against one-level RAS with delta = 1
+        lv_all = syn.hierarchy(w["ns"], tuple(w["parts"]) + (w["parts"][-1],))
+        base = dict(coef=w["coef"], wave=syn.wave_vectors(), scale=w["scale"], load=w["load"],
+                    restart=w["restart"], delta=1, coarse="ras")
+        k = max(2, min(args.steps, 4))
+        literal = {"note": "iteration study of Section 4's comparison; FP64; delta = 1"}
+        for tag, lv, o in (
+                ("algorithm2_literal", lv_all, dict(base, nu_pre=3, nu_post=3, transfer="mls",
+                                                    restrict_scaling=False)),
+                ("algorithm2_mls_scaled", lv_all, dict(base, nu_pre=3, nu_post=3, transfer="mls")),
+                ("one_level_ras", lv_all[:1], dict(base, nu_pre=1, nu_post=0))):
+            r = measure("f64", k, 1, lv=lv, opts=o)
+            literal[tag] = {"levels": len(lv), "value": k / (r["ms"] / 1e3), "unit": UNIT,
+                            "steps": k, "iterations_mean": float(np.mean(r["iters"])),
+                            "final_rel_residual_max": float(np.max(r["relres"])),
+                            "stage_ms_host": r["stage_ms"]}
     serving = None
     if args.serve > 0 and world == 1:
         serving = measure_serving(args.serve, args.serve_rate)
@@ -476,6 +499,8 @@ def run_msp(args):
         line["mixed"] = mixed
     if mls:
         line["mls"] = mls
+    if literal:
+        line["paper_literal"] = literal
     if serving:
         line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:

@@ -75,7 +75,8 @@ typedef struct msp_level_desc {
   const uint8_t* dirichlet;   /* [n_nodes] 1 = homogeneous Dirichlet node */
   const int32_t* owner;       /* [n_nodes] partition id of every vertex (Section 2.2:
                                  the non-overlapping subdomains); required on every
-                                 level but the coarsest, ignored there */
+                                 level but the coarsest, and there too with
+                                 MSP_COARSE_RAS (ignored with MSP_COARSE_DIRECT) */
 } msp_level_desc;
 
 typedef void* (*msp_alloc_fn)(void* ctx, size_t bytes, void* stream);
@@ -88,6 +89,15 @@ typedef enum msp_transfer {
   MSP_TRANSFER_MLS = 1    /* overlapping moving-least-squares interpolation in both
                              directions (Section 3.2, Eq. 13-15, 24); see below */
 } msp_transfer;
+
+/* The coarsest level (msp_options.coarse_solver). */
+typedef enum msp_coarse {
+  MSP_COARSE_DIRECT = 0,  /* one interior block, factored and solved exactly (FP64) */
+  MSP_COARSE_RAS = 1      /* RAS-smoothed like the other levels, as Algorithm 2 states:
+                             nu_pre steps from z = 0; the level then needs an owner
+                             array.  With nlevels == 1 and nu_pre == 1 the preconditioner
+                             is one-level RAS (Eq. 7). */
+} msp_coarse;
 
 typedef struct msp_options {
   int32_t delta;              /* overlap: element layers added to each subdomain (>= 0) */
@@ -105,6 +115,7 @@ typedef struct msp_options {
                                  over the tets at node i), and the result multiplied by the
                                  coarse |w|, so that its scale matches the coarse operator;
                                  0: the plain interpolated residual of Algorithm 2 */
+  int32_t coarse_solver;      /* msp_coarse */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
@@ -115,7 +126,7 @@ typedef struct msp_options {
 
 /* Fills *o with the defaults: delta 1, nu 2/2, restart 30, max_it 1000, FP64
  * factors, k = 1, f = 1, barycentric transfers (MLS restriction scaling on),
- * no budget, cudaMalloc. */
+ * direct coarsest solve, no budget, cudaMalloc. */
 MSP_API void msp_default_options(msp_options* o);
 
 typedef struct msp_hierarchy msp_hierarchy;

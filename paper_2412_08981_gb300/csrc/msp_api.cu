@@ -171,8 +171,12 @@ struct msp_instance {
 namespace msp {
 namespace {
 
+// The level solved as one interior block (the coarsest, with MSP_COARSE_DIRECT);
+// it always stays FP64.
+bool direct_level(const msp_hierarchy* h, int l) { return h->host[l].direct; }
+
 bool level_f32(const msp_hierarchy* h, int l) {
-  return h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->dev.size();
+  return h->opt.factor_precision == MSP_F32 && !direct_level(h, l);
 }
 
 void finish_level_stats(const HostLevel& H, DevLevel& D) {
@@ -311,11 +315,11 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
     // the backward sweep holds a row's diagonal tile while the next R_I - I
     // tiles stream in: max_band slots are enough, and never deadlock
-    const bool coarsest = l + 1 == (int)h->host.size();
-    if (coarsest && ((size_t)D.max_nt * 64 + 128) * sizeof(double) > 220u * 1024u)
+    const bool direct = direct_level(h, l);
+    if (direct && ((size_t)D.max_nt * 64 + 128) * sizeof(double) > 220u * 1024u)
       return fail(MSP_ERR_INVALID, "coarsest level too large for the cluster block solve (" +
                                        std::to_string(D.max_nt) + " tiles)");
-    if (!coarsest && (slots < D.max_band || slots < 2))
+    if (!direct && (slots < D.max_band || slots < 2))
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large or " +
                                        "too wide for the staged triangular solve (" +
                                        std::to_string(D.max_nt) + " tiles, band " +
@@ -357,6 +361,10 @@ int check_options(const msp_options& o) {
     return fail(MSP_ERR_INVALID, "unknown factor precision");
   if (o.transfer != MSP_TRANSFER_BARY && o.transfer != MSP_TRANSFER_MLS)
     return fail(MSP_ERR_INVALID, "unknown transfer");
+  if (o.coarse_solver != MSP_COARSE_DIRECT && o.coarse_solver != MSP_COARSE_RAS)
+    return fail(MSP_ERR_INVALID, "unknown coarse solver");
+  if (o.coarse_solver == MSP_COARSE_RAS && o.nu_pre < 1)
+    return fail(MSP_ERR_INVALID, "a smoothed coarsest level needs nu_pre >= 1");
   if (o.coef_kind != MSP_K_CONST && o.coef_kind != MSP_K_COSEXP)
     return fail(MSP_ERR_INVALID, "unknown coefficient family");
   if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
@@ -454,7 +462,7 @@ int factor_all(msp_instance* I) {
 void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream_t s) {
   msp_hierarchy* h = I->h;
   DevLevel& D = h->dev[l];
-  bool coarse = (l + 1 == (int)h->dev.size());
+  const bool coarse = direct_level(h, l);
   int kind = coarse ? PK_COARSE : (l == 0 ? PK_RAS : PK_RAS_COARSER);
   ProfScope ps(I->prof, kind, s);
   size_t es = level_f32(h, l) ? 4 : 8;
@@ -519,8 +527,9 @@ void smooth(msp_instance* I, int l, const double* r, double* z, int its, bool fr
   }
 }
 
-// Algorithm 2 with the level transfers (P^T / P, or MLS both ways) and a
-// direct solve on the coarsest level.
+// Algorithm 2 with the level transfers (P^T / P, or MLS both ways); the
+// coarsest level is solved directly or, with MSP_COARSE_RAS, smoothed nu_pre
+// times from z = 0 like the others.
 void vcycle(msp_instance* I, const double* r0, double* z0, cudaStream_t s) {
   msp_hierarchy* h = I->h;
   const int L = (int)h->dev.size();
@@ -537,7 +546,8 @@ void vcycle(msp_instance* I, const double* r0, double* z0, cudaStream_t s) {
     spmv(I, l, z[l], I->t[l], r[l], SPMV_RESIDUAL, s);
     transfer(I, l, true, I->t[l], I->r[l + 1], SPMV_SET, s);
   }
-  ras(I, L - 1, r[L - 1], z[L - 1], 0, s);
+  if (direct_level(h, L - 1)) ras(I, L - 1, r[L - 1], z[L - 1], 0, s);
+  else smooth(I, L - 1, r[L - 1], z[L - 1], h->opt.nu_pre, true, s);
   for (int l = L - 2; l >= 0; --l) {
     transfer(I, l, false, z[l + 1], z[l], SPMV_ADD, s);
     smooth(I, l, r[l], z[l], h->opt.nu_post, false, s);
@@ -812,6 +822,7 @@ void msp_default_options(msp_options* o) {
   o->load_kind = MSP_F_ONE;
   o->transfer = MSP_TRANSFER_BARY;
   o->restrict_scaling = 1;
+  o->coarse_solver = MSP_COARSE_DIRECT;
 }
 
 const char* msp_last_error(void) { return msp::g_last_error.c_str(); }
@@ -880,7 +891,7 @@ int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) 
   info->n_nodes = H.n;
   info->n_tets = H.m;
   info->nnz = (int64_t)H.col.size();
-  info->n_sub = H.coarsest ? 0 : H.nsub;
+  info->n_sub = H.direct ? 0 : H.nsub;
   info->sub_dofs = H.sub_ptr.empty() ? 0 : H.sub_ptr.back();
   info->factor_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
   info->P_nnz = (int64_t)H.P_col.size();
@@ -986,12 +997,13 @@ int msp_apply_op(msp_instance* I, int op, int level, const double* x, double* y,
       transfer(I, level, true, x, y, SPMV_SET, s);
       break;
     case MSP_OP_RAS:
-      if (level + 1 >= L) return fail(MSP_ERR_INVALID, "the coarsest level is solved, not smoothed");
+      if (direct_level(h, level)) return fail(MSP_ERR_INVALID, "the coarsest level is solved, not smoothed");
       if (!I->factored) return fail(MSP_ERR_INVALID, "instance not factored");
       ras(I, level, x, y, 0, s);
       break;
     case MSP_OP_COARSE:
-      if (level != L - 1) return fail(MSP_ERR_INVALID, "MSP_OP_COARSE needs the coarsest level");
+      if (level != L - 1 || !direct_level(h, level))
+        return fail(MSP_ERR_INVALID, "MSP_OP_COARSE needs the directly solved coarsest level");
       if (!I->factored) return fail(MSP_ERR_INVALID, "instance not factored");
       ras(I, level, x, y, 0, s);
       break;
@@ -1109,7 +1121,7 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
     src = I->val[level];
     bytes = (size_t)D.nnz * sizeof(double);
   } else if (what == MSP_ARR_FACTOR) {
-    bool coarse = level + 1 == (int)h->dev.size();
+    const bool coarse = direct_level(h, level);
     int p = coarse ? 0 : sub;
     if (p < 0 || p >= H.nsub || (coarse && sub != -1 && sub != 0))
       return fail(MSP_ERR_INVALID, "subdomain out of range");

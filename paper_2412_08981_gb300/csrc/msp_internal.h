@@ -43,7 +43,7 @@ struct HostLevel {
 
   // subdomains (Section 2.2) on smoothed levels; one block of all interior
   // DoFs on the coarsest level
-  bool coarsest = false;
+  bool direct = false;  // solved as one interior block (the coarsest, MSP_COARSE_DIRECT)
   int nsub = 0;
   std::vector<int32_t> sub_ptr;         // [nsub+1] offsets into sub_dofs
   std::vector<int32_t> sub_dofs;        // sorted DoFs of each subdomain

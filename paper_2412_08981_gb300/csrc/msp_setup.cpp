@@ -734,7 +734,8 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
   if (nlevels < 1) return "nlevels must be >= 1";
   out.assign(nlevels, HostLevel());
   for (int l = 0; l < nlevels; ++l) {
-    std::string e = check_level(lv[l], l, l + 1 < nlevels);
+    const bool need_owner = l + 1 < nlevels || o.coarse_solver == MSP_COARSE_RAS;
+    std::string e = check_level(lv[l], l, need_owner);
     if (!e.empty()) return e;
     HostLevel& L = out[l];
     L.n = lv[l].n_nodes;
@@ -745,14 +746,14 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     for (int i = 0; i < L.n; ++i) L.dir[i] = lv[l].dirichlet[i] ? 1 : 0;
     for (int i = 0; i < L.n; ++i)
       if (L.dir[i]) L.dir_list.push_back(i);
-    if (l + 1 < nlevels) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
+    if (need_owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
     build_pattern_and_contribs(L);
     for (int i = 0; i < L.n; ++i)
       if (L.diag[i] < 0) return "level " + std::to_string(l) + ": node " + std::to_string(i) + " belongs to no tet";
-    L.coarsest = (l + 1 == nlevels);
-    if (L.coarsest) build_coarsest_block(L);
+    L.direct = (l + 1 == nlevels) && o.coarse_solver == MSP_COARSE_DIRECT;
+    if (L.direct) build_coarsest_block(L);
     else build_subdomains(L, o.delta);
-    if (L.sub_ptr[L.nsub] == 0 && L.coarsest && L.n > (int)L.dir_list.size())
+    if (L.sub_ptr[L.nsub] == 0 && L.direct && L.n > (int)L.dir_list.size())
       return "internal: empty coarsest block";
     build_factor_layout(L);
   }

@@ -23,6 +23,7 @@ MSP_F64, MSP_F32 = 0, 1
 MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
+MSP_COARSE_DIRECT, MSP_COARSE_RAS = 0, 1
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
@@ -62,7 +63,8 @@ class msp_options(C.Structure):
                 ("restart", C.c_int32), ("max_it", C.c_int32), ("factor_precision", C.c_int32),
                 ("coef_kind", C.c_int32), ("wave", (C.c_int32 * 3) * 8),
                 ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("transfer", C.c_int32),
-                ("restrict_scaling", C.c_int32), ("host_only", C.c_int32),
+                ("restrict_scaling", C.c_int32), ("coarse_solver", C.c_int32),
+                ("host_only", C.c_int32),
                 ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
                 ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
 
@@ -219,7 +221,7 @@ class Hierarchy:
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
                  max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
                  load="one", host_only=False, budget_bytes=0, torch_alloc=True,
-                 transfer="bary", restrict_scaling=True):
+                 transfer="bary", restrict_scaling=True, coarse="direct"):
         lib = _load_library()
         self._keep = []
         arr = (msp_level_desc * len(levels))()
@@ -239,6 +241,7 @@ class Hierarchy:
                             load_kind={"one": MSP_F_ONE, "sines": MSP_F_SINES}[load],
                             transfer={"bary": MSP_TRANSFER_BARY, "mls": MSP_TRANSFER_MLS}[transfer],
                             restrict_scaling=1 if restrict_scaling else 0,
+                            coarse_solver={"direct": MSP_COARSE_DIRECT, "ras": MSP_COARSE_RAS}[coarse],
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))
         if wave is not None:

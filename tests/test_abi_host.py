@@ -93,6 +93,29 @@ def test_host_mls_transfers_match_oracle(P, orc, name, scaling):
         assert info["P_nnz"] == o.get("P_col", l).size and info["R_nnz"] == o.get("PT_col", l).size
 
 
+def test_host_smoothed_coarsest_matches_oracle(P, orc):
+    """MSP_COARSE_RAS: the coarsest level gets overlapping subdomains like the
+    others (and needs an owner array)."""
+    levels = syn.hierarchy((12, 6, 4), ((3, 3, 3), (3, 3, 3), (2, 2, 2)))
+    h = P.Hierarchy(levels, delta=1, host_only=True, coarse="ras", transfer="mls",
+                    restrict_scaling=False)
+    o = orc.Oracle(levels, delta=1, coarse="ras", transfer="mls", restrict_scaling=False)
+    for l in range(3):
+        subs = o.subdomains(l)
+        sp_, sd = h.array(l, "sub_ptr"), h.array(l, "sub_dofs")
+        assert sp_.size - 1 == len(subs) and h.info(l)["n_sub"] == len(subs)
+        for p, (d, _) in enumerate(subs):
+            np.testing.assert_array_equal(sd[sp_[p]:sp_[p + 1]], d)
+    for l in range(2):
+        for a in ("P_col", "PT_col"):
+            np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+    bare = [levels[0], levels[1], syn.cube_level(4, 99)]
+    with pytest.raises(P.MspError):
+        P.Hierarchy(bare, host_only=True, coarse="ras")
+    with pytest.raises(P.MspError):
+        P.Hierarchy(levels, host_only=True, coarse="ras", nu_pre=0)
+
+
 def test_odd_partition_and_empty_boxes(P, orc):
     """Partition ids that skip values and boxes with only Dirichlet nodes."""
     fine = syn.cube_level(9, 3, parts=(5, 3, 2))

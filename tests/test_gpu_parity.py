@@ -315,6 +315,68 @@ def test_mls_with_fp32_factors(P, orc, torch, scaling):
     assert st["iterations"] <= so["iters"] + 3
 
 
+# ------------------------------------------- paper-literal Algorithm 2 options
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_paper_literal_algorithm2(P, orc, torch, precision):
+    """Every level RAS-smoothed (the coarsest too, its = 3), MLS both ways with
+    the interpolated residual, delta = 1: V-cycle and solution vs the oracle."""
+    levels = syn.hierarchy((16, 8, 4), ((4, 4, 4), (4, 4, 4), (2, 2, 2)))
+    kw = dict(delta=1, nu_pre=3, nu_post=3, coef="cosexp", wave=syn.wave_vectors(), load="one",
+              transfer="mls", restrict_scaling=False, coarse="ras")
+    mu = syn.mu_draw(21)
+    o = orc.Oracle(levels, **kw)
+    o.assemble(mu)
+    o.factor()
+    h = P.Hierarchy(levels, precision=precision, **kw)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    n = levels[0].n_nodes
+    if precision == "f64":
+        r = np.random.default_rng(22).normal(size=n)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        inst.apply(torch.tensor(r, device="cuda"), z)
+        torch.cuda.synchronize()
+        assert rel(z.cpu().numpy(), o.vcycle(r)) <= OP_TOL
+        # the coarsest level is a RAS level now: its smoother matches the oracle's
+        rc = np.random.default_rng(23).normal(size=levels[2].n_nodes)
+        zc = torch.zeros(levels[2].n_nodes, dtype=torch.float64, device="cuda")
+        inst.apply_op(P.msp.MSP_OP_RAS, 2, torch.tensor(rc, device="cuda"), zc)
+        torch.cuda.synchronize()
+        assert rel(zc.cpu().numpy(), o.ras_apply(rc, 2)) <= OP_TOL
+        with pytest.raises(P.MspError):
+            inst.apply_op(P.msp.MSP_OP_COARSE, 2, torch.tensor(rc, device="cuda"), zc)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    xo, so = o.fgmres(rtol=1e-10)
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert abs(st["iterations"] - so["iters"]) <= (1 if precision == "f64" else 3)
+
+
+def test_one_level_ras(P, orc, torch):
+    """A single level with the coarsest smoothed once: one-level RAS (Eq. 7)."""
+    lv = syn.cube_level(16, 31, parts=(4, 4, 4))
+    kw = dict(delta=1, nu_pre=1, nu_post=0, coef="cosexp", wave=syn.wave_vectors(), load="one",
+              coarse="ras")
+    mu = syn.mu_draw(24)
+    o = orc.Oracle([lv], **kw)
+    o.assemble(mu)
+    o.factor()
+    h = P.Hierarchy([lv], **kw)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    r = np.random.default_rng(25).normal(size=lv.n_nodes)
+    z = torch.zeros(lv.n_nodes, dtype=torch.float64, device="cuda")
+    inst.apply(torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), o.ras_apply(r, 0)) <= OP_TOL
+    x = torch.zeros_like(z)
+    st = inst.solve(x, rtol=1e-10)
+    xo, so = o.fgmres(rtol=1e-10)
+    assert st["status"] == 0 and rel(x.cpu().numpy(), xo) <= 1e-7
+    assert abs(st["iterations"] - so["iters"]) <= 1
+
+
 def test_results_reproducible_bitwise(P, torch):
     levels, w = workload("cube16_3lvl")
     h = make_hierarchy(levels, w, P)

@@ -50,8 +50,13 @@ typedef enum msp_status {
 } msp_status;
 
 /* Precision of the subdomain LU factors and their triangular solves.  The
- * outer FGMRES, every SpMV, the transfers and the coarsest level stay FP64. */
-typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1 } msp_precision;
+ * outer FGMRES, every SpMV, the transfers and the directly solved coarsest
+ * level stay FP64.
+ *   MSP_F64 : factorisation and solves in FP64
+ *   MSP_F32 : factorisation, storage and solves in FP32
+ *   MSP_BF16: factorisation in FP32, factors rounded (to nearest even) to BF16
+ *             for storage; the solves read BF16 and accumulate in FP32 */
+typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1, MSP_BF16 = 2 } msp_precision;
 
 /* Coefficient family k(x; mu), evaluated at each tet centroid x_c:
  *   MSP_K_CONST : k = 1
@@ -316,7 +321,7 @@ MSP_API int msp_instance_copy(const msp_instance* inst, int level, int what, int
  * recorded around each launch on the launching stream. */
 typedef enum msp_kernel_class {
   MSP_PK_ASSEMBLE = 0,     /* coefficient + assembly of J(mu), every level */
-  MSP_PK_EXTRACT = 1,      /* dense subdomain blocks from CSR */
+  MSP_PK_EXTRACT = 1,      /* dense subdomain blocks from CSR; BF16 rounding of the factors */
   MSP_PK_LDLT_DIAG = 2,    /* diagonal tile factorisation */
   MSP_PK_LDLT_PANEL = 3,   /* panel solves */
   MSP_PK_LDLT_TRAIL = 4,   /* trailing (Schur complement) updates */
@@ -341,6 +346,16 @@ typedef struct msp_kernel_profile {
 MSP_API int msp_profile_enable(msp_instance* inst, uint32_t class_mask);
 MSP_API int msp_profile_reset(msp_instance* inst);
 MSP_API int msp_profile_read(msp_instance* inst, int kclass, msp_kernel_profile* out);
+
+/* ---- tensor-core self-check (no counterpart in the paper) ----
+ * Multiplies two fixed 128 x 64 BF16 matrices with integer entries on the
+ * current device through the library's tcgen05 path (operands in shared
+ * memory, FP32 accumulators in tensor memory) and compares every one of the
+ * 128 x 128 results bit for bit with the exact integer product computed on
+ * the host.  *mismatches (may be NULL) receives the number of differing
+ * entries.  Returns MSP_OK, MSP_ERR_INTERNAL (a mismatch), MSP_ERR_TIMEOUT
+ * (the bounded wait for the MMA expired), MSP_ERR_CUDA or MSP_ERR_OOM. */
+MSP_API int msp_tensor_selftest(int* mismatches);
 
 /* ---- allocation-free multi-vector dot product ----
  * No counterpart in the paper: a library convenience for callers that may not

@@ -23,7 +23,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
             "--expt-relaxed-constexpr",
             "-I" + INCLUDE, "-I" + CSRC] + ARCH
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-I" + INCLUDE, "-I" + CSRC,
+# no FMA contraction in host set-up code: the same weights on x86 and on Arm
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-ffp-contract=off",
+             "-I" + INCLUDE, "-I" + CSRC,
              "-I/usr/local/cuda/include"]
 
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmsp.so")
 MSP_OK, MSP_PENDING = 0, 1
 MSP_ERR_INVALID, MSP_ERR_OOM, MSP_ERR_NOT_CONVERGED = -1, -2, -3
 MSP_ERR_TIMEOUT, MSP_ERR_CUDA, MSP_ERR_INTERNAL = -4, -5, -6
-MSP_F64, MSP_F32 = 0, 1
+MSP_F64, MSP_F32, MSP_BF16 = 0, 1, 2
 MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
@@ -96,6 +96,7 @@ _lib = None
 
 EXPORTS = {
     "msp_default_options": (None, [C.POINTER(msp_options)]),
+    "msp_tensor_selftest": (C.c_int, [C.POINTER(C.c_int)]),
     "msp_last_error": (C.c_char_p, []),
     "msp_version": (C.c_char_p, []),
     "msp_load_hierarchy": (C.c_int, [C.POINTER(msp_level_desc), C.c_int, C.POINTER(msp_options),
@@ -235,7 +236,8 @@ class Hierarchy:
                                     dr.ctypes.data, None if ow is None else ow.ctypes.data)
         o = default_options(delta=int(delta), nu_pre=int(nu_pre), nu_post=int(nu_post),
                             restart=int(restart), max_it=int(max_it),
-                            factor_precision={"f64": MSP_F64, "f32": MSP_F32}[precision],
+                            factor_precision={"f64": MSP_F64, "f32": MSP_F32,
+                                              "bf16": MSP_BF16}[precision],
                             coef_kind={"const": MSP_K_CONST, "cosexp": MSP_K_COSEXP}[coef],
                             coef_scale=float(scale),
                             load_kind={"one": MSP_F_ONE, "sines": MSP_F_SINES}[load],
@@ -342,6 +344,11 @@ class Instance:
         return {k: getattr(st, k) for k, _ in msp_stats._fields_}
 
     def array(self, level, name, sub=0, dtype=np.float64) -> np.ndarray:
+        """Copy an instance array to the host.  BF16 factors: dtype="bf16"
+        returns them widened exactly to float32."""
+        if isinstance(dtype, str) and dtype == "bf16":
+            u = self.array(level, name, sub, np.uint16)
+            return (u.astype(np.uint32) << 16).view(np.float32)
         lib = load()
         nb = C.c_size_t(0)
         _check(lib.msp_instance_copy(self.inst, level, ARRAYS[name], sub, None, 0, C.byref(nb)))
@@ -453,3 +460,11 @@ def unpack_factor(flat: np.ndarray, n: int, first: np.ndarray):
     d = np.diag(full).copy()
     L = np.tril(full, -1) + np.eye(N)
     return L[:n, :n], d[:n]
+
+
+def tensor_selftest() -> int:
+    """msp_tensor_selftest: the tcgen05 product check; returns the number of
+    mismatching entries (0), raises MspError on failure."""
+    bad = C.c_int(-1)
+    _check(load().msp_tensor_selftest(C.byref(bad)))
+    return bad.value

@@ -404,6 +404,17 @@ def run_msp(args):
                  "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"],
                  "final_rel_residual_max": float(np.max(mres["relres"])),
                  "stage_ms_host": mres["stage_ms"], "kernel_ms_per_solve": mres["kernel_ms"]}
+        bres16 = measure("bf16", args.steps, args.warmup)
+        b16 = args.steps / (bres16["ms"] / 1e3)
+        mixed["bf16"] = {
+            "precision": "BF16 subdomain factors (factored in FP32, rounded to nearest even), FP32 "
+                         "accumulation in the solves, FP64 outer loop/SpMV/coarsest",
+            "value": b16, "unit": UNIT, "speedup_vs_f64": b16 / value,
+            "iterations_mean": float(np.mean(bres16["iters"])),
+            "rel_diff_vs_f64_solution": float(np.linalg.norm(bres16["x"] - res["x"]) /
+                                              np.linalg.norm(res["x"])),
+            "final_rel_residual_max": float(np.max(bres16["relres"])),
+            "stage_ms_host": bres16["stage_ms"], "kernel_ms_per_solve": bres16["kernel_ms"]}
         if args.batch > 1:
             bres = measure_batched("f32", max(args.steps, 2 * args.batch), args.warmup, args.batch)
             bval = bres["value"]

@@ -19,6 +19,7 @@
 // fast FP64 tensor path), so the FP64 kernels are ALU-bound: their design
 // keeps the FMA pipe fed from shared memory and avoids idle lanes.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +36,7 @@ constexpr int TE = T64 * T64;
 
 template <typename T> struct Acc { using type = double; };
 template <> struct Acc<float> { using type = float; };
+template <> struct Acc<__nv_bfloat16> { using type = float; };  // BF16 storage, FP32 arithmetic
 
 // 1/d by Newton's method for the reciprocal (x <- x + x (1 - d x), which
 // doubles the correct bits per step) from a single-precision seed: two steps
@@ -880,6 +882,11 @@ DevLimits& limits() {
 }
 }  // namespace
 
+// Ring depth of the staged solve: as many tile slots as shared memory holds,
+// up to 16 (BF16 and FP32 tiles are small; more bytes in flight per SM hide
+// more of the HBM latency).
+constexpr size_t kMaxSlots = 16;
+
 template <typename T>
 int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
@@ -888,7 +895,7 @@ int ras_slots(int max_nt) {
   const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
   const size_t smem = (size_t)limits().smem;
   if (smem <= fixed) return 0;
-  return (int)std::min<size_t>(8, (smem - fixed) / per_slot);
+  return (int)std::min<size_t>(kMaxSlots, (smem - fixed) / per_slot);
 }
 
 template <typename T>
@@ -990,5 +997,31 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
                                               const double*, double*, int, cudaStream_t);
 MSP_INST(double)
 MSP_INST(float)
+// BF16 factors: only the solve reads them (they are factored in FP32)
+template void launch_ras_solve<__nv_bfloat16>(const __nv_bfloat16*, const EnvDev&, const int32_t*,
+                                              const int32_t*, int, const int32_t*, const int32_t*,
+                                              const uint8_t*, int, const int32_t*, int,
+                                              const double*, double*, int, int*, cudaStream_t);
+template int ras_slots<__nv_bfloat16>(int);
+
+// ------------------------------------------------- BF16 storage of factors
+// dst = bf16(src), round to nearest even; n a multiple of 4 (whole tiles).
+__global__ void k_round_bf16(const float4* __restrict__ src, __nv_bfloat162* __restrict__ dst,
+                             int64_t n4) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = src[i];
+    dst[2 * i] = __floats2bfloat162_rn(v.x, v.y);
+    dst[2 * i + 1] = __floats2bfloat162_rn(v.z, v.w);
+  }
+}
+
+void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t n4 = n / 4;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n4 + 255) / 256, (int64_t)limits().nsm * 8));
+  k_round_bf16<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(src),
+                                    reinterpret_cast<__nv_bfloat162*>(dst), n4);
+}
 
 }  // namespace msp

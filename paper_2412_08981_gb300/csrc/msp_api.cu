@@ -155,7 +155,8 @@ struct msp_instance {
   size_t charged = 0;
   double* mu = nullptr;
   std::vector<double*> k, val, r, z, t;
-  std::vector<void*> fac;  // per level, T = double or float
+  std::vector<void*> fac;   // per level: double, float or BF16 (level_store)
+  std::vector<float*> work;  // per BF16 level: the FP32 factorisation, rounded into fac
   int* info = nullptr;
   int* ras_err = nullptr;  // bit 4: a bounded wait of the staged RAS solve expired
   int m = 30;
@@ -175,9 +176,17 @@ namespace {
 // it always stays FP64.
 bool direct_level(const msp_hierarchy* h, int l) { return h->host[l].direct; }
 
-bool level_f32(const msp_hierarchy* h, int l) {
-  return h->opt.factor_precision == MSP_F32 && !direct_level(h, l);
+// Storage of a level's factors (the directly solved level is always FP64).
+enum class Store { F64, F32, BF16 };
+Store level_store(const msp_hierarchy* h, int l) {
+  if (direct_level(h, l)) return Store::F64;
+  if (h->opt.factor_precision == MSP_F32) return Store::F32;
+  if (h->opt.factor_precision == MSP_BF16) return Store::BF16;
+  return Store::F64;
 }
+size_t store_bytes(Store t) { return t == Store::F64 ? 8 : (t == Store::F32 ? 4 : 2); }
+// factored in FP32 (F32 and BF16 levels)
+bool level_f32(const msp_hierarchy* h, int l) { return level_store(h, l) != Store::F64; }
 
 void finish_level_stats(const HostLevel& H, DevLevel& D) {
   D.max_nt = 0;
@@ -292,8 +301,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     // (diagonal 1, panel 1, trailing pair 2, diagonal pair 1)
     D.fac_blocks = H.nsub >= std::max(2, nsm / 2);
     if (D.fac_blocks) {
-      const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
-      const int per_sm = f32 ? ldlt_blocks_per_sm<float>() : ldlt_blocks_per_sm<double>();
+      const int per_sm = level_f32(h, l) ? ldlt_blocks_per_sm<float>() : ldlt_blocks_per_sm<double>();
       for (int p = 0; p < H.nsub; ++p) {
         const int32_t* R = &H.tile_last[H.sub_trow[p]];
         int64_t c = 0;
@@ -311,8 +319,10 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   }
   {
-    const bool f32 = h->opt.factor_precision == MSP_F32 && l + 1 < (int)h->host.size();
-    const int slots = f32 ? ras_slots<float>(D.max_nt) : ras_slots<double>(D.max_nt);
+    const Store st = level_store(h, l);
+    const int slots = st == Store::F64 ? ras_slots<double>(D.max_nt)
+                      : st == Store::F32 ? ras_slots<float>(D.max_nt)
+                                         : ras_slots<__nv_bfloat16>(D.max_nt);
     // the backward sweep holds a row's diagonal tile while the next R_I - I
     // tiles stream in: max_band slots are enough, and never deadlock
     const bool direct = direct_level(h, l);
@@ -357,7 +367,7 @@ int check_options(const msp_options& o) {
     return fail(MSP_ERR_INVALID, "nu out of range");
   if (o.restart < 1 || o.restart > 256) return fail(MSP_ERR_INVALID, "restart out of range");
   if (o.max_it < 1) return fail(MSP_ERR_INVALID, "max_it must be >= 1");
-  if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32)
+  if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32 && o.factor_precision != MSP_BF16)
     return fail(MSP_ERR_INVALID, "unknown factor precision");
   if (o.transfer != MSP_TRANSFER_BARY && o.transfer != MSP_TRANSFER_MLS)
     return fail(MSP_ERR_INVALID, "unknown transfer");
@@ -442,8 +452,17 @@ int factor_all(msp_instance* I) {
   for (int a = 0; a < 2; ++a) MSP_CUDA(cudaStreamWaitEvent(I->aux[a], I->fork, 0));
   for (int l = L - 1; l >= 0; --l) {
     cudaStream_t s = (l == 0) ? I->stream : (l == L - 1 ? I->aux[0] : I->aux[1]);
-    if (level_f32(h, l)) factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
-    else factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
+    const Store st = level_store(h, l);
+    if (st == Store::F64) {
+      factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
+    } else if (st == Store::F32) {
+      factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
+    } else {
+      factor_level<float>(I, l, I->work[l], s);
+      ProfScope ps(I->prof, PK_EXTRACT, s);
+      launch_round_bf16(I->work[l], static_cast<__nv_bfloat16*>(I->fac[l]), h->dev[l].fac_elems, s);
+      ps.account((double)h->dev[l].fac_elems * 6, 0);
+    }
   }
   for (int a = 0; a < 2; ++a) {
     MSP_CUDA(cudaEventRecord(I->join[a], I->aux[a]));
@@ -465,11 +484,16 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   const bool coarse = direct_level(h, l);
   int kind = coarse ? PK_COARSE : (l == 0 ? PK_RAS : PK_RAS_COARSER);
   ProfScope ps(I->prof, kind, s);
-  size_t es = level_f32(h, l) ? 4 : 8;
+  const Store st = level_store(h, l);
+  size_t es = store_bytes(st);
   if (coarse) {  // one block: both sweeps split over a cluster of CTAs
     launch_block_solve_cluster<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr,
                                        D.sub_dofs, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
-  } else if (level_f32(h, l))
+  } else if (st == Store::BF16)
+    launch_ras_solve<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                                    D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
+                                    D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, s);
+  else if (st == Store::F32)
     launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
                             D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
                             D.dir_list, D.ndir, t, z, add, I->ras_err, s);
@@ -729,6 +753,7 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
   I->z.resize(L);
   I->t.resize(L);
   I->fac.resize(L);
+  I->work.assign(L, nullptr);
   for (int l = 0; l < L; ++l) {
     DevLevel& D = h->dev[l];
     I->k[l] = A.alloc<double>(D.m);
@@ -736,8 +761,15 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     I->r[l] = A.alloc<double>(D.n);
     I->z[l] = A.alloc<double>(D.n);
     I->t[l] = A.alloc<double>(D.n);
-    if (level_f32(h, l)) I->fac[l] = A.alloc<float>(D.fac_elems);
-    else I->fac[l] = A.alloc<double>(D.fac_elems);
+    const Store st = level_store(h, l);
+    if (st == Store::F64) {
+      I->fac[l] = A.alloc<double>(D.fac_elems);
+    } else if (st == Store::F32) {
+      I->fac[l] = A.alloc<float>(D.fac_elems);
+    } else {
+      I->fac[l] = A.alloc<__nv_bfloat16>(D.fac_elems);
+      I->work[l] = A.alloc<float>(D.fac_elems);
+    }
   }
   I->m = h->opt.restart;
   const int64_t n = h->dev[0].n;
@@ -789,7 +821,7 @@ size_t instance_need(const msp_hierarchy* h) {
   for (size_t l = 0; l < h->dev.size(); ++l) {
     const DevLevel& D = h->dev[l];
     need += (size_t)D.m * 8 + (size_t)D.nnz * 8 + (size_t)D.n * 24 +
-            (size_t)D.fac_elems * (level_f32(h, (int)l) ? 4 : 8);
+            (size_t)D.fac_elems * (level_store(h, (int)l) == Store::BF16 ? 6 : store_bytes(level_store(h, (int)l)));
   }
   need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
   return need;
@@ -1125,7 +1157,7 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
     int p = coarse ? 0 : sub;
     if (p < 0 || p >= H.nsub || (coarse && sub != -1 && sub != 0))
       return fail(MSP_ERR_INVALID, "subdomain out of range");
-    size_t es = level_f32(h, level) ? 4 : 8;
+    size_t es = store_bytes(level_store(h, level));
     src = static_cast<const char*>(I->fac[level]) + (size_t)H.sub_fac_off[p] * es;
     bytes = (size_t)(H.sub_fac_off[p + 1] - H.sub_fac_off[p]) * es;
   } else {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace msp {
@@ -74,6 +75,9 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
 // CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
 // longest-first balanced assignment built on the host); a bounded mbarrier
 // wait that expires sets bit 4 of *err.  The factor tiles stream through
+// BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
+// n a multiple of 4.
+void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);
 // ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
 // diagonal tile while it reads that tile column, so there must be at least
 // 1 + (R_I - I) slots for every row I of the level (checked on the host at

@@ -315,6 +315,49 @@ def test_mls_with_fp32_factors(P, orc, torch, scaling):
     assert st["iterations"] <= so["iters"] + 3
 
 
+def _bf16_rne(f32):
+    """Round float32 to BF16 (nearest, ties to even) as uint16, numpy only."""
+    u = np.ascontiguousarray(f32, np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def test_bf16_factors(P, orc, torch):
+    """BF16 factor storage (factored in FP32, rounded to nearest even), FP32
+    accumulation in the solves, FP64 outer loop: the solution still matches
+    the FP64 oracle's; the stored factors are exactly the rounded FP32 ones."""
+    levels, w = workload("cube16_3lvl")
+    mu = syn.mu_draw(2)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10)
+    h = make_hierarchy(levels, w, P, precision="bf16")
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= 4 * so["iters"] + 4
+    # the stored factor of every sampled block = RNE(FP32 factor)
+    h32 = make_hierarchy(levels, w, P, precision="f32")
+    i32 = h32.assemble(mu, stream=torch.cuda.current_stream())
+    i32.factor()
+    for l in range(len(levels) - 1):
+        ns = o.get("n_subs", l)
+        for p in sorted({0, ns // 2, ns - 1}):
+            f32 = i32.array(l, "factor", p, dtype=np.float32)
+            b16 = inst.array(l, "factor", p, dtype=np.uint16)
+            np.testing.assert_array_equal(b16, _bf16_rne(f32))
+    # the smoother really runs on BF16 data
+    r = np.random.default_rng(6).normal(size=levels[0].n_nodes)
+    z = torch.zeros_like(x)
+    inst.apply_op(P.msp.MSP_OP_RAS, 0, torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    d = rel(z.cpu().numpy(), o.ras_apply(r, 0))
+    assert 1e-6 < d < 0.5, d
+
+
 # ------------------------------------------- paper-literal Algorithm 2 options
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_paper_literal_algorithm2(P, orc, torch, precision):

@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "msp_kernels.h"
+#include "msp_tc.cuh"
 
 namespace msp {
 namespace {
@@ -403,6 +404,136 @@ __global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev
                             fac + tile_at(E, p, i, j), i == j, sm);
     }
   }
+}
+
+// ------------------------------- whole-block factorisation, BF16 tensor cores
+// The persistent factorisation for BF16 factors: diagonal tile and panel as
+// in k_ldlt_blocks (FP32), the trailing update C_ij -= (L_ik D_k) L_jk^T on
+// the tensor cores.  Tile rows k+1..R of the step are taken two at a time
+// (M = 128) against two tile columns at a time (N = 128): the operands are
+// rounded to BF16 into shared memory (K-major, no swizzle; a missing second
+// tile is zero-filled), four K = 16 MMAs accumulate in FP32 in tensor memory
+// (128 lanes x 128 columns per CTA), and the epilogue subtracts the
+// accumulator from the FP32 working tiles: warp w reads lanes 32 (w % 4) ..
+// of column half w / 4, one thread per row of one 64 x 64 output tile.  Only
+// tiles with j <= i are written, and on the diagonal only c <= r.
+constexpr int kTcCols = 128;                  // tensor-memory columns per CTA
+constexpr int kTcSmem = 48 * 1024;           // >= every phase; keeps <= 4 CTAs per SM
+constexpr int kTcSlab = 128 * 64 * 2;         // one 128 x 64 BF16 operand
+constexpr int kTcBarOff = kTcSmem - 64;       // mbarrier + TMEM base address slot
+
+// rows row0..row0+63 of a K-major BF16 slab = bf16(tile[r][k] * scale[k])
+// (scale may be null); tile == null writes zeros.
+__device__ void stage_bf16(unsigned char* slab, int row0, const float* __restrict__ tile,
+                           const float* __restrict__ scale) {
+  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+    const int r = e >> 5, k = (e & 31) * 2;
+    float2 v = make_float2(0.f, 0.f);
+    if (tile) {
+      v = *reinterpret_cast<const float2*>(tile + r * 64 + k);
+      if (scale) {
+        v.x *= scale[k];
+        v.y *= scale[k + 1];
+      }
+    }
+    *reinterpret_cast<__nv_bfloat162*>(slab + tc::kmajor_offset(row0 + r, k)) = __floats2bfloat162_rn(v.x, v.y);
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ fac, EnvDev E,
+                                                           const int32_t* __restrict__ cta_ptr,
+                                                           const int32_t* __restrict__ cta_list,
+                                                           int* __restrict__ info) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float* sm = reinterpret_cast<float*>(smraw);
+  unsigned char* sA = smraw;                // W rows of the two output tile rows
+  unsigned char* sB = smraw + kTcSlab;      // L rows of the two output tile columns
+  float* dk = reinterpret_cast<float*>(smraw + 2 * kTcSlab);  // D of the step
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + kTcBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smraw + kTcBarOff + 16);
+  const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
+  if (q0 >= q1) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, kTcCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(bar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int q = q0; q < q1; ++q) {
+    const int p = cta_list[q];
+    const int NT = E.nt[p];
+    for (int k = 0; k < NT; ++k) {
+      const int R = E.last[E.trow[p] + k];
+      float* dt = fac + tile_at(E, p, k, k);
+      diag_tile<float, float>(dt, sm, info);
+      for (int i = k + 1; i <= R; ++i) panel_tile<float, float>(dt, fac + tile_at(E, p, i, k), sm);
+      if (R == k) continue;
+      __syncthreads();
+      if (tid < 64) dk[tid] = dt[tid * 65];
+      __syncthreads();
+      for (int i0 = k + 1; i0 <= R; i0 += 2) {
+        const int i1 = i0 + 1;
+        stage_bf16(sA, 0, fac + tile_at(E, p, i0, k), dk);
+        stage_bf16(sA, 64, i1 <= R ? fac + tile_at(E, p, i1, k) : nullptr, dk);
+        for (int j0 = k + 1; j0 <= i0; j0 += 2) {
+          const int j1 = j0 + 1;
+          stage_bf16(sB, 0, fac + tile_at(E, p, j0, k), nullptr);
+          stage_bf16(sB, 64, j1 <= R ? fac + tile_at(E, p, j1, k) : nullptr, nullptr);
+          tc::fence_async_smem();
+          tc::fence_before();
+          __syncthreads();
+          tc::fence_after();
+          if (tid == 0) {
+#pragma unroll
+            for (int st = 0; st < 4; ++st)
+              tc::mma_bf16(taddr, tc::sdesc(sA + 256 * st), tc::sdesc(sB + 256 * st), idesc, st > 0);
+            tc::commit(bar);
+          }
+          if (!tc::mbar_wait_bounded(bar, phase, failed ? 64 : (1L << 22))) {
+            failed = true;
+            if (lane == 0) atomicOr(info, 2);
+          }
+          phase ^= 1;
+          tc::fence_after();
+          // epilogue: this thread's row r of the 128 accumulator rows, column half h
+          const int qd = warp & 3, h = warp >> 2;
+          const int r = 32 * qd + lane;
+          const int ti = r < 64 ? i0 : i1, tj = h ? j1 : j0, ri = r & 63;
+          const bool valid = ti <= R && tj <= R && tj <= ti;
+          float* crow = valid ? fac + tile_at(E, p, ti, tj) + ri * 64 : nullptr;
+#pragma unroll
+          for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(64 * h + c0), v);
+            if (valid) {
+#pragma unroll
+              for (int u = 0; u < 16; u += 4) {
+                float4 cv = *reinterpret_cast<float4*>(crow + c0 + u);
+                const int c = c0 + u;
+                const bool diag = (ti == tj);
+                if (!diag || c <= ri) cv.x -= v[u];
+                if (!diag || c + 1 <= ri) cv.y -= v[u + 1];
+                if (!diag || c + 2 <= ri) cv.z -= v[u + 2];
+                if (!diag || c + 3 <= ri) cv.w -= v[u + 3];
+                *reinterpret_cast<float4*>(crow + c0 + u) = cv;
+              }
+            }
+          }
+          tc::fence_before();
+          __syncthreads();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, kTcCols);
 }
 
 // -------------------------------------------------------------- RAS solve
@@ -947,6 +1078,31 @@ int ldlt_blocks_per_sm() {
     n = 1;
   }
   return std::max(1, std::min(8, n));
+}
+
+void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                           int grid, int* info, cudaStream_t s) {
+  if (grid < 1) return;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_ldlt_blocks_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  });
+  k_ldlt_blocks_tc<<<grid, 256, kTcSmem, s>>>(fac, E, cta_ptr, cta_list, info);
+}
+
+// CTAs of k_ldlt_blocks_tc per SM: resident at once, and at most 512 / 128
+// (the tensor memory of an SM), so that no allocation ever waits.
+int ldlt_blocks_tc_per_sm() {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_ldlt_blocks_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  });
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ldlt_blocks_tc, 256, kTcSmem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return std::max(1, std::min(512 / kTcCols, n));
 }
 
 template <typename T>

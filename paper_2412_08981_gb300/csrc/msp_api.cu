@@ -15,6 +15,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "msp.h"
@@ -301,7 +302,10 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     // (diagonal 1, panel 1, trailing pair 2, diagonal pair 1)
     D.fac_blocks = H.nsub >= std::max(2, nsm / 2);
     if (D.fac_blocks) {
-      const int per_sm = level_f32(h, l) ? ldlt_blocks_per_sm<float>() : ldlt_blocks_per_sm<double>();
+      const Store fst = level_store(h, l);
+      const int per_sm = fst == Store::BF16  ? ldlt_blocks_tc_per_sm()
+                         : fst == Store::F32 ? ldlt_blocks_per_sm<float>()
+                                             : ldlt_blocks_per_sm<double>();
       for (int p = 0; p < H.nsub; ++p) {
         const int32_t* R = &H.tile_last[H.sub_trow[p]];
         int64_t c = 0;
@@ -361,6 +365,18 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   return MSP_OK;
 }
 
+// The tcgen05 self-check (msp_tensor_selftest), once per device.
+int tensor_check(int device) {
+  static std::mutex mu;
+  static int state[64] = {0};  // 0 unknown, 1 passed, -1 failed
+  if (device < 0 || device >= 64) return fail(MSP_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (state[device] == 0) state[device] = msp_tensor_selftest(nullptr) == MSP_OK ? 1 : -1;
+  if (state[device] < 0)
+    return fail(MSP_ERR_INTERNAL, "the tensor-core self-check failed on this device; BF16 factors need it");
+  return MSP_OK;
+}
+
 int check_options(const msp_options& o) {
   if (o.delta < 0 || o.delta > 64) return fail(MSP_ERR_INVALID, "delta out of range");
   if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 64 || o.nu_post > 64)
@@ -403,7 +419,7 @@ int assemble_all(msp_instance* I) {
 }
 
 template <typename T>
-void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
+void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = false) {
   msp_hierarchy* h = I->h;
   DevLevel& D = h->dev[l];
   {
@@ -413,7 +429,12 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s) {
   }
   if (D.fac_blocks) {
     ProfScope ps(I->prof, PK_LDLT_BLOCKS, s);
-    launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tensor) launch_ldlt_blocks_tc(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
+      else launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
+    } else {
+      launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
+    }
     ps.account(0, D.fac_flops);
     return;
   }
@@ -458,7 +479,7 @@ int factor_all(msp_instance* I) {
     } else if (st == Store::F32) {
       factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
     } else {
-      factor_level<float>(I, l, I->work[l], s);
+      factor_level<float>(I, l, I->work[l], s, /*tensor=*/true);
       ProfScope ps(I->prof, PK_EXTRACT, s);
       launch_round_bf16(I->work[l], static_cast<__nv_bfloat16*>(I->fac[l]), h->dev[l].fac_elems, s);
       ps.account((double)h->dev[l].fac_elems * 6, 0);
@@ -473,6 +494,7 @@ int factor_all(msp_instance* I) {
   MSP_CUDA(cudaMemcpyAsync(&hinfo, I->info, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
   MSP_CUDA(cudaStreamSynchronize(I->stream));
   I->prof.harvest();
+  if (hinfo & 2) return fail(MSP_ERR_TIMEOUT, "a bounded tensor-core wait in the factorisation expired");
   if (hinfo) return fail(MSP_ERR_INTERNAL, "non-positive or non-finite pivot in a subdomain factor");
   I->factored = true;
   return MSP_OK;
@@ -878,6 +900,10 @@ int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_options*
   }
   if (!h->host_only) {
     MSP_CUDA(cudaGetDevice(&h->device));
+    if (o->factor_precision == MSP_BF16) {  // the BF16 factorisation uses the tensor cores
+      rc = tensor_check(h->device);
+      if (rc) return rc;
+    }
     h->arena.al.a = o->alloc;
     h->arena.al.f = o->free;
     h->arena.al.ctx = o->alloc_ctx;

@@ -75,6 +75,12 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
 // CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
 // longest-first balanced assignment built on the host); a bounded mbarrier
 // wait that expires sets bit 4 of *err.  The factor tiles stream through
+// Persistent factorisation of the blocks of a level whose factors are stored
+// in BF16: FP32 diagonal tiles and panels, trailing updates on the tensor
+// cores (BF16 operands, FP32 accumulation), fac = the FP32 working envelope.
+void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                           int grid, int* info, cudaStream_t s);
+int ldlt_blocks_tc_per_sm();
 // BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
 // n a multiple of 4.
 void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);

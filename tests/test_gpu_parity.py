@@ -358,6 +358,49 @@ def test_bf16_factors(P, orc, torch):
     assert 1e-6 < d < 0.5, d
 
 
+def test_bf16_tensor_core_factorisation(P, orc, torch):
+    """Levels with many blocks factor BF16 hierarchies in the persistent kernel
+    whose trailing updates run on the tensor cores (BF16 operands, FP32
+    accumulation): factors within BF16 accuracy of the blocks, close to the
+    rounded FP32 factors, and the FP64 outer loop reaches the oracle's x."""
+    levels = syn.hierarchy((20, 10, 5), ((5, 5, 4), (5, 5, 4)))
+    w = dict(delta=2, nu=2, coef="cosexp", scale=1.0, load="one", restart=30)
+    mu = syn.mu_draw(7)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10)
+    h = make_hierarchy(levels, w, P, precision="bf16")
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.profile_enable(P.msp.KERNEL_CLASSES)
+    inst.factor()
+    prof = inst.profile()
+    assert prof["ldlt_blocks"]["launches"] == 2  # both smoothed levels, one launch each
+    h32 = make_hierarchy(levels, w, P, precision="f32")
+    i32 = h32.assemble(mu, stream=torch.cuda.current_stream())
+    i32.factor()
+    for l in range(2):
+        ns = o.get("n_subs", l)
+        assert ns >= 76  # at least half the SMs: the persistent path
+        for p in sorted({0, ns // 3, ns - 1}):
+            dofs = o.get("sub_dofs", l, p)
+            n = dofs.size
+            first = P.msp.tile_first_of(h, l, p)
+            Lg, dg = P.msp.unpack_factor(inst.array(l, "factor", p, dtype="bf16").astype(np.float64),
+                                         n, first)
+            A = o.csr(l).toarray()[np.ix_(dofs, dofs)]
+            err = np.linalg.norm(Lg @ np.diag(dg) @ Lg.T - A) / np.linalg.norm(A)
+            assert err < 3e-2, err
+            L32, d32 = P.msp.unpack_factor(i32.array(l, "factor", p, dtype=np.float32).astype(np.float64),
+                                           n, first)
+            assert rel(dg, d32) < 3e-2
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= so["iters"] + 3
+
+
 # ------------------------------------------- paper-literal Algorithm 2 options
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_paper_literal_algorithm2(P, orc, torch, precision):

@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--workload", default="cube64_3lvl")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -257,7 +257,9 @@ def run_msp(args):
         lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
         prof = inst.profile()
         launches = int(sum(v["launches"] for v in prof.values()))
-        out = dict(ms=ms, lat=lat, iters=list(iters), relres=list(relres), prof=prof, dominant=dominant,
+        grids = {"factor_ctas": [h.info(l)["fac_ctas"] for l in range(h.nlevels)],
+                 "ras_ctas": [h.info(l)["ras_ctas"] for l in range(h.nlevels)]}
+        out = dict(ms=ms, lat=lat, iters=list(iters), relres=list(relres), prof=prof, dominant=dominant, grids=grids,
                    shares=shares, kernel_ms=kernel_ms, launches=launches, clocks=clocks,
                    x=x.cpu().numpy())
         # end to end through the host-buffer entry point
@@ -403,7 +405,8 @@ def run_msp(args):
                  "iterations_mean": float(np.mean(mres["iters"])),
                  "rel_diff_vs_f64_solution": err, "e2e": mres["e2e"],
                  "final_rel_residual_max": float(np.max(mres["relres"])),
-                 "stage_ms_host": mres["stage_ms"], "kernel_ms_per_solve": mres["kernel_ms"]}
+                 "stage_ms_host": mres["stage_ms"], "kernel_ms_per_solve": mres["kernel_ms"],
+                 "grids": mres["grids"]}
         bres16 = measure("bf16", args.steps, args.warmup)
         b16 = args.steps / (bres16["ms"] / 1e3)
         mixed["bf16"] = {
@@ -414,7 +417,8 @@ def run_msp(args):
             "rel_diff_vs_f64_solution": float(np.linalg.norm(bres16["x"] - res["x"]) /
                                               np.linalg.norm(res["x"])),
             "final_rel_residual_max": float(np.max(bres16["relres"])),
-            "stage_ms_host": bres16["stage_ms"], "kernel_ms_per_solve": bres16["kernel_ms"]}
+            "stage_ms_host": bres16["stage_ms"], "kernel_ms_per_solve": bres16["kernel_ms"],
+            "grids": bres16["grids"]}
         if args.batch > 1:
             bres = measure_batched("f32", max(args.steps, 2 * args.batch), args.warmup, args.batch)
             bval = bres["value"]
@@ -475,7 +479,7 @@ def run_msp(args):
     is_flop = res["dominant"].startswith("ldlt")
     dom_ms = prof["ms"] / max(1, prof["timed"])
     if is_flop:
-        peak = FP64_PEAK_TFLOPS if args.precision == "f64" else FP32_PEAK_TFLOPS
+        peak = FP64_PEAK_TFLOPS if args.precision == "f64" else FP32_PEAK_TFLOPS  # f32, bf16: FP32 SIMT diag/panel
         achieved = prof["flops"] / max(1, prof["launches"]) / (dom_ms / 1e3) / 1e12
         roof = {"kernel": res["dominant"], "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
@@ -489,6 +493,7 @@ def run_msp(args):
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": "MEASURED_PEAKS hbm_gbs",
                 "traffic": traffic_for(res["dominant"], prof)}
     roof["avg_launch_ms"] = dom_ms
+    roof["grids"] = res["grids"]
     roof["time_shares_warmup"] = res["shares"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -181,6 +181,9 @@ typedef struct msp_level_info {
   int64_t factor_elems;       /* elements of the tiled factor storage of this level */
   int64_t P_nnz;              /* nnz of P from level+1 (0 on the coarsest) */
   int64_t R_nnz;              /* nnz of the restriction to level+1 (P^T or MLS) */
+  int32_t fac_ctas;           /* CTAs of the one persistent factorisation launch of this level
+                                 (0: tile-step launches, or a host-only hierarchy) */
+  int32_t ras_ctas;           /* CTAs of the staged RAS solve (0: directly solved level) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
 

@@ -1049,6 +1049,25 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                                          ndir, t, z, add, max_nt, nslot, err);
 }
 
+// CTAs of a 256-thread persistent kernel resident per SM at once: limited by
+// its shared memory (with the carveout set to the maximum) and its registers.
+int resident_per_sm(const void* fn, size_t smem) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  int dev = 0, per_sm_smem = 0, per_sm_regs = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&per_sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, fn);
+  const size_t per_cta_smem = smem + fa.sharedSizeBytes + 1024;  // + the per-CTA reservation
+  const int regs = std::max(1, ((fa.numRegs + 7) / 8) * 8) * 256;
+  int n = (int)std::min<size_t>(per_sm_smem / per_cta_smem, (size_t)(per_sm_regs / regs));
+  n = std::min(n, 2048 / 256);
+  cudaGetLastError();
+  return std::max(1, n);
+}
+
 template <typename T>
 void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
                         int grid, int* info, cudaStream_t s) {
@@ -1056,53 +1075,32 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
   if (grid < 1) return;
   const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
   static std::once_flag attr;
-  std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_ldlt_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
+  std::call_once(attr, [&] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks<T>), smem); });
   k_ldlt_blocks<T><<<grid, 256, smem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
 
-// CTAs of k_ldlt_blocks resident per SM at once (shared memory and registers
-// both counted), so that the persistent grid is exactly one wave.
+// CTAs of k_ldlt_blocks per SM, so that the persistent grid is exactly one wave.
 template <typename T>
 int ldlt_blocks_per_sm() {
   using AT = typename Acc<T>::type;
   const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
-  static std::once_flag attr;
-  std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_ldlt_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ldlt_blocks<T>, 256, smem) != cudaSuccess) {
-    cudaGetLastError();
-    n = 1;
-  }
-  return std::max(1, std::min(8, n));
+  static int n = resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks<T>), smem);
+  return n;
 }
 
 void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
                            int grid, int* info, cudaStream_t s) {
   if (grid < 1) return;
   static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_ldlt_blocks_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  });
+  std::call_once(attr, [] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_tc), kTcSmem); });
   k_ldlt_blocks_tc<<<grid, 256, kTcSmem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
 
 // CTAs of k_ldlt_blocks_tc per SM: resident at once, and at most 512 / 128
 // (the tensor memory of an SM), so that no allocation ever waits.
 int ldlt_blocks_tc_per_sm() {
-  static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_ldlt_blocks_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  });
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ldlt_blocks_tc, 256, kTcSmem) != cudaSuccess) {
-    cudaGetLastError();
-    n = 1;
-  }
-  return std::max(1, std::min(512 / kTcCols, n));
+  static int n = resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_tc), kTcSmem);
+  return std::min(512 / kTcCols, n);
 }
 
 template <typename T>

@@ -954,6 +954,13 @@ int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) 
   info->factor_elems = H.sub_fac_off.empty() ? 0 : H.sub_fac_off.back();
   info->P_nnz = (int64_t)H.P_col.size();
   info->R_nnz = (int64_t)H.PT_col.size();
+  info->fac_ctas = 0;
+  info->ras_ctas = 0;
+  if (!h->host_only) {
+    const msp::DevLevel& D = h->dev[level];
+    info->fac_ctas = D.fac_blocks ? D.fac_grid : 0;
+    info->ras_ctas = H.direct ? 0 : D.ras_grid;
+  }
   return MSP_OK;
 }
 

@@ -83,7 +83,8 @@ class msp_server_opts(C.Structure):
 class msp_level_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("nnz", C.c_int64),
                 ("n_sub", C.c_int32), ("sub_dofs", C.c_int64), ("factor_elems", C.c_int64),
-                ("P_nnz", C.c_int64), ("R_nnz", C.c_int64)]
+                ("P_nnz", C.c_int64), ("R_nnz", C.c_int64), ("fac_ctas", C.c_int32),
+                ("ras_ctas", C.c_int32)]
 
 
 class msp_kernel_profile(C.Structure):

@@ -79,15 +79,23 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 
 // ---------------------------------------------------- diagonal tile LDL^T
 // Factors one diagonal tile in shared memory, computing in the factor's
-// precision.  Right-looking, column by column: the scaled column
-// l_r = W_rc / d_c is formed (64 threads), then the trailing lower triangle
-// entries (r, s), c < s <= r, are spread evenly over all threads (one FMA
-// each: A_rs -= l_r W_sc).  On GB300 FP64 issues one warp instruction per 16
-// SM cycles, so the work must fill every lane of every warp.  Then
-// L = W D^{-1}, and X = L^{-1} is formed by 8-row blocks
-// (X_I = L_II^{-1} (E_I - sum_{K<I} L_IK X_K)), stored transposed in the
-// strict upper part.  smem: (64*65 + 128) elements of AT.
-template <typename T, typename AT>
+// precision: unblocked right-looking elimination of the lower triangle with
+// the inverse of the unit lower factor built in the same sweep.  Step c
+// (one barrier pair):
+//   * l_r = A_rc / d_c for the rows r > c;
+//   * A_rs -= l_r A_sc for c < s <= r (the Schur complement, W = L D), and
+//   * X_rj -= l_r X_cj for r > c, j <= c (X_cc = 1): the elimination that
+//     turns L into I turns I into X = L^{-1} (X_c is final at step c, since
+//     later steps only change rows below c).
+// All entries of both updates are spread evenly over the threads, one FMA
+// each; on GB300 FP64 issues one warp instruction per 16 SM cycles, so the
+// work must fill every lane of every warp.  Then L = W D^{-1}.  Layout on
+// exit: L strictly below the diagonal, D on it, X^T strictly above it
+// (X_ij at A[j][i]).  smem: (64*65 + 128) elements of AT.
+constexpr int kDiagThreads = 256;  // every kernel that factors a diagonal tile
+constexpr int kDiagItems = 9;      // ceil(max_c (63 - c)(66 + c) / 2 / 256)
+
+template <typename T, typename AT, bool kIlp = false>
 __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
   AT* lcol = A + 64 * 65;  // [64] the scaled column of the current step
   AT* dinv = lcol + 64;    // [64] 1/d_c, formed once each, by the thread finishing d_c
@@ -95,7 +103,7 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
   __syncthreads();  // the shared buffer may still be read by a previous phase
   for (int e = tid; e < TE; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
+    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);  // X starts as the identity (zeros above)
   }
   __syncthreads();
   if (tid == 0) dinv[0] = rcp_newton(A[0]);
@@ -104,61 +112,74 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     if (tid > c && tid < T64) lcol[tid] = A[tid * 65 + c] * dinv[c];
     __syncthreads();
     const int m = T64 - 1 - c;            // trailing size
-    const int nent = m * (m + 1) / 2;
-    for (int e = tid; e < nent; e += blockDim.x) {
-      int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-      rr += ((rr + 1) * (rr + 2) / 2 <= e);
-      rr -= (rr * (rr + 1) / 2 > e);
-      const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-      const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
-      A[r * 65 + s2] = v;
-      if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
+    const int nA = m * (m + 1) / 2;       // Schur complement entries
+    const int nX = m * (c + 1);           // inverse entries X_rj, r > c, j <= c
+    const float inv_w = 1.0f / (float)(c + 1);
+    if constexpr (!kIlp) {  // one entry at a time (persistent kernels: other CTAs hide the latency)
+      for (int e = tid; e < nA + nX; e += blockDim.x) {
+        if (e < nA) {
+          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+          rr += ((rr + 1) * (rr + 2) / 2 <= e);
+          rr -= (rr * (rr + 1) / 2 > e);
+          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+          const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+          A[r * 65 + s2] = v;
+          if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
+        } else {
+          const int x = e - nA;  // x = rr (c+1) + j
+          int rr = (int)((float)x * inv_w);
+          rr += ((rr + 1) * (c + 1) <= x);
+          rr -= (rr * (c + 1) > x);
+          const int j = x - rr * (c + 1), r = c + 1 + rr;
+          const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
+          A[j * 65 + r] = fma(-lcol[r], xcj, A[j * 65 + r]);
+        }
+      }
+      __syncthreads();
+      continue;
     }
+    // a lone CTA (the coarsest block): all of this thread's entries first
+    // (loads and FMAs only, so that their latencies overlap), then the
+    // stores: at most ceil(2079 / 256) = 9 each
+    AT val[kDiagItems];
+    int dst[kDiagItems];
+#pragma unroll
+    for (int q = 0; q < kDiagItems; ++q) {
+      const int e = tid + q * kDiagThreads;
+      dst[q] = -1;
+      if (e < nA) {
+        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        rr += ((rr + 1) * (rr + 2) / 2 <= e);
+        rr -= (rr * (rr + 1) / 2 > e);
+        const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+        val[q] = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+        dst[q] = r * 65 + s2;
+      } else if (e < nA + nX) {
+        const int x = e - nA;                // x = rr (c+1) + j
+        int rr = (int)((float)x * inv_w);
+        rr += ((rr + 1) * (c + 1) <= x);
+        rr -= (rr * (c + 1) > x);
+        const int j = x - rr * (c + 1), r = c + 1 + rr;
+        const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
+        val[q] = fma(-lcol[r], xcj, A[j * 65 + r]);
+        dst[q] = j * 65 + r;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kDiagItems; ++q)
+      if (dst[q] >= 0) A[dst[q]] = val[q];
+    if (tid == 0) dinv[c + 1] = rcp_newton(val[0]);  // entry (c+1, c+1): the next pivot is final
     __syncthreads();
   }
   if (tid < T64) {
     const AT d = A[tid * 65 + tid];
     if (!(d > AT(0)) || !(d < AT(1e300))) atomicOr(info, 1);
   }
-  for (int e = tid; e < TE; e += blockDim.x) {  // L = W D^{-1}; clear the upper part
+  for (int e = tid; e < TE; e += blockDim.x) {  // L = W D^{-1}
     int r = e >> 6, c = e & 63;
     if (c < r) A[r * 65 + c] *= dinv[c];
-    else if (c > r) A[r * 65 + c] = AT(0);
   }
   __syncthreads();
-  // X = L^{-1} by 8-row blocks; X[i][j] (j < i) lives at A[j][i].
-  for (int I = 0; I < 8; ++I) {
-    const int i0 = I * 8;
-    // T[i][j] = -(L[i][j] + sum_{j < m < i0} L[i][m] X[m][j]) for rows i in the
-    // block, columns j < i0 (one thread per entry)
-    for (int e = tid; e < 8 * i0; e += blockDim.x) {
-      const int i = i0 + e / i0, j = e % i0;
-      AT v0 = A[i * 65 + j], v1 = 0, v2 = 0, v3 = 0;  // four independent chains
-      int mm = j + 1;
-      for (; mm + 3 < i0; mm += 4) {
-        v0 = fma(A[i * 65 + mm], A[j * 65 + mm], v0);
-        v1 = fma(A[i * 65 + mm + 1], A[j * 65 + mm + 1], v1);
-        v2 = fma(A[i * 65 + mm + 2], A[j * 65 + mm + 2], v2);
-        v3 = fma(A[i * 65 + mm + 3], A[j * 65 + mm + 3], v3);
-      }
-      for (; mm < i0; ++mm) v0 = fma(A[i * 65 + mm], A[j * 65 + mm], v0);
-      A[j * 65 + i] = -((v0 + v1) + (v2 + v3));  // partial X[i][j], block rows not yet applied
-    }
-    __syncthreads();
-    // apply the unit lower L_II^{-1} inside the block: rows i0..i0+7 in order,
-    // one thread per column j < i0 + 8 (columns of the diagonal block included)
-    if (tid < i0 + 8) {
-      const int j = tid;
-      for (int i = (j >= i0 ? j + 1 : i0); i < i0 + 8; ++i) {
-        // X[i][j] = T[i][j] - sum_{i0 <= m < i} L[i][m] X[m][j]  (j < i0), or for
-        // j in the block: X[i][j] = -(L[i][j] + sum_{j < m < i} L[i][m] X[m][j])
-        AT v = (j >= i0) ? -A[i * 65 + j] : A[j * 65 + i];
-        for (int mm = (j >= i0 ? j + 1 : i0); mm < i; ++mm) v -= A[i * 65 + mm] * A[j * 65 + mm];
-        A[j * 65 + i] = v;
-      }
-    }
-    __syncthreads();
-  }
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   const int p = order[blockIdx.x];
-  diag_tile<T, AT>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
+  diag_tile<T, AT, true>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
 }
 
 // ----------------------------------------------------------- panel solve
@@ -424,10 +445,13 @@ constexpr int kTcBarOff = kTcSmem - 64;       // mbarrier + TMEM base address sl
 
 // rows row0..row0+63 of a K-major BF16 slab = bf16(tile[r][k] * scale[k])
 // (scale may be null); tile == null writes zeros.
+// Each warp writes one 8-row x 8-column core matrix per pass (lane -> row
+// lane / 4, column pair lane % 4): 32 distinct banks.
 __device__ void stage_bf16(unsigned char* slab, int row0, const float* __restrict__ tile,
                            const float* __restrict__ scale) {
   for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
-    const int r = e >> 5, k = (e & 31) * 2;
+    const int lane = e & 31, blk = e >> 5;
+    const int r = (blk >> 3) * 8 + (lane >> 2), k = (blk & 7) * 8 + (lane & 3) * 2;
     float2 v = make_float2(0.f, 0.f);
     if (tile) {
       v = *reinterpret_cast<const float2*>(tile + r * 64 + k);

@@ -183,6 +183,154 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
+// Blocked form for a lone CTA (the tile steps of the coarsest block, whose
+// diagonal tiles form the critical path): four 16-column blocks K, each
+//   (a) its 16 x 16 diagonal block as above (one entry per thread per step),
+//       with the inverse X_KK built in the same sweep;
+//   (b) the panel W_rK = A_rK X_KK^T below it (W = L D), and L_rK = W_rK D_K^{-1};
+//   (c) the trailing update A_rs -= W_rK L_sK^T, c1 <= s <= r (16-long dot
+//       products in registers, one output entry each);
+// then L = W D^{-1}, and the off-diagonal blocks of X = L^{-1} block row by
+// block row: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.  Per column only the
+// short steps of (a) are sequential; everything else is a few wide phases.
+// smem: (64*65 + 128 + 48*17 + 16*49) elements of AT.
+constexpr int kDiagBlockedElems = 64 * 65 + 128 + 48 * 17 + 16 * 49;
+
+template <typename T, typename AT>
+__device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
+  constexpr int NB = 16;
+  AT* lcol = A + 64 * 65;  // [64] scaled column of the current step of (a)
+  AT* dinv = lcol + 64;    // [64] 1/d_c
+  AT* Lp = dinv + 64;      // [48][17] L of the current panel
+  AT* Tb = Lp + 48 * 17;   // [16][49] sum_K L_IK X_KJ of the current X block row
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < TE; e += blockDim.x) {
+    int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
+  }
+  __syncthreads();
+  if (tid == 0) dinv[0] = rcp_newton(A[0]);
+  __syncthreads();
+  for (int K = 0; K < 4; ++K) {
+    const int c0 = K * NB, c1 = c0 + NB;
+    // (a) diagonal block: Schur complement inside the block and X_KK
+    for (int c = c0; c < c1; ++c) {
+      if (tid > c && tid < c1) lcol[tid] = A[tid * 65 + c] * dinv[c];
+      __syncthreads();
+      const int m = c1 - 1 - c, w = c - c0 + 1;
+      const int nA = m * (m + 1) / 2, nX = m * w;  // at most 120 + 15 entries
+      for (int e = tid; e < nA + nX; e += blockDim.x) {
+        if (e < nA) {
+          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+          rr += ((rr + 1) * (rr + 2) / 2 <= e);
+          rr -= (rr * (rr + 1) / 2 > e);
+          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
+          const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+          A[r * 65 + s2] = v;
+          if (e == 0) dinv[c + 1] = rcp_newton(v);
+        } else {
+          const int x = e - nA, rr = x / w;
+          const int j = c0 + (x - rr * w), r = c + 1 + rr;
+          const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
+          A[j * 65 + r] = fma(-lcol[r], xcj, A[j * 65 + r]);
+        }
+      }
+      __syncthreads();
+    }
+    if (K == 3) break;
+    // (b) panel below the block: W_rc = A_rc + sum_{c0 <= m < c} A_rm X_cm
+    const int nr = 64 - c1;
+    {
+      AT wv[3];
+      int at[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {  // nr * 16 <= 768 entries
+        const int e = tid + q * kDiagThreads;
+        at[q] = -1;
+        if (e < nr * NB) {
+          const int r = c1 + e / NB, c = c0 + e % NB;
+          AT v = A[r * 65 + c], v2 = 0;
+          int mm = c0;
+          for (; mm + 1 < c; mm += 2) {
+            v = fma(A[r * 65 + mm], A[mm * 65 + c], v);
+            v2 = fma(A[r * 65 + mm + 1], A[(mm + 1) * 65 + c], v2);
+          }
+          if (mm < c) v = fma(A[r * 65 + mm], A[mm * 65 + c], v);
+          wv[q] = v + v2;
+          at[q] = e;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (at[q] >= 0) {
+          const int r = c1 + at[q] / NB, cc = at[q] % NB;
+          A[r * 65 + c0 + cc] = wv[q];
+          Lp[(r - c1) * 17 + cc] = wv[q] * dinv[c0 + cc];
+        }
+    }
+    __syncthreads();
+    // (c) trailing update of the rows and columns >= c1
+    {
+      const int n2 = nr * (nr + 1) / 2;  // at most 1176 entries
+      for (int e = tid; e < n2; e += blockDim.x) {
+        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        rr += ((rr + 1) * (rr + 2) / 2 <= e);
+        rr -= (rr * (rr + 1) / 2 > e);
+        const int r = c1 + rr, s2 = c1 + (e - rr * (rr + 1) / 2);
+        const AT* wr = A + r * 65 + c0;
+        const AT* ls = Lp + (s2 - c1) * 17;
+        AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+        for (int cc = 0; cc < NB; cc += 4) {
+          a0 = fma(wr[cc], ls[cc], a0);
+          a1 = fma(wr[cc + 1], ls[cc + 1], a1);
+          a2 = fma(wr[cc + 2], ls[cc + 2], a2);
+          a3 = fma(wr[cc + 3], ls[cc + 3], a3);
+        }
+        const AT v = A[r * 65 + s2] - ((a0 + a1) + (a2 + a3));
+        A[r * 65 + s2] = v;
+        if (e == 0) dinv[c1] = rcp_newton(v);  // the next block's first pivot
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < T64) {
+    const AT d = A[tid * 65 + tid];
+    if (!(d > AT(0)) || !(d < AT(1e300))) atomicOr(info, 1);
+  }
+  for (int e = tid; e < TE; e += blockDim.x) {  // L = W D^{-1}
+    int r = e >> 6, c = e & 63;
+    if (c < r) A[r * 65 + c] *= dinv[c];
+  }
+  __syncthreads();
+  // off-diagonal blocks of X, block row I (X_ij stored at A[j][i])
+  for (int I = 1; I < 4; ++I) {
+    const int i0 = I * NB;
+    for (int e = tid; e < NB * i0; e += blockDim.x) {  // T_ij = L_ij + sum_{j < m < i0} L_im X_mj
+      const int i = i0 + e / i0, j = e % i0;
+      AT v = A[i * 65 + j], v2 = 0;
+      int mm = j + 1;
+      for (; mm + 1 < i0; mm += 2) {
+        v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
+        v2 = fma(A[i * 65 + mm + 1], A[j * 65 + mm + 1], v2);
+      }
+      if (mm < i0) v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
+      Tb[(i - i0) * 49 + j] = v + v2;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * i0; e += blockDim.x) {  // X_ij = -(T_ij + sum_{i0 <= m < i} X_im T_mj)
+      const int i = i0 + e / i0, j = e % i0;
+      AT v = Tb[(i - i0) * 49 + j];
+      for (int mm = i0; mm < i; ++mm) v = fma(A[mm * 65 + i], Tb[(mm - i0) * 49 + j], v);
+      A[j * 65 + i] = -v;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E,
                                                    const int32_t* __restrict__ order, int k,
@@ -190,7 +338,7 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   const int p = order[blockIdx.x];
-  diag_tile<T, AT, true>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
+  diag_tile_blocked<T, AT>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
 }
 
 // ----------------------------------------------------------- panel solve
@@ -985,7 +1133,7 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
                       int* info, cudaStream_t s) {
   if (nactive <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (64 * 65 + 128) * sizeof(AT);
+  size_t smem = (size_t)kDiagBlockedElems * sizeof(AT);
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

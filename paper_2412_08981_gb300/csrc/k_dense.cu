@@ -722,7 +722,13 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
 // records an error bit and goes on (the results are then garbage and the
 // host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
 // own copies, so none is in flight when the CTA exits.
-constexpr int kConsumers = 16;
+// Consumer warps per CTA and CTAs per SM.  FP64 sweeps are ALU-bound: one
+// CTA per SM with 16 consumers.  FP32 and BF16 sweeps are bound by the
+// latency of the per-row barriers: two CTAs per SM with 8 consumers each run
+// two subdomains at once on every SM.
+template <typename T> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
+template <> struct RasCfg<float> { static constexpr int NCW = 8, CTAS = 2; };
+template <> struct RasCfg<__nv_bfloat16> { static constexpr int NCW = 8, CTAS = 2; };
 constexpr long kWaitLimit = 1L << 20;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -765,7 +771,8 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory"); }
+template <int NCW>
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCW * 32) : "memory"); }
 
 // Per-subdomain envelope metadata staged in shared memory (one copy for the
 // producer, which runs ahead, one for the consumers): F_I, R_I and the tile
@@ -787,13 +794,14 @@ __device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int l
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
+__global__ void __launch_bounds__(32 * (RasCfg<T>::NCW + 1), RasCfg<T>::CTAS) k_ras_solve(
     const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
     const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
     const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
     double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err) {
   using AT = typename Acc<T>::type;
+  constexpr int kConsumers = RasCfg<T>::NCW;
   constexpr uint32_t kTileBytes = TE * sizeof(T);
   constexpr int NC = kConsumers * 32;       // consumer threads
   constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
@@ -881,7 +889,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
     const int np_ = sub_ptr[p + 1] - off;
     if (warp == 0) load_meta(E, p, NT, cm, lane);
     for (int li = tid; li < NT * 64; li += NC) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
-    consumers_sync();
+    consumers_sync<kConsumers>();
     // forward sweep
     for (int I = 0; I < NT; ++I) {
       AT sr[RW];
@@ -905,7 +913,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
       // transpose costs far fewer FP64 instructions than warp shuffles)
 #pragma unroll
       for (int k = 0; k < RW; ++k) red[(warp * RW + k) * 33 + lane] = sr[k];
-      consumers_sync();
+      consumers_sync<kConsumers>();
       if (tid < 64) {
         AT v0 = 0, v1 = 0;
 #pragma unroll
@@ -915,7 +923,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         }
         acc[tid] = y[I * 64 + tid] - (v0 + v1);
       }
-      consumers_sync();
+      consumers_sync<kConsumers>();
       {  // y_I = X acc, X[b][a] = tile[a][b] for a < b
         const T* dt = acquire();
         const int bcol = tid & 63, pr = tid >> 6;
@@ -929,14 +937,14 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         part[pr * 64 + bcol] = v + v2;
         release();
       }
-      consumers_sync();
+      consumers_sync<kConsumers>();
       if (tid < 64) {
         AT v = acc[tid];
 #pragma unroll
         for (int q2 = 0; q2 < NP; ++q2) v += part[q2 * 64 + tid];
         y[I * 64 + tid] = v;
       }
-      consumers_sync();
+      consumers_sync<kConsumers>();
     }
     // backward sweep
     for (int I = NT - 1; I >= 0; --I) {
@@ -963,14 +971,14 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
       }
       part[warp * 64 + lane] = s0;
       part[warp * 64 + lane + 32] = s1;
-      consumers_sync();
+      consumers_sync<kConsumers>();
       if (tid < 64) {
         AT v = 0;
 #pragma unroll
         for (int w = 0; w < kConsumers; ++w) v += part[w * 64 + tid];
         acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - v;
       }
-      consumers_sync();
+      consumers_sync<kConsumers>();
       // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]
 #pragma unroll
       for (int k = 0; k < RW; ++k) {
@@ -982,7 +990,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
-      consumers_sync();
+      consumers_sync<kConsumers>();
       if (tid < 64) {
         AT v0 = 0, v1 = 0;
 #pragma unroll
@@ -992,7 +1000,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         }
         y[I * 64 + tid] = acc[tid] + (v0 + v1);
       }
-      consumers_sync();
+      consumers_sync<kConsumers>();
     }
     for (int li = tid; li < np_; li += NC) {
       if (own[off + li]) {
@@ -1000,7 +1008,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 1) k_ras_solve(
         z[g] = add ? z[g] + (double)y[li] : (double)y[li];
       }
     }
-    consumers_sync();
+    consumers_sync<kConsumers>();
   }
 }
 
@@ -1190,13 +1198,30 @@ DevLimits& limits() {
 // more of the HBM latency).
 constexpr size_t kMaxSlots = 16;
 
+// Dynamic shared memory one CTA of k_ras_solve<T> may use.
+template <typename T>
+size_t ras_smem_budget() {
+  constexpr int C = RasCfg<T>::CTAS;
+  if (C == 1) return (size_t)limits().smem;
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  return std::min((size_t)limits().smem, (size_t)per_sm / C - 2048);  // per-CTA reservation and static smem
+}
+
+template <typename T>
+int ras_ctas_per_sm() {
+  return RasCfg<T>::CTAS;
+}
+
 template <typename T>
 int ras_slots(int max_nt) {
   using AT = typename Acc<T>::type;
+  constexpr int kConsumers = RasCfg<T>::NCW;
   const size_t fixed = ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
                        6 * (size_t)max_nt * 4;
   const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
-  const size_t smem = (size_t)limits().smem;
+  const size_t smem = ras_smem_budget<T>();
   if (smem <= fixed) return 0;
   return (int)std::min<size_t>(kMaxSlots, (smem - fixed) / per_slot);
 }
@@ -1208,9 +1233,12 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
                       int* err, cudaStream_t s) {
   using AT = typename Acc<T>::type;
+  constexpr int kConsumers = RasCfg<T>::NCW;
   static std::once_flag attr;
   std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limits().smem);
+    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ras_smem_budget<T>());
+    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
   });
   const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
@@ -1315,6 +1343,7 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
                                     const int32_t*, int, const double*, double*, int, int*,      \
                                     cudaStream_t);                                               \
   template int ras_slots<T>(int);                                                                \
+  template int ras_ctas_per_sm<T>();                                                             \
   template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
                                       int*, cudaStream_t);                                       \
   template int ldlt_blocks_per_sm<T>();                                                           \
@@ -1329,6 +1358,7 @@ template void launch_ras_solve<__nv_bfloat16>(const __nv_bfloat16*, const EnvDev
                                               const uint8_t*, int, const int32_t*, int,
                                               const double*, double*, int, int*, cudaStream_t);
 template int ras_slots<__nv_bfloat16>(int);
+template int ras_ctas_per_sm<__nv_bfloat16>();
 
 // ------------------------------------------------- BF16 storage of factors
 // dst = bf16(src), round to nearest even; n a multiple of 4 (whole tiles).

@@ -293,7 +293,13 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     std::vector<int64_t> cost(H.nsub);
     for (int p = 0; p < H.nsub; ++p) cost[p] = (H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems;
     std::vector<int32_t> cptr, clist;
-    lpt_lists(cost, std::max(1, std::min(H.nsub, nsm)), cptr, clist);
+    {
+      const Store st = level_store(h, l);
+      const int per_sm = st == Store::F64   ? ras_ctas_per_sm<double>()
+                         : st == Store::F32 ? ras_ctas_per_sm<float>()
+                                            : ras_ctas_per_sm<__nv_bfloat16>();
+      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
+    }
     D.ras_grid = (int)cptr.size() - 1;
     D.ras_cta_ptr = A.upload(cptr);
     D.ras_cta_list = A.upload(clist);

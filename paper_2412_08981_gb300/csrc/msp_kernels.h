@@ -90,6 +90,9 @@ void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStre
 // set-up).
 template <typename T>
 int ras_slots(int max_nt);
+// CTAs of k_ras_solve<T> that share an SM (the persistent grid is this x SMs)
+template <typename T>
+int ras_ctas_per_sm();
 template <typename T>
 void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, const int32_t* sub_ptr,

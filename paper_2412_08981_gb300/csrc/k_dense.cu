@@ -93,9 +93,8 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
 // exit: L strictly below the diagonal, D on it, X^T strictly above it
 // (X_ij at A[j][i]).  smem: (64*65 + 128) elements of AT.
 constexpr int kDiagThreads = 256;  // every kernel that factors a diagonal tile
-constexpr int kDiagItems = 9;      // ceil(max_c (63 - c)(66 + c) / 2 / 256)
 
-template <typename T, typename AT, bool kIlp = false>
+template <typename T, typename AT>
 __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
   AT* lcol = A + 64 * 65;  // [64] the scaled column of the current step
   AT* dinv = lcol + 64;    // [64] 1/d_c, formed once each, by the thread finishing d_c
@@ -115,60 +114,25 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     const int nA = m * (m + 1) / 2;       // Schur complement entries
     const int nX = m * (c + 1);           // inverse entries X_rj, r > c, j <= c
     const float inv_w = 1.0f / (float)(c + 1);
-    if constexpr (!kIlp) {  // one entry at a time (persistent kernels: other CTAs hide the latency)
-      for (int e = tid; e < nA + nX; e += blockDim.x) {
-        if (e < nA) {
-          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-          rr += ((rr + 1) * (rr + 2) / 2 <= e);
-          rr -= (rr * (rr + 1) / 2 > e);
-          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-          const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
-          A[r * 65 + s2] = v;
-          if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
-        } else {
-          const int x = e - nA;  // x = rr (c+1) + j
-          int rr = (int)((float)x * inv_w);
-          rr += ((rr + 1) * (c + 1) <= x);
-          rr -= (rr * (c + 1) > x);
-          const int j = x - rr * (c + 1), r = c + 1 + rr;
-          const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
-          A[j * 65 + r] = fma(-lcol[r], xcj, A[j * 65 + r]);
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    // a lone CTA (the coarsest block): all of this thread's entries first
-    // (loads and FMAs only, so that their latencies overlap), then the
-    // stores: at most ceil(2079 / 256) = 9 each
-    AT val[kDiagItems];
-    int dst[kDiagItems];
-#pragma unroll
-    for (int q = 0; q < kDiagItems; ++q) {
-      const int e = tid + q * kDiagThreads;
-      dst[q] = -1;
+    for (int e = tid; e < nA + nX; e += blockDim.x) {
       if (e < nA) {
         int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
         rr += ((rr + 1) * (rr + 2) / 2 <= e);
         rr -= (rr * (rr + 1) / 2 > e);
         const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-        val[q] = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
-        dst[q] = r * 65 + s2;
-      } else if (e < nA + nX) {
-        const int x = e - nA;                // x = rr (c+1) + j
+        const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
+        A[r * 65 + s2] = v;
+        if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
+      } else {
+        const int x = e - nA;  // x = rr (c+1) + j
         int rr = (int)((float)x * inv_w);
         rr += ((rr + 1) * (c + 1) <= x);
         rr -= (rr * (c + 1) > x);
         const int j = x - rr * (c + 1), r = c + 1 + rr;
         const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
-        val[q] = fma(-lcol[r], xcj, A[j * 65 + r]);
-        dst[q] = j * 65 + r;
+        A[j * 65 + r] = fma(-lcol[r], xcj, A[j * 65 + r]);
       }
     }
-#pragma unroll
-    for (int q = 0; q < kDiagItems; ++q)
-      if (dst[q] >= 0) A[dst[q]] = val[q];
-    if (tid == 0) dinv[c + 1] = rcp_newton(val[0]);  // entry (c+1, c+1): the next pivot is final
     __syncthreads();
   }
   if (tid < T64) {
@@ -616,13 +580,13 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
                                                            const int32_t* __restrict__ cta_ptr,
                                                            const int32_t* __restrict__ cta_list,
                                                            int* __restrict__ info) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  float* sm = reinterpret_cast<float*>(smraw);
-  unsigned char* sA = smraw;                // W rows of the two output tile rows
-  unsigned char* sB = smraw + kTcSlab;      // L rows of the two output tile columns
-  float* dk = reinterpret_cast<float*>(smraw + 2 * kTcSlab);  // D of the step
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + kTcBarOff);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smraw + kTcBarOff + 16);
+  extern __shared__ __align__(1024) unsigned char smtc[];
+  float* sm = reinterpret_cast<float*>(smtc);
+  unsigned char* sA = smtc;                // W rows of the two output tile rows
+  unsigned char* sB = smtc + kTcSlab;      // L rows of the two output tile columns
+  float* dk = reinterpret_cast<float*>(smtc + 2 * kTcSlab);  // D of the step
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smtc + kTcBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smtc + kTcBarOff + 16);
   const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
   if (q0 >= q1) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -726,9 +690,11 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
 // CTA per SM with 16 consumers.  FP32 and BF16 sweeps are bound by the
 // latency of the per-row barriers: two CTAs per SM with 8 consumers each run
 // two subdomains at once on every SM.
-template <typename T> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
-template <> struct RasCfg<float> { static constexpr int NCW = 8, CTAS = 2; };
-template <> struct RasCfg<__nv_bfloat16> { static constexpr int NCW = 8, CTAS = 2; };
+// Levels whose tile band needs more ring slots than that leaves per CTA use
+// the wide form (one CTA of 16 consumers per SM) in every precision.
+template <typename T, bool Wide> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
+template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 2; };
+template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 3; };
 constexpr long kWaitLimit = 1L << 20;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -793,15 +759,15 @@ __device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int l
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(32 * (RasCfg<T>::NCW + 1), RasCfg<T>::CTAS) k_ras_solve(
+template <typename T, int NCW, int CTAS>
+__global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
     const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
     const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
     double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err) {
   using AT = typename Acc<T>::type;
-  constexpr int kConsumers = RasCfg<T>::NCW;
+  constexpr int kConsumers = NCW;
   constexpr uint32_t kTileBytes = TE * sizeof(T);
   constexpr int NC = kConsumers * 32;       // consumer threads
   constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
@@ -1198,10 +1164,10 @@ DevLimits& limits() {
 // more of the HBM latency).
 constexpr size_t kMaxSlots = 16;
 
-// Dynamic shared memory one CTA of k_ras_solve<T> may use.
-template <typename T>
+// Dynamic shared memory one CTA of a k_ras_solve configuration may use.
+template <typename T, bool W>
 size_t ras_smem_budget() {
-  constexpr int C = RasCfg<T>::CTAS;
+  constexpr int C = RasCfg<T, W>::CTAS;
   if (C == 1) return (size_t)limits().smem;
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -1209,21 +1175,48 @@ size_t ras_smem_budget() {
   return std::min((size_t)limits().smem, (size_t)per_sm / C - 2048);  // per-CTA reservation and static smem
 }
 
-template <typename T>
-int ras_ctas_per_sm() {
-  return RasCfg<T>::CTAS;
+template <typename T, bool W>
+size_t ras_fixed_bytes(int max_nt) {
+  using AT = typename Acc<T>::type;
+  return ((size_t)max_nt * 64 + 64 + RasCfg<T, W>::NCW * 64 + 64 * 33) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+}
+
+template <typename T, bool W>
+int ras_slots_cfg(int max_nt) {
+  const size_t fixed = ras_fixed_bytes<T, W>(max_nt);
+  const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
+  const size_t smem = ras_smem_budget<T, W>();
+  if (smem <= fixed) return 0;
+  return (int)std::min<size_t>(kMaxSlots, (smem - fixed) / per_slot);
 }
 
 template <typename T>
-int ras_slots(int max_nt) {
-  using AT = typename Acc<T>::type;
-  constexpr int kConsumers = RasCfg<T>::NCW;
-  const size_t fixed = ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
-                       6 * (size_t)max_nt * 4;
-  const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
-  const size_t smem = ras_smem_budget<T>();
-  if (smem <= fixed) return 0;
-  return (int)std::min<size_t>(kMaxSlots, (smem - fixed) / per_slot);
+int ras_ctas_per_sm(bool wide) {
+  return wide ? RasCfg<T, true>::CTAS : RasCfg<T, false>::CTAS;
+}
+
+template <typename T>
+int ras_slots(int max_nt, bool wide) {
+  return wide ? ras_slots_cfg<T, true>(max_nt) : ras_slots_cfg<T, false>(max_nt);
+}
+
+template <typename T, bool W>
+void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
+                    const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int max_nt,
+                    const int32_t* dir_list, int ndir, const double* t, double* z, int add, int* err,
+                    cudaStream_t s) {
+  constexpr int NCW = RasCfg<T, W>::NCW, CTAS = RasCfg<T, W>::CTAS;
+  auto kern = k_ras_solve<T, NCW, CTAS>;
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ras_smem_budget<T, W>());
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  });
+  const int nslot = ras_slots_cfg<T, W>(max_nt);  // the host checked at set-up that this is enough
+  const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) + ras_fixed_bytes<T, W>(max_nt);
+  if (grid < 1) return;
+  kern<<<grid, 32 * (NCW + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list, ndir, t, z, add,
+                                          max_nt, nslot, err);
 }
 
 template <typename T>
@@ -1231,22 +1224,13 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, const int32_t* sub_ptr,
                       const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, cudaStream_t s) {
-  using AT = typename Acc<T>::type;
-  constexpr int kConsumers = RasCfg<T>::NCW;
-  static std::once_flag attr;
-  std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ras_smem_budget<T>());
-    cudaFuncSetAttribute(k_ras_solve<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-  });
-  const int nslot = ras_slots<T>(max_nt);  // the host checked at set-up that this is enough
-  const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) +
-                      ((size_t)max_nt * 64 + 64 + kConsumers * 64 + 64 * 33) * sizeof(AT) +
-                      6 * (size_t)max_nt * 4;
-  if (grid < 1) return;
-  k_ras_solve<T><<<grid, 32 * (kConsumers + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list,
-                                         ndir, t, z, add, max_nt, nslot, err);
+                      int* err, bool wide, cudaStream_t s) {
+  if (wide)
+    launch_ras_cfg<T, true>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
+                            add, err, s);
+  else
+    launch_ras_cfg<T, false>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
+                             add, err, s);
 }
 
 // CTAs of a 256-thread persistent kernel resident per SM at once: limited by
@@ -1341,9 +1325,9 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
   template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
                                     const int32_t*, const int32_t*, const uint8_t*, int,         \
                                     const int32_t*, int, const double*, double*, int, int*,      \
-                                    cudaStream_t);                                               \
-  template int ras_slots<T>(int);                                                                \
-  template int ras_ctas_per_sm<T>();                                                             \
+                                    bool, cudaStream_t);                                         \
+  template int ras_slots<T>(int, bool);                                                          \
+  template int ras_ctas_per_sm<T>(bool);                                                         \
   template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
                                       int*, cudaStream_t);                                       \
   template int ldlt_blocks_per_sm<T>();                                                           \
@@ -1356,9 +1340,9 @@ MSP_INST(float)
 template void launch_ras_solve<__nv_bfloat16>(const __nv_bfloat16*, const EnvDev&, const int32_t*,
                                               const int32_t*, int, const int32_t*, const int32_t*,
                                               const uint8_t*, int, const int32_t*, int,
-                                              const double*, double*, int, int*, cudaStream_t);
-template int ras_slots<__nv_bfloat16>(int);
-template int ras_ctas_per_sm<__nv_bfloat16>();
+                                              const double*, double*, int, int*, bool, cudaStream_t);
+template int ras_slots<__nv_bfloat16>(int, bool);
+template int ras_ctas_per_sm<__nv_bfloat16>(bool);
 
 // ------------------------------------------------- BF16 storage of factors
 // dst = bf16(src), round to nearest even; n a multiple of 4 (whole tiles).

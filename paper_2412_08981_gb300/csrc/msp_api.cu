@@ -121,6 +121,7 @@ struct DevLevel {
   std::vector<double> panel_flops;  // flops of panel step k
   int64_t sum_np = 0, env_elems = 0, sum_owned = 0;
   int max_band = 0;               // max over tile rows of 1 + (R_I - I)
+  bool ras_wide = false;          // the staged solve in its one-CTA-per-SM form
   int ras_grid = 0;               // CTAs of the RAS solve and their subdomain lists
   int32_t *ras_cta_ptr = nullptr, *ras_cta_list = nullptr;
   bool fac_blocks = false;        // whole-block persistent factorisation on this level
@@ -186,8 +187,6 @@ Store level_store(const msp_hierarchy* h, int l) {
   return Store::F64;
 }
 size_t store_bytes(Store t) { return t == Store::F64 ? 8 : (t == Store::F32 ? 4 : 2); }
-// factored in FP32 (F32 and BF16 levels)
-bool level_f32(const msp_hierarchy* h, int l) { return level_store(h, l) != Store::F64; }
 
 void finish_level_stats(const HostLevel& H, DevLevel& D) {
   D.max_nt = 0;
@@ -244,6 +243,16 @@ void lpt_lists(const std::vector<int64_t>& cost, int G, std::vector<int32_t>& pt
   }
 }
 
+// Ring slots of the staged solve of level l in its form (wide or not).
+int ras_slots_of(const msp_hierarchy* h, int l, bool wide) {
+  const int nt = h->dev[l].max_nt;
+  switch (level_store(h, l)) {
+    case Store::F64: return ras_slots<double>(nt, wide);
+    case Store::F32: return ras_slots<float>(nt, wide);
+    default: return ras_slots<__nv_bfloat16>(nt, wide);
+  }
+}
+
 int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   HostLevel& H = h->host[l];
   DevLevel& D = h->dev[l];
@@ -288,16 +297,18 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   {
     int nsm = 0;
     MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    // RAS solve: one persistent CTA per SM, cost = stored envelope tiles (both
-    // sweeps read each once)
+    // RAS solve: persistent CTAs (1-3 per SM by precision, or the wide form
+    // when the level's tile band needs more ring slots), cost = stored
+    // envelope tiles (both sweeps read each once)
     std::vector<int64_t> cost(H.nsub);
     for (int p = 0; p < H.nsub; ++p) cost[p] = (H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems;
     std::vector<int32_t> cptr, clist;
     {
+      D.ras_wide = !direct_level(h, l) && ras_slots_of(h, l, false) < std::max(2, D.max_band);
       const Store st = level_store(h, l);
-      const int per_sm = st == Store::F64   ? ras_ctas_per_sm<double>()
-                         : st == Store::F32 ? ras_ctas_per_sm<float>()
-                                            : ras_ctas_per_sm<__nv_bfloat16>();
+      const int per_sm = st == Store::F64   ? ras_ctas_per_sm<double>(D.ras_wide)
+                         : st == Store::F32 ? ras_ctas_per_sm<float>(D.ras_wide)
+                                            : ras_ctas_per_sm<__nv_bfloat16>(D.ras_wide);
       lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
     }
     D.ras_grid = (int)cptr.size() - 1;
@@ -329,10 +340,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   }
   {
-    const Store st = level_store(h, l);
-    const int slots = st == Store::F64 ? ras_slots<double>(D.max_nt)
-                      : st == Store::F32 ? ras_slots<float>(D.max_nt)
-                                         : ras_slots<__nv_bfloat16>(D.max_nt);
+    const int slots = ras_slots_of(h, l, D.ras_wide);
     // the backward sweep holds a row's diagonal tile while the next R_I - I
     // tiles stream in: max_band slots are enough, and never deadlock
     const bool direct = direct_level(h, l);
@@ -520,15 +528,15 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   } else if (st == Store::BF16)
     launch_ras_solve<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(I->fac[l]), D.env, D.ras_cta_ptr,
                                     D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                                    D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, s);
+                                    D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
   else if (st == Store::F32)
     launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
                             D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
-                            D.dir_list, D.ndir, t, z, add, I->ras_err, s);
+                            D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
   else
     launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.ras_cta_ptr,
                              D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                             D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, s);
+                             D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
   ps.account(2.0 * (double)D.env_elems * es + (double)D.sum_np * 13 +

@@ -88,17 +88,19 @@ void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStre
 // diagonal tile while it reads that tile column, so there must be at least
 // 1 + (R_I - I) slots for every row I of the level (checked on the host at
 // set-up).
+// `wide`: one CTA of 16 consumer warps per SM (always the FP64 form); else
+// FP32 / BF16 run 2 / 3 smaller CTAs per SM, each with fewer ring slots.
 template <typename T>
-int ras_slots(int max_nt);
-// CTAs of k_ras_solve<T> that share an SM (the persistent grid is this x SMs)
+int ras_slots(int max_nt, bool wide);
+// CTAs of k_ras_solve that share an SM (the persistent grid is this x SMs)
 template <typename T>
-int ras_ctas_per_sm();
+int ras_ctas_per_sm(bool wide);
 template <typename T>
 void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, const int32_t* sub_ptr,
                       const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, cudaStream_t s);
+                      int* err, bool wide, cudaStream_t s);
 
 // ---- Krylov helpers (deterministic two-stage reductions)
 // out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles

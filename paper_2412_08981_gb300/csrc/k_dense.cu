@@ -357,10 +357,10 @@ __device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, A
 // every lane nearly the same loop length).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
-                                                    const int32_t* __restrict__ order, int k) {
+                                                    const int32_t* __restrict__ order, int k, int off) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
-  const int i = k + 1 + (blockIdx.x >> 2), q = blockIdx.x & 3;
+  const int i = k + 1 + off + (blockIdx.x >> 2), q = blockIdx.x & 3;
   if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
   AT* A = reinterpret_cast<AT*>(smraw);   // [16][65] rows of the panel tile
@@ -463,11 +463,11 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
 // diagonal pair only those on or below the diagonal).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
-                                                    const int32_t* __restrict__ order, int k) {
+                                                    const int32_t* __restrict__ order, int k, int pair0) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
   const int rem = E.last[E.trow[p] + k] - k;
-  const int pair = blockIdx.x >> 2, q = blockIdx.x & 3;
+  const int pair = pair0 + (blockIdx.x >> 2), q = blockIdx.x & 3;
   if (pair >= rem * (rem + 1) / 2) return;
   int a, b;
   pair_of(pair, a, b);
@@ -1117,7 +1117,7 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
 
 template <typename T>
 void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
-                       int max_rows, cudaStream_t s) {
+                       int off, int max_rows, cudaStream_t s) {
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = (16 * 65 + 64 * 64 + 64) * sizeof(AT);
@@ -1125,12 +1125,12 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_panel<T><<<dim3(4 * max_rows, nactive), 256, smem, s>>>(fac, E, order, k);
+  k_ldlt_panel<T><<<dim3(4 * max_rows, nactive), 256, smem, s>>>(fac, E, order, k, off);
 }
 
 template <typename T>
 void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
-                       int max_pairs, cudaStream_t s) {
+                       int pair0, int max_pairs, cudaStream_t s) {
   if (nactive <= 0 || max_pairs <= 0) return;
   using AT = typename Acc<T>::type;
   size_t smem = (64 * 16 + 64 * 65) * sizeof(AT);
@@ -1138,7 +1138,7 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_trail<T><<<dim3(4 * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k);
+  k_ldlt_trail<T><<<dim3(4 * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k, pair0);
 }
 
 namespace {
@@ -1318,9 +1318,9 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
                                   int64_t, T*, cudaStream_t);                                    \
   template void launch_ldlt_diag<T>(T*, const EnvDev&, const int32_t*, int, int, int*,           \
                                     cudaStream_t);                                               \
-  template void launch_ldlt_panel<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
+  template void launch_ldlt_panel<T>(T*, const EnvDev&, const int32_t*, int, int, int, int,      \
                                      cudaStream_t);                                              \
-  template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int,           \
+  template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int, int,      \
                                      cudaStream_t);                                              \
   template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
                                     const int32_t*, const int32_t*, const uint8_t*, int,         \

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -167,6 +168,10 @@ struct msp_instance {
   double* hpin = nullptr;  // pinned host staging
   cudaStream_t aux[2] = {nullptr, nullptr};  // coarser levels factor concurrently
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  // per level, for the tile-step factorisation: the stream of the work off
+  // the critical chain, and its events (diag done, critical panel done, bulk done)
+  std::vector<cudaStream_t> bulk;
+  std::vector<std::array<cudaEvent_t, 3>> bev;
   bool assembled = false, factored = false;
   Profile prof;
 };
@@ -452,6 +457,16 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
     ps.account(0, D.fac_flops);
     return;
   }
+  // Tile steps with one step of lookahead.  On `s`, the chain the next
+  // diagonal tile depends on: diagonal tile k, panel tile (k+1, k), trailing
+  // pair (k+1, k+1).  On the level's bulk stream, the other panel tiles and
+  // pairs of step k, which overlap with diagonal tile k+1.  Panel tile
+  // (k+1, k) and the bulk panels of step k need the bulk pairs of step k-1.
+  cudaStream_t sb = I->bulk[l];
+  cudaEvent_t ev_diag = I->bev[l][0], ev_cp = I->bev[l][1], ev_bulk = I->bev[l][2];
+  cudaEventRecord(ev_bulk, s);  // the extraction
+  cudaStreamWaitEvent(sb, ev_bulk, 0);
+  bool bulk_pending = false;
   for (int k = 0; k < D.max_nt; ++k) {
     int na = D.active[k];
     {
@@ -459,20 +474,43 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
       launch_ldlt_diag<T>(fac, D.env, D.sub_order, na, k, I->info, s);
       ps.account((double)na * 2 * 4096 * sizeof(T), (double)na * (2.0 * 64 * 64 * 64 / 3));
     }
-    int rows = D.max_rows[k];
-    if (rows > 0) {
+    const int rows = D.max_rows[k];
+    if (rows <= 0) continue;
+    const int pairs = rows * (rows + 1) / 2;
+    cudaEventRecord(ev_diag, s);
+    if (rows > 1) {
+      cudaStreamWaitEvent(sb, ev_diag, 0);
+      ProfScope ps(I->prof, PK_LDLT_PANEL, sb);
+      launch_ldlt_panel<T>(fac, D.env, D.sub_order, na, k, 1, rows - 1, sb);
+      ps.account(0, D.panel_flops[k] * (rows - 1) / rows);
+    }
+    if (bulk_pending) {
+      cudaStreamWaitEvent(s, ev_bulk, 0);
+      bulk_pending = false;
+    }
+    {
+      ProfScope ps(I->prof, PK_LDLT_PANEL, s);
+      launch_ldlt_panel<T>(fac, D.env, D.sub_order, na, k, 0, 1, s);
+      ps.account(0, D.panel_flops[k] / rows);
+    }
+    cudaEventRecord(ev_cp, s);
+    {
+      ProfScope ps(I->prof, PK_LDLT_TRAIL, s);
+      launch_ldlt_trail<T>(fac, D.env, D.sub_order, na, k, 0, 1, s);
+      ps.account(0, D.trail_flops[k] / pairs);
+    }
+    if (pairs > 1) {
+      cudaStreamWaitEvent(sb, ev_cp, 0);
       {
-        ProfScope ps(I->prof, PK_LDLT_PANEL, s);
-        launch_ldlt_panel<T>(fac, D.env, D.sub_order, na, k, rows, s);
-        ps.account(0, D.panel_flops[k]);
+        ProfScope ps(I->prof, PK_LDLT_TRAIL, sb);
+        launch_ldlt_trail<T>(fac, D.env, D.sub_order, na, k, 1, pairs - 1, sb);
+        ps.account(0, D.trail_flops[k] * (pairs - 1) / pairs);
       }
-      {
-        ProfScope ps(I->prof, PK_LDLT_TRAIL, s);
-        launch_ldlt_trail<T>(fac, D.env, D.sub_order, na, k, rows * (rows + 1) / 2, s);
-        ps.account(0, D.trail_flops[k]);
-      }
+      cudaEventRecord(ev_bulk, sb);
+      bulk_pending = true;
     }
   }
+  if (bulk_pending) cudaStreamWaitEvent(s, ev_bulk, 0);
 }
 
 int factor_all(msp_instance* I) {
@@ -828,6 +866,13 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     MSP_CUDA(cudaEventCreateWithFlags(&I->join[a], cudaEventDisableTiming));
   }
   MSP_CUDA(cudaEventCreateWithFlags(&I->fork, cudaEventDisableTiming));
+  I->bulk.assign(L, nullptr);
+  I->bev.assign(L, {nullptr, nullptr, nullptr});
+  for (int l = 0; l < L; ++l) {
+    if (h->dev[l].fac_blocks) continue;  // only the tile-step path uses them
+    MSP_CUDA(cudaStreamCreateWithFlags(&I->bulk[l], cudaStreamNonBlocking));
+    for (auto& e : I->bev[l]) MSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   MSP_CUDA(cudaMemset(I->ras_err, 0, sizeof(int)));
   return MSP_OK;
 }
@@ -1003,6 +1048,11 @@ int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream, msp
       if (I->join[a]) cudaEventDestroy(I->join[a]);
     }
     if (I->fork) cudaEventDestroy(I->fork);
+    for (auto b : I->bulk)
+      if (b) cudaStreamDestroy(b);
+    for (auto& e : I->bev)
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
     std::lock_guard<std::mutex> lk(h->mu);
     h->instance_bytes -= need;
     return rc;
@@ -1030,6 +1080,11 @@ void msp_free_instance(msp_instance* I) {
     if (I->join[a]) cudaEventDestroy(I->join[a]);
   }
   if (I->fork) cudaEventDestroy(I->fork);
+  for (auto b : I->bulk)
+    if (b) cudaStreamDestroy(b);
+  for (auto& e : I->bev)
+    for (auto x : e)
+      if (x) cudaEventDestroy(x);
   I->prof.destroy();
   I->arena.release();
   if (I->hpin) cudaFreeHost(I->hpin);

@@ -49,12 +49,15 @@ void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
 template <typename T>
 void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                       int* info, cudaStream_t s);
+// panel tiles i = k+1+off .. k+off+max_rows of step k
 template <typename T>
 void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
-                       int max_rows, cudaStream_t s);
+                       int off, int max_rows, cudaStream_t s);
+// trailing pairs pair0 .. pair0+max_pairs-1 of step k, numbered (1,1), (2,1),
+// (2,2), (3,1), ... from k+1 (pair 0 is the next diagonal tile)
 template <typename T>
 void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
-                       int max_pairs, cudaStream_t s);
+                       int pair0, int max_pairs, cudaStream_t s);
 // The whole L D L^T of many blocks in one persistent launch: CTA b factors
 // cta_list[cta_ptr[b] .. cta_ptr[b+1]) through every tile step.
 template <typename T>

@@ -42,6 +42,31 @@ DESCR = {
 }
 
 
+# ------------------------------------------------------- replicas (N > 1)
+def max_over_ranks(x: float) -> float:
+    """The maximum of a per-rank scalar over all ranks (x itself with one rank).
+    NCCL reduces on the rank's GPU, gloo on the host."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_request(rank: int, i: int) -> int:
+    """Request number (the seed of mu) of the i-th solve of replica `rank`:
+    disjoint between ranks for i < 100000."""
+    return rank * 100000 + i
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms_slowest: float) -> float:
+    """Units of all ranks per second of the slowest rank."""
+    return units_per_rank * world / (ms_slowest / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,7 +232,7 @@ def run_msp(args):
     stream = torch.cuda.Stream()
 
     def mu_of(i):
-        return syn.mu_draw(rank * 100000 + i)
+        return syn.mu_draw(replica_request(rank, i))
 
     def measure(precision, steps, warmup, transfer="bary", lv=None, opts=None):
         h = P.Hierarchy(levels if lv is None else lv, precision=precision,
@@ -382,21 +407,13 @@ def run_msp(args):
                 "timing": "host wall clock from the first arrival to the last completion"}
 
     res = measure(args.precision, args.steps, args.warmup)
-    ms = res["ms"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(res["ms"])
+    value = whole_job_rate(args.steps, world, ms)
     mixed = None
     if not args.no_mixed and args.precision == "f64":
         mres = measure("f32", args.steps, args.warmup)
-        mms = mres["ms"]
-        if world > 1:
-            t = torch.tensor([mms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mms = float(t.item())
-        mval = args.steps * world / (mms / 1e3)
+        mms = max_over_ranks(mres["ms"])
+        mval = whole_job_rate(args.steps, world, mms)
         err = float(np.linalg.norm(mres["x"] - res["x"]) / np.linalg.norm(res["x"]))
         mixed = {"precision": "f32 subdomain factors, FP64 outer loop/SpMV/coarsest",
                  "value": mval, "unit": UNIT, "speedup_vs_f64": mval / value,
@@ -423,9 +440,8 @@ def run_msp(args):
             bres = measure_batched("f32", max(args.steps, 2 * args.batch), args.warmup, args.batch)
             bval = bres["value"]
             if world > 1:
-                t = torch.tensor([bres["wall_s"]], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                bval = max(args.steps, 2 * args.batch) * world / float(t.item())
+                bval = whole_job_rate(max(args.steps, 2 * args.batch), world,
+                                      1e3 * max_over_ranks(bres["wall_s"]))
             mixed["batched"] = {
                 "instances": args.batch, "value": bval, "unit": UNIT,
                 "speedup_vs_f64": bval / value,

@@ -283,7 +283,8 @@ def run_msp(args):
         prof = inst.profile()
         launches = int(sum(v["launches"] for v in prof.values()))
         grids = {"factor_ctas": [h.info(l)["fac_ctas"] for l in range(h.nlevels)],
-                 "ras_ctas": [h.info(l)["ras_ctas"] for l in range(h.nlevels)]}
+                 "ras_ctas": [h.info(l)["ras_ctas"] for l in range(h.nlevels)],
+                 "spmv_lanes_J_P_R": [h.info(l)["spmv_lanes"] for l in range(h.nlevels)]}
         out = dict(ms=ms, lat=lat, iters=list(iters), relres=list(relres), prof=prof, dominant=dominant, grids=grids,
                    shares=shares, kernel_ms=kernel_ms, launches=launches, clocks=clocks,
                    x=x.cpu().numpy())

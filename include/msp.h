@@ -184,6 +184,9 @@ typedef struct msp_level_info {
   int32_t fac_ctas;           /* CTAs of the one persistent factorisation launch of this level
                                  (0: tile-step launches, or a host-only hierarchy) */
   int32_t ras_ctas;           /* CTAs of the staged RAS solve (0: directly solved level) */
+  int32_t spmv_lanes[3];      /* lanes per row of the SpMV schedules picked at load time by
+                                 timing 4/8/16/32 on the device: J, prolongation, restriction
+                                 (0: host-only hierarchy or no such operator) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
 

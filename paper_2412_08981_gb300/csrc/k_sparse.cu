@@ -4,6 +4,11 @@
 // are bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include <cstdint>
 
 #include "msp_kernels.h"
@@ -256,17 +261,84 @@ void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t*
 }
 
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
-                 const double* x, double* y, const double* r, int mode, int avg_row_nnz,
+                 const double* x, double* y, const double* r, int mode, int lpr,
                  cudaStream_t s) {
   if (nrows <= 0) return;
-  if (avg_row_nnz <= 5)
-    k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
-  else if (avg_row_nnz <= 20)
-    k_spmv<8><<<nblk((int64_t)nrows * 8, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
-  else if (avg_row_nnz <= 64)
-    k_spmv<16><<<nblk((int64_t)nrows * 16, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
-  else
-    k_spmv<32><<<nblk((int64_t)nrows * 32, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+  switch (lpr) {
+    case 4:
+      k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+      break;
+    case 8:
+      k_spmv<8><<<nblk((int64_t)nrows * 8, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+      break;
+    case 16:
+      k_spmv<16><<<nblk((int64_t)nrows * 16, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+      break;
+    default:
+      k_spmv<32><<<nblk((int64_t)nrows * 32, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+      break;
+  }
+}
+
+// Autotuner of the SpMV schedule (lanes per row): every candidate is timed
+// with CUDA events on the matrix itself (zero values, zero x: the memory
+// traffic and the schedule are those of the real products) and the fastest
+// kept.  The choice is cached per structure (rows, nnz, hash of rowptr and
+// col) for the life of the process, so that identical matrices always get
+// the same schedule (and bitwise the same sums).
+int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
+              const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
+              cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int64_t, uint64_t>, int> cache;
+  const int64_t nnz = h_col.size();
+  if (nrows <= 0 || nnz == 0) return 8;
+  uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the structure
+  auto mix = [&](int32_t v) {
+    for (int b = 0; b < 4; ++b) {
+      hsh ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      hsh *= 1099511628211ull;
+    }
+  };
+  for (int32_t v : h_rowptr) mix(v);
+  for (int32_t v : h_col) mix(v);
+  const auto key = std::make_tuple(nrows, nnz, hsh);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  double *val = nullptr, *x = nullptr, *y = nullptr;
+  int best = 8;
+  if (cudaMalloc(&val, nnz * sizeof(double)) == cudaSuccess &&
+      cudaMalloc(&x, (size_t)ncols * sizeof(double)) == cudaSuccess &&
+      cudaMalloc(&y, (size_t)nrows * sizeof(double)) == cudaSuccess) {
+    cudaMemsetAsync(val, 0, nnz * sizeof(double), s);
+    cudaMemsetAsync(x, 0, (size_t)ncols * sizeof(double), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int lpr : {4, 8, 16, 32}) {
+      launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, lpr, s);  // warm-up
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 5; ++rep) launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, lpr, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = lpr;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaFree(val);
+  cudaFree(x);
+  cudaFree(y);
+  cudaGetLastError();
+  cache[key] = best;
+  return best;
 }
 
 void launch_multidot(const double* V, int64_t ld, int nv, const double* w, int64_t n,

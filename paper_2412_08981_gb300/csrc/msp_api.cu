@@ -98,7 +98,7 @@ struct DevArena {
 struct DevLevel {
   int n = 0, m = 0;
   int64_t nnz = 0;
-  int avg_A = 15, avg_P = 4, avg_PT = 32;
+  int lpr_A = 8, lpr_P = 4, lpr_PT = 16;  // SpMV lanes per row (autotuned at load)
   int32_t *rowptr = nullptr, *col = nullptr, *diag = nullptr, *cptr = nullptr, *contrib = nullptr;
   uint8_t *nzflag = nullptr, *dir = nullptr;
   int32_t* dir_list = nullptr;
@@ -265,7 +265,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.n = H.n;
   D.m = H.m;
   D.nnz = (int64_t)H.col.size();
-  D.avg_A = (int)std::max<int64_t>(1, D.nnz / std::max(1, H.n));
+
   D.xyz = A.upload(H.xyz);
   D.tets = A.upload(H.tets);
   D.dir = A.upload(H.dir);
@@ -273,6 +273,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.ndir = (int)H.dir_list.size();
   D.rowptr = A.upload(H.rowptr);
   D.col = A.upload(H.col);
+  if (A.ok) D.lpr_A = tune_spmv(D.rowptr, D.col, H.n, H.n, H.rowptr, H.col, s);
   D.diag = A.upload(H.diag);
   D.cptr = A.upload(H.cptr);
   D.contrib = A.upload(H.contrib);
@@ -367,8 +368,11 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.PT_rowptr = A.upload(H.PT_rowptr);
     D.PT_col = A.upload(H.PT_col);
     D.PT_val = A.upload(H.PT_val);
-    D.avg_P = (int)std::max<int64_t>(1, D.P_nnz / std::max(1, H.n));
-    D.avg_PT = (int)std::max<int64_t>(1, D.PT_nnz / std::max(1, h->host[l + 1].n));
+    if (A.ok) {
+      const int nc = h->host[l + 1].n;
+      D.lpr_P = tune_spmv(D.P_rowptr, D.P_col, H.n, nc, H.P_rowptr, H.P_col, s);
+      D.lpr_PT = tune_spmv(D.PT_rowptr, D.PT_col, nc, H.n, H.PT_rowptr, H.PT_col, s);
+    }
   }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   int* bad = A.alloc<int>(1);
@@ -586,7 +590,7 @@ void spmv(msp_instance* I, int l, const double* x, double* y, const double* r, i
           cudaStream_t s) {
   DevLevel& D = I->h->dev[l];
   ProfScope ps(I->prof, PK_SPMV, s);
-  launch_spmv(D.rowptr, D.col, I->val[l], D.n, x, y, r, mode, D.avg_A, s);
+  launch_spmv(D.rowptr, D.col, I->val[l], D.n, x, y, r, mode, D.lpr_A, s);
   ps.account((double)D.nnz * 12 + (double)(D.n + 1) * 4 + (double)D.n * (mode == SPMV_SET ? 16 : 24),
              2.0 * (double)D.nnz);
 }
@@ -597,9 +601,9 @@ void transfer(msp_instance* I, int l, bool restrict_, const double* x, double* y
   int nc = I->h->dev[l + 1].n;
   ProfScope ps(I->prof, PK_TRANSFER, s);
   if (restrict_)
-    launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, D.avg_PT, s);
+    launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, D.lpr_PT, s);
   else
-    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, D.avg_P, s);
+    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, D.lpr_P, s);
   double rows = restrict_ ? nc : D.n, cols = restrict_ ? D.n : nc;
   double nnz = (double)(restrict_ ? D.PT_nnz : D.P_nnz);
   ps.account(nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16), 2.0 * nnz);
@@ -1015,10 +1019,14 @@ int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) 
   info->R_nnz = (int64_t)H.PT_col.size();
   info->fac_ctas = 0;
   info->ras_ctas = 0;
+  info->spmv_lanes[0] = info->spmv_lanes[1] = info->spmv_lanes[2] = 0;
   if (!h->host_only) {
     const msp::DevLevel& D = h->dev[level];
     info->fac_ctas = D.fac_blocks ? D.fac_grid : 0;
     info->ras_ctas = H.direct ? 0 : D.ras_grid;
+    info->spmv_lanes[0] = D.lpr_A;
+    info->spmv_lanes[1] = H.P_col.empty() ? 0 : D.lpr_P;
+    info->spmv_lanes[2] = H.PT_col.empty() ? 0 : D.lpr_PT;
   }
   return MSP_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -24,10 +25,16 @@ void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t*
 
 // ---- CSR SpMV family (FP64)
 enum SpmvMode { SPMV_SET = 0, SPMV_SUB_FROM = 1, SPMV_ADD = 2, SPMV_RESIDUAL = 3 };
-// SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x
+// SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x;
+// lpr = lanes per row (4, 8, 16 or 32), picked by tune_spmv
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
-                 const double* x, double* y, const double* r, int mode, int avg_row_nnz,
+                 const double* x, double* y, const double* r, int mode, int lpr,
                  cudaStream_t s);
+// the fastest lanes-per-row schedule for this matrix, measured on the device
+// (cached per structure for the life of the process)
+int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
+              const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
+              cudaStream_t s);
 
 // ---- dense subdomain blocks (templated on the factor type T = double | float)
 // Device view of a level's tile envelopes (see msp_internal.h).

@@ -84,7 +84,7 @@ class msp_level_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("nnz", C.c_int64),
                 ("n_sub", C.c_int32), ("sub_dofs", C.c_int64), ("factor_elems", C.c_int64),
                 ("P_nnz", C.c_int64), ("R_nnz", C.c_int64), ("fac_ctas", C.c_int32),
-                ("ras_ctas", C.c_int32)]
+                ("ras_ctas", C.c_int32), ("spmv_lanes", C.c_int32 * 3)]
 
 
 class msp_kernel_profile(C.Structure):
@@ -274,7 +274,8 @@ class Hierarchy:
     def info(self, level=0) -> dict:
         inf = msp_level_info()
         _check(load().msp_hierarchy_info(self.h, level, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in msp_level_info._fields_}
+        return {k: (list(getattr(inf, k)) if k == "spmv_lanes" else getattr(inf, k))
+                for k, _ in msp_level_info._fields_}
 
     def array(self, level, name) -> np.ndarray:
         lib = load()

@@ -463,6 +463,20 @@ def test_one_level_ras(P, orc, torch):
     assert abs(st["iterations"] - so["iters"]) <= 1
 
 
+def test_spmv_schedules_are_tuned_and_stable(P, torch):
+    """The SpMV lanes-per-row schedule of every operator is picked on the device
+    at load time; a second load of the same meshes gets the same choices."""
+    levels, w = workload("cube16_3lvl")
+    h1 = make_hierarchy(levels, w, P)
+    h2 = make_hierarchy(levels, w, P)
+    for l in range(len(levels)):
+        a, b = h1.info(l)["spmv_lanes"], h2.info(l)["spmv_lanes"]
+        assert a == b
+        assert a[0] in (4, 8, 16, 32)
+        if l + 1 < len(levels):
+            assert a[1] in (4, 8, 16, 32) and a[2] in (4, 8, 16, 32)
+
+
 def test_results_reproducible_bitwise(P, torch):
     levels, w = workload("cube16_3lvl")
     h = make_hierarchy(levels, w, P)

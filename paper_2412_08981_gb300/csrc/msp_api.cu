@@ -172,6 +172,10 @@ struct msp_instance {
   // the critical chain, and its events (diag done, critical panel done, bulk done)
   std::vector<cudaStream_t> bulk;
   std::vector<std::array<cudaEvent_t, 3>> bev;
+  // the factorisation as a CUDA graph (see factor_all)
+  int fac_calls = 0;
+  cudaGraphExec_t fac_graph = nullptr;
+  msp_kernel_profile fac_graph_counts[PK_COUNT] = {};
   bool assembled = false, factored = false;
   Profile prof;
 };
@@ -514,10 +518,13 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
       bulk_pending = true;
     }
   }
-  if (bulk_pending) cudaStreamWaitEvent(s, ev_bulk, 0);
+  cudaEventRecord(ev_bulk, sb);  // join the bulk stream back (always: graph capture needs it)
+  cudaStreamWaitEvent(s, ev_bulk, 0);
 }
 
-int factor_all(msp_instance* I) {
+// Enqueues the whole factorisation on the instance stream (with forks onto
+// the auxiliary and bulk streams, all joined back).
+int enqueue_factor(msp_instance* I) {
   msp_hierarchy* h = I->h;
   MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
   // The levels are independent: level 0 on the instance stream, the coarser
@@ -546,6 +553,52 @@ int factor_all(msp_instance* I) {
     MSP_CUDA(cudaStreamWaitEvent(I->stream, I->join[a], 0));
   }
   MSP_CUDA(cudaGetLastError());
+  return MSP_OK;
+}
+
+// The factorisation runs the same launches for every mu, so from its second
+// call on it is replayed from a CUDA graph captured once (one launch for
+// hundreds of kernels, and no host gaps in the coarsest block's chain).  The
+// graph is used only while no kernel class is being timed; the per-class
+// launch, byte and flop counts of one factorisation are added per replay.
+int factor_all(msp_instance* I) {
+  msp_hierarchy* h = I->h;
+  const bool graph_ok = I->prof.mask == 0;
+  if (graph_ok && !I->fac_graph && I->fac_calls >= 1) {
+    msp_kernel_profile before[PK_COUNT];
+    std::memcpy(before, I->prof.c, sizeof(before));
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rc = enqueue_factor(I);
+      const cudaError_t ec = cudaStreamEndCapture(I->stream, &g);
+      if (rc == MSP_OK && ec == cudaSuccess && g &&
+          cudaGraphInstantiate(&I->fac_graph, g, 0) == cudaSuccess) {
+        for (int k = 0; k < PK_COUNT; ++k) {
+          I->fac_graph_counts[k].launches = I->prof.c[k].launches - before[k].launches;
+          I->fac_graph_counts[k].bytes = I->prof.c[k].bytes - before[k].bytes;
+          I->fac_graph_counts[k].flops = I->prof.c[k].flops - before[k].flops;
+        }
+      } else {
+        I->fac_graph = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    std::memcpy(I->prof.c, before, sizeof(before));  // counted again per replay below
+    cudaGetLastError();
+    msp::g_last_error.clear();
+  }
+  if (graph_ok && I->fac_graph) {
+    MSP_CUDA(cudaGraphLaunch(I->fac_graph, I->stream));
+    for (int k = 0; k < PK_COUNT; ++k) {
+      I->prof.c[k].launches += I->fac_graph_counts[k].launches;
+      I->prof.c[k].bytes += I->fac_graph_counts[k].bytes;
+      I->prof.c[k].flops += I->fac_graph_counts[k].flops;
+    }
+  } else {
+    const int rc = enqueue_factor(I);
+    if (rc) return rc;
+  }
+  I->fac_calls++;
   int hinfo = 0;
   MSP_CUDA(cudaMemcpyAsync(&hinfo, I->info, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
   MSP_CUDA(cudaStreamSynchronize(I->stream));
@@ -1093,6 +1146,7 @@ void msp_free_instance(msp_instance* I) {
   for (auto& e : I->bev)
     for (auto x : e)
       if (x) cudaEventDestroy(x);
+  if (I->fac_graph) cudaGraphExecDestroy(I->fac_graph);
   I->prof.destroy();
   I->arena.release();
   if (I->hpin) cudaFreeHost(I->hpin);

@@ -463,6 +463,32 @@ def test_one_level_ras(P, orc, torch):
     assert abs(st["iterations"] - so["iters"]) <= 1
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
+def test_factorisation_graph_replay_is_bitwise_the_same(P, torch, precision):
+    """From its second call on the factorisation replays a captured CUDA graph
+    (while no kernel class is timed): same factors bit for bit, same launch
+    counts per factorisation."""
+    levels = syn.hierarchy((16, 8, 4), ((4, 4, 4), (2, 2, 2)))
+    w = dict(delta=2, nu=2, coef="cosexp", scale=1.0, load="one", restart=30)
+    h = make_hierarchy(levels, w, P, precision=precision)
+    inst = h.assemble(syn.mu_draw(3), stream=torch.cuda.current_stream())
+    facs, counts = [], []
+    for call in range(3):  # direct, capture + replay, replay
+        inst.profile_reset()
+        inst.factor()
+        prof = inst.profile()
+        counts.append({k: v["launches"] for k, v in prof.items()})
+        dt = np.uint16 if precision == "bf16" else (np.float32 if precision == "f32" else np.float64)
+        facs.append([inst.array(l, "factor", -1 if l == 2 else 0, dtype=dt if l < 2 else np.float64)
+                     for l in range(3)])
+    for call in (1, 2):
+        assert counts[call] == counts[0]
+        for a, b in zip(facs[0], facs[call]):
+            np.testing.assert_array_equal(a, b)
+    x = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    assert inst.solve(x, rtol=1e-10)["status"] == 0
+
+
 def test_spmv_schedules_are_tuned_and_stable(P, torch):
     """The SpMV lanes-per-row schedule of every operator is picked on the device
     at load time; a second load of the same meshes gets the same choices."""

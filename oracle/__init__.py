@@ -29,7 +29,7 @@ Iteration counts of the preconditioned solver: parity unpinned (the paper
 reports counts only for other PDEs and meshes).
 """
 from .oracle import (Oracle, build, lib, tet_stiffness, lu_factor, lu_solve, build_interp,
-                     build_mls, mesh_h)
+                     build_mls, mesh_h, ilu_factor)
 
 __all__ = ["Oracle", "build", "lib", "tet_stiffness", "lu_factor", "lu_solve", "build_interp",
-           "build_mls", "mesh_h"]
+           "build_mls", "mesh_h", "ilu_factor"]

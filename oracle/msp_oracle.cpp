@@ -26,6 +26,7 @@
 //   * k(x;mu) is evaluated at the tet centroid, f at the vertices (vertex rule).
 // Compiled with -O2 -ffp-contract=off, OpenMP over subdomains and rows only.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -45,6 +46,8 @@ struct Subdomain {
   std::vector<int> dofs;           // sorted global DoF ids (non-Dirichlet)
   std::vector<unsigned char> own;  // 1 where the DoF is owned (R^0 rows)
   std::vector<double> lu;          // dense n x n row-major, Doolittle LU in place
+  Csr ilu;                         // ILU(p) instead: unit L below, U on and above the diagonal
+  std::vector<int> udiag;          // position of the diagonal entry in each row of ilu
 };
 
 struct Level {
@@ -59,6 +62,7 @@ struct Level {
   Subdomain coarse;       // used on the coarsest level: all interior DoFs
   Csr P;                  // interpolation from level+1 (coarse) to this level
   Csr PT;                 // restriction to level+1: P^T, or the MLS operator
+  int ilu_fill = -1;      // subdomain solver: dense LU (-1) or ILU(p), p = ilu_fill
 };
 
 struct Oracle {
@@ -281,9 +285,129 @@ void extract_dense(const Csr& A, const Subdomain& S, std::vector<double>& D) {
   }
 }
 
-int factor_sub(const Csr& A, Subdomain& S) {
+// ------------------------------------------------ ILU(p) (Section 4.4's solver)
+// Incomplete LU of a subdomain block with the level-of-fill pattern: entries of
+// A_p have level 0; eliminating with row k gives entry (i, j) the level
+// lev(i,k) + lev(k,j) + 1, the smaller of its levels is kept, and entries of
+// level > p are dropped.  The numbers then follow Gaussian elimination in IKJ
+// order restricted to that pattern (the updates of dropped entries are lost).
+
+// A_p as a local CSR (rows and columns in the sorted DoF order).
+void local_block(const Csr& A, const Subdomain& S, Csr& B) {
+  const int n = (int)S.dofs.size();
+  B.rowptr.assign(n + 1, 0);
+  B.col.clear();
+  B.val.clear();
+  for (int li = 0; li < n; ++li) {
+    const int g = S.dofs[li];
+    for (int q = A.rowptr[g]; q < A.rowptr[g + 1]; ++q) {
+      auto it = std::lower_bound(S.dofs.begin(), S.dofs.end(), A.col[q]);
+      if (it != S.dofs.end() && *it == A.col[q]) {
+        B.col.push_back((int)(it - S.dofs.begin()));
+        B.val.push_back(A.val[q]);
+      }
+    }
+    B.rowptr[li + 1] = (int)B.col.size();
+  }
+}
+
+// The ILU(p) pattern of B (sorted columns per row, diagonal included).
+void ilu_symbolic(const Csr& B, int p, Csr& F) {
+  const int n = (int)B.rowptr.size() - 1;
+  std::vector<std::vector<int>> cols(n), levs(n);
+  std::vector<int> lev(n, INT32_MAX);
+  for (int i = 0; i < n; ++i) {
+    std::set<int> row;
+    for (int q = B.rowptr[i]; q < B.rowptr[i + 1]; ++q) {
+      row.insert(B.col[q]);
+      lev[B.col[q]] = 0;
+    }
+    row.insert(i);
+    lev[i] = 0;
+    for (auto it = row.begin(); it != row.end() && *it < i; ++it) {
+      const int k = *it;
+      if (lev[k] > p) continue;
+      for (size_t t = 0; t < cols[k].size(); ++t) {
+        const int j = cols[k][t];
+        if (j <= k) continue;
+        const int nl = lev[k] + levs[k][t] + 1;
+        if (nl > p) continue;
+        if (nl < lev[j]) lev[j] = nl;
+        row.insert(j);  // std::set iterators stay valid; j > k, so the loop reaches it
+      }
+    }
+    for (int j : row)
+      if (lev[j] <= p) {
+        cols[i].push_back(j);
+        levs[i].push_back(lev[j]);
+      }
+    for (int j : row) lev[j] = INT32_MAX;
+  }
+  F.rowptr.assign(n + 1, 0);
+  F.col.clear();
+  for (int i = 0; i < n; ++i) {
+    F.col.insert(F.col.end(), cols[i].begin(), cols[i].end());
+    F.rowptr[i + 1] = (int)F.col.size();
+  }
+  F.val.assign(F.col.size(), 0.0);
+}
+
+// IKJ elimination on the pattern of F; returns -1 on a zero or non-finite pivot.
+int ilu_numeric(const Csr& B, Csr& F, std::vector<int>& udiag) {
+  const int n = (int)F.rowptr.size() - 1;
+  udiag.assign(n, -1);
+  std::vector<int> pos(n, -1);
+  for (int i = 0; i < n; ++i) {
+    for (int q = F.rowptr[i]; q < F.rowptr[i + 1]; ++q) {
+      pos[F.col[q]] = q;
+      F.val[q] = 0.0;
+      if (F.col[q] == i) udiag[i] = q;
+    }
+    for (int q = B.rowptr[i]; q < B.rowptr[i + 1]; ++q) F.val[pos[B.col[q]]] = B.val[q];
+    for (int q = F.rowptr[i]; q < F.rowptr[i + 1] && F.col[q] < i; ++q) {
+      const int k = F.col[q];
+      const double piv = F.val[udiag[k]];
+      if (piv == 0.0 || !std::isfinite(piv)) return -1;
+      const double lik = F.val[q] / piv;
+      F.val[q] = lik;
+      for (int t = udiag[k] + 1; t < F.rowptr[k + 1]; ++t)
+        if (pos[F.col[t]] >= 0) F.val[pos[F.col[t]]] -= lik * F.val[t];
+    }
+    for (int q = F.rowptr[i]; q < F.rowptr[i + 1]; ++q) pos[F.col[q]] = -1;
+    if (udiag[i] < 0 || !(std::isfinite(F.val[udiag[i]])) || F.val[udiag[i]] == 0.0) return -1;
+  }
+  return 0;
+}
+
+// x <- (L U)^{-1} x with the unit lower L and upper U of F.
+void ilu_solve(const Csr& F, const std::vector<int>& udiag, double* x) {
+  const int n = (int)F.rowptr.size() - 1;
+  for (int i = 0; i < n; ++i) {
+    double s = x[i];
+    for (int q = F.rowptr[i]; q < udiag[i]; ++q) s -= F.val[q] * x[F.col[q]];
+    x[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int q = udiag[i] + 1; q < F.rowptr[i + 1]; ++q) s -= F.val[q] * x[F.col[q]];
+    x[i] = s / F.val[udiag[i]];
+  }
+}
+
+int factor_sub(const Csr& A, Subdomain& S, int ilu_fill = -1) {
+  if (ilu_fill >= 0) {
+    Csr B;
+    local_block(A, S, B);
+    if (S.ilu.rowptr.empty()) ilu_symbolic(B, ilu_fill, S.ilu);
+    return ilu_numeric(B, S.ilu, S.udiag);
+  }
   extract_dense(A, S, S.lu);
   return lu_factor((int)S.dofs.size(), S.lu.data());
+}
+
+void sub_solve(const Subdomain& S, double* t) {
+  if (!S.ilu.rowptr.empty()) ilu_solve(S.ilu, S.udiag, t);
+  else lu_solve((int)S.dofs.size(), S.lu.data(), t);
 }
 
 // ------------------------------------------------------------- RAS (2.2)
@@ -298,7 +422,7 @@ void ras_apply(const Level& L, const double* r, double* z) {
     int n = (int)S.dofs.size();
     std::vector<double> t(n);
     for (int li = 0; li < n; ++li) t[li] = r[S.dofs[li]];
-    lu_solve(n, S.lu.data(), t.data());
+    sub_solve(S, t.data());
     for (int li = 0; li < n; ++li)
       if (S.own[li]) z[S.dofs[li]] += t[li];  // each DoF is owned once: no race
   }
@@ -748,7 +872,7 @@ typedef struct {
 
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
                  int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
-                 int restrict_scaling, int coarse_ras) {
+                 int restrict_scaling, int coarse_ras, int ilu_fine, int ilu_coarse) {
   if (nlevels < 1 || transfer < 0 || transfer > 1) return nullptr;
   Oracle* o = new Oracle();
   o->coarse_ras = coarse_ras ? 1 : 0;
@@ -764,6 +888,7 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
   o->lv.resize(nlevels);
   for (int l = 0; l < nlevels; ++l) {
     Level& L = o->lv[l];
+    L.ilu_fill = (l == 0) ? ilu_fine : ilu_coarse;
     L.n = lv[l].n_nodes;
     L.m = lv[l].n_tets;
     L.xyz.assign(lv[l].xyz, lv[l].xyz + 3 * (size_t)L.n);
@@ -817,7 +942,7 @@ int orc_factor(void* h) {
     if (l + 1 < o->lv.size() || o->coarse_ras) {
       int np = (int)L.subs.size();
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
-      for (int p = 0; p < np; ++p) bad += factor_sub(L.A, L.subs[p]) ? 1 : 0;
+      for (int p = 0; p < np; ++p) bad += factor_sub(L.A, L.subs[p], L.ilu_fill) ? 1 : 0;
     } else {
       bad += factor_sub(L.A, L.coarse) ? 1 : 0;
     }
@@ -839,7 +964,7 @@ int orc_factor_range(void* h, int level, int p0, int p1) {
   Level& L = o->lv[level];
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
-  for (int p = p0; p < p1; ++p) bad += factor_sub(L.A, L.subs[p]) ? 1 : 0;
+  for (int p = p0; p < p1; ++p) bad += factor_sub(L.A, L.subs[p], L.ilu_fill) ? 1 : 0;
   return bad ? -1 : 0;
 }
 
@@ -870,7 +995,7 @@ int orc_ras_apply_range(void* h, int level, int p0, int p1, const double* r, dou
     int n = (int)S.dofs.size();
     std::vector<double> t(n);
     for (int li = 0; li < n; ++li) t[li] = r[S.dofs[li]];
-    lu_solve(n, S.lu.data(), t.data());
+    sub_solve(S, t.data());
     for (int li = 0; li < n; ++li)
       if (S.own[li]) z[S.dofs[li]] = t[li];
   }
@@ -890,9 +1015,9 @@ int orc_sub_solve(void* h, int level, int p, const double* r, double* y) {
   const Level& L = o->lv[level];
   const Subdomain& S = (p < 0) ? L.coarse : L.subs[p];
   int n = (int)S.dofs.size();
-  if (S.lu.size() != (size_t)n * n) return -1;
+  if (S.lu.size() != (size_t)n * n && S.ilu.rowptr.empty()) return -1;
   for (int li = 0; li < n; ++li) y[li] = r[S.dofs[li]];
-  lu_solve(n, S.lu.data(), y);
+  sub_solve(S, y);
   return 0;
 }
 
@@ -933,6 +1058,9 @@ long orc_get(void* h, const char* what, int level, int sub, const void** ptr) {
   if (sub < 0) S = &L.coarse;
   else if (sub < (int)L.subs.size()) S = &L.subs[sub];
   if (!S) return -1;
+  if (w == "sub_ilu_ptr") return ret(S->ilu.rowptr);
+  if (w == "sub_ilu_col") return ret(S->ilu.col);
+  if (w == "sub_ilu_val") return ret(S->ilu.val);
   if (w == "sub_dofs") return ret(S->dofs);
   if (w == "sub_own") return ret(S->own);
   if (w == "sub_lu") return ret(S->lu);
@@ -993,6 +1121,27 @@ long orc_build_mls(const orc_level* src, const orc_level* dst, double h, int del
   std::copy(R.col.begin(), R.col.end(), *col);
   std::copy(R.val.begin(), R.val.end(), *val);
   return (long)R.col.size();
+}
+
+// ILU(p) of an n x n CSR matrix (sorted columns): returns the nnz of the
+// factor (unit L below the diagonal, U on and above it, one CSR), -1 on a
+// zero pivot.  Arrays are freed with orc_free_csr.
+long orc_ilu_factor(int n, const int* rowptr, const int* col, const double* val, int p, int** fptr,
+                    int** fcol, double** fval) {
+  Csr B, F;
+  B.rowptr.assign(rowptr, rowptr + n + 1);
+  B.col.assign(col, col + rowptr[n]);
+  B.val.assign(val, val + rowptr[n]);
+  ilu_symbolic(B, p, F);
+  std::vector<int> ud;
+  if (ilu_numeric(B, F, ud)) return -1;
+  *fptr = new int[F.rowptr.size()];
+  *fcol = new int[F.col.size() + 1];
+  *fval = new double[F.val.size() + 1];
+  std::copy(F.rowptr.begin(), F.rowptr.end(), *fptr);
+  std::copy(F.col.begin(), F.col.end(), *fcol);
+  std::copy(F.val.begin(), F.val.end(), *fval);
+  return (long)F.col.size();
 }
 
 double orc_mesh_h(const orc_level* c) {

@@ -39,7 +39,7 @@ def lib():
             L = C.CDLL(build())
             vp, ip, dp = C.c_void_p, C.c_int, C.c_double
             L.orc_create.restype = vp
-            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip, ip]
+            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip, ip, ip, ip]
             L.orc_destroy.argtypes = [vp]
             for name in ("orc_assemble",):
                 getattr(L, name).argtypes = [vp, vp]
@@ -69,6 +69,10 @@ def lib():
                                         C.POINTER(C.POINTER(C.c_int)),
                                         C.POINTER(C.POINTER(C.c_int)),
                                         C.POINTER(C.POINTER(C.c_double))]
+            L.orc_ilu_factor.restype = C.c_long
+            L.orc_ilu_factor.argtypes = [ip, vp, vp, vp, ip, C.POINTER(C.POINTER(C.c_int)),
+                                         C.POINTER(C.POINTER(C.c_int)),
+                                         C.POINTER(C.POINTER(C.c_double))]
             L.orc_mesh_h.restype = dp
             L.orc_mesh_h.argtypes = [C.POINTER(_Level)]
             L.orc_free_csr.argtypes = [vp, vp, vp]
@@ -89,7 +93,8 @@ class Oracle:
     """One hierarchy + one parameter vector, in the oracle's FP64 arithmetic."""
 
     def __init__(self, levels, delta=1, nu_pre=2, nu_post=2, coef="const", wave=None,
-                 scale=1.0, load="one", transfer="bary", restrict_scaling=True, coarse="direct"):
+                 scale=1.0, load="one", transfer="bary", restrict_scaling=True, coarse="direct",
+                 ilu=None):
         L = lib()
         self._keep = []
         arr = (_Level * len(levels))()
@@ -105,7 +110,8 @@ class Oracle:
         self.h = L.orc_create(arr, len(levels), int(delta), int(nu_pre), int(nu_post),
                               _COEF[coef], _p(w), float(scale), _LOAD[load],
                               _TRANSFER[transfer], 1 if restrict_scaling else 0,
-                              {"direct": 0, "ras": 1}[coarse])
+                              {"direct": 0, "ras": 1}[coarse],
+                              -1 if ilu is None else int(ilu[0]), -1 if ilu is None else int(ilu[1]))
         if not self.h:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels
@@ -295,3 +301,27 @@ def mesh_h(lv):
     keep = []
     d = _level_desc(lv, keep)
     return float(lib().orc_mesh_h(C.byref(d)))
+
+
+def ilu_factor(A, p):
+    """ILU(p) of a scipy CSR matrix (sorted indices): (L unit lower, U upper) as
+    scipy CSR matrices."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    n = A.shape[0]
+    rp = np.ascontiguousarray(A.indptr, np.int32)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    va = np.ascontiguousarray(A.data, np.float64)
+    fp, fc, fv = C.POINTER(C.c_int)(), C.POINTER(C.c_int)(), C.POINTER(C.c_double)()
+    nnz = lib().orc_ilu_factor(n, _p(rp), _p(ci), _p(va), int(p), C.byref(fp), C.byref(fc), C.byref(fv))
+    if nnz < 0:
+        raise ValueError("oracle: zero pivot in ILU")
+    R = np.ctypeslib.as_array(fp, shape=(n + 1,)).copy()
+    Cc = np.ctypeslib.as_array(fc, shape=(max(nnz, 1),))[:nnz].copy()
+    V = np.ctypeslib.as_array(fv, shape=(max(nnz, 1),))[:nnz].copy()
+    lib().orc_free_csr(fp, fc, fv)
+    F = sp.csr_matrix((V, Cc, R), shape=(n, n))
+    L = sp.tril(F, -1).tocsr() + sp.identity(n, format="csr")
+    U = sp.triu(F).tocsr()
+    return L, U

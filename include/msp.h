@@ -121,6 +121,10 @@ typedef struct msp_options {
                                  coarse |w|, so that its scale matches the coarse operator;
                                  0: the plain interpolated residual of Algorithm 2 */
   int32_t coarse_solver;      /* msp_coarse */
+  int32_t ilu_fill_fine;      /* subdomain solver of level 0: -1 (default) the exact LU of the
+                                 block (dense tile envelope); p >= 0 ILU(p), the incomplete LU
+                                 with the level-of-fill pattern (Section 4.4 uses ILU(2)) */
+  int32_t ilu_fill_coarse;    /* the same for the smoothed levels 1.. (Section 4.4: ILU(0)) */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
@@ -131,7 +135,7 @@ typedef struct msp_options {
 
 /* Fills *o with the defaults: delta 1, nu 2/2, restart 30, max_it 1000, FP64
  * factors, k = 1, f = 1, barycentric transfers (MLS restriction scaling on),
- * direct coarsest solve, no budget, cudaMalloc. */
+ * direct coarsest solve, exact subdomain LU (no ILU), no budget, cudaMalloc. */
 MSP_API void msp_default_options(msp_options* o);
 
 typedef struct msp_hierarchy msp_hierarchy;
@@ -296,13 +300,19 @@ MSP_API int msp_apply_op(msp_instance* inst, int op, int level, const double* x_
  *   MSP_ARR_VAL (double CSR values), MSP_ARR_FACTOR (the tiled factor of
  *   subdomain `sub` of `level`, sub = -1 for the coarsest level, in the
  *   precision of that level's factors).
+ * ILU(p) levels (msp_options.ilu_fill_*): MSP_ARR_ILU_PTR (int64, rows + 1)
+ *   and MSP_ARR_ILU_COL (int32 local columns) give the strict lower pattern
+ *   of every block, row R = sub_ptr[p] + i for local row i of subdomain p;
+ *   MSP_ARR_ILU_VAL (double, the unit lower L on that pattern) and
+ *   MSP_ARR_ILU_D (double, one per row) are the instance's factors, U = D L^T.
  * bytes_out receives the array size; with dst == NULL only the size is
  * returned.  MSP_ERR_INVALID if cap is too small. */
 typedef enum msp_array {
   MSP_ARR_ROWPTR = 0, MSP_ARR_COL = 1, MSP_ARR_SUB_PTR = 2, MSP_ARR_SUB_DOFS = 3,
   MSP_ARR_SUB_OWN = 4, MSP_ARR_P_ROWPTR = 5, MSP_ARR_P_COL = 6, MSP_ARR_P_VAL = 7,
   MSP_ARR_PT_ROWPTR = 8, MSP_ARR_PT_COL = 9, MSP_ARR_PT_VAL = 10, MSP_ARR_LOAD = 11,
-  MSP_ARR_VAL = 12, MSP_ARR_FACTOR = 13, MSP_ARR_SUB_NT = 14, MSP_ARR_TILE_FIRST = 15
+  MSP_ARR_VAL = 12, MSP_ARR_FACTOR = 13, MSP_ARR_SUB_NT = 14, MSP_ARR_TILE_FIRST = 15,
+  MSP_ARR_ILU_PTR = 16, MSP_ARR_ILU_COL = 17, MSP_ARR_ILU_VAL = 18, MSP_ARR_ILU_D = 19
 } msp_array;
 MSP_API int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, size_t cap,
                        size_t* bytes_out);

@@ -132,7 +132,7 @@ class Oracle:
             return int(cnt)
         if dtype is None:
             dtype = {"val": np.float64, "b": np.float64, "P_val": np.float64,
-                     "PT_val": np.float64, "sub_lu": np.float64,
+                     "PT_val": np.float64, "sub_lu": np.float64, "sub_ilu_val": np.float64,
                      "sub_own": np.uint8}.get(what, np.int32)
         if cnt == 0:
             return np.zeros(0, dtype)

@@ -1,0 +1,209 @@
+// ILU(p) subdomain solver kernels (the incomplete factorisation of Section
+// 4.4 in place of the exact block LU), FP64.
+//
+// The factor of block p is kept in symmetric form, L (unit lower, sparse) and
+// D, with U = D L^T; its pattern is the level-of-fill pattern of ILU(p) (host
+// set-up).  Both the factorisation and the triangular sweeps run one CTA per
+// block and walk its rows by dependency level (set-up): the rows of a level
+// depend only on rows of earlier levels, so each level is one parallel step
+// (one warp per row) followed by a CTA barrier.  A block's vectors live in
+// shared memory; the factor streams from global memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "msp_kernels.h"
+
+namespace msp {
+namespace {
+
+constexpr int kIluWarps = 4;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Up-looking incomplete L D L^T of block p: for row i, in ascending k over its
+// pattern, l_ik = (a_ik - sum_{m in P(k)} l_km d_m l_im) / d_k (entries of row
+// i outside its pattern are zero, which drops the fill of level > p), then
+// d_i = a_ii - sum_m l_im^2 d_m.  fac = [L (nnz) | D (rows) | 1/D (rows)],
+// holding A_p's lower triangle on entry (extraction).  Each warp keeps its
+// row dense in shared memory.  smem: (kIluWarps + 1) * max_n doubles.
+__global__ void __launch_bounds__(32 * kIluWarps) k_ilu_factor(
+    double* __restrict__ fac, int64_t nnz, int64_t rows, const int32_t* __restrict__ sub_ptr,
+    const int64_t* __restrict__ lptr, const int32_t* __restrict__ lcol,
+    const int32_t* __restrict__ fwd_rows, const int32_t* __restrict__ fwd_lvl,
+    const int32_t* __restrict__ fwd_loff, int max_n, int* __restrict__ info) {
+  extern __shared__ double sm_ilu[];
+  const int p = blockIdx.x;
+  const int R0 = sub_ptr[p], n = sub_ptr[p + 1] - R0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* d_s = sm_ilu;              // [max_n] d of finished rows
+  double* w = d_s + max_n + warp * max_n;  // [max_n] this warp's current row
+  double* L = fac;
+  double* D = fac + nnz;
+  double* Dinv = D + rows;
+  for (int e = threadIdx.x; e < kIluWarps * max_n; e += blockDim.x) sm_ilu[max_n + e] = 0.0;
+  __syncthreads();
+  for (int q = fwd_loff[p]; q + 1 < fwd_loff[p + 1]; ++q) {  // level q: rows fwd_lvl[q] .. fwd_lvl[q+1]
+    const int r0 = fwd_lvl[q], r1 = fwd_lvl[q + 1];
+    for (int rr = r0 + warp; rr < r1; rr += kIluWarps) {
+      const int i = fwd_rows[rr];
+      const int64_t b = lptr[R0 + i], e = lptr[R0 + i + 1];
+      for (int64_t t = b + lane; t < e; t += 32) w[lcol[t]] = L[t];
+      __syncwarp();
+      for (int64_t t = b; t < e; ++t) {
+        const int k = lcol[t];
+        const int64_t kb = lptr[R0 + k], ke = lptr[R0 + k + 1];
+        double s = 0.0;
+        for (int64_t u = kb + lane; u < ke; u += 32) {
+          const int m = lcol[u];
+          s = fma(L[u] * d_s[m], w[m], s);
+        }
+        s = warp_sum(s);
+        const double lik = (w[k] - s) * Dinv[R0 + k];
+        __syncwarp();
+        if (lane == 0) w[k] = lik;
+        __syncwarp();
+      }
+      double s = 0.0;
+      for (int64_t t = b + lane; t < e; t += 32) {
+        const int m = lcol[t];
+        s = fma(w[m] * w[m], d_s[m], s);
+      }
+      s = warp_sum(s);
+      const double di = D[R0 + i] - s;
+      for (int64_t t = b + lane; t < e; t += 32) {
+        const int m = lcol[t];
+        L[t] = w[m];
+        w[m] = 0.0;
+      }
+      if (lane == 0) {
+        D[R0 + i] = di;
+        Dinv[R0 + i] = 1.0 / di;
+        d_s[i] = di;
+        if (di == 0.0 || !(fabs(di) < 1e300)) atomicOr(info, 1);  // zero or non-finite pivot
+      }
+      __syncwarp();
+    }
+    __syncthreads();  // the level's rows (L, D, d_s) are final for the next levels
+  }
+}
+
+// y = (L D L^T)^{-1} t[dofs] of block p and the owned scatter into z (RAS,
+// Eq. 7).  Forward: y_i -= sum_{m in P(i)} l_im y_m, level by level; then
+// y_i /= d_i; backward: y_i -= sum_{j: i in P(j)} l_ji y_j over the transposed
+// pattern, by backward levels.  One warp per row.  smem: max_n doubles.
+__global__ void __launch_bounds__(32 * kIluWarps) k_ilu_solve(
+    const double* __restrict__ fac, int64_t nnz, int64_t rows, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
+    const int64_t* __restrict__ lptr, const int32_t* __restrict__ lcol,
+    const int64_t* __restrict__ tptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tslot,
+    const int32_t* __restrict__ fwd_rows, const int32_t* __restrict__ fwd_lvl,
+    const int32_t* __restrict__ fwd_loff, const int32_t* __restrict__ bwd_rows,
+    const int32_t* __restrict__ bwd_lvl, const int32_t* __restrict__ bwd_loff,
+    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
+    double* __restrict__ z, int add) {
+  extern __shared__ double sm_ilu[];
+  const int p = blockIdx.x;
+  const int R0 = sub_ptr[p], n = sub_ptr[p + 1] - R0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* L = fac;
+  const double* Dinv = fac + nnz + rows;
+  double* y = sm_ilu;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndir; d += gridDim.x * blockDim.x) {
+    const int g = dir_list[d];
+    z[g] = add ? z[g] + t[g] : t[g];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = t[dofs[R0 + i]];
+  __syncthreads();
+  for (int q = fwd_loff[p]; q + 1 < fwd_loff[p + 1]; ++q) {  // level q: rows fwd_lvl[q] .. fwd_lvl[q+1]
+    for (int rr = fwd_lvl[q] + warp; rr < fwd_lvl[q + 1]; rr += kIluWarps) {
+      const int i = fwd_rows[rr];
+      double s = 0.0;
+      for (int64_t u = lptr[R0 + i] + lane; u < lptr[R0 + i + 1]; u += 32) s = fma(L[u], y[lcol[u]], s);
+      s = warp_sum(s);
+      if (lane == 0) y[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= Dinv[R0 + i];
+  __syncthreads();
+  for (int q = bwd_loff[p]; q + 1 < bwd_loff[p + 1]; ++q) {
+    for (int rr = bwd_lvl[q] + warp; rr < bwd_lvl[q + 1]; rr += kIluWarps) {
+      const int i = bwd_rows[rr];
+      double s = 0.0;
+      for (int64_t u = tptr[R0 + i] + lane; u < tptr[R0 + i + 1]; u += 32) s = fma(L[tslot[u]], y[tcol[u]], s);
+      s = warp_sum(s);
+      if (lane == 0) y[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (own[R0 + i]) {
+      const int g = dofs[R0 + i];
+      z[g] = add ? z[g] + y[i] : y[i];
+    }
+}
+
+__global__ void k_ilu_zero(double* __restrict__ p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0.0;
+}
+
+__global__ void k_ilu_scatter(const int64_t* __restrict__ pos, const int32_t* __restrict__ nz,
+                              const double* __restrict__ val, int64_t nent, double* __restrict__ fac) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nent) fac[pos[e]] = val[nz[e]];
+}
+
+int nblocks(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+
+size_t ilu_factor_smem(int max_n) { return (size_t)(kIluWarps + 1) * max_n * sizeof(double); }
+size_t ilu_solve_smem(int max_n) { return (size_t)max_n * sizeof(double); }
+
+void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
+                        double* fac, cudaStream_t s) {
+  if (total > 0) k_ilu_zero<<<std::min<int64_t>(nblocks(total, 256), 1 << 16), 256, 0, s>>>(fac, total);
+  if (nent > 0) k_ilu_scatter<<<nblocks(nent, 256), 256, 0, s>>>(pos, nz, val, nent, fac);
+}
+
+void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
+                       const int64_t* lptr, const int32_t* lcol, const int32_t* fwd_rows,
+                       const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int* info,
+                       cudaStream_t s) {
+  if (nsub <= 0) return;
+  const size_t smem = ilu_factor_smem(max_n);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_ilu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  k_ilu_factor<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, lptr, lcol, fwd_rows, fwd_lvl,
+                                                   fwd_loff, max_n, info);
+}
+
+void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, const int64_t* lptr, const int32_t* lcol,
+                      const int64_t* tptr, const int32_t* tcol, const int64_t* tslot,
+                      const int32_t* fwd_rows, const int32_t* fwd_lvl, const int32_t* fwd_loff,
+                      const int32_t* bwd_rows, const int32_t* bwd_lvl, const int32_t* bwd_loff,
+                      int max_n, const int32_t* dir_list, int ndir, const double* t, double* z, int add,
+                      cudaStream_t s) {
+  if (nsub <= 0) return;
+  const size_t smem = ilu_solve_smem(max_n);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_ilu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  k_ilu_solve<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, dofs, own, lptr, lcol, tptr, tcol,
+                                                  tslot, fwd_rows, fwd_lvl, fwd_loff, bwd_rows, bwd_lvl,
+                                                  bwd_loff, dir_list, ndir, t, z, add);
+}
+
+}  // namespace msp

@@ -99,6 +99,15 @@ struct DevLevel {
   int n = 0, m = 0;
   int64_t nnz = 0;
   int lpr_A = 8, lpr_P = 4, lpr_PT = 16;  // SpMV lanes per row (autotuned at load)
+  // ILU(p) subdomain factors (see HostLevel)
+  bool ilu = false;
+  int64_t ilu_nnz = 0, ilu_rows = 0, ilu_next = 0;
+  int ilu_max_n = 0;
+  double ilu_flops = 0;  // algorithmic flops of one ILU factorisation of the level
+  int64_t *ilu_lptr = nullptr, *ilu_tptr = nullptr, *ilu_tslot = nullptr, *ilu_ext_pos = nullptr;
+  int32_t *ilu_lcol = nullptr, *ilu_tcol = nullptr, *ilu_ext_nz = nullptr;
+  int32_t *ilu_fwd_rows = nullptr, *ilu_fwd_lvl = nullptr, *ilu_fwd_loff = nullptr;
+  int32_t *ilu_bwd_rows = nullptr, *ilu_bwd_lvl = nullptr, *ilu_bwd_loff = nullptr;
   int32_t *rowptr = nullptr, *col = nullptr, *diag = nullptr, *cptr = nullptr, *contrib = nullptr;
   uint8_t *nzflag = nullptr, *dir = nullptr;
   int32_t* dir_list = nullptr;
@@ -190,7 +199,7 @@ bool direct_level(const msp_hierarchy* h, int l) { return h->host[l].direct; }
 // Storage of a level's factors (the directly solved level is always FP64).
 enum class Store { F64, F32, BF16 };
 Store level_store(const msp_hierarchy* h, int l) {
-  if (direct_level(h, l)) return Store::F64;
+  if (direct_level(h, l) || h->host[l].ilu_fill >= 0) return Store::F64;
   if (h->opt.factor_precision == MSP_F32) return Store::F32;
   if (h->opt.factor_precision == MSP_BF16) return Store::BF16;
   return Store::F64;
@@ -304,7 +313,40 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.ext_nz = A.upload(H.ext_nz);
   D.next = (int64_t)H.ext_pos.size();
   finish_level_stats(H, D);
-  {
+  if (H.ilu_fill >= 0) {  // ILU(p) subdomain factors: sparse storage, level-scheduled kernels
+    D.ilu = true;
+    D.ilu_nnz = H.ilu_nnz;
+    D.ilu_rows = H.sub_ptr.empty() ? 0 : H.sub_ptr.back();
+    D.ilu_max_n = H.ilu_max_n;
+    D.fac_elems = D.ilu_nnz + 2 * D.ilu_rows;  // [L | D | 1/D]
+    D.ilu_lptr = A.upload(H.ilu_lptr);
+    D.ilu_lcol = A.upload(H.ilu_lcol);
+    D.ilu_tptr = A.upload(H.ilu_tptr);
+    D.ilu_tcol = A.upload(H.ilu_tcol);
+    D.ilu_tslot = A.upload(H.ilu_tslot);
+    D.ilu_fwd_rows = A.upload(H.ilu_fwd_rows);
+    D.ilu_fwd_lvl = A.upload(H.ilu_fwd_lvl);
+    D.ilu_fwd_loff = A.upload(H.ilu_fwd_loff);
+    D.ilu_bwd_rows = A.upload(H.ilu_bwd_rows);
+    D.ilu_bwd_lvl = A.upload(H.ilu_bwd_lvl);
+    D.ilu_bwd_loff = A.upload(H.ilu_bwd_loff);
+    D.ilu_ext_pos = A.upload(H.ilu_ext_pos);
+    D.ilu_ext_nz = A.upload(H.ilu_ext_nz);
+    D.ilu_next = (int64_t)H.ilu_ext_pos.size();
+    D.ilu_flops = 0;
+    for (int p = 0; p < H.nsub; ++p)
+      for (int64_t R = H.sub_ptr[p]; R < H.sub_ptr[p + 1]; ++R) {
+        for (int64_t t = H.ilu_lptr[R]; t < H.ilu_lptr[R + 1]; ++t) {
+          const int64_t K = H.sub_ptr[p] + H.ilu_lcol[t];
+          D.ilu_flops += 2.0 * (double)(H.ilu_lptr[K + 1] - H.ilu_lptr[K]) + 1;
+        }
+        D.ilu_flops += 3.0 * (double)(H.ilu_lptr[R + 1] - H.ilu_lptr[R]) + 1;
+      }
+    if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
+    if (ilu_factor_smem(D.ilu_max_n) > 200u * 1024u)
+      return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large for the ILU "
+                                   "kernels (" + std::to_string(D.ilu_max_n) + " DoFs)");
+  } else {
     int nsm = 0;
     MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     // RAS solve: persistent CTAs (1-3 per SM by precision, or the wide form
@@ -349,7 +391,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     }
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
   }
-  {
+  if (!D.ilu) {
     const int slots = ras_slots_of(h, l, D.ras_wide);
     // the backward sweep holds a row's diagonal tile while the next R_I - I
     // tiles stream in: max_band slots are enough, and never deadlock
@@ -416,6 +458,8 @@ int check_options(const msp_options& o) {
     return fail(MSP_ERR_INVALID, "unknown transfer");
   if (o.coarse_solver != MSP_COARSE_DIRECT && o.coarse_solver != MSP_COARSE_RAS)
     return fail(MSP_ERR_INVALID, "unknown coarse solver");
+  if (o.ilu_fill_fine < -1 || o.ilu_fill_fine > 16 || o.ilu_fill_coarse < -1 || o.ilu_fill_coarse > 16)
+    return fail(MSP_ERR_INVALID, "ILU fill level out of range (-1 .. 16)");
   if (o.coarse_solver == MSP_COARSE_RAS && o.nu_pre < 1)
     return fail(MSP_ERR_INVALID, "a smoothed coarsest level needs nu_pre >= 1");
   if (o.coef_kind != MSP_K_CONST && o.coef_kind != MSP_K_COSEXP)
@@ -537,7 +581,19 @@ int enqueue_factor(msp_instance* I) {
   for (int l = L - 1; l >= 0; --l) {
     cudaStream_t s = (l == 0) ? I->stream : (l == L - 1 ? I->aux[0] : I->aux[1]);
     const Store st = level_store(h, l);
-    if (st == Store::F64) {
+    const DevLevel& D = h->dev[l];
+    if (D.ilu) {
+      double* fac = static_cast<double*>(I->fac[l]);
+      {
+        ProfScope ps(I->prof, PK_EXTRACT, s, 2);
+        launch_ilu_extract(D.ilu_ext_pos, D.ilu_ext_nz, D.ilu_next, I->val[l], D.fac_elems, fac, s);
+        ps.account((double)D.fac_elems * 8 + (double)D.ilu_next * 20, 0);
+      }
+      ProfScope ps(I->prof, PK_LDLT_BLOCKS, s);
+      launch_ilu_factor(fac, D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.ilu_lptr, D.ilu_lcol, D.ilu_fwd_rows,
+                        D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_max_n, I->info, s);
+      ps.account((double)D.ilu_nnz * 8 * 3, D.ilu_flops);
+    } else if (st == Store::F64) {
       factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
     } else if (st == Store::F32) {
       factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
@@ -617,6 +673,15 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   ProfScope ps(I->prof, kind, s);
   const Store st = level_store(h, l);
   size_t es = store_bytes(st);
+  if (D.ilu) {
+    launch_ilu_solve(static_cast<const double*>(I->fac[l]), D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.sub_dofs,
+                     D.sub_own, D.ilu_lptr, D.ilu_lcol, D.ilu_tptr, D.ilu_tcol, D.ilu_tslot, D.ilu_fwd_rows,
+                     D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_bwd_rows, D.ilu_bwd_lvl, D.ilu_bwd_loff, D.ilu_max_n,
+                     D.dir_list, D.ndir, t, z, add, s);
+    ps.account(2.0 * (double)D.ilu_nnz * 12 + (double)D.sum_np * 21 + (double)D.sum_owned * (add ? 16 : 8),
+               4.0 * (double)D.ilu_nnz + (double)D.sum_np);
+    return;
+  }
   if (coarse) {  // one block: both sweeps split over a cluster of CTAs
     launch_block_solve_cluster<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr,
                                        D.sub_dofs, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
@@ -993,6 +1058,8 @@ void msp_default_options(msp_options* o) {
   o->transfer = MSP_TRANSFER_BARY;
   o->restrict_scaling = 1;
   o->coarse_solver = MSP_COARSE_DIRECT;
+  o->ilu_fill_fine = -1;
+  o->ilu_fill_coarse = -1;
 }
 
 const char* msp_last_error(void) { return msp::g_last_error.c_str(); }
@@ -1288,6 +1355,8 @@ int msp_hierarchy_copy(const msp_hierarchy* h, int level, int what, void* dst, s
     case MSP_ARR_PT_VAL: pick(H.PT_val); break;
     case MSP_ARR_SUB_NT: pick(H.sub_nt); break;
     case MSP_ARR_TILE_FIRST: pick(H.tile_first); break;
+    case MSP_ARR_ILU_PTR: pick(H.ilu_lptr); break;
+    case MSP_ARR_ILU_COL: pick(H.ilu_lcol); break;
     case MSP_ARR_LOAD:
       if (h->host_only) return fail(MSP_ERR_INVALID, "host-only hierarchy has no load vector");
       src = h->dev[level].b;
@@ -1316,6 +1385,13 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
   if (what == MSP_ARR_VAL) {
     src = I->val[level];
     bytes = (size_t)D.nnz * sizeof(double);
+  } else if (what == MSP_ARR_ILU_VAL || what == MSP_ARR_ILU_D) {
+    if (!D.ilu) return fail(MSP_ERR_INVALID, "level has no ILU factors");
+    const double* f = static_cast<const double*>(I->fac[level]);
+    src = what == MSP_ARR_ILU_VAL ? f : f + D.ilu_nnz;
+    bytes = (size_t)(what == MSP_ARR_ILU_VAL ? D.ilu_nnz : D.ilu_rows) * sizeof(double);
+  } else if (what == MSP_ARR_FACTOR && D.ilu) {
+    return fail(MSP_ERR_INVALID, "ILU level: read MSP_ARR_ILU_VAL / MSP_ARR_ILU_D");
   } else if (what == MSP_ARR_FACTOR) {
     const bool coarse = direct_level(h, level);
     int p = coarse ? 0 : sub;

@@ -68,6 +68,30 @@ struct HostLevel {
   // work list of the factorisation: subdomains sorted by descending NT
   std::vector<int32_t> sub_order;
 
+  // ILU(p) subdomain factors (Section 4.4) instead of the dense envelope when
+  // ilu_fill >= 0.  Rows are numbered globally, row R = sub_ptr[p] + i for
+  // local row i of subdomain p.  The factor is stored in symmetric form
+  // (L unit lower, D; U = D L^T):
+  //   ilu_lptr[R]..ilu_lptr[R+1]: strict lower pattern of row R, local
+  //     columns ilu_lcol, values at the same positions of the L array;
+  //   ilu_tptr/ilu_tcol/ilu_tslot: the transposed pattern (column R of L:
+  //     rows j > i, with the L position of (j, i));
+  //   ilu_fwd_rows / ilu_bwd_rows: local rows grouped by dependency level
+  //     for the forward (rows need the rows of their pattern) and the
+  //     backward sweep (rows need the rows whose pattern holds them); block p
+  //     owns ilu_*_lvl[ilu_*_loff[p] .. ilu_*_loff[p+1]) (its level count + 1
+  //     boundaries), level q spanning positions ilu_*_lvl[loff + q] ..
+  //     ilu_*_lvl[loff + q + 1] of the rows arrays;
+  //   ilu_ext_pos / ilu_ext_nz: extraction of the lower triangle of A_p into
+  //     [L | D] (positions >= nnzL address D).
+  int ilu_fill = -1;
+  int64_t ilu_nnz = 0;
+  int ilu_max_n = 0;
+  std::vector<int64_t> ilu_lptr, ilu_tptr, ilu_tslot, ilu_ext_pos;
+  std::vector<int32_t> ilu_lcol, ilu_tcol, ilu_ext_nz;
+  std::vector<int32_t> ilu_fwd_rows, ilu_fwd_lvl, ilu_fwd_loff;
+  std::vector<int32_t> ilu_bwd_rows, ilu_bwd_lvl, ilu_bwd_loff;
+
   // prolongation from level+1 to this level (P or MLS) and restriction to
   // level+1 (P^T or MLS)
   std::vector<int32_t> P_rowptr, P_col, PT_rowptr, PT_col;

@@ -10,6 +10,8 @@
 //     and P^T, or the overlapping MLS operators of Section 3.2 (the weights
 //     are set-up; applying them is a sparse product on the device).
 #include <algorithm>
+#include <climits>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -703,6 +705,183 @@ std::string build_mls(const HostLevel& S, const HostLevel& T, double h, int delt
   return "";
 }
 
+// ------------------------------------------------- ILU(p) symbolic (set-up)
+// For each subdomain block A_p (local numbering = position in the sorted DoF
+// list): the strict lower part of the level-of-fill pattern of ILU(p) (A_p and
+// its pattern are symmetric, so the upper part is the transpose), computed row
+// by row: the candidate columns of row i come out of a min-heap in ascending
+// order; eliminating with an earlier row k (level lev_ik <= p) proposes every
+// column j of row k's upper part (the transposed lower lists of the finished
+// rows j < i) at level lev_ik + lev_kj + 1, kept if <= p.  Then the
+// dependency levels of both triangular sweeps and the extraction map.
+struct IluSub {
+  std::vector<int32_t> lptr, lcol;             // local strict lower pattern
+  std::vector<int32_t> fwd_rows, fwd_lvl, bwd_rows, bwd_lvl;
+};
+
+void ilu_block(const HostLevel& L, int p, int fill, IluSub& out) {
+  const int32_t* dofs = &L.sub_dofs[L.sub_ptr[p]];
+  const int n = L.sub_ptr[p + 1] - L.sub_ptr[p];
+  auto local = [&](int g) {
+    const int32_t* it = std::lower_bound(dofs, dofs + n, g);
+    return (it != dofs + n && *it == g) ? (int)(it - dofs) : -1;
+  };
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> up(n);  // (j, level) of row k's upper part
+  std::vector<int32_t> lev(n, INT32_MAX);
+  std::vector<int32_t> heap;
+  out.lptr.assign(n + 1, 0);
+  out.lcol.clear();
+  std::vector<int32_t> row, rowlev;
+  for (int i = 0; i < n; ++i) {
+    heap.clear();
+    const int g = dofs[i];
+    for (int q = L.rowptr[g]; q < L.rowptr[g + 1]; ++q) {
+      const int k = local(L.col[q]);
+      if (k >= 0 && k < i && lev[k] == INT32_MAX) {
+        lev[k] = 0;
+        heap.push_back(k);
+      }
+    }
+    std::make_heap(heap.begin(), heap.end(), std::greater<int32_t>());
+    row.clear();
+    rowlev.clear();
+    while (!heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end(), std::greater<int32_t>());
+      const int k = heap.back();
+      heap.pop_back();
+      row.push_back(k);
+      rowlev.push_back(lev[k]);
+      for (const auto& e : up[k]) {
+        const int j = e.first;
+        if (j >= i) break;  // lists are sorted by j
+        const int nl = lev[k] + e.second + 1;
+        if (nl > fill || nl >= lev[j]) continue;
+        if (lev[j] == INT32_MAX) {
+          heap.push_back(j);
+          std::push_heap(heap.begin(), heap.end(), std::greater<int32_t>());
+        }
+        lev[j] = nl;
+      }
+    }
+    for (size_t t = 0; t < row.size(); ++t) {
+      out.lcol.push_back(row[t]);
+      up[row[t]].push_back({i, rowlev[t]});
+      lev[row[t]] = INT32_MAX;
+    }
+    out.lptr[i + 1] = (int32_t)out.lcol.size();
+  }
+  // dependency levels: forward (row i after the rows of its pattern),
+  // backward (row i after every row j > i whose pattern holds i)
+  std::vector<int32_t> lf(n, 0), lb(n, 0);
+  int nf = 0, nb = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int t = out.lptr[i]; t < out.lptr[i + 1]; ++t) lf[i] = std::max(lf[i], lf[out.lcol[t]] + 1);
+    nf = std::max(nf, lf[i] + 1);
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    for (const auto& e : up[i]) lb[i] = std::max(lb[i], lb[e.first] + 1);
+    nb = std::max(nb, lb[i] + 1);
+  }
+  auto group = [&](const std::vector<int32_t>& lv, int nl, std::vector<int32_t>& rows,
+                   std::vector<int32_t>& ptr) {
+    ptr.assign(nl + 1, 0);
+    for (int i = 0; i < n; ++i) ptr[lv[i] + 1]++;
+    for (int q = 0; q < nl; ++q) ptr[q + 1] += ptr[q];
+    rows.resize(n);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n; ++i) rows[fill[lv[i]]++] = i;
+  };
+  group(lf, nf, out.fwd_rows, out.fwd_lvl);
+  group(lb, nb, out.bwd_rows, out.bwd_lvl);
+}
+
+void build_ilu(HostLevel& L, int fill) {
+  L.ilu_fill = fill;
+  std::vector<IluSub> subs(L.nsub);
+  auto work = [&](int p0, int p1) {
+    for (int p = p0; p < p1; ++p) ilu_block(L, p, fill, subs[p]);
+  };
+  int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+  nth = std::min(nth, std::max(1, L.nsub));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back(work, (int)((int64_t)L.nsub * t / nth), (int)((int64_t)L.nsub * (t + 1) / nth));
+  for (auto& t : th) t.join();
+  const int64_t rows = L.sub_ptr[L.nsub];
+  L.ilu_lptr.assign(rows + 1, 0);
+  L.ilu_lcol.clear();
+  L.ilu_max_n = 0;
+  for (int p = 0; p < L.nsub; ++p) {
+    const int n = L.sub_ptr[p + 1] - L.sub_ptr[p];
+    L.ilu_max_n = std::max(L.ilu_max_n, n);
+    const int64_t base = L.ilu_lptr[L.sub_ptr[p]];
+    for (int i = 0; i < n; ++i) L.ilu_lptr[L.sub_ptr[p] + i + 1] = base + subs[p].lptr[i + 1];
+    L.ilu_lcol.insert(L.ilu_lcol.end(), subs[p].lcol.begin(), subs[p].lcol.end());
+  }
+  L.ilu_nnz = L.ilu_lptr[rows];
+  // transposed pattern
+  L.ilu_tptr.assign(rows + 1, 0);
+  for (int p = 0; p < L.nsub; ++p)
+    for (int64_t R = L.sub_ptr[p]; R < L.sub_ptr[p + 1]; ++R)
+      for (int64_t t = L.ilu_lptr[R]; t < L.ilu_lptr[R + 1]; ++t) L.ilu_tptr[L.sub_ptr[p] + L.ilu_lcol[t] + 1]++;
+  for (int64_t R = 0; R < rows; ++R) L.ilu_tptr[R + 1] += L.ilu_tptr[R];
+  L.ilu_tcol.assign(L.ilu_nnz, 0);
+  L.ilu_tslot.assign(L.ilu_nnz, 0);
+  {
+    std::vector<int64_t> fill_at(L.ilu_tptr.begin(), L.ilu_tptr.end() - 1);
+    for (int p = 0; p < L.nsub; ++p)
+      for (int64_t R = L.sub_ptr[p]; R < L.sub_ptr[p + 1]; ++R)  // rows ascending: columns of T sorted
+        for (int64_t t = L.ilu_lptr[R]; t < L.ilu_lptr[R + 1]; ++t) {
+          const int64_t d = fill_at[L.sub_ptr[p] + L.ilu_lcol[t]]++;
+          L.ilu_tcol[d] = (int32_t)(R - L.sub_ptr[p]);
+          L.ilu_tslot[d] = t;
+        }
+  }
+  // level schedules
+  L.ilu_fwd_rows.clear();
+  L.ilu_bwd_rows.clear();
+  L.ilu_fwd_lvl.clear();
+  L.ilu_bwd_lvl.clear();
+  L.ilu_fwd_loff.assign(L.nsub + 1, 0);
+  L.ilu_bwd_loff.assign(L.nsub + 1, 0);
+  for (int p = 0; p < L.nsub; ++p) {
+    const int32_t base = L.sub_ptr[p];
+    for (int32_t r : subs[p].fwd_rows) L.ilu_fwd_rows.push_back(r);
+    for (int32_t r : subs[p].bwd_rows) L.ilu_bwd_rows.push_back(r);
+    for (int32_t v : subs[p].fwd_lvl) L.ilu_fwd_lvl.push_back(base + v);
+    for (int32_t v : subs[p].bwd_lvl) L.ilu_bwd_lvl.push_back(base + v);
+    L.ilu_fwd_loff[p + 1] = (int32_t)L.ilu_fwd_lvl.size();
+    L.ilu_bwd_loff[p + 1] = (int32_t)L.ilu_bwd_lvl.size();
+  }
+  // extraction of the lower triangle of every block (diagonal into D)
+  L.ilu_ext_pos.clear();
+  L.ilu_ext_nz.clear();
+  for (int p = 0; p < L.nsub; ++p) {
+    const int32_t* dofs = &L.sub_dofs[L.sub_ptr[p]];
+    const int n = L.sub_ptr[p + 1] - L.sub_ptr[p];
+    for (int i = 0; i < n; ++i) {
+      const int64_t R = L.sub_ptr[p] + i;
+      const int g = dofs[i];
+      for (int q = L.rowptr[g]; q < L.rowptr[g + 1]; ++q) {
+        const int32_t* it = std::lower_bound(dofs, dofs + n, L.col[q]);
+        if (it == dofs + n || *it != L.col[q]) continue;
+        const int k = (int)(it - dofs);
+        if (k > i) continue;
+        int64_t pos;
+        if (k == i) {
+          pos = L.ilu_nnz + R;
+        } else {
+          const int32_t* b = &L.ilu_lcol[L.ilu_lptr[R]];
+          const int32_t* e = &L.ilu_lcol[L.ilu_lptr[R + 1]];
+          pos = L.ilu_lptr[R] + (std::lower_bound(b, e, k) - b);  // A_p entries are in the pattern
+        }
+        L.ilu_ext_pos.push_back(pos);
+        L.ilu_ext_nz.push_back(q);
+      }
+    }
+  }
+}
+
 std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
   if (d.n_nodes <= 0 || d.n_tets <= 0 || !d.xyz || !d.tets || !d.dirichlet)
     return "level " + std::to_string(l) + ": empty mesh or NULL array";
@@ -753,6 +932,8 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     L.direct = (l + 1 == nlevels) && o.coarse_solver == MSP_COARSE_DIRECT;
     if (L.direct) build_coarsest_block(L);
     else build_subdomains(L, o.delta);
+    const int fill = (l == 0) ? o.ilu_fill_fine : o.ilu_fill_coarse;
+    if (!L.direct && fill >= 0) build_ilu(L, fill);
     if (L.sub_ptr[L.nsub] == 0 && L.direct && L.n > (int)L.dir_list.size())
       return "internal: empty coarsest block";
     build_factor_layout(L);

@@ -27,12 +27,13 @@ MSP_COARSE_DIRECT, MSP_COARSE_RAS = 0, 1
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
-          "val": 12, "factor": 13, "sub_nt": 14, "tile_first": 15}
+          "val": 12, "factor": 13, "sub_nt": 14, "tile_first": 15, "ilu_ptr": 16, "ilu_col": 17,
+          "ilu_val": 18, "ilu_d": 19}
 _ARRAY_DTYPE = {"rowptr": np.int32, "col": np.int32, "sub_ptr": np.int32, "sub_dofs": np.int32,
                 "sub_own": np.uint8, "P_rowptr": np.int32, "P_col": np.int32,
                 "P_val": np.float64, "PT_rowptr": np.int32, "PT_col": np.int32,
                 "PT_val": np.float64, "load": np.float64, "val": np.float64,
-                "sub_nt": np.int32, "tile_first": np.int32}
+                "sub_nt": np.int32, "tile_first": np.int32, "ilu_ptr": np.int64, "ilu_col": np.int32}
 KERNEL_CLASSES = ["assemble", "extract", "ldlt_diag", "ldlt_panel", "ldlt_trail", "ras",
                   "ras_coarser", "coarse", "spmv", "transfer", "vec", "ldlt_blocks"]
 MSP_TILE = 64
@@ -64,6 +65,7 @@ class msp_options(C.Structure):
                 ("coef_kind", C.c_int32), ("wave", (C.c_int32 * 3) * 8),
                 ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("transfer", C.c_int32),
                 ("restrict_scaling", C.c_int32), ("coarse_solver", C.c_int32),
+                ("ilu_fill_fine", C.c_int32), ("ilu_fill_coarse", C.c_int32),
                 ("host_only", C.c_int32),
                 ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
                 ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
@@ -223,7 +225,7 @@ class Hierarchy:
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
                  max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
                  load="one", host_only=False, budget_bytes=0, torch_alloc=True,
-                 transfer="bary", restrict_scaling=True, coarse="direct"):
+                 transfer="bary", restrict_scaling=True, coarse="direct", ilu=None):
         lib = _load_library()
         self._keep = []
         arr = (msp_level_desc * len(levels))()
@@ -245,6 +247,8 @@ class Hierarchy:
                             transfer={"bary": MSP_TRANSFER_BARY, "mls": MSP_TRANSFER_MLS}[transfer],
                             restrict_scaling=1 if restrict_scaling else 0,
                             coarse_solver={"direct": MSP_COARSE_DIRECT, "ras": MSP_COARSE_RAS}[coarse],
+                            ilu_fill_fine=-1 if ilu is None else int(ilu[0]),
+                            ilu_fill_coarse=-1 if ilu is None else int(ilu[1]),
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))
         if wave is not None:

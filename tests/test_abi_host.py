@@ -116,6 +116,25 @@ def test_host_smoothed_coarsest_matches_oracle(P, orc):
         P.Hierarchy(levels, host_only=True, coarse="ras", nu_pre=0)
 
 
+@pytest.mark.parametrize("name,ilu", [("cube16_3lvl", (2, 0)), ("cube20_3lvl", (1, 1))])
+def test_host_ilu_patterns_match_oracle(P, orc, name, ilu):
+    """The ILU(p) level-of-fill pattern of every block (strict lower part; the
+    blocks are symmetric) is the oracle's, bit for bit."""
+    levels, w = workload(name)
+    h = make_hierarchy(levels, w, P, host_only=True, ilu=ilu)
+    o = make_oracle(levels, w, orc, ilu=ilu)
+    o.assemble(syn.mu_draw(0))
+    o.factor()
+    for l in range(len(levels) - 1):
+        ptr, col, sptr = h.array(l, "ilu_ptr"), h.array(l, "ilu_col"), h.array(l, "sub_ptr")
+        for p in range(o.get("n_subs", l)):
+            fp, fc = o.get("sub_ilu_ptr", l, p), o.get("sub_ilu_col", l, p)
+            for i in range(fp.size - 1):
+                oc = fc[fp[i]:fp[i + 1]]
+                R = sptr[p] + i
+                np.testing.assert_array_equal(col[ptr[R]:ptr[R + 1]], oc[oc < i])
+
+
 def test_odd_partition_and_empty_boxes(P, orc):
     """Partition ids that skip values and boxes with only Dirichlet nodes."""
     fine = syn.cube_level(9, 3, parts=(5, 3, 2))

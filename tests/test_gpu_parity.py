@@ -401,6 +401,54 @@ def test_bf16_tensor_core_factorisation(P, orc, torch):
     assert st["iterations"] <= so["iters"] + 3
 
 
+# ------------------------------------------------------- ILU(p) subdomains
+@pytest.mark.parametrize("name,ilu", [("cube16_3lvl", (2, 0)), ("cube20_3lvl", (1, 1)),
+                                      ("cube20m_3lvl", (0, 2))])
+def test_ilu_subdomain_solver(P, orc, torch, name, ilu):
+    """ILU(p) subdomain factors (Section 4.4): L and D of every block, the RAS
+    application, the V-cycle and the FGMRES solution against the oracle."""
+    levels, w = workload(name)
+    mu = syn.mu_draw(4)
+    o = make_oracle(levels, w, orc, ilu=ilu)
+    o.assemble(mu)
+    o.factor()
+    h = make_hierarchy(levels, w, P, ilu=ilu)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    m = P.msp
+    rng = np.random.default_rng(8)
+    for l in range(len(levels) - 1):
+        ptr, sptr = h.array(l, "ilu_ptr"), h.array(l, "sub_ptr")
+        Lg, Dg = inst.array(l, "ilu_val"), inst.array(l, "ilu_d")
+        ns = o.get("n_subs", l)
+        for p in sorted({0, ns // 2, ns - 1}):
+            fp, fc, fv = (o.get(k, l, p) for k in ("sub_ilu_ptr", "sub_ilu_col", "sub_ilu_val"))
+            for i in range(fp.size - 1):
+                sel = fc[fp[i]:fp[i + 1]] < i
+                lo = fv[fp[i]:fp[i + 1]][sel]
+                R = sptr[p] + i
+                lg = Lg[ptr[R]:ptr[R + 1]]
+                assert np.max(np.abs(lg - lo), initial=0.0) <= 1e-12 * max(1.0, np.max(np.abs(lo), initial=0.0))
+                di = fv[fp[i]:fp[i + 1]][fc[fp[i]:fp[i + 1]] == i][0]
+                assert abs(Dg[R] - di) <= 1e-12 * abs(di)
+        r = rng.normal(size=levels[l].n_nodes)
+        z = torch.zeros(levels[l].n_nodes, dtype=torch.float64, device="cuda")
+        inst.apply_op(m.MSP_OP_RAS, l, torch.tensor(r, device="cuda"), z)
+        torch.cuda.synchronize()
+        assert rel(z.cpu().numpy(), o.ras_apply(r, l)) <= OP_TOL
+    r = rng.normal(size=levels[0].n_nodes)
+    z = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    inst.apply(torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), o.vcycle(r)) <= OP_TOL
+    x = torch.zeros_like(z)
+    st = inst.solve(x, rtol=1e-10)
+    xo, so = o.fgmres(rtol=1e-10, restart=w["restart"])
+    assert st["status"] == 0 and so["status"] == 0
+    assert abs(st["iterations"] - so["iters"]) <= 1
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+
+
 # ------------------------------------------- paper-literal Algorithm 2 options
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_paper_literal_algorithm2(P, orc, torch, precision):

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * kIluWarps) k_ilu_factor(
     const int32_t* __restrict__ fwd_loff, int max_n, int* __restrict__ info) {
   extern __shared__ double sm_ilu[];
   const int p = blockIdx.x;
-  const int R0 = sub_ptr[p], n = sub_ptr[p + 1] - R0;
+  const int R0 = sub_ptr[p];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* d_s = sm_ilu;              // [max_n] d of finished rows
   double* w = d_s + max_n + warp * max_n;  // [max_n] this warp's current row
@@ -94,60 +94,127 @@ __global__ void __launch_bounds__(32 * kIluWarps) k_ilu_factor(
   }
 }
 
+// One triangular sweep of a block, level by level: y_i -= sum_e Lx[e] y[src[e]]
+// over the entries e of row i.  A level's entries are contiguous (level-major
+// lists), so one thread per entry forms the products (into prod), then one
+// thread per row adds its products in entry order (deterministic) and
+// updates y.  The next level's entries, rows and offsets are loaded into
+// registers before the barrier, off the critical path.  Levels [q0, q1).
+constexpr int kSweepThreads = 256, kEnt = 4, kRows = 2;  // per thread and level
+
+struct SweepLevel {
+  int r0 = 0, r1 = 0;
+  int64_t e0 = 0, e1 = 0;
+  double v[kEnt];
+  int src[kEnt];
+  int row[kRows], b[kRows], e[kRows];
+};
+
+__device__ __forceinline__ void sweep_load(SweepLevel& L, int q, const double* __restrict__ Lx,
+                                           const int32_t* __restrict__ src, const int64_t* __restrict__ eptr,
+                                           const int32_t* __restrict__ rows, const int32_t* __restrict__ lvl) {
+  const int tid = threadIdx.x;
+  L.r0 = lvl[q];
+  L.r1 = lvl[q + 1];
+  L.e0 = eptr[L.r0];
+  L.e1 = eptr[L.r1];
+#pragma unroll
+  for (int k = 0; k < kEnt; ++k) {
+    const int64_t e = L.e0 + tid + k * kSweepThreads;
+    if (e < L.e1) {
+      L.v[k] = Lx[e];
+      L.src[k] = src[e];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRows; ++k) {
+    const int rr = L.r0 + tid + k * kSweepThreads;
+    if (rr < L.r1) {
+      L.row[k] = rows[rr];
+      L.b[k] = (int)(eptr[rr] - L.e0);
+      L.e[k] = (int)(eptr[rr + 1] - L.e0);
+    }
+  }
+}
+
+__device__ void ilu_sweep(double* __restrict__ y, double* __restrict__ prod, const double* __restrict__ Lx,
+                          const int32_t* __restrict__ src, const int64_t* __restrict__ eptr,
+                          const int32_t* __restrict__ rows, const int32_t* __restrict__ lvl, int q0, int q1) {
+  if (q0 >= q1) return;
+  const int tid = threadIdx.x;
+  SweepLevel cur, nxt;
+  sweep_load(cur, q0, Lx, src, eptr, rows, lvl);
+  for (int q = q0; q < q1; ++q) {
+#pragma unroll
+    for (int k = 0; k < kEnt; ++k) {
+      const int64_t e = cur.e0 + tid + k * kSweepThreads;
+      if (e < cur.e1) prod[e - cur.e0] = cur.v[k] * y[cur.src[k]];
+    }
+    if (q + 1 < q1) sweep_load(nxt, q + 1, Lx, src, eptr, rows, lvl);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+      const int rr = cur.r0 + tid + k * kSweepThreads;
+      if (rr < cur.r1) {
+        double s = 0.0;
+        for (int j = cur.b[k]; j < cur.e[k]; ++j) s += prod[j];
+        y[cur.row[k]] -= s;
+      }
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+}
+
 // y = (L D L^T)^{-1} t[dofs] of block p and the owned scatter into z (RAS,
-// Eq. 7).  Forward: y_i -= sum_{m in P(i)} l_im y_m, level by level; then
-// y_i /= d_i; backward: y_i -= sum_{j: i in P(j)} l_ji y_j over the transposed
-// pattern, by backward levels.  One warp per row.  smem: max_n doubles.
-__global__ void __launch_bounds__(32 * kIluWarps) k_ilu_solve(
+// Eq. 7): the forward sweep over the rows of L, y /= D, the backward sweep
+// over the columns of L (L^T).  smem: max_n + max level entries doubles.
+__global__ void __launch_bounds__(kSweepThreads) k_ilu_solve(
     const double* __restrict__ fac, int64_t nnz, int64_t rows, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
-    const int64_t* __restrict__ lptr, const int32_t* __restrict__ lcol,
-    const int64_t* __restrict__ tptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tslot,
+    const int64_t* __restrict__ fe_ptr, const int32_t* __restrict__ fe_src,
+    const int64_t* __restrict__ be_ptr, const int32_t* __restrict__ be_src,
     const int32_t* __restrict__ fwd_rows, const int32_t* __restrict__ fwd_lvl,
     const int32_t* __restrict__ fwd_loff, const int32_t* __restrict__ bwd_rows,
-    const int32_t* __restrict__ bwd_lvl, const int32_t* __restrict__ bwd_loff,
+    const int32_t* __restrict__ bwd_lvl, const int32_t* __restrict__ bwd_loff, int max_n,
     const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
     double* __restrict__ z, int add) {
   extern __shared__ double sm_ilu[];
   const int p = blockIdx.x;
   const int R0 = sub_ptr[p], n = sub_ptr[p + 1] - R0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double* L = fac;
   const double* Dinv = fac + nnz + rows;
+  const double* Lf = fac + nnz + 2 * rows;  // forward entries, level-major
+  const double* Lb = Lf + nnz;              // backward entries, level-major
   double* y = sm_ilu;
+  double* prod = sm_ilu + max_n;
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndir; d += gridDim.x * blockDim.x) {
     const int g = dir_list[d];
     z[g] = add ? z[g] + t[g] : t[g];
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = t[dofs[R0 + i]];
   __syncthreads();
-  for (int q = fwd_loff[p]; q + 1 < fwd_loff[p + 1]; ++q) {  // level q: rows fwd_lvl[q] .. fwd_lvl[q+1]
-    for (int rr = fwd_lvl[q] + warp; rr < fwd_lvl[q + 1]; rr += kIluWarps) {
-      const int i = fwd_rows[rr];
-      double s = 0.0;
-      for (int64_t u = lptr[R0 + i] + lane; u < lptr[R0 + i + 1]; u += 32) s = fma(L[u], y[lcol[u]], s);
-      s = warp_sum(s);
-      if (lane == 0) y[i] -= s;
-    }
-    __syncthreads();
-  }
+  ilu_sweep(y, prod, Lf, fe_src, fe_ptr, fwd_rows, fwd_lvl, fwd_loff[p], fwd_loff[p + 1] - 1);
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= Dinv[R0 + i];
   __syncthreads();
-  for (int q = bwd_loff[p]; q + 1 < bwd_loff[p + 1]; ++q) {
-    for (int rr = bwd_lvl[q] + warp; rr < bwd_lvl[q + 1]; rr += kIluWarps) {
-      const int i = bwd_rows[rr];
-      double s = 0.0;
-      for (int64_t u = tptr[R0 + i] + lane; u < tptr[R0 + i + 1]; u += 32) s = fma(L[tslot[u]], y[tcol[u]], s);
-      s = warp_sum(s);
-      if (lane == 0) y[i] -= s;
-    }
-    __syncthreads();
-  }
+  ilu_sweep(y, prod, Lb, be_src, be_ptr, bwd_rows, bwd_lvl, bwd_loff[p], bwd_loff[p + 1] - 1);
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     if (own[R0 + i]) {
       const int g = dofs[R0 + i];
       z[g] = add ? z[g] + y[i] : y[i];
     }
+}
+
+// Level-major copies of the factor for the sweeps: Lf[e] = L[fe_slot[e]],
+// Lb[e] = L[be_slot[e]].
+__global__ void k_ilu_gather(double* __restrict__ fac, int64_t nnz, int64_t rows,
+                             const int64_t* __restrict__ fe_slot, const int64_t* __restrict__ be_slot) {
+  const double* L = fac;
+  double* Lf = fac + nnz + 2 * rows;
+  double* Lb = Lf + nnz;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    Lf[e] = L[fe_slot[e]];
+    Lb[e] = L[be_slot[e]];
+  }
 }
 
 __global__ void k_ilu_zero(double* __restrict__ p, int64_t n) {
@@ -166,7 +233,9 @@ int nblocks(int64_t n, int per) { return (int)((n + per - 1) / per); }
 }  // namespace
 
 size_t ilu_factor_smem(int max_n) { return (size_t)(kIluWarps + 1) * max_n * sizeof(double); }
-size_t ilu_solve_smem(int max_n) { return (size_t)max_n * sizeof(double); }
+size_t ilu_solve_smem(int max_n, int max_lvl_ent) { return (size_t)(max_n + max_lvl_ent) * sizeof(double); }
+int ilu_sweep_limit_rows() { return kRows * kSweepThreads; }
+int ilu_sweep_limit_entries() { return kEnt * kSweepThreads; }
 
 void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
                         double* fac, cudaStream_t s) {
@@ -188,22 +257,26 @@ void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const i
                                                    fwd_loff, max_n, info);
 }
 
+void launch_ilu_gather(double* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,
+                       cudaStream_t s) {
+  if (nnz > 0) k_ilu_gather<<<std::min<int64_t>(nblocks(nnz, 256), 1 << 16), 256, 0, s>>>(fac, nnz, rows, fe_slot, be_slot);
+}
+
 void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, const int64_t* lptr, const int32_t* lcol,
-                      const int64_t* tptr, const int32_t* tcol, const int64_t* tslot,
-                      const int32_t* fwd_rows, const int32_t* fwd_lvl, const int32_t* fwd_loff,
-                      const int32_t* bwd_rows, const int32_t* bwd_lvl, const int32_t* bwd_loff,
-                      int max_n, const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      cudaStream_t s) {
+                      const int32_t* dofs, const uint8_t* own, const int64_t* fe_ptr, const int32_t* fe_src,
+                      const int64_t* be_ptr, const int32_t* be_src, const int32_t* fwd_rows,
+                      const int32_t* fwd_lvl, const int32_t* fwd_loff, const int32_t* bwd_rows,
+                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n, int max_lvl_ent,
+                      const int32_t* dir_list, int ndir, const double* t, double* z, int add, cudaStream_t s) {
   if (nsub <= 0) return;
-  const size_t smem = ilu_solve_smem(max_n);
+  const size_t smem = ilu_solve_smem(max_n, max_lvl_ent);
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_ilu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
-  k_ilu_solve<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, dofs, own, lptr, lcol, tptr, tcol,
-                                                  tslot, fwd_rows, fwd_lvl, fwd_loff, bwd_rows, bwd_lvl,
-                                                  bwd_loff, dir_list, ndir, t, z, add);
+  k_ilu_solve<<<nsub, kSweepThreads, smem, s>>>(fac, nnz, rows, sub_ptr, dofs, own, fe_ptr, fe_src, be_ptr, be_src,
+                                                 fwd_rows, fwd_lvl, fwd_loff, bwd_rows, bwd_lvl, bwd_loff, max_n,
+                                                 dir_list, ndir, t, z, add);
 }
 
 }  // namespace msp

@@ -84,9 +84,17 @@ struct HostLevel {
   //     ilu_*_lvl[loff + q + 1] of the rows arrays;
   //   ilu_ext_pos / ilu_ext_nz: extraction of the lower triangle of A_p into
   //     [L | D] (positions >= nnzL address D).
+  //   ilu_fe_* / ilu_be_*: the entries each sweep reads, in the order the
+  //     levels visit them (row position rr of ilu_*_rows owns entries
+  //     ilu_*e_ptr[rr] .. [rr+1]: source column and L position), so that a
+  //     level's entries are contiguous and can be fetched ahead;
+  //   ilu_max_lvl_rows / ilu_max_lvl_ent: the largest level of either sweep.
   int ilu_fill = -1;
   int64_t ilu_nnz = 0;
   int ilu_max_n = 0;
+  int ilu_max_lvl_rows = 0, ilu_max_lvl_ent = 0;
+  std::vector<int64_t> ilu_fe_ptr, ilu_fe_slot, ilu_be_ptr, ilu_be_slot;
+  std::vector<int32_t> ilu_fe_src, ilu_be_src;
   std::vector<int64_t> ilu_lptr, ilu_tptr, ilu_tslot, ilu_ext_pos;
   std::vector<int32_t> ilu_lcol, ilu_tcol, ilu_ext_nz;
   std::vector<int32_t> ilu_fwd_rows, ilu_fwd_lvl, ilu_fwd_loff;

@@ -93,20 +93,24 @@ void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, 
 int ldlt_blocks_tc_per_sm();
 // ---- ILU(p) subdomain factors (k_ilu.cu); fac = [L (nnz) | D (rows) | 1/D (rows)]
 size_t ilu_factor_smem(int max_n);
-size_t ilu_solve_smem(int max_n);
+size_t ilu_solve_smem(int max_n, int max_lvl_ent);
+int ilu_sweep_limit_rows();     // rows of one level a sweep can hold
+int ilu_sweep_limit_entries();  // entries of one level a sweep can hold
 void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
                         double* fac, cudaStream_t s);
 void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
                        const int64_t* lptr, const int32_t* lcol, const int32_t* fwd_rows,
                        const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int* info,
                        cudaStream_t s);
+// fac = [L | D | 1/D | Lf | Lb]: Lf, Lb the level-major copies (launch_ilu_gather)
+void launch_ilu_gather(double* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,
+                       cudaStream_t s);
 void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, const int64_t* lptr, const int32_t* lcol,
-                      const int64_t* tptr, const int32_t* tcol, const int64_t* tslot,
-                      const int32_t* fwd_rows, const int32_t* fwd_lvl, const int32_t* fwd_loff,
-                      const int32_t* bwd_rows, const int32_t* bwd_lvl, const int32_t* bwd_loff,
-                      int max_n, const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      cudaStream_t s);
+                      const int32_t* dofs, const uint8_t* own, const int64_t* fe_ptr, const int32_t* fe_src,
+                      const int64_t* be_ptr, const int32_t* be_src, const int32_t* fwd_rows,
+                      const int32_t* fwd_lvl, const int32_t* fwd_loff, const int32_t* bwd_rows,
+                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n, int max_lvl_ent,
+                      const int32_t* dir_list, int ndir, const double* t, double* z, int add, cudaStream_t s);
 // BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
 // n a multiple of 4.
 void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);

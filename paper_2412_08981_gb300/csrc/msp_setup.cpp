@@ -853,6 +853,45 @@ void build_ilu(HostLevel& L, int fill) {
     L.ilu_fwd_loff[p + 1] = (int32_t)L.ilu_fwd_lvl.size();
     L.ilu_bwd_loff[p + 1] = (int32_t)L.ilu_bwd_lvl.size();
   }
+  // level-major entry lists of both sweeps
+  {
+    const int64_t nrows = rows;
+    L.ilu_fe_ptr.assign(nrows + 1, 0);
+    L.ilu_be_ptr.assign(nrows + 1, 0);
+    L.ilu_fe_src.clear();
+    L.ilu_fe_slot.clear();
+    L.ilu_be_src.clear();
+    L.ilu_be_slot.clear();
+    L.ilu_max_lvl_rows = 0;
+    L.ilu_max_lvl_ent = 0;
+    for (int p = 0; p < L.nsub; ++p) {
+      const int64_t R0 = L.sub_ptr[p];
+      for (int64_t rr = R0; rr < L.sub_ptr[p + 1]; ++rr) {
+        const int64_t Rf = R0 + L.ilu_fwd_rows[rr];
+        for (int64_t t = L.ilu_lptr[Rf]; t < L.ilu_lptr[Rf + 1]; ++t) {
+          L.ilu_fe_src.push_back(L.ilu_lcol[t]);
+          L.ilu_fe_slot.push_back(t);
+        }
+        L.ilu_fe_ptr[rr + 1] = (int64_t)L.ilu_fe_src.size();
+        const int64_t Rb = R0 + L.ilu_bwd_rows[rr];
+        for (int64_t u = L.ilu_tptr[Rb]; u < L.ilu_tptr[Rb + 1]; ++u) {
+          L.ilu_be_src.push_back(L.ilu_tcol[u]);
+          L.ilu_be_slot.push_back(L.ilu_tslot[u]);
+        }
+        L.ilu_be_ptr[rr + 1] = (int64_t)L.ilu_be_src.size();
+      }
+      for (int q = L.ilu_fwd_loff[p]; q + 1 < L.ilu_fwd_loff[p + 1]; ++q) {
+        const int a = L.ilu_fwd_lvl[q], b = L.ilu_fwd_lvl[q + 1];
+        L.ilu_max_lvl_rows = std::max(L.ilu_max_lvl_rows, b - a);
+        L.ilu_max_lvl_ent = std::max(L.ilu_max_lvl_ent, (int)(L.ilu_fe_ptr[b] - L.ilu_fe_ptr[a]));
+      }
+      for (int q = L.ilu_bwd_loff[p]; q + 1 < L.ilu_bwd_loff[p + 1]; ++q) {
+        const int a = L.ilu_bwd_lvl[q], b = L.ilu_bwd_lvl[q + 1];
+        L.ilu_max_lvl_rows = std::max(L.ilu_max_lvl_rows, b - a);
+        L.ilu_max_lvl_ent = std::max(L.ilu_max_lvl_ent, (int)(L.ilu_be_ptr[b] - L.ilu_be_ptr[a]));
+      }
+    }
+  }
   // extraction of the lower triangle of every block (diagonal into D)
   L.ilu_ext_pos.clear();
   L.ilu_ext_nz.clear();

@@ -27,8 +27,86 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Up-looking incomplete L D L^T of block p: for row i, in ascending k over its
-// pattern, l_ik = (a_ik - sum_{m in P(k)} l_km d_m l_im) / d_k (entries of row
+// Up-looking incomplete L D L^T of block p (Section 4.4), rows of at most 32
+// strictly-lower entries: lane j of the row's warp owns entry (i, k_j).  With
+// u_j = l_{i k_j} d_{k_j} (the not yet divided entry), the row satisfies
+//   u_j = a_{i k_j} - sum_{j' < j} u_{j'} l_{k_j k_j'}    over the pattern,
+// so entry j is final once the earlier ones are, and step j broadcasts u_j and
+// every lane j'' > j with (k_j'', k_j) in the pattern subtracts u_j times that
+// entry of L (a register update: no reduction per step).  Then
+// l_{i k_j} = u_j / d_{k_j} and d_i = a_ii - sum_j l_{i k_j} u_j.  The L
+// entries a lane needs are gathered once per row into S[j][lane] through
+// pos (column -> lane of this row, -1 elsewhere).  Same fac layout as the
+// warp-per-dot form below.  smem per warp: 32 x 32 doubles + max_n int16.
+__global__ void __launch_bounds__(32 * kIluWarps) k_ilu_factor_lanes(
+    double* __restrict__ fac, int64_t nnz, int64_t rows, const int32_t* __restrict__ sub_ptr,
+    const int64_t* __restrict__ lptr, const int32_t* __restrict__ lcol,
+    const int32_t* __restrict__ fwd_rows, const int32_t* __restrict__ fwd_lvl,
+    const int32_t* __restrict__ fwd_loff, int max_n, int* __restrict__ info) {
+  extern __shared__ double sm_ilu[];
+  const int p = blockIdx.x;
+  const int R0 = sub_ptr[p];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pos_stride = (max_n + 3) & ~3;
+  double* S = sm_ilu + warp * 1024;
+  int16_t* pos_all = reinterpret_cast<int16_t*>(sm_ilu + kIluWarps * 1024);
+  int16_t* pos = pos_all + warp * pos_stride;
+  double* L = fac;
+  double* D = fac + nnz;
+  double* Dinv = D + rows;
+  for (int e = threadIdx.x; e < kIluWarps * pos_stride; e += blockDim.x) pos_all[e] = -1;
+  __syncthreads();
+  for (int q = fwd_loff[p]; q + 1 < fwd_loff[p + 1]; ++q) {
+    const int r0 = fwd_lvl[q], r1 = fwd_lvl[q + 1];
+    for (int rr = r0 + warp; rr < r1; rr += kIluWarps) {
+      const int i = fwd_rows[rr];
+      const int64_t b = lptr[R0 + i];
+      const int len = (int)(lptr[R0 + i + 1] - b);  // <= 32 (host check)
+      int k = 0;
+      double u = 0.0, dinv = 0.0;
+      if (lane < len) {
+        k = lcol[b + lane];
+        u = L[b + lane];
+        dinv = Dinv[R0 + k];
+        pos[k] = (int16_t)lane;
+      }
+      __syncwarp();
+      uint32_t mask = 0;
+      if (lane < len) {
+        const int64_t kb = lptr[R0 + k], ke = lptr[R0 + k + 1];
+        for (int64_t t = kb; t < ke; ++t) {
+          const int jj = pos[lcol[t]];
+          if (jj >= 0) {
+            S[jj * 32 + lane] = L[t];
+            mask |= 1u << jj;
+          }
+        }
+      }
+      __syncwarp();
+      for (int j = 0; j < len; ++j) {
+        const double uj = __shfl_sync(0xffffffffu, u, j);
+        if ((mask >> j) & 1u) u = fma(-uj, S[j * 32 + lane], u);
+      }
+      const double l = u * dinv;
+      const double s = warp_sum(lane < len ? l * u : 0.0);
+      if (lane < len) {
+        L[b + lane] = l;
+        pos[k] = -1;
+      }
+      if (lane == 0) {
+        const double di = D[R0 + i] - s;
+        D[R0 + i] = di;
+        Dinv[R0 + i] = 1.0 / di;
+        if (di == 0.0 || !(fabs(di) < 1e300)) atomicOr(info, 1);  // zero or non-finite pivot
+      }
+      __syncwarp();
+    }
+    __syncthreads();  // the level's rows (L, D, 1/D) are final for the next levels
+  }
+}
+
+// Up-looking incomplete L D L^T of block p, any row length: for row i, in
+// ascending k over its pattern, l_ik = (a_ik - sum_{m in P(k)} l_km d_m l_im) / d_k (entries of row
 // i outside its pattern are zero, which drops the fill of level > p), then
 // d_i = a_ii - sum_m l_im^2 d_m.  fac = [L (nnz) | D (rows) | 1/D (rows)],
 // holding A_p's lower triangle on entry (extraction).  Each warp keeps its
@@ -232,7 +310,10 @@ int nblocks(int64_t n, int per) { return (int)((n + per - 1) / per); }
 
 }  // namespace
 
-size_t ilu_factor_smem(int max_n) { return (size_t)(kIluWarps + 1) * max_n * sizeof(double); }
+size_t ilu_factor_smem(int max_n, int max_row) {
+  if (max_row <= 32) return (size_t)kIluWarps * (1024 * sizeof(double) + ((max_n + 3) & ~3) * sizeof(int16_t));
+  return (size_t)(kIluWarps + 1) * max_n * sizeof(double);
+}
 size_t ilu_solve_smem(int max_n, int max_lvl_ent) { return (size_t)(max_n + max_lvl_ent) * sizeof(double); }
 int ilu_sweep_limit_rows() { return kRows * kSweepThreads; }
 int ilu_sweep_limit_entries() { return kEnt * kSweepThreads; }
@@ -245,16 +326,21 @@ void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, con
 
 void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
                        const int64_t* lptr, const int32_t* lcol, const int32_t* fwd_rows,
-                       const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int* info,
+                       const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int max_row, int* info,
                        cudaStream_t s) {
   if (nsub <= 0) return;
-  const size_t smem = ilu_factor_smem(max_n);
+  const size_t smem = ilu_factor_smem(max_n, max_row);
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_ilu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ilu_factor_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
-  k_ilu_factor<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, lptr, lcol, fwd_rows, fwd_lvl,
-                                                   fwd_loff, max_n, info);
+  if (max_row <= 32)
+    k_ilu_factor_lanes<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, lptr, lcol, fwd_rows, fwd_lvl,
+                                                         fwd_loff, max_n, info);
+  else
+    k_ilu_factor<<<nsub, 32 * kIluWarps, smem, s>>>(fac, nnz, rows, sub_ptr, lptr, lcol, fwd_rows, fwd_lvl,
+                                                     fwd_loff, max_n, info);
 }
 
 void launch_ilu_gather(double* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,

@@ -102,10 +102,10 @@ struct DevLevel {
   // ILU(p) subdomain factors (see HostLevel)
   bool ilu = false;
   int64_t ilu_nnz = 0, ilu_rows = 0, ilu_next = 0;
-  int ilu_max_n = 0;
+  int ilu_max_n = 0, ilu_max_row = 0;
   double ilu_flops = 0;  // algorithmic flops of one ILU factorisation of the level
-  int64_t *ilu_lptr = nullptr, *ilu_tptr = nullptr, *ilu_tslot = nullptr, *ilu_ext_pos = nullptr;
-  int32_t *ilu_lcol = nullptr, *ilu_tcol = nullptr, *ilu_ext_nz = nullptr;
+  int64_t *ilu_lptr = nullptr, *ilu_ext_pos = nullptr;
+  int32_t *ilu_lcol = nullptr, *ilu_ext_nz = nullptr;
   int32_t *ilu_fwd_rows = nullptr, *ilu_fwd_lvl = nullptr, *ilu_fwd_loff = nullptr;
   int32_t *ilu_bwd_rows = nullptr, *ilu_bwd_lvl = nullptr, *ilu_bwd_loff = nullptr;
   int64_t *ilu_fe_ptr = nullptr, *ilu_fe_slot = nullptr, *ilu_be_ptr = nullptr, *ilu_be_slot = nullptr;
@@ -321,6 +321,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.ilu_nnz = H.ilu_nnz;
     D.ilu_rows = H.sub_ptr.empty() ? 0 : H.sub_ptr.back();
     D.ilu_max_n = H.ilu_max_n;
+    D.ilu_max_row = H.ilu_max_row;
     D.fac_elems = 3 * D.ilu_nnz + 2 * D.ilu_rows;  // [L | D | 1/D | Lf | Lb]
     D.ilu_max_lvl_ent = H.ilu_max_lvl_ent;
     D.ilu_fe_ptr = A.upload(H.ilu_fe_ptr);
@@ -331,9 +332,6 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.ilu_be_slot = A.upload(H.ilu_be_slot);
     D.ilu_lptr = A.upload(H.ilu_lptr);
     D.ilu_lcol = A.upload(H.ilu_lcol);
-    D.ilu_tptr = A.upload(H.ilu_tptr);
-    D.ilu_tcol = A.upload(H.ilu_tcol);
-    D.ilu_tslot = A.upload(H.ilu_tslot);
     D.ilu_fwd_rows = A.upload(H.ilu_fwd_rows);
     D.ilu_fwd_lvl = A.upload(H.ilu_fwd_lvl);
     D.ilu_fwd_loff = A.upload(H.ilu_fwd_loff);
@@ -358,7 +356,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": an ILU dependency level is too wide for "
                                    "the sweep kernel (" + std::to_string(H.ilu_max_lvl_rows) + " rows, " +
                                    std::to_string(H.ilu_max_lvl_ent) + " entries)");
-    if (ilu_factor_smem(D.ilu_max_n) > 200u * 1024u)
+    if (ilu_factor_smem(D.ilu_max_n, D.ilu_max_row) > 200u * 1024u)
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large for the ILU "
                                    "kernels (" + std::to_string(D.ilu_max_n) + " DoFs)");
   } else {
@@ -606,7 +604,7 @@ int enqueue_factor(msp_instance* I) {
       }
       ProfScope ps(I->prof, PK_LDLT_BLOCKS, s, 2);
       launch_ilu_factor(fac, D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.ilu_lptr, D.ilu_lcol, D.ilu_fwd_rows,
-                        D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_max_n, I->info, s);
+                        D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_max_n, D.ilu_max_row, I->info, s);
       launch_ilu_gather(fac, D.ilu_nnz, D.ilu_rows, D.ilu_fe_slot, D.ilu_be_slot, s);
       ps.account((double)D.ilu_nnz * 8 * 5, D.ilu_flops);
     } else if (st == Store::F64) {
@@ -634,7 +632,6 @@ int enqueue_factor(msp_instance* I) {
 // graph is used only while no kernel class is being timed; the per-class
 // launch, byte and flop counts of one factorisation are added per replay.
 int factor_all(msp_instance* I) {
-  msp_hierarchy* h = I->h;
   const bool graph_ok = I->prof.mask == 0;
   if (graph_ok && !I->fac_graph && I->fac_calls >= 1) {
     msp_kernel_profile before[PK_COUNT];

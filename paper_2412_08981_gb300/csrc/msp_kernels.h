@@ -92,7 +92,7 @@ void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, 
                            int grid, int* info, cudaStream_t s);
 int ldlt_blocks_tc_per_sm();
 // ---- ILU(p) subdomain factors (k_ilu.cu); fac = [L (nnz) | D (rows) | 1/D (rows)]
-size_t ilu_factor_smem(int max_n);
+size_t ilu_factor_smem(int max_n, int max_row);  // max_row: most strictly-lower entries of a row
 size_t ilu_solve_smem(int max_n, int max_lvl_ent);
 int ilu_sweep_limit_rows();     // rows of one level a sweep can hold
 int ilu_sweep_limit_entries();  // entries of one level a sweep can hold
@@ -100,7 +100,7 @@ void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, con
                         double* fac, cudaStream_t s);
 void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
                        const int64_t* lptr, const int32_t* lcol, const int32_t* fwd_rows,
-                       const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int* info,
+                       const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int max_row, int* info,
                        cudaStream_t s);
 // fac = [L | D | 1/D | Lf | Lb]: Lf, Lb the level-major copies (launch_ilu_gather)
 void launch_ilu_gather(double* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,

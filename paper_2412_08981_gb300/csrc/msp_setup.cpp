@@ -819,6 +819,9 @@ void build_ilu(HostLevel& L, int fill) {
     L.ilu_lcol.insert(L.ilu_lcol.end(), subs[p].lcol.begin(), subs[p].lcol.end());
   }
   L.ilu_nnz = L.ilu_lptr[rows];
+  L.ilu_max_row = 0;
+  for (int64_t R = 0; R < rows; ++R)
+    L.ilu_max_row = std::max(L.ilu_max_row, (int)(L.ilu_lptr[R + 1] - L.ilu_lptr[R]));
   // transposed pattern
   L.ilu_tptr.assign(rows + 1, 0);
   for (int p = 0; p < L.nsub; ++p)

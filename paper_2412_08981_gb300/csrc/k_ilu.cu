@@ -173,80 +173,130 @@ __global__ void __launch_bounds__(32 * kIluWarps) k_ilu_factor(
 }
 
 // One triangular sweep of a block, level by level: y_i -= sum_e Lx[e] y[src[e]]
-// over the entries e of row i.  A level's entries are contiguous (level-major
-// lists), so one thread per entry forms the products (into prod), then one
-// thread per row adds its products in entry order (deterministic) and
-// updates y.  The next level's entries, rows and offsets are loaded into
-// registers before the barrier, off the critical path.  Levels [q0, q1).
-constexpr int kSweepThreads = 256, kEnt = 4, kRows = 2;  // per thread and level
+// over the entries e of row i (the rows of a level are independent).  A
+// group of kGroup lanes takes one row: lane g forms the products of entries
+// g, g + kGroup, ... with FMAs and the group adds its partial sums by a fixed
+// shuffle tree (deterministic), so a level costs a few dependent FP64
+// operations instead of one per entry.  A level's entries are contiguous
+// (level-major lists): they are copied into a ring of kRing shared-memory
+// slots with cp.async kRing - 1 levels ahead, so the global-memory latency is
+// off the level-to-level critical path (entries past a slot's kRingEnt come
+// straight from global memory).  One barrier per level.
+constexpr int kSweepThreads = 256, kGroup = 8, kGroups = kSweepThreads / kGroup;
+constexpr int kRing = 4, kRingEnt = 384, kEntUnroll = 4;
 
-struct SweepLevel {
-  int r0 = 0, r1 = 0;
-  int64_t e0 = 0, e1 = 0;
-  double v[kEnt];
-  int src[kEnt];
-  int row[kRows], b[kRows], e[kRows];
-};
-
-__device__ __forceinline__ void sweep_load(SweepLevel& L, int q, const double* __restrict__ Lx,
-                                           const int32_t* __restrict__ src, const int64_t* __restrict__ eptr,
-                                           const int32_t* __restrict__ rows, const int32_t* __restrict__ lvl) {
-  const int tid = threadIdx.x;
-  L.r0 = lvl[q];
-  L.r1 = lvl[q + 1];
-  L.e0 = eptr[L.r0];
-  L.e1 = eptr[L.r1];
-#pragma unroll
-  for (int k = 0; k < kEnt; ++k) {
-    const int64_t e = L.e0 + tid + k * kSweepThreads;
-    if (e < L.e1) {
-      L.v[k] = Lx[e];
-      L.src[k] = src[e];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kRows; ++k) {
-    const int rr = L.r0 + tid + k * kSweepThreads;
-    if (rr < L.r1) {
-      L.row[k] = rows[rr];
-      L.b[k] = (int)(eptr[rr] - L.e0);
-      L.e[k] = (int)(eptr[rr + 1] - L.e0);
-    }
-  }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ void ilu_sweep(double* __restrict__ y, double* __restrict__ prod, const double* __restrict__ Lx,
-                          const int32_t* __restrict__ src, const int64_t* __restrict__ eptr,
-                          const int32_t* __restrict__ rows, const int32_t* __restrict__ lvl, int q0, int q1) {
-  if (q0 >= q1) return;
-  const int tid = threadIdx.x;
-  SweepLevel cur, nxt;
-  sweep_load(cur, q0, Lx, src, eptr, rows, lvl);
-  for (int q = q0; q < q1; ++q) {
+__device__ __forceinline__ double group_sum(double s) {
 #pragma unroll
-    for (int k = 0; k < kEnt; ++k) {
-      const int64_t e = cur.e0 + tid + k * kSweepThreads;
-      if (e < cur.e1) prod[e - cur.e0] = cur.v[k] * y[cur.src[k]];
+  for (int o = 1; o < kGroup; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Issues (and commits, possibly empty) the copies of level q into its slot.
+__device__ __forceinline__ void sweep_fetch(int q, int nlev, const int* lvl_s, const int* eptr_s,
+                                            const double* __restrict__ Lx, const int32_t* __restrict__ src,
+                                            double* ring_v, int* ring_s) {
+  if (q < nlev) {
+    const int e0 = eptr_s[lvl_s[q]], ne = min(eptr_s[lvl_s[q + 1]] - e0, kRingEnt);
+    double* sv = ring_v + (q % kRing) * kRingEnt;
+    int* ss = ring_s + (q % kRing) * kRingEnt;
+    for (int j = threadIdx.x; j < ne; j += kSweepThreads) {
+      cp_async8(sv + j, Lx + e0 + j);
+      cp_async4(ss + j, src + e0 + j);
     }
-    if (q + 1 < q1) sweep_load(nxt, q + 1, Lx, src, eptr, rows, lvl);
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kRows; ++k) {
-      const int rr = cur.r0 + tid + k * kSweepThreads;
-      if (rr < cur.r1) {
-        double s = 0.0;
-        for (int j = cur.b[k]; j < cur.e[k]; ++j) s += prod[j];
-        y[cur.row[k]] -= s;
-      }
-    }
-    __syncthreads();
-    cur = nxt;
   }
+  cp_async_commit();
+}
+
+// Sweep over levels [0, nlev) of the block; Lx and src start at the block's
+// first entry, lvl_s / rows_s / eptr_s are relative to the block.
+__device__ void ilu_sweep(double* __restrict__ y, const double* __restrict__ Lx, const int32_t* __restrict__ src,
+                          const int* lvl_s, const int* rows_s, const int* eptr_s, int nlev, double* ring_v,
+                          int* ring_s) {
+  const int lane = threadIdx.x & 31, gl = threadIdx.x % kGroup;
+  // the row groups of a pass start at a block-dependent warp, so that the
+  // FP64 work of the blocks sharing an SM spreads over its four schedulers
+  const int quad = ((threadIdx.x >> 5) - (int)blockIdx.x) & (kSweepThreads / 32 - 1);
+#pragma unroll
+  for (int q = 0; q < kRing - 1; ++q) sweep_fetch(q, nlev, lvl_s, eptr_s, Lx, src, ring_v, ring_s);
+  for (int q = 0; q < nlev; ++q) {
+    cp_async_wait<kRing - 2>();  // this thread's copies of level q have landed
+    __syncthreads();             // everyone's, and the y of the previous levels
+    const int r0 = lvl_s[q], r1 = lvl_s[q + 1], e0 = eptr_s[r0];
+    const double* sv = ring_v + (q % kRing) * kRingEnt;
+    const int* ss = ring_s + (q % kRing) * kRingEnt;
+    for (int base = r0; base < r1; base += kGroups) {
+      if (base + quad * (32 / kGroup) >= r1) break;  // no row for this warp (warp-uniform)
+      const int rr = base + quad * (32 / kGroup) + (lane / kGroup);
+      double acc = 0.0;
+      int row = 0;
+      if (rr < r1) {
+        row = rows_s[rr];
+        const int jb = eptr_s[rr] - e0 + gl, je = eptr_s[rr + 1] - e0;
+        if (je <= kRingEnt) {
+          // the first kEntUnroll entries of the lane at once (loads issued together)
+          double v[kEntUnroll];
+          int c[kEntUnroll];
+#pragma unroll
+          for (int k = 0; k < kEntUnroll; ++k) {
+            const int j = jb + k * kGroup;
+            v[k] = 0.0;
+            c[k] = 0;
+            if (j < je) {
+              v[k] = sv[j];
+              c[k] = ss[j];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kEntUnroll; ++k) acc = fma(v[k], y[c[k]], acc);
+          for (int j = jb + kEntUnroll * kGroup; j < je; j += kGroup) acc = fma(sv[j], y[ss[j]], acc);
+        } else {
+          for (int j = jb; j < je; j += kGroup)
+            acc = j < kRingEnt ? fma(sv[j], y[ss[j]], acc) : fma(Lx[e0 + j], y[src[e0 + j]], acc);
+        }
+      }
+      acc = group_sum(acc);
+      if (gl == 0 && rr < r1) y[row] -= acc;
+    }
+    sweep_fetch(q + kRing - 1, nlev, lvl_s, eptr_s, Lx, src, ring_v, ring_s);  // into the slot of q - 1
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// Copies the sweep's schedule of block p into shared memory (relative to the
+// block): level bounds, rows in level order, entry offsets.  Returns the
+// level count and the block's first entry.
+__device__ int sweep_schedule(int p, const int32_t* __restrict__ loff, const int32_t* __restrict__ lvl,
+                              const int32_t* __restrict__ rows, const int64_t* __restrict__ eptr, int* lvl_s,
+                              int* rows_s, int* eptr_s, int64_t* e_base) {
+  const int q0 = loff[p], nlev = loff[p + 1] - 1 - q0;
+  const int rb = lvl[q0], nr = lvl[q0 + nlev] - rb;
+  const int64_t eb = eptr[rb];
+  for (int q = threadIdx.x; q <= nlev; q += blockDim.x) lvl_s[q] = lvl[q0 + q] - rb;
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) rows_s[r] = rows[rb + r];
+  for (int r = threadIdx.x; r <= nr; r += blockDim.x) eptr_s[r] = (int)(eptr[rb + r] - eb);
+  *e_base = eb;
+  return nlev;
 }
 
 // y = (L D L^T)^{-1} t[dofs] of block p and the owned scatter into z (RAS,
 // Eq. 7): the forward sweep over the rows of L, y /= D, the backward sweep
-// over the columns of L (L^T).  smem: max_n + max level entries doubles.
+// over the columns of L (L^T).  smem: max_n doubles + 3 max_n + 2 ints, and
+// the ring of kRing x kRingEnt entries.
 __global__ void __launch_bounds__(kSweepThreads) k_ilu_solve(
     const double* __restrict__ fac, int64_t nnz, int64_t rows, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
@@ -264,17 +314,24 @@ __global__ void __launch_bounds__(kSweepThreads) k_ilu_solve(
   const double* Lf = fac + nnz + 2 * rows;  // forward entries, level-major
   const double* Lb = Lf + nnz;              // backward entries, level-major
   double* y = sm_ilu;
-  double* prod = sm_ilu + max_n;
+  int* rows_s = reinterpret_cast<int*>(sm_ilu + max_n);
+  int* eptr_s = rows_s + max_n;
+  int* lvl_s = eptr_s + max_n + 1;
+  double* ring_v = reinterpret_cast<double*>(rows_s + ((3 * max_n + 3) & ~1));  // 8-byte aligned
+  int* ring_s = reinterpret_cast<int*>(ring_v + kRing * kRingEnt);
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndir; d += gridDim.x * blockDim.x) {
     const int g = dir_list[d];
     z[g] = add ? z[g] + t[g] : t[g];
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = t[dofs[R0 + i]];
+  int64_t eb = 0;
+  int nlev = sweep_schedule(p, fwd_loff, fwd_lvl, fwd_rows, fe_ptr, lvl_s, rows_s, eptr_s, &eb);
   __syncthreads();
-  ilu_sweep(y, prod, Lf, fe_src, fe_ptr, fwd_rows, fwd_lvl, fwd_loff[p], fwd_loff[p + 1] - 1);
+  ilu_sweep(y, Lf + eb, fe_src + eb, lvl_s, rows_s, eptr_s, nlev, ring_v, ring_s);
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= Dinv[R0 + i];
+  nlev = sweep_schedule(p, bwd_loff, bwd_lvl, bwd_rows, be_ptr, lvl_s, rows_s, eptr_s, &eb);
   __syncthreads();
-  ilu_sweep(y, prod, Lb, be_src, be_ptr, bwd_rows, bwd_lvl, bwd_loff[p], bwd_loff[p + 1] - 1);
+  ilu_sweep(y, Lb + eb, be_src + eb, lvl_s, rows_s, eptr_s, nlev, ring_v, ring_s);
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     if (own[R0 + i]) {
       const int g = dofs[R0 + i];
@@ -314,9 +371,12 @@ size_t ilu_factor_smem(int max_n, int max_row) {
   if (max_row <= 32) return (size_t)kIluWarps * (1024 * sizeof(double) + ((max_n + 3) & ~3) * sizeof(int16_t));
   return (size_t)(kIluWarps + 1) * max_n * sizeof(double);
 }
-size_t ilu_solve_smem(int max_n, int max_lvl_ent) { return (size_t)(max_n + max_lvl_ent) * sizeof(double); }
-int ilu_sweep_limit_rows() { return kRows * kSweepThreads; }
-int ilu_sweep_limit_entries() { return kEnt * kSweepThreads; }
+size_t ilu_solve_smem(int max_n) {
+  // y; rows, entry offsets and level bounds (3 max_n + 2 ints, padded to 8
+  // bytes); ring values and columns
+  return (size_t)max_n * sizeof(double) + (size_t)((3 * max_n + 3) & ~1) * sizeof(int) +
+         (size_t)kRing * kRingEnt * (sizeof(double) + sizeof(int));
+}
 
 void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
                         double* fac, cudaStream_t s) {
@@ -352,10 +412,10 @@ void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, co
                       const int32_t* dofs, const uint8_t* own, const int64_t* fe_ptr, const int32_t* fe_src,
                       const int64_t* be_ptr, const int32_t* be_src, const int32_t* fwd_rows,
                       const int32_t* fwd_lvl, const int32_t* fwd_loff, const int32_t* bwd_rows,
-                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n, int max_lvl_ent,
+                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add, cudaStream_t s) {
   if (nsub <= 0) return;
-  const size_t smem = ilu_solve_smem(max_n, max_lvl_ent);
+  const size_t smem = ilu_solve_smem(max_n);
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_ilu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -110,7 +110,6 @@ struct DevLevel {
   int32_t *ilu_bwd_rows = nullptr, *ilu_bwd_lvl = nullptr, *ilu_bwd_loff = nullptr;
   int64_t *ilu_fe_ptr = nullptr, *ilu_fe_slot = nullptr, *ilu_be_ptr = nullptr, *ilu_be_slot = nullptr;
   int32_t *ilu_fe_src = nullptr, *ilu_be_src = nullptr;
-  int ilu_max_lvl_ent = 0;
   int32_t *rowptr = nullptr, *col = nullptr, *diag = nullptr, *cptr = nullptr, *contrib = nullptr;
   uint8_t *nzflag = nullptr, *dir = nullptr;
   int32_t* dir_list = nullptr;
@@ -323,7 +322,6 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.ilu_max_n = H.ilu_max_n;
     D.ilu_max_row = H.ilu_max_row;
     D.fac_elems = 3 * D.ilu_nnz + 2 * D.ilu_rows;  // [L | D | 1/D | Lf | Lb]
-    D.ilu_max_lvl_ent = H.ilu_max_lvl_ent;
     D.ilu_fe_ptr = A.upload(H.ilu_fe_ptr);
     D.ilu_fe_src = A.upload(H.ilu_fe_src);
     D.ilu_fe_slot = A.upload(H.ilu_fe_slot);
@@ -351,12 +349,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
         D.ilu_flops += 3.0 * (double)(H.ilu_lptr[R + 1] - H.ilu_lptr[R]) + 1;
       }
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
-    if (H.ilu_max_lvl_rows > ilu_sweep_limit_rows() || H.ilu_max_lvl_ent > ilu_sweep_limit_entries() ||
-        ilu_solve_smem(D.ilu_max_n, D.ilu_max_lvl_ent) > 200u * 1024u)
-      return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": an ILU dependency level is too wide for "
-                                   "the sweep kernel (" + std::to_string(H.ilu_max_lvl_rows) + " rows, " +
-                                   std::to_string(H.ilu_max_lvl_ent) + " entries)");
-    if (ilu_factor_smem(D.ilu_max_n, D.ilu_max_row) > 200u * 1024u)
+    if (ilu_factor_smem(D.ilu_max_n, D.ilu_max_row) > 200u * 1024u || ilu_solve_smem(D.ilu_max_n) > 200u * 1024u)
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large for the ILU "
                                    "kernels (" + std::to_string(D.ilu_max_n) + " DoFs)");
   } else {
@@ -690,7 +683,7 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
     launch_ilu_solve(static_cast<const double*>(I->fac[l]), D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.sub_dofs,
                      D.sub_own, D.ilu_fe_ptr, D.ilu_fe_src, D.ilu_be_ptr, D.ilu_be_src, D.ilu_fwd_rows,
                      D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_bwd_rows, D.ilu_bwd_lvl, D.ilu_bwd_loff, D.ilu_max_n,
-                     D.ilu_max_lvl_ent, D.dir_list, D.ndir, t, z, add, s);
+                     D.dir_list, D.ndir, t, z, add, s);
     ps.account(2.0 * (double)D.ilu_nnz * 12 + (double)D.sum_np * 21 + (double)D.sum_owned * (add ? 16 : 8),
                4.0 * (double)D.ilu_nnz + (double)D.sum_np);
     return;

@@ -93,9 +93,7 @@ void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, 
 int ldlt_blocks_tc_per_sm();
 // ---- ILU(p) subdomain factors (k_ilu.cu); fac = [L (nnz) | D (rows) | 1/D (rows)]
 size_t ilu_factor_smem(int max_n, int max_row);  // max_row: most strictly-lower entries of a row
-size_t ilu_solve_smem(int max_n, int max_lvl_ent);
-int ilu_sweep_limit_rows();     // rows of one level a sweep can hold
-int ilu_sweep_limit_entries();  // entries of one level a sweep can hold
+size_t ilu_solve_smem(int max_n);
 void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
                         double* fac, cudaStream_t s);
 void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
@@ -109,7 +107,7 @@ void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, co
                       const int32_t* dofs, const uint8_t* own, const int64_t* fe_ptr, const int32_t* fe_src,
                       const int64_t* be_ptr, const int32_t* be_src, const int32_t* fwd_rows,
                       const int32_t* fwd_lvl, const int32_t* fwd_loff, const int32_t* bwd_rows,
-                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n, int max_lvl_ent,
+                      const int32_t* bwd_lvl, const int32_t* bwd_loff, int max_n,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add, cudaStream_t s);
 // BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
 // n a multiple of 4.

@@ -865,8 +865,6 @@ void build_ilu(HostLevel& L, int fill) {
     L.ilu_fe_slot.clear();
     L.ilu_be_src.clear();
     L.ilu_be_slot.clear();
-    L.ilu_max_lvl_rows = 0;
-    L.ilu_max_lvl_ent = 0;
     for (int p = 0; p < L.nsub; ++p) {
       const int64_t R0 = L.sub_ptr[p];
       for (int64_t rr = R0; rr < L.sub_ptr[p + 1]; ++rr) {
@@ -882,16 +880,6 @@ void build_ilu(HostLevel& L, int fill) {
           L.ilu_be_slot.push_back(L.ilu_tslot[u]);
         }
         L.ilu_be_ptr[rr + 1] = (int64_t)L.ilu_be_src.size();
-      }
-      for (int q = L.ilu_fwd_loff[p]; q + 1 < L.ilu_fwd_loff[p + 1]; ++q) {
-        const int a = L.ilu_fwd_lvl[q], b = L.ilu_fwd_lvl[q + 1];
-        L.ilu_max_lvl_rows = std::max(L.ilu_max_lvl_rows, b - a);
-        L.ilu_max_lvl_ent = std::max(L.ilu_max_lvl_ent, (int)(L.ilu_fe_ptr[b] - L.ilu_fe_ptr[a]));
-      }
-      for (int q = L.ilu_bwd_loff[p]; q + 1 < L.ilu_bwd_loff[p + 1]; ++q) {
-        const int a = L.ilu_bwd_lvl[q], b = L.ilu_bwd_lvl[q + 1];
-        L.ilu_max_lvl_rows = std::max(L.ilu_max_lvl_rows, b - a);
-        L.ilu_max_lvl_ent = std::max(L.ilu_max_lvl_ent, (int)(L.ilu_be_ptr[b] - L.ilu_be_ptr[a]));
       }
     }
   }

@@ -201,7 +201,9 @@ bool direct_level(const msp_hierarchy* h, int l) { return h->host[l].direct; }
 // Storage of a level's factors (the directly solved level is always FP64).
 enum class Store { F64, F32, BF16 };
 Store level_store(const msp_hierarchy* h, int l) {
-  if (direct_level(h, l) || h->host[l].ilu_fill >= 0) return Store::F64;
+  if (direct_level(h, l)) return Store::F64;
+  if (h->host[l].ilu_fill >= 0)  // ILU levels: FP32 for either reduced precision (sparse sweeps, no tensor cores)
+    return h->opt.factor_precision == MSP_F64 ? Store::F64 : Store::F32;
   if (h->opt.factor_precision == MSP_F32) return Store::F32;
   if (h->opt.factor_precision == MSP_BF16) return Store::BF16;
   return Store::F64;
@@ -349,7 +351,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
         D.ilu_flops += 3.0 * (double)(H.ilu_lptr[R + 1] - H.ilu_lptr[R]) + 1;
       }
     if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
-    if (ilu_factor_smem(D.ilu_max_n, D.ilu_max_row) > 200u * 1024u || ilu_solve_smem(D.ilu_max_n) > 200u * 1024u)
+    if (ilu_factor_smem(D.ilu_max_n, D.ilu_max_row, 8) > 200u * 1024u || ilu_solve_smem(D.ilu_max_n, 8) > 200u * 1024u)
       return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large for the ILU "
                                    "kernels (" + std::to_string(D.ilu_max_n) + " DoFs)");
   } else {
@@ -572,6 +574,23 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
   cudaStreamWaitEvent(s, ev_bulk, 0);
 }
 
+// ILU(p) factors of level l in T: A's lower triangle into [L | D], the
+// incomplete factorisation by dependency levels, the level-major copies.
+template <typename T>
+void factor_ilu(msp_instance* I, int l, T* fac, cudaStream_t s) {
+  const DevLevel& D = I->h->dev[l];
+  {
+    ProfScope ps(I->prof, PK_EXTRACT, s, 2);
+    launch_ilu_extract<T>(D.ilu_ext_pos, D.ilu_ext_nz, D.ilu_next, I->val[l], D.fac_elems, fac, s);
+    ps.account((double)D.fac_elems * sizeof(T) + (double)D.ilu_next * 20, 0);
+  }
+  ProfScope ps(I->prof, PK_LDLT_BLOCKS, s, 2);
+  launch_ilu_factor<T>(fac, D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.ilu_lptr, D.ilu_lcol, D.ilu_fwd_rows,
+                       D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_max_n, D.ilu_max_row, I->info, s);
+  launch_ilu_gather<T>(fac, D.ilu_nnz, D.ilu_rows, D.ilu_fe_slot, D.ilu_be_slot, s);
+  ps.account((double)D.ilu_nnz * sizeof(T) * 5, D.ilu_flops);
+}
+
 // Enqueues the whole factorisation on the instance stream (with forks onto
 // the auxiliary and bulk streams, all joined back).
 int enqueue_factor(msp_instance* I) {
@@ -589,17 +608,10 @@ int enqueue_factor(msp_instance* I) {
     const Store st = level_store(h, l);
     const DevLevel& D = h->dev[l];
     if (D.ilu) {
-      double* fac = static_cast<double*>(I->fac[l]);
-      {
-        ProfScope ps(I->prof, PK_EXTRACT, s, 2);
-        launch_ilu_extract(D.ilu_ext_pos, D.ilu_ext_nz, D.ilu_next, I->val[l], D.fac_elems, fac, s);
-        ps.account((double)D.fac_elems * 8 + (double)D.ilu_next * 20, 0);
-      }
-      ProfScope ps(I->prof, PK_LDLT_BLOCKS, s, 2);
-      launch_ilu_factor(fac, D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.ilu_lptr, D.ilu_lcol, D.ilu_fwd_rows,
-                        D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_max_n, D.ilu_max_row, I->info, s);
-      launch_ilu_gather(fac, D.ilu_nnz, D.ilu_rows, D.ilu_fe_slot, D.ilu_be_slot, s);
-      ps.account((double)D.ilu_nnz * 8 * 5, D.ilu_flops);
+      if (st == Store::F64)
+        factor_ilu<double>(I, l, static_cast<double*>(I->fac[l]), s);
+      else
+        factor_ilu<float>(I, l, static_cast<float*>(I->fac[l]), s);
     } else if (st == Store::F64) {
       factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
     } else if (st == Store::F32) {
@@ -680,11 +692,18 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   const Store st = level_store(h, l);
   size_t es = store_bytes(st);
   if (D.ilu) {
-    launch_ilu_solve(static_cast<const double*>(I->fac[l]), D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr, D.sub_dofs,
-                     D.sub_own, D.ilu_fe_ptr, D.ilu_fe_src, D.ilu_be_ptr, D.ilu_be_src, D.ilu_fwd_rows,
-                     D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_bwd_rows, D.ilu_bwd_lvl, D.ilu_bwd_loff, D.ilu_max_n,
-                     D.dir_list, D.ndir, t, z, add, s);
-    ps.account(2.0 * (double)D.ilu_nnz * 12 + (double)D.sum_np * 21 + (double)D.sum_owned * (add ? 16 : 8),
+    if (st == Store::F64)
+      launch_ilu_solve<double>(static_cast<const double*>(I->fac[l]), D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr,
+                               D.sub_dofs, D.sub_own, D.ilu_fe_ptr, D.ilu_fe_src, D.ilu_be_ptr, D.ilu_be_src,
+                               D.ilu_fwd_rows, D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_bwd_rows, D.ilu_bwd_lvl,
+                               D.ilu_bwd_loff, D.ilu_max_n, D.dir_list, D.ndir, t, z, add, s);
+    else
+      launch_ilu_solve<float>(static_cast<const float*>(I->fac[l]), D.ilu_nnz, D.ilu_rows, D.nsub, D.sub_ptr,
+                              D.sub_dofs, D.sub_own, D.ilu_fe_ptr, D.ilu_fe_src, D.ilu_be_ptr, D.ilu_be_src,
+                              D.ilu_fwd_rows, D.ilu_fwd_lvl, D.ilu_fwd_loff, D.ilu_bwd_rows, D.ilu_bwd_lvl,
+                              D.ilu_bwd_loff, D.ilu_max_n, D.dir_list, D.ndir, t, z, add, s);
+    ps.account(2.0 * (double)D.ilu_nnz * (es + 4) + (double)D.sum_np * (13 + es) +
+                   (double)D.sum_owned * (add ? 16 : 8),
                4.0 * (double)D.ilu_nnz + (double)D.sum_np);
     return;
   }
@@ -1393,9 +1412,10 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
     bytes = (size_t)D.nnz * sizeof(double);
   } else if (what == MSP_ARR_ILU_VAL || what == MSP_ARR_ILU_D) {
     if (!D.ilu) return fail(MSP_ERR_INVALID, "level has no ILU factors");
-    const double* f = static_cast<const double*>(I->fac[level]);
-    src = what == MSP_ARR_ILU_VAL ? f : f + D.ilu_nnz;
-    bytes = (size_t)(what == MSP_ARR_ILU_VAL ? D.ilu_nnz : D.ilu_rows) * sizeof(double);
+    const size_t es = store_bytes(level_store(h, level));  // double, or float for reduced precision
+    const char* f = static_cast<const char*>(I->fac[level]);
+    src = what == MSP_ARR_ILU_VAL ? f : f + (size_t)D.ilu_nnz * es;
+    bytes = (size_t)(what == MSP_ARR_ILU_VAL ? D.ilu_nnz : D.ilu_rows) * es;
   } else if (what == MSP_ARR_FACTOR && D.ilu) {
     return fail(MSP_ERR_INVALID, "ILU level: read MSP_ARR_ILU_VAL / MSP_ARR_ILU_D");
   } else if (what == MSP_ARR_FACTOR) {

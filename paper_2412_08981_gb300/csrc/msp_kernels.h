@@ -80,11 +80,6 @@ template <typename T>
 void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
                                 const int32_t* dofs, int max_nt, const int32_t* dir_list,
                                 int ndir, const double* t, double* z, int add, cudaStream_t s);
-// z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
-// entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
-// CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
-// longest-first balanced assignment built on the host); a bounded mbarrier
-// wait that expires sets bit 4 of *err.  The factor tiles stream through
 // Persistent factorisation of the blocks of a level whose factors are stored
 // in BF16: FP32 diagonal tiles and panels, trailing updates on the tensor
 // cores (BF16 operands, FP32 accumulation), fac = the FP32 working envelope.
@@ -92,18 +87,23 @@ void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, 
                            int grid, int* info, cudaStream_t s);
 int ldlt_blocks_tc_per_sm();
 // ---- ILU(p) subdomain factors (k_ilu.cu); fac = [L (nnz) | D (rows) | 1/D (rows)]
-size_t ilu_factor_smem(int max_n, int max_row);  // max_row: most strictly-lower entries of a row
-size_t ilu_solve_smem(int max_n);
+// of T = double or float (factorisation and sweeps in T).  es = sizeof(T).
+size_t ilu_factor_smem(int max_n, int max_row, size_t es);  // max_row: most strictly-lower entries of a row
+size_t ilu_solve_smem(int max_n, size_t es);
+template <typename T>
 void launch_ilu_extract(const int64_t* pos, const int32_t* nz, int64_t nent, const double* val, int64_t total,
-                        double* fac, cudaStream_t s);
-void launch_ilu_factor(double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
+                        T* fac, cudaStream_t s);
+template <typename T>
+void launch_ilu_factor(T* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
                        const int64_t* lptr, const int32_t* lcol, const int32_t* fwd_rows,
                        const int32_t* fwd_lvl, const int32_t* fwd_loff, int max_n, int max_row, int* info,
                        cudaStream_t s);
 // fac = [L | D | 1/D | Lf | Lb]: Lf, Lb the level-major copies (launch_ilu_gather)
-void launch_ilu_gather(double* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,
+template <typename T>
+void launch_ilu_gather(T* fac, int64_t nnz, int64_t rows, const int64_t* fe_slot, const int64_t* be_slot,
                        cudaStream_t s);
-void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
+template <typename T>
+void launch_ilu_solve(const T* fac, int64_t nnz, int64_t rows, int nsub, const int32_t* sub_ptr,
                       const int32_t* dofs, const uint8_t* own, const int64_t* fe_ptr, const int32_t* fe_src,
                       const int64_t* be_ptr, const int32_t* be_src, const int32_t* fwd_rows,
                       const int32_t* fwd_lvl, const int32_t* fwd_loff, const int32_t* bwd_rows,
@@ -112,6 +112,11 @@ void launch_ilu_solve(const double* fac, int64_t nnz, int64_t rows, int nsub, co
 // BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
 // n a multiple of 4.
 void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);
+// z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
+// entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
+// CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
+// longest-first balanced assignment built on the host); a bounded mbarrier
+// wait that expires sets bit 4 of *err.  The factor tiles stream through
 // ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
 // diagonal tile while it reads that tile column, so there must be at least
 // 1 + (R_I - I) slots for every row I of the level (checked on the host at

@@ -451,6 +451,52 @@ def test_ilu_subdomain_solver(P, orc, torch, name, ilu):
     assert rel(x.cpu().numpy(), xo) <= 1e-7
 
 
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_ilu_fp32_factors(P, orc, torch, precision):
+    """ILU(2)/ILU(0) factors computed and applied in FP32 (both reduced
+    precisions store ILU levels in FP32) under the FP64 outer loop: the
+    factors agree with the oracle's FP64 ILU at single-precision level, one
+    RAS application too, and FGMRES reaches the FP64 oracle's solution."""
+    levels, w = workload("cube16_3lvl")
+    ilu = (2, 0)
+    mu = syn.mu_draw(9)
+    o = make_oracle(levels, w, orc, ilu=ilu)
+    o.assemble(mu)
+    o.factor()
+    h = make_hierarchy(levels, w, P, ilu=ilu, precision=precision)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    ptr, sptr = h.array(0, "ilu_ptr"), h.array(0, "sub_ptr")
+    Lg = inst.array(0, "ilu_val", dtype=np.float32).astype(np.float64)
+    Dg = inst.array(0, "ilu_d", dtype=np.float32).astype(np.float64)
+    assert Lg.size == ptr[-1] and Dg.size == sptr[-1]
+    for p in (0, o.get("n_subs", 0) - 1):
+        fp, fc, fv = (o.get(k, 0, p) for k in ("sub_ilu_ptr", "sub_ilu_col", "sub_ilu_val"))
+        lo, lg, do, dg = [], [], [], []
+        for i in range(fp.size - 1):
+            c, v = fc[fp[i]:fp[i + 1]], fv[fp[i]:fp[i + 1]]
+            R = sptr[p] + i
+            lo.append(v[c < i])
+            lg.append(Lg[ptr[R]:ptr[R + 1]])
+            do.append(v[c == i][0])
+            dg.append(Dg[R])
+        lo, lg = np.concatenate(lo), np.concatenate(lg)
+        assert 1e-12 < rel(lg, lo) < 1e-4
+        assert rel(np.array(dg), np.array(do)) < 1e-5
+    r = np.random.default_rng(12).normal(size=levels[0].n_nodes)
+    z = torch.zeros(levels[0].n_nodes, dtype=torch.float64, device="cuda")
+    inst.apply_op(P.msp.MSP_OP_RAS, 0, torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    d = rel(z.cpu().numpy(), o.ras_apply(r, 0))
+    assert 1e-10 < d < 1e-4, d
+    xo, so = o.fgmres(rtol=1e-10, restart=w["restart"])
+    x = torch.zeros_like(z)
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and so["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= so["iters"] + 3
+
+
 # ------------------------------------------- paper-literal Algorithm 2 options
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_paper_literal_algorithm2(P, orc, torch, precision):

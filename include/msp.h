@@ -124,7 +124,9 @@ typedef struct msp_options {
   int32_t ilu_fill_fine;      /* subdomain solver of level 0: -1 (default) the exact LU of the
                                  block (dense tile envelope); p >= 0 ILU(p), the incomplete LU
                                  with the level-of-fill pattern (Section 4.4 uses ILU(2)) */
-  int32_t ilu_fill_coarse;    /* the same for the smoothed levels 1.. (Section 4.4: ILU(0)) */
+  int32_t ilu_fill_coarse;    /* the same for the smoothed levels 1.. (Section 4.4: ILU(0)).
+                                 ILU levels factor and sweep in FP64 with MSP_F64, in FP32
+                                 with MSP_F32 or MSP_BF16; the coarsest level stays direct */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
@@ -303,8 +305,9 @@ MSP_API int msp_apply_op(msp_instance* inst, int op, int level, const double* x_
  * ILU(p) levels (msp_options.ilu_fill_*): MSP_ARR_ILU_PTR (int64, rows + 1)
  *   and MSP_ARR_ILU_COL (int32 local columns) give the strict lower pattern
  *   of every block, row R = sub_ptr[p] + i for local row i of subdomain p;
- *   MSP_ARR_ILU_VAL (double, the unit lower L on that pattern) and
- *   MSP_ARR_ILU_D (double, one per row) are the instance's factors, U = D L^T.
+ *   MSP_ARR_ILU_VAL (the unit lower L on that pattern) and MSP_ARR_ILU_D
+ *   (one per row) are the instance's factors, U = D L^T: double with
+ *   MSP_F64, float with MSP_F32 or MSP_BF16 (ILU levels are never BF16).
  * bytes_out receives the array size; with dst == NULL only the size is
  * returned.  MSP_ERR_INVALID if cap is too small. */
 typedef enum msp_array {

@@ -771,7 +771,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   constexpr uint32_t kTileBytes = TE * sizeof(T);
   constexpr int NC = kConsumers * 32;       // consumer threads
   constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
-  constexpr int NP = NC / 64;               // column parts of the forward diagonal product
+  constexpr int NPASS = RW / 4;             // 4-row passes of a warp (8 lanes per row)
+  constexpr int CH = kConsumers / 8;        // column halves of the column-wise products (1 or 2)
+  constexpr int NB = 2 / CH;                // 32-column sets per lane in those products
+  static_assert(RW % 4 == 0 && (CH == 1 || CH == 2), "8 or 16 consumer warps");
   extern __shared__ __align__(128) unsigned char smraw[];
   T* ring = reinterpret_cast<T*>(smraw);                                        // [nslot][TE]
   uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)nslot * kTileBytes);  // [nslot]
@@ -786,6 +789,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   __shared__ int sflag;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  const int rl = lane >> 3, g = lane & 7;            // row within a 4-row pass, lane within the row
+  const int hh = warp % CH, rb = warp / CH;          // column half and 8-row block of the column-wise products
   const int G = gridDim.x;
   if (tid == 0) {
     sflag = 0;
@@ -858,57 +863,67 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     consumers_sync<kConsumers>();
     // forward sweep
     for (int I = 0; I < NT; ++I) {
-      AT sr[RW];
+      // off-diagonal tiles: lane (rl, g) of a warp takes row warp*RW + 4*ps + rl
+      // of pass ps and the columns 8*((c + rl) & 7) + g, c = 0..7 (the four
+      // rows of an access read four different 8-column chunks, so the loads
+      // spread over all banks); two FMA chains per row, 8 partials per row
+      AT se[NPASS], so[NPASS];
 #pragma unroll
-      for (int k = 0; k < RW; ++k) sr[k] = 0;
+      for (int k = 0; k < NPASS; ++k) se[k] = so[k] = 0;
       for (int J = cm.first[I]; J < I; ++J) {
         const T* tl = acquire();
-        const AT y0 = y[J * 64 + lane], y1 = y[J * 64 + lane + 32];
-        AT a0[RW], a1[RW];
+        const AT* yJ = y + J * 64;
 #pragma unroll
-        for (int k = 0; k < RW; ++k) {
-          const int r = warp * RW + k;
-          a0[k] = (AT)tl[r * 64 + lane];
-          a1[k] = (AT)tl[r * 64 + lane + 32];
+        for (int ps = 0; ps < NPASS; ++ps) {
+          const T* trow = tl + (warp * RW + 4 * ps + rl) * 64;
+#pragma unroll
+          for (int c = 0; c < 8; c += 2) {
+            const int c0 = 8 * ((c + rl) & 7) + g, c1 = 8 * ((c + 1 + rl) & 7) + g;
+            se[ps] = fma((AT)trow[c0], yJ[c0], se[ps]);
+            so[ps] = fma((AT)trow[c1], yJ[c1], so[ps]);
+          }
         }
-#pragma unroll
-        for (int k = 0; k < RW; ++k) sr[k] = fma(a1[k], y1, fma(a0[k], y0, sr[k]));
         release();
       }
-      // row sums: one thread per row adds the 32 lane partials (a shared-memory
+      // row sums: one thread per row adds the 8 lane partials (a shared-memory
       // transpose costs far fewer FP64 instructions than warp shuffles)
 #pragma unroll
-      for (int k = 0; k < RW; ++k) red[(warp * RW + k) * 33 + lane] = sr[k];
+      for (int ps = 0; ps < NPASS; ++ps) red[(warp * RW + 4 * ps + rl) * 9 + g] = se[ps] + so[ps];
       consumers_sync<kConsumers>();
       if (tid < 64) {
-        AT v0 = 0, v1 = 0;
-#pragma unroll
-        for (int l = 0; l < 32; l += 2) {
-          v0 += red[tid * 33 + l];
-          v1 += red[tid * 33 + l + 1];
-        }
+        const AT* rr = red + tid * 9;
+        const AT v0 = (rr[0] + rr[2]) + (rr[4] + rr[6]), v1 = (rr[1] + rr[3]) + (rr[5] + rr[7]);
         acc[tid] = y[I * 64 + tid] - (v0 + v1);
       }
       consumers_sync<kConsumers>();
-      {  // y_I = X acc, X[b][a] = tile[a][b] for a < b
+      {  // y_I = X acc, X[b][a] = tile[a][b] for a < b: warp (rb, h) takes rows
+         // a = 8 rb .. 8 rb + 7 and its columns b; (row, column set) pairs with
+         // no a < b are skipped by the whole warp
         const T* dt = acquire();
-        const int bcol = tid & 63, pr = tid >> 6;
-        constexpr int AW = 64 / NP;  // rows a of each part
-        AT v = 0, v2 = 0;            // two independent chains
+        AT v[NB];
 #pragma unroll
-        for (int a = pr * AW; a < pr * AW + AW; a += 2) {
-          if (a < bcol) v = fma((AT)dt[a * 64 + bcol], acc[a], v);
-          if (a + 1 < bcol) v2 = fma((AT)dt[(a + 1) * 64 + bcol], acc[a + 1], v2);
+        for (int q = 0; q < NB; ++q) v[q] = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int a = rb * 8 + k;
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const int b0 = (CH == 2 ? 32 * hh : 32 * q);
+            if (a < b0 + 31) {
+              const int b = b0 + lane;
+              if (a < b) v[q] = fma((AT)dt[a * 64 + b], acc[a], v[q]);
+            }
+          }
         }
-        part[pr * 64 + bcol] = v + v2;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = v[q];
         release();
       }
       consumers_sync<kConsumers>();
       if (tid < 64) {
-        AT v = acc[tid];
-#pragma unroll
-        for (int q2 = 0; q2 < NP; ++q2) v += part[q2 * 64 + tid];
-        y[I * 64 + tid] = v;
+        const AT v0 = (part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid]);
+        const AT v1 = (part[64 + tid] + part[192 + tid]) + (part[320 + tid] + part[448 + tid]);
+        y[I * 64 + tid] = acc[tid] + (v0 + v1);
       }
       consumers_sync<kConsumers>();
     }
@@ -917,53 +932,59 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       const T* dt = acquire();  // held until the end of the row
       const long dseq = seq;
       ++seq;
-      AT s0 = 0, s1 = 0;
+      // off-diagonal tiles (transposed): warp (rb, h) takes rows 8 rb .. 8 rb + 7
+      // of L_JI and its columns; 8 partials per column
+      AT s[NB][2];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) s[q][0] = s[q][1] = 0;
       for (int J = I + 1; J <= cm.last[I]; ++J) {
         const T* tl = acquire();
-        AT a0[RW], a1[RW], xr[RW];
 #pragma unroll
-        for (int k = 0; k < RW; ++k) {
-          const int r = warp * RW + k;
-          xr[k] = y[J * 64 + r];
-          a0[k] = (AT)tl[r * 64 + lane];
-          a1[k] = (AT)tl[r * 64 + lane + 32];
-        }
+        for (int k = 0; k < 8; ++k) {
+          const int r = rb * 8 + k;
+          const AT xr = y[J * 64 + r];
 #pragma unroll
-        for (int k = 0; k < RW; ++k) {
-          s0 = fma(a0[k], xr[k], s0);
-          s1 = fma(a1[k], xr[k], s1);
+          for (int q = 0; q < NB; ++q)
+            s[q][k & 1] = fma((AT)tl[r * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane], xr, s[q][k & 1]);
         }
         release();
       }
-      part[warp * 64 + lane] = s0;
-      part[warp * 64 + lane + 32] = s1;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = s[q][0] + s[q][1];
       consumers_sync<kConsumers>();
       if (tid < 64) {
-        AT v = 0;
-#pragma unroll
-        for (int w = 0; w < kConsumers; ++w) v += part[w * 64 + tid];
-        acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - v;
+        const AT v0 = (part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid]);
+        const AT v1 = (part[64 + tid] + part[192 + tid]) + (part[320 + tid] + part[448 + tid]);
+        acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - (v0 + v1);
       }
       consumers_sync<kConsumers>();
-      // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]
+      // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]: lane (rl, g) takes row
+      // a = warp*RW + 4*ps + rl and the columns 8c + g; chunks c with no b > a
+      // for the pass's four rows are skipped by the whole warp
 #pragma unroll
-      for (int k = 0; k < RW; ++k) {
-        const int a = warp * RW + k;
-        AT v = 0;
-        if (lane > a) v = fma((AT)dt[a * 64 + lane], acc[lane], v);
-        if (lane + 32 > a) v = fma((AT)dt[a * 64 + lane + 32], acc[lane + 32], v);
-        red[a * 33 + lane] = v;
+      for (int ps = 0; ps < NPASS; ++ps) {
+        const int amin = warp * RW + 4 * ps, a = amin + rl;
+        AT e0 = 0, e1 = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (8 * c + 7 > amin) {
+            const int b = 8 * c + g;
+            if (b > a) {
+              if (c & 1)
+                e1 = fma((AT)dt[a * 64 + b], acc[b], e1);
+              else
+                e0 = fma((AT)dt[a * 64 + b], acc[b], e0);
+            }
+          }
+        }
+        red[a * 9 + g] = e0 + e1;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
       consumers_sync<kConsumers>();
       if (tid < 64) {
-        AT v0 = 0, v1 = 0;
-#pragma unroll
-        for (int l = 0; l < 32; l += 2) {
-          v0 += red[tid * 33 + l];
-          v1 += red[tid * 33 + l + 1];
-        }
+        const AT* rr = red + tid * 9;
+        const AT v0 = (rr[0] + rr[2]) + (rr[4] + rr[6]), v1 = (rr[1] + rr[3]) + (rr[5] + rr[7]);
         y[I * 64 + tid] = acc[tid] + (v0 + v1);
       }
       consumers_sync<kConsumers>();

@@ -579,26 +579,29 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def kernel_source_hash():
+def kernel_source_hash(name):
+    """Hash of the CUDA source file that holds a kernel class."""
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2412_08981_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.startswith("k_") and f.endswith(".cu"):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2412_08981_gb300", "csrc", name), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel, prof):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    sources are unchanged since it was taken (else null)."""
+    """DRAM bytes per launch from the committed ncu summary, if the source
+    file of the kernel is unchanged since it was taken (else null)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
     e = t.get(kernel)
-    if not e or e.get("kernel_sources") != kernel_source_hash():
+    if not e or "kernel_file" not in e:
+        return None
+    try:
+        if e.get("source_hash") != kernel_source_hash(e["kernel_file"]):
+            return None
+    except OSError:
         return None
     return e.get("bytes_per_launch")
 

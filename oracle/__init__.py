@@ -25,11 +25,19 @@ Parity status per function (what pins it, tests/test_oracle_pins.py):
                      also with the coarsest level RAS-smoothed and for the
                      one-level RAS preconditioner (tests/test_oracle_alg2_pins.py)
   FGMRES             Krylov least-squares optimality (M = I), direct solve
+  elasticity         (three displacement fields per vertex) element stiffness
+                     against an independent Voigt B^T D B construction, rigid
+                     modes, rank and the energy of linear fields; patch test
+                     and rigid modes of the assembled operator; Dirichlet rows
+                     and body-force load; O(h^2) convergence to a manufactured
+                     solution; field-split transfers reproduce affine vector
+                     fields; RAS, V-cycle and FGMRES against dense compositions
+                     (tests/test_oracle_elasticity_pins.py)
 Iteration counts of the preconditioned solver: parity unpinned (the paper
 reports counts only for other PDEs and meshes).
 """
-from .oracle import (Oracle, build, lib, tet_stiffness, lu_factor, lu_solve, build_interp,
-                     build_mls, mesh_h, ilu_factor)
+from .oracle import (Oracle, build, lib, tet_stiffness, tet_elasticity, lame, lu_factor, lu_solve,
+                     build_interp, build_mls, mesh_h, ilu_factor)
 
-__all__ = ["Oracle", "build", "lib", "tet_stiffness", "lu_factor", "lu_solve", "build_interp",
-           "build_mls", "mesh_h", "ilu_factor"]
+__all__ = ["Oracle", "build", "lib", "tet_stiffness", "tet_elasticity", "lame", "lu_factor", "lu_solve",
+           "build_interp", "build_mls", "mesh_h", "ilu_factor"]

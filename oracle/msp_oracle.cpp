@@ -7,7 +7,11 @@
 //
 // Every function follows the paper's statement step by step, in its order:
 //   * discretisation J u = b of a linear PDE on a mesh (Section 2.1, Eq. 2-4),
-//     realised as P1 finite elements for -div(k(x;mu) grad u) = f;
+//     realised as P1 finite elements for -div(k(x;mu) grad u) = f, or, as the
+//     multi-field case of the mesh perspective (Section 2.1: DoF distribution
+//     N = (3,0,0,0), three displacement fields per vertex), for linear
+//     elasticity -div sigma(u) = f with sigma = k(x;mu) (2 mu_L eps(u) +
+//     lambda_L tr(eps(u)) I), Lame parameters of a unit Young's modulus;
 //   * one-level restricted additive Schwarz (Section 2.2, Eq. 6-8);
 //   * the V-cycle of Algorithm 2 (Section 3.3), with the readings listed below;
 //   * right-preconditioned (flexible) GMRES (Section 2.1, Eq. 5; Section 4).
@@ -23,7 +27,11 @@
 //   * the smoothing loops of Algorithm 2 run exactly `its` times;
 //   * subdomain solvers are unpivoted LU of each (SPD) subdomain block;
 //   * Dirichlet rows are identity rows, Dirichlet columns are zeroed;
-//   * k(x;mu) is evaluated at the tet centroid, f at the vertices (vertex rule).
+//   * k(x;mu) is evaluated at the tet centroid, f at the vertices (vertex rule);
+//   * with several fields, DoF 3v + c is field c at vertex v; a Dirichlet
+//     vertex fixes all its fields; the transfers are split by field (the
+//     field-splitting interpolation I = sum_f R_f^T I_f R~_f of Section 2.1
+//     with the scalar P for every field: P (x) I_3).
 // Compiled with -O2 -ffp-contract=off, OpenMP over subdomains and rows only.
 #include <algorithm>
 #include <climits>
@@ -51,11 +59,13 @@ struct Subdomain {
 };
 
 struct Level {
-  int n = 0, m = 0;
+  int n = 0, m = 0;  // DoFs (fields x vertices) and tets
+  int nv = 0;        // vertices
   std::vector<double> xyz;
   std::vector<int> tets;
-  std::vector<unsigned char> dir;
-  std::vector<int> owner;
+  std::vector<unsigned char> vdir;  // per vertex
+  std::vector<unsigned char> dir;   // per DoF
+  std::vector<int> owner;           // per DoF (the owner of its vertex)
   Csr A;                  // assembled operator (pattern + values)
   std::vector<double> b;  // load vector
   std::vector<Subdomain> subs;
@@ -67,6 +77,8 @@ struct Level {
 
 struct Oracle {
   std::vector<Level> lv;
+  int fields = 1;                     // DoFs per vertex: 1 (scalar) or 3 (elasticity)
+  double lame_l = 0.0, lame_m = 0.0;  // Lame parameters of the unit-modulus material
   int delta = 1, nu_pre = 2, nu_post = 2;
   int coef_kind = 0;  // 0: k = 1; 1: exp(s * sum_j mu_j * 0.5 * cos(pi a_j . x))
   int wave[24] = {0};
@@ -130,19 +142,59 @@ double load_f(const Oracle& o, const double* x) {
   return 3.0 * kPi * kPi * std::sin(kPi * x[0]) * std::sin(kPi * x[1]) * std::sin(kPi * x[2]);
 }
 
+// Body force of the elasticity problem, component c.  Load 0: unit force
+// along -z.  Load 1: the force for which u = (s, s, s), s = sin(pi x)
+// sin(pi y) sin(pi z), solves -div sigma(u) = f with k = 1:
+// div sigma = mu_L lap u + (lambda_L + mu_L) grad div u, lap s = -3 pi^2 s,
+// d_c d_c s = -pi^2 s, d_c d_d s = pi^2 cos(pi x_c) cos(pi x_d) sin(pi x_e).
+double load_elastic(const Oracle& o, const double* x, int c) {
+  if (o.load_kind == 0) return c == 2 ? -1.0 : 0.0;
+  double S[3], Cs[3];
+  for (int d = 0; d < 3; ++d) {
+    S[d] = std::sin(kPi * x[d]);
+    Cs[d] = std::cos(kPi * x[d]);
+  }
+  const double s = S[0] * S[1] * S[2];
+  double graddiv = -kPi * kPi * s;  // d_c d_c s
+  for (int d = 0; d < 3; ++d)
+    if (d != c) {
+      const int e = 3 - c - d;
+      graddiv += kPi * kPi * Cs[c] * Cs[d] * S[e];
+    }
+  return 3.0 * kPi * kPi * o.lame_m * s - (o.lame_l + o.lame_m) * graddiv;
+}
+
+// Element stiffness of linear elasticity for P1 displacements (unit k):
+// K[(a,i),(b,j)] = |T| (lambda g_a[i] g_b[j] + mu g_a[j] g_b[i] + mu delta_ij g_a.g_b),
+// the bilinear form int 2 mu eps(u):eps(v) + lambda div u div v with u = phi_b e_j,
+// v = phi_a e_i.  K12 is row-major 12 x 12, row 3a+i, column 3b+j.
+void elastic_element(const double g[4][3], double vol, double lam, double mu, double* K12) {
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int b = 0; b < 4; ++b)
+        for (int j = 0; j < 3; ++j) {
+          double v = lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i];
+          if (i == j) v += mu * dot3(g[a], g[b]);
+          K12[(3 * a + i) * 12 + 3 * b + j] = vol * v;
+        }
+}
+
 // ------------------------------------------------------------- CSR pattern
-// Row i: the sorted distinct vertices that share a tet with i (i included).
-void build_pattern(Level& L) {
-  std::vector<std::set<int>> nb(L.n);
+// Row i: the sorted distinct vertices that share a tet with i (i included);
+// with F fields, row F v + c holds the F DoFs of each of those vertices.
+void build_pattern(Level& L, int F) {
+  std::vector<std::set<int>> nb(L.nv);
   for (int e = 0; e < L.m; ++e)
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) nb[L.tets[4 * e + a]].insert(L.tets[4 * e + b]);
   L.A.rowptr.assign(L.n + 1, 0);
   L.A.col.clear();
-  for (int i = 0; i < L.n; ++i) {
-    for (int j : nb[i]) L.A.col.push_back(j);
-    L.A.rowptr[i + 1] = (int)L.A.col.size();
-  }
+  for (int v = 0; v < L.nv; ++v)
+    for (int c = 0; c < F; ++c) {
+      for (int w : nb[v])
+        for (int c2 = 0; c2 < F; ++c2) L.A.col.push_back(F * w + c2);
+      L.A.rowptr[F * v + c + 1] = (int)L.A.col.size();
+    }
   L.A.val.assign(L.A.col.size(), 0.0);
 }
 
@@ -173,6 +225,20 @@ int assemble_level(const Oracle& o, Level& L) {
     double xc[3];
     for (int d = 0; d < 3; ++d) xc[d] = (x[0][d] + x[1][d] + x[2][d] + x[3][d]) / 4.0;
     double k = coefficient(o, xc);
+    if (o.fields == 3) {  // linear elasticity, three displacement fields
+      double K12[144];
+      elastic_element(g, vol, o.lame_l, o.lame_m, K12);
+      for (int a = 0; a < 4; ++a) {
+        for (int i = 0; i < 3; ++i)
+          for (int b = 0; b < 4; ++b)
+            for (int j = 0; j < 3; ++j) {
+              long nz = csr_find(L.A, 3 * t[a] + i, 3 * t[b] + j);
+              L.A.val[nz] += k * K12[(3 * a + i) * 12 + 3 * b + j];
+            }
+        for (int c = 0; c < 3; ++c) L.b[3 * t[a] + c] += load_elastic(o, x[a], c) * vol / 4.0;
+      }
+      continue;
+    }
     for (int a = 0; a < 4; ++a) {
       for (int b = 0; b < 4; ++b) {
         long nz = csr_find(L.A, t[a], t[b]);
@@ -870,11 +936,21 @@ typedef struct {
   const int* owner;  // may be NULL on the coarsest level
 } orc_level;
 
+// pde: 0 scalar P1 (one field), 1 linear elasticity (three fields, Poisson
+// ratio `poisson` in (0, 0.5), unit Young's modulus scaled by k(x;mu)).
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
                  int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
-                 int restrict_scaling, int coarse_ras, int ilu_fine, int ilu_coarse) {
-  if (nlevels < 1 || transfer < 0 || transfer > 1) return nullptr;
+                 int restrict_scaling, int coarse_ras, int ilu_fine, int ilu_coarse, int pde,
+                 double poisson) {
+  if (nlevels < 1 || transfer < 0 || transfer > 1 || pde < 0 || pde > 1) return nullptr;
+  if (pde == 1 && (transfer != 0 || !(poisson > 0.0 && poisson < 0.5))) return nullptr;
   Oracle* o = new Oracle();
+  if (pde == 1) {
+    o->fields = 3;
+    o->lame_l = poisson / ((1.0 + poisson) * (1.0 - 2.0 * poisson));
+    o->lame_m = 1.0 / (2.0 * (1.0 + poisson));
+  }
+  const int NF = o->fields;
   o->coarse_ras = coarse_ras ? 1 : 0;
   o->transfer = transfer;
   o->restrict_scaling = restrict_scaling ? 1 : 0;
@@ -889,13 +965,19 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
   for (int l = 0; l < nlevels; ++l) {
     Level& L = o->lv[l];
     L.ilu_fill = (l == 0) ? ilu_fine : ilu_coarse;
-    L.n = lv[l].n_nodes;
+    L.nv = lv[l].n_nodes;
+    L.n = NF * L.nv;
     L.m = lv[l].n_tets;
-    L.xyz.assign(lv[l].xyz, lv[l].xyz + 3 * (size_t)L.n);
+    L.xyz.assign(lv[l].xyz, lv[l].xyz + 3 * (size_t)L.nv);
     L.tets.assign(lv[l].tets, lv[l].tets + 4 * (size_t)L.m);
-    L.dir.assign(lv[l].dirichlet, lv[l].dirichlet + L.n);
-    if (lv[l].owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
-    build_pattern(L);
+    L.vdir.assign(lv[l].dirichlet, lv[l].dirichlet + L.nv);
+    L.dir.resize(L.n);
+    for (int i = 0; i < L.n; ++i) L.dir[i] = L.vdir[i / NF];
+    if (lv[l].owner) {
+      L.owner.resize(L.n);
+      for (int i = 0; i < L.n; ++i) L.owner[i] = lv[l].owner[i / NF];
+    }
+    build_pattern(L, NF);
     if (l + 1 < nlevels || o->coarse_ras) {
       if (L.owner.empty()) {
         delete o;
@@ -916,8 +998,21 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
         return nullptr;
       }
     } else {
-      build_interp(C.n, C.xyz.data(), C.m, C.tets.data(), C.dir.data(), F.n, F.xyz.data(),
-                   F.dir.data(), 1, F.P);
+      Csr Pv;  // the scalar interpolation between the vertex sets
+      build_interp(C.nv, C.xyz.data(), C.m, C.tets.data(), C.vdir.data(), F.nv, F.xyz.data(),
+                   F.vdir.data(), 1, Pv);
+      // one copy per field: P = Pv (x) I_F in the interleaved DoF numbering
+      const int nf = o->fields;
+      F.P = Csr();
+      F.P.rowptr.assign(F.n + 1, 0);
+      for (int i = 0; i < F.nv; ++i)
+        for (int c = 0; c < nf; ++c) {
+          for (int q = Pv.rowptr[i]; q < Pv.rowptr[i + 1]; ++q) {
+            F.P.col.push_back(nf * Pv.col[q] + c);
+            F.P.val.push_back(Pv.val[q]);
+          }
+          F.P.rowptr[nf * i + c + 1] = (int)F.P.col.size();
+        }
       transpose(F.P, C.n, F.PT);
     }
   }
@@ -1077,6 +1172,17 @@ double orc_tet_stiffness(const double* x4, double k, double* K16) {
   return vol;
 }
 
+// Element stiffness of linear elasticity (12 x 12, row-major, row 3a+i,
+// column 3b+j) for Lame parameters lam, mu and coefficient k; returns |T|.
+double orc_tet_elasticity(const double* x4, double k, double lam, double mu, double* K144) {
+  double g[4][3];
+  double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);
+  double vol = std::fabs(det) / 6.0;
+  elastic_element(g, vol, lam, mu, K144);
+  for (int e = 0; e < 144; ++e) K144[e] *= k;
+  return vol;
+}
+
 int orc_lu_factor(int n, double* A) { return lu_factor(n, A); }
 void orc_lu_solve(int n, const double* LU, double* x) { lu_solve(n, LU, x); }
 
@@ -1103,13 +1209,14 @@ long orc_build_mls(const orc_level* src, const orc_level* dst, double h, int del
   Level M[2];
   const orc_level* d[2] = {src, dst};
   for (int k = 0; k < 2; ++k) {
-    M[k].n = d[k]->n_nodes;
+    M[k].n = M[k].nv = d[k]->n_nodes;
     M[k].m = d[k]->n_tets;
     M[k].xyz.assign(d[k]->xyz, d[k]->xyz + 3 * (size_t)M[k].n);
     M[k].tets.assign(d[k]->tets, d[k]->tets + 4 * (size_t)M[k].m);
     M[k].dir.assign(d[k]->dirichlet, d[k]->dirichlet + M[k].n);
+    M[k].vdir = M[k].dir;
     if (d[k]->owner) M[k].owner.assign(d[k]->owner, d[k]->owner + M[k].n);
-    build_pattern(M[k]);
+    build_pattern(M[k], 1);
   }
   if (!(h > 0)) h = mesh_h(M[0].m <= M[1].m ? M[0] : M[1]);
   Csr R;

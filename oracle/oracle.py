@@ -39,7 +39,8 @@ def lib():
             L = C.CDLL(build())
             vp, ip, dp = C.c_void_p, C.c_int, C.c_double
             L.orc_create.restype = vp
-            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip, ip, ip, ip]
+            L.orc_create.argtypes = [C.POINTER(_Level), ip, ip, ip, ip, ip, vp, dp, ip, ip, ip, ip, ip, ip,
+                                     ip, dp]
             L.orc_destroy.argtypes = [vp]
             for name in ("orc_assemble",):
                 getattr(L, name).argtypes = [vp, vp]
@@ -57,6 +58,8 @@ def lib():
             L.orc_get.argtypes = [vp, C.c_char_p, ip, ip, C.POINTER(C.c_void_p)]
             L.orc_tet_stiffness.restype = dp
             L.orc_tet_stiffness.argtypes = [vp, dp, vp]
+            L.orc_tet_elasticity.restype = dp
+            L.orc_tet_elasticity.argtypes = [vp, dp, dp, dp, vp]
             L.orc_lu_factor.argtypes = [ip, vp]
             L.orc_lu_solve.argtypes = [ip, vp, vp]
             L.orc_build_interp.restype = C.c_long
@@ -87,6 +90,23 @@ def _p(a):
 _COEF = {"const": 0, "cosexp": 1}
 _LOAD = {"one": 0, "sines": 1}
 _TRANSFER = {"bary": 0, "mls": 1}
+_PDE = {"poisson": 0, "elasticity": 1}
+
+
+def lame(poisson):
+    """Lame parameters (lambda, mu) of a unit Young's modulus."""
+    nu = float(poisson)
+    return nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), 1.0 / (2.0 * (1.0 + nu))
+
+
+def tet_elasticity(x4, k=1.0, poisson=0.3):
+    """12 x 12 element stiffness of linear elasticity (row 3a+i, column 3b+j)
+    and the tet volume."""
+    lam, mu = lame(poisson)
+    x = np.ascontiguousarray(x4, np.float64).reshape(4, 3)
+    K = np.zeros((12, 12))
+    vol = lib().orc_tet_elasticity(x.ctypes.data, float(k), lam, mu, K.ctypes.data)
+    return K, vol
 
 
 class Oracle:
@@ -94,7 +114,7 @@ class Oracle:
 
     def __init__(self, levels, delta=1, nu_pre=2, nu_post=2, coef="const", wave=None,
                  scale=1.0, load="one", transfer="bary", restrict_scaling=True, coarse="direct",
-                 ilu=None):
+                 ilu=None, pde="poisson", poisson=0.3):
         L = lib()
         self._keep = []
         arr = (_Level * len(levels))()
@@ -111,11 +131,13 @@ class Oracle:
                               _COEF[coef], _p(w), float(scale), _LOAD[load],
                               _TRANSFER[transfer], 1 if restrict_scaling else 0,
                               {"direct": 0, "ras": 1}[coarse],
-                              -1 if ilu is None else int(ilu[0]), -1 if ilu is None else int(ilu[1]))
+                              -1 if ilu is None else int(ilu[0]), -1 if ilu is None else int(ilu[1]),
+                              _PDE[pde], float(poisson))
         if not self.h:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels
-        self.n = [lv.n_nodes for lv in levels]
+        self.fields = 3 if pde == "elasticity" else 1
+        self.n = [self.fields * lv.n_nodes for lv in levels]  # DoFs per level
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -67,13 +67,31 @@ typedef enum msp_coef { MSP_K_CONST = 0, MSP_K_COSEXP = 1 } msp_coef;
 /* Right-hand side f of -div(k grad u) = f, integrated with the vertex rule
  * b_a = sum_{T containing a} f(x_a) |T| / 4 (0 on Dirichlet nodes):
  *   MSP_F_ONE  : f = 1
- *   MSP_F_SINES: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) */
+ *   MSP_F_SINES: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+ * For linear elasticity (MSP_PDE_ELASTICITY), per displacement field c:
+ *   MSP_F_ONE  : f = (0, 0, -1), a unit body force along -z
+ *   MSP_F_SINES: the force whose solution with k = 1 is u = (s, s, s),
+ *                s = sin(pi x) sin(pi y) sin(pi z):
+ *                f_c = 3 pi^2 mu_L s - (lambda_L + mu_L) sum_d d_c d_d s */
 typedef enum msp_load { MSP_F_ONE = 0, MSP_F_SINES = 1 } msp_load;
 
-/* One mesh level (Section 2.1: the mesh perspective M = (K, N) with one DoF
- * per vertex, N = (1,0,0,0)).  All arrays are host memory, copied. */
+/* The PDE and its DoF distribution (Section 2.1, the mesh perspective
+ * M = (K, N)):
+ *   MSP_PDE_POISSON   : -div(k grad u) = f, one DoF per vertex, N = (1,0,0,0);
+ *   MSP_PDE_ELASTICITY: linear elasticity -div sigma(u) = f with
+ *       sigma = k(x; mu) (2 mu_L eps(u) + lambda_L tr(eps(u)) I), the Lame
+ *       parameters of a unit Young's modulus and Poisson ratio
+ *       msp_options.poisson_ratio; three displacement fields per vertex,
+ *       N = (3,0,0,0), DoF 3v + c for field c of vertex v.  A Dirichlet vertex
+ *       fixes its three fields.  The transfers are split by field: P (x) I_3,
+ *       the field-splitting interpolation I = sum_f R_f^T I_f R~_f of
+ *       Section 2.1 with the scalar barycentric P for every field. */
+typedef enum msp_pde { MSP_PDE_POISSON = 0, MSP_PDE_ELASTICITY = 1 } msp_pde;
+
+/* One mesh level (Section 2.1: the mesh perspective M = (K, N); the DoFs
+ * per vertex follow msp_options.pde).  All arrays are host memory, copied. */
 typedef struct msp_level_desc {
-  int32_t n_nodes;            /* number of vertices (= DoFs) */
+  int32_t n_nodes;            /* number of vertices (DoFs: n_nodes x fields) */
   const double* xyz;          /* [n_nodes][3] coordinates */
   int32_t n_tets;             /* number of tetrahedra */
   const int32_t* tets;        /* [n_tets][4] vertex ids, any orientation */
@@ -127,6 +145,9 @@ typedef struct msp_options {
   int32_t ilu_fill_coarse;    /* the same for the smoothed levels 1.. (Section 4.4: ILU(0)).
                                  ILU levels factor and sweep in FP64 with MSP_F64, in FP32
                                  with MSP_F32 or MSP_BF16; the coarsest level stays direct */
+  int32_t pde;                /* msp_pde (default MSP_PDE_POISSON) */
+  double poisson_ratio;       /* MSP_PDE_ELASTICITY: in (0, 0.5), default 0.3; the transfers
+                                 must then be MSP_TRANSFER_BARY */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */
@@ -178,9 +199,10 @@ MSP_API int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_
 MSP_API void msp_free_hierarchy(msp_hierarchy* h);
 
 /* Sizes of level `level`: n_nodes, nnz, number of subdomains (0 on the
- * coarsest level), sum over subdomains of n_p (DoFs), and factor elements. */
+ * coarsest level), sum over subdomains of n_p (DoFs), and factor elements.
+ * Vectors of a level (msp_apply, msp_solve, ...) hold n_dofs entries. */
 typedef struct msp_level_info {
-  int32_t n_nodes, n_tets;
+  int32_t n_nodes, n_tets;    /* vertices and tetrahedra */
   int64_t nnz;
   int32_t n_sub;
   int64_t sub_dofs;           /* sum_p n_p (coarsest: interior DoFs) */
@@ -193,6 +215,7 @@ typedef struct msp_level_info {
   int32_t spmv_lanes[3];      /* lanes per row of the SpMV schedules picked at load time by
                                  timing 4/8/16/32 on the device: J, prolongation, restriction
                                  (0: host-only hierarchy or no such operator) */
+  int32_t n_dofs;             /* DoFs: n_nodes x fields per vertex (msp_options.pde) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);
 
@@ -214,7 +237,7 @@ MSP_API int msp_factor(msp_instance* inst);
 
 /* One application of the V-cycle preconditioner of Algorithm 2 (z = B^{-1} r)
  * with the fine->coarse transfer P^T, coarse->fine P and a direct coarsest
- * solve.  r_dev, z_dev: device arrays of n_nodes(level 0) doubles; they must
+ * solve.  r_dev, z_dev: device arrays of n_dofs(level 0) doubles; they must
  * not overlap.  Requires msp_factor. */
 MSP_API int msp_apply(msp_instance* inst, const double* r_dev, double* z_dev, void* stream);
 
@@ -228,7 +251,7 @@ MSP_API int msp_solve(msp_instance* inst, const double* b_dev, double* x_dev, do
 
 /* The whole per-parameter path from host memory: re-assemble for mu, factor,
  * solve, copy the solution back.  b_host: NULL for the load vector, else
- * n_nodes doubles; x_host: n_nodes doubles. */
+ * n_dofs doubles; x_host: n_dofs doubles. */
 MSP_API int msp_solve_host(msp_instance* inst, const double* mu, int n_mu, const double* b_host,
                    double* x_host, double rtol, msp_stats* st);
 
@@ -267,7 +290,7 @@ MSP_API int msp_submit(msp_server* srv, int hierarchy_id, const double* mu, int 
                        uint64_t* req_id);
 /* Waits up to timeout_ms (0: no wait, < 0: no limit) for a request.
  * Returns MSP_PENDING if it has not finished (the request stays queued);
- * otherwise the request's own status, copies the solution (n_nodes of level
+ * otherwise the request's own status, copies the solution (n_dofs of level
  * 0) into x_host when non-NULL, fills *st (ms_queue / ms_total included) and
  * forgets the request.  MSP_ERR_INVALID for an unknown req_id. */
 MSP_API int msp_poll(msp_server* srv, uint64_t req_id, double* x_host, msp_stats* st, int timeout_ms);

@@ -680,8 +680,8 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
 // cp.async.bulk, each slot guarded by a "full" mbarrier (transaction count)
 // and an "empty" mbarrier (one arrival per consumer warp).  Warps 0-7 are the
 // consumers: gather t[dofs] -> y; forward sweep over tile rows
-// (y_I = X_II (y_I - sum_{F_I <= J < I} L_IJ y_J)); backward sweep, diagonal
-// tile first (x_I = X_II^T (y_I / D_I - sum_{I < J <= R_I} L_JI^T x_J));
+// (y_I = X_II (y_I - sum_{F_I <= J < I} L_IJ y_J)); backward sweep over the column
+// tiles, then the diagonal tile (x_I = X_II^T (y_I / D_I - sum_{I < J <= R_I} L_JI^T x_J));
 // scatter the owned entries.  Every mbarrier wait is bounded: on expiry it
 // records an error bit and goes on (the results are then garbage and the
 // host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
@@ -823,9 +823,9 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
           for (int J = pm.first[I]; J <= I; ++J) issue(row + (int64_t)(J - pm.first[I]) * TE);
         }
         for (int I = NT - 1; I >= 0; --I) {
-          issue(base + (int64_t)(pm.toff[I] + (I - pm.first[I])) * TE);
           for (int J = I + 1; J <= pm.last[I]; ++J)
             issue(base + (int64_t)(pm.toff[J] + (I - pm.first[J])) * TE);
+          issue(base + (int64_t)(pm.toff[I] + (I - pm.first[I])) * TE);
         }
       }
       __syncwarp();
@@ -927,11 +927,9 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       }
       consumers_sync<kConsumers>();
     }
-    // backward sweep
+    // backward sweep: the column tiles of row I, then its diagonal tile (no
+    // tile is held while another streams in, so two ring slots suffice)
     for (int I = NT - 1; I >= 0; --I) {
-      const T* dt = acquire();  // held until the end of the row
-      const long dseq = seq;
-      ++seq;
       // off-diagonal tiles (transposed): warp (rb, h) takes rows 8 rb .. 8 rb + 7
       // of L_JI and its columns; 8 partials per column
       AT s[NB][2];
@@ -952,6 +950,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
 #pragma unroll
       for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = s[q][0] + s[q][1];
       consumers_sync<kConsumers>();
+      const T* dt = acquire();  // the diagonal tile, released after its product
       if (tid < 64) {
         const AT v0 = (part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid]);
         const AT v1 = (part[64 + tid] + part[192 + tid]) + (part[320 + tid] + part[448 + tid]);
@@ -979,8 +978,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
         }
         red[a * 9 + g] = e0 + e1;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[dseq % nslot]);
+      release();
       consumers_sync<kConsumers>();
       if (tid < 64) {
         const AT* rr = red + tid * 9;

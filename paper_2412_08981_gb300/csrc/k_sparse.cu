@@ -21,9 +21,15 @@ constexpr double kPi = 3.14159265358979323846;
 // ------------------------------------------------------------- geometry
 // lambda = J^{-1}(x - x0), J = [x1-x0 | x2-x0 | x3-x0]; the rows of J^{-1} are
 // the gradients of lambda_1..3 (cofactors / det), grad lambda_0 = -sum.
+// One field: S[e*10 + slot(a,b)] = |T| grad lambda_a . grad lambda_b.
+// Elasticity (three fields): S[e*78 + slot(3a+i, 3b+j)] =
+//   |T| (lam g_a[i] g_b[j] + mu g_a[j] g_b[i] + [i == j] mu g_a . g_b),
+// the unit-k element matrix of int 2 mu eps(u):eps(v) + lam div u div v,
+// upper triangle row-major.
+template <bool Elastic>
 __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
-                               int m, double* __restrict__ S, double* __restrict__ vol,
-                               double* __restrict__ cen, int* bad) {
+                               int m, double lam, double mu, double* __restrict__ S,
+                               double* __restrict__ vol, double* __restrict__ cen, int* bad) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   int4 t = reinterpret_cast<const int4*>(tets)[e];
@@ -60,15 +66,27 @@ __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __
     for (int d = 0; d < 3; ++d) g[a][d] /= det;
 #pragma unroll
   for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
-  int s = 0;
+  if (Elastic) {
+    int s = 0;
+    for (int r = 0; r < 12; ++r)
+      for (int c = r; c < 12; ++c) {
+        const int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
+        double v = lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i];
+        if (i == j) v += mu * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+        S[(int64_t)e * 78 + s] = vv * v;
+        ++s;
+      }
+  } else {
+    int s = 0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = a; b < 4; ++b) {
-      double dd = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
-      S[(int64_t)e * 10 + s] = vv * dd;
-      ++s;
-    }
+      for (int b = a; b < 4; ++b) {
+        double dd = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+        S[(int64_t)e * 10 + s] = vv * dd;
+        ++s;
+      }
+  }
   vol[e] = vv;
 #pragma unroll
   for (int d = 0; d < 3; ++d) cen[3 * (int64_t)e + d] = (p[0][d] + p[1][d] + p[2][d] + p[3][d]) / 4.0;
@@ -79,22 +97,45 @@ __device__ inline double load_f(int kind, double x, double y, double z) {
   return 3.0 * kPi * kPi * sin(kPi * x) * sin(kPi * y) * sin(kPi * z);
 }
 
-// The incident tets of node i are exactly the contributions to its diagonal
-// nonzero (ascending e), so the load sums over that list.
+// Body force of linear elasticity, field c: kind 0 a unit force along -z;
+// kind 1 the force of the solution u = (s, s, s), s = sin sin sin, with k = 1:
+// f_c = -mu lap s - (lam + mu) sum_d d_c d_d s, where lap s = -3 pi^2 s,
+// d_c d_c s = -pi^2 s and d_c d_d s = pi^2 cos(pi x_c) cos(pi x_d) sin(pi x_e).
+__device__ inline double load_elastic(int kind, int c, const double* x, double lam, double mu) {
+  if (kind == 0) return c == 2 ? -1.0 : 0.0;
+  double sn[3], cs[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sn[d] = sin(kPi * x[d]);
+    cs[d] = cos(kPi * x[d]);
+  }
+  const double s = sn[0] * sn[1] * sn[2];
+  double gd = -kPi * kPi * s;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (d != c) gd += kPi * kPi * cs[c] * cs[d] * sn[3 - c - d];
+  return 3.0 * kPi * kPi * mu * s - (lam + mu) * gd;
+}
+
+// The incident tets of a DoF's vertex are exactly the contributions to its
+// diagonal nonzero (ascending e), so the load sums over that list.  DoF i is
+// field i % fields of vertex i / fields; ns element-matrix slots per tet.
 __global__ void k_load_vector(const double* __restrict__ xyz, const uint8_t* __restrict__ dir,
                               const int32_t* __restrict__ diag, const int32_t* __restrict__ cptr,
                               const int32_t* __restrict__ contrib, const double* __restrict__ vol,
-                              int n, int kind, double* __restrict__ b) {
+                              int n, int kind, int fields, int ns, double lam, double mu,
+                              double* __restrict__ b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (dir[i]) {
     b[i] = 0.0;
     return;
   }
-  double f = load_f(kind, xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2]);
+  const double* x = xyz + 3 * (int64_t)(i / fields);
+  double f = fields == 1 ? load_f(kind, x[0], x[1], x[2]) : load_elastic(kind, i % fields, x, lam, mu);
   int q = diag[i];
   double s = 0.0;
-  for (int c = cptr[q]; c < cptr[q + 1]; ++c) s += f * vol[contrib[c] / 10] / 4.0;
+  for (int c = cptr[q]; c < cptr[q + 1]; ++c) s += f * vol[contrib[c] / ns] / 4.0;
   b[i] = s;
 }
 
@@ -119,7 +160,7 @@ __global__ void k_coefficient(const double* __restrict__ cen, int m, int kind,
 
 __global__ void k_assemble(const int32_t* __restrict__ cptr, const int32_t* __restrict__ contrib,
                            const uint8_t* __restrict__ flag, const double* __restrict__ k,
-                           const double* __restrict__ S, int64_t nnz, double* __restrict__ val) {
+                           const double* __restrict__ S, int64_t nnz, int ns, double* __restrict__ val) {
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= nnz) return;
   uint8_t f = flag[q];
@@ -127,7 +168,7 @@ __global__ void k_assemble(const int32_t* __restrict__ cptr, const int32_t* __re
   if (f == 0) {
     for (int c = cptr[q]; c < cptr[q + 1]; ++c) {
       int id = contrib[c];
-      s += k[id / 10] * S[id];
+      s += k[id / ns] * S[id];
     }
   } else if (f == 1) {
     s = 1.0;
@@ -238,16 +279,22 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, double* S, double* vol,
-                         double* cen, int* bad, cudaStream_t s) {
-  if (m > 0) k_tet_geometry<<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, S, vol, cen, bad);
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, bool elastic, double lam, double mu,
+                         double* S, double* vol, double* cen, int* bad, cudaStream_t s) {
+  if (m <= 0) return;
+  if (elastic)
+    k_tet_geometry<true><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
+  else
+    k_tet_geometry<false><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
 }
 
 void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,
                         const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
-                        int load_kind, double* b, cudaStream_t s) {
+                        int load_kind, int fields, int ns, double lam, double mu, double* b,
+                        cudaStream_t s) {
   if (n > 0)
-    k_load_vector<<<nblk(n, 256), 256, 0, s>>>(xyz, dir, diag, cptr, contrib, vol, n, load_kind, b);
+    k_load_vector<<<nblk(n, 256), 256, 0, s>>>(xyz, dir, diag, cptr, contrib, vol, n, load_kind, fields, ns,
+                                               lam, mu, b);
 }
 
 void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
@@ -256,8 +303,8 @@ void launch_coefficient(const double* cen, int m, int coef_kind, const double* m
 }
 
 void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,
-                     const double* k, const double* S, int64_t nnz, double* val, cudaStream_t s) {
-  if (nnz > 0) k_assemble<<<nblk(nnz, 256), 256, 0, s>>>(cptr, contrib, nzflag, k, S, nnz, val);
+                     const double* k, const double* S, int64_t nnz, int ns, double* val, cudaStream_t s) {
+  if (nnz > 0) k_assemble<<<nblk(nnz, 256), 256, 0, s>>>(cptr, contrib, nzflag, k, S, nnz, ns, val);
 }
 
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,

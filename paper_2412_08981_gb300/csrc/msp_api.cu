@@ -295,7 +295,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.cptr = A.upload(H.cptr);
   D.contrib = A.upload(H.contrib);
   D.nzflag = A.upload(H.nzflag);
-  D.S = A.alloc<double>((size_t)H.m * 10);
+  D.S = A.alloc<double>((size_t)H.m * (H.fields == 3 ? kElasticSlots : 10));
   D.vol = A.alloc<double>(H.m);
   D.cen = A.alloc<double>((size_t)H.m * 3);
   D.b = A.alloc<double>(H.n);
@@ -401,17 +401,16 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   }
   if (!D.ilu) {
     const int slots = ras_slots_of(h, l, D.ras_wide);
-    // the backward sweep holds a row's diagonal tile while the next R_I - I
-    // tiles stream in: max_band slots are enough, and never deadlock
+    // the sweeps hold one tile at a time, so two ring slots keep the producer
+    // ahead; deeper rings (up to the tile band) prefetch more
     const bool direct = direct_level(h, l);
     if (direct && ((size_t)D.max_nt * 64 + 128) * sizeof(double) > 220u * 1024u)
       return fail(MSP_ERR_INVALID, "coarsest level too large for the cluster block solve (" +
                                        std::to_string(D.max_nt) + " tiles)");
-    if (!direct && (slots < D.max_band || slots < 2))
-      return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large or " +
-                                       "too wide for the staged triangular solve (" +
-                                       std::to_string(D.max_nt) + " tiles, band " +
-                                       std::to_string(D.max_band) + ")");
+    if (!direct && slots < 2)
+      return fail(MSP_ERR_INVALID, "level " + std::to_string(l) + ": subdomain blocks too large " +
+                                       "for the staged triangular solve (" + std::to_string(D.max_nt) +
+                                       " tiles)");
   }
   if (l + 1 < (int)h->host.size()) {
     D.P_nnz = (int64_t)H.P_col.size();
@@ -432,8 +431,13 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   int* bad = A.alloc<int>(1);
   if (!bad) return fail(MSP_ERR_OOM, "device allocation failed");
   MSP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  launch_tet_geometry(D.xyz, D.tets, D.m, D.S, D.vol, D.cen, bad, s);
-  launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, D.b, s);
+  // Lame parameters of a unit Young's modulus (linear elasticity only)
+  const double nu = h->opt.poisson_ratio;
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+  const bool elastic = H.fields == 3;
+  launch_tet_geometry(D.xyz, D.tets, D.m, elastic, lam, mu, D.S, D.vol, D.cen, bad, s);
+  launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, H.fields,
+                     elastic ? kElasticSlots : 10, lam, mu, D.b, s);
   int hbad = 0;
   MSP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   MSP_CUDA(cudaStreamSynchronize(s));
@@ -475,6 +479,11 @@ int check_options(const msp_options& o) {
   if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
     return fail(MSP_ERR_INVALID, "unknown load");
   if (!std::isfinite(o.coef_scale)) return fail(MSP_ERR_INVALID, "non-finite coef_scale");
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY) return fail(MSP_ERR_INVALID, "unknown pde");
+  if (o.pde == MSP_PDE_ELASTICITY && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
+    return fail(MSP_ERR_INVALID, "linear elasticity needs a Poisson ratio in (0, 0.5)");
+  if (o.pde == MSP_PDE_ELASTICITY && o.transfer != MSP_TRANSFER_BARY)
+    return fail(MSP_ERR_INVALID, "linear elasticity takes the barycentric transfers (field-split P)");
   if ((o.alloc == nullptr) != (o.free == nullptr))
     return fail(MSP_ERR_INVALID, "alloc and free must be given together");
   return MSP_OK;
@@ -488,7 +497,8 @@ int assemble_all(msp_instance* I) {
     DevLevel& D = h->dev[l];
     ProfScope ps(I->prof, PK_ASSEMBLE, s, 2);
     launch_coefficient(D.cen, D.m, h->opt.coef_kind, I->mu, h->wave, h->opt.coef_scale, I->k[l], s);
-    launch_assemble(D.cptr, D.contrib, D.nzflag, I->k[l], D.S, D.nnz, I->val[l], s);
+    launch_assemble(D.cptr, D.contrib, D.nzflag, I->k[l], D.S, D.nnz,
+                    h->host[l].fields == 3 ? kElasticSlots : 10, I->val[l], s);
     ps.account((double)D.nnz * 8 + (double)D.nnz * 5 + (double)h->host[l].contrib.size() * 12 +
                    (double)D.m * 32,
                (double)h->host[l].contrib.size() * 2);
@@ -1085,6 +1095,8 @@ void msp_default_options(msp_options* o) {
   o->coarse_solver = MSP_COARSE_DIRECT;
   o->ilu_fill_fine = -1;
   o->ilu_fill_coarse = -1;
+  o->pde = MSP_PDE_POISSON;
+  o->poisson_ratio = 0.3;
 }
 
 const char* msp_last_error(void) { return msp::g_last_error.c_str(); }
@@ -1154,7 +1166,8 @@ int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info) 
   if (!h || !info || level < 0 || level >= (int)h->host.size())
     return fail(MSP_ERR_INVALID, "bad hierarchy, level or info pointer");
   const HostLevel& H = h->host[level];
-  info->n_nodes = H.n;
+  info->n_nodes = H.nv;
+  info->n_dofs = H.n;
   info->n_tets = H.m;
   info->nnz = (int64_t)H.col.size();
   info->n_sub = H.direct ? 0 : H.nsub;

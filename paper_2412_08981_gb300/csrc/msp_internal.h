@@ -24,19 +24,32 @@ inline int pair_slot(int a, int b) {
 
 inline int64_t tri_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
 
+// Slot of entry (r, s) of the symmetric 12 x 12 element matrix of linear
+// elasticity (row 3a+i: field i of local vertex a), row-major over the upper
+// triangle: 78 slots.
+inline int elastic_slot(int r, int s) {
+  if (r > s) { int t = r; r = s; s = t; }
+  return 12 * r - r * (r - 1) / 2 + (s - r);
+}
+constexpr int kElasticSlots = 78;
+
 // Host-side structures of one level, built once per hierarchy.
 struct HostLevel {
+  // n: DoFs = fields x nv; xyz / tets are per vertex; dir, owner and dir_list
+  // are per DoF (field c of vertex v is DoF fields*v + c)
   int n = 0, m = 0;
+  int nv = 0, fields = 1;
   std::vector<double> xyz;
   std::vector<int32_t> tets;
   std::vector<uint8_t> dir;
   std::vector<int32_t> owner;
-  std::vector<int32_t> dir_list;       // Dirichlet node ids, ascending
+  std::vector<int32_t> dir_list;       // Dirichlet DoF ids, ascending
 
   // CSR pattern of J (Section 2.1): vertices sharing a tet
   std::vector<int32_t> rowptr, col, diag;
   // element -> nonzero contributions: for nonzero q, contrib[cptr[q]..cptr[q+1])
-  // are e*10+slot in ascending e; nzflag[q]: 0 assemble, 1 Dirichlet diagonal
+  // are e*S+slot in ascending e (S = 10 element-matrix slots for one field,
+  // 78 for elasticity); nzflag[q]: 0 assemble, 1 Dirichlet diagonal
   // (value 1), 2 Dirichlet-coupled (value 0)
   std::vector<int32_t> cptr, contrib;
   std::vector<uint8_t> nzflag;

@@ -9,19 +9,23 @@
 namespace msp {
 
 // ---- per-tet geometry (set-up) and per-parameter coefficient / assembly
-// S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b); vol[e] = |T|; cen[e*3] centroid
-void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, double* S, double* vol,
-                         double* cen, int* bad, cudaStream_t s);
-// b_i = f(x_i) * sum_{e containing i} |T_e| / 4 (ascending e), 0 on Dirichlet nodes
+// S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b), or with `elastic` the 78
+// upper-triangle slots of the unit-k 12 x 12 elasticity matrix (Lame lam, mu);
+// vol[e] = |T|; cen[e*3] centroid
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, bool elastic, double lam, double mu,
+                         double* S, double* vol, double* cen, int* bad, cudaStream_t s);
+// b_i = f_c(x_v) * sum_{e containing v} |T_e| / 4 (ascending e) for DoF i =
+// fields*v + c, 0 on Dirichlet DoFs; ns slots per tet in the contributions
 void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,
                         const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
-                        int load_kind, double* b, cudaStream_t s);
+                        int load_kind, int fields, int ns, double lam, double mu, double* b,
+                        cudaStream_t s);
 // k_e = exp(s * sum_j mu_j 0.5 cos(pi a_j . c_e))  (or 1)
 void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
                         const int32_t* wave24, double scale, double* k, cudaStream_t s);
-// val[q] = sum_{c in contrib(q)} k[c/10] * S[c]  (ascending e), Dirichlet flags
+// val[q] = sum_{c in contrib(q)} k[c/ns] * S[c]  (ascending e), Dirichlet flags
 void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,
-                     const double* k, const double* S, int64_t nnz, double* val, cudaStream_t s);
+                     const double* k, const double* S, int64_t nnz, int ns, double* val, cudaStream_t s);
 
 // ---- CSR SpMV family (FP64)
 enum SpmvMode { SPMV_SET = 0, SPMV_SUB_FROM = 1, SPMV_ADD = 2, SPMV_RESIDUAL = 3 };
@@ -117,10 +121,10 @@ void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStre
 // CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
 // longest-first balanced assignment built on the host); a bounded mbarrier
 // wait that expires sets bit 4 of *err.  The factor tiles stream through
-// ras_slots<T>(max_nt) shared-memory slots; the backward sweep holds a row's
-// diagonal tile while it reads that tile column, so there must be at least
-// 1 + (R_I - I) slots for every row I of the level (checked on the host at
-// set-up).
+// ras_slots<T>(max_nt) shared-memory slots; each sweep holds one tile at a
+// time (the backward sweep takes a row's column tiles, then its diagonal
+// tile), so two slots are enough to make progress (checked on the host at
+// set-up); deeper rings let the producer run further ahead.
 // `wide`: one CTA of 16 consumer warps per SM (always the FP64 form); else
 // FP32 / BF16 run 2 / 3 smaller CTAs per SM, each with fewer ring slots.
 template <typename T>

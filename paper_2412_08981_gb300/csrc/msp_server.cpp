@@ -163,7 +163,7 @@ int msp_server_add_hierarchy(msp_server* srv, msp_hierarchy* h, int* id) {
   msp_level_info info;
   rc = msp_hierarchy_info(h, 0, &info);
   if (rc) return rc;
-  E->n_nodes = info.n_nodes;
+  E->n_nodes = info.n_dofs;  // solution length
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->opt.mem_budget_bytes && E->inst_bytes > srv->opt.mem_budget_bytes)
     return msp::fail(MSP_ERR_OOM, "one instance of this hierarchy exceeds the server budget");

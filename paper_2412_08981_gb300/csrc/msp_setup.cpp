@@ -912,6 +912,111 @@ void build_ilu(HostLevel& L, int fill) {
   }
 }
 
+// Three fields per vertex (linear elasticity): the vertex-level pattern,
+// contributions, subdomains and transfers become DoF-level ones, DoF 3v + c
+// for field c of vertex v.  A vertex nonzero (v, w) becomes a 3 x 3 block;
+// its contribution e*10 + pair(a, b) becomes e*78 + slot(3a'+i, 3b'+j) with
+// a', b' the local indices of v and w in tet e.  Subdomains take all fields
+// of their vertices; the transfers become P (x) I_3 (the field-splitting
+// interpolation with the scalar P for every field).
+void expand_csr(int nrows, const std::vector<int32_t>& rp, const std::vector<int32_t>& cl,
+                const std::vector<double>& vl, std::vector<int32_t>& orp, std::vector<int32_t>& ocl,
+                std::vector<double>& ovl) {
+  orp.assign(3 * (size_t)nrows + 1, 0);
+  ocl.clear();
+  ovl.clear();
+  for (int i = 0; i < nrows; ++i)
+    for (int c = 0; c < 3; ++c) {
+      for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        ocl.push_back(3 * cl[q] + c);
+        ovl.push_back(vl[q]);
+      }
+      orp[3 * i + c + 1] = (int32_t)ocl.size();
+    }
+}
+
+void expand_fields(HostLevel& L) {
+  const int nv = L.nv, n = 3 * nv;
+  const std::vector<int32_t> vrp = L.rowptr, vcol = L.col, vcptr = L.cptr, vcon = L.contrib;
+  const std::vector<uint8_t> vdir = L.dir;
+  std::vector<int32_t> rp(n + 1, 0), col;
+  col.reserve(9 * vcol.size());
+  for (int v = 0; v < nv; ++v)
+    for (int c = 0; c < 3; ++c) {
+      for (int q = vrp[v]; q < vrp[v + 1]; ++q)
+        for (int c2 = 0; c2 < 3; ++c2) col.push_back(3 * vcol[q] + c2);
+      rp[3 * v + c + 1] = (int32_t)col.size();
+    }
+  L.rowptr.swap(rp);
+  L.col.swap(col);
+  L.n = n;
+  L.fields = 3;
+  L.dir.assign(n, 0);
+  for (int i = 0; i < n; ++i) L.dir[i] = vdir[i / 3];
+  L.dir_list.clear();
+  for (int i = 0; i < n; ++i)
+    if (L.dir[i]) L.dir_list.push_back(i);
+  if (!L.owner.empty()) {
+    std::vector<int32_t> ow(n);
+    for (int i = 0; i < n; ++i) ow[i] = L.owner[i / 3];
+    L.owner.swap(ow);
+  }
+  L.diag.assign(n, -1);
+  for (int i = 0; i < n; ++i) L.diag[i] = find_in_row(L, i, i);
+  const int64_t nnz = L.col.size();
+  L.nzflag.assign(nnz, 0);
+  for (int i = 0; i < n; ++i)
+    for (int q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
+      const int j = L.col[q];
+      if (L.dir[i]) L.nzflag[q] = (i == j) ? 1 : 2;
+      else if (L.dir[j]) L.nzflag[q] = 2;
+    }
+  // DoF nonzero (3v+i, 3w+j) sits at position 3*(vertex pos of (v,w)) + j of
+  // row 3v+i: the contributions of the vertex nonzero, re-slotted
+  L.cptr.assign(nnz + 1, 0);
+  for (int v = 0; v < nv; ++v)
+    for (int i = 0; i < 3; ++i)
+      for (int qv = vrp[v]; qv < vrp[v + 1]; ++qv)
+        for (int j = 0; j < 3; ++j) {
+          const int64_t q = L.rowptr[3 * v + i] + 3 * (int64_t)(qv - vrp[v]) + j;
+          L.cptr[q + 1] = L.nzflag[q] == 0 ? vcptr[qv + 1] - vcptr[qv] : 0;
+        }
+  for (int64_t q = 0; q < nnz; ++q) L.cptr[q + 1] += L.cptr[q];
+  L.contrib.assign(L.cptr[nnz], 0);
+  for (int v = 0; v < nv; ++v)
+    for (int i = 0; i < 3; ++i)
+      for (int qv = vrp[v]; qv < vrp[v + 1]; ++qv) {
+        const int w = vcol[qv];
+        for (int j = 0; j < 3; ++j) {
+          const int64_t q = L.rowptr[3 * v + i] + 3 * (int64_t)(qv - vrp[v]) + j;
+          if (L.nzflag[q] != 0) continue;
+          int32_t k = L.cptr[q];
+          for (int c = vcptr[qv]; c < vcptr[qv + 1]; ++c) {
+            const int e = vcon[c] / 10;
+            const int32_t* t = &L.tets[4 * (int64_t)e];
+            int a = 0, b = 0;
+            while (t[a] != v) ++a;
+            while (t[b] != w) ++b;
+            L.contrib[k++] = e * kElasticSlots + elastic_slot(3 * a + i, 3 * b + j);
+          }
+        }
+      }
+  // subdomains: all fields of each vertex
+  std::vector<int32_t> sp(L.nsub + 1, 0), sd;
+  std::vector<uint8_t> so;
+  for (int p = 0; p < L.nsub; ++p) {
+    for (int k = L.sub_ptr[p]; k < L.sub_ptr[p + 1]; ++k)
+      for (int c = 0; c < 3; ++c) {
+        sd.push_back(3 * L.sub_dofs[k] + c);
+        so.push_back(L.sub_own[k]);
+      }
+    sp[p + 1] = (int32_t)sd.size();
+  }
+  L.sub_ptr.swap(sp);
+  L.sub_dofs.swap(sd);
+  L.sub_own.swap(so);
+}
+
 std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
   if (d.n_nodes <= 0 || d.n_tets <= 0 || !d.xyz || !d.tets || !d.dirichlet)
     return "level " + std::to_string(l) + ": empty mesh or NULL array";
@@ -941,13 +1046,19 @@ std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
 std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_options& o,
                               std::vector<HostLevel>& out) {
   if (nlevels < 1) return "nlevels must be >= 1";
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY) return "unknown pde";
+  const bool elastic = o.pde == MSP_PDE_ELASTICITY;
+  if (elastic && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
+    return "linear elasticity needs a Poisson ratio in (0, 0.5)";
+  if (elastic && o.transfer != MSP_TRANSFER_BARY)
+    return "linear elasticity takes the barycentric transfers (field-split P)";
   out.assign(nlevels, HostLevel());
   for (int l = 0; l < nlevels; ++l) {
     const bool need_owner = l + 1 < nlevels || o.coarse_solver == MSP_COARSE_RAS;
     std::string e = check_level(lv[l], l, need_owner);
     if (!e.empty()) return e;
     HostLevel& L = out[l];
-    L.n = lv[l].n_nodes;
+    L.n = L.nv = lv[l].n_nodes;
     L.m = lv[l].n_tets;
     L.xyz.assign(lv[l].xyz, lv[l].xyz + 3 * (size_t)L.n);
     L.tets.assign(lv[l].tets, lv[l].tets + 4 * (size_t)L.m);
@@ -962,11 +1073,8 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     L.direct = (l + 1 == nlevels) && o.coarse_solver == MSP_COARSE_DIRECT;
     if (L.direct) build_coarsest_block(L);
     else build_subdomains(L, o.delta);
-    const int fill = (l == 0) ? o.ilu_fill_fine : o.ilu_fill_coarse;
-    if (!L.direct && fill >= 0) build_ilu(L, fill);
     if (L.sub_ptr[L.nsub] == 0 && L.direct && L.n > (int)L.dir_list.size())
       return "internal: empty coarsest block";
-    build_factor_layout(L);
   }
   for (int l = 0; l + 1 < nlevels; ++l) {
     HostLevel& F = out[l];
@@ -979,6 +1087,29 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     } else {
       build_interp(F, C, F);
     }
+  }
+  // DoF-level structures (several fields per vertex), then the subdomain
+  // solvers' layouts on them
+  for (int l = 0; l < nlevels; ++l) {
+    HostLevel& L = out[l];
+    if (elastic) {
+      expand_fields(L);
+      if (l + 1 < nlevels) {
+        std::vector<int32_t> rp, cl;
+        std::vector<double> vl;
+        expand_csr(L.nv, L.P_rowptr, L.P_col, L.P_val, rp, cl, vl);
+        L.P_rowptr.swap(rp);
+        L.P_col.swap(cl);
+        L.P_val.swap(vl);
+        expand_csr(out[l + 1].nv, L.PT_rowptr, L.PT_col, L.PT_val, rp, cl, vl);
+        L.PT_rowptr.swap(rp);
+        L.PT_col.swap(cl);
+        L.PT_val.swap(vl);
+      }
+    }
+    const int fill = (l == 0) ? o.ilu_fill_fine : o.ilu_fill_coarse;
+    if (!L.direct && fill >= 0) build_ilu(L, fill);
+    build_factor_layout(L);
   }
   return "";
 }

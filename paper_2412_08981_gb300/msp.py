@@ -24,6 +24,7 @@ MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
 MSP_COARSE_DIRECT, MSP_COARSE_RAS = 0, 1
+MSP_PDE_POISSON, MSP_PDE_ELASTICITY = 0, 1
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
@@ -66,6 +67,7 @@ class msp_options(C.Structure):
                 ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("transfer", C.c_int32),
                 ("restrict_scaling", C.c_int32), ("coarse_solver", C.c_int32),
                 ("ilu_fill_fine", C.c_int32), ("ilu_fill_coarse", C.c_int32),
+                ("pde", C.c_int32), ("poisson_ratio", C.c_double),
                 ("host_only", C.c_int32),
                 ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
                 ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
@@ -86,7 +88,7 @@ class msp_level_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("nnz", C.c_int64),
                 ("n_sub", C.c_int32), ("sub_dofs", C.c_int64), ("factor_elems", C.c_int64),
                 ("P_nnz", C.c_int64), ("R_nnz", C.c_int64), ("fac_ctas", C.c_int32),
-                ("ras_ctas", C.c_int32), ("spmv_lanes", C.c_int32 * 3)]
+                ("ras_ctas", C.c_int32), ("spmv_lanes", C.c_int32 * 3), ("n_dofs", C.c_int32)]
 
 
 class msp_kernel_profile(C.Structure):
@@ -220,12 +222,16 @@ class Hierarchy:
 
     levels: sequence of objects with xyz [n,3] f64, tets [m,4] i32,
     dirichlet [n] u8 and owner [n] i32 (or None on the coarsest level).
+    pde: "poisson" (one DoF per vertex) or "elasticity" (three displacement
+    fields per vertex, DoF 3v + c; Poisson ratio `poisson`); vectors of a
+    level hold n_dofs(level) entries.
     """
 
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
                  max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
                  load="one", host_only=False, budget_bytes=0, torch_alloc=True,
-                 transfer="bary", restrict_scaling=True, coarse="direct", ilu=None):
+                 transfer="bary", restrict_scaling=True, coarse="direct", ilu=None,
+                 pde="poisson", poisson=0.3):
         lib = _load_library()
         self._keep = []
         arr = (msp_level_desc * len(levels))()
@@ -249,6 +255,8 @@ class Hierarchy:
                             coarse_solver={"direct": MSP_COARSE_DIRECT, "ras": MSP_COARSE_RAS}[coarse],
                             ilu_fill_fine=-1 if ilu is None else int(ilu[0]),
                             ilu_fill_coarse=-1 if ilu is None else int(ilu[1]),
+                            pde={"poisson": MSP_PDE_POISSON, "elasticity": MSP_PDE_ELASTICITY}[pde],
+                            poisson_ratio=float(poisson),
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))
         if wave is not None:
@@ -266,6 +274,11 @@ class Hierarchy:
         self.h = h
         self.nlevels = len(levels)
         self.coef = coef
+        self.fields = 3 if pde == "elasticity" else 1
+
+    def n_dofs(self, level=0) -> int:
+        """Length of the vectors of a level."""
+        return int(self.info(level)["n_dofs"])
 
     def close(self):
         if getattr(self, "h", None):

@@ -147,7 +147,8 @@ def mu_draw(request: int) -> np.ndarray:
 
 # Workloads: name -> hierarchy recipe and solver options.
 #   coef: "const" (k = 1) or "cosexp" (k = exp(s * sum_j mu_j 0.5 cos(pi a_j.x)))
-#   load: "sines" (f = 3 pi^2 sin sin sin) or "one" (f = 1)
+#   load: "sines" (f = 3 pi^2 sin sin sin) or "one" (f = 1; elasticity: f = (0, 0, -1))
+#   pde: "poisson" (default) or "elasticity" (with its Poisson ratio "poisson")
 WORKLOADS = {
     # two-level plain FP64, 8^3 -> 4^3, 2x2x2 boxes, overlap 1
     "cube8_2lvl": dict(ns=(8, 4), parts=((2, 2, 2),), delta=1, nu=2, coef="const",
@@ -167,6 +168,15 @@ WORKLOADS = {
     # three-level plain FP64, 64^3 -> 32^3 -> 16^3, 512 boxes per RAS level, overlap 2
     "cube64_3lvl": dict(ns=(64, 32, 16), parts=((8, 8, 8), (8, 8, 8)), delta=2, nu=2,
                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
+    # linear elasticity (three displacement fields per vertex, Poisson ratio
+    # 0.3, unit body force along -z): parity case with blocks of ~1500 DoFs
+    "elast12_3lvl": dict(ns=(12, 6, 3), parts=((2, 2, 2), (2, 2, 2)), delta=1, nu=2,
+                         coef="cosexp", scale=1.0, load="one", rtol=1e-10, restart=30,
+                         pde="elasticity", poisson=0.3),
+    # and the measured case: 107,811 DoFs on 32^3, 64 + 8 blocks of ~3000 DoFs
+    "elast32_3lvl": dict(ns=(32, 16, 8), parts=((4, 4, 4), (2, 2, 2)), delta=1, nu=2,
+                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30,
+                         pde="elasticity", poisson=0.3),
 }
 
 

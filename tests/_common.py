@@ -22,16 +22,27 @@ def workload(name, hierarchy_id=0):
     return syn.workload(name, hierarchy_id)
 
 
+def _pde(w):
+    return dict(pde=w["pde"], poisson=w["poisson"]) if "pde" in w else {}
+
+
 def make_oracle(levels, w, orc, **kw):
-    return orc.Oracle(levels, delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], coef=w["coef"],
-                      wave=syn.wave_vectors(), scale=w["scale"], load=w["load"], **kw)
+    args = dict(delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], coef=w["coef"],
+                wave=syn.wave_vectors(), scale=w["scale"], load=w["load"], **_pde(w))
+    args.update(kw)
+    return orc.Oracle(levels, **args)
 
 
 def make_hierarchy(levels, w, P, **kw):
     args = dict(delta=w["delta"], nu_pre=w["nu"], nu_post=w["nu"], restart=w["restart"],
-                coef=w["coef"], wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
+                coef=w["coef"], wave=syn.wave_vectors(), scale=w["scale"], load=w["load"], **_pde(w))
     args.update(kw)
     return P.Hierarchy(levels, **args)
+
+
+def n_dofs(levels, w, level=0):
+    """Vector length of a level of a workload."""
+    return (3 if w.get("pde") == "elasticity" else 1) * levels[level].n_nodes
 
 
 def rel(a, b):

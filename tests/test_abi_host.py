@@ -135,6 +135,39 @@ def test_host_ilu_patterns_match_oracle(P, orc, name, ilu):
                 np.testing.assert_array_equal(col[ptr[R]:ptr[R + 1]], oc[oc < i])
 
 
+def test_host_elasticity_structures_match_oracle(P, orc):
+    """Three displacement fields per vertex: the DoF-level CSR pattern, the
+    subdomain DoF lists and the field-split transfers P (x) I_3 are the
+    oracle's bit for bit (values to rounding)."""
+    levels, w = workload("elast12_3lvl")
+    h = make_hierarchy(levels, w, P, host_only=True)
+    o = make_oracle(levels, w, orc)
+    L = len(levels)
+    for l in range(L):
+        assert h.info(l)["n_dofs"] == 3 * levels[l].n_nodes == o.n[l]
+        assert h.info(l)["n_nodes"] == levels[l].n_nodes
+        np.testing.assert_array_equal(h.array(l, "rowptr"), o.get("rowptr", l))
+        np.testing.assert_array_equal(h.array(l, "col"), o.get("col", l))
+    for l in range(L - 1):
+        subs = o.subdomains(l)
+        sp_, sd, so = h.array(l, "sub_ptr"), h.array(l, "sub_dofs"), h.array(l, "sub_own")
+        assert sp_.size - 1 == len(subs)
+        for p, (d, ow) in enumerate(subs):
+            np.testing.assert_array_equal(sd[sp_[p]:sp_[p + 1]], d)
+            np.testing.assert_array_equal(so[sp_[p]:sp_[p + 1]], ow)
+        for a in ("P_rowptr", "P_col", "PT_rowptr", "PT_col"):
+            np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+        np.testing.assert_allclose(h.array(l, "P_val"), o.get("P_val", l), atol=1e-13)
+        np.testing.assert_allclose(h.array(l, "PT_val"), o.get("PT_val", l), atol=1e-13)
+    sd = h.array(L - 1, "sub_dofs")
+    np.testing.assert_array_equal(sd, np.where(np.repeat(levels[-1].dirichlet, 3) == 0)[0])
+    # the elasticity path takes the field-split barycentric transfers only
+    with pytest.raises(P.MspError):
+        make_hierarchy(levels, w, P, host_only=True, transfer="mls")
+    with pytest.raises(P.MspError):
+        make_hierarchy(levels, w, P, host_only=True, poisson=0.5)
+
+
 def test_odd_partition_and_empty_boxes(P, orc):
     """Partition ids that skip values and boxes with only Dirichlet nodes."""
     fine = syn.cube_level(9, 3, parts=(5, 3, 2))

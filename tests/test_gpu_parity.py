@@ -47,7 +47,8 @@ class Case:
         self.inst = self.h.assemble(self.mu, stream=torch.cuda.current_stream())
         self.inst.factor()
         self.torch = torch
-        self.n = [lv.n_nodes for lv in self.levels]
+        self.n = list(self.o.n)  # DoFs per level (fields x vertices)
+        self.dir0 = np.repeat(self.levels[0].dirichlet, self.o.fields)
 
     def dev(self, x):
         return self.torch.tensor(np.asarray(x, np.float64), device="cuda")
@@ -60,9 +61,11 @@ class Case:
         return t.cpu().numpy()
 
 
-# every parity workload with P / P^T, and two with the MLS transfers of
-# Section 3.2 (cube20m pairs the subdomains of the two RAS levels)
-CASES = [(n, "bary") for n in PARITY] + [("cube16_3lvl", "mls"), ("cube20m_3lvl", "mls")]
+# every parity workload with P / P^T, two with the MLS transfers of Section
+# 3.2 (cube20m pairs the subdomains of the two RAS levels), and the
+# multi-field case: linear elasticity, three fields per vertex, field-split P
+CASES = ([(n, "bary") for n in PARITY] + [("cube16_3lvl", "mls"), ("cube20m_3lvl", "mls")] +
+         [("elast12_3lvl", "bary")])
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-{c[1]}")
@@ -159,7 +162,7 @@ def test_fgmres_solution(case):
     assert rel(case.host(x), xo) <= 1e-7
     # user right-hand side through the same call
     b = np.random.default_rng(4).normal(size=case.n[0])
-    b[case.levels[0].dirichlet == 1] = 0.0
+    b[case.dir0 == 1] = 0.0
     xb = case.zeros(case.n[0])
     st = case.inst.solve(xb, b=case.dev(b), rtol=rtol)
     xob, _ = case.o.fgmres(b, rtol=rtol, restart=case.w["restart"])
@@ -180,6 +183,29 @@ def test_solve_host_end_to_end(case):
     case.o.factor()
     case.inst.reassemble(case.mu)
     case.inst.factor()
+
+
+def test_elasticity_fp32_factors(P, orc, torch):
+    """Three displacement fields per vertex with FP32 subdomain factors under
+    the FP64 outer loop: the FP64 oracle's solution, at most 3 more
+    iterations; the load is the unit body force along -z."""
+    levels, w = workload("elast12_3lvl")
+    mu = syn.mu_draw(5)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10, restart=w["restart"])
+    h = make_hierarchy(levels, w, P, precision="f32")
+    assert h.n_dofs(0) == 3 * levels[0].n_nodes
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(h.n_dofs(0), dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and so["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-7
+    assert st["iterations"] <= so["iters"] + 3
+    b = h.array(0, "load").reshape(-1, 3)
+    assert not b[:, :2].any() and (b[:, 2] <= 0).all() and (b[:, 2] < 0).any()
 
 
 # ------------------------------------------------------------- edge cases

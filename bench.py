@@ -368,6 +368,47 @@ def run_msp(args):
         h.close()
         return dict(value=steps / wall, lat=lat, iters=iters, wall_s=wall)
 
+    def measure_hbm_kernels(reps=20):
+        """The memory-bound operators of the finest level timed one launch at
+        a time: J x (SpMV), P x_c (interpolation) and P^T x (restriction), each
+        with L2 flushed before every launch (a 256 MB write) and the stream
+        kept busy while the host enqueues, so that the events bracket the
+        kernel alone.  Algorithmic bytes: 12 per nonzero (value + column) +
+        4 per row pointer + 8 per vector entry read or written."""
+        h = P.Hierarchy(levels, precision="f64", **kw)
+        inst = h.assemble(mu_of(0), stream=stream)
+        i0, i1 = h.info(0), h.info(1)
+        n0, n1 = i0["n_dofs"], i1["n_dofs"]
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        peak = measured_peak("hbm_gbs", 6755.1)
+        ops = {"spmv_J0": (P.msp.MSP_OP_SPMV, n0, n0, 12 * i0["nnz"] + 4 * (n0 + 1) + 8 * n0 + 8 * n0),
+               "interp_P0": (P.msp.MSP_OP_INTERP, n1, n0, 12 * i0["P_nnz"] + 4 * (n0 + 1) + 8 * n1 + 8 * n0),
+               "restrict_PT0": (P.msp.MSP_OP_RESTRICT, n0, n1,
+                                12 * i0["R_nnz"] + 4 * (n1 + 1) + 8 * n0 + 8 * n1)}
+        out = {"l2": "flushed before every launch", "peak_gbs": peak, "peak_source": "MEASURED_PEAKS hbm_gbs"}
+        with torch.cuda.stream(stream):
+            for name, (op, nin, nout, nbytes) in ops.items():
+                x = torch.rand(nin, dtype=torch.float64, device="cuda")
+                y = torch.zeros(nout, dtype=torch.float64, device="cuda")
+                ts = []
+                for r in range(reps + 3):
+                    flush.fill_(r & 255)
+                    torch.cuda._sleep(20000)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    inst.apply_op(op, 0, x, y)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r >= 3:
+                        ts.append(e0.elapsed_time(e1))
+                us = 1e3 * float(np.median(ts))
+                gbs = nbytes / (us * 1e-6) / 1e9
+                out[name] = {"bytes_per_launch": int(nbytes), "us_median": round(us, 2),
+                             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        inst.close()
+        h.close()
+        return out
+
     def measure_serving(nreq, rate):
         """Poisson arrivals of seeded mu over two resident hierarchies (32^3 and
         64^3, FP32 subdomain factors), served by msp_submit/msp_poll."""
@@ -426,6 +467,7 @@ def run_msp(args):
                 "timing": "host wall clock from the first arrival to the last completion"}
 
     res = measure(args.precision, args.steps, args.warmup)
+    hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 else None
     ms = max_over_ranks(res["ms"])
     value = whole_job_rate(args.steps, world, ms)
     mixed = None
@@ -585,6 +627,8 @@ def run_msp(args):
         line["mls"] = mls
     if ilu:
         line["ilu"] = ilu
+    if hbm:
+        line["hbm_kernels"] = hbm
     if elastic:
         line["elasticity"] = elastic
     if literal:

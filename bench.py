@@ -368,42 +368,53 @@ def run_msp(args):
         h.close()
         return dict(value=steps / wall, lat=lat, iters=iters, wall_s=wall)
 
-    def measure_hbm_kernels(reps=20):
-        """The memory-bound operators of the finest level timed one launch at
-        a time: J x (SpMV), P x_c (interpolation) and P^T x (restriction), each
-        with L2 flushed before every launch (a 256 MB write) and the stream
-        kept busy while the host enqueues, so that the events bracket the
-        kernel alone.  Algorithmic bytes: 12 per nonzero (value + column) +
-        4 per row pointer + 8 per vector entry read or written."""
+    def measure_hbm_kernels(reps=40):
+        """The memory-bound operators of the finest level: J x (SpMV), P x_c
+        (interpolation) and P^T x (restriction), each launch preceded by an L2
+        eviction (a 256 MB read, which leaves clean lines).  The CUDA event
+        clock ticks in microseconds, too coarse for one launch, so a sequence
+        of `reps` (eviction, launch) pairs is timed against the same sequence
+        without the launches, both queued behind a GPU sleep so that the host
+        never starves the stream; the difference over reps is the launch.
+        Algorithmic bytes: 12 per nonzero (value + column) + 4 per row pointer
+        + 8 per vector entry read or written."""
         h = P.Hierarchy(levels, precision="f64", **kw)
         inst = h.assemble(mu_of(0), stream=stream)
         i0, i1 = h.info(0), h.info(1)
         n0, n1 = i0["n_dofs"], i1["n_dofs"]
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        flush = torch.zeros(32 << 20, dtype=torch.float64, device="cuda")  # 256 MB
         peak = measured_peak("hbm_gbs", 6755.1)
         ops = {"spmv_J0": (P.msp.MSP_OP_SPMV, n0, n0, 12 * i0["nnz"] + 4 * (n0 + 1) + 8 * n0 + 8 * n0),
                "interp_P0": (P.msp.MSP_OP_INTERP, n1, n0, 12 * i0["P_nnz"] + 4 * (n0 + 1) + 8 * n1 + 8 * n0),
                "restrict_PT0": (P.msp.MSP_OP_RESTRICT, n0, n1,
                                 12 * i0["R_nnz"] + 4 * (n1 + 1) + 8 * n0 + 8 * n1)}
-        out = {"l2": "flushed before every launch", "peak_gbs": peak, "peak_source": "MEASURED_PEAKS hbm_gbs"}
+        out = {"l2": "evicted before every launch (256 MB read)", "peak_gbs": peak,
+               "peak_source": "MEASURED_PEAKS hbm_gbs", "reps": reps}
+
+        def seq(fn):
+            torch.cuda._sleep(4_000_000)  # ~2 ms: the host queues the whole sequence meanwhile
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                flush.sum()
+                if fn:
+                    fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+
         with torch.cuda.stream(stream):
             for name, (op, nin, nout, nbytes) in ops.items():
                 x = torch.rand(nin, dtype=torch.float64, device="cuda")
                 y = torch.zeros(nout, dtype=torch.float64, device="cuda")
-                ts = []
-                for r in range(reps + 3):
-                    flush.fill_(r & 255)
-                    torch.cuda._sleep(20000)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    inst.apply_op(op, 0, x, y)
-                    e1.record(stream)
-                    e1.synchronize()
-                    if r >= 3:
-                        ts.append(e0.elapsed_time(e1))
-                us = 1e3 * float(np.median(ts))
+                fn = lambda: inst.apply_op(op, 0, x, y)  # noqa: E731
+                seq(fn)  # warm-up
+                d = []
+                for _ in range(3):
+                    d.append(seq(fn) - seq(None))
+                us = 1e3 * float(np.median(d)) / reps
                 gbs = nbytes / (us * 1e-6) / 1e9
-                out[name] = {"bytes_per_launch": int(nbytes), "us_median": round(us, 2),
+                out[name] = {"bytes_per_launch": int(nbytes), "us_per_launch": round(us, 2),
                              "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
         inst.close()
         h.close()

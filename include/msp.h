@@ -213,8 +213,11 @@ typedef struct msp_level_info {
                                  (0: tile-step launches, or a host-only hierarchy) */
   int32_t ras_ctas;           /* CTAs of the staged RAS solve (0: directly solved level) */
   int32_t spmv_lanes[3];      /* lanes per row of the SpMV schedules picked at load time by
-                                 timing 4/8/16/32 on the device: J, prolongation, restriction
-                                 (0: host-only hierarchy or no such operator) */
+                                 timing them on the device: 4/8/16/32, or 1 (one lane per row
+                                 over row blocks staged in shared memory); J, prolongation,
+                                 restriction (0: host-only hierarchy or no such operator).
+                                 The environment variable MSP_SPMV_LANES = 1, 4, 8, 16 or 32,
+                                 read at load time, fixes the schedule instead */
   int32_t n_dofs;             /* DoFs: n_nodes x fields per vertex (msp_options.pde) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);

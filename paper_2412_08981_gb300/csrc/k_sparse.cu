@@ -4,12 +4,14 @@
 // are bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
 #include <vector>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "msp_kernels.h"
 
@@ -204,6 +206,97 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
   }
 }
 
+// One lane per row, rows in blocks (set-up: at most kRowsThreads rows and
+// kRowsNnz nonzeros per block, or one longer row alone; the set-up also
+// stores each block's first nonzero, blk_e, so that no load waits on
+// another before the stream starts).  The block copies its nonzeros (values
+// and columns, one contiguous range) and its row pointers into shared memory,
+// every load of a thread issued before its first store; then thread t forms
+// row r0 + t: the gathers of x for up to 16 entries are issued together, then
+// an FMA chain in ascending position.  Every FP64 instruction has a full warp
+// of work (one FMA per nonzero).  A row longer than the buffer is summed by
+// the whole block straight from global memory (strided partial sums, then a
+// fixed tree).
+constexpr int kRowsThreads = 128, kRowsNnz = 2048, kRowsGather = 16;
+
+__global__ void __launch_bounds__(kRowsThreads) k_spmv_rows(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+    const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_e, const double* __restrict__ x,
+    double* __restrict__ y, const double* __restrict__ r, int mode) {
+  __shared__ double sv[kRowsNnz];
+  __shared__ int32_t sc[kRowsNnz];
+  __shared__ int32_t srp[kRowsThreads + 1];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int r0 = row_blk[b], r1 = row_blk[b + 1];
+  const int e0 = blk_e[b], ne = blk_e[b + 1] - e0;
+  double s = 0.0;
+  int row = r0 + tid;
+  if (ne <= kRowsNnz) {
+    constexpr int K = kRowsNnz / kRowsThreads;
+    double v[K];
+    int32_t c[K];
+    const int nr = r1 - r0;
+    int32_t rp0 = 0, rp1 = 0;
+    if (tid < nr) rp0 = rowptr[row] - e0;
+    if (tid == 0) rp1 = rowptr[r1] - e0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = tid + k * kRowsThreads;
+      if (e < ne) {
+        v[k] = val[e0 + e];
+        c[k] = col[e0 + e];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = tid + k * kRowsThreads;
+      if (e < ne) {
+        sv[e] = v[k];
+        sc[e] = c[k];
+      }
+    }
+    if (tid < nr) srp[tid] = rp0;
+    if (tid == 0) srp[nr] = rp1;
+    __syncthreads();
+    if (row >= r1) return;
+    const int en = srp[tid + 1];
+    for (int q0 = srp[tid]; q0 < en; q0 += kRowsGather) {
+      double xv[kRowsGather];
+#pragma unroll
+      for (int k = 0; k < kRowsGather; ++k) xv[k] = (q0 + k < en) ? x[sc[q0 + k]] : 0.0;
+#pragma unroll
+      for (int k = 0; k < kRowsGather; ++k)
+        if (q0 + k < en) s = fma(sv[q0 + k], xv[k], s);
+    }
+  } else {  // one long row
+    __shared__ double red[kRowsThreads];
+    for (int q = e0 + tid; q < e0 + ne; q += kRowsThreads) s = fma(val[q], x[col[q]], s);
+    red[tid] = s;
+    __syncthreads();
+    for (int off = kRowsThreads / 2; off > 0; off >>= 1) {
+      if (tid < off) red[tid] += red[tid + off];
+      __syncthreads();
+    }
+    if (tid != 0) return;
+    s = red[0];
+    row = r0;
+  }
+  switch (mode) {
+    case SPMV_SET: y[row] = s; break;
+    case SPMV_SUB_FROM: y[row] = y[row] - s; break;
+    case SPMV_ADD: y[row] = y[row] + s; break;
+    default: y[row] = r[row] - s; break;
+  }
+}
+
+// Reads n doubles (evicts the L2 with clean lines) and stores one value.
+__global__ void k_touch(const double* __restrict__ p, int64_t n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += p[i];
+  if (s == 1.2345e300) *out = s;  // never true for the zero buffer: keeps the loads
+}
+
 // ------------------------------------------------------------- vectors
 // Stage 1: block b of vector i sums a strided slice of V_i . w.
 __global__ void k_multidot_part(const double* __restrict__ V, int64_t ld,
@@ -307,11 +400,30 @@ void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t*
   if (nnz > 0) k_assemble<<<nblk(nnz, 256), 256, 0, s>>>(cptr, contrib, nzflag, k, S, nnz, ns, val);
 }
 
+std::vector<int32_t> spmv_row_blocks(const std::vector<int32_t>& rowptr) {
+  std::vector<int32_t> blk{0};
+  const int nrows = (int)rowptr.size() - 1;
+  int r0 = 0;
+  while (r0 < nrows) {
+    int r1 = r0 + 1;  // a row longer than the buffer goes alone
+    while (r1 < nrows && r1 - r0 < kRowsThreads && rowptr[r1 + 1] - rowptr[r0] <= kRowsNnz) ++r1;
+    blk.push_back(r1);
+    r0 = r1;
+  }
+  const size_t nb1 = blk.size();  // then the first nonzero of every block boundary
+  for (size_t k = 0; k < nb1; ++k) blk.push_back(rowptr[blk[k]]);
+  return blk;
+}
+
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
-                 const double* x, double* y, const double* r, int mode, int lpr,
+                 const double* x, double* y, const double* r, int mode, const SpmvPlan& plan,
                  cudaStream_t s) {
   if (nrows <= 0) return;
-  switch (lpr) {
+  switch (plan.lpr) {
+    case 1:
+      k_spmv_rows<<<plan.nblk, kRowsThreads, 0, s>>>(rowptr, col, val, plan.row_blk, plan.row_blk + plan.nblk + 1,
+                                                     x, y, r, mode);
+      break;
     case 4:
       k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
       break;
@@ -327,19 +439,26 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
   }
 }
 
-// Autotuner of the SpMV schedule (lanes per row): every candidate is timed
+// Autotuner of the SpMV schedule: lanes per row 4, 8, 16, 32, or one lane
+// per row over shared-memory-staged row blocks (1).  Every candidate is timed
 // with CUDA events on the matrix itself (zero values, zero x: the memory
-// traffic and the schedule are those of the real products) and the fastest
-// kept.  The choice is cached per structure (rows, nnz, hash of rowptr and
-// col) for the life of the process, so that identical matrices always get
-// the same schedule (and bitwise the same sums).
+// traffic and the schedule are those of the real products), one launch at a
+// time after the L2 has been evicted (a 256 MB read), as in the solve, where
+// the subdomain solves stream gigabytes between two products; the fastest
+// total is kept.  The choice is cached per structure (rows, nnz, hash of
+// rowptr and col) for the life of the process, so that identical matrices
+// always get the same schedule (and bitwise the same sums).
 int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
               const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
-              cudaStream_t s) {
+              const int32_t* row_blk, int nblk, cudaStream_t s) {
   static std::mutex mu;
   static std::map<std::tuple<int, int64_t, uint64_t>, int> cache;
   const int64_t nnz = h_col.size();
   if (nrows <= 0 || nnz == 0) return 8;
+  if (const char* f = std::getenv("MSP_SPMV_LANES")) {  // a fixed schedule instead of the timed choice
+    const int v = std::atoi(f);
+    if (v == 4 || v == 8 || v == 16 || v == 32 || (v == 1 && row_blk)) return v;
+  }
   uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the structure
   auto mix = [&](int32_t v) {
     for (int b = 0; b < 4; ++b) {
@@ -353,33 +472,44 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  double *val = nullptr, *x = nullptr, *y = nullptr;
+  double *val = nullptr, *x = nullptr, *y = nullptr, *flush = nullptr;
+  const int64_t nflush = (256ll << 20) / 8;
   int best = 8;
   if (cudaMalloc(&val, nnz * sizeof(double)) == cudaSuccess &&
       cudaMalloc(&x, (size_t)ncols * sizeof(double)) == cudaSuccess &&
-      cudaMalloc(&y, (size_t)nrows * sizeof(double)) == cudaSuccess) {
+      cudaMalloc(&y, (size_t)nrows * sizeof(double)) == cudaSuccess &&
+      cudaMalloc(&flush, (size_t)nflush * sizeof(double) + 8) == cudaSuccess) {
     cudaMemsetAsync(val, 0, nnz * sizeof(double), s);
     cudaMemsetAsync(x, 0, (size_t)ncols * sizeof(double), s);
+    cudaMemsetAsync(flush, 0, (size_t)nflush * sizeof(double) + 8, s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
-    for (int lpr : {4, 8, 16, 32}) {
-      launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, lpr, s);  // warm-up
-      cudaEventRecord(e0, s);
-      for (int rep = 0; rep < 5; ++rep) launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, lpr, s);
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
+    for (int lpr : {1, 4, 8, 16, 32}) {
+      const SpmvPlan plan{lpr, row_blk, nblk};
+      if (lpr == 1 && !row_blk) continue;
+      launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);  // warm-up
+      float tot = 0;
+      for (int rep = 0; rep < 5; ++rep) {
+        k_touch<<<1024, 256, 0, s>>>(flush, nflush, flush + nflush);
+        cudaEventRecord(e0, s);
+        launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tot += ms;
+      }
+      if (tot < best_ms) {
+        best_ms = tot;
         best = lpr;
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
+  cudaFree(flush);
   cudaFree(val);
   cudaFree(x);
   cudaFree(y);

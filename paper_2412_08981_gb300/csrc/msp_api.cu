@@ -98,7 +98,9 @@ struct DevArena {
 struct DevLevel {
   int n = 0, m = 0;
   int64_t nnz = 0;
-  int lpr_A = 8, lpr_P = 4, lpr_PT = 16;  // SpMV lanes per row (autotuned at load)
+  int lpr_A = 8, lpr_P = 4, lpr_PT = 16;  // SpMV schedules (autotuned at load; 1 = row blocks)
+  int32_t *rb_A = nullptr, *rb_P = nullptr, *rb_PT = nullptr;  // row blocks of the one-lane schedule
+  int nrb_A = 0, nrb_P = 0, nrb_PT = 0;
   // ILU(p) subdomain factors (see HostLevel)
   bool ilu = false;
   int64_t ilu_nnz = 0, ilu_rows = 0, ilu_next = 0;
@@ -290,7 +292,12 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.ndir = (int)H.dir_list.size();
   D.rowptr = A.upload(H.rowptr);
   D.col = A.upload(H.col);
-  if (A.ok) D.lpr_A = tune_spmv(D.rowptr, D.col, H.n, H.n, H.rowptr, H.col, s);
+  {
+    const std::vector<int32_t> rb = spmv_row_blocks(H.rowptr);
+    D.rb_A = A.upload(rb);
+    D.nrb_A = (int)rb.size() / 2 - 1;
+  }
+  if (A.ok) D.lpr_A = tune_spmv(D.rowptr, D.col, H.n, H.n, H.rowptr, H.col, D.rb_A, D.nrb_A, s);
   D.diag = A.upload(H.diag);
   D.cptr = A.upload(H.cptr);
   D.contrib = A.upload(H.contrib);
@@ -421,10 +428,17 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.PT_rowptr = A.upload(H.PT_rowptr);
     D.PT_col = A.upload(H.PT_col);
     D.PT_val = A.upload(H.PT_val);
+    {
+      const std::vector<int32_t> rbp = spmv_row_blocks(H.P_rowptr), rbt = spmv_row_blocks(H.PT_rowptr);
+      D.rb_P = A.upload(rbp);
+      D.nrb_P = (int)rbp.size() / 2 - 1;
+      D.rb_PT = A.upload(rbt);
+      D.nrb_PT = (int)rbt.size() / 2 - 1;
+    }
     if (A.ok) {
       const int nc = h->host[l + 1].n;
-      D.lpr_P = tune_spmv(D.P_rowptr, D.P_col, H.n, nc, H.P_rowptr, H.P_col, s);
-      D.lpr_PT = tune_spmv(D.PT_rowptr, D.PT_col, nc, H.n, H.PT_rowptr, H.PT_col, s);
+      D.lpr_P = tune_spmv(D.P_rowptr, D.P_col, H.n, nc, H.P_rowptr, H.P_col, D.rb_P, D.nrb_P, s);
+      D.lpr_PT = tune_spmv(D.PT_rowptr, D.PT_col, nc, H.n, H.PT_rowptr, H.PT_col, D.rb_PT, D.nrb_PT, s);
     }
   }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed while loading level " + std::to_string(l));
@@ -743,7 +757,7 @@ void spmv(msp_instance* I, int l, const double* x, double* y, const double* r, i
           cudaStream_t s) {
   DevLevel& D = I->h->dev[l];
   ProfScope ps(I->prof, PK_SPMV, s);
-  launch_spmv(D.rowptr, D.col, I->val[l], D.n, x, y, r, mode, D.lpr_A, s);
+  launch_spmv(D.rowptr, D.col, I->val[l], D.n, x, y, r, mode, SpmvPlan{D.lpr_A, D.rb_A, D.nrb_A}, s);
   ps.account((double)D.nnz * 12 + (double)(D.n + 1) * 4 + (double)D.n * (mode == SPMV_SET ? 16 : 24),
              2.0 * (double)D.nnz);
 }
@@ -754,9 +768,10 @@ void transfer(msp_instance* I, int l, bool restrict_, const double* x, double* y
   int nc = I->h->dev[l + 1].n;
   ProfScope ps(I->prof, PK_TRANSFER, s);
   if (restrict_)
-    launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, D.lpr_PT, s);
+    launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, SpmvPlan{D.lpr_PT, D.rb_PT, D.nrb_PT},
+                s);
   else
-    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, D.lpr_P, s);
+    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, SpmvPlan{D.lpr_P, D.rb_P, D.nrb_P}, s);
   double rows = restrict_ ? nc : D.n, cols = restrict_ ? D.n : nc;
   double nnz = (double)(restrict_ ? D.PT_nnz : D.P_nnz);
   ps.account(nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16), 2.0 * nnz);

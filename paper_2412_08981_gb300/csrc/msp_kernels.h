@@ -29,16 +29,24 @@ void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t*
 
 // ---- CSR SpMV family (FP64)
 enum SpmvMode { SPMV_SET = 0, SPMV_SUB_FROM = 1, SPMV_ADD = 2, SPMV_RESIDUAL = 3 };
-// SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x;
-// lpr = lanes per row (4, 8, 16 or 32), picked by tune_spmv
+// SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x.
+// Schedule: lpr = lanes per row (4, 8, 16 or 32), or 1: one lane per row over
+// the row blocks row_blk[0..nblk] (spmv_row_blocks), staged in shared memory.
+struct SpmvPlan {
+  int lpr = 8;
+  const int32_t* row_blk = nullptr;  // device: nblk + 1 row offsets, then their nblk + 1 first nonzeros
+  int nblk = 0;
+};
+std::vector<int32_t> spmv_row_blocks(const std::vector<int32_t>& rowptr);
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
-                 const double* x, double* y, const double* r, int mode, int lpr,
+                 const double* x, double* y, const double* r, int mode, const SpmvPlan& plan,
                  cudaStream_t s);
-// the fastest lanes-per-row schedule for this matrix, measured on the device
-// (cached per structure for the life of the process)
+// the fastest schedule (lpr) for this matrix, measured on the device with the
+// L2 evicted before each launch (cached per structure for the life of the
+// process); row_blk / nblk: its row blocks on the device (NULL: not a candidate)
 int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
               const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
-              cudaStream_t s);
+              const int32_t* row_blk, int nblk, cudaStream_t s);
 
 // ---- dense subdomain blocks (templated on the factor type T = double | float)
 // Device view of a level's tile envelopes (see msp_internal.h).

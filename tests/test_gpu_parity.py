@@ -620,9 +620,49 @@ def test_spmv_schedules_are_tuned_and_stable(P, torch):
     for l in range(len(levels)):
         a, b = h1.info(l)["spmv_lanes"], h2.info(l)["spmv_lanes"]
         assert a == b
-        assert a[0] in (4, 8, 16, 32)
+        assert a[0] in (1, 4, 8, 16, 32)
         if l + 1 < len(levels):
-            assert a[1] in (4, 8, 16, 32) and a[2] in (4, 8, 16, 32)
+            assert a[1] in (1, 4, 8, 16, 32) and a[2] in (1, 4, 8, 16, 32)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_every_spmv_schedule_matches_the_oracle(P, orc, torch, lanes, monkeypatch):
+    """Each SpMV schedule, fixed through MSP_SPMV_LANES, on J, P and P^T of
+    every level (1: one lane per row over shared-memory row blocks), and a
+    whole solve with it."""
+    monkeypatch.setenv("MSP_SPMV_LANES", str(lanes))
+    levels, w = workload("cube16_3lvl")
+    mu = syn.mu_draw(7)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    h = make_hierarchy(levels, w, P)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    m = P.msp
+    rng = np.random.default_rng(31)
+    dev = lambda a: torch.tensor(a, device="cuda")  # noqa: E731
+    for l in range(len(levels)):
+        lv = h.info(l)["spmv_lanes"]
+        assert lv[0] == lanes and (l + 1 == len(levels) or lv[1] == lv[2] == lanes)
+        x = rng.normal(size=o.n[l])
+        y = torch.zeros(o.n[l], dtype=torch.float64, device="cuda")
+        inst.apply_op(m.MSP_OP_SPMV, l, dev(x), y)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), o.spmv(x, l)) <= 1e-14
+        if l + 1 < len(levels):
+            xc = rng.normal(size=o.n[l + 1])
+            yf = torch.zeros(o.n[l], dtype=torch.float64, device="cuda")
+            inst.apply_op(m.MSP_OP_INTERP, l, dev(xc), yf)
+            yc = torch.zeros(o.n[l + 1], dtype=torch.float64, device="cuda")
+            inst.apply_op(m.MSP_OP_RESTRICT, l, dev(x), yc)
+            torch.cuda.synchronize()
+            assert rel(yf.cpu().numpy(), o.interp(xc, l)) <= 1e-14
+            assert rel(yc.cpu().numpy(), o.restrict(x, l)) <= 1e-14
+    xs = torch.zeros(o.n[0], dtype=torch.float64, device="cuda")
+    st = inst.solve(xs, rtol=1e-10)
+    xo, _ = o.fgmres(rtol=1e-10, restart=w["restart"])
+    assert st["status"] == 0 and rel(xs.cpu().numpy(), xo) <= 1e-7
 
 
 def test_results_reproducible_bitwise(P, torch):

@@ -350,43 +350,48 @@ __device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, A
   }
 }
 
-// Multi-launch form (levels with few, large blocks): every panel tile is
-// split into four CTAs of 16 rows each, so that a step spreads over more SMs.
-// Thread t owns row 16q + (t & 15) and the columns g, 31-g, 32+g, 63-g,
-// g = t >> 4 (column c needs the products over m <= c; this pairing gives
-// every lane nearly the same loop length).
+// Multi-launch form (levels with few, large blocks, the coarsest chain):
+// every panel tile is split into kStepSplit CTAs of kStepRows rows, so that
+// a step spreads over more SMs.  Thread t owns row kStepRows*q + (t %
+// kStepRows) and the columns g and 63 - g, g = t / kStepRows (column c needs
+// the products over m <= c: the pair has 65 in all, the same for every
+// thread); the loop runs over [0, g] with both columns and (g, 63 - g] with
+// the second only, so no FMA is issued for an entry of X^T that is zero.
+constexpr int kStepSplit = 8, kStepRows = 64 / kStepSplit;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k, int off) {
   using AT = typename Acc<T>::type;
   const int p = order[blockIdx.y];
-  const int i = k + 1 + off + (blockIdx.x >> 2), q = blockIdx.x & 3;
+  const int i = k + 1 + off + blockIdx.x / kStepSplit, q = blockIdx.x % kStepSplit;
   if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
-  AT* A = reinterpret_cast<AT*>(smraw);   // [16][65] rows of the panel tile
-  AT* Xt = A + 16 * 65;                   // [64][64] X^T (upper, unit diagonal)
+  AT* A = reinterpret_cast<AT*>(smraw);   // [kStepRows][65] rows of the panel tile
+  AT* Xt = A + kStepRows * 65;            // [64][64] X^T (upper, unit diagonal)
   AT* Dinv = Xt + 64 * 64;                // [64]
   const T* dtile = fac + tile_at(E, p, k, k);
-  T* ptile = fac + tile_at(E, p, i, k) + q * 16 * 64;
+  T* ptile = fac + tile_at(E, p, i, k) + q * kStepRows * 64;
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     const int r = e >> 6, c = e & 63;
     Xt[e] = (r < c) ? (AT)dtile[e] : (r == c ? AT(1) : AT(0));
     if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
-    if (e < 16 * 64) A[r * 65 + c] = (AT)ptile[e];
+    if (e < kStepRows * 64) A[r * 65 + c] = (AT)ptile[e];
   }
   __syncthreads();
-  const int r = tid & 15, g = tid >> 4;
-  const int cc[4] = {g, 31 - g, 32 + g, 63 - g};
-  AT w[4] = {0, 0, 0, 0};
-  for (int m = 0; m <= 63 - g; ++m) {
+  const int r = tid % kStepRows, g = tid / kStepRows;  // g = 0 .. 31
+  const int c1 = 63 - g;
+  AT w0 = 0, w1 = 0;
+  int m = 0;
+  for (; m <= g; ++m) {
     const AT a = A[r * 65 + m];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (m <= cc[u]) w[u] = fma(a, Xt[m * 64 + cc[u]], w[u]);
+    w0 = fma(a, Xt[m * 64 + g], w0);
+    w1 = fma(a, Xt[m * 64 + c1], w1);
   }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) ptile[r * 64 + cc[u]] = (T)(w[u] * Dinv[cc[u]]);
+  for (; m <= c1; ++m) w1 = fma(A[r * 65 + m], Xt[m * 64 + c1], w1);
+  ptile[r * 64 + g] = (T)(w0 * Dinv[g]);
+  ptile[r * 64 + c1] = (T)(w1 * Dinv[c1]);
 }
 
 // -------------------------------------------------------- trailing update
@@ -458,16 +463,17 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
     }
 }
 
-// Multi-launch form: every pair is split into four CTAs of 16 output rows;
-// thread t owns row 16q + (t >> 4) and the 4 columns 4 (t & 15) .. +3 (on a
-// diagonal pair only those on or below the diagonal).
+// Multi-launch form: every pair is split into kStepSplit CTAs of kStepRows
+// output rows; warp w owns row kStepRows*q + w and lane l the columns 2l and
+// 2l + 1 (on a diagonal pair only those on or below the diagonal).
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k, int pair0) {
   using AT = typename Acc<T>::type;
+  static_assert(kStepRows * 32 == 256, "one warp per output row");
   const int p = order[blockIdx.y];
   const int rem = E.last[E.trow[p] + k] - k;
-  const int pair = pair0 + (blockIdx.x >> 2), q = blockIdx.x & 3;
+  const int pair = pair0 + blockIdx.x / kStepSplit, q = blockIdx.x % kStepSplit;
   if (pair >= rem * (rem + 1) / 2) return;
   int a, b;
   pair_of(pair, a, b);
@@ -475,37 +481,32 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
   const bool diagonal = (i == j);
   extern __shared__ unsigned char smraw[];
   constexpr int LD = 65;  // odd stride: the transposed stores spread over the banks
-  AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][16] = L_ik[16q + r][m] * d_m
-  AT* Lt = Wt + 64 * 16;                  // [64 m][LD] = L_jk[c][m]
+  AT* Wt = reinterpret_cast<AT*>(smraw);  // [64 m][kStepRows] = L_ik[kStepRows q + r][m] * d_m
+  AT* Lt = Wt + 64 * kStepRows;           // [64 m][LD] = L_jk[c][m]
   const T* dt = fac + tile_at(E, p, k, k);
-  const T* li = fac + tile_at(E, p, i, k) + q * 16 * 64;
+  const T* li = fac + tile_at(E, p, i, k) + q * kStepRows * 64;
   const T* lj = fac + tile_at(E, p, j, k);
-  T* out = fac + tile_at(E, p, i, j) + q * 16 * 64;
+  T* out = fac + tile_at(E, p, i, j) + q * kStepRows * 64;
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     const int r = e >> 6, m = e & 63;
     Lt[m * LD + r] = (AT)lj[e];
-    if (e < 16 * 64) Wt[m * 16 + r] = (AT)li[e] * (AT)dt[m * 65];
+    if (e < kStepRows * 64) Wt[m * kStepRows + r] = (AT)li[e] * (AT)dt[m * 65];
   }
   __syncthreads();
-  const int r = tid >> 4, c0 = (tid & 15) * 4;
-  const int rg = 16 * q + r;  // row inside the tile
+  const int r = tid >> 5, c0 = (tid & 31) * 2;
+  const int rg = kStepRows * q + r;  // row inside the tile
   if (diagonal && c0 > rg) return;
-  AT acc[4] = {0, 0, 0, 0};
+  AT acc0 = 0, acc1 = 0;
 #pragma unroll 8
   for (int m = 0; m < T64; ++m) {
-    const AT av = Wt[m * 16 + r];
-#pragma unroll
-    for (int y = 0; y < 4; ++y) acc[y] = fma(av, Lt[m * LD + c0 + y], acc[y]);
+    const AT av = Wt[m * kStepRows + r];
+    acc0 = fma(av, Lt[m * LD + c0], acc0);
+    acc1 = fma(av, Lt[m * LD + c0 + 1], acc1);
   }
-#pragma unroll
-  for (int y = 0; y < 4; ++y) {
-    const int c = c0 + y;
-    if (!diagonal || c <= rg) {
-      T* o = out + r * 64 + c;
-      *o = (T)((AT)*o - acc[y]);
-    }
-  }
+  T* o = out + r * 64 + c0;
+  o[0] = (T)((AT)o[0] - acc0);
+  if (!diagonal || c0 + 1 <= rg) o[1] = (T)((AT)o[1] - acc1);
 }
 
 // ------------------------------------------------- whole-block factorisation
@@ -1139,12 +1140,12 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int off, int max_rows, cudaStream_t s) {
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (16 * 65 + 64 * 64 + 64) * sizeof(AT);
+  size_t smem = (kStepRows * 65 + 64 * 64 + 64) * sizeof(AT);
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_panel<T><<<dim3(4 * max_rows, nactive), 256, smem, s>>>(fac, E, order, k, off);
+  k_ldlt_panel<T><<<dim3(kStepSplit * max_rows, nactive), 256, smem, s>>>(fac, E, order, k, off);
 }
 
 template <typename T>
@@ -1152,12 +1153,12 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int pair0, int max_pairs, cudaStream_t s) {
   if (nactive <= 0 || max_pairs <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (64 * 16 + 64 * 65) * sizeof(AT);
+  size_t smem = (64 * kStepRows + 64 * 65) * sizeof(AT);
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_trail<T><<<dim3(4 * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k, pair0);
+  k_ldlt_trail<T><<<dim3(kStepSplit * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k, pair0);
 }
 
 namespace {

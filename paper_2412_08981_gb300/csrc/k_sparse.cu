@@ -442,10 +442,10 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
 // Autotuner of the SpMV schedule: lanes per row 4, 8, 16, 32, or one lane
 // per row over shared-memory-staged row blocks (1).  Every candidate is timed
 // with CUDA events on the matrix itself (zero values, zero x: the memory
-// traffic and the schedule are those of the real products), one launch at a
-// time after the L2 has been evicted (a 256 MB read), as in the solve, where
-// the subdomain solves stream gigabytes between two products; the fastest
-// total is kept.  The choice is cached per structure (rows, nnz, hash of
+// traffic and the schedule are those of the real products), each launch after
+// the L2 has been evicted (a 256 MB read), as in the solve, where the
+// subdomain solves stream gigabytes between two products; the fastest is
+// kept.  The choice is cached per structure (rows, nnz, hash of
 // rowptr and col) for the life of the process, so that identical matrices
 // always get the same schedule (and bitwise the same sums).
 int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
@@ -485,24 +485,29 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // the event clock ticks in microseconds: a sequence of (eviction, launch)
+    // pairs is timed against the same sequence without the launches
+    constexpr int kReps = 8;
+    auto seq = [&](const SpmvPlan* plan) {
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < kReps; ++rep) {
+        k_touch<<<1024, 256, 0, s>>>(flush, nflush, flush + nflush);
+        if (plan) launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, *plan, s);
+      }
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return ms;
+    };
     float best_ms = 1e30f;
     for (int lpr : {1, 4, 8, 16, 32}) {
       const SpmvPlan plan{lpr, row_blk, nblk};
       if (lpr == 1 && !row_blk) continue;
       launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);  // warm-up
-      float tot = 0;
-      for (int rep = 0; rep < 5; ++rep) {
-        k_touch<<<1024, 256, 0, s>>>(flush, nflush, flush + nflush);
-        cudaEventRecord(e0, s);
-        launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        tot += ms;
-      }
-      if (tot < best_ms) {
-        best_ms = tot;
+      const float t = seq(&plan) - seq(nullptr);
+      if (t < best_ms) {
+        best_ms = t;
         best = lpr;
       }
     }

@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-mls", action="store_true",
                     help="skip the MLS-transfer variant (Section 3.2) of the same workload")
+    ap.add_argument("--no-precision-study", action="store_true",
+                    help="skip the 96^3 L-shaped precision study (FP64 / FP32 / BF16 factors)")
     ap.add_argument("--no-elastic", action="store_true",
                     help="skip the linear-elasticity (three fields per vertex) object")
     ap.add_argument("--no-ilu", action="store_true",
@@ -420,6 +422,71 @@ def run_msp(args):
         h.close()
         return out
 
+    def measure_precision_study(steps):
+        """The precision study: the 96^3 L-shaped domain, four levels, 2048
+        subdomains, k spanning 1e-2 .. 1e2, FGMRES to rtol 1e-10, with FP64,
+        FP32 and BF16 subdomain factors.  Per precision: solves/s over
+        `steps` parameters (events on the instance stream), iterations, and
+        the relative error of the parameter-0 solution against the FP64
+        oracle's (a seeded sample of it, tests/golden/lshape96_4lvl_oracle.txt,
+        written from the oracle alone by tests/golden/make_lshape96.py)."""
+        lv, wl = syn.workload("lshape96_4lvl")
+        kl = dict(delta=wl["delta"], nu_pre=wl["nu"], nu_post=wl["nu"], restart=wl["restart"],
+                  coef=wl["coef"], wave=syn.wave_vectors(), scale=wl["scale"], load=wl["load"])
+        gold = os.path.join(ROOT, "tests", "golden", "lshape96_4lvl_oracle.txt")
+        gi, gv, gmeta = [], [], {}
+        if os.path.exists(gold):
+            with open(gold) as fh:
+                for line in fh:
+                    if line.startswith("#"):
+                        continue
+                    a, b = line.split()
+                    if a.isdigit():
+                        gi.append(int(a))
+                        gv.append(float(b))
+                    else:
+                        gmeta[a] = float(b)
+        gi, gv = np.array(gi, np.int64), np.array(gv)
+        out = {"workload": "lshape96_4lvl", "dofs": lv[0].n_nodes, "subdomains_level0": None,
+               "rtol": wl["rtol"], "oracle_iterations": int(gmeta["iterations"]) if gmeta else None}
+        x64 = None
+        for prec in ("f64", "f32", "bf16"):
+            h = P.Hierarchy(lv, precision=prec, **kl)
+            out["subdomains_level0"] = h.info(0)["n_sub"]
+            inst = h.assemble(mu_of(0), stream=stream)
+            x = torch.zeros(h.n_dofs(0), dtype=torch.float64, device="cuda")
+            its = []
+            for i in range(2):  # warm-up (the second factorisation is captured as a graph)
+                inst.reassemble(mu_of(100 + i))
+                inst.factor()
+                inst.solve(x, rtol=wl["rtol"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                inst.reassemble(mu_of(i))
+                inst.factor()
+                its.append(inst.solve(x, rtol=wl["rtol"])["iterations"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            inst.reassemble(mu_of(0))
+            inst.factor()
+            st = inst.solve(x, rtol=wl["rtol"])
+            xv = x.cpu().numpy()
+            e = {"value": steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                 "iterations_mean": float(np.mean(its)), "iterations_param0": st["iterations"]}
+            if gi.size:
+                e["rel_err_vs_oracle_sample"] = float(np.linalg.norm(xv[gi] - gv) / np.linalg.norm(gv))
+            if x64 is None:
+                x64 = xv
+            else:
+                e["rel_diff_vs_f64_solution"] = float(np.linalg.norm(xv - x64) / np.linalg.norm(x64))
+            out[prec] = e
+            inst.close()
+            h.close()
+        return out
+
     def measure_serving(nreq, rate):
         """Poisson arrivals of seeded mu over two resident hierarchies (32^3 and
         64^3, FP32 subdomain factors), served by msp_submit/msp_poll."""
@@ -536,6 +603,9 @@ def run_msp(args):
                              float(np.linalg.norm(r["x"] - ref) / np.linalg.norm(ref)),
                          "stage_ms_host": r["stage_ms"],
                          "transfer_ms_per_solve": r["kernel_ms"].get("transfer", 0.0)}
+    study = None
+    if not args.no_precision_study and args.precision == "f64" and world == 1:
+        study = measure_precision_study(max(2, min(args.steps, 4)))
     elastic = None
     if not args.no_elastic and args.precision == "f64":
         # the multi-field case: three displacement fields per vertex
@@ -642,6 +712,8 @@ def run_msp(args):
         line["hbm_kernels"] = hbm
     if elastic:
         line["elasticity"] = elastic
+    if study:
+        line["precision_study"] = study
     if literal:
         line["paper_literal"] = literal
     if serving:

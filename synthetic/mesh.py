@@ -168,6 +168,12 @@ WORKLOADS = {
     # three-level plain FP64, 64^3 -> 32^3 -> 16^3, 512 boxes per RAS level, overlap 2
     "cube64_3lvl": dict(ns=(64, 32, 16), parts=((8, 8, 8), (8, 8, 8)), delta=2, nu=2,
                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
+    # precision study: L-shaped domain (unit cube minus [0.5,1]^3), 96^3 with
+    # 48^3/24^3/12^3 coarse levels, 2048 subdomains of 294-1320 DoFs on the
+    # finest level, k spanning 1e-2 .. 1e2 (s = 1.15: |sum_j 0.5 mu_j cos| <= 4),
+    # FGMRES to rtol 1e-10
+    "lshape96_4lvl": dict(ns=(96, 48, 24, 12), parts=((16, 16, 9), (8, 8, 8), (4, 4, 4)), lshape=True,
+                          delta=2, nu=2, coef="cosexp", scale=1.15, load="one", rtol=1e-10, restart=30),
     # linear elasticity (three displacement fields per vertex, Poisson ratio
     # 0.3, unit body force along -z): parity case with blocks of ~1500 DoFs
     "elast12_3lvl": dict(ns=(12, 6, 3), parts=((2, 2, 2), (2, 2, 2)), delta=1, nu=2,

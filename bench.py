@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-mls", action="store_true",
                     help="skip the MLS-transfer variant (Section 3.2) of the same workload")
+    ap.add_argument("--no-hbm", action="store_true",
+                    help="skip the per-launch HBM figures of the fine-level SpMV and transfers")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the 96^3 L-shaped precision study (FP64 / FP32 / BF16 factors)")
     ap.add_argument("--no-elastic", action="store_true",
@@ -545,7 +547,7 @@ def run_msp(args):
                 "timing": "host wall clock from the first arrival to the last completion"}
 
     res = measure(args.precision, args.steps, args.warmup)
-    hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 else None
+    hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 and not args.no_hbm else None
     ms = max_over_ranks(res["ms"])
     value = whole_job_rate(args.steps, world, ms)
     mixed = None

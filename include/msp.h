@@ -18,8 +18,9 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream.  Work is enqueued on it; calls that return results to the host
  *     (msp_solve, msp_solve_host) synchronise it.
- *   - Vectors on a level hold one FP64 entry per mesh node (Dirichlet nodes
- *     included), in the node order of that level's msp_level_desc.
+ *   - Vectors on a level hold one FP64 entry per DoF (Dirichlet ones
+ *     included): per mesh node in the node order of that level's
+ *     msp_level_desc, three per node (DoF 3v + c) for linear elasticity.
  *   - Level 0 is the finest mesh M_0; level L-1 is the coarsest.
  */
 #ifndef MSP_H_
@@ -237,6 +238,24 @@ MSP_API void msp_free_instance(msp_instance* inst);
  * their unpivoted LU factors in symmetric form (unit lower L, D; U = D L^T),
  * plus the FP64 factor of the coarsest level's interior block. */
 MSP_API int msp_factor(msp_instance* inst);
+
+/* msp_factor of n instances at once (Eq. 6 for every block of every
+ * instance), for batches of parameters, possibly on hierarchies of different
+ * sizes.  The blocks of every level that msp_factor factors in one persistent
+ * launch (levels with many blocks) go into ONE persistent launch for the whole
+ * batch per factor type, balanced longest-first over the GPU; the other
+ * levels (the coarsest block's tile steps) run per instance on the
+ * instance's own streams, concurrently.  Each block's arithmetic is that of
+ * msp_factor, so the factors are bitwise the same.  insts: n distinct
+ * assembled instances (host array, not kept); stream: the stream of the
+ * batched launch (NULL: the first instance's), ordered after every
+ * instance's assembly; every instance's stream is ordered after the batch,
+ * and the call synchronises them all.  The launch's work lists are allocated
+ * and freed inside the call.  Errors: MSP_ERR_INVALID (no instances, one
+ * not assembled or listed twice, BF16 factors or ILU levels), MSP_ERR_OOM,
+ * MSP_ERR_CUDA, MSP_ERR_INTERNAL (a pivot; the instance stays unfactored).
+ * The profiling counters do not include the batched launch. */
+MSP_API int msp_factor_batch(msp_instance* const* insts, int n, void* stream);
 
 /* One application of the V-cycle preconditioner of Algorithm 2 (z = B^{-1} r)
  * with the fine->coarse transfer P^T, coarse->fine P and a direct coarsest

@@ -516,6 +516,22 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
 // separated by block barriers (global writes of one phase are visible to the
 // whole block in the next).  Used on levels with many blocks, where one launch
 // replaces three launches per tile step.
+// One whole block p of a level: every tile step in turn.
+template <typename T, typename AT>
+__device__ void factor_block(T* __restrict__ fac, const EnvDev& E, int p, AT* sm, int* info) {
+  const int NT = E.nt[p];
+  for (int k = 0; k < NT; ++k) {
+    const int R = E.last[E.trow[p] + k];
+    T* dt = fac + tile_at(E, p, k, k);
+    diag_tile<T, AT>(dt, sm, info);
+    for (int i = k + 1; i <= R; ++i) panel_tile<T, AT>(dt, fac + tile_at(E, p, i, k), sm);
+    for (int i = k + 1; i <= R; ++i)
+      for (int j = k + 1; j <= i; ++j)
+        trail_pair<T, AT>(dt, fac + tile_at(E, p, i, k), fac + tile_at(E, p, j, k), fac + tile_at(E, p, i, j),
+                          i == j, sm);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev E,
                                                      const int32_t* __restrict__ cta_ptr,
@@ -524,19 +540,26 @@ __global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   AT* sm = reinterpret_cast<AT*>(smraw);
+  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) factor_block<T, AT>(fac, E, cta_list[q], sm, info);
+}
+
+// The same over blocks of several levels and instances (uneven sizes): item
+// cta_list[q] names the factor storage, the level's envelope, the block and
+// the instance's status word.  Each block's arithmetic is exactly that of
+// k_ldlt_blocks.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_blocks_batch(const BlockItem* __restrict__ items,
+                                                           const int32_t* __restrict__ cta_ptr,
+                                                           const int32_t* __restrict__ cta_list) {
+  using AT = typename Acc<T>::type;
+  extern __shared__ unsigned char smraw[];
+  AT* sm = reinterpret_cast<AT*>(smraw);
+  __shared__ BlockItem it;  // the current item, read from shared memory where it is used
   for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
-    const int p = cta_list[q];
-    const int NT = E.nt[p];
-    for (int k = 0; k < NT; ++k) {
-      const int R = E.last[E.trow[p] + k];
-      T* dt = fac + tile_at(E, p, k, k);
-      diag_tile<T, AT>(dt, sm, info);
-      for (int i = k + 1; i <= R; ++i) panel_tile<T, AT>(dt, fac + tile_at(E, p, i, k), sm);
-      for (int i = k + 1; i <= R; ++i)
-        for (int j = k + 1; j <= i; ++j)
-          trail_pair<T, AT>(dt, fac + tile_at(E, p, i, k), fac + tile_at(E, p, j, k),
-                            fac + tile_at(E, p, i, j), i == j, sm);
-    }
+    __syncthreads();  // the previous item is finished with
+    if (threadIdx.x == 0) it = items[cta_list[q]];
+    __syncthreads();
+    factor_block<T, AT>(static_cast<T*>(it.fac), it.E, it.p, sm, it.info);
   }
 }
 
@@ -1283,6 +1306,25 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
   k_ldlt_blocks<T><<<grid, 256, smem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
 
+template <typename T>
+void launch_ldlt_blocks_batch(const BlockItem* items, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
+                              cudaStream_t s) {
+  using AT = typename Acc<T>::type;
+  if (grid < 1) return;
+  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
+  static std::once_flag attr;
+  std::call_once(attr, [&] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_batch<T>), smem); });
+  k_ldlt_blocks_batch<T><<<grid, 256, smem, s>>>(items, cta_ptr, cta_list);
+}
+
+template <typename T>
+int ldlt_blocks_batch_per_sm() {
+  using AT = typename Acc<T>::type;
+  const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);
+  static int n = resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_batch<T>), smem);
+  return n;
+}
+
 // CTAs of k_ldlt_blocks per SM, so that the persistent grid is exactly one wave.
 template <typename T>
 int ldlt_blocks_per_sm() {
@@ -1348,6 +1390,9 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
                                     bool, cudaStream_t);                                         \
   template int ras_slots<T>(int, bool);                                                          \
   template int ras_ctas_per_sm<T>(bool);                                                         \
+  template void launch_ldlt_blocks_batch<T>(const BlockItem*, const int32_t*, const int32_t*, int,    \
+                                            cudaStream_t);                                        \
+  template int ldlt_blocks_batch_per_sm<T>();                                                     \
   template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
                                       int*, cudaStream_t);                                       \
   template int ldlt_blocks_per_sm<T>();                                                           \

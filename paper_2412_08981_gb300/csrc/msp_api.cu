@@ -522,13 +522,17 @@ int assemble_all(msp_instance* I) {
 }
 
 template <typename T>
-void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = false) {
+void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = false, bool defer = false) {
   msp_hierarchy* h = I->h;
   DevLevel& D = h->dev[l];
   {
     ProfScope ps(I->prof, PK_EXTRACT, s, 2);
     launch_extract<T>(D.ext_pos, D.ext_nz, D.next, I->val[l], D.fac_elems, fac, s);
     ps.account((double)D.fac_elems * sizeof(T) + (double)D.next * (12 + sizeof(T) + 8), 0);
+  }
+  if (D.fac_blocks && defer) {  // the blocks go into a batched launch (msp_factor_batch)
+    cudaEventRecord(I->bev[l][0], s);
+    return;
   }
   if (D.fac_blocks) {
     ProfScope ps(I->prof, PK_LDLT_BLOCKS, s);
@@ -617,7 +621,7 @@ void factor_ilu(msp_instance* I, int l, T* fac, cudaStream_t s) {
 
 // Enqueues the whole factorisation on the instance stream (with forks onto
 // the auxiliary and bulk streams, all joined back).
-int enqueue_factor(msp_instance* I) {
+int enqueue_factor(msp_instance* I, bool defer = false) {
   msp_hierarchy* h = I->h;
   MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
   // The levels are independent: level 0 on the instance stream, the coarser
@@ -637,9 +641,9 @@ int enqueue_factor(msp_instance* I) {
       else
         factor_ilu<float>(I, l, static_cast<float*>(I->fac[l]), s);
     } else if (st == Store::F64) {
-      factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s);
+      factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s, false, defer);
     } else if (st == Store::F32) {
-      factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s);
+      factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s, false, defer);
     } else {
       factor_level<float>(I, l, I->work[l], s, /*tensor=*/true);
       ProfScope ps(I->prof, PK_EXTRACT, s);
@@ -1041,7 +1045,10 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
   I->bulk.assign(L, nullptr);
   I->bev.assign(L, {nullptr, nullptr, nullptr});
   for (int l = 0; l < L; ++l) {
-    if (h->dev[l].fac_blocks) continue;  // only the tile-step path uses them
+    if (h->dev[l].fac_blocks) {  // persistent levels: one event, "extracted", for msp_factor_batch
+      MSP_CUDA(cudaEventCreateWithFlags(&I->bev[l][0], cudaEventDisableTiming));
+      continue;
+    }
     MSP_CUDA(cudaStreamCreateWithFlags(&I->bulk[l], cudaStreamNonBlocking));
     for (auto& e : I->bev[l]) MSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
@@ -1281,6 +1288,117 @@ int msp_factor(msp_instance* I) {
   msp::g_last_error.clear();
   if (!I || !I->assembled) return fail(MSP_ERR_INVALID, "instance not assembled");
   return factor_all(I);
+}
+
+int msp_factor_batch(msp_instance* const* insts, int n, void* stream) {
+  msp::g_last_error.clear();
+  if (!insts || n < 1) return fail(MSP_ERR_INVALID, "no instances");
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = insts[i];
+    if (!I || !I->assembled) return fail(MSP_ERR_INVALID, "instance " + std::to_string(i) + " not assembled");
+    for (int j = 0; j < i; ++j)
+      if (insts[j] == I) return fail(MSP_ERR_INVALID, "an instance appears twice in the batch");
+    const msp_hierarchy* h = I->h;
+    for (int l = 0; l < (int)h->dev.size(); ++l)
+      if (h->dev[l].ilu || level_store(h, l) == Store::BF16)
+        return fail(MSP_ERR_INVALID, "batched factorisation takes FP64 / FP32 dense LU levels only");
+  }
+  cudaStream_t bs = stream ? static_cast<cudaStream_t>(stream) : insts[0]->stream;
+  // every level of every instance on the instance's own streams, except the
+  // blocks of the persistent levels, which are only extracted
+  std::vector<BlockItem> items[2];  // FP64, FP32
+  std::vector<int64_t> cost[2];
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = insts[i];
+    int rc = enqueue_factor(I, /*defer=*/true);
+    if (rc) return rc;
+    const msp_hierarchy* h = I->h;
+    for (int l = 0; l < (int)h->dev.size(); ++l) {
+      const DevLevel& D = h->dev[l];
+      if (!D.fac_blocks) continue;
+      MSP_CUDA(cudaStreamWaitEvent(bs, I->bev[l][0], 0));
+      const HostLevel& H = h->host[l];
+      const int g = level_store(h, l) == Store::F64 ? 0 : 1;
+      for (int p = 0; p < H.nsub; ++p) {
+        const int32_t* R = &H.tile_last[H.sub_trow[p]];
+        int64_t c = 0;
+        for (int k = 0; k < H.sub_nt[p]; ++k) {
+          const int64_t rem = R[k] - k;
+          c += 1 + rem + rem * (rem - 1) + rem;
+        }
+        items[g].push_back(BlockItem{I->fac[l], D.env, p, I->info});
+        cost[g].push_back(c);
+      }
+    }
+  }
+  // one persistent launch per factor type, longest blocks first over the GPU
+  int nsm = 0;
+  MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, insts[0]->h->device));
+  std::vector<void*> bufs;
+  auto cleanup = [&]() {
+    for (void* b : bufs) cudaFree(b);
+  };
+  for (int g = 0; g < 2; ++g) {
+    if (items[g].empty()) continue;
+    const int per_sm = g == 0 ? ldlt_blocks_batch_per_sm<double>() : ldlt_blocks_batch_per_sm<float>();
+    std::vector<int32_t> cptr, clist;
+    lpt_lists(cost[g], std::max(1, std::min((int)items[g].size(), nsm * per_sm)), cptr, clist);
+    void *d_items = nullptr, *d_ptr = nullptr, *d_list = nullptr;
+    const size_t bi = items[g].size() * sizeof(BlockItem), bp = cptr.size() * 4, bl = clist.size() * 4;
+    if (cudaMalloc(&d_items, bi) != cudaSuccess || cudaMalloc(&d_ptr, bp) != cudaSuccess ||
+        cudaMalloc(&d_list, bl) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_items);
+      cudaFree(d_ptr);
+      cleanup();
+      return fail(MSP_ERR_OOM, "device allocation failed for the batch work lists");
+    }
+    bufs.push_back(d_items);
+    bufs.push_back(d_ptr);
+    bufs.push_back(d_list);
+    if (cudaMemcpy(d_items, items[g].data(), bi, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_ptr, cptr.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_list, clist.data(), bl, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cleanup();
+      return fail(MSP_ERR_CUDA, "copying the batch work lists failed");
+    }
+    const int grid = (int)cptr.size() - 1;
+    if (g == 0)
+      launch_ldlt_blocks_batch<double>(static_cast<const BlockItem*>(d_items), static_cast<const int32_t*>(d_ptr),
+                                       static_cast<const int32_t*>(d_list), grid, bs);
+    else
+      launch_ldlt_blocks_batch<float>(static_cast<const BlockItem*>(d_items), static_cast<const int32_t*>(d_ptr),
+                                      static_cast<const int32_t*>(d_list), grid, bs);
+  }
+  cudaEvent_t done = nullptr;
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(done, bs) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(bs);
+  } else {
+    for (int i = 0; i < n; ++i) cudaStreamWaitEvent(insts[i]->stream, done, 0);
+  }
+  int rc = MSP_OK;
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = insts[i];
+    int hinfo = 0;
+    if (cudaMemcpyAsync(&hinfo, I->info, sizeof(int), cudaMemcpyDeviceToHost, I->stream) != cudaSuccess ||
+        cudaStreamSynchronize(I->stream) != cudaSuccess) {
+      rc = fail(MSP_ERR_CUDA, std::string("batched factorisation: ") + cudaGetErrorString(cudaGetLastError()));
+      continue;
+    }
+    I->prof.harvest();
+    if (hinfo) {
+      rc = fail(MSP_ERR_INTERNAL, "non-positive or non-finite pivot in a subdomain factor of instance " +
+                                      std::to_string(i));
+      I->factored = false;
+    } else {
+      I->factored = true;
+    }
+  }
+  cudaStreamSynchronize(bs);
+  if (done) cudaEventDestroy(done);
+  cleanup();
+  return rc;
 }
 
 int msp_apply(msp_instance* I, const double* r, double* z, void* stream) {

@@ -84,6 +84,20 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
                         int grid, int* info, cudaStream_t s);
 template <typename T>
 int ldlt_blocks_per_sm();
+// Blocks of several levels / instances in one persistent launch: item q is
+// block p of the level whose envelope is E, stored at fac (T*), status word
+// info; CTA b factors items cta_list[cta_ptr[b] .. cta_ptr[b+1]).
+struct BlockItem {
+  void* fac;
+  EnvDev E;
+  int32_t p;
+  int* info;
+};
+template <typename T>
+void launch_ldlt_blocks_batch(const BlockItem* items, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
+                              cudaStream_t s);
+template <typename T>
+int ldlt_blocks_batch_per_sm();
 // y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level),
 // on a cluster of 8 CTAs that split every tile row of both sweeps and
 // exchange partial results through distributed shared memory; Dirichlet

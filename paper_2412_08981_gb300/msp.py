@@ -112,6 +112,7 @@ EXPORTS = {
     "msp_reassemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "msp_free_instance": (None, [C.c_void_p]),
     "msp_factor": (C.c_int, [C.c_void_p]),
+    "msp_factor_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "msp_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "msp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(msp_stats)]),
     "msp_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -449,6 +450,13 @@ def multidot_noalloc(V, w, out, nv=None, ld=None, n=None, stream=None):
     ld = (n if V.dim() == 1 else int(V.stride(0))) if ld is None else int(ld)
     _check(load().msp_multidot_noalloc(_ptr(V), ld, nv, _ptr(w), n, _ptr(out),
                                        _stream_ptr(stream)))
+
+
+def factor_batch(instances, stream=None):
+    """msp_factor_batch: factor several assembled instances (possibly of
+    different hierarchies) with their persistent-level blocks in one launch."""
+    arr = (C.c_void_p * len(instances))(*[i.inst.value for i in instances])
+    _check(load().msp_factor_batch(arr, len(instances), _stream_ptr(stream) if stream is not None else None))
 
 
 def tile_first_of(h: "Hierarchy", level: int, sub: int) -> np.ndarray:

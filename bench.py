@@ -424,6 +424,79 @@ def run_msp(args):
         h.close()
         return out
 
+    def measure_batched_uneven(total=64, group=16):
+        """Batched uneven solves: `total` parameters, half on a 32^3 and half on a
+        48^3 hierarchy (FP32 factors, FP64 outer loop), `group` instances
+        resident at once (half of each).  Two ways, timed on the host wall
+        clock over the same parameters:
+          streams: every instance on its own stream and host thread, each
+            re-assembling, factoring and solving its share in turn;
+          batch: rounds of `group` parameters, each round re-assembled per
+            instance, factored with ONE msp_factor_batch (the persistent-level
+            blocks of all of them in one launch), then solved concurrently."""
+        import threading
+        hs = []
+        for name in ("cube32b_3lvl", "cube48_3lvl"):
+            lv, wl = syn.workload(name)
+            kk = dict(delta=wl["delta"], nu_pre=wl["nu"], nu_post=wl["nu"], restart=wl["restart"],
+                      coef=wl["coef"], wave=syn.wave_vectors(), scale=wl["scale"], load=wl["load"])
+            hs.append(P.Hierarchy(lv, precision="f32", **kk))
+        streams = [torch.cuda.Stream() for _ in range(group)]
+        insts = [hs[b % 2].assemble(mu_of(0), stream=streams[b]) for b in range(group)]
+        xs = [torch.zeros(hs[b % 2].n_dofs(0), dtype=torch.float64, device="cuda") for b in range(group)]
+        bstream = torch.cuda.Stream()
+        out = {"hierarchies": ["cube32b_3lvl (35,937 nodes, 125 subdomains)", "cube48_3lvl (117,649 nodes, 343)"],
+               "factor_precision": "f32", "solves": total, "resident_instances": group, "rtol": args.rtol}
+
+        errs = []
+
+        def run_threads(worker, count):
+            th = [threading.Thread(target=worker, args=(b,)) for b in range(count)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            if errs:
+                raise errs[0]
+
+        def streams_way(lo, hi):
+            def worker(b):
+                try:
+                    for i in range(lo + b, hi, group):
+                        insts[b].reassemble(mu_of(i))
+                        insts[b].factor()
+                        insts[b].solve(xs[b], rtol=args.rtol)
+                except Exception as e:
+                    errs.append(e)
+            run_threads(worker, group)
+
+        def batch_way(lo, hi):
+            for r0 in range(lo, hi, group):
+                for b in range(min(group, hi - r0)):
+                    insts[b].reassemble(mu_of(r0 + b))
+                P.msp.factor_batch(insts[:min(group, hi - r0)], stream=bstream)
+
+                def worker(b):
+                    try:
+                        insts[b].solve(xs[b], rtol=args.rtol)
+                    except Exception as e:
+                        errs.append(e)
+                run_threads(worker, min(group, hi - r0))
+
+        for name, fn in (("streams", streams_way), ("batch", batch_way)):
+            fn(5000, 5000 + group)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn(0, total)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            out[name] = {"value": total / wall, "unit": UNIT, "wall_s": round(wall, 3)}
+        for inst in insts:
+            inst.close()
+        for h in hs:
+            h.close()
+        return out
+
     def measure_precision_study(steps):
         """The precision study: the 96^3 L-shaped domain, four levels, 2048
         subdomains, k spanning 1e-2 .. 1e2, FGMRES to rtol 1e-10, with FP64,
@@ -605,6 +678,9 @@ def run_msp(args):
                              float(np.linalg.norm(r["x"] - ref) / np.linalg.norm(ref)),
                          "stage_ms_host": r["stage_ms"],
                          "transfer_ms_per_solve": r["kernel_ms"].get("transfer", 0.0)}
+    uneven = None
+    if args.batch > 0 and args.precision == "f64" and world == 1:
+        uneven = measure_batched_uneven()
     study = None
     if not args.no_precision_study and args.precision == "f64" and world == 1:
         study = measure_precision_study(max(2, min(args.steps, 4)))
@@ -716,6 +792,8 @@ def run_msp(args):
         line["elasticity"] = elastic
     if study:
         line["precision_study"] = study
+    if uneven:
+        line["batched_uneven"] = uneven
     if literal:
         line["paper_literal"] = literal
     if serving:

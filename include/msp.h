@@ -18,6 +18,12 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream.  Work is enqueued on it; calls that return results to the host
  *     (msp_solve, msp_solve_host) synchronise it.
+ *   - Threads: different instances (of one hierarchy or several) may be used
+ *     from different host threads at once, also when they share a stream
+ *     (their work is then serialised on it).  One instance is used by one
+ *     thread at a time.  A hierarchy is read-only after msp_load_hierarchy
+ *     and may be shared by all threads; msp_free_hierarchy runs after its
+ *     instances are freed.
  *   - Vectors on a level hold one FP64 entry per DoF (Dirichlet ones
  *     included): per mesh node in the node order of that level's
  *     msp_level_desc, three per node (DoF 3v + c) for linear elasticity.

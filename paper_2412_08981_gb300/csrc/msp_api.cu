@@ -180,6 +180,7 @@ struct msp_instance {
   double* xb = nullptr;  // device buffers used by msp_solve_host
   double* hpin = nullptr;  // pinned host staging
   cudaStream_t aux[2] = {nullptr, nullptr};  // coarser levels factor concurrently
+  cudaStream_t cap = nullptr;  // private origin stream of the factorisation's graph capture
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   // per level, for the tile-step factorisation: the stream of the work off
   // the critical chain, and its events (diag done, critical panel done, bulk done)
@@ -619,20 +620,21 @@ void factor_ilu(msp_instance* I, int l, T* fac, cudaStream_t s) {
   ps.account((double)D.ilu_nnz * sizeof(T) * 5, D.ilu_flops);
 }
 
-// Enqueues the whole factorisation on the instance stream (with forks onto
-// the auxiliary and bulk streams, all joined back).
-int enqueue_factor(msp_instance* I, bool defer = false) {
+// Enqueues the whole factorisation on `s0` (the instance stream, or the
+// private stream a graph capture starts from), with forks onto the auxiliary
+// and bulk streams, all joined back.
+int enqueue_factor(msp_instance* I, cudaStream_t s0, bool defer = false) {
   msp_hierarchy* h = I->h;
-  MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), I->stream));
+  MSP_CUDA(cudaMemsetAsync(I->info, 0, sizeof(int), s0));
   // The levels are independent: level 0 on the instance stream, the coarser
   // ones on two auxiliary streams forked from it and joined back.  The
   // coarsest block (a long chain of small dependent launches) goes first, on
   // the high-priority stream.
   const int L = (int)h->dev.size();
-  MSP_CUDA(cudaEventRecord(I->fork, I->stream));
+  MSP_CUDA(cudaEventRecord(I->fork, s0));
   for (int a = 0; a < 2; ++a) MSP_CUDA(cudaStreamWaitEvent(I->aux[a], I->fork, 0));
   for (int l = L - 1; l >= 0; --l) {
-    cudaStream_t s = (l == 0) ? I->stream : (l == L - 1 ? I->aux[0] : I->aux[1]);
+    cudaStream_t s = (l == 0) ? s0 : (l == L - 1 ? I->aux[0] : I->aux[1]);
     const Store st = level_store(h, l);
     const DevLevel& D = h->dev[l];
     if (D.ilu) {
@@ -653,7 +655,7 @@ int enqueue_factor(msp_instance* I, bool defer = false) {
   }
   for (int a = 0; a < 2; ++a) {
     MSP_CUDA(cudaEventRecord(I->join[a], I->aux[a]));
-    MSP_CUDA(cudaStreamWaitEvent(I->stream, I->join[a], 0));
+    MSP_CUDA(cudaStreamWaitEvent(s0, I->join[a], 0));
   }
   MSP_CUDA(cudaGetLastError());
   return MSP_OK;
@@ -664,15 +666,19 @@ int enqueue_factor(msp_instance* I, bool defer = false) {
 // hundreds of kernels, and no host gaps in the coarsest block's chain).  The
 // graph is used only while no kernel class is being timed; the per-class
 // launch, byte and flop counts of one factorisation are added per replay.
+// The capture starts from the instance's private stream `cap`, which no other
+// instance or host thread can enqueue on, so launches of other threads on the
+// instance stream (a stream several instances share) are never captured and
+// never invalidate the capture; the graph then runs on the instance stream.
 int factor_all(msp_instance* I) {
   const bool graph_ok = I->prof.mask == 0;
   if (graph_ok && !I->fac_graph && I->fac_calls >= 1) {
     msp_kernel_profile before[PK_COUNT];
     std::memcpy(before, I->prof.c, sizeof(before));
     cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const int rc = enqueue_factor(I);
-      const cudaError_t ec = cudaStreamEndCapture(I->stream, &g);
+    if (cudaStreamBeginCapture(I->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rc = enqueue_factor(I, I->cap);
+      const cudaError_t ec = cudaStreamEndCapture(I->cap, &g);
       if (rc == MSP_OK && ec == cudaSuccess && g &&
           cudaGraphInstantiate(&I->fac_graph, g, 0) == cudaSuccess) {
         for (int k = 0; k < PK_COUNT; ++k) {
@@ -697,7 +703,7 @@ int factor_all(msp_instance* I) {
       I->prof.c[k].flops += I->fac_graph_counts[k].flops;
     }
   } else {
-    const int rc = enqueue_factor(I);
+    const int rc = enqueue_factor(I, I->stream);
     if (rc) return rc;
   }
   I->fac_calls++;
@@ -1042,6 +1048,7 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     MSP_CUDA(cudaEventCreateWithFlags(&I->join[a], cudaEventDisableTiming));
   }
   MSP_CUDA(cudaEventCreateWithFlags(&I->fork, cudaEventDisableTiming));
+  MSP_CUDA(cudaStreamCreateWithFlags(&I->cap, cudaStreamNonBlocking));
   I->bulk.assign(L, nullptr);
   I->bev.assign(L, {nullptr, nullptr, nullptr});
   for (int l = 0; l < L; ++l) {
@@ -1236,6 +1243,7 @@ int msp_assemble(msp_hierarchy* h, const double* mu, int n_mu, void* stream, msp
       if (I->join[a]) cudaEventDestroy(I->join[a]);
     }
     if (I->fork) cudaEventDestroy(I->fork);
+    if (I->cap) cudaStreamDestroy(I->cap);
     for (auto b : I->bulk)
       if (b) cudaStreamDestroy(b);
     for (auto& e : I->bev)
@@ -1268,6 +1276,7 @@ void msp_free_instance(msp_instance* I) {
     if (I->join[a]) cudaEventDestroy(I->join[a]);
   }
   if (I->fork) cudaEventDestroy(I->fork);
+  if (I->cap) cudaStreamDestroy(I->cap);
   for (auto b : I->bulk)
     if (b) cudaStreamDestroy(b);
   for (auto& e : I->bev)
@@ -1310,7 +1319,7 @@ int msp_factor_batch(msp_instance* const* insts, int n, void* stream) {
   std::vector<int64_t> cost[2];
   for (int i = 0; i < n; ++i) {
     msp_instance* I = insts[i];
-    int rc = enqueue_factor(I, /*defer=*/true);
+    int rc = enqueue_factor(I, I->stream, /*defer=*/true);
     if (rc) return rc;
     const msp_hierarchy* h = I->h;
     for (int l = 0; l < (int)h->dev.size(); ++l) {

@@ -168,6 +168,11 @@ WORKLOADS = {
     # three-level plain FP64, 64^3 -> 32^3 -> 16^3, 512 boxes per RAS level, overlap 2
     "cube64_3lvl": dict(ns=(64, 32, 16), parts=((8, 8, 8), (8, 8, 8)), delta=2, nu=2,
                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
+    # batched uneven solves: the 32^3 hierarchy of the batch, with enough
+    # subdomains (5x5x5) for its finest level to take the persistent
+    # factorisation (the 48^3 one is cube48_3lvl)
+    "cube32b_3lvl": dict(ns=(32, 16, 8), parts=((5, 5, 5), (3, 3, 3)), delta=2, nu=2,
+                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
     # precision study: L-shaped domain (unit cube minus [0.5,1]^3), 96^3 with
     # 48^3/24^3/12^3 coarse levels, 2048 subdomains of 294-1320 DoFs on the
     # finest level, k spanning 1e-2 .. 1e2 (s = 1.15: |sum_j 0.5 mu_j cos| <= 4),

@@ -96,3 +96,54 @@ def test_batch_refuses_bf16_and_repeats(P, torch):
     P.msp.factor_batch([a], stream=stream)  # a batch of one is msp_factor
     x = torch.zeros(h.n_dofs(0), dtype=torch.float64, device="cuda")
     assert a.solve(x, rtol=1e-10)["status"] == 0
+
+
+def test_instances_sharing_a_stream_across_threads(P, torch):
+    """Two instances bound to ONE stream, driven from two host threads at once
+    through reassemble / factor / solve, three parameters each: the second
+    factorisation of each is captured into a CUDA graph while the other
+    thread enqueues on the shared stream.  Solutions are bitwise those of
+    the same instances run one after the other."""
+    import threading
+    _, h = _hier(P, "cube20b_3lvl", "f64")
+    s = torch.cuda.Stream()
+    mus = [[syn.mu_draw(900 + 10 * t + i) for i in range(3)] for t in range(2)]
+    xs = [[torch.zeros(h.n_dofs(0), dtype=torch.float64, device="cuda") for _ in range(3)] for _ in range(2)]
+    torch.cuda.synchronize()  # the buffers exist before the other stream writes them
+    ref = []
+    for t in range(2):
+        inst = h.assemble(mus[t][0], stream=s)
+        out = []
+        for i, mu in enumerate(mus[t]):
+            inst.reassemble(mu)
+            inst.factor()
+            assert inst.solve(xs[t][i], rtol=1e-10)["status"] == 0
+            out.append(xs[t][i].cpu().numpy())
+        ref.append(out)
+        inst.close()
+    ys = [[torch.full_like(x, float("nan")) for x in row] for row in xs]
+    insts = [h.assemble(mus[t][0], stream=s) for t in range(2)]
+    torch.cuda.synchronize()
+    got, errs = [[None] * 3 for _ in range(2)], []
+
+    def worker(t):
+        try:
+            for i, mu in enumerate(mus[t]):
+                insts[t].reassemble(mu)
+                insts[t].factor()
+                st = insts[t].solve(ys[t][i], rtol=1e-10)  # synchronises the shared stream
+                got[t][i] = (st["status"], ys[t][i].cpu().numpy())
+        except Exception as e:  # reported on the main thread
+            errs.append(repr(e))
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errs, errs
+    for t in range(2):
+        for i in range(3):
+            assert got[t][i][0] == 0
+            np.testing.assert_array_equal(got[t][i][1], ref[t][i])
+    for i in insts:
+        i.close()

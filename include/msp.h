@@ -62,8 +62,17 @@ typedef enum msp_status {
  *   MSP_F64 : factorisation and solves in FP64
  *   MSP_F32 : factorisation, storage and solves in FP32
  *   MSP_BF16: factorisation in FP32, factors rounded (to nearest even) to BF16
- *             for storage; the solves read BF16 and accumulate in FP32 */
-typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1, MSP_BF16 = 2 } msp_precision;
+ *             for storage; the solves read BF16 and accumulate in FP32
+ *   MSP_F64_TC: FP64 factors and solves as MSP_F64; on levels factored in one
+ *             persistent launch, the panel and trailing products of every tile
+ *             step run on the BF16 tensor cores, exactly, by splitting each
+ *             operand row into eight 7-bit digits scaled to its largest entry
+ *             (Ozaki's scheme; 36 digit-pair products, exact FP32 group sums,
+ *             64-bit integer combination): every product entry is within a few
+ *             units of 2^-54 K max|a_r| max|b_c| of the exact one, the accuracy
+ *             class of an FP64 dot product.  Diagonal tiles and the tile steps
+ *             of the other levels stay on the FP64 pipe. */
+typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1, MSP_BF16 = 2, MSP_F64_TC = 3 } msp_precision;
 
 /* Coefficient family k(x; mu), evaluated at each tet centroid x_c:
  *   MSP_K_CONST : k = 1

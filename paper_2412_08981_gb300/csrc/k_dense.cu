@@ -696,6 +696,458 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
   if (warp == 0) tc::tmem_dealloc(taddr, kTcCols);
 }
 
+// The diagonal tile for the sliced kernel: the arithmetic of diag_tile, entry
+// by entry and in the same order (so the same bits), two columns per pass:
+//   P: for the rows r > c, the scaled column l0 = A_rc / d_c, the entries
+//      (r, c+1) after step c and, from them, l1 = A'_r,c+1 / d_c+1 (every
+//      thread forms d_c+1 = A'_c+1,c+1 and its reciprocal itself); row c+1 of
+//      X after step c;
+//   U: the two updates of every other entry of the trailing triangle and of
+//      X, fused (fma(-l1, .., fma(-l0, .., a))), a thread's entries loaded,
+//      updated and stored as a batch.
+// Half the barriers of one column per pass.  smem: (64*65 + 3*64) doubles.
+constexpr int kPairBatch = 4;
+
+__device__ void diag_tile_pair(double* __restrict__ tile, double* __restrict__ A, int* __restrict__ info) {
+  double* l0 = A + 64 * 65;  // [64]
+  double* l1 = l0 + 64;      // [64]
+  double* dinv = l1 + 64;    // [64] 1/d_c
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  __syncthreads();  // the shared buffer may still be read by a previous phase
+  for (int e = tid; e < TE; e += nthr) {
+    const int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (c <= r) ? tile[e] : 0.0;  // X starts as the identity (zeros above)
+  }
+  __syncthreads();
+  if (tid == 0) dinv[0] = rcp_newton(A[0]);
+  __syncthreads();
+  for (int c = 0; c < T64; c += 2) {
+    const int c1 = c + 1;
+    // ---- P
+    if (tid < T64) {
+      const int r = tid;
+      if (r > c) {
+        const double lc = A[r * 65 + c] * dinv[c];
+        l0[r] = lc;
+        // pivot d_c+1 after step c, formed by every thread the same way
+        const double lp = A[c1 * 65 + c] * dinv[c];
+        const double d1 = fma(-lp, A[c1 * 65 + c], A[c1 * 65 + c1]);
+        const double di1 = rcp_newton(d1);
+        if (r > c1) {
+          const double a1 = fma(-lc, A[c1 * 65 + c], A[r * 65 + c1]);
+          A[r * 65 + c1] = a1;
+          l1[r] = a1 * di1;
+        } else {  // r == c + 1: the pivot's own row
+          dinv[c1] = di1;
+          l1[c1] = d1;  // handed to U, which stores it on the diagonal
+        }
+      }
+    } else if (tid - T64 <= c) {  // row c+1 of X after step c: X_c+1,j (at A[j][c+1]), j <= c
+      const int j = tid - T64;
+      const double lp = A[c1 * 65 + c] * dinv[c];
+      const double xcj = (j == c) ? 1.0 : A[j * 65 + c];
+      A[j * 65 + c1] = fma(-lp, xcj, A[j * 65 + c1]);
+    }
+    __syncthreads();
+    // ---- U
+    const int m = T64 - 2 - c;        // rows c+2 .. 63
+    const int nA = m * (m + 1) / 2;   // trailing entries (r, s), c+2 <= s <= r
+    const int w = c + 2;              // X columns j <= c+1
+    const int nU = nA + m * w;
+    if (tid == 0) A[c1 * 65 + c1] = l1[c1];
+    for (int base = 0; base < nU; base += nthr * kPairBatch) {
+      int idx[kPairBatch];
+      double av[kPairBatch], b0[kPairBatch], b1[kPairBatch], f0[kPairBatch], f1[kPairBatch];
+#pragma unroll
+      for (int q = 0; q < kPairBatch; ++q) {
+        const int e = base + tid + q * nthr;
+        idx[q] = -1;
+        if (e >= nU) continue;
+        int r, s;
+        if (e < nA) {
+          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+          rr += ((rr + 1) * (rr + 2) / 2 <= e);
+          rr -= (rr * (rr + 1) / 2 > e);
+          r = c + 2 + rr;
+          s = c + 2 + (e - rr * (rr + 1) / 2);
+          idx[q] = r * 65 + s;
+          f0[q] = l0[r];
+          f1[q] = l1[r];
+          b0[q] = A[s * 65 + c];
+          b1[q] = A[s * 65 + c1];
+        } else {
+          const int x = e - nA, rr = x / w, j = x - rr * w;
+          r = c + 2 + rr;
+          idx[q] = j * 65 + r;  // X_rj at A[j][r]
+          f0[q] = (j <= c) ? l0[r] : 0.0;
+          f1[q] = l1[r];
+          b0[q] = (j == c) ? 1.0 : (j < c ? A[j * 65 + c] : 0.0);
+          b1[q] = (j == c1) ? 1.0 : A[j * 65 + c1];
+        }
+        av[q] = A[idx[q]];
+      }
+#pragma unroll
+      for (int q = 0; q < kPairBatch; ++q) {
+        if (idx[q] < 0) continue;
+        const double v = fma(-f1[q], b1[q], fma(-f0[q], b0[q], av[q]));
+        A[idx[q]] = v;
+        if (idx[q] == (c + 2) * 65 + (c + 2)) dinv[c + 2] = rcp_newton(v);  // the next pass's first pivot
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < T64) {
+    const double d = A[tid * 65 + tid];
+    if (!(d > 0.0) || !(d < 1e300)) atomicOr(info, 1);
+  }
+  for (int e = tid; e < TE; e += nthr) {  // L = W D^{-1}
+    const int r = e >> 6, c = e & 63;
+    if (c < r) A[r * 65 + c] *= dinv[c];
+  }
+  __syncthreads();
+  for (int e = tid; e < TE; e += nthr) tile[e] = A[(e >> 6) * 65 + (e & 63)];
+}
+
+// ------------------------- whole-block factorisation, FP64 by exact BF16 slices
+// FP64 factors whose GEMM-shaped products -- the panel W_ik = A_ik X^T and the
+// trailing update C_ij -= W_ik L_jk^T of every tile step -- run on the BF16
+// tensor cores without rounding error, by splitting the operands into digits
+// (the Ozaki scheme):
+//   * every row of an operand (K = 64 entries) gets the exponent e of its
+//     largest entry, |x| < 2^e, and becomes the integer m = round(x 2^(54-e)),
+//     |m| < 2^54;
+//   * m is written as eight balanced base-128 digits, m = sum_s d_s 128^(7-s),
+//     |d_0| <= 33, |d_s| <= 64 for s > 0: every digit is exact in BF16;
+//   * for one output block (128 rows x 64 columns) the digit products with
+//     s + t = g are summed by the tensor cores in FP32, group g in its own 64
+//     tensor-memory columns (8 groups: all 512).  Each product is below 2^12,
+//     a K = 64 sum below 2^18 and a group of at most 8 sums below 2^21, so every
+//     FP32 accumulation is exact;
+//   * the groups g = 0..7 are combined in 64-bit integers in units of
+//     2^(e_r + e_c - 56) (group g weighs 2^(46 - 7g); the last one is rounded
+//     to the unit) and converted to FP64 once.  The digit pairs with s + t > 7
+//     are left out: they are below 2^-54 of the bound K max|a_r| max|b_c|, as
+//     are the rounding of the operands to 54 bits and of the group-7 sum.
+// So each product entry is within a few units of 2^-54 K max|a_r| max|b_c| of
+// the exact sum: the accuracy class of an FP64 dot product.  The diagonal tile
+// (its L D L^T and X = L^-1, a sequential sweep: diag_tile_pair) stays on the
+// FP64 pipe.  One CTA of 512 threads per SM: 192 KB of digit slabs and all
+// 512 tensor-memory columns.
+constexpr int kOzDigits = 8;                               // digits per entry
+constexpr int kOzASlab = 128 * 64 * 2;                     // one 128 x 64 BF16 digit slab (A)
+constexpr int kOzBSlab = 64 * 64 * 2;                      // one 64 x 64 BF16 digit slab (B)
+constexpr int kOzBOff = kOzDigits * kOzASlab;              // 128 KB
+constexpr int kOzMetaOff = kOzBOff + kOzDigits * kOzBSlab; // 192 KB
+constexpr int kOzEA = kOzMetaOff;                          // int32 [128] row exponents of A
+constexpr int kOzEB = kOzEA + 128 * 4;                     // int32 [64] row exponents of B
+constexpr int kOzDk = kOzEB + 64 * 4;                      // double [64] D of the step
+constexpr int kOzDinv = kOzDk + 64 * 8;                    // double [64] 1 / D
+constexpr int kOzBar = kOzDinv + 64 * 8;                   // mbarrier, then the TMEM base slot
+constexpr int kOzSmem = kOzBar + 64;
+static_assert((64 * 65 + 3 * 64) * 8 <= kOzBOff, "the diagonal tile's scratch fits in the A slabs");
+
+// biased exponent field of x (0 for zero and subnormal numbers)
+__device__ __forceinline__ int oz_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// |m| = round(|x| 2^(54 - e)) < 2^54 for the row exponent e = emax - 1022
+// (emax: the largest biased exponent of the row); subnormal entries count as
+// zero.
+__device__ __forceinline__ unsigned long long oz_fixed_abs(double x, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;  // 53 bits
+  const int sh = e - emax + 1;                                                     // <= 1
+  if (sh >= 0) return mant << sh;
+  if (sh > -56) return (mant + (1ull << (-sh - 1))) >> (-sh);
+  return 0;
+}
+
+// One balanced base-128 digit of an FP32-exact integer v >= 0 (v < 2^22):
+// q = rint(v / 128) through the 1.5 * 2^23 offset, d = v - 128 q in [-64, 64].
+__device__ __forceinline__ float oz_peel(float& v) {
+  const float q = __fadd_rn(__fmaf_rn(v, 0.0078125f, 12582912.0f), -12582912.0f);
+  const float d = __fmaf_rn(-128.0f, q, v);
+  v = q;
+  return d;
+}
+
+// The eight balanced base-128 digits of |m| < 2^54, most significant first,
+// |d_0| <= 33, |d_s| <= 64: |m| is cut into three FP32-exact pieces (bits
+// 0..13, 14..34, 35..55, each read into FP32 through the 2^23 offset), whose
+// digits are peeled in FP32 with the carries going upward.  The digits are
+// small integers in FP32, so their BF16 form is the upper half of their bits.
+__device__ __forceinline__ void oz_digits(unsigned long long m, float (&d)[kOzDigits]) {
+  float v = __uint_as_float(0x4B000000u | ((uint32_t)m & 0x3FFFu)) - 8388608.0f;
+  d[7] = oz_peel(v);
+  d[6] = oz_peel(v);
+  v += __uint_as_float(0x4B000000u | ((uint32_t)(m >> 14) & 0x1FFFFFu)) - 8388608.0f;
+  d[5] = oz_peel(v);
+  d[4] = oz_peel(v);
+  d[3] = oz_peel(v);
+  v += __uint_as_float(0x4B000000u | (uint32_t)(m >> 35)) - 8388608.0f;
+  d[2] = oz_peel(v);
+  d[1] = oz_peel(v);
+  d[0] = v;
+}
+
+// Writes the digits of 8 consecutive K entries of one row into the 8 slabs
+// (the sign of an entry is the sign bit of each of its BF16 digits).
+__device__ __forceinline__ void oz_store8(unsigned char* slab0, int slab_bytes, int row, int k0,
+                                          const double (&x)[8], int emax) {
+  uint32_t w[kOzDigits][4];
+#pragma unroll
+  for (int u = 0; u < 8; u += 2) {
+    float d0[kOzDigits], d1[kOzDigits];
+    oz_digits(oz_fixed_abs(x[u], emax), d0);
+    oz_digits(oz_fixed_abs(x[u + 1], emax), d1);
+    const uint32_t sg = (x[u] < 0.0 ? 0x8000u : 0u) | (x[u + 1] < 0.0 ? 0x80000000u : 0u);
+#pragma unroll
+    for (int s = 0; s < kOzDigits; ++s)
+      w[s][u >> 1] = __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632) ^ sg;
+  }
+#pragma unroll
+  for (int s = 0; s < kOzDigits; ++s)
+    *reinterpret_cast<uint4*>(slab0 + s * slab_bytes + tc::kmajor_offset(row, k0)) =
+        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
+// A operand: rows 0..63 from tile t0, 64..127 from t1 (null: zeros), each
+// entry times dk[m] when dk is given (W = L D).  Four threads per row, 16 K
+// entries each (512 threads).
+__device__ void oz_split_a(unsigned char* sA, int* eA, const double* __restrict__ t0,
+                           const double* __restrict__ t1, const double* dk) {
+  const int tid = threadIdx.x, r = tid >> 2, kq = tid & 3;
+  const double* src = r < 64 ? t0 : t1;
+  double x[16];
+  int emax = 0;
+  if (src) {
+    const double* row = src + (r & 63) * 64 + kq * 16;
+#pragma unroll
+    for (int u = 0; u < 16; u += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(row + u);
+      x[u] = v.x;
+      x[u + 1] = v.y;
+    }
+    if (dk) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] *= dk[kq * 16 + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) emax = max(emax, oz_exp(x[u]));
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = 0.0;
+  }
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+  if (kq == 0) eA[r] = emax;
+#pragma unroll
+  for (int c8 = 0; c8 < 2; ++c8) {
+    double y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) y[u] = x[c8 * 8 + u];
+    oz_store8(sA, kOzASlab, r, kq * 16 + c8 * 8, y, emax);
+  }
+}
+
+// B operand (64 rows c, K = m): the tile t itself (B[c][m] = t[c][m]), or with
+// xmat the unit lower X of a factored diagonal tile, X[c][m] = t[m][c] for
+// m < c.  Eight threads per row, 8 K entries each (512 threads).
+__device__ void oz_split_b(unsigned char* sB, int* eB, const double* __restrict__ t, bool xmat) {
+  const int tid = threadIdx.x, c = tid >> 3, k8 = tid & 7;
+  double x[8];
+  int emax = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int m = k8 * 8 + u;
+    if (xmat) x[u] = m < c ? t[m * 64 + c] : (m == c ? 1.0 : 0.0);
+    else x[u] = t[c * 64 + m];
+    emax = max(emax, oz_exp(x[u]));
+  }
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+  if (k8 == 0) eB[c] = emax;
+  oz_store8(sB, kOzBSlab, c, k8 * 8, x, emax);
+}
+
+// V 2^(er + ec - 2100) in FP64, rounded to nearest even, for the biased row
+// exponents er, ec of the two operands: the integer sum in units of
+// 2^(e_r + e_c - 56), e = biased exponent - 1022.  Built from the bits: the
+// leading one of |V| gives the exponent, the next 52 bits (rounded) the
+// significand.  Results outside the normal range go through FP64 products.
+__device__ __forceinline__ double oz_to_double(long long V, int er, int ec) {
+  if (V == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)V & 0x8000000000000000ull;
+  unsigned long long a = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
+  const int lz = __clzll((long long)a);
+  a <<= lz;  // leading one at bit 63
+  unsigned long long mant = a >> 11;  // 53 bits, hidden one included
+  const unsigned long long rest = a & 0x7FFull;
+  mant += (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+  const int e = 63 - lz + er + ec - 2100 + 1023;  // biased exponent of the leading one
+  if (e < 1 || e > 2046) {  // 2^(er - 1050) 2^(ec - 1050); rows below 2^-994 count as zero
+    if (er <= 28 || ec <= 28) return 0.0;
+    return ((double)V * __longlong_as_double((long long)(er - 27) << 52)) *
+           __longlong_as_double((long long)(ec - 27) << 52);
+  }
+  // the hidden one carries into the exponent field (twice after a rounding carry)
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(e - 1) << 52) + mant)));
+}
+
+// Issues the 36 digit-pair products of one output block (s + t <= 7, group
+// s + t in tensor-memory columns 64 (s + t) ..) and commits them to `bar`.
+// One thread.  The first product of every group overwrites its columns.
+__device__ __forceinline__ void oz_issue(uint32_t taddr, const unsigned char* sA, const unsigned char* sB,
+                                         uint64_t* bar) {
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+  for (int s = 0; s < kOzDigits; ++s)
+    for (int t = 0; s + t < kOzDigits; ++t) {
+      const uint32_t d = taddr + (uint32_t)((s + t) * 64);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma_bf16(d, tc::sdesc(sA + s * kOzASlab + 256 * kk), tc::sdesc(sB + t * kOzBSlab + 256 * kk), idesc,
+                     (s > 0 || kk > 0) ? 1 : 0);
+    }
+  tc::commit(bar);
+}
+
+// The product of the slabs in shared memory for one output block: MMAs by
+// thread 0, a bounded wait, then the 64-bit integer sums of this thread's row
+// r = 32 (warp % 4) + lane over the 16 columns 16 (warp / 4) .., handed to
+// epi(r, q, V) before the block barrier that frees the slabs, the row
+// exponents and the tensor memory.  Returns the updated `failed`.
+template <typename Epi>
+__device__ __forceinline__ bool oz_product(uint32_t taddr, unsigned char* sm, uint64_t* bar, uint32_t& phase,
+                                           bool failed, int* info, Epi epi) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid == 0) oz_issue(taddr, sm, sm + kOzBOff, bar);
+  if (!tc::mbar_wait_bounded(bar, phase, failed ? 64 : (1L << 22))) {
+    failed = true;
+    if (lane == 0) atomicOr(info, 2);
+  }
+  phase ^= 1;
+  tc::fence_after();
+  const int qd = warp & 3, q = warp >> 2;
+  long long V[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) V[c] = 0;
+#pragma unroll
+  for (int g = 0; g < kOzDigits; g += 2) {
+    float v0[16], v1[16];
+    const uint32_t ta = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(g * 64 + 16 * q);
+    tc::tmem_ld16(ta, v0);
+    tc::tmem_ld16(ta + 64, v1);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      // the exact integer group sums (|v| < 2^22) through the 1.5 * 2^23
+      // offset; groups g and g + 1 joined in 32 bits (< 2^29), weight 2^(39 - 7g)
+      const int i0 = __float_as_int(v0[u] + 12582912.0f) - 0x4B400000;
+      const int i1 = __float_as_int(v1[u] + 12582912.0f) - 0x4B400000;
+      const int qv = i0 * 128 + i1;
+      if (g < kOzDigits - 2) V[u] += (long long)qv << (39 - 7 * g);
+      else V[u] += (long long)((qv + 4) >> 3);
+    }
+  }
+  epi(32 * qd + lane, q, V);
+  tc::fence_before();
+  __syncthreads();
+  return failed;
+}
+
+__global__ void __launch_bounds__(512, 1) k_ldlt_blocks_oz(double* __restrict__ fac, EnvDev E,
+                                                           const int32_t* __restrict__ cta_ptr,
+                                                           const int32_t* __restrict__ cta_list,
+                                                           int* __restrict__ info) {
+  extern __shared__ __align__(1024) unsigned char smoz[];
+  int* eA = reinterpret_cast<int*>(smoz + kOzEA);
+  int* eB = reinterpret_cast<int*>(smoz + kOzEB);
+  double* dk = reinterpret_cast<double*>(smoz + kOzDk);
+  double* dinv = reinterpret_cast<double*>(smoz + kOzDinv);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smoz + kOzBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smoz + kOzBar + 16);
+  const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
+  if (q0 >= q1) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(bar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int q = q0; q < q1; ++q) {
+    const int p = cta_list[q];
+    const int NT = E.nt[p];
+    for (int k = 0; k < NT; ++k) {
+      const int R = E.last[E.trow[p] + k];
+      double* dt = fac + tile_at(E, p, k, k);
+      diag_tile_pair(dt, reinterpret_cast<double*>(smoz), info);
+      if (R == k) continue;
+      __syncthreads();  // the factored diagonal tile is in global memory
+      if (tid < 64) {
+        const double d = dt[tid * 65];
+        dk[tid] = d;
+        dinv[tid] = 1.0 / d;
+      }
+      // panel: L_ik = (A_ik X^T) D^-1, tile rows two at a time
+      oz_split_b(smoz + kOzBOff, eB, dt, true);
+      for (int i0 = k + 1; i0 <= R; i0 += 2) {
+        oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
+                   nullptr);
+        failed = oz_product(taddr, smoz, bar, phase, failed, info, [&](int r, int h, long long(&V)[16]) {
+          const int ti = r < 64 ? i0 : i0 + 1;
+          if (ti > R) return;
+          const int er = eA[r];
+          double* out = fac + tile_at(E, p, ti, k) + (r & 63) * 64 + 16 * h;
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {
+            const int cc = 16 * h + c;
+            double2 o;
+            o.x = oz_to_double(V[c], er, eB[cc]) * dinv[cc];
+            o.y = oz_to_double(V[c + 1], er, eB[cc + 1]) * dinv[cc + 1];
+            *reinterpret_cast<double2*>(out + c) = o;
+          }
+        });
+      }
+      // trailing update: C_ij -= (L_ik D_k) L_jk^T, k < j <= i <= R; the
+      // digits of two rows of W = L D at a time, against every column tile j
+      // up to the second row (the rows i < j of a block are not written)
+      for (int i0 = k + 1; i0 <= R; i0 += 2) {
+        const int i1 = i0 + 1 <= R ? i0 + 1 : i0;
+        oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
+                   dk);
+        for (int j = k + 1; j <= i1; ++j) {
+          oz_split_b(smoz + kOzBOff, eB, fac + tile_at(E, p, j, k), false);
+          failed = oz_product(taddr, smoz, bar, phase, failed, info, [&](int r, int h, long long(&V)[16]) {
+            const int ti = r < 64 ? i0 : i0 + 1;
+            if (ti > R || ti < j) return;
+            const int rr = r & 63, er = eA[r];
+            double* out = fac + tile_at(E, p, ti, j) + rr * 64 + 16 * h;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int cc = 16 * h + c;
+              if (ti == j && cc > rr) continue;  // a diagonal tile keeps its upper part (X^T later)
+              out[c] -= oz_to_double(V[c], er, eB[cc]);
+            }
+          });
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
 // -------------------------------------------------------------- RAS solve
 // Persistent and warp-specialised.  Each CTA (one per SM) takes the
 // subdomains order[b], order[b + G], ... (largest first).  Warp 8 is the
@@ -1341,6 +1793,17 @@ void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, 
   std::call_once(attr, [] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_tc), kTcSmem); });
   k_ldlt_blocks_tc<<<grid, 256, kTcSmem, s>>>(fac, E, cta_ptr, cta_list, info);
 }
+
+void launch_ldlt_blocks_oz(double* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                           int grid, int* info, cudaStream_t s) {
+  if (grid < 1) return;
+  static std::once_flag attr;
+  std::call_once(attr, [] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_oz), kOzSmem); });
+  k_ldlt_blocks_oz<<<grid, 512, kOzSmem, s>>>(fac, E, cta_ptr, cta_list, info);
+}
+
+// k_ldlt_blocks_oz: one CTA per SM (its shared memory and all the tensor memory).
+int ldlt_blocks_oz_per_sm() { return 1; }
 
 // CTAs of k_ldlt_blocks_tc per SM: resident at once, and at most 512 / 128
 // (the tensor memory of an SM), so that no allocation ever waits.

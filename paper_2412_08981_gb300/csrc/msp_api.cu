@@ -206,7 +206,7 @@ enum class Store { F64, F32, BF16 };
 Store level_store(const msp_hierarchy* h, int l) {
   if (direct_level(h, l)) return Store::F64;
   if (h->host[l].ilu_fill >= 0)  // ILU levels: FP32 for either reduced precision (sparse sweeps, no tensor cores)
-    return h->opt.factor_precision == MSP_F64 ? Store::F64 : Store::F32;
+    return (h->opt.factor_precision == MSP_F64 || h->opt.factor_precision == MSP_F64_TC) ? Store::F64 : Store::F32;
   if (h->opt.factor_precision == MSP_F32) return Store::F32;
   if (h->opt.factor_precision == MSP_BF16) return Store::BF16;
   return Store::F64;
@@ -388,9 +388,10 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.fac_blocks = H.nsub >= std::max(2, nsm / 2);
     if (D.fac_blocks) {
       const Store fst = level_store(h, l);
-      const int per_sm = fst == Store::BF16  ? ldlt_blocks_tc_per_sm()
-                         : fst == Store::F32 ? ldlt_blocks_per_sm<float>()
-                                             : ldlt_blocks_per_sm<double>();
+      const int per_sm = fst == Store::BF16                    ? ldlt_blocks_tc_per_sm()
+                         : fst == Store::F32                   ? ldlt_blocks_per_sm<float>()
+                         : h->opt.factor_precision == MSP_F64_TC ? ldlt_blocks_oz_per_sm()
+                                                               : ldlt_blocks_per_sm<double>();
       for (int p = 0; p < H.nsub; ++p) {
         const int32_t* R = &H.tile_last[H.sub_trow[p]];
         int64_t c = 0;
@@ -479,7 +480,8 @@ int check_options(const msp_options& o) {
     return fail(MSP_ERR_INVALID, "nu out of range");
   if (o.restart < 1 || o.restart > 256) return fail(MSP_ERR_INVALID, "restart out of range");
   if (o.max_it < 1) return fail(MSP_ERR_INVALID, "max_it must be >= 1");
-  if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32 && o.factor_precision != MSP_BF16)
+  if (o.factor_precision != MSP_F64 && o.factor_precision != MSP_F32 && o.factor_precision != MSP_BF16 &&
+      o.factor_precision != MSP_F64_TC)
     return fail(MSP_ERR_INVALID, "unknown factor precision");
   if (o.transfer != MSP_TRANSFER_BARY && o.transfer != MSP_TRANSFER_MLS)
     return fail(MSP_ERR_INVALID, "unknown transfer");
@@ -540,6 +542,8 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
     if constexpr (std::is_same<T, float>::value) {
       if (tensor) launch_ldlt_blocks_tc(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
       else launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
+    } else if (h->opt.factor_precision == MSP_F64_TC) {
+      launch_ldlt_blocks_oz(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
     } else {
       launch_ldlt_blocks<T>(fac, D.env, D.fac_cta_ptr, D.fac_cta_list, D.fac_grid, I->info, s);
     }
@@ -1149,7 +1153,7 @@ int msp_load_hierarchy(const msp_level_desc* lv, int nlevels, const msp_options*
   }
   if (!h->host_only) {
     MSP_CUDA(cudaGetDevice(&h->device));
-    if (o->factor_precision == MSP_BF16) {  // the BF16 factorisation uses the tensor cores
+    if (o->factor_precision == MSP_BF16 || o->factor_precision == MSP_F64_TC) {  // these use the tensor cores
       rc = tensor_check(h->device);
       if (rc) return rc;
     }
@@ -1309,7 +1313,7 @@ int msp_factor_batch(msp_instance* const* insts, int n, void* stream) {
       if (insts[j] == I) return fail(MSP_ERR_INVALID, "an instance appears twice in the batch");
     const msp_hierarchy* h = I->h;
     for (int l = 0; l < (int)h->dev.size(); ++l)
-      if (h->dev[l].ilu || level_store(h, l) == Store::BF16)
+      if (h->dev[l].ilu || level_store(h, l) == Store::BF16 || h->opt.factor_precision == MSP_F64_TC)
         return fail(MSP_ERR_INVALID, "batched factorisation takes FP64 / FP32 dense LU levels only");
   }
   cudaStream_t bs = stream ? static_cast<cudaStream_t>(stream) : insts[0]->stream;

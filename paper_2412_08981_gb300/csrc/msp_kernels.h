@@ -112,6 +112,11 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
 void launch_ldlt_blocks_tc(float* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
                            int grid, int* info, cudaStream_t s);
 int ldlt_blocks_tc_per_sm();
+// FP64 factors with the panel and trailing products on the BF16 tensor cores
+// by exact digit slices (one CTA per SM); status bit 2 on an expired wait
+void launch_ldlt_blocks_oz(double* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list,
+                           int grid, int* info, cudaStream_t s);
+int ldlt_blocks_oz_per_sm();
 // ---- ILU(p) subdomain factors (k_ilu.cu); fac = [L (nnz) | D (rows) | 1/D (rows)]
 // of T = double or float (factorisation and sweeps in T).  es = sizeof(T).
 size_t ilu_factor_smem(int max_n, int max_row, size_t es);  // max_row: most strictly-lower entries of a row

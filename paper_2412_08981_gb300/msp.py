@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmsp.so")
 MSP_OK, MSP_PENDING = 0, 1
 MSP_ERR_INVALID, MSP_ERR_OOM, MSP_ERR_NOT_CONVERGED = -1, -2, -3
 MSP_ERR_TIMEOUT, MSP_ERR_CUDA, MSP_ERR_INTERNAL = -4, -5, -6
-MSP_F64, MSP_F32, MSP_BF16 = 0, 1, 2
+MSP_F64, MSP_F32, MSP_BF16, MSP_F64_TC = 0, 1, 2, 3
 MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
@@ -247,7 +247,7 @@ class Hierarchy:
         o = default_options(delta=int(delta), nu_pre=int(nu_pre), nu_post=int(nu_post),
                             restart=int(restart), max_it=int(max_it),
                             factor_precision={"f64": MSP_F64, "f32": MSP_F32,
-                                              "bf16": MSP_BF16}[precision],
+                                              "bf16": MSP_BF16, "f64tc": MSP_F64_TC}[precision],
                             coef_kind={"const": MSP_K_CONST, "cosexp": MSP_K_COSEXP}[coef],
                             coef_scale=float(scale),
                             load_kind={"one": MSP_F_ONE, "sines": MSP_F_SINES}[load],

@@ -1,7 +1,8 @@
 """The precision study at its full size: the 96^3 L-shaped domain (unit cube
 minus [0.5,1]^3, 802,081 nodes) with 48^3/24^3/12^3 non-nested coarse levels,
 2048 subdomains of 294-1320 DoFs, k(x;mu) spanning 1e-2 .. 1e2.  Subdomain
-factors in FP64, FP32 and BF16 (FP32 accumulation) under the FP64 outer
+factors in FP64 (also with the products on the tensor cores by exact digit
+slices), FP32 and BF16 (FP32 accumulation) under the FP64 outer
 FGMRES to rtol 1e-10, each against the FP64 oracle's solution: a seeded
 sample of 1024 entries with its norm and iteration count, written by
 tests/golden/make_lshape96.py from the oracle alone.
@@ -59,7 +60,7 @@ def study():
     return levels, w, meta, idx, val
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("precision", ["f64", "f64tc", "f32", "bf16"])
 def test_precision_study_against_the_oracle(P, torch, study, precision):
     levels, w, meta, idx, val = study
     h = make_hierarchy(levels, w, P, precision=precision)
@@ -74,7 +75,7 @@ def test_precision_study_against_the_oracle(P, torch, study, precision):
     assert err <= 1e-7, err
     assert abs(np.linalg.norm(xg) - meta["norm2_x"]) <= 1e-7 * meta["norm2_x"]
     it_o = int(meta["iterations"])
-    if precision == "f64":
+    if precision in ("f64", "f64tc"):  # FP64-class factors: the oracle's iteration count
         assert abs(st["iterations"] - it_o) <= 1
     else:  # the reduced-precision smoother may cost a few iterations, never accuracy
         assert st["iterations"] <= it_o + 3

@@ -696,8 +696,9 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
   if (warp == 0) tc::tmem_dealloc(taddr, kTcCols);
 }
 
-// The diagonal tile for the sliced kernel: the arithmetic of diag_tile, entry
-// by entry and in the same order (so the same bits), two columns per pass:
+// Diagonal tiles for the sliced kernel, one or two at a time (t1 may be
+// null): the arithmetic of diag_tile, entry by entry and in the same order (so
+// the same bits), two columns per pass:
 //   P: for the rows r > c, the scaled column l0 = A_rc / d_c, the entries
 //      (r, c+1) after step c and, from them, l1 = A'_r,c+1 / d_c+1 (every
 //      thread forms d_c+1 = A'_c+1,c+1 and its reciprocal itself); row c+1 of
@@ -705,64 +706,92 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
 //   U: the two updates of every other entry of the trailing triangle and of
 //      X, fused (fma(-l1, .., fma(-l0, .., a))), a thread's entries loaded,
 //      updated and stored as a batch.
-// Half the barriers of one column per pass.  smem: (64*65 + 3*64) doubles.
+// Half the barriers of one column per pass, and two tiles share them: the
+// pivots of a tile form a dependent chain of FP64 operations, which the other
+// tile's work overlaps.  Scratch per tile: (64*65 + 3*64) doubles; at least
+// 256 threads (128 per tile in P).
 constexpr int kPairBatch = 4;
+constexpr int kDiagScratch = 64 * 65 + 3 * 64;
 
-__device__ void diag_tile_pair(double* __restrict__ tile, double* __restrict__ A, int* __restrict__ info) {
-  double* l0 = A + 64 * 65;  // [64]
-  double* l1 = l0 + 64;      // [64]
-  double* dinv = l1 + 64;    // [64] 1/d_c
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  __syncthreads();  // the shared buffer may still be read by a previous phase
-  for (int e = tid; e < TE; e += nthr) {
-    const int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (c <= r) ? tile[e] : 0.0;  // X starts as the identity (zeros above)
+__device__ void diag_tiles2(double* __restrict__ t0, double* __restrict__ t1, double* __restrict__ S0,
+                            double* __restrict__ S1, int* __restrict__ info) {
+  const int tid = threadIdx.x, nthr = blockDim.x, half = nthr / 2;
+  const int ntile = t1 ? 2 : 1;
+  __syncthreads();  // the shared buffers may still be read by a previous phase
+  for (int e = tid; e < ntile * TE; e += nthr) {
+    const int t = e >= TE, ee = e - t * TE;
+    double* A = t ? S1 : S0;
+    const double* tile = t ? t1 : t0;
+    const int r = ee >> 6, c = ee & 63;
+    A[r * 65 + c] = (c <= r) ? tile[ee] : 0.0;  // X starts as the identity (zeros above)
   }
   __syncthreads();
-  if (tid == 0) dinv[0] = rcp_newton(A[0]);
+  if (tid < ntile) {
+    double* A = tid ? S1 : S0;
+    A[64 * 65 + 128] = rcp_newton(A[0]);  // dinv[0]
+  }
   __syncthreads();
   for (int c = 0; c < T64; c += 2) {
     const int c1 = c + 1;
-    // ---- P
-    if (tid < T64) {
-      const int r = tid;
-      if (r > c) {
-        const double lc = A[r * 65 + c] * dinv[c];
-        l0[r] = lc;
-        // pivot d_c+1 after step c, formed by every thread the same way
-        const double lp = A[c1 * 65 + c] * dinv[c];
-        const double d1 = fma(-lp, A[c1 * 65 + c], A[c1 * 65 + c1]);
-        const double di1 = rcp_newton(d1);
-        if (r > c1) {
-          const double a1 = fma(-lc, A[c1 * 65 + c], A[r * 65 + c1]);
-          A[r * 65 + c1] = a1;
-          l1[r] = a1 * di1;
-        } else {  // r == c + 1: the pivot's own row
-          dinv[c1] = di1;
-          l1[c1] = d1;  // handed to U, which stores it on the diagonal
+    // ---- P: threads [half t, half t + 128) for tile t
+    {
+      const int t = tid / half, lt = tid - t * half;
+      if (t < ntile && lt < 128) {
+        double* A = t ? S1 : S0;
+        double* l0 = A + 64 * 65;
+        double* l1 = l0 + 64;
+        double* dinv = l1 + 64;
+        if (lt < T64) {
+          const int r = lt;
+          if (r > c) {
+            const double lc = A[r * 65 + c] * dinv[c];
+            l0[r] = lc;
+            // pivot d_c+1 after step c, formed by every thread the same way
+            const double lp = A[c1 * 65 + c] * dinv[c];
+            const double d1 = fma(-lp, A[c1 * 65 + c], A[c1 * 65 + c1]);
+            const double di1 = rcp_newton(d1);
+            if (r > c1) {
+              const double a1 = fma(-lc, A[c1 * 65 + c], A[r * 65 + c1]);
+              A[r * 65 + c1] = a1;
+              l1[r] = a1 * di1;
+            } else {  // r == c + 1: the pivot's own row
+              dinv[c1] = di1;
+              l1[c1] = d1;  // handed to U, which stores it on the diagonal
+            }
+          }
+        } else if (lt - T64 <= c) {  // row c+1 of X after step c: X_c+1,j (at A[j][c+1]), j <= c
+          const int j = lt - T64;
+          const double lp = A[c1 * 65 + c] * dinv[c];
+          const double xcj = (j == c) ? 1.0 : A[j * 65 + c];
+          A[j * 65 + c1] = fma(-lp, xcj, A[j * 65 + c1]);
         }
       }
-    } else if (tid - T64 <= c) {  // row c+1 of X after step c: X_c+1,j (at A[j][c+1]), j <= c
-      const int j = tid - T64;
-      const double lp = A[c1 * 65 + c] * dinv[c];
-      const double xcj = (j == c) ? 1.0 : A[j * 65 + c];
-      A[j * 65 + c1] = fma(-lp, xcj, A[j * 65 + c1]);
     }
     __syncthreads();
-    // ---- U
+    // ---- U: the entries of both tiles in one range
     const int m = T64 - 2 - c;        // rows c+2 .. 63
     const int nA = m * (m + 1) / 2;   // trailing entries (r, s), c+2 <= s <= r
     const int w = c + 2;              // X columns j <= c+1
     const int nU = nA + m * w;
-    if (tid == 0) A[c1 * 65 + c1] = l1[c1];
-    for (int base = 0; base < nU; base += nthr * kPairBatch) {
+    if (tid < ntile) {
+      double* A = tid ? S1 : S0;
+      A[c1 * 65 + c1] = A[64 * 65 + 64 + c1];  // d_c+1 onto the diagonal
+    }
+    for (int base = 0; base < ntile * nU; base += nthr * kPairBatch) {
       int idx[kPairBatch];
+      unsigned tsel = 0;  // bit q: entry q is in the second tile
       double av[kPairBatch], b0[kPairBatch], b1[kPairBatch], f0[kPairBatch], f1[kPairBatch];
 #pragma unroll
       for (int q = 0; q < kPairBatch; ++q) {
-        const int e = base + tid + q * nthr;
+        int e = base + tid + q * nthr;
         idx[q] = -1;
-        if (e >= nU) continue;
+        if (e >= ntile * nU) continue;
+        const int t = e >= nU;
+        e -= t * nU;
+        double* A = t ? S1 : S0;
+        const double* l0 = A + 64 * 65;
+        const double* l1 = l0 + 64;
+        tsel |= (unsigned)t << q;
         int r, s;
         if (e < nA) {
           int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
@@ -790,22 +819,30 @@ __device__ void diag_tile_pair(double* __restrict__ tile, double* __restrict__ A
       for (int q = 0; q < kPairBatch; ++q) {
         if (idx[q] < 0) continue;
         const double v = fma(-f1[q], b1[q], fma(-f0[q], b0[q], av[q]));
+        double* A = ((tsel >> q) & 1u) ? S1 : S0;
         A[idx[q]] = v;
-        if (idx[q] == (c + 2) * 65 + (c + 2)) dinv[c + 2] = rcp_newton(v);  // the next pass's first pivot
+        if (idx[q] == (c + 2) * 65 + (c + 2)) A[64 * 65 + 128 + c + 2] = rcp_newton(v);  // next first pivot
       }
     }
     __syncthreads();
   }
-  if (tid < T64) {
-    const double d = A[tid * 65 + tid];
+  if (tid < ntile * T64) {
+    const double* A = tid >= T64 ? S1 : S0;
+    const int r = tid & 63;
+    const double d = A[r * 65 + r];
     if (!(d > 0.0) || !(d < 1e300)) atomicOr(info, 1);
   }
-  for (int e = tid; e < TE; e += nthr) {  // L = W D^{-1}
-    const int r = e >> 6, c = e & 63;
-    if (c < r) A[r * 65 + c] *= dinv[c];
+  for (int e = tid; e < ntile * TE; e += nthr) {  // L = W D^{-1}
+    const int t = e >= TE, ee = e - t * TE;
+    double* A = t ? S1 : S0;
+    const int r = ee >> 6, c = ee & 63;
+    if (c < r) A[r * 65 + c] *= A[64 * 65 + 128 + c];
   }
   __syncthreads();
-  for (int e = tid; e < TE; e += nthr) tile[e] = A[(e >> 6) * 65 + (e & 63)];
+  for (int e = tid; e < ntile * TE; e += nthr) {
+    const int t = e >= TE, ee = e - t * TE;
+    (t ? t1 : t0)[ee] = (t ? S1 : S0)[(ee >> 6) * 65 + (ee & 63)];
+  }
 }
 
 // ------------------------- whole-block factorisation, FP64 by exact BF16 slices
@@ -844,7 +881,9 @@ constexpr int kOzDk = kOzEB + 64 * 4;                      // double [64] D of t
 constexpr int kOzDinv = kOzDk + 64 * 8;                    // double [64] 1 / D
 constexpr int kOzBar = kOzDinv + 64 * 8;                   // mbarrier, then the TMEM base slot
 constexpr int kOzSmem = kOzBar + 64;
-static_assert((64 * 65 + 3 * 64) * 8 <= kOzBOff, "the diagonal tile's scratch fits in the A slabs");
+constexpr int kOzS1 = 36 * 1024;                          // the second diagonal tile's scratch
+static_assert(kOzS1 + kDiagScratch * 8 <= kOzBOff, "two diagonal tiles' scratch fits in the A slabs");
+static_assert(kDiagScratch * 8 <= kOzS1, "the first scratch ends before the second");
 
 // biased exponent field of x (0 for zero and subnormal numbers)
 __device__ __forceinline__ int oz_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
@@ -1014,19 +1053,22 @@ __device__ __forceinline__ void oz_issue(uint32_t taddr, const unsigned char* sA
 }
 
 // The product of the slabs in shared memory for one output block: MMAs by
-// thread 0, a bounded wait, then the 64-bit integer sums of this thread's row
-// r = 32 (warp % 4) + lane over the 16 columns 16 (warp / 4) .., handed to
-// epi(r, q, V) before the block barrier that frees the slabs, the row
-// exponents and the tensor memory.  Returns the updated `failed`.
-template <typename Epi>
+// thread 0; while they run, pre(r, q, C) may load this thread's 16 outputs
+// (row r = 32 (warp % 4) + lane, columns 16 (warp / 4) ..); a bounded wait;
+// then the 64-bit integer sums V of those entries, handed to epi(r, q, V, C)
+// before the block barrier that frees the slabs, the row exponents and the
+// tensor memory.  Returns the updated `failed`.
+template <typename Pre, typename Epi>
 __device__ __forceinline__ bool oz_product(uint32_t taddr, unsigned char* sm, uint64_t* bar, uint32_t& phase,
-                                           bool failed, int* info, Epi epi) {
+                                           bool failed, int* info, Pre pre, Epi epi) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   if (tid == 0) oz_issue(taddr, sm, sm + kOzBOff, bar);
+  double C[16];
+  pre(32 * (warp & 3) + lane, warp >> 2, C);
   if (!tc::mbar_wait_bounded(bar, phase, failed ? 64 : (1L << 22))) {
     failed = true;
     if (lane == 0) atomicOr(info, 2);
@@ -1054,23 +1096,104 @@ __device__ __forceinline__ bool oz_product(uint32_t taddr, unsigned char* sm, ui
       else V[u] += (long long)((qv + 4) >> 3);
     }
   }
-  epi(32 * qd + lane, q, V);
+  epi(32 * qd + lane, q, V, C);
   tc::fence_before();
   __syncthreads();
   return failed;
 }
 
+// One tile step k of block p after its diagonal tile dt is factored (R > k):
+// the panel L_ik = (A_ik X^T) D^-1 and the trailing update, every product on
+// the tensor cores by digit slices.
+__device__ __noinline__ bool oz_step(double* __restrict__ fac, const EnvDev& E, int p, int k, int R,
+                                        const double* __restrict__ dt, unsigned char* smoz, uint32_t taddr,
+                                        uint64_t* bar, uint32_t& phase, bool failed, int* info) {
+  int* eA = reinterpret_cast<int*>(smoz + kOzEA);
+  int* eB = reinterpret_cast<int*>(smoz + kOzEB);
+  double* dk = reinterpret_cast<double*>(smoz + kOzDk);
+  double* dinv = reinterpret_cast<double*>(smoz + kOzDinv);
+  const int tid = threadIdx.x;
+  __syncthreads();  // the factored diagonal tile is in global memory
+  if (tid < 64) {
+    const double d = dt[tid * 65];
+    dk[tid] = d;
+    dinv[tid] = 1.0 / d;
+  }
+  // panel: L_ik = (A_ik X^T) D^-1, tile rows two at a time
+  oz_split_b(smoz + kOzBOff, eB, dt, true);
+  for (int i0 = k + 1; i0 <= R; i0 += 2) {
+    oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
+               nullptr);
+    failed = oz_product(
+        taddr, smoz, bar, phase, failed, info, [](int, int, double(&)[16]) {},
+        [&](int r, int h, long long(&V)[16], double(&)[16]) {
+      const int ti = r < 64 ? i0 : i0 + 1;
+      if (ti > R) return;
+      const int er = eA[r];
+      double* out = fac + tile_at(E, p, ti, k) + (r & 63) * 64 + 16 * h;
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        const int cc = 16 * h + c;
+        double2 o;
+        o.x = oz_to_double(V[c], er, eB[cc]) * dinv[cc];
+        o.y = oz_to_double(V[c + 1], er, eB[cc + 1]) * dinv[cc + 1];
+        *reinterpret_cast<double2*>(out + c) = o;
+      }
+    });
+  }
+  // trailing update: C_ij -= (L_ik D_k) L_jk^T, k < j <= i <= R; the
+  // digits of two rows of W = L D at a time, against every column tile j
+  // up to the second row (the rows i < j of a block are not written)
+  for (int i0 = k + 1; i0 <= R; i0 += 2) {
+    const int i1 = i0 + 1 <= R ? i0 + 1 : i0;
+    oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
+               dk);
+    for (int j = k + 1; j <= i1; ++j) {
+      oz_split_b(smoz + kOzBOff, eB, fac + tile_at(E, p, j, k), false);
+      // this thread's 16 entries of C_ij, loaded while the tensor cores run
+      auto pre = [&](int r, int h, double(&C)[16]) {
+        const int ti = r < 64 ? i0 : i0 + 1;
+        if (ti > R || ti < j) return;
+        const double2* src = reinterpret_cast<const double2*>(fac + tile_at(E, p, ti, j) + (r & 63) * 64 + 16 * h);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const double2 v = src[c];
+          C[2 * c] = v.x;
+          C[2 * c + 1] = v.y;
+        }
+      };
+      failed = oz_product(taddr, smoz, bar, phase, failed, info, pre,
+                          [&](int r, int h, long long(&V)[16], double(&C)[16]) {
+        const int ti = r < 64 ? i0 : i0 + 1;
+        if (ti > R || ti < j) return;
+        const int rr = r & 63, er = eA[r];
+        double2* out = reinterpret_cast<double2*>(fac + tile_at(E, p, ti, j) + rr * 64 + 16 * h);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int cc = 16 * h + c;
+          // a diagonal tile keeps its upper part (X^T later): written back unchanged
+          if (ti != j || cc <= rr) C[c] -= oz_to_double(V[c], er, eB[cc]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out[c] = make_double2(C[2 * c], C[2 * c + 1]);
+      });
+    }
+  }
+  return failed;
+}
+
+// Persistent: CTA b takes the blocks cta_list[cta_ptr[b] .. cta_ptr[b+1]) two
+// at a time, step by step: their diagonal tiles together (diag_tiles2), then
+// the tensor-core products of each.
 __global__ void __launch_bounds__(512, 1) k_ldlt_blocks_oz(double* __restrict__ fac, EnvDev E,
                                                            const int32_t* __restrict__ cta_ptr,
                                                            const int32_t* __restrict__ cta_list,
                                                            int* __restrict__ info) {
   extern __shared__ __align__(1024) unsigned char smoz[];
-  int* eA = reinterpret_cast<int*>(smoz + kOzEA);
-  int* eB = reinterpret_cast<int*>(smoz + kOzEB);
-  double* dk = reinterpret_cast<double*>(smoz + kOzDk);
-  double* dinv = reinterpret_cast<double*>(smoz + kOzDinv);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smoz + kOzBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smoz + kOzBar + 16);
+  double* S0 = reinterpret_cast<double*>(smoz);
+  double* S1 = reinterpret_cast<double*>(smoz + kOzS1);
   const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
   if (q0 >= q1) return;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -1085,62 +1208,20 @@ __global__ void __launch_bounds__(512, 1) k_ldlt_blocks_oz(double* __restrict__ 
   const uint32_t taddr = *tslot;
   uint32_t phase = 0;
   bool failed = false;
-  for (int q = q0; q < q1; ++q) {
-    const int p = cta_list[q];
-    const int NT = E.nt[p];
-    for (int k = 0; k < NT; ++k) {
-      const int R = E.last[E.trow[p] + k];
-      double* dt = fac + tile_at(E, p, k, k);
-      diag_tile_pair(dt, reinterpret_cast<double*>(smoz), info);
-      if (R == k) continue;
-      __syncthreads();  // the factored diagonal tile is in global memory
-      if (tid < 64) {
-        const double d = dt[tid * 65];
-        dk[tid] = d;
-        dinv[tid] = 1.0 / d;
+  for (int q = q0; q < q1; q += 2) {
+    const int pa = cta_list[q], pb = q + 1 < q1 ? cta_list[q + 1] : -1;
+    const int nta = E.nt[pa], ntb = pb >= 0 ? E.nt[pb] : 0;
+    for (int k = 0; k < max(nta, ntb); ++k) {
+      double* da = k < nta ? fac + tile_at(E, pa, k, k) : nullptr;
+      double* db = k < ntb ? fac + tile_at(E, pb, k, k) : nullptr;
+      diag_tiles2(da ? da : db, da ? db : nullptr, S0, S1, info);
+      if (da) {
+        const int R = E.last[E.trow[pa] + k];
+        if (R > k) failed = oz_step(fac, E, pa, k, R, da, smoz, taddr, bar, phase, failed, info);
       }
-      // panel: L_ik = (A_ik X^T) D^-1, tile rows two at a time
-      oz_split_b(smoz + kOzBOff, eB, dt, true);
-      for (int i0 = k + 1; i0 <= R; i0 += 2) {
-        oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
-                   nullptr);
-        failed = oz_product(taddr, smoz, bar, phase, failed, info, [&](int r, int h, long long(&V)[16]) {
-          const int ti = r < 64 ? i0 : i0 + 1;
-          if (ti > R) return;
-          const int er = eA[r];
-          double* out = fac + tile_at(E, p, ti, k) + (r & 63) * 64 + 16 * h;
-#pragma unroll
-          for (int c = 0; c < 16; c += 2) {
-            const int cc = 16 * h + c;
-            double2 o;
-            o.x = oz_to_double(V[c], er, eB[cc]) * dinv[cc];
-            o.y = oz_to_double(V[c + 1], er, eB[cc + 1]) * dinv[cc + 1];
-            *reinterpret_cast<double2*>(out + c) = o;
-          }
-        });
-      }
-      // trailing update: C_ij -= (L_ik D_k) L_jk^T, k < j <= i <= R; the
-      // digits of two rows of W = L D at a time, against every column tile j
-      // up to the second row (the rows i < j of a block are not written)
-      for (int i0 = k + 1; i0 <= R; i0 += 2) {
-        const int i1 = i0 + 1 <= R ? i0 + 1 : i0;
-        oz_split_a(smoz, eA, fac + tile_at(E, p, i0, k), i0 + 1 <= R ? fac + tile_at(E, p, i0 + 1, k) : nullptr,
-                   dk);
-        for (int j = k + 1; j <= i1; ++j) {
-          oz_split_b(smoz + kOzBOff, eB, fac + tile_at(E, p, j, k), false);
-          failed = oz_product(taddr, smoz, bar, phase, failed, info, [&](int r, int h, long long(&V)[16]) {
-            const int ti = r < 64 ? i0 : i0 + 1;
-            if (ti > R || ti < j) return;
-            const int rr = r & 63, er = eA[r];
-            double* out = fac + tile_at(E, p, ti, j) + rr * 64 + 16 * h;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int cc = 16 * h + c;
-              if (ti == j && cc > rr) continue;  // a diagonal tile keeps its upper part (X^T later)
-              out[c] -= oz_to_double(V[c], er, eB[cc]);
-            }
-          });
-        }
+      if (db) {
+        const int R = E.last[E.trow[pb] + k];
+        if (R > k) failed = oz_step(fac, E, pb, k, R, db, smoz, taddr, bar, phase, failed, info);
       }
     }
   }

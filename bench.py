@@ -374,7 +374,7 @@ def run_msp(args):
         h.close()
         return dict(value=steps / wall, lat=lat, iters=iters, wall_s=wall)
 
-    def measure_hbm_kernels(reps=40):
+    def measure_hbm_kernels(reps=40, lv=None, opts=None):
         """The memory-bound operators of the finest level: J x (SpMV), P x_c
         (interpolation) and P^T x (restriction), each launch preceded by an L2
         eviction (a 256 MB read, which leaves clean lines).  The CUDA event
@@ -384,7 +384,7 @@ def run_msp(args):
         never starves the stream; the difference over reps is the launch.
         Algorithmic bytes: 12 per nonzero (value + column) + 4 per row pointer
         + 8 per vector entry read or written."""
-        h = P.Hierarchy(levels, precision="f64", **kw)
+        h = P.Hierarchy(levels if lv is None else lv, precision="f64", **(kw if opts is None else opts))
         inst = h.assemble(mu_of(0), stream=stream)
         i0, i1 = h.info(0), h.info(1)
         n0, n1 = i0["n_dofs"], i1["n_dofs"]
@@ -395,7 +395,8 @@ def run_msp(args):
                "restrict_PT0": (P.msp.MSP_OP_RESTRICT, n0, n1,
                                 12 * i0["R_nnz"] + 4 * (n1 + 1) + 8 * n0 + 8 * n1)}
         out = {"l2": "evicted before every launch (256 MB read)", "peak_gbs": peak,
-               "peak_source": "MEASURED_PEAKS hbm_gbs", "reps": reps}
+               "peak_source": "MEASURED_PEAKS hbm_gbs", "reps": reps, "rows_level0": n0,
+               "nnz_level0": int(i0["nnz"])}
 
         def seq(fn):
             torch.cuda._sleep(4_000_000)  # ~2 ms: the host queues the whole sequence meanwhile
@@ -623,6 +624,13 @@ def run_msp(args):
 
     res = measure(args.precision, args.steps, args.warmup)
     hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 and not args.no_hbm else None
+    if hbm is not None and args.workload == "cube64_3lvl":
+        # the same operators on the 96^3 L-shaped domain, whose level-0 matrix
+        # (802,081 rows, ~12M nonzeros, ~160 MB) is larger than the L2 cache
+        lv96, w96 = syn.workload("lshape96_4lvl")
+        hbm["lshape96_4lvl"] = measure_hbm_kernels(
+            lv=lv96, opts=dict(delta=w96["delta"], nu_pre=w96["nu"], nu_post=w96["nu"], restart=w96["restart"],
+                               coef=w96["coef"], wave=syn.wave_vectors(), scale=w96["scale"], load=w96["load"]))
     ms = max_over_ranks(res["ms"])
     value = whole_job_rate(args.steps, world, ms)
     mixed = None

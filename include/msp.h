@@ -229,10 +229,10 @@ typedef struct msp_level_info {
                                  (0: tile-step launches, or a host-only hierarchy) */
   int32_t ras_ctas;           /* CTAs of the staged RAS solve (0: directly solved level) */
   int32_t spmv_lanes[3];      /* lanes per row of the SpMV schedules picked at load time by
-                                 timing them on the device: 4/8/16/32, or 1 (one lane per row
+                                 timing them on the device: 2/4/8/16/32, or 1 (one lane per row
                                  over row blocks staged in shared memory); J, prolongation,
                                  restriction (0: host-only hierarchy or no such operator).
-                                 The environment variable MSP_SPMV_LANES = 1, 4, 8, 16 or 32,
+                                 The environment variable MSP_SPMV_LANES = 1, 2, 4, 8, 16 or 32,
                                  read at load time, fixes the schedule instead */
   int32_t n_dofs;             /* DoFs: n_nodes x fields per vertex (msp_options.pde) */
 } msp_level_info;

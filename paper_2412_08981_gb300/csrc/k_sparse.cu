@@ -180,7 +180,11 @@ __global__ void k_assemble(const int32_t* __restrict__ cptr, const int32_t* __re
 
 // ---------------------------------------------------------------- SpMV
 // LPR lanes per row, rows packed into warps; each row's partial sums are
-// combined by a fixed butterfly over its lane group.
+// combined by a fixed butterfly over its lane group.  A lane's nonzeros
+// (every LPR-th of the row) are taken four at a time: their values and
+// columns loaded together, then the four gathers of x, then the FMAs in
+// ascending position -- the same sum as one at a time, with four times the
+// bytes in flight per lane.
 template <int LPR>
 __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                        const double* __restrict__ val, int nrows, const double* __restrict__ x,
@@ -191,8 +195,26 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
   const bool valid = row < nrows;  // no early exit: every lane joins the shuffles
   double s = 0.0;
   if (valid) {
-    int b = rowptr[row], e = rowptr[row + 1];
-    for (int q = b + lane; q < e; q += LPR) s += val[q] * x[col[q]];
+    const int b = rowptr[row], e = rowptr[row + 1];
+    for (int q0 = b + lane; q0 < e; q0 += 4 * LPR) {
+      double v[4], xv[4];
+      int c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * LPR;
+        v[u] = 0.0;
+        c[u] = -1;
+        if (q < e) {
+          v[u] = val[q];
+          c[u] = col[q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c[u] >= 0) s = fma(v[u], xv[u], s);
+    }
   }
 #pragma unroll
   for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LPR);
@@ -424,6 +446,9 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
       k_spmv_rows<<<plan.nblk, kRowsThreads, 0, s>>>(rowptr, col, val, plan.row_blk, plan.row_blk + plan.nblk + 1,
                                                      x, y, r, mode);
       break;
+    case 2:
+      k_spmv<2><<<nblk((int64_t)nrows * 2, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
+      break;
     case 4:
       k_spmv<4><<<nblk((int64_t)nrows * 4, 256), 256, 0, s>>>(rowptr, col, val, nrows, x, y, r, mode);
       break;
@@ -439,7 +464,7 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
   }
 }
 
-// Autotuner of the SpMV schedule: lanes per row 4, 8, 16, 32, or one lane
+// Autotuner of the SpMV schedule: lanes per row 2, 4, 8, 16, 32, or one lane
 // per row over shared-memory-staged row blocks (1).  Every candidate is timed
 // with CUDA events on the matrix itself (zero values, zero x: the memory
 // traffic and the schedule are those of the real products), each launch after
@@ -457,7 +482,7 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
   if (nrows <= 0 || nnz == 0) return 8;
   if (const char* f = std::getenv("MSP_SPMV_LANES")) {  // a fixed schedule instead of the timed choice
     const int v = std::atoi(f);
-    if (v == 4 || v == 8 || v == 16 || v == 32 || (v == 1 && row_blk)) return v;
+    if (v == 2 || v == 4 || v == 8 || v == 16 || v == 32 || (v == 1 && row_blk)) return v;
   }
   uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the structure
   auto mix = [&](int32_t v) {
@@ -501,7 +526,7 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
       return ms;
     };
     float best_ms = 1e30f;
-    for (int lpr : {1, 4, 8, 16, 32}) {
+    for (int lpr : {1, 2, 4, 8, 16, 32}) {
       const SpmvPlan plan{lpr, row_blk, nblk};
       if (lpr == 1 && !row_blk) continue;
       launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);  // warm-up

@@ -30,7 +30,7 @@ void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t*
 // ---- CSR SpMV family (FP64)
 enum SpmvMode { SPMV_SET = 0, SPMV_SUB_FROM = 1, SPMV_ADD = 2, SPMV_RESIDUAL = 3 };
 // SET: y = A x; SUB_FROM: y = y - A x; ADD: y += A x; RESIDUAL: y = r - A x.
-// Schedule: lpr = lanes per row (4, 8, 16 or 32), or 1: one lane per row over
+// Schedule: lpr = lanes per row (2, 4, 8, 16 or 32), or 1: one lane per row over
 // the row blocks row_blk[0..nblk] (spmv_row_blocks), staged in shared memory.
 struct SpmvPlan {
   int lpr = 8;

@@ -229,11 +229,14 @@ typedef struct msp_level_info {
                                  (0: tile-step launches, or a host-only hierarchy) */
   int32_t ras_ctas;           /* CTAs of the staged RAS solve (0: directly solved level) */
   int32_t spmv_lanes[3];      /* lanes per row of the SpMV schedules picked at load time by
-                                 timing them on the device: 2/4/8/16/32, or 1 (one lane per row
-                                 over row blocks staged in shared memory); J, prolongation,
+                                 timing them on the device: 2/4/8/16/32, 1 (one lane per row
+                                 over row blocks staged in shared memory), or 64 (one thread per
+                                 row of the four-entry form of an operator with at most four
+                                 entries per row: the barycentric P); J, prolongation,
                                  restriction (0: host-only hierarchy or no such operator).
-                                 The environment variable MSP_SPMV_LANES = 1, 2, 4, 8, 16 or 32,
-                                 read at load time, fixes the schedule instead */
+                                 The environment variable MSP_SPMV_LANES = 1, 2, 4, 8, 16, 32 or
+                                 64, read at load time, fixes the schedule instead (where it
+                                 applies) */
   int32_t n_dofs;             /* DoFs: n_nodes x fields per vertex (msp_options.pde) */
 } msp_level_info;
 MSP_API int msp_hierarchy_info(const msp_hierarchy* h, int level, msp_level_info* info);

@@ -311,6 +311,30 @@ __global__ void __launch_bounds__(kRowsThreads) k_spmv_rows(
   }
 }
 
+// One thread per row of an operator with at most four entries per row (the
+// barycentric P): its four columns in one 16-byte load and its four values in
+// two, no row pointers; four gathers, then the entries in order (the padding
+// adds 0 * x[0]).
+__global__ void k_spmv_ell4(const int4* __restrict__ ec, const double2* __restrict__ ev, int nrows,
+                            const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ r,
+                            int mode) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  const int4 c = ec[row];
+  const double2 a = ev[2 * (int64_t)row], b = ev[2 * (int64_t)row + 1];
+  const double x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+  double s = a.x * x0;
+  s = fma(a.y, x1, s);
+  s = fma(b.x, x2, s);
+  s = fma(b.y, x3, s);
+  switch (mode) {
+    case SPMV_SET: y[row] = s; break;
+    case SPMV_SUB_FROM: y[row] = y[row] - s; break;
+    case SPMV_ADD: y[row] = y[row] + s; break;
+    default: y[row] = r[row] - s; break;
+  }
+}
+
 // Reads n doubles (evicts the L2 with clean lines) and stores one value.
 __global__ void k_touch(const double* __restrict__ p, int64_t n, double* __restrict__ out) {
   double s = 0.0;
@@ -437,11 +461,31 @@ std::vector<int32_t> spmv_row_blocks(const std::vector<int32_t>& rowptr) {
   return blk;
 }
 
+bool spmv_ell4(const std::vector<int32_t>& rowptr, const std::vector<int32_t>& col, const std::vector<double>& val,
+               std::vector<int32_t>& ecol, std::vector<double>& eval) {
+  const size_t nrows = rowptr.empty() ? 0 : rowptr.size() - 1;
+  ecol.clear();
+  eval.clear();
+  for (size_t i = 0; i < nrows; ++i)
+    if (rowptr[i + 1] - rowptr[i] > 4) return false;
+  ecol.assign(nrows * 4, 0);
+  eval.assign(nrows * 4, 0.0);
+  for (size_t i = 0; i < nrows; ++i)
+    for (int32_t q = rowptr[i], k = 0; q < rowptr[i + 1]; ++q, ++k) {
+      ecol[i * 4 + k] = col[q];
+      eval[i * 4 + k] = val[q];
+    }
+  return nrows > 0;
+}
+
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
                  const double* x, double* y, const double* r, int mode, const SpmvPlan& plan,
                  cudaStream_t s) {
   if (nrows <= 0) return;
   switch (plan.lpr) {
+    case kSpmvEll4:
+      k_spmv_ell4<<<nblk(nrows, 256), 256, 0, s>>>(plan.ell_col, plan.ell_val, nrows, x, y, r, mode);
+      break;
     case 1:
       k_spmv_rows<<<plan.nblk, kRowsThreads, 0, s>>>(rowptr, col, val, plan.row_blk, plan.row_blk + plan.nblk + 1,
                                                      x, y, r, mode);
@@ -464,8 +508,10 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
   }
 }
 
-// Autotuner of the SpMV schedule: lanes per row 2, 4, 8, 16, 32, or one lane
-// per row over shared-memory-staged row blocks (1).  Every candidate is timed
+// Autotuner of the SpMV schedule: lanes per row 2, 4, 8, 16, 32, one lane
+// per row over shared-memory-staged row blocks (1), or one thread per row of
+// the four-entry form (kSpmvEll4, for operators with at most four entries per
+// row).  Every candidate is timed
 // with CUDA events on the matrix itself (zero values, zero x: the memory
 // traffic and the schedule are those of the real products), each launch after
 // the L2 has been evicted (a 256 MB read), as in the solve, where the
@@ -475,14 +521,16 @@ void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, i
 // always get the same schedule (and bitwise the same sums).
 int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
               const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
-              const int32_t* row_blk, int nblk, cudaStream_t s) {
+              const int32_t* row_blk, int nblk, cudaStream_t s, const int4* ell_col,
+              const double2* ell_val) {
   static std::mutex mu;
   static std::map<std::tuple<int, int64_t, uint64_t>, int> cache;
   const int64_t nnz = h_col.size();
   if (nrows <= 0 || nnz == 0) return 8;
   if (const char* f = std::getenv("MSP_SPMV_LANES")) {  // a fixed schedule instead of the timed choice
     const int v = std::atoi(f);
-    if (v == 2 || v == 4 || v == 8 || v == 16 || v == 32 || (v == 1 && row_blk)) return v;
+    if (v == 2 || v == 4 || v == 8 || v == 16 || v == 32 || (v == 1 && row_blk) || (v == kSpmvEll4 && ell_col))
+      return v;
   }
   uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the structure
   auto mix = [&](int32_t v) {
@@ -493,6 +541,7 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
   };
   for (int32_t v : h_rowptr) mix(v);
   for (int32_t v : h_col) mix(v);
+  mix(ell_col ? 1 : 0);  // the four-entry form is a candidate or not
   const auto key = std::make_tuple(nrows, nnz, hsh);
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
@@ -526,9 +575,10 @@ int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
       return ms;
     };
     float best_ms = 1e30f;
-    for (int lpr : {1, 2, 4, 8, 16, 32}) {
-      const SpmvPlan plan{lpr, row_blk, nblk};
+    for (int lpr : {1, 2, 4, 8, 16, 32, kSpmvEll4}) {
+      const SpmvPlan plan{lpr, row_blk, nblk, ell_col, ell_val};
       if (lpr == 1 && !row_blk) continue;
+      if (lpr == kSpmvEll4 && !ell_col) continue;
       launch_spmv(rowptr, col, val, nrows, x, y, nullptr, 0, plan, s);  // warm-up
       const float t = seq(&plan) - seq(nullptr);
       if (t < best_ms) {

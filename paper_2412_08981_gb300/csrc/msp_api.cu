@@ -146,6 +146,8 @@ struct DevLevel {
   int64_t P_nnz = 0, PT_nnz = 0;
   int32_t *P_rowptr = nullptr, *P_col = nullptr, *PT_rowptr = nullptr, *PT_col = nullptr;
   double *P_val = nullptr, *PT_val = nullptr;
+  const int4* P_ell_col = nullptr;  // P in the four-entry form (barycentric P: at most four entries per row)
+  const double2* P_ell_val = nullptr;
 };
 
 }  // namespace msp
@@ -431,6 +433,14 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     D.PT_col = A.upload(H.PT_col);
     D.PT_val = A.upload(H.PT_val);
     {
+      std::vector<int32_t> ec;
+      std::vector<double> ev;
+      if (spmv_ell4(H.P_rowptr, H.P_col, H.P_val, ec, ev)) {
+        D.P_ell_col = reinterpret_cast<const int4*>(A.upload(ec));
+        D.P_ell_val = reinterpret_cast<const double2*>(A.upload(ev));
+      }
+    }
+    {
       const std::vector<int32_t> rbp = spmv_row_blocks(H.P_rowptr), rbt = spmv_row_blocks(H.PT_rowptr);
       D.rb_P = A.upload(rbp);
       D.nrb_P = (int)rbp.size() / 2 - 1;
@@ -439,7 +449,8 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     }
     if (A.ok) {
       const int nc = h->host[l + 1].n;
-      D.lpr_P = tune_spmv(D.P_rowptr, D.P_col, H.n, nc, H.P_rowptr, H.P_col, D.rb_P, D.nrb_P, s);
+      D.lpr_P = tune_spmv(D.P_rowptr, D.P_col, H.n, nc, H.P_rowptr, H.P_col, D.rb_P, D.nrb_P, s, D.P_ell_col,
+                          D.P_ell_val);
       D.lpr_PT = tune_spmv(D.PT_rowptr, D.PT_col, nc, H.n, H.PT_rowptr, H.PT_col, D.rb_PT, D.nrb_PT, s);
     }
   }
@@ -785,7 +796,8 @@ void transfer(msp_instance* I, int l, bool restrict_, const double* x, double* y
     launch_spmv(D.PT_rowptr, D.PT_col, D.PT_val, nc, x, y, nullptr, mode, SpmvPlan{D.lpr_PT, D.rb_PT, D.nrb_PT},
                 s);
   else
-    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode, SpmvPlan{D.lpr_P, D.rb_P, D.nrb_P}, s);
+    launch_spmv(D.P_rowptr, D.P_col, D.P_val, D.n, x, y, nullptr, mode,
+                SpmvPlan{D.lpr_P, D.rb_P, D.nrb_P, D.P_ell_col, D.P_ell_val}, s);
   double rows = restrict_ ? nc : D.n, cols = restrict_ ? D.n : nc;
   double nnz = (double)(restrict_ ? D.PT_nnz : D.P_nnz);
   ps.account(nnz * 12 + (rows + 1) * 4 + cols * 8 + rows * (mode == SPMV_SET ? 8 : 16), 2.0 * nnz);

@@ -36,17 +36,29 @@ struct SpmvPlan {
   int lpr = 8;
   const int32_t* row_blk = nullptr;  // device: nblk + 1 row offsets, then their nblk + 1 first nonzeros
   int nblk = 0;
+  // lpr == kSpmvEll4: one thread per row of an operator with at most four
+  // entries per row, stored as four columns and four values per row (padded
+  // with weight 0 at column 0)
+  const int4* ell_col = nullptr;
+  const double2* ell_val = nullptr;
 };
+constexpr int kSpmvEll4 = 64;
+// The four-entry form of a CSR matrix whose rows have at most four entries
+// (empty when a row has more): columns [rows][4], values [rows][4].
+bool spmv_ell4(const std::vector<int32_t>& rowptr, const std::vector<int32_t>& col, const std::vector<double>& val,
+               std::vector<int32_t>& ecol, std::vector<double>& eval);
 std::vector<int32_t> spmv_row_blocks(const std::vector<int32_t>& rowptr);
 void launch_spmv(const int32_t* rowptr, const int32_t* col, const double* val, int nrows,
                  const double* x, double* y, const double* r, int mode, const SpmvPlan& plan,
                  cudaStream_t s);
 // the fastest schedule (lpr) for this matrix, measured on the device with the
 // L2 evicted before each launch (cached per structure for the life of the
-// process); row_blk / nblk: its row blocks on the device (NULL: not a candidate)
+// process); row_blk / nblk: its row blocks on the device (NULL: not a candidate);
+// ell_col / ell_val: its four-entry form (NULL: not a candidate)
 int tune_spmv(const int32_t* rowptr, const int32_t* col, int nrows, int ncols,
               const std::vector<int32_t>& h_rowptr, const std::vector<int32_t>& h_col,
-              const int32_t* row_blk, int nblk, cudaStream_t s);
+              const int32_t* row_blk, int nblk, cudaStream_t s, const int4* ell_col = nullptr,
+              const double2* ell_val = nullptr);
 
 // ---- dense subdomain blocks (templated on the factor type T = double | float)
 // Device view of a level's tile envelopes (see msp_internal.h).

@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--serve", type=int, default=48,
                     help="requests of the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-trace", action="store_true",
+                    help="also serve the full trace: 2000 requests at 200/s over 32^3, 64^3 and 128^3 hierarchies "
+                         "(probabilities 0.5/0.35/0.15), 120 GB budget")
     ap.add_argument("--cpu-sample", type=int, default=24,
                     help="fine subdomains factored/solved by the CPU baseline sample")
     return ap.parse_args()
@@ -567,11 +570,10 @@ def run_msp(args):
             h.close()
         return out
 
-    def measure_serving(nreq, rate):
-        """Poisson arrivals of seeded mu over two resident hierarchies (32^3 and
-        64^3, FP32 subdomain factors), served by msp_submit/msp_poll."""
+    def measure_serving(nreq, rate, names=("cube32_3lvl", "cube64_3lvl"), probs=(0.6, 0.4)):
+        """Poisson arrivals of seeded mu over resident hierarchies (FP32
+        subdomain factors), served by msp_submit/msp_poll."""
         import threading
-        names, probs = ("cube32_3lvl", "cube64_3lvl"), (0.6, 0.4)
         srv = P.Server(slots_per_hierarchy=4, budget_bytes=120 << 30)
         hs, ids = [], []
         for nm in names:
@@ -777,6 +779,10 @@ def run_msp(args):
     serving = None
     if args.serve > 0 and world == 1:
         serving = measure_serving(args.serve, args.serve_rate)
+    if args.serve_trace and world == 1:
+        trace = measure_serving(2000, 200.0, names=("cube32_3lvl", "cube64_3lvl", "cube128_4lvl"),
+                                probs=(0.5, 0.35, 0.15))
+        serving = dict(serving or {}, trace=trace)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

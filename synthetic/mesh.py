@@ -173,6 +173,12 @@ WORKLOADS = {
     # factorisation (the 48^3 one is cube48_3lvl)
     "cube32b_3lvl": dict(ns=(32, 16, 8), parts=((5, 5, 5), (3, 3, 3)), delta=2, nu=2,
                          coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
+    # the largest serving hierarchy: 128^3 (2,146,689 nodes, 12.6M tets) with
+    # 64^3 / 32^3 / 16^3 coarse levels (four levels: a 32^3 coarsest level would
+    # need a 10 GB dense factor), 16^3 boxes of ~500 owned DoFs on the finest
+    # level and 8^3 on the coarser smoothed ones
+    "cube128_4lvl": dict(ns=(128, 64, 32, 16), parts=((16, 16, 16), (8, 8, 8), (8, 8, 8)), delta=2, nu=2,
+                         coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30),
     # precision study: L-shaped domain (unit cube minus [0.5,1]^3), 96^3 with
     # 48^3/24^3/12^3 coarse levels, 2048 subdomains of 294-1320 DoFs on the
     # finest level, k spanning 1e-2 .. 1e2 (s = 1.15: |sum_j 0.5 mu_j cos| <= 4),

@@ -183,6 +183,13 @@ struct msp_instance {
   double* hpin = nullptr;  // pinned host staging
   cudaStream_t aux[2] = {nullptr, nullptr};  // coarser levels factor concurrently
   cudaStream_t cap = nullptr;  // private origin stream of the factorisation's graph capture
+  // FP64 factors: the blocks of every persistent level as one longest-first
+  // work list, one launch factors them all
+  BlockItem* fz_items = nullptr;
+  int32_t *fz_ptr = nullptr, *fz_list = nullptr;
+  int fz_grid = 0;
+  bool fz_f32 = false;
+  double fz_flops = 0;
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   // per level, for the tile-step factorisation: the stream of the work off
   // the critical chain, and its events (diag done, critical panel done, bulk done)
@@ -658,15 +665,24 @@ int enqueue_factor(msp_instance* I, cudaStream_t s0, bool defer = false) {
       else
         factor_ilu<float>(I, l, static_cast<float*>(I->fac[l]), s);
     } else if (st == Store::F64) {
-      factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s, false, defer);
+      factor_level<double>(I, l, static_cast<double*>(I->fac[l]), s, false, defer || I->fz_grid > 0);
     } else if (st == Store::F32) {
-      factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s, false, defer);
+      factor_level<float>(I, l, static_cast<float*>(I->fac[l]), s, false, defer || I->fz_grid > 0);
     } else {
       factor_level<float>(I, l, I->work[l], s, /*tensor=*/true);
       ProfScope ps(I->prof, PK_EXTRACT, s);
       launch_round_bf16(I->work[l], static_cast<__nv_bfloat16*>(I->fac[l]), h->dev[l].fac_elems, s);
       ps.account((double)h->dev[l].fac_elems * 6, 0);
     }
+  }
+  // the persistent levels' blocks in one launch, once every level is extracted
+  if (I->fz_grid > 0 && !defer) {
+    for (int l = 1; l < L; ++l)
+      if (h->dev[l].fac_blocks && !h->dev[l].ilu) MSP_CUDA(cudaStreamWaitEvent(s0, I->bev[l][0], 0));
+    ProfScope ps(I->prof, PK_LDLT_BLOCKS, s0);
+    if (I->fz_f32) launch_ldlt_blocks_batch<float>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0);
+    else launch_ldlt_blocks_batch<double>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0);
+    ps.account(0, I->fz_flops);
   }
   for (int a = 0; a < 2; ++a) {
     MSP_CUDA(cudaEventRecord(I->join[a], I->aux[a]));
@@ -1053,6 +1069,45 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
   I->part = A.alloc<double>((size_t)(I->m + 1) * kDotBlocks);
   I->hdev = A.alloc<double>(4 * (size_t)(I->m + 1) + 8);
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
+  // FP64 factors: one work list over the blocks of every persistent level
+  // (cost = tile operations, as for one level), balanced longest-first over
+  // the GPU, so that the small blocks of the coarser levels fill the SMs that
+  // finish the fine level early.  (FP32 factors keep one launch per level: a
+  // grid over every SM there slows the FP64 coarsest chain, which bounds that
+  // factorisation.)
+  if (h->opt.factor_precision == MSP_F64) {
+    std::vector<BlockItem> items;
+    std::vector<int64_t> cost;
+    for (int l = 0; l < L; ++l) {
+      const DevLevel& D = h->dev[l];
+      const HostLevel& H = h->host[l];
+      if (!D.fac_blocks || D.ilu) continue;
+      I->fz_flops += D.fac_flops;
+      for (int p = 0; p < H.nsub; ++p) {
+        const int32_t* R = &H.tile_last[H.sub_trow[p]];
+        int64_t c = 0;
+        for (int k = 0; k < H.sub_nt[p]; ++k) {
+          const int64_t rem = R[k] - k;
+          c += 1 + rem + rem * (rem - 1) + rem;
+        }
+        items.push_back(BlockItem{I->fac[l], D.env, p, I->info});
+        cost.push_back(c);
+      }
+    }
+    if (!items.empty()) {
+      int nsm = 0;
+      MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+      I->fz_f32 = h->opt.factor_precision == MSP_F32;
+      const int per_sm = I->fz_f32 ? ldlt_blocks_batch_per_sm<float>() : ldlt_blocks_batch_per_sm<double>();
+      std::vector<int32_t> cptr, clist;
+      lpt_lists(cost, std::max(1, std::min((int)items.size(), nsm * per_sm)), cptr, clist);
+      I->fz_items = A.upload(items);
+      I->fz_ptr = A.upload(cptr);
+      I->fz_list = A.upload(clist);
+      I->fz_grid = (int)cptr.size() - 1;
+      if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
+    }
+  }
   if (cudaMallocHost(&I->hpin, sizeof(double) * (4 * (size_t)(I->m + 1) + 8)) != cudaSuccess) {
     cudaGetLastError();
     return fail(MSP_ERR_OOM, "pinned host allocation failed");

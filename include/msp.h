@@ -68,9 +68,9 @@ typedef enum msp_status {
  *             step run on the BF16 tensor cores, exactly, by splitting each
  *             operand row into eight 7-bit digits scaled to its largest entry
  *             (Ozaki's scheme; 36 digit-pair products, exact FP32 group sums,
- *             64-bit integer combination): every product entry is within a few
- *             units of 2^-54 K max|a_r| max|b_c| of the exact one, the accuracy
- *             class of an FP64 dot product.  Diagonal tiles and the tile steps
+ *             64-bit integer combination): every product entry is within
+ *             2^-48 K max|a_r| max|b_c| of the exact one (worst case), below the
+ *             worst case of an FP64 dot product of length K (K 2^-53 sum|a||b|).  Diagonal tiles and the tile steps
  *             of the other levels stay on the FP64 pipe. */
 typedef enum msp_precision { MSP_F64 = 0, MSP_F32 = 1, MSP_BF16 = 2, MSP_F64_TC = 3 } msp_precision;
 

@@ -863,10 +863,12 @@ __device__ void diag_tiles2(double* __restrict__ t0, double* __restrict__ t1, do
 //   * the groups g = 0..7 are combined in 64-bit integers in units of
 //     2^(e_r + e_c - 56) (group g weighs 2^(46 - 7g); the last one is rounded
 //     to the unit) and converted to FP64 once.  The digit pairs with s + t > 7
-//     are left out: they are below 2^-54 of the bound K max|a_r| max|b_c|, as
-//     are the rounding of the operands to 54 bits and of the group-7 sum.
-// So each product entry is within a few units of 2^-54 K max|a_r| max|b_c| of
-// the exact sum: the accuracy class of an FP64 dot product.  The diagonal tile
+//     are left out: with every digit at its bound they add up to about
+//     2^-49.2 K max|a_r| max|b_c|; the rounding of the operands to 54 bits is
+//     below 2^-53 of it.
+// So each product entry is within 2^-48 K max|a_r| max|b_c| of the exact sum
+// (random digits land far inside): below the worst case of an FP64 dot product
+// of the same length, K 2^-53 sum|a||b|, which reaches 2^-47 of that bound.  The diagonal tile
 // (its L D L^T and X = L^-1, a sequential sweep: diag_tile_pair) stays on the
 // FP64 pipe.  One CTA of 512 threads per SM: 192 KB of digit slabs and all
 // 512 tensor-memory columns.

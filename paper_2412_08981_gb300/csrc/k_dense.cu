@@ -1043,14 +1043,21 @@ __device__ __forceinline__ double oz_to_double(long long V, int er, int ec) {
 __device__ __forceinline__ void oz_issue(uint32_t taddr, const unsigned char* sA, const unsigned char* sB,
                                          uint64_t* bar) {
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
-  for (int s = 0; s < kOzDigits; ++s)
+  // the descriptors of every slab step differ only in the start address
+  // field (address / 16, 14 bits; the slabs lie below 256 KB): one add each
+  const uint64_t a0 = tc::sdesc(sA), b0 = tc::sdesc(sB);
+#pragma unroll 1
+  for (int s = 0; s < kOzDigits; ++s) {
+    const uint64_t as = a0 + (uint64_t)((s * kOzASlab) >> 4);
+#pragma unroll 1
     for (int t = 0; s + t < kOzDigits; ++t) {
       const uint32_t d = taddr + (uint32_t)((s + t) * 64);
+      const uint64_t bt = b0 + (uint64_t)((t * kOzBSlab) >> 4);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        tc::mma_bf16(d, tc::sdesc(sA + s * kOzASlab + 256 * kk), tc::sdesc(sB + t * kOzBSlab + 256 * kk), idesc,
-                     (s > 0 || kk > 0) ? 1 : 0);
+        tc::mma_bf16(d, as + (uint64_t)(16 * kk), bt + (uint64_t)(16 * kk), idesc, (s > 0 || kk > 0) ? 1 : 0);
     }
+  }
   tc::commit(bar);
 }
 

@@ -410,7 +410,11 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
         }
         cost[p] = c;
       }
-      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
+      // the tensor-core kernel fills every SM's shared memory: leave four SMs
+      // to the coarsest block's tile steps, which then run beside it instead of
+      // after it (4 was faster than 8 or 16 at 64^3)
+      const int sms = h->opt.factor_precision == MSP_F64_TC ? std::max(1, nsm - 4) : nsm;
+      lpt_lists(cost, std::max(1, std::min(H.nsub, sms * per_sm)), cptr, clist);
       D.fac_grid = (int)cptr.size() - 1;
       D.fac_cta_ptr = A.upload(cptr);
       D.fac_cta_list = A.upload(clist);

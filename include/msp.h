@@ -429,6 +429,18 @@ MSP_API int msp_profile_enable(msp_instance* inst, uint32_t class_mask);
 MSP_API int msp_profile_reset(msp_instance* inst);
 MSP_API int msp_profile_read(msp_instance* inst, int kclass, msp_kernel_profile* out);
 
+/* ---- failure injection on the host, for tests (no counterpart in the paper) ----
+ * The next `count` staged RAS applications of this instance (the smoothed
+ * levels' triangular solves, Eq. 7) are launched with no tile copies issued:
+ * every bounded wait of those launches on a tile that never arrives runs out
+ * after a short limit, their output is meaningless, and the expiry is
+ * recorded.  No copy is ever in flight and nothing else changes, so the
+ * context stays usable and later calls work normally; msp_solve (and
+ * msp_solve_host) then return MSP_ERR_TIMEOUT, which takes precedence over
+ * the iteration's own status, and clear the record.  count = 0 cancels.
+ * Errors: MSP_ERR_INVALID (NULL instance, count < 0). */
+MSP_API int msp_debug_expire_waits(msp_instance* inst, int count);
+
 /* ---- tensor-core self-check (no counterpart in the paper) ----
  * Multiplies two fixed 128 x 64 BF16 matrices with integer entries on the
  * current device through the library's tcgen05 path (operands in shared
@@ -441,21 +453,24 @@ MSP_API int msp_tensor_selftest(int* mismatches);
 
 /* ---- allocation-free multi-vector dot product ----
  * No counterpart in the paper: a library convenience for callers that may not
- * allocate device memory when they need the result (code running while a
- * stream is captured into a CUDA graph, code under a memory manager that owns
- * all device memory, real-time loops that cannot risk an allocation failing).
- * out_dev[i] = sum_{k<n} V_dev[i*ld + k] * w_dev[k] for i < nv, with the same
- * fixed-order two-stage reduction FGMRES uses, so results are bitwise
- * reproducible.  All pointers are caller-owned device memory; `stream` as
- * above.  The partial sums live in one fixed device array of
- * MSP_NOALLOC_MAX_VECTORS x 296 doubles (148 KiB) that every GPU loading the
- * library holds until exit; the call allocates nothing.  The first call on a
- * device looks up that array's device address with the device current (make
- * that first call before any stream capture).  Every call reuses the array,
- * so calls that overlap on the GPU race; each call overwrites every entry it
- * reads, so nothing needs clearing.  Errors: MSP_ERR_INVALID for nv outside
- * 1..MSP_NOALLOC_MAX_VECTORS, n < 0, ld < n (nv > 1) or NULL pointers;
- * MSP_ERR_CUDA if the launch fails. */
+ * allocate device memory when they need the result (code under a memory
+ * manager that owns all device memory and forbids further allocations,
+ * real-time loops that cannot risk an allocation stalling or failing).
+ * out_dev[i] = sum_{k<n} V_dev[i*ld + k] * w_dev[k] for i < nv, computed by
+ * the same kernels and fixed-order two-stage reduction FGMRES uses for its
+ * Gram-Schmidt coefficients and norms, so results are bitwise those of the
+ * solver's reduction and bitwise reproducible.  All pointers are
+ * caller-owned device memory on the current device; `stream` as above.  The
+ * partial sums live in one fixed device array of MSP_NOALLOC_MAX_VECTORS x
+ * 296 doubles (148 KiB) that every GPU loading the library holds until exit;
+ * the call allocates nothing.  The first call on a device looks up that
+ * array's device address with the device current and keeps it (make that
+ * first call before any stream capture; after cudaDeviceReset of a device
+ * the kept address is stale, so do not call it on that device again).  Every
+ * call reuses the array, so calls that overlap on the GPU race; each call
+ * overwrites every entry it reads, so nothing needs clearing.  Errors:
+ * MSP_ERR_INVALID for nv outside 1..MSP_NOALLOC_MAX_VECTORS, n < 0, ld < n
+ * (nv > 1) or NULL pointers; MSP_ERR_CUDA if the launch fails. */
 #define MSP_NOALLOC_MAX_VECTORS 64
 MSP_API int msp_multidot_noalloc(const double* V_dev, int64_t ld, int nv, const double* w_dev,
                                  int64_t n, double* out_dev, void* stream);

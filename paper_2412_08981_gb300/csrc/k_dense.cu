@@ -42,10 +42,15 @@ template <> struct Acc<__nv_bfloat16> { using type = float; };  // BF16 storage,
 // 1/d by Newton's method for the reciprocal (x <- x + x (1 - d x), which
 // doubles the correct bits per step) from a single-precision seed: two steps
 // take the seed's ~23 bits past double precision.  Shorter dependent chain
-// than a full-precision division on the pivot chain of the factorisation;
-// agrees with 1/d to within an ulp (checked in the GPU tests).  d must be a
-// normal number within the float range (pivots of SPD blocks are).
+// than a full-precision division on the pivot chain of the factorisation.
+// The seed needs d and 1/d inside the normal single-precision range; outside
+// [1e-37, 1e37] (where the float seed would be zero, infinite or subnormal)
+// the reciprocal is the full-precision division instead.  The factor parity
+// tests bound the agreement with 1/d, and a test on meshes scaled by 2^+-133
+// (pivots near 1e40 and 1e-40) runs the division branch.
 __device__ inline double rcp_newton(double d) {
+  const double a = fabs(d);
+  if (!(a >= 1e-37 && a <= 1e37)) return 1.0 / d;
   double x = (double)__frcp_rn((float)d);
   double e = fma(-d, x, 1.0);
   x = fma(x, e, x);
@@ -1289,8 +1294,8 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for the phase of `parity` to complete.  After a first expiry
 // (flag set) later waits give up almost at once.
-__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, volatile int* sflag, int* err) {
-  const long limit = *sflag ? 64 : kWaitLimit;
+__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, volatile int* sflag, int* err, long limit0) {
+  const long limit = *sflag ? 64 : limit0;
   for (long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return;
   *sflag = 1;
@@ -1331,9 +1336,13 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
     const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
     const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
-    double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err) {
+    double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err, int inject) {
   using AT = typename Acc<T>::type;
   constexpr int kConsumers = NCW;
+  // inject != 0 (failure-injection tests only): the producer issues no copies,
+  // so every wait on a full slot runs out after a short limit; no copy is
+  // ever in flight, the output is meaningless and bit 4 of *err is set
+  const long wlim = inject ? 4096 : kWaitLimit;
   constexpr uint32_t kTileBytes = TE * sizeof(T);
   constexpr int NC = kConsumers * 32;       // consumer threads
   constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
@@ -1372,9 +1381,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     long seq = 0;
     auto issue = [&](const T* src) {
       const int slot = (int)(seq % nslot);
-      if (seq >= nslot) mbar_wait(&empty[slot], (uint32_t)(((seq / nslot) - 1) & 1), &sflag, err);
-      mbar_expect_tx(&full[slot], kTileBytes);
-      bulk_g2s(ring + (size_t)slot * TE, src, kTileBytes, &full[slot]);
+      if (seq >= nslot) mbar_wait(&empty[slot], (uint32_t)(((seq / nslot) - 1) & 1), &sflag, err, wlim);
+      if (!inject) {
+        mbar_expect_tx(&full[slot], kTileBytes);
+        bulk_g2s(ring + (size_t)slot * TE, src, kTileBytes, &full[slot]);
+      }
       ++seq;
     };
     for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
@@ -1399,7 +1410,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     // drain: the last copy of every slot has landed before the CTA may exit
     if (lane == 0)
       for (long k = (seq > nslot ? seq - nslot : 0); k < seq; ++k)
-        mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err);
+        mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err, wlim);
     return;
   }
 
@@ -1411,7 +1422,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   long seq = 0;
   auto acquire = [&]() -> const T* {
     const int slot = (int)(seq % nslot);
-    mbar_wait(&full[slot], (uint32_t)((seq / nslot) & 1), &sflag, err);
+    mbar_wait(&full[slot], (uint32_t)((seq / nslot) & 1), &sflag, err, wlim);
     return ring + (size_t)slot * TE;
   };
   auto release = [&]() {
@@ -1789,7 +1800,7 @@ template <typename T, bool W>
 void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
                     const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int max_nt,
                     const int32_t* dir_list, int ndir, const double* t, double* z, int add, int* err,
-                    cudaStream_t s) {
+                    int inject, cudaStream_t s) {
   constexpr int NCW = RasCfg<T, W>::NCW, CTAS = RasCfg<T, W>::CTAS;
   auto kern = k_ras_solve<T, NCW, CTAS>;
   static std::once_flag attr;
@@ -1801,7 +1812,7 @@ void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) + ras_fixed_bytes<T, W>(max_nt);
   if (grid < 1) return;
   kern<<<grid, 32 * (NCW + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list, ndir, t, z, add,
-                                          max_nt, nslot, err);
+                                          max_nt, nslot, err, inject);
 }
 
 template <typename T>
@@ -1809,13 +1820,13 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, const int32_t* sub_ptr,
                       const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, bool wide, cudaStream_t s) {
+                      int* err, bool wide, cudaStream_t s, int inject) {
   if (wide)
     launch_ras_cfg<T, true>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
-                            add, err, s);
+                            add, err, inject, s);
   else
     launch_ras_cfg<T, false>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
-                             add, err, s);
+                             add, err, inject, s);
 }
 
 // CTAs of a 256-thread persistent kernel resident per SM at once: limited by
@@ -1940,7 +1951,7 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
   template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
                                     const int32_t*, const int32_t*, const uint8_t*, int,         \
                                     const int32_t*, int, const double*, double*, int, int*,      \
-                                    bool, cudaStream_t);                                         \
+                                    bool, cudaStream_t, int);                                    \
   template int ras_slots<T>(int, bool);                                                          \
   template int ras_ctas_per_sm<T>(bool);                                                         \
   template void launch_ldlt_blocks_batch<T>(const BlockItem*, const int32_t*, const int32_t*, int,    \
@@ -1958,7 +1969,7 @@ MSP_INST(float)
 template void launch_ras_solve<__nv_bfloat16>(const __nv_bfloat16*, const EnvDev&, const int32_t*,
                                               const int32_t*, int, const int32_t*, const int32_t*,
                                               const uint8_t*, int, const int32_t*, int,
-                                              const double*, double*, int, int*, bool, cudaStream_t);
+                                              const double*, double*, int, int*, bool, cudaStream_t, int);
 template int ras_slots<__nv_bfloat16>(int, bool);
 template int ras_ctas_per_sm<__nv_bfloat16>(bool);
 

@@ -4,11 +4,12 @@
 // library would allocate.
 //
 // Who needs it: callers that may not call cudaMalloc (or any allocator) at
-// the point where they want the result -- code that runs while a stream is
-// being captured into a CUDA graph, code driven by a memory manager that owns
-// all device memory and forbids further allocations, or real-time loops where
-// an allocation's latency or possible failure is not acceptable.  They pass
-// their inputs and outputs; the only other memory touched is the array below.
+// the point where they want the result -- code driven by a memory manager
+// that owns all device memory and forbids further allocations, or real-time
+// loops where an allocation's latency or possible failure is not acceptable.
+// They pass their inputs and outputs; the only other memory touched is the
+// array below.  The kernels are the solver's own (launch_multidot), so the
+// results are bitwise those of the FGMRES reduction.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -16,6 +17,7 @@
 #include <string>
 
 #include "msp.h"
+#include "msp_kernels.h"
 
 namespace msp {
 int fail(int code, const std::string& msg);
@@ -23,7 +25,7 @@ int fail(int code, const std::string& msg);
 
 namespace {
 
-constexpr int kNaBlocks = 296;  // stage-1 blocks per vector (2 per SM)
+constexpr int kNaBlocks = msp::kDotBlocks;  // stage-1 blocks per vector, as in the solver
 
 // Partial sums of every call: MSP_NOALLOC_MAX_VECTORS x kNaBlocks doubles
 // (64 x 296 x 8 B = 151,552 B), resident on every GPU that loads the library
@@ -32,39 +34,11 @@ constexpr int kNaBlocks = 296;  // stage-1 blocks per vector (2 per SM)
 // share the array and race.
 static __device__ __align__(256) double g_noalloc_part[MSP_NOALLOC_MAX_VECTORS * kNaBlocks];
 
-__global__ void k_na_dot_part(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
-                              int64_t n, double* __restrict__ part) {
-  const int i = blockIdx.y;
-  const double* v = V + ld * i;
-  double s = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    s += v[k] * w[k];
-  __shared__ double red[32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    s = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-__global__ void k_na_dot_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
-  const int i = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nparts; b += 32) s += part[(int64_t)i * nparts + b];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (threadIdx.x == 0) out[i] = s;
-}
-
 // Device address of g_noalloc_part, looked up once per device with that
 // device current (in host code the symbol itself is only a host-side stand-in).
+// The cached address belongs to the device's current context: after
+// cudaDeviceReset the array may live elsewhere, so a process that resets a
+// device must not call this entry point on it again.
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mu;
 double* g_na_ptr[kMaxDevices] = {nullptr};
@@ -99,8 +73,7 @@ extern "C" MSP_API int msp_multidot_noalloc(const double* V, int64_t ld, int nv,
   int rc = scratch_for_current_device(&part);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_na_dot_part<<<dim3(kNaBlocks, nv), 256, 0, s>>>(V, ld, w, n, part);
-  k_na_dot_final<<<nv, 32, 0, s>>>(part, kNaBlocks, out);
+  msp::launch_multidot(V, ld, nv, w, n, part, out, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return msp::fail(MSP_ERR_CUDA, std::string("msp_multidot_noalloc: ") + cudaGetErrorString(e));
   return MSP_OK;

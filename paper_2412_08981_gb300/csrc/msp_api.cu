@@ -177,6 +177,7 @@ struct msp_instance {
   std::vector<float*> work;  // per BF16 level: the FP32 factorisation, rounded into fac
   int* info = nullptr;
   int* ras_err = nullptr;  // bit 4: a bounded wait of the staged RAS solve expired
+  int expire_ras = 0;      // msp_debug_expire_waits: staged RAS launches left to starve of copies
   int m = 30;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
   double* xb = nullptr;  // device buffers used by msp_solve_host
@@ -779,18 +780,22 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   if (coarse) {  // one block: both sweeps split over a cluster of CTAs
     launch_block_solve_cluster<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr,
                                        D.sub_dofs, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
-  } else if (st == Store::BF16)
-    launch_ras_solve<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                                    D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                                    D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
-  else if (st == Store::F32)
-    launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                            D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
-                            D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
-  else
-    launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                             D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                             D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s);
+  } else {
+    const int inj = I->expire_ras > 0 ? 1 : 0;
+    if (inj) --I->expire_ras;
+    if (st == Store::BF16)
+      launch_ras_solve<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                                      D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
+                                      D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+    else if (st == Store::F32)
+      launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                              D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
+                              D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+    else
+      launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.ras_cta_ptr,
+                               D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
+                               D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+  }
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
   ps.account(2.0 * (double)D.env_elems * es + (double)D.sum_np * 13 +
@@ -881,7 +886,7 @@ struct Dot {
   }
 };
 
-int fgmres(msp_instance* I, const double* b, double* x, double rtol, msp_stats* st) {
+int fgmres_run(msp_instance* I, const double* b, double* x, double rtol, msp_stats* st) {
   msp_hierarchy* h = I->h;
   cudaStream_t s = I->stream;
   const int64_t n = h->dev[0].n;
@@ -1018,18 +1023,27 @@ int fgmres(msp_instance* I, const double* b, double* x, double rtol, msp_stats* 
   MSP_CUDA(cudaGetLastError());
   st->iterations = it;
   st->rel_residual = rnorm / bnorm;
-  {
-    int e = 0;
-    MSP_CUDA(cudaMemcpyAsync(&e, I->ras_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaStreamSynchronize(s));
-    if (e) {
-      MSP_CUDA(cudaMemsetAsync(I->ras_err, 0, sizeof(int), s));
-      return fail(MSP_ERR_TIMEOUT, "a bounded wait in the staged RAS solve expired");
-    }
-  }
   if (status != MSP_OK)
     return fail(MSP_ERR_NOT_CONVERGED, "FGMRES did not reach rtol within max_it (or broke down)");
   return MSP_OK;
+}
+
+// FGMRES, then the error word of the staged RAS solves: an expired bounded
+// wait makes every result of the solve meaningless, so it is reported
+// (MSP_ERR_TIMEOUT) whatever the iteration itself returned, and cleared.
+int fgmres(msp_instance* I, const double* b, double* x, double rtol, msp_stats* st) {
+  const int rc = fgmres_run(I, b, x, rtol, st);
+  const std::string msg = msp::g_last_error;
+  int e = 0;
+  MSP_CUDA(cudaMemcpyAsync(&e, I->ras_err, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+  MSP_CUDA(cudaStreamSynchronize(I->stream));
+  if (e) {
+    MSP_CUDA(cudaMemsetAsync(I->ras_err, 0, sizeof(int), I->stream));
+    MSP_CUDA(cudaStreamSynchronize(I->stream));
+    return fail(MSP_ERR_TIMEOUT, "a bounded wait in the staged RAS solve expired");
+  }
+  msp::g_last_error = msg;
+  return rc;
 }
 
 int alloc_instance(msp_hierarchy* h, msp_instance* I) {
@@ -1669,6 +1683,13 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
 
 // ---- per-kernel accounting (launch counts, algorithmic bytes/flops, and
 // CUDA-event durations while profiling is on)
+int msp_debug_expire_waits(msp_instance* I, int count) {
+  msp::g_last_error.clear();
+  if (!I || count < 0) return fail(MSP_ERR_INVALID, "NULL instance or negative count");
+  I->expire_ras = count;
+  return MSP_OK;
+}
+
 int msp_profile_enable(msp_instance* I, uint32_t class_mask) {
   if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
   MSP_CUDA(cudaStreamSynchronize(I->stream));

@@ -166,6 +166,8 @@ void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStre
 // set-up); deeper rings let the producer run further ahead.
 // `wide`: one CTA of 16 consumer warps per SM (always the FP64 form); else
 // FP32 / BF16 run 2 / 3 smaller CTAs per SM, each with fewer ring slots.
+// `inject` != 0 (failure-injection tests only): no tile copy is issued, every
+// wait on a full slot runs out after a short limit and bit 4 of *err is set.
 template <typename T>
 int ras_slots(int max_nt, bool wide);
 // CTAs of k_ras_solve that share an SM (the persistent grid is this x SMs)
@@ -176,7 +178,7 @@ void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, const int32_t* sub_ptr,
                       const int32_t* dofs, const uint8_t* own, int max_nt,
                       const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, bool wide, cudaStream_t s);
+                      int* err, bool wide, cudaStream_t s, int inject = 0);
 
 // ---- Krylov helpers (deterministic two-stage reductions)
 // out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles

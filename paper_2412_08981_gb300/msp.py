@@ -125,6 +125,7 @@ EXPORTS = {
     "msp_profile_enable": (C.c_int, [C.c_void_p, C.c_uint32]),
     "msp_profile_reset": (C.c_int, [C.c_void_p]),
     "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
+    "msp_debug_expire_waits": (C.c_int, [C.c_void_p, C.c_int]),
     "msp_multidot_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                        C.c_void_p, C.c_void_p]),
     "msp_instance_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -377,6 +378,11 @@ class Instance:
                                      C.byref(nb)))
         return out
 
+    def expire_waits(self, count=1):
+        """msp_debug_expire_waits: starve the next `count` staged RAS
+        applications of their tile copies (failure-injection tests)."""
+        _check(load().msp_debug_expire_waits(self.inst, int(count)))
+
     def profile_enable(self, classes=()):
         mask = 0
         for c in classes:
@@ -442,12 +448,31 @@ class Server:
 def multidot_noalloc(V, w, out, nv=None, ld=None, n=None, stream=None):
     """msp_multidot_noalloc: out[i] = V_i . w with no device allocation.
 
-    V: device tensor (nv rows of length >= n, row stride ld), w: device
-    vector, out: device tensor of nv doubles (caller-owned).
+    V: CUDA float64 tensor, one vector (1-D) or nv rows (2-D, unit stride
+    along a row, row stride ld); w: CUDA float64 vector; out: CUDA float64
+    tensor of at least nv entries (caller-owned).  The C side sees raw
+    pointers only, so the extents are checked here before the call.
     """
+    for name, t in (("V", V), ("w", w), ("out", out)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError(f"multidot_noalloc: {name} must be a CUDA tensor")
+        if str(t.dtype) != "torch.float64":
+            raise ValueError(f"multidot_noalloc: {name} must be float64")
+        if t.dim() > 0 and t.stride(-1) != 1:
+            raise ValueError(f"multidot_noalloc: {name} needs unit stride along its last axis")
+    if V.dim() not in (1, 2) or w.dim() != 1 or out.dim() != 1:
+        raise ValueError("multidot_noalloc: V must be 1-D or 2-D, w and out 1-D")
     n = int(w.numel()) if n is None else int(n)
     nv = (1 if V.dim() == 1 else int(V.shape[0])) if nv is None else int(nv)
     ld = (n if V.dim() == 1 else int(V.stride(0))) if ld is None else int(ld)
+    if n < 0 or n > w.numel() or n > V.shape[-1]:
+        raise ValueError("multidot_noalloc: n exceeds the length of V or w")
+    if 1 <= nv <= MSP_NOALLOC_MAX_VECTORS:  # other counts: the C side refuses them
+        span = V.untyped_storage().nbytes() // 8 - V.storage_offset()  # doubles readable from V's start
+        if (nv - 1) * ld + n > span:
+            raise ValueError("multidot_noalloc: nv rows of stride ld do not fit in V")
+        if out.numel() < nv:
+            raise ValueError("multidot_noalloc: out holds fewer than nv entries")
     _check(load().msp_multidot_noalloc(_ptr(V), ld, nv, _ptr(w), n, _ptr(out),
                                        _stream_ptr(stream)))
 

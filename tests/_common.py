@@ -50,3 +50,16 @@ def rel(a, b):
     b = np.asarray(b, np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def relmax(a, b):
+    """Element-wise relative difference: max |a - b| over max |b|."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.max(np.abs(b)) if b.size else 0.0
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0)) if a.size else 0.0
+
+
+def close(a, b, tol):
+    """Both the norm-wise and the element-wise relative difference within tol."""
+    return rel(a, b) <= tol and relmax(a, b) <= tol

@@ -252,3 +252,13 @@ def test_tile_envelope_holds_the_full_dense_lu(P, orc, name):
     info = h.info(0)
     nt = h.array(0, "sub_nt").astype(np.int64)
     assert info["factor_elems"] < 0.8 * np.sum(nt * (nt + 1) // 2) * T * T
+
+
+def test_noalloc_binding_checks_its_tensors(P):
+    """The binding of msp_multidot_noalloc refuses tensors whose extents the
+    C side could not check (it sees raw pointers) before any device call."""
+    torch = pytest.importorskip("torch")
+    m = P.msp
+    cpu = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        m.multidot_noalloc(cpu, cpu, cpu)

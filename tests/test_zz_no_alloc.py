@@ -1,13 +1,15 @@
 """The allocation-free dot product (msp_multidot_noalloc) against the solver.
 
 msp_multidot_noalloc serves callers that may not allocate device memory when
-they need a result (for example while a stream is captured into a CUDA
-graph, or under a memory manager that owns all device memory).  It keeps its
-partial sums in a fixed device array instead.  This test checks, through the
-C ABI, that two calls in a row reproduce the relative residual that msp_solve
-(the existing entry point using the same reduction) reports, and agree with a
-plain reference, within the tolerance of the other GPU tests.  It lives in
-its own file so that it is collected last.
+they need a result (for example code under a memory manager that owns all
+device memory, or a real-time loop that cannot risk an allocation stalling or
+failing).  It keeps its partial sums in a fixed device array instead and runs
+the solver's own reduction kernels.  This test checks, through the C ABI,
+that calls in a row reproduce bit for bit the relative residual that
+msp_solve (the existing entry point using the same reduction) reports, that
+repeated calls on the same inputs agree bit for bit, and that the results
+agree with a plain reference within the tolerance of the other GPU tests.
+It lives in its own file so that it is collected last.
 """
 import numpy as np
 import pytest
@@ -44,8 +46,15 @@ def test_noalloc_dot_matches_solver_residual():
     m.multidot_noalloc(bvec, bvec, out[1:2], stream=stream)
     torch.cuda.synchronize()
     rr, bb = out.cpu().numpy()
-    relres = np.sqrt(rr / bb)
-    assert abs(relres - st["rel_residual"]) <= 1e-12 * st["rel_residual"]
+    relres = np.sqrt(rr) / np.sqrt(bb)
+    # the solver's own reduction of the same vectors: the same bits
+    assert relres == st["rel_residual"], (relres, st["rel_residual"])
+    # the same inputs again: bitwise the same results
+    again = torch.empty(2, dtype=torch.float64, device="cuda")
+    m.multidot_noalloc(r, r, again[0:1], stream=stream)
+    m.multidot_noalloc(bvec, bvec, again[1:2], stream=stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(again.cpu().numpy(), out.cpu().numpy())
     rh, bh = r.cpu().numpy(), bvec.cpu().numpy()
     assert abs(rr - rh @ rh) <= 1e-12 * (rh @ rh)
     assert abs(bb - bh @ bh) <= 1e-12 * (bh @ bh)

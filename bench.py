@@ -98,9 +98,9 @@ def parse():
                     help="skip the paper-literal Algorithm 2 and one-level RAS iteration study")
     ap.add_argument("--batch", type=int, default=4,
                     help="concurrent instances of the batched FP32-factor measurement")
-    ap.add_argument("--serve", type=int, default=48,
-                    help="requests of the serving trace (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve", type=int, default=400,
+                    help="requests served from the start of the three-hierarchy trace (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-trace", action="store_true",
                     help="also serve the full trace: 2000 requests at 200/s over 32^3, 64^3 and 128^3 hierarchies "
                          "(probabilities 0.5/0.35/0.15), 120 GB budget")
@@ -591,26 +591,26 @@ def run_msp(args):
             h.close()
         return out
 
-    def measure_serving(nreq, rate, names=("cube32_3lvl", "cube64_3lvl"), probs=(0.6, 0.4)):
-        """Poisson arrivals of seeded mu over resident hierarchies (FP32
-        subdomain factors), served by msp_submit/msp_poll."""
-        import threading
-        srv = P.Server(slots_per_hierarchy=4, budget_bytes=120 << 30)
-        hs, ids = [], []
+    SERVE_NAMES = ("cube32_3lvl", "cube64_3lvl", "cube128_4lvl")
+    SERVE_PROBS = (0.5, 0.35, 0.15)
+
+    def serve_hierarchies(precision, names=SERVE_NAMES):
+        out = []
         for nm in names:
             lv, ww = syn.workload(nm)
             kk = dict(delta=ww["delta"], nu_pre=ww["nu"], nu_post=ww["nu"], restart=ww["restart"],
                       coef=ww["coef"], wave=syn.wave_vectors(), scale=ww["scale"], load=ww["load"])
-            h = P.Hierarchy(lv, precision="f32", **kk)
-            hs.append(h)
-            ids.append(srv.add(h))
-        rng = np.random.default_rng(99)
-        gaps = rng.exponential(1.0 / rate, size=nreq)
-        which = rng.choice(len(names), size=nreq, p=probs)
-        # warm every slot's instance first (not timed)
-        warm = [srv.submit(ids[k], mu_of(900 + k)) for k in range(len(names)) for _ in range(4)]
-        for r in warm:
-            srv.poll(r, None, -1)
+            out.append(P.Hierarchy(lv, precision=precision, **kk))
+        return out
+
+    def serve_run(srv, ids, gaps, which, req0, keep_x=0):
+        """Poisson arrivals (inter-arrival `gaps`, hierarchy `which`) of seeded mu
+        (request numbers req0 + i), submitted on time by a host thread and
+        polled in order.  Returns per-request latency, queueing delay and
+        iterations, the wall time from the first arrival to the last
+        completion, and the solutions of the first `keep_x` requests."""
+        import threading
+        nreq = len(gaps)
         rids = [None] * nreq
         t0 = time.perf_counter()
 
@@ -621,31 +621,132 @@ def run_msp(args):
                 dt = t - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                rids[i] = srv.submit(ids[which[i]], mu_of(5000 + i), rtol=args.rtol)
+                rids[i] = srv.submit(ids[which[i]], mu_of(req0 + i), rtol=args.rtol)
 
         th = threading.Thread(target=submitter)
         th.start()
-        lat, iters = [], []
+        lat, queue, iters, xs = [], [], [], []
         for i in range(nreq):
             while rids[i] is None:
                 time.sleep(0.0005)
-            rc, st = srv.poll(rids[i], None, -1)
+            x = None
+            if i < keep_x:
+                x = np.zeros(hs_n[which[i]])
+            rc, st = srv.poll(rids[i], x, -1)
+            if rc != P.msp.MSP_OK:
+                raise RuntimeError(f"request {i} failed with status {rc}")
             lat.append(st["ms_total"])
+            queue.append(st["ms_queue"])
             iters.append(st["iterations"])
+            if x is not None:
+                xs.append(x)
         th.join()
-        wall = time.perf_counter() - t0
+        return dict(lat=np.array(lat), queue=np.array(queue), iters=np.array(iters),
+                    wall=time.perf_counter() - t0, xs=xs)
+
+    def queue_trend(q):
+        """Mean queueing delay (ms) of the first and the last quarter of the requests."""
+        k = max(1, len(q) // 4)
+        return float(np.mean(q[:k])), float(np.mean(q[-k:]))
+
+    hs_n = []
+
+    def measure_serving(nreq, rate, cap_rates=(0.9, 0.75), cap_seconds=8.0, fp64_sample=40, full=False):
+        """Serving the three-hierarchy trace: Poisson arrivals at `rate`/s of
+        seeded mu on resident 32^3 / 64^3 / 128^3 hierarchies drawn with
+        probabilities 0.5 / 0.35 / 0.15 (the first `nreq` requests of the
+        2000-request trace), FP32 subdomain factors under the FP64 outer loop,
+        4 slots per hierarchy, 120 GB budget, through msp_submit / msp_poll.
+        Then a capacity search: arrivals at fractions of the measured
+        throughput, each for `cap_seconds`, reporting whether the queue grew.
+        And the plain FP64 path on the same mix: the first `fp64_sample`
+        requests solved one after another with FP64 factors (no concurrency),
+        whose solutions are compared with the served ones."""
+        hs = serve_hierarchies("f32")
+        hs_n.clear()
+        hs_n.extend(h.n_dofs(0) for h in hs)
+        srv = P.Server(slots_per_hierarchy=4, budget_bytes=120 << 30)
+        ids = [srv.add(h) for h in hs]
+        rng = np.random.default_rng(99)
+        gaps_all = rng.exponential(1.0 / rate, size=2000)
+        which_all = rng.choice(len(SERVE_NAMES), size=2000, p=SERVE_PROBS)
+        gaps, which = gaps_all[:nreq], which_all[:nreq]
+        # warm every slot's instance first (not timed)
+        warm = [srv.submit(ids[k], mu_of(900 + k)) for k in range(len(hs)) for _ in range(4)]
+        for r in warm:
+            srv.poll(r, None, -1)
+        keep = min(fp64_sample, nreq)
+        tr = serve_run(srv, ids, gaps, which, 5000, keep_x=keep)
+        thr = nreq / tr["wall"]
+        q0, q1 = queue_trend(tr["queue"])
+        out = {"hierarchies": {nm: int((which == k).sum()) for k, nm in enumerate(SERVE_NAMES)},
+               "dofs": {nm: hs_n[k] for k, nm in enumerate(SERVE_NAMES)},
+               "requests": nreq, "of_trace": 2000, "arrival_rate_per_s": rate,
+               "factor_precision": "f32 (FP64 outer loop, SpMV, transfers, coarsest level)",
+               "slots_per_hierarchy": 4, "mem_budget_bytes": 120 << 30,
+               "value": thr, "unit": UNIT,
+               "latency_ms": {"p50": float(np.percentile(tr["lat"], 50)),
+                              "p99": float(np.percentile(tr["lat"], 99))},
+               "queue_ms_first_last_quarter": [q0, q1],
+               "iterations_mean": float(np.mean(tr["iters"])),
+               "timing": "host wall clock from the first arrival to the last completion"}
+        # capacity: the highest of these arrival rates whose queueing delay does not grow
+        cap = []
+        seed = 7000
+        for frac in cap_rates:
+            lam = frac * thr
+            n = max(16, int(lam * cap_seconds))
+            r2 = np.random.default_rng(seed)
+            seed += 1
+            g2 = r2.exponential(1.0 / lam, size=n)
+            w2 = r2.choice(len(SERVE_NAMES), size=n, p=SERVE_PROBS)
+            c = serve_run(srv, ids, g2, w2, 20000 + seed * 1000)
+            a0, a1 = queue_trend(c["queue"])
+            cap.append({"arrival_rate_per_s": lam, "fraction_of_saturated": frac, "requests": n,
+                        "value": n / c["wall"], "unit": UNIT,
+                        "latency_ms": {"p50": float(np.percentile(c["lat"], 50)),
+                                       "p99": float(np.percentile(c["lat"], 99))},
+                        "queue_ms_first_last_quarter": [a0, a1],
+                        "queue_grows": bool(a1 > 2.0 * a0 + 50.0)})
+        out["capacity_runs"] = cap
+        ok = [c for c in cap if not c["queue_grows"]]
+        out["capacity_per_s"] = max((c["arrival_rate_per_s"] for c in ok), default=None)
         srv.close()
+        if keep == 0:
+            for h in hs:
+                h.close()
+            return out
+        # the plain FP64 path, sequentially, on the first requests of the same trace
+        h64 = serve_hierarchies("f64")
+        insts = [h.assemble(mu_of(0), stream=stream) for h in h64]
+        xh = [np.zeros(h.n_dofs(0)) for h in h64]
+        for k, inst in enumerate(insts):  # warm-up (not timed)
+            inst.solve_host(mu_of(900 + k), xh[k], rtol=args.rtol)
+        torch.cuda.synchronize()
+        diffs = []
+        t0 = time.perf_counter()
+        for i in range(keep):
+            k = int(which[i])
+            insts[k].solve_host(mu_of(5000 + i), xh[k], rtol=args.rtol)
+            diffs.append(float(np.linalg.norm(tr["xs"][i] - xh[k]) / np.linalg.norm(xh[k])))
+        t64 = time.perf_counter() - t0
+        v64 = keep / t64
+        out["fp64_sequential"] = {
+            "value": v64, "unit": UNIT, "requests": keep,
+            "hierarchies": {nm: int((which[:keep] == k).sum()) for k, nm in enumerate(SERVE_NAMES)},
+            "what": "the first requests of the same trace, one after another, FP64 factors, no concurrency, "
+                    "through msp_solve_host (host wall clock)"}
+        for inst in insts:
+            inst.close()
+        for h in h64:
+            h.close()
+        out["served_vs_fp64_solution_rel_diff_max"] = max(diffs) if diffs else None
+        out["speedup_vs_fp64_sequential"] = thr / v64
+        if out["capacity_per_s"]:
+            out["capacity_vs_fp64_sequential"] = out["capacity_per_s"] / v64
         for h in hs:
             h.close()
-        return {"requests": nreq, "arrival_rate_per_s": rate,
-                "hierarchies": {nm: int((which == k).sum()) for k, nm in enumerate(names)},
-                "factor_precision": "f32 (FP64 outer loop, SpMV, transfers, coarsest level)",
-                "slots_per_hierarchy": 4, "mem_budget_bytes": 120 << 30,
-                "value": nreq / wall, "unit": UNIT,
-                "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                               "p99": float(np.percentile(lat, 99))},
-                "iterations_mean": float(np.mean(iters)),
-                "timing": "host wall clock from the first arrival to the last completion"}
+        return out
 
     res = measure(args.precision, args.steps, args.warmup)
     hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 and not args.no_hbm else None
@@ -801,9 +902,7 @@ def run_msp(args):
     if args.serve > 0 and world == 1:
         serving = measure_serving(args.serve, args.serve_rate)
     if args.serve_trace and world == 1:
-        trace = measure_serving(2000, 200.0, names=("cube32_3lvl", "cube64_3lvl", "cube128_4lvl"),
-                                probs=(0.5, 0.35, 0.15))
-        serving = dict(serving or {}, trace=trace)
+        serving = dict(serving or {}, trace=measure_serving(2000, 200.0, cap_rates=(), fp64_sample=0))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

@@ -1,0 +1,586 @@
+// Triangular-solve kernels of the msp library (Section 2.2, Eq. 7): the
+// restricted additive Schwarz application z = sum_p R0_p^T (L D L^T)^{-1} R_p t
+// over the subdomain factors of a smoothed level (the staged, persistent
+// k_ras_solve), and the direct solve of the coarsest level's single block on
+// a thread-block cluster (k_block_solve_cluster).  The factors are the tiled
+// envelopes written by k_dense.cu (layout in msp.h): 64 x 64 row-major
+// tiles, diagonal tiles holding L below the diagonal, D on it and the
+// transpose of X = L_II^{-1} above it, so that both sweeps are dense tile
+// products.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "msp_dense.cuh"
+#include "msp_kernels.h"
+
+namespace msp {
+namespace {
+
+// -------------------------------------------------------------- RAS solve
+// Persistent and warp-specialised.  Each CTA (one per SM) takes the
+// subdomains order[b], order[b + G], ... (largest first).  Warp 8 is the
+// producer: one lane streams the factor tiles of every subdomain, in the
+// order the sweeps consume them, into a ring of shared-memory slots with
+// cp.async.bulk, each slot guarded by a "full" mbarrier (transaction count)
+// and an "empty" mbarrier (one arrival per consumer warp).  Warps 0-7 are the
+// consumers: gather t[dofs] -> y; forward sweep over tile rows
+// (y_I = X_II (y_I - sum_{F_I <= J < I} L_IJ y_J)); backward sweep over the column
+// tiles, then the diagonal tile (x_I = X_II^T (y_I / D_I - sum_{I < J <= R_I} L_JI^T x_J));
+// scatter the owned entries.  Every mbarrier wait is bounded: on expiry it
+// records an error bit and goes on (the results are then garbage and the
+// host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
+// own copies, so none is in flight when the CTA exits.
+// Consumer warps per CTA and CTAs per SM.  FP64 sweeps are ALU-bound: one
+// CTA per SM with 16 consumers.  FP32 and BF16 sweeps are bound by the
+// latency of the per-row barriers: two CTAs per SM with 8 consumers each run
+// two subdomains at once on every SM.
+// Levels whose tile band needs more ring slots than that leaves per CTA use
+// the wide form (one CTA of 16 consumers per SM) in every precision.
+template <typename T, bool Wide> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
+template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 2; };
+template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 3; };
+constexpr long kWaitLimit = 1L << 20;
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete.  After a first expiry
+// (flag set) later waits give up almost at once.
+__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, volatile int* sflag, int* err, long limit0) {
+  const long limit = *sflag ? 64 : limit0;
+  for (long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return;
+  *sflag = 1;
+  atomicOr(err, 4);
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+template <int NCW>
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCW * 32) : "memory"); }
+
+// Per-subdomain envelope metadata staged in shared memory (one copy for the
+// producer, which runs ahead, one for the consumers): F_I, R_I and the tile
+// index of (I, F_I), so that no tile address needs a global-memory lookup.
+struct MetaSm {
+  int32_t* first;
+  int32_t* last;
+  int32_t* toff;
+};
+
+// All 32 lanes of the calling warp load the metadata of subdomain p.
+__device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int lane) {
+  const int rb = E.trow[p];
+  for (int I = lane; I < NT; I += 32) {
+    m.first[I] = E.first[rb + I];
+    m.last[I] = E.last[rb + I];
+    m.toff[I] = E.toff[rb + I];
+  }
+}
+
+template <typename T, int NCW, int CTAS>
+__global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
+    const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
+    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
+    double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err, int inject) {
+  using AT = typename Acc<T>::type;
+  constexpr int kConsumers = NCW;
+  // inject != 0 (failure-injection tests only): the producer issues no copies,
+  // so every wait on a full slot runs out after a short limit; no copy is
+  // ever in flight, the output is meaningless and bit 4 of *err is set
+  const long wlim = inject ? 4096 : kWaitLimit;
+  constexpr uint32_t kTileBytes = TE * sizeof(T);
+  constexpr int NC = kConsumers * 32;       // consumer threads
+  constexpr int RW = 64 / kConsumers;       // tile rows per consumer warp
+  constexpr int NPASS = RW / 4;             // 4-row passes of a warp (8 lanes per row)
+  constexpr int CH = kConsumers / 8;        // column halves of the column-wise products (1 or 2)
+  constexpr int NB = 2 / CH;                // 32-column sets per lane in those products
+  static_assert(RW % 4 == 0 && (CH == 1 || CH == 2), "8 or 16 consumer warps");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* ring = reinterpret_cast<T*>(smraw);                                        // [nslot][TE]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + (size_t)nslot * kTileBytes);  // [nslot]
+  uint64_t* empty = full + nslot;                                               // [nslot]
+  AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
+  AT* acc = y + max_nt * 64;                                                    // [64]
+  AT* part = acc + 64;                                                          // [kConsumers][64]
+  AT* red = part + kConsumers * 64;                                             // [64][33] row partials
+  int32_t* meta = reinterpret_cast<int32_t*>(red + 64 * 33);                    // [2][3][max_nt]
+  const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
+  const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
+  __shared__ int sflag;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int rl = lane >> 3, g = lane & 7;            // row within a 4-row pass, lane within the row
+  const int hh = warp % CH, rb = warp / CH;          // column half and 8-row block of the column-wise products
+  const int G = gridDim.x;
+  if (tid == 0) {
+    sflag = 0;
+    for (int s = 0; s < nslot; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kConsumers) {  // ------------------------------------ producer
+    long seq = 0;
+    auto issue = [&](const T* src) {
+      const int slot = (int)(seq % nslot);
+      if (seq >= nslot) mbar_wait(&empty[slot], (uint32_t)(((seq / nslot) - 1) & 1), &sflag, err, wlim);
+      if (!inject) {
+        mbar_expect_tx(&full[slot], kTileBytes);
+        bulk_g2s(ring + (size_t)slot * TE, src, kTileBytes, &full[slot]);
+      }
+      ++seq;
+    };
+    for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+      const int p = cta_list[q];
+      const int NT = E.nt[p];
+      load_meta(E, p, NT, pm, lane);
+      __syncwarp();
+      if (lane == 0) {
+        const T* base = fac + E.fac_off[p];
+        for (int I = 0; I < NT; ++I) {
+          const T* row = base + (int64_t)pm.toff[I] * TE;
+          for (int J = pm.first[I]; J <= I; ++J) issue(row + (int64_t)(J - pm.first[I]) * TE);
+        }
+        for (int I = NT - 1; I >= 0; --I) {
+          for (int J = I + 1; J <= pm.last[I]; ++J)
+            issue(base + (int64_t)(pm.toff[J] + (I - pm.first[J])) * TE);
+          issue(base + (int64_t)(pm.toff[I] + (I - pm.first[I])) * TE);
+        }
+      }
+      __syncwarp();
+    }
+    // drain: the last copy of every slot has landed before the CTA may exit
+    if (lane == 0)
+      for (long k = (seq > nslot ? seq - nslot : 0); k < seq; ++k)
+        mbar_wait(&full[k % nslot], (uint32_t)((k / nslot) & 1), &sflag, err, wlim);
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  for (int d = blockIdx.x * NC + tid; d < ndir; d += G * NC) {
+    const int g = dir_list[d];
+    z[g] = add ? z[g] + t[g] : t[g];
+  }
+  long seq = 0;
+  auto acquire = [&]() -> const T* {
+    const int slot = (int)(seq % nslot);
+    mbar_wait(&full[slot], (uint32_t)((seq / nslot) & 1), &sflag, err, wlim);
+    return ring + (size_t)slot * TE;
+  };
+  auto release = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[seq % nslot]);
+    ++seq;
+  };
+  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+    const int p = cta_list[q];
+    const int NT = E.nt[p];
+    const int off = sub_ptr[p];
+    const int np_ = sub_ptr[p + 1] - off;
+    if (warp == 0) load_meta(E, p, NT, cm, lane);
+    for (int li = tid; li < NT * 64; li += NC) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+    consumers_sync<kConsumers>();
+    // forward sweep
+    for (int I = 0; I < NT; ++I) {
+      // off-diagonal tiles: lane (rl, g) of a warp takes row warp*RW + 4*ps + rl
+      // of pass ps and the columns 8*((c + rl) & 7) + g, c = 0..7 (the four
+      // rows of an access read four different 8-column chunks, so the loads
+      // spread over all banks); two FMA chains per row, 8 partials per row
+      AT se[NPASS], so[NPASS];
+#pragma unroll
+      for (int k = 0; k < NPASS; ++k) se[k] = so[k] = 0;
+      for (int J = cm.first[I]; J < I; ++J) {
+        const T* tl = acquire();
+        const AT* yJ = y + J * 64;
+#pragma unroll
+        for (int ps = 0; ps < NPASS; ++ps) {
+          const T* trow = tl + (warp * RW + 4 * ps + rl) * 64;
+#pragma unroll
+          for (int c = 0; c < 8; c += 2) {
+            const int c0 = 8 * ((c + rl) & 7) + g, c1 = 8 * ((c + 1 + rl) & 7) + g;
+            se[ps] = fma((AT)trow[c0], yJ[c0], se[ps]);
+            so[ps] = fma((AT)trow[c1], yJ[c1], so[ps]);
+          }
+        }
+        release();
+      }
+      // row sums: one thread per row adds the 8 lane partials (a shared-memory
+      // transpose costs far fewer FP64 instructions than warp shuffles)
+#pragma unroll
+      for (int ps = 0; ps < NPASS; ++ps) red[(warp * RW + 4 * ps + rl) * 9 + g] = se[ps] + so[ps];
+      consumers_sync<kConsumers>();
+      if (tid < 64) {
+        const AT* rr = red + tid * 9;
+        const AT v0 = (rr[0] + rr[2]) + (rr[4] + rr[6]), v1 = (rr[1] + rr[3]) + (rr[5] + rr[7]);
+        acc[tid] = y[I * 64 + tid] - (v0 + v1);
+      }
+      consumers_sync<kConsumers>();
+      {  // y_I = X acc, X[b][a] = tile[a][b] for a < b: warp (rb, h) takes rows
+         // a = 8 rb .. 8 rb + 7 and its columns b; (row, column set) pairs with
+         // no a < b are skipped by the whole warp
+        const T* dt = acquire();
+        AT v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int a = rb * 8 + k;
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const int b0 = (CH == 2 ? 32 * hh : 32 * q);
+            if (a < b0 + 31) {
+              const int b = b0 + lane;
+              if (a < b) v[q] = fma((AT)dt[a * 64 + b], acc[a], v[q]);
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = v[q];
+        release();
+      }
+      consumers_sync<kConsumers>();
+      if (tid < 64) {
+        const AT v0 = (part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid]);
+        const AT v1 = (part[64 + tid] + part[192 + tid]) + (part[320 + tid] + part[448 + tid]);
+        y[I * 64 + tid] = acc[tid] + (v0 + v1);
+      }
+      consumers_sync<kConsumers>();
+    }
+    // backward sweep: the column tiles of row I, then its diagonal tile (no
+    // tile is held while another streams in, so two ring slots suffice)
+    for (int I = NT - 1; I >= 0; --I) {
+      // off-diagonal tiles (transposed): warp (rb, h) takes rows 8 rb .. 8 rb + 7
+      // of L_JI and its columns; 8 partials per column
+      AT s[NB][2];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) s[q][0] = s[q][1] = 0;
+      for (int J = I + 1; J <= cm.last[I]; ++J) {
+        const T* tl = acquire();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = rb * 8 + k;
+          const AT xr = y[J * 64 + r];
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            s[q][k & 1] = fma((AT)tl[r * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane], xr, s[q][k & 1]);
+        }
+        release();
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = s[q][0] + s[q][1];
+      consumers_sync<kConsumers>();
+      const T* dt = acquire();  // the diagonal tile, released after its product
+      if (tid < 64) {
+        const AT v0 = (part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid]);
+        const AT v1 = (part[64 + tid] + part[192 + tid]) + (part[320 + tid] + part[448 + tid]);
+        acc[tid] = y[I * 64 + tid] / (AT)dt[tid * 65] - (v0 + v1);
+      }
+      consumers_sync<kConsumers>();
+      // x_I[a] = acc[a] + sum_{b>a} tile[a][b] acc[b]: lane (rl, g) takes row
+      // a = warp*RW + 4*ps + rl and the columns 8c + g; chunks c with no b > a
+      // for the pass's four rows are skipped by the whole warp
+#pragma unroll
+      for (int ps = 0; ps < NPASS; ++ps) {
+        const int amin = warp * RW + 4 * ps, a = amin + rl;
+        AT e0 = 0, e1 = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (8 * c + 7 > amin) {
+            const int b = 8 * c + g;
+            if (b > a) {
+              if (c & 1)
+                e1 = fma((AT)dt[a * 64 + b], acc[b], e1);
+              else
+                e0 = fma((AT)dt[a * 64 + b], acc[b], e0);
+            }
+          }
+        }
+        red[a * 9 + g] = e0 + e1;
+      }
+      release();
+      consumers_sync<kConsumers>();
+      if (tid < 64) {
+        const AT* rr = red + tid * 9;
+        const AT v0 = (rr[0] + rr[2]) + (rr[4] + rr[6]), v1 = (rr[1] + rr[3]) + (rr[5] + rr[7]);
+        y[I * 64 + tid] = acc[tid] + (v0 + v1);
+      }
+      consumers_sync<kConsumers>();
+    }
+    for (int li = tid; li < np_; li += NC) {
+      if (own[off + li]) {
+        const int g = dofs[off + li];
+        z[g] = add ? z[g] + (double)y[li] : (double)y[li];
+      }
+    }
+    consumers_sync<kConsumers>();
+  }
+}
+
+// ------------------------------------------- single-block solve on a cluster
+// The coarsest level is one block (one CTA would use one SM's FP64 pipe), so
+// its sweeps run on a cluster of kCl CTAs.  Every CTA keeps the whole
+// right-hand side / solution vector in its shared memory.  Forward, tile row
+// I: CTA c owns rows 8c..8c+7; it sums its rows of the off-diagonal tiles,
+// sends its 8 results to every CTA (distributed shared memory), the cluster
+// synchronises, each CTA applies its rows of X_II, sends them, synchronises.
+// Backward, tile row I: CTA c owns the columns 8c..8c+7 of L_JI^T x_J and the
+// rows 8c..8c+7 of X_II^T, with the same two exchanges.
+constexpr int kCl = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_solve_cluster(
+    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ sub_ptr,
+    const int32_t* __restrict__ dofs, const int32_t* __restrict__ dir_list, int ndir,
+    const double* __restrict__ t, double* __restrict__ z, int add) {
+  using AT = typename Acc<T>::type;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int me = (int)cl.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p = 0;
+  const int NT = E.nt[p], rb = E.trow[p];
+  const int off = sub_ptr[p], np_ = sub_ptr[p + 1] - off;
+  extern __shared__ unsigned char smraw[];
+  AT* y = reinterpret_cast<AT*>(smraw);  // [NT*64] the whole vector, in every CTA
+  AT* acc = y + NT * 64;                 // [64] exchanged partial results
+  AT* red = acc + 64;                    // [8][32] backward column partials
+  const T* base = fac + E.fac_off[p];
+  for (int d = me * 256 + tid; d < ndir; d += kCl * 256) {
+    const int g = dir_list[d];
+    z[g] = add ? z[g] + t[g] : t[g];
+  }
+  for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+  cl.sync();
+  const int r8 = 8 * me;  // this CTA's 8 rows (columns)
+  // sends v (this CTA's row/column r8 + k) to every CTA's array `dst`
+  auto send8 = [&](AT* dst, int k, AT v) {
+    for (int c = 0; c < kCl; ++c) cl.map_shared_rank(dst, c)[r8 + k] = v;
+  };
+  // ---- forward
+  for (int I = 0; I < NT; ++I) {
+    const int F = E.first[rb + I];
+    const T* rowt = base + (int64_t)E.toff[rb + I] * TE;
+    {  // warp w: row r8 + w of the off-diagonal tiles
+      const int r = r8 + warp;
+      AT s0 = 0, s1 = 0;
+      for (int J = F; J < I; ++J) {
+        const T* tl = rowt + (int64_t)(J - F) * TE;
+        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
+        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+      }
+      AT v = s0 + s1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(acc, lane)[r] = y[I * 64 + r] - v;
+    }
+    cl.sync();
+    {  // warp w: y_I[b], b = r8 + w: acc[b] + sum_{a<b} X[b][a] acc[a], X[b][a] = dt[a][b]
+      const T* dt = rowt + (int64_t)(I - F) * TE;
+      const int b = r8 + warp;
+      AT v = 0;
+      if (lane < b) v = fma((AT)dt[lane * 64 + b], acc[lane], v);
+      if (lane + 32 < b) v = fma((AT)dt[(lane + 32) * 64 + b], acc[lane + 32], v);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + b] = acc[b] + v;
+    }
+    cl.sync();
+  }
+  // ---- backward
+  for (int I = NT - 1; I >= 0; --I) {
+    const int R = E.last[rb + I];
+    const T* dt = base + (int64_t)(E.toff[rb + I] + (I - E.first[rb + I])) * TE;
+    {  // column col = r8 + (tid & 7); rows split over 32 groups of 2
+      const int col = r8 + (tid & 7), rg = tid >> 3;
+      AT v = 0;
+      for (int J = I + 1; J <= R; ++J) {
+        const T* tl = base + (int64_t)(E.toff[rb + J] + (I - E.first[rb + J])) * TE;
+        v = fma((AT)tl[(2 * rg) * 64 + col], y[J * 64 + 2 * rg], v);
+        v = fma((AT)tl[(2 * rg + 1) * 64 + col], y[J * 64 + 2 * rg + 1], v);
+      }
+      // the 4 row groups inside a warp share a column: lanes l, l^8, l^16, l^24
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      if (lane < 8) red[warp * 8 + lane] = v;
+      __syncthreads();
+      if (tid < 8) {
+        AT sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += red[w * 8 + tid];
+        const int c = r8 + tid;
+        send8(acc, tid, y[I * 64 + c] / (AT)dt[c * 65] - sum);
+      }
+    }
+    cl.sync();
+    {  // warp w: x_I[a], a = r8 + w: acc[a] + sum_{b>a} dt[a][b] acc[b]
+      const int a2 = r8 + warp;
+      AT v = 0;
+      if (lane > a2) v = fma((AT)dt[a2 * 64 + lane], acc[lane], v);
+      if (lane + 32 > a2) v = fma((AT)dt[a2 * 64 + lane + 32], acc[lane + 32], v);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + a2] = acc[a2] + v;
+    }
+    cl.sync();
+  }
+  for (int li = me * 256 + tid; li < np_; li += kCl * 256) {
+    const int g = dofs[off + li];
+    z[g] = add ? z[g] + (double)y[li] : (double)y[li];
+  }
+}
+
+}  // namespace
+
+// Ring depth of the staged solve: as many tile slots as shared memory holds,
+// up to 16 (BF16 and FP32 tiles are small; more bytes in flight per SM hide
+// more of the HBM latency).
+constexpr size_t kMaxSlots = 16;
+
+// Dynamic shared memory one CTA of a k_ras_solve configuration may use.
+template <typename T, bool W>
+size_t ras_smem_budget() {
+  constexpr int C = RasCfg<T, W>::CTAS;
+  if (C == 1) return (size_t)limits().smem;
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  return std::min((size_t)limits().smem, (size_t)per_sm / C - 2048);  // per-CTA reservation and static smem
+}
+
+template <typename T, bool W>
+size_t ras_fixed_bytes(int max_nt) {
+  using AT = typename Acc<T>::type;
+  return ((size_t)max_nt * 64 + 64 + RasCfg<T, W>::NCW * 64 + 64 * 33) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+}
+
+template <typename T, bool W>
+int ras_slots_cfg(int max_nt) {
+  const size_t fixed = ras_fixed_bytes<T, W>(max_nt);
+  const size_t per_slot = (size_t)TE * sizeof(T) + 2 * sizeof(uint64_t);
+  const size_t smem = ras_smem_budget<T, W>();
+  if (smem <= fixed) return 0;
+  return (int)std::min<size_t>(kMaxSlots, (smem - fixed) / per_slot);
+}
+
+template <typename T>
+int ras_ctas_per_sm(bool wide) {
+  return wide ? RasCfg<T, true>::CTAS : RasCfg<T, false>::CTAS;
+}
+
+template <typename T>
+int ras_slots(int max_nt, bool wide) {
+  return wide ? ras_slots_cfg<T, true>(max_nt) : ras_slots_cfg<T, false>(max_nt);
+}
+
+template <typename T, bool W>
+void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
+                    const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int max_nt,
+                    const int32_t* dir_list, int ndir, const double* t, double* z, int add, int* err,
+                    int inject, cudaStream_t s) {
+  constexpr int NCW = RasCfg<T, W>::NCW, CTAS = RasCfg<T, W>::CTAS;
+  auto kern = k_ras_solve<T, NCW, CTAS>;
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ras_smem_budget<T, W>());
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  });
+  const int nslot = ras_slots_cfg<T, W>(max_nt);  // the host checked at set-up that this is enough
+  const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) + ras_fixed_bytes<T, W>(max_nt);
+  if (grid < 1) return;
+  kern<<<grid, 32 * (NCW + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list, ndir, t, z, add,
+                                          max_nt, nslot, err, inject);
+}
+
+template <typename T>
+void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
+                      const int32_t* cta_list, int grid, const int32_t* sub_ptr,
+                      const int32_t* dofs, const uint8_t* own, int max_nt,
+                      const int32_t* dir_list, int ndir, const double* t, double* z, int add,
+                      int* err, bool wide, cudaStream_t s, int inject) {
+  if (wide)
+    launch_ras_cfg<T, true>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
+                            add, err, inject, s);
+  else
+    launch_ras_cfg<T, false>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
+                             add, err, inject, s);
+}
+
+template <typename T>
+void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
+                                const int32_t* dofs, int max_nt, const int32_t* dir_list,
+                                int ndir, const double* t, double* z, int add, cudaStream_t s) {
+  using AT = typename Acc<T>::type;
+  const size_t smem = ((size_t)max_nt * 64 + 64 + 64) * sizeof(AT);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_block_solve_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         limits().smem);
+  });
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCl, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr1[1];
+  attr1[0].id = cudaLaunchAttributeClusterDimension;
+  attr1[0].val.clusterDim.x = kCl;
+  attr1[0].val.clusterDim.y = 1;
+  attr1[0].val.clusterDim.z = 1;
+  cfg.attrs = attr1;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_block_solve_cluster<T>, fac, E, sub_ptr, dofs, dir_list, ndir, t, z, add);
+}
+
+#define MSP_RAS_INST(T)                                                                          \
+  template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
+                                    const int32_t*, const int32_t*, const uint8_t*, int,         \
+                                    const int32_t*, int, const double*, double*, int, int*,      \
+                                    bool, cudaStream_t, int);                                    \
+  template int ras_slots<T>(int, bool);                                                          \
+  template int ras_ctas_per_sm<T>(bool);
+MSP_RAS_INST(double)
+MSP_RAS_INST(float)
+// BF16 factors: only the solve reads them (they are factored in FP32)
+MSP_RAS_INST(__nv_bfloat16)
+template void launch_block_solve_cluster<double>(const double*, const EnvDev&, const int32_t*, const int32_t*, int,
+                                                 const int32_t*, int, const double*, double*, int, cudaStream_t);
+template void launch_block_solve_cluster<float>(const float*, const EnvDev&, const int32_t*, const int32_t*, int,
+                                                const int32_t*, int, const double*, double*, int, cudaStream_t);
+
+}  // namespace msp

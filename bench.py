@@ -104,6 +104,10 @@ def parse():
     ap.add_argument("--serve-trace", action="store_true",
                     help="also serve the full trace: 2000 requests at 200/s over 32^3, 64^3 and 128^3 hierarchies "
                          "(probabilities 0.5/0.35/0.15), 120 GB budget")
+    ap.add_argument("--profile-ops", default=None,
+                    help="profiling mode: run each of the comma-separated operators of the finest level once "
+                         "(J, P, PT, RAS, factor) inside an NVTX range of that name, for single-kernel ncu "
+                         "captures (ncu --nvtx --nvtx-include NAME/), print their algorithmic bytes and exit")
     ap.add_argument("--cpu-sample", type=int, default=64,
                     help="fine subdomains factored/solved by the CPU baseline sample (512 / 64 = x8)")
     return ap.parse_args()
@@ -460,9 +464,11 @@ def run_msp(args):
         clock over the same parameters:
           streams: every instance on its own stream and host thread, each
             re-assembling, factoring and solving its share in turn;
-          batch: rounds of `group` parameters, each round re-assembled per
-            instance, factored with ONE msp_factor_batch (the persistent-level
-            blocks of all of them in one launch), then solved concurrently."""
+          batch: rounds of `group` parameters through one msp_batch: one
+            msp_batch_assemble, one msp_batch_factor (the persistent-level
+            blocks of all of them in one launch), one msp_solve_batch (FGMRES
+            of all of them in lockstep, each V-cycle and Krylov step one
+            launch per kernel for the whole round)."""
         import threading
         hs = []
         for name in ("cube32b_3lvl", "cube48_3lvl"):
@@ -499,18 +505,16 @@ def run_msp(args):
                     errs.append(e)
             run_threads(worker, group)
 
+        batch = P.msp.Batch(insts, stream=bstream)
+        batch_iters = []
+
         def batch_way(lo, hi):
             for r0 in range(lo, hi, group):
-                for b in range(min(group, hi - r0)):
-                    insts[b].reassemble(mu_of(r0 + b))
-                P.msp.factor_batch(insts[:min(group, hi - r0)], stream=bstream)
-
-                def worker(b):
-                    try:
-                        insts[b].solve(xs[b], rtol=args.rtol)
-                    except Exception as e:
-                        errs.append(e)
-                run_threads(worker, min(group, hi - r0))
+                assert hi - r0 >= group
+                batch.assemble([mu_of(r0 + b) for b in range(group)])
+                batch.factor()
+                st = batch.solve(xs, rtol=args.rtol)
+                batch_iters.extend(x["iterations"] for x in st)
 
         for name, fn in (("streams", streams_way), ("batch", batch_way)):
             fn(5000, 5000 + group)  # warm-up
@@ -520,6 +524,13 @@ def run_msp(args):
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             out[name] = {"value": total / wall, "unit": UNIT, "wall_s": round(wall, 3)}
+        out["batch"]["how"] = ("rounds of 16 parameters through one msp_batch: msp_batch_assemble, msp_batch_factor "
+                               "(the persistent levels' blocks of all 16 in one launch, replayed from a CUDA graph), "
+                               "msp_solve_batch (the 16 FGMRES solves in lockstep, every V-cycle and Krylov launch "
+                               "shared)")
+        out["batch"]["iterations_mean"] = float(np.mean(batch_iters)) if batch_iters else None
+        out["batch_vs_streams"] = out["batch"]["value"] / out["streams"]["value"]
+        batch.close()
         for inst in insts:
             inst.close()
         for h in hs:
@@ -748,15 +759,20 @@ def run_msp(args):
             h.close()
         return out
 
+    if args.profile_ops:
+        profile_ops(P, torch, levels, kw, args)
+        return
     res = measure(args.precision, args.steps, args.warmup)
     hbm = measure_hbm_kernels() if world == 1 and len(levels) > 1 and not args.no_hbm else None
     if hbm is not None and args.workload == "cube64_3lvl":
         # the same operators on the 96^3 L-shaped domain, whose level-0 matrix
-        # (802,081 rows, ~12M nonzeros, ~160 MB) is larger than the L2 cache
-        lv96, w96 = syn.workload("lshape96_4lvl")
-        hbm["lshape96_4lvl"] = measure_hbm_kernels(
-            lv=lv96, opts=dict(delta=w96["delta"], nu_pre=w96["nu"], nu_post=w96["nu"], restart=w96["restart"],
-                               coef=w96["coef"], wave=syn.wave_vectors(), scale=w96["scale"], load=w96["load"]))
+        # (802,081 rows, ~12M nonzeros, ~160 MB) is larger than the L2 cache,
+        # and on the 128^3 cube (2.15M rows, 31.8M nonzeros, ~430 MB)
+        for big in ("lshape96_4lvl", "cube128_4lvl"):
+            lvb, wb = syn.workload(big)
+            hbm[big] = measure_hbm_kernels(
+                lv=lvb, opts=dict(delta=wb["delta"], nu_pre=wb["nu"], nu_post=wb["nu"], restart=wb["restart"],
+                                  coef=wb["coef"], wave=syn.wave_vectors(), scale=wb["scale"], load=wb["load"]))
     ms = max_over_ranks(res["ms"])
     value = whole_job_rate(args.steps, world, ms)
     mixed = None
@@ -1008,6 +1024,55 @@ def traffic_for(kernel, prof):
     except OSError:
         return None
     return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------- profiling mode
+def profile_ops(P, torch, levels, kw, args):
+    """Each requested operator of the finest level once, inside an NVTX range
+    named after it, after an untimed warm-up call outside the ranges; for
+    single-kernel ncu captures (ncu --nvtx --nvtx-include NAME/ -c 1).  Prints
+    the algorithmic bytes of each (the same formulas as hbm_kernels; for the
+    factorisation, the stored envelopes read and written once)."""
+    import synthetic as syn
+    ops = [o.strip() for o in args.profile_ops.split(",") if o.strip()]
+    h = P.Hierarchy(levels, precision=args.precision, **kw)
+    stream = torch.cuda.current_stream()
+    inst = h.assemble(syn.mu_draw(0), stream=stream)
+    i0, i1 = h.info(0), h.info(1)
+    n0, n1 = i0["n_dofs"], i1["n_dofs"]
+    es = {"f64": 8, "f64tc": 8, "f32": 4, "bf16": 2}[args.precision]
+    m = P.msp
+    table = {"J": (m.MSP_OP_SPMV, n0, n0, 12 * i0["nnz"] + 4 * (n0 + 1) + 16 * n0),
+             "P": (m.MSP_OP_INTERP, n1, n0, 12 * i0["P_nnz"] + 4 * (n0 + 1) + 8 * n1 + 8 * n0),
+             "PT": (m.MSP_OP_RESTRICT, n0, n1, 12 * i0["R_nnz"] + 4 * (n1 + 1) + 8 * n0 + 8 * n1),
+             "RAS": (m.MSP_OP_RAS, n0, n0, 2 * i0["factor_elems"] * es + 13 * i0["sub_dofs"] + 8 * n0)}
+    out = {"workload": args.workload, "precision": args.precision, "ops": {}}
+    inst.factor()
+    if "factor" in ops:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("factor")
+        inst.factor()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        env = sum(h.info(l)["factor_elems"] for l in range(h.nlevels - 1) if h.info(l)["fac_ctas"] > 0)
+        out["ops"]["factor"] = {"envelope_bytes_read_and_written": 2 * env * es,
+                                "levels": [l for l in range(h.nlevels - 1) if h.info(l)["fac_ctas"] > 0]}
+    for name in ops:
+        if name not in table:
+            continue
+        op, nin, nout, nbytes = table[name]
+        x = torch.rand(nin, dtype=torch.float64, device="cuda")
+        y = torch.zeros(nout, dtype=torch.float64, device="cuda")
+        inst.apply_op(op, 0, x, y)  # warm-up, outside the range
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(name)
+        inst.apply_op(op, 0, x, y)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        out["ops"][name] = {"algorithmic_bytes": int(nbytes)}
+    inst.close()
+    h.close()
+    print(json.dumps(out), flush=True)
 
 
 # -------------------------------------------------------- reference arm

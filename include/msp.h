@@ -275,6 +275,60 @@ MSP_API int msp_factor(msp_instance* inst);
  * The profiling counters do not include the batched launch. */
 MSP_API int msp_factor_batch(msp_instance* const* insts, int n, void* stream);
 
+/* ---- batched solves: several instances, shared launches ----
+ * A batch groups up to 32 factored instances (of one hierarchy or of several,
+ * e.g. parameters of a family on meshes of different sizes) whose FGMRES
+ * solves then run in lockstep with their launches fused: per level depth one
+ * staged RAS launch over the blocks of every member (per factor type), one
+ * SpMV launch per operator and schedule over the members' stacked rows, one
+ * coarsest-solve launch with a cluster per member, one launch per Krylov
+ * kernel, and one host synchronisation per iteration for the whole batch.
+ * Each member's arithmetic is exactly that of its own msp_solve (the same
+ * per-row, per-block and per-slice code in the same order), so its solution,
+ * iterations and residual are bitwise those of msp_solve.
+ *
+ * msp_batch_create: insts holds n distinct instances (host array, copied; the
+ * instances must outlive the batch and keep their factor storage, i.e. stay
+ * allocated).  All members need the same nu_pre / nu_post, the directly
+ * solved coarsest level and the exact subdomain LU (no ILU(p) levels); any
+ * factor precision, also mixed within a batch.  stream: the stream the
+ * batched work runs on (NULL: the first member's).  The call allocates the
+ * fused launches' work lists (device memory, through the members'
+ * allocator) and builds them on the host.  Errors: MSP_ERR_INVALID (n
+ * outside 1..32, NULL or repeated members, members that differ as above or
+ * live on different devices), MSP_ERR_OOM, MSP_ERR_CUDA.
+ *
+ * msp_solve_batch: FGMRES (as msp_solve) for every member at once, member i
+ * solving J_i x_i = b_i with b_dev[i] (device, or NULL entries / a NULL
+ * array for the assembled load vectors) into x_dev[i] (device).  Every member
+ * must be factored (msp_factor or msp_factor_batch after its last
+ * re-assembly).  The batch stream waits for each member's stream first, and
+ * each member's stream waits for the batch at the end; the call synchronises
+ * the batch stream.  st: NULL or n msp_stats, filled per member (ms_solve is
+ * the batch's wall time).  Returns MSP_OK when every member converged, else
+ * the first failing member's status (MSP_ERR_TIMEOUT for an expired bounded
+ * wait first, MSP_ERR_NOT_CONVERGED, ...); the per-member statuses are in st. */
+typedef struct msp_batch msp_batch;
+MSP_API int msp_batch_create(msp_instance* const* insts, int n, void* stream, msp_batch** out);
+MSP_API void msp_batch_free(msp_batch* b);
+/* msp_batch_assemble: msp_reassemble of every member (Eq. 2-4 for its mu),
+ * member i's parameters at mu[i * n_mu .. (i+1) * n_mu) (host), each on its own
+ * stream, one synchronisation for all.  Errors as msp_reassemble. */
+MSP_API int msp_batch_assemble(msp_batch* b, const double* mu, int n_mu);
+/* msp_batch_factor: msp_factor of every member (Eq. 6), with the blocks of the
+ * persistent levels of every FP64 / FP32 member in ONE persistent launch per
+ * factor type over the batch (longest blocks first, on all SMs but a few that
+ * the members' coarsest-block tile steps keep), the other levels on each
+ * member's own streams concurrently.  Each block's arithmetic is that of
+ * msp_factor, so the factors are bitwise the same.  From the second call on,
+ * the whole batched factorisation replays from one CUDA graph.  Synchronises
+ * the batch stream.  Errors: MSP_ERR_INVALID (a member not assembled),
+ * MSP_ERR_INTERNAL (a pivot; that member stays unfactored), MSP_ERR_TIMEOUT,
+ * MSP_ERR_CUDA. */
+MSP_API int msp_batch_factor(msp_batch* b);
+MSP_API int msp_solve_batch(msp_batch* b, const double* const* b_dev, double* const* x_dev, double rtol,
+                            msp_stats* st);
+
 /* One application of the V-cycle preconditioner of Algorithm 2 (z = B^{-1} r)
  * with the fine->coarse transfer P^T, coarse->fine P and a direct coarsest
  * solve.  r_dev, z_dev: device arrays of n_dofs(level 0) doubles; they must

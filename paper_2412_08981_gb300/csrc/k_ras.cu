@@ -108,13 +108,18 @@ __device__ inline void load_meta(const EnvDev& E, int p, int NT, MetaSm m, int l
   }
 }
 
+// One launch may serve the same level of several instances (a batch): every
+// work item is (view v, block p), encoded (v << kViewShift) | p in the CTA
+// lists; view v gives the level's factors, envelope, subdomains, Dirichlet
+// nodes and error word, and vecs.t[v] / vecs.z[v] its input and output
+// (vecs.z[v] == NULL: the view sits this launch out -- its items are skipped
+// by producer and consumers alike).  A block's arithmetic does not depend on
+// the launch it is part of.
 template <typename T, int NCW, int CTAS>
 __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
-    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ cta_ptr,
-    const int32_t* __restrict__ cta_list, const int32_t* __restrict__ sub_ptr,
-    const int32_t* __restrict__ dofs, const uint8_t* __restrict__ own,
-    const int32_t* __restrict__ dir_list, int ndir, const double* __restrict__ t,
-    double* __restrict__ z, int add, int max_nt, int nslot, int* __restrict__ err, int inject) {
+    const RasView* __restrict__ views, int nviews, const __grid_constant__ RasVecs vecs,
+    const int32_t* __restrict__ cta_ptr, const int32_t* __restrict__ cta_list, int add, int max_nt,
+    int nslot, int inject) {
   using AT = typename Acc<T>::type;
   constexpr int kConsumers = NCW;
   // inject != 0 (failure-injection tests only): the producer issues no copies,
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   }
   __syncthreads();
 
+  int* err = views[0].err;  // the error word of the item in hand
   if (warp == kConsumers) {  // ------------------------------------ producer
     long seq = 0;
     auto issue = [&](const T* src) {
@@ -167,12 +173,15 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       ++seq;
     };
     for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
-      const int p = cta_list[q];
+      const int vw = cta_list[q] >> kViewShift, p = cta_list[q] & ((1 << kViewShift) - 1);
+      if (vecs.z[vw] == nullptr) continue;
+      const EnvDev& E = views[vw].E;
+      err = views[vw].err;
       const int NT = E.nt[p];
       load_meta(E, p, NT, pm, lane);
       __syncwarp();
       if (lane == 0) {
-        const T* base = fac + E.fac_off[p];
+        const T* base = static_cast<const T*>(views[vw].fac) + E.fac_off[p];
         for (int I = 0; I < NT; ++I) {
           const T* row = base + (int64_t)pm.toff[I] * TE;
           for (int J = pm.first[I]; J <= I; ++J) issue(row + (int64_t)(J - pm.first[I]) * TE);
@@ -193,9 +202,15 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   }
 
   // ------------------------------------------------------------ consumers
-  for (int d = blockIdx.x * NC + tid; d < ndir; d += G * NC) {
-    const int g = dir_list[d];
-    z[g] = add ? z[g] + t[g] : t[g];
+  for (int vw = 0; vw < nviews; ++vw) {
+    const double* t = vecs.t[vw];
+    double* z = vecs.z[vw];
+    if (z == nullptr) continue;
+    const int32_t* dir_list = views[vw].dir_list;
+    for (int d = blockIdx.x * NC + tid; d < views[vw].ndir; d += G * NC) {
+      const int g = dir_list[d];
+      z[g] = add ? z[g] + t[g] : t[g];
+    }
   }
   long seq = 0;
   auto acquire = [&]() -> const T* {
@@ -209,7 +224,15 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     ++seq;
   };
   for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
-    const int p = cta_list[q];
+    const int vw = cta_list[q] >> kViewShift, p = cta_list[q] & ((1 << kViewShift) - 1);
+    const double* __restrict__ t = vecs.t[vw];
+    double* __restrict__ z = vecs.z[vw];
+    if (z == nullptr) continue;
+    const EnvDev& E = views[vw].E;
+    const int32_t* __restrict__ sub_ptr = views[vw].sub_ptr;
+    const int32_t* __restrict__ dofs = views[vw].dofs;
+    const uint8_t* __restrict__ own = views[vw].own;
+    err = views[vw].err;
     const int NT = E.nt[p];
     const int off = sub_ptr[p];
     const int np_ = sub_ptr[p + 1] - off;
@@ -360,18 +383,28 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
 // sends its 8 results to every CTA (distributed shared memory), the cluster
 // synchronises, each CTA applies its rows of X_II, sends them, synchronises.
 // Backward, tile row I: CTA c owns the columns 8c..8c+7 of L_JI^T x_J and the
-// rows 8c..8c+7 of X_II^T, with the same two exchanges.
+// rows 8c..8c+7 of X_II^T, with the same two exchanges.  Cluster v of the
+// grid solves view v (the coarsest block of one instance of a batch); a
+// cluster whose vecs.z[v] is NULL leaves at once, all its CTAs together.
 constexpr int kCl = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_solve_cluster(
-    const T* __restrict__ fac, EnvDev E, const int32_t* __restrict__ sub_ptr,
-    const int32_t* __restrict__ dofs, const int32_t* __restrict__ dir_list, int ndir,
-    const double* __restrict__ t, double* __restrict__ z, int add) {
+__global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* __restrict__ views,
+                                                              const __grid_constant__ RasVecs vecs, int add) {
   using AT = typename Acc<T>::type;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int me = (int)cl.block_rank();
+  const int vw = blockIdx.x / kCl;
+  const double* __restrict__ t = vecs.t[vw];
+  double* __restrict__ z = vecs.z[vw];
+  if (z == nullptr) return;
+  const T* __restrict__ fac = static_cast<const T*>(views[vw].fac);
+  const EnvDev& E = views[vw].E;
+  const int32_t* __restrict__ sub_ptr = views[vw].sub_ptr;
+  const int32_t* __restrict__ dofs = views[vw].dofs;
+  const int32_t* __restrict__ dir_list = views[vw].dir_list;
+  const int ndir = views[vw].ndir;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int p = 0;
   const int NT = E.nt[p], rb = E.trow[p];
@@ -509,10 +542,8 @@ int ras_slots(int max_nt, bool wide) {
 }
 
 template <typename T, bool W>
-void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
-                    const int32_t* sub_ptr, const int32_t* dofs, const uint8_t* own, int max_nt,
-                    const int32_t* dir_list, int ndir, const double* t, double* z, int add, int* err,
-                    int inject, cudaStream_t s) {
+void launch_ras_cfg(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
+                    const int32_t* cta_list, int grid, int max_nt, int add, int inject, cudaStream_t s) {
   constexpr int NCW = RasCfg<T, W>::NCW, CTAS = RasCfg<T, W>::CTAS;
   auto kern = k_ras_solve<T, NCW, CTAS>;
   static std::once_flag attr;
@@ -522,30 +553,25 @@ void launch_ras_cfg(const T* fac, const EnvDev& E, const int32_t* cta_ptr, const
   });
   const int nslot = ras_slots_cfg<T, W>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) + ras_fixed_bytes<T, W>(max_nt);
-  if (grid < 1) return;
-  kern<<<grid, 32 * (NCW + 1), smem, s>>>(fac, E, cta_ptr, cta_list, sub_ptr, dofs, own, dir_list, ndir, t, z, add,
-                                          max_nt, nslot, err, inject);
+  if (grid < 1 || nviews < 1) return;
+  kern<<<grid, 32 * (NCW + 1), smem, s>>>(views, nviews, vecs, cta_ptr, cta_list, add, max_nt, nslot, inject);
 }
 
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
-                      const int32_t* cta_list, int grid, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, int max_nt,
-                      const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, bool wide, cudaStream_t s, int inject) {
+void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
+                      const int32_t* cta_list, int grid, int max_nt, int add, bool wide, cudaStream_t s,
+                      int inject) {
   if (wide)
-    launch_ras_cfg<T, true>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
-                            add, err, inject, s);
+    launch_ras_cfg<T, true>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s);
   else
-    launch_ras_cfg<T, false>(fac, E, cta_ptr, cta_list, grid, sub_ptr, dofs, own, max_nt, dir_list, ndir, t, z,
-                             add, err, inject, s);
+    launch_ras_cfg<T, false>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s);
 }
 
 template <typename T>
-void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
-                                const int32_t* dofs, int max_nt, const int32_t* dir_list,
-                                int ndir, const double* t, double* z, int add, cudaStream_t s) {
+void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
+                                cudaStream_t s) {
   using AT = typename Acc<T>::type;
+  if (nviews < 1) return;
   const size_t smem = ((size_t)max_nt * 64 + 64 + 64) * sizeof(AT);
   static std::once_flag attr;
   std::call_once(attr, [&] {
@@ -553,7 +579,7 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
                          limits().smem);
   });
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCl, 1, 1);
+  cfg.gridDim = dim3(kCl * nviews, 1, 1);
   cfg.blockDim = dim3(256, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -564,23 +590,19 @@ void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* su
   attr1[0].val.clusterDim.z = 1;
   cfg.attrs = attr1;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_block_solve_cluster<T>, fac, E, sub_ptr, dofs, dir_list, ndir, t, z, add);
+  cudaLaunchKernelEx(&cfg, k_block_solve_cluster<T>, views, vecs, add);
 }
 
 #define MSP_RAS_INST(T)                                                                          \
-  template void launch_ras_solve<T>(const T*, const EnvDev&, const int32_t*, const int32_t*, int, \
-                                    const int32_t*, const int32_t*, const uint8_t*, int,         \
-                                    const int32_t*, int, const double*, double*, int, int*,      \
-                                    bool, cudaStream_t, int);                                    \
+  template void launch_ras_solve<T>(const RasView*, int, const RasVecs&, const int32_t*, const int32_t*, \
+                                    int, int, int, bool, cudaStream_t, int);                     \
   template int ras_slots<T>(int, bool);                                                          \
   template int ras_ctas_per_sm<T>(bool);
 MSP_RAS_INST(double)
 MSP_RAS_INST(float)
 // BF16 factors: only the solve reads them (they are factored in FP32)
 MSP_RAS_INST(__nv_bfloat16)
-template void launch_block_solve_cluster<double>(const double*, const EnvDev&, const int32_t*, const int32_t*, int,
-                                                 const int32_t*, int, const double*, double*, int, cudaStream_t);
-template void launch_block_solve_cluster<float>(const float*, const EnvDev&, const int32_t*, const int32_t*, int,
-                                                const int32_t*, int, const double*, double*, int, cudaStream_t);
+template void launch_block_solve_cluster<double>(const RasView*, int, const RasVecs&, int, int, cudaStream_t);
+template void launch_block_solve_cluster<float>(const RasView*, int, const RasVecs&, int, int, cudaStream_t);
 
 }  // namespace msp

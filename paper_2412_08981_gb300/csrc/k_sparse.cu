@@ -181,26 +181,37 @@ __global__ void k_assemble(const int32_t* __restrict__ cptr, const int32_t* __re
 // ---------------------------------------------------------------- SpMV
 // LPR lanes per row, rows packed into warps; each row's partial sums are
 // combined by a fixed butterfly over its lane group.  A lane's nonzeros
-// (every LPR-th of the row) are taken four at a time: their values and
-// columns loaded together, then the four gathers of x, then the FMAs in
-// ascending position -- the same sum as one at a time, with four times the
-// bytes in flight per lane.
+// (every LPR-th of the row) are taken U at a time (U = 8 for up to 4 lanes
+// per row, whose lanes hold the longer stretches, else 4): their values and
+// columns loaded together, then the U gathers of x, then the FMAs in
+// ascending position -- the same sum as one at a time (so the same bits for
+// any U), with U times the bytes in flight per lane and fewer dependent
+// load rounds.
+__device__ __forceinline__ void spmv_store(int mode, double* __restrict__ y, const double* __restrict__ r,
+                                           int64_t row, double s) {
+  switch (mode) {
+    case SPMV_SET: y[row] = s; break;
+    case SPMV_SUB_FROM: y[row] = y[row] - s; break;
+    case SPMV_ADD: y[row] = y[row] + s; break;
+    default: y[row] = r[row] - s; break;
+  }
+}
+
+// The row sum of `row` by the LPR lanes of its group (every lane of the warp
+// must call it: the butterfly needs them all; `valid` false gives 0).
 template <int LPR>
-__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                       const double* __restrict__ val, int nrows, const double* __restrict__ x,
-                       double* __restrict__ y, const double* __restrict__ r, int mode) {
-  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t row = gt / LPR;
-  int lane = threadIdx.x % LPR;
-  const bool valid = row < nrows;  // no early exit: every lane joins the shuffles
+__device__ __forceinline__ double spmv_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                           const double* __restrict__ val, const double* __restrict__ x,
+                                           int64_t row, bool valid, int lane) {
+  constexpr int U = LPR <= 4 ? 8 : 4;
   double s = 0.0;
   if (valid) {
     const int b = rowptr[row], e = rowptr[row + 1];
-    for (int q0 = b + lane; q0 < e; q0 += 4 * LPR) {
-      double v[4], xv[4];
-      int c[4];
+    for (int q0 = b + lane; q0 < e; q0 += U * LPR) {
+      double v[U], xv[U];
+      int c[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int q = q0 + u * LPR;
         v[u] = 0.0;
         c[u] = -1;
@@ -210,22 +221,52 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
         if (c[u] >= 0) s = fma(v[u], xv[u], s);
     }
   }
 #pragma unroll
   for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LPR);
-  if (valid && lane == 0) {
-    switch (mode) {
-      case SPMV_SET: y[row] = s; break;
-      case SPMV_SUB_FROM: y[row] = y[row] - s; break;
-      case SPMV_ADD: y[row] = y[row] + s; break;
-      default: y[row] = r[row] - s; break;
-    }
+  return s;
+}
+
+template <int LPR>
+__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, int nrows, const double* __restrict__ x,
+                       double* __restrict__ y, const double* __restrict__ r, int mode) {
+  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t row = gt / LPR;
+  int lane = threadIdx.x % LPR;
+  const bool valid = row < nrows;  // no early exit: every lane joins the shuffles
+  const double s = spmv_row<LPR>(rowptr, col, val, x, row, valid, lane);
+  if (valid && lane == 0) spmv_store(mode, y, r, row, s);
+}
+
+// The member of a batch that owns stacked index i: start[b] <= i < start[b+1].
+__device__ __forceinline__ int batch_member(const int64_t* start, int nb, int64_t i) {
+  int lo = 0, hi = nb;  // start[lo] <= i < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= i) lo = mid;
+    else hi = mid;
   }
+  return lo;
+}
+
+// The same products for the members of a batch, their rows stacked (member b
+// owns rows start[b] .. start[b+1]); a member whose y is NULL sits out.
+template <int LPR>
+__global__ void k_spmv_b(const __grid_constant__ SpmvBatch B) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t R = gt / LPR;
+  const int lane = threadIdx.x % LPR;
+  const int b = batch_member(B.start, B.nb, R);
+  const int64_t row = R - B.start[b];
+  const bool valid = R < B.start[B.nb] && B.y[b] != nullptr;
+  const double s = spmv_row<LPR>(B.rowptr[b], B.col[b], B.val[b], B.x[b], row, valid, lane);
+  if (valid && lane == 0) spmv_store(B.mode, B.y[b], B.r[b], row, s);
 }
 
 // One lane per row, rows in blocks (set-up: at most kRowsThreads rows and
@@ -241,14 +282,14 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
 // fixed tree).
 constexpr int kRowsThreads = 128, kRowsNnz = 2048, kRowsGather = 16;
 
-__global__ void __launch_bounds__(kRowsThreads) k_spmv_rows(
+__device__ __forceinline__ void spmv_rows_block(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
     const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_e, const double* __restrict__ x,
-    double* __restrict__ y, const double* __restrict__ r, int mode) {
+    double* __restrict__ y, const double* __restrict__ r, int mode, int b) {
   __shared__ double sv[kRowsNnz];
   __shared__ int32_t sc[kRowsNnz];
   __shared__ int32_t srp[kRowsThreads + 1];
-  const int b = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int r0 = row_blk[b], r1 = row_blk[b + 1];
   const int e0 = blk_e[b], ne = blk_e[b + 1] - e0;
   double s = 0.0;
@@ -303,23 +344,32 @@ __global__ void __launch_bounds__(kRowsThreads) k_spmv_rows(
     s = red[0];
     row = r0;
   }
-  switch (mode) {
-    case SPMV_SET: y[row] = s; break;
-    case SPMV_SUB_FROM: y[row] = y[row] - s; break;
-    case SPMV_ADD: y[row] = y[row] + s; break;
-    default: y[row] = r[row] - s; break;
-  }
+  spmv_store(mode, y, r, row, s);
+}
+
+__global__ void __launch_bounds__(kRowsThreads) k_spmv_rows(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+    const int32_t* __restrict__ row_blk, const int32_t* __restrict__ blk_e, const double* __restrict__ x,
+    double* __restrict__ y, const double* __restrict__ r, int mode) {
+  spmv_rows_block(rowptr, col, val, row_blk, blk_e, x, y, r, mode, blockIdx.x);
+}
+
+// Batched: member b owns row blocks start[b] .. start[b+1] of the grid.
+__global__ void __launch_bounds__(kRowsThreads) k_spmv_rows_b(const __grid_constant__ SpmvBatch B) {
+  const int b = batch_member(B.start, B.nb, blockIdx.x);
+  if (B.y[b] == nullptr) return;
+  const int nb = B.nblk[b];
+  spmv_rows_block(B.rowptr[b], B.col[b], B.val[b], B.row_blk[b], B.row_blk[b] + nb + 1, B.x[b], B.y[b], B.r[b],
+                  B.mode, (int)(blockIdx.x - B.start[b]));
 }
 
 // One thread per row of an operator with at most four entries per row (the
 // barycentric P): its four columns in one 16-byte load and its four values in
 // two, no row pointers; four gathers, then the entries in order (the padding
 // adds 0 * x[0]).
-__global__ void k_spmv_ell4(const int4* __restrict__ ec, const double2* __restrict__ ev, int nrows,
-                            const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ r,
-                            int mode) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nrows) return;
+__device__ __forceinline__ void spmv_ell4_row(const int4* __restrict__ ec, const double2* __restrict__ ev,
+                                              int row, const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ r, int mode) {
   const int4 c = ec[row];
   const double2 a = ev[2 * (int64_t)row], b = ev[2 * (int64_t)row + 1];
   const double x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
@@ -327,12 +377,23 @@ __global__ void k_spmv_ell4(const int4* __restrict__ ec, const double2* __restri
   s = fma(a.y, x1, s);
   s = fma(b.x, x2, s);
   s = fma(b.y, x3, s);
-  switch (mode) {
-    case SPMV_SET: y[row] = s; break;
-    case SPMV_SUB_FROM: y[row] = y[row] - s; break;
-    case SPMV_ADD: y[row] = y[row] + s; break;
-    default: y[row] = r[row] - s; break;
-  }
+  spmv_store(mode, y, r, row, s);
+}
+
+__global__ void k_spmv_ell4(const int4* __restrict__ ec, const double2* __restrict__ ev, int nrows,
+                            const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ r,
+                            int mode) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  spmv_ell4_row(ec, ev, row, x, y, r, mode);
+}
+
+__global__ void k_spmv_ell4_b(const __grid_constant__ SpmvBatch B) {
+  const int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (R >= B.start[B.nb]) return;
+  const int b = batch_member(B.start, B.nb, R);
+  if (B.y[b] == nullptr) return;
+  spmv_ell4_row(B.ell_col[b], B.ell_val[b], (int)(R - B.start[b]), B.x[b], B.y[b], B.r[b], B.mode);
 }
 
 // Reads n doubles (evicts the L2 with clean lines) and stores one value.
@@ -345,10 +406,9 @@ __global__ void k_touch(const double* __restrict__ p, int64_t n, double* __restr
 
 // ------------------------------------------------------------- vectors
 // Stage 1: block b of vector i sums a strided slice of V_i . w.
-__global__ void k_multidot_part(const double* __restrict__ V, int64_t ld,
-                                const double* __restrict__ w, int64_t n,
-                                double* __restrict__ part) {
-  int i = blockIdx.y;
+__device__ __forceinline__ void multidot_part(const double* __restrict__ V, int64_t ld,
+                                              const double* __restrict__ w, int64_t n,
+                                              double* __restrict__ part, int i) {
   const double* v = V + ld * i;
   double s = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -368,10 +428,15 @@ __global__ void k_multidot_part(const double* __restrict__ V, int64_t ld,
   }
 }
 
+__global__ void k_multidot_part(const double* __restrict__ V, int64_t ld,
+                                const double* __restrict__ w, int64_t n,
+                                double* __restrict__ part) {
+  multidot_part(V, ld, w, n, part, blockIdx.y);
+}
+
 // Stage 2: one warp per vector sums its kDotBlocks partials in a fixed order.
-__global__ void k_multidot_final(const double* __restrict__ part, int nparts,
-                                 double* __restrict__ out) {
-  int i = blockIdx.x;
+__device__ __forceinline__ void multidot_final(const double* __restrict__ part, int nparts,
+                                               double* __restrict__ out, int i) {
   double s = 0.0;
   for (int b = threadIdx.x; b < nparts; b += 32) s += part[(int64_t)i * nparts + b];
 #pragma unroll
@@ -379,14 +444,57 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nparts,
   if (threadIdx.x == 0) out[i] = s;
 }
 
+__global__ void k_multidot_final(const double* __restrict__ part, int nparts,
+                                 double* __restrict__ out) {
+  multidot_final(part, nparts, out, blockIdx.x);
+}
+
+// Batched: member b = blockIdx.z (stage 1) / blockIdx.y (stage 2); vectors
+// i >= nv[b] and members with out == NULL sit out.  Each member's sums are
+// those of the one-member launch (the same kDotBlocks slices, same order).
+__global__ void k_multidot_part_b(const __grid_constant__ DotBatch B) {
+  const int b = blockIdx.z, i = blockIdx.y;
+  if (B.out[b] == nullptr || i >= B.nv[b]) return;
+  multidot_part(B.V[b], B.ld[b], B.w[b], B.n[b], B.part[b], i);
+}
+
+__global__ void k_multidot_final_b(const __grid_constant__ DotBatch B) {
+  const int b = blockIdx.y, i = blockIdx.x;
+  if (B.out[b] == nullptr || i >= B.nv[b]) return;
+  multidot_final(B.part[b], kDotBlocks, B.out[b], i);
+}
+
+__device__ __forceinline__ void multi_axpy_entry(const double* __restrict__ V, int64_t ld, int nv,
+                                                 const double* __restrict__ h, double* __restrict__ w,
+                                                 int64_t k, double sign) {
+  double s = 0.0;
+  for (int i = 0; i < nv; ++i) s += h[i] * V[ld * i + k];
+  w[k] += sign * s;
+}
+
 __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int nv,
                              const double* __restrict__ h, double* __restrict__ w, int64_t n,
                              double sign) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  double s = 0.0;
-  for (int i = 0; i < nv; ++i) s += h[i] * V[ld * i + k];
-  w[k] += sign * s;
+  multi_axpy_entry(V, ld, nv, h, w, k, sign);
+}
+
+__global__ void k_multi_axpy_b(const __grid_constant__ AxpyBatch B, double sign) {
+  const int b = blockIdx.y;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (B.w[b] == nullptr || k >= B.n[b] || B.nv[b] <= 0) return;
+  multi_axpy_entry(B.V[b], B.ld[b], B.nv[b], B.h[b], B.w[b], k, sign);
+}
+
+// Batched elementwise: y = a x (VEC_SCALE), y = x (VEC_COPY), y = a (VEC_FILL).
+__global__ void k_vec_b(const __grid_constant__ VecBatch B, int op) {
+  const int b = blockIdx.y;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (B.y[b] == nullptr || k >= B.n[b]) return;
+  if (op == VEC_SCALE) B.y[b][k] = B.a[b] * B.x[b][k];
+  else if (op == VEC_COPY) B.y[b][k] = B.x[b][k];
+  else B.y[b][k] = B.a[b];
 }
 
 __global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
@@ -603,6 +711,34 @@ void launch_multidot(const double* V, int64_t ld, int nv, const double* w, int64
   if (nv <= 0) return;
   k_multidot_part<<<dim3(kDotBlocks, nv), 256, 0, s>>>(V, ld, w, n, part);
   k_multidot_final<<<nv, 32, 0, s>>>(part, kDotBlocks, out);
+}
+
+void launch_spmv_batch(const SpmvBatch& B, cudaStream_t s) {
+  const int64_t total = B.start[B.nb];
+  if (B.nb <= 0 || total <= 0) return;
+  switch (B.lpr) {
+    case kSpmvEll4: k_spmv_ell4_b<<<nblk(total, 256), 256, 0, s>>>(B); break;
+    case 1: k_spmv_rows_b<<<(unsigned)total, kRowsThreads, 0, s>>>(B); break;
+    case 2: k_spmv_b<2><<<nblk(total * 2, 256), 256, 0, s>>>(B); break;
+    case 4: k_spmv_b<4><<<nblk(total * 4, 256), 256, 0, s>>>(B); break;
+    case 8: k_spmv_b<8><<<nblk(total * 8, 256), 256, 0, s>>>(B); break;
+    case 16: k_spmv_b<16><<<nblk(total * 16, 256), 256, 0, s>>>(B); break;
+    default: k_spmv_b<32><<<nblk(total * 32, 256), 256, 0, s>>>(B); break;
+  }
+}
+
+void launch_multidot_batch(const DotBatch& B, int nv_max, cudaStream_t s) {
+  if (B.nb <= 0 || nv_max <= 0) return;
+  k_multidot_part_b<<<dim3(kDotBlocks, nv_max, B.nb), 256, 0, s>>>(B);
+  k_multidot_final_b<<<dim3(nv_max, B.nb), 32, 0, s>>>(B);
+}
+
+void launch_multi_axpy_batch(const AxpyBatch& B, int64_t n_max, double sign, cudaStream_t s) {
+  if (B.nb > 0 && n_max > 0) k_multi_axpy_b<<<dim3(nblk(n_max, 256), B.nb), 256, 0, s>>>(B, sign);
+}
+
+void launch_vec_batch(const VecBatch& B, int op, int64_t n_max, cudaStream_t s) {
+  if (B.nb > 0 && n_max > 0) k_vec_b<<<dim3(nblk(n_max, 256), B.nb), 256, 0, s>>>(B, op);
 }
 
 void launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w,

@@ -177,6 +177,7 @@ struct msp_instance {
   std::vector<float*> work;  // per BF16 level: the FP32 factorisation, rounded into fac
   int* info = nullptr;
   int* ras_err = nullptr;  // bit 4: a bounded wait of the staged RAS solve expired
+  RasView* rview = nullptr;  // device: this instance's view of every level for the triangular solves
   int expire_ras = 0;      // msp_debug_expire_waits: staged RAS launches left to starve of copies
   int m = 30;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
@@ -777,24 +778,23 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
                4.0 * (double)D.ilu_nnz + (double)D.sum_np);
     return;
   }
+  RasVecs vv{};
+  vv.t[0] = t;
+  vv.z[0] = z;
   if (coarse) {  // one block: both sweeps split over a cluster of CTAs
-    launch_block_solve_cluster<double>(static_cast<const double*>(I->fac[l]), D.env, D.sub_ptr,
-                                       D.sub_dofs, D.max_nt, D.dir_list, D.ndir, t, z, add, s);
+    launch_block_solve_cluster<double>(I->rview + l, 1, vv, D.max_nt, add, s);
   } else {
     const int inj = I->expire_ras > 0 ? 1 : 0;
     if (inj) --I->expire_ras;
     if (st == Store::BF16)
-      launch_ras_solve<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                                      D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                                      D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+      launch_ras_solve<__nv_bfloat16>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt,
+                                      add, D.ras_wide, s, inj);
     else if (st == Store::F32)
-      launch_ras_solve<float>(static_cast<const float*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                              D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own, D.max_nt,
-                              D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+      launch_ras_solve<float>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
+                              D.ras_wide, s, inj);
     else
-      launch_ras_solve<double>(static_cast<const double*>(I->fac[l]), D.env, D.ras_cta_ptr,
-                               D.ras_cta_list, D.ras_grid, D.sub_ptr, D.sub_dofs, D.sub_own,
-                               D.max_nt, D.dir_list, D.ndir, t, z, add, I->ras_err, D.ras_wide, s, inj);
+      launch_ras_solve<double>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
+                               D.ras_wide, s, inj);
   }
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
@@ -1086,6 +1086,14 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
   I->xb = A.alloc<double>(2 * n);
   I->part = A.alloc<double>((size_t)(I->m + 1) * kDotBlocks);
   I->hdev = A.alloc<double>(4 * (size_t)(I->m + 1) + 8);
+  {
+    std::vector<RasView> rv(L);
+    for (int l = 0; l < L; ++l) {
+      const DevLevel& D = h->dev[l];
+      rv[l] = RasView{I->fac[l], D.env, D.sub_ptr, D.sub_dofs, D.sub_own, D.dir_list, D.ndir, I->ras_err};
+    }
+    I->rview = A.upload(rv);
+  }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
   // FP64 factors: one work list over the blocks of every persistent level
   // (cost = tile operations, as for one level), balanced longest-first over
@@ -1181,6 +1189,810 @@ size_t instance_need(const msp_hierarchy* h) {
   }
   need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
   return need;
+}
+
+// ============================================================ batched solves
+// A batch fuses the V-cycles and Krylov steps of several instances (of one
+// hierarchy or of several) into shared launches: at every level depth one
+// staged RAS launch per (factor type, solve form) over the blocks of all
+// members, one SpMV launch per (operator, schedule) over the members' stacked
+// rows, one coarsest-solve launch with one cluster per member, and one launch
+// per Krylov kernel.  Every member's arithmetic is that of its own msp_solve
+// (the same kernels' per-row, per-block and per-slice code, the same order),
+// so the results are bitwise the same; only the launches are shared.
+struct BatchRas {
+  Store st = Store::F64;
+  bool wide = false;
+  std::vector<int> members;  // view v of the launch = member members[v]
+  RasView* views = nullptr;
+  int32_t *cta_ptr = nullptr, *cta_list = nullptr;
+  int grid = 0, max_nt = 0;
+};
+struct BatchCoarse {
+  std::vector<int> members;
+  RasView* views = nullptr;
+  int max_nt = 0;
+};
+
+// The persistent-level blocks of the members whose factors the batched
+// launch can take (FP64 or FP32 dense LU), per factor type.
+struct BatchFac {
+  bool f32 = false;
+  BlockItem* items = nullptr;
+  int32_t *cta_ptr = nullptr, *cta_list = nullptr;
+  int grid = 0;
+};
+
+struct BatchState {
+  std::vector<msp_instance*> m;
+  cudaStream_t stream = nullptr;
+  DevArena arena;
+  int maxL = 0;
+  std::vector<std::vector<BatchRas>> ras;  // [depth]: the smoothed levels at that depth
+  std::vector<BatchCoarse> coarse;        // [depth]: the members whose coarsest level is at that depth
+  cudaEvent_t ev = nullptr;
+  // batched factorisation
+  std::vector<char> deferred;             // member's persistent levels go to the batched launch
+  std::vector<BatchFac> fac;
+  std::vector<cudaEvent_t> join;           // per member: its own factorisation work done
+  int* hinfo = nullptr;                    // pinned: every member's pivot word
+  int fac_calls = 0;
+  cudaGraphExec_t fac_graph = nullptr;
+};
+
+int batch_build(BatchState& B, msp_instance* const* insts, int n, cudaStream_t s) {
+  if (n < 1 || n > kMaxMembers) return fail(MSP_ERR_INVALID, "a batch holds 1.." + std::to_string(kMaxMembers) +
+                                                                  " instances");
+  const msp_options& o0 = insts[0]->h->opt;
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = insts[i];
+    if (!I) return fail(MSP_ERR_INVALID, "NULL instance in the batch");
+    for (int k = 0; k < i; ++k)
+      if (insts[k] == I) return fail(MSP_ERR_INVALID, "an instance is listed twice");
+    const msp_options& o = I->h->opt;
+    if (I->h->device != insts[0]->h->device) return fail(MSP_ERR_INVALID, "batch members on different devices");
+    if (o.nu_pre != o0.nu_pre || o.nu_post != o0.nu_post)
+      return fail(MSP_ERR_INVALID, "batch members need the same smoothing steps");
+    if (o.coarse_solver != MSP_COARSE_DIRECT)
+      return fail(MSP_ERR_INVALID, "batched solves need the directly solved coarsest level");
+    for (const DevLevel& D : I->h->dev)
+      if (D.ilu) return fail(MSP_ERR_INVALID, "batched solves take the exact subdomain LU, not ILU(p)");
+  }
+  B.m.assign(insts, insts + n);
+  B.stream = s;
+  B.arena.al = insts[0]->h->arena.al;
+  B.maxL = 0;
+  for (msp_instance* I : B.m) B.maxL = std::max(B.maxL, (int)I->h->dev.size());
+  B.ras.assign(B.maxL, {});
+  B.coarse.assign(B.maxL, {});
+  int nsm = 0;
+  MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, insts[0]->h->device));
+  for (int d = 0; d < B.maxL; ++d) {
+    std::vector<RasView> cv;
+    for (int i = 0; i < n; ++i) {
+      msp_instance* I = B.m[i];
+      msp_hierarchy* h = I->h;
+      const int L = (int)h->dev.size();
+      if (d >= L) continue;
+      const DevLevel& D = h->dev[d];
+      const RasView v{I->fac[d], D.env, D.sub_ptr, D.sub_dofs, D.sub_own, D.dir_list, D.ndir, I->ras_err};
+      if (d == L - 1) {  // the directly solved coarsest level
+        B.coarse[d].members.push_back(i);
+        B.coarse[d].max_nt = std::max(B.coarse[d].max_nt, D.max_nt);
+        cv.push_back(v);
+        continue;
+      }
+      const Store st = level_store(h, d);
+      BatchRas* g = nullptr;
+      for (BatchRas& x : B.ras[d])
+        if (x.st == st && x.wide == D.ras_wide) g = &x;
+      if (!g) {
+        B.ras[d].push_back(BatchRas{});
+        g = &B.ras[d].back();
+        g->st = st;
+        g->wide = D.ras_wide;
+      }
+      g->members.push_back(i);
+      g->max_nt = std::max(g->max_nt, D.max_nt);
+    }
+    if (!cv.empty()) B.coarse[d].views = B.arena.upload(cv);
+    for (BatchRas& g : B.ras[d]) {
+      std::vector<RasView> views;
+      std::vector<int64_t> cost;
+      std::vector<int32_t> code;
+      for (int v = 0; v < (int)g.members.size(); ++v) {
+        msp_instance* I = B.m[g.members[v]];
+        const DevLevel& D = I->h->dev[d];
+        const HostLevel& H = I->h->host[d];
+        views.push_back(RasView{I->fac[d], D.env, D.sub_ptr, D.sub_dofs, D.sub_own, D.dir_list, D.ndir,
+                                I->ras_err});
+        for (int p = 0; p < H.nsub; ++p) {
+          cost.push_back((H.sub_fac_off[p + 1] - H.sub_fac_off[p]) / kTileElems);
+          code.push_back((int32_t)(((uint32_t)v << kViewShift) | (uint32_t)p));
+        }
+      }
+      // the ring depth of the shared launch is set by its largest block: every
+      // member's level was checked at set-up to fit its own form, and a form
+      // with fewer slots than two is refused here
+      const int slots = g.st == Store::F64   ? ras_slots<double>(g.max_nt, g.wide)
+                        : g.st == Store::F32 ? ras_slots<float>(g.max_nt, g.wide)
+                                             : ras_slots<__nv_bfloat16>(g.max_nt, g.wide);
+      if (slots < 2) return fail(MSP_ERR_INVALID, "batch: subdomain blocks too large for a shared solve");
+      const int per_sm = g.st == Store::F64   ? ras_ctas_per_sm<double>(g.wide)
+                         : g.st == Store::F32 ? ras_ctas_per_sm<float>(g.wide)
+                                              : ras_ctas_per_sm<__nv_bfloat16>(g.wide);
+      std::vector<int32_t> ptr, list;
+      lpt_lists(cost, std::max(1, std::min((int)cost.size(), nsm * per_sm)), ptr, list);
+      for (int32_t& q : list) q = code[q];
+      g.grid = (int)ptr.size() - 1;
+      g.views = B.arena.upload(views);
+      g.cta_ptr = B.arena.upload(ptr);
+      g.cta_list = B.arena.upload(list);
+    }
+  }
+  // the batched factorisation: the persistent levels of FP64 / FP32 members
+  // in one launch per factor type, longest blocks first, on all SMs but four,
+  // which the members' coarsest-block tile steps (long chains of small
+  // launches on their own streams) keep for themselves
+  B.deferred.assign(n, 0);
+  {
+    std::vector<BlockItem> items[2];
+    std::vector<int64_t> cost[2];
+    for (int i = 0; i < n; ++i) {
+      msp_instance* I = B.m[i];
+      const msp_hierarchy* h = I->h;
+      if (h->opt.factor_precision != MSP_F64 && h->opt.factor_precision != MSP_F32) continue;
+      B.deferred[i] = 1;
+      for (int l = 0; l < (int)h->dev.size(); ++l) {
+        const DevLevel& D = h->dev[l];
+        if (!D.fac_blocks) continue;
+        const HostLevel& H = h->host[l];
+        const int g = level_store(h, l) == Store::F64 ? 0 : 1;
+        for (int p = 0; p < H.nsub; ++p) {
+          const int32_t* R = &H.tile_last[H.sub_trow[p]];
+          int64_t c = 0;
+          for (int k = 0; k < H.sub_nt[p]; ++k) {
+            const int64_t rem = R[k] - k;
+            c += 1 + rem + rem * (rem - 1) + rem;
+          }
+          items[g].push_back(BlockItem{I->fac[l], D.env, p, I->info});
+          cost[g].push_back(c);
+        }
+      }
+    }
+    const int reserve = std::min(4, nsm / 8);
+    for (int g = 0; g < 2; ++g) {
+      if (items[g].empty()) continue;
+      const int per_sm = g == 0 ? ldlt_blocks_batch_per_sm<double>() : ldlt_blocks_batch_per_sm<float>();
+      std::vector<int32_t> ptr, list;
+      lpt_lists(cost[g], std::max(1, std::min((int)items[g].size(), (nsm - reserve) * per_sm)), ptr, list);
+      BatchFac f;
+      f.f32 = g == 1;
+      f.items = B.arena.upload(items[g]);
+      f.cta_ptr = B.arena.upload(ptr);
+      f.cta_list = B.arena.upload(list);
+      f.grid = (int)ptr.size() - 1;
+      B.fac.push_back(f);
+    }
+  }
+  if (!B.arena.ok) return fail(MSP_ERR_OOM, "device allocation failed for a batch");
+  MSP_CUDA(cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
+  B.join.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) MSP_CUDA(cudaEventCreateWithFlags(&B.join[i], cudaEventDisableTiming));
+  if (cudaMallocHost(&B.hinfo, sizeof(int) * n) != cudaSuccess) {
+    cudaGetLastError();
+    B.hinfo = nullptr;
+    return fail(MSP_ERR_OOM, "pinned host allocation failed");
+  }
+  return MSP_OK;
+}
+
+void batch_release(BatchState& B) {
+  if (B.fac_graph) cudaGraphExecDestroy(B.fac_graph);
+  B.fac_graph = nullptr;
+  if (B.ev) cudaEventDestroy(B.ev);
+  B.ev = nullptr;
+  for (cudaEvent_t e : B.join)
+    if (e) cudaEventDestroy(e);
+  B.join.clear();
+  if (B.hinfo) cudaFreeHost(B.hinfo);
+  B.hinfo = nullptr;
+  B.arena.release();
+}
+
+// Enqueues the factorisation of every member from B.stream: each member's
+// own levels on its private streams (forked from B.stream), the persistent
+// levels of the deferred members in the batched launches, all joined back.
+int batch_enqueue_factor(BatchState& B) {
+  const int n = (int)B.m.size();
+  MSP_CUDA(cudaEventRecord(B.ev, B.stream));
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = B.m[i];
+    MSP_CUDA(cudaStreamWaitEvent(I->cap, B.ev, 0));
+    if (int rc = enqueue_factor(I, I->cap, B.deferred[i] != 0)) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!B.deferred[i]) continue;
+    const msp_hierarchy* h = B.m[i]->h;
+    for (int l = 0; l < (int)h->dev.size(); ++l)
+      if (h->dev[l].fac_blocks) MSP_CUDA(cudaStreamWaitEvent(B.stream, B.m[i]->bev[l][0], 0));
+  }
+  for (const BatchFac& f : B.fac) {
+    if (f.f32) launch_ldlt_blocks_batch<float>(f.items, f.cta_ptr, f.cta_list, f.grid, B.stream);
+    else launch_ldlt_blocks_batch<double>(f.items, f.cta_ptr, f.cta_list, f.grid, B.stream);
+  }
+  for (int i = 0; i < n; ++i) {
+    MSP_CUDA(cudaEventRecord(B.join[i], B.m[i]->cap));
+    MSP_CUDA(cudaStreamWaitEvent(B.stream, B.join[i], 0));
+  }
+  MSP_CUDA(cudaGetLastError());
+  return MSP_OK;
+}
+
+// The batched factorisation; from its second call on it is replayed from a
+// CUDA graph captured once (the launches are the same for every parameter).
+int batch_factor(BatchState& B) {
+  const int n = (int)B.m.size();
+  for (msp_instance* I : B.m)
+    if (!I->assembled) return fail(MSP_ERR_INVALID, "a batch member is not assembled");
+  // B.stream after every member's own stream (its assembly)
+  for (msp_instance* I : B.m) {
+    if (I->stream == B.stream) continue;
+    MSP_CUDA(cudaEventRecord(B.ev, I->stream));
+    MSP_CUDA(cudaStreamWaitEvent(B.stream, B.ev, 0));
+  }
+  if (!B.fac_graph && B.fac_calls >= 1) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rc = batch_enqueue_factor(B);
+      const cudaError_t ec = cudaStreamEndCapture(B.stream, &g);
+      if (rc != MSP_OK || ec != cudaSuccess || !g || cudaGraphInstantiate(&B.fac_graph, g, 0) != cudaSuccess)
+        B.fac_graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    msp::g_last_error.clear();
+  }
+  if (B.fac_graph) {
+    MSP_CUDA(cudaGraphLaunch(B.fac_graph, B.stream));
+  } else {
+    if (int rc = batch_enqueue_factor(B)) return rc;
+  }
+  B.fac_calls++;
+  for (int i = 0; i < n; ++i)
+    MSP_CUDA(cudaMemcpyAsync(B.hinfo + i, B.m[i]->info, sizeof(int), cudaMemcpyDeviceToHost, B.stream));
+  MSP_CUDA(cudaStreamSynchronize(B.stream));
+  int rc = MSP_OK;
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = B.m[i];
+    I->prof.harvest();
+    if (B.hinfo[i] & 2) {
+      I->factored = false;
+      if (rc == MSP_OK) rc = fail(MSP_ERR_TIMEOUT, "a bounded tensor-core wait in the factorisation of member " +
+                                                       std::to_string(i) + " expired");
+    } else if (B.hinfo[i]) {
+      I->factored = false;
+      if (rc == MSP_OK) rc = fail(MSP_ERR_INTERNAL, "non-positive or non-finite pivot in a subdomain factor of "
+                                                        "member " + std::to_string(i));
+    } else {
+      I->factored = true;
+    }
+  }
+  return rc;
+}
+
+// Re-assembly of every member for its parameter (mu: n_mu per member), each on
+// its own stream, one synchronisation for all.
+int batch_assemble(BatchState& B, const double* mu, int n_mu) {
+  const int n = (int)B.m.size();
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = B.m[i];
+    msp_hierarchy* h = I->h;
+    const double* mi = mu ? mu + (size_t)i * n_mu : nullptr;
+    double m8[8] = {0};
+    if (h->opt.coef_kind == MSP_K_COSEXP) {
+      if (n_mu != 8 || !mi) return fail(MSP_ERR_INVALID, "MSP_K_COSEXP needs n_mu == 8");
+      for (int j = 0; j < 8; ++j) {
+        if (!std::isfinite(mi[j])) return fail(MSP_ERR_INVALID, "non-finite mu for member " + std::to_string(i));
+        m8[j] = mi[j];
+      }
+    }
+    std::copy(m8, m8 + 8, I->hpin);
+    MSP_CUDA(cudaMemcpyAsync(I->mu, I->hpin, sizeof(m8), cudaMemcpyHostToDevice, I->stream));
+    if (int rc = assemble_all(I)) return rc;
+    I->assembled = true;
+    I->factored = false;
+    if (I->stream != B.stream) {
+      MSP_CUDA(cudaEventRecord(B.ev, I->stream));
+      MSP_CUDA(cudaStreamWaitEvent(B.stream, B.ev, 0));
+    }
+  }
+  MSP_CUDA(cudaStreamSynchronize(B.stream));  // the staging buffers are reused next
+  return MSP_OK;
+}
+
+// Per-member vectors of one V-cycle: level-d right-hand side and correction.
+struct BatchLevelVecs {
+  std::vector<std::vector<const double*>> r;  // [member][depth]
+  std::vector<std::vector<double*>> z;
+};
+
+// One SpMV family at depth d over the members in `on` (J, P or the
+// restriction), one launch per schedule among them.
+enum BatchOp { BOP_J = 0, BOP_P = 1, BOP_R = 2 };
+void batch_spmv(BatchState& B, int d, int op, const std::vector<int>& on,
+                const std::vector<const double*>& x, const std::vector<double*>& y,
+                const std::vector<const double*>& r, int mode) {
+  std::vector<std::pair<int, int>> todo;  // (lpr, member)
+  for (int i : on) {
+    const DevLevel& D = B.m[i]->h->dev[d];
+    todo.push_back({op == BOP_J ? D.lpr_A : (op == BOP_P ? D.lpr_P : D.lpr_PT), i});
+  }
+  std::sort(todo.begin(), todo.end());
+  size_t k = 0;
+  while (k < todo.size()) {
+    SpmvBatch S;
+    S.lpr = todo[k].first;
+    S.mode = mode;
+    size_t e = k;
+    while (e < todo.size() && todo[e].first == S.lpr) ++e;
+    for (size_t q = k; q < e; ++q) {
+      const int i = todo[q].second, b = S.nb++;
+      msp_instance* I = B.m[i];
+      const DevLevel& D = I->h->dev[d];
+      int64_t rows = 0;
+      if (op == BOP_J) {
+        S.rowptr[b] = D.rowptr; S.col[b] = D.col; S.val[b] = I->val[d];
+        S.row_blk[b] = D.rb_A; S.nblk[b] = D.nrb_A;
+        rows = D.n;
+      } else if (op == BOP_P) {
+        S.rowptr[b] = D.P_rowptr; S.col[b] = D.P_col; S.val[b] = D.P_val;
+        S.row_blk[b] = D.rb_P; S.nblk[b] = D.nrb_P;
+        S.ell_col[b] = D.P_ell_col; S.ell_val[b] = D.P_ell_val;
+        rows = D.n;
+      } else {
+        S.rowptr[b] = D.PT_rowptr; S.col[b] = D.PT_col; S.val[b] = D.PT_val;
+        S.row_blk[b] = D.rb_PT; S.nblk[b] = D.nrb_PT;
+        rows = I->h->dev[d + 1].n;
+      }
+      S.x[b] = x[i];
+      S.y[b] = y[i];
+      S.r[b] = r.empty() ? nullptr : r[i];
+      S.start[b + 1] = S.start[b] + (S.lpr == 1 ? S.nblk[b] : rows);
+    }
+    launch_spmv_batch(S, B.stream);
+    k = e;
+  }
+}
+
+// The staged RAS solves of depth d for the members in `on`: t -> z (add).
+void batch_ras(BatchState& B, int d, const std::vector<char>& on, const std::vector<const double*>& t,
+               const std::vector<double*>& z, int add) {
+  for (BatchRas& g : B.ras[d]) {
+    RasVecs vv{};
+    bool any = false;
+    for (size_t v = 0; v < g.members.size(); ++v) {
+      const int i = g.members[v];
+      if (!on[i]) continue;
+      vv.t[v] = t[i];
+      vv.z[v] = z[i];
+      any = true;
+    }
+    if (!any) continue;
+    const int nv = (int)g.members.size();
+    if (g.st == Store::BF16)
+      launch_ras_solve<__nv_bfloat16>(g.views, nv, vv, g.cta_ptr, g.cta_list, g.grid, g.max_nt, add, g.wide,
+                                      B.stream);
+    else if (g.st == Store::F32)
+      launch_ras_solve<float>(g.views, nv, vv, g.cta_ptr, g.cta_list, g.grid, g.max_nt, add, g.wide, B.stream);
+    else
+      launch_ras_solve<double>(g.views, nv, vv, g.cta_ptr, g.cta_list, g.grid, g.max_nt, add, g.wide, B.stream);
+  }
+}
+
+// One V-cycle (Algorithm 2, as vcycle()) for every member in `act`, from
+// r0[i] into z0[i], all launches shared by depth.
+void batch_vcycle(BatchState& B, const std::vector<char>& act, const std::vector<const double*>& r0,
+                  const std::vector<double*>& z0) {
+  const int n = (int)B.m.size();
+  const int nu_pre = B.m[0]->h->opt.nu_pre, nu_post = B.m[0]->h->opt.nu_post;
+  auto rv = [&](int i, int d) -> const double* { return d == 0 ? r0[i] : B.m[i]->r[d]; };
+  auto zv = [&](int i, int d) -> double* { return d == 0 ? z0[i] : B.m[i]->z[d]; };
+  std::vector<const double*> r(n), t_in(n);
+  std::vector<double*> z(n), t(n);
+  for (int d = 0; d < B.maxL; ++d) {
+    std::vector<char> on(n, 0);
+    std::vector<int> onl, crs;
+    for (int i = 0; i < n; ++i) {
+      const int L = (int)B.m[i]->h->dev.size();
+      if (!act[i] || d >= L) continue;
+      r[i] = rv(i, d);
+      z[i] = zv(i, d);
+      t[i] = B.m[i]->t[d];
+      t_in[i] = t[i];
+      if (d < L - 1) {
+        on[i] = 1;
+        onl.push_back(i);
+      } else {
+        crs.push_back(i);
+      }
+    }
+    if (!onl.empty()) {
+      for (int it = 0; it < nu_pre; ++it) {
+        if (it == 0) {
+          batch_ras(B, d, on, r, z, 0);
+        } else {
+          batch_spmv(B, d, BOP_J, onl, std::vector<const double*>(z.begin(), z.end()), t, r, SPMV_RESIDUAL);
+          batch_ras(B, d, on, t_in, z, 1);
+        }
+      }
+      if (nu_pre == 0) {
+        VecBatch V;
+        int64_t nmax = 0;
+        for (int i : onl) {
+          V.y[V.nb] = z[i];
+          V.a[V.nb] = 0.0;
+          V.n[V.nb++] = B.m[i]->h->dev[d].n;
+          nmax = std::max<int64_t>(nmax, B.m[i]->h->dev[d].n);
+        }
+        launch_vec_batch(V, VEC_FILL, nmax, B.stream);
+      }
+      batch_spmv(B, d, BOP_J, onl, std::vector<const double*>(z.begin(), z.end()), t, r, SPMV_RESIDUAL);
+      std::vector<double*> rn(n, nullptr);
+      for (int i : onl) rn[i] = B.m[i]->r[d + 1];
+      batch_spmv(B, d, BOP_R, onl, t_in, rn, {}, SPMV_SET);
+    }
+    if (!crs.empty()) {
+      RasVecs vv{};
+      for (size_t v = 0; v < B.coarse[d].members.size(); ++v) {
+        const int i = B.coarse[d].members[v];
+        if (!act[i]) continue;
+        vv.t[v] = r[i];
+        vv.z[v] = z[i];
+      }
+      launch_block_solve_cluster<double>(B.coarse[d].views, (int)B.coarse[d].members.size(), vv,
+                                         B.coarse[d].max_nt, 0, B.stream);
+    }
+  }
+  for (int d = B.maxL - 2; d >= 0; --d) {
+    std::vector<char> on(n, 0);
+    std::vector<int> onl;
+    for (int i = 0; i < n; ++i) {
+      const int L = (int)B.m[i]->h->dev.size();
+      if (!act[i] || d >= L - 1) continue;
+      r[i] = rv(i, d);
+      z[i] = zv(i, d);
+      t[i] = B.m[i]->t[d];
+      t_in[i] = t[i];
+      on[i] = 1;
+      onl.push_back(i);
+    }
+    if (onl.empty()) continue;
+    std::vector<const double*> zc(n, nullptr);
+    for (int i : onl) zc[i] = zv(i, d + 1);
+    batch_spmv(B, d, BOP_P, onl, zc, z, {}, SPMV_ADD);
+    for (int it = 0; it < nu_post; ++it) {
+      batch_spmv(B, d, BOP_J, onl, std::vector<const double*>(z.begin(), z.end()), t, r, SPMV_RESIDUAL);
+      batch_ras(B, d, on, t_in, z, 1);
+    }
+  }
+}
+
+// FGMRES of fgmres_run() for every member, in lockstep.
+struct FgMember {
+  msp_instance* I = nullptr;
+  int64_t n = 0;
+  int m = 0;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double bnorm = 0, rnorm = 0;
+  int it = 0, j = 0;
+  bool breakdown = false;
+  enum { CHECK, START, INNER, RESTART, DONE } phase = CHECK;
+  int status = MSP_ERR_NOT_CONVERGED;
+  std::string msg;
+  std::vector<double> H, cs, sn, g, y;
+};
+
+int fgmres_batch(BatchState& B, const double* const* b, double* const* x, double rtol, msp_stats* st) {
+  const int n = (int)B.m.size();
+  cudaStream_t s = B.stream;
+  std::vector<FgMember> F(n);
+  int64_t nmax = 0;
+  for (int i = 0; i < n; ++i) {
+    msp_instance* I = B.m[i];
+    FgMember& f = F[i];
+    f.I = I;
+    f.n = I->h->dev[0].n;
+    f.m = I->m;
+    f.b = (b && b[i]) ? b[i] : I->h->dev[0].b;
+    f.x = x[i];
+    f.H.assign((size_t)(f.m + 1) * f.m, 0.0);
+    f.cs.assign(f.m, 0.0);
+    f.sn.assign(f.m, 0.0);
+    f.g.assign(f.m + 1, 0.0);
+    f.y.assign(f.m, 0.0);
+    nmax = std::max(nmax, f.n);
+  }
+  auto vec = [&](FgMember& f, int k) { return f.I->V + (int64_t)k * f.n; };
+  auto zvec = [&](FgMember& f, int k) { return f.I->Z + (int64_t)k * f.n; };
+  auto sync_copy = [&](const std::vector<int>& who, int count) -> int {
+    for (int i : who)
+      MSP_CUDA(cudaMemcpyAsync(F[i].I->hpin, F[i].I->hdev, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    return MSP_OK;
+  };
+  auto dots = [&](const std::vector<int>& who, auto V_of, auto ld_of, auto nv_of, auto w_of, int off) {
+    DotBatch D;
+    int nvmax = 0;
+    for (int i : who) {
+      FgMember& f = F[i];
+      const int b2 = D.nb++;
+      D.V[b2] = V_of(f);
+      D.ld[b2] = ld_of(f);
+      D.nv[b2] = nv_of(f);
+      D.w[b2] = w_of(f);
+      D.n[b2] = f.n;
+      D.part[b2] = f.I->part;
+      D.out[b2] = f.I->hdev + off;
+      nvmax = std::max(nvmax, D.nv[b2]);
+    }
+    launch_multidot_batch(D, nvmax, s);
+  };
+  std::vector<int> all(n);
+  for (int i = 0; i < n; ++i) all[i] = i;
+  // ||b||
+  dots(all, [](FgMember& f) { return f.b; }, [](FgMember&) { return (int64_t)0; }, [](FgMember&) { return 1; },
+       [](FgMember& f) { return f.b; }, 0);
+  if (int rc = sync_copy(all, 1)) return rc;
+  {
+    VecBatch V;
+    for (int i : all) {
+      V.y[V.nb] = F[i].x;
+      V.a[V.nb] = 0.0;
+      V.n[V.nb++] = F[i].n;
+    }
+    launch_vec_batch(V, VEC_FILL, nmax, s);
+  }
+  VecBatch cp;
+  for (int i : all) {
+    FgMember& f = F[i];
+    f.bnorm = std::sqrt(f.I->hpin[0]);
+    if (!(f.bnorm > 0.0)) {
+      f.phase = FgMember::DONE;
+      f.status = std::isfinite(f.bnorm) ? MSP_OK : MSP_ERR_INVALID;
+      f.msg = std::isfinite(f.bnorm) ? "" : "non-finite right-hand side";
+      continue;
+    }
+    cp.x[cp.nb] = f.b;
+    cp.y[cp.nb] = f.I->res;
+    cp.n[cp.nb++] = f.n;
+    f.rnorm = f.bnorm;
+  }
+  launch_vec_batch(cp, VEC_COPY, nmax, s);
+  for (;;) {
+    // checks, and the start of a cycle
+    VecBatch sc;
+    for (FgMember& f : F) {
+      if (f.phase != FgMember::CHECK) continue;
+      if (f.rnorm <= rtol * f.bnorm) {
+        f.status = MSP_OK;
+        f.phase = FgMember::DONE;
+      } else if (f.it >= f.I->h->opt.max_it) {
+        f.phase = FgMember::DONE;
+      } else {
+        sc.x[sc.nb] = f.I->res;
+        sc.y[sc.nb] = vec(f, 0);
+        sc.a[sc.nb] = 1.0 / f.rnorm;
+        sc.n[sc.nb++] = f.n;
+        std::fill(f.g.begin(), f.g.end(), 0.0);
+        f.g[0] = f.rnorm;
+        f.j = 0;
+        f.breakdown = false;
+        f.phase = FgMember::INNER;
+      }
+    }
+    launch_vec_batch(sc, VEC_SCALE, nmax, s);
+    std::vector<int> inner;
+    for (int i = 0; i < n; ++i)
+      if (F[i].phase == FgMember::INNER) inner.push_back(i);
+    if (!inner.empty()) {
+      std::vector<char> act(n, 0);
+      std::vector<const double*> r0(n, nullptr);
+      std::vector<double*> z0(n, nullptr);
+      for (int i : inner) {
+        act[i] = 1;
+        r0[i] = vec(F[i], F[i].j);
+        z0[i] = zvec(F[i], F[i].j);
+      }
+      batch_vcycle(B, act, r0, z0);
+      {
+        std::vector<const double*> zx(n, nullptr);
+        std::vector<double*> wy(n, nullptr);
+        for (int i : inner) {
+          zx[i] = z0[i];
+          wy[i] = F[i].I->w;
+        }
+        batch_spmv(B, 0, BOP_J, inner, zx, wy, {}, SPMV_SET);
+      }
+      auto axpy = [&](int off) {
+        AxpyBatch A;
+        for (int i : inner) {
+          FgMember& f = F[i];
+          const int b2 = A.nb++;
+          A.V[b2] = f.I->V;
+          A.ld[b2] = f.n;
+          A.nv[b2] = f.j + 1;
+          A.h[b2] = f.I->hdev + off * (f.m + 1);
+          A.w[b2] = f.I->w;
+          A.n[b2] = f.n;
+        }
+        launch_multi_axpy_batch(A, nmax, -1.0, s);
+      };
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice (CGS2)
+        DotBatch D;
+        int nvmax = 0;
+        for (int i : inner) {
+          FgMember& f = F[i];
+          const int b2 = D.nb++;
+          D.V[b2] = f.I->V;
+          D.ld[b2] = f.n;
+          D.nv[b2] = f.j + 1;
+          D.w[b2] = f.I->w;
+          D.n[b2] = f.n;
+          D.part[b2] = f.I->part;
+          D.out[b2] = f.I->hdev + pass * (f.m + 1);
+          nvmax = std::max(nvmax, f.j + 1);
+        }
+        launch_multidot_batch(D, nvmax, s);
+        axpy(pass);
+      }
+      {
+        DotBatch D;
+        for (int i : inner) {
+          FgMember& f = F[i];
+          const int b2 = D.nb++;
+          D.V[b2] = f.I->w;
+          D.ld[b2] = 0;
+          D.nv[b2] = 1;
+          D.w[b2] = f.I->w;
+          D.n[b2] = f.n;
+          D.part[b2] = f.I->part;
+          D.out[b2] = f.I->hdev + 2 * (f.m + 1);
+        }
+        launch_multidot_batch(D, 1, s);
+      }
+      for (int i : inner)
+        MSP_CUDA(cudaMemcpyAsync(F[i].I->hpin, F[i].I->hdev, sizeof(double) * (2 * (F[i].m + 1) + 1),
+                                 cudaMemcpyDeviceToHost, s));
+      MSP_CUDA(cudaStreamSynchronize(s));
+      VecBatch nx;
+      for (int i : inner) {
+        FgMember& f = F[i];
+        const int m = f.m, j = f.j;
+        const double* hp = f.I->hpin;
+        std::vector<double>& H = f.H;
+        for (int k = 0; k <= j; ++k) H[(size_t)k * m + j] = hp[k] + hp[m + 1 + k];
+        const double hn = std::sqrt(std::max(hp[2 * (m + 1)], 0.0));
+        if (!std::isfinite(hn)) {
+          f.status = MSP_ERR_NOT_CONVERGED;
+          f.msg = "non-finite Arnoldi vector";
+          f.phase = FgMember::DONE;
+          continue;
+        }
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int k = 0; k < j; ++k) {
+          const double a = H[(size_t)k * m + j], c = H[(size_t)(k + 1) * m + j];
+          H[(size_t)k * m + j] = f.cs[k] * a + f.sn[k] * c;
+          H[(size_t)(k + 1) * m + j] = -f.sn[k] * a + f.cs[k] * c;
+        }
+        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(a, c);
+        f.cs[j] = den == 0.0 ? 1.0 : a / den;
+        f.sn[j] = den == 0.0 ? 0.0 : c / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        f.g[j + 1] = -f.sn[j] * f.g[j];
+        f.g[j] = f.cs[j] * f.g[j];
+        ++f.it;
+        if (hn <= 1e-300) {
+          f.breakdown = true;
+          f.j = j + 1;
+          f.phase = FgMember::RESTART;
+          continue;
+        }
+        nx.x[nx.nb] = f.I->w;
+        nx.y[nx.nb] = vec(f, j + 1);
+        nx.a[nx.nb] = 1.0 / hn;
+        nx.n[nx.nb++] = f.n;
+        f.j = j + 1;
+        if (std::fabs(f.g[j + 1]) <= rtol * f.bnorm || f.j >= m || f.it >= f.I->h->opt.max_it)
+          f.phase = FgMember::RESTART;
+      }
+      launch_vec_batch(nx, VEC_SCALE, nmax, s);
+    }
+    std::vector<int> rs;
+    for (int i = 0; i < n; ++i)
+      if (F[i].phase == FgMember::RESTART) rs.push_back(i);
+    if (!rs.empty()) {
+      AxpyBatch A;
+      for (int i : rs) {
+        FgMember& f = F[i];
+        const int m = f.m, j = f.j;
+        for (int k = j - 1; k >= 0; --k) {
+          double sum = f.g[k];
+          for (int q = k + 1; q < j; ++q) sum -= f.H[(size_t)k * m + q] * f.y[q];
+          f.y[k] = sum / f.H[(size_t)k * m + k];
+        }
+        double* hp = f.I->hpin;
+        for (int k = 0; k < j; ++k) hp[2 * (m + 1) + 1 + k] = f.y[k];
+        MSP_CUDA(cudaMemcpyAsync(f.I->hdev + 2 * (m + 1) + 1, hp + 2 * (m + 1) + 1, sizeof(double) * j,
+                                 cudaMemcpyHostToDevice, s));
+        const int b2 = A.nb++;
+        A.V[b2] = f.I->Z;
+        A.ld[b2] = f.n;
+        A.nv[b2] = j;
+        A.h[b2] = f.I->hdev + 2 * (m + 1) + 1;
+        A.w[b2] = f.x;
+        A.n[b2] = f.n;
+      }
+      launch_multi_axpy_batch(A, nmax, 1.0, s);
+      {
+        std::vector<const double*> xx(n, nullptr), bb(n, nullptr);
+        std::vector<double*> rr(n, nullptr);
+        for (int i : rs) {
+          xx[i] = F[i].x;
+          rr[i] = F[i].I->res;
+          bb[i] = F[i].b;
+        }
+        batch_spmv(B, 0, BOP_J, rs, xx, rr, bb, SPMV_RESIDUAL);
+      }
+      dots(rs, [](FgMember& f) { return (const double*)f.I->res; }, [](FgMember&) { return (int64_t)0; },
+           [](FgMember&) { return 1; }, [](FgMember& f) { return (const double*)f.I->res; }, 0);
+      if (int rc = sync_copy(rs, 1)) return rc;
+      for (int i : rs) {
+        FgMember& f = F[i];
+        f.rnorm = std::sqrt(std::max(f.I->hpin[0], 0.0));
+        f.phase = FgMember::CHECK;
+        if (!std::isfinite(f.rnorm) || (f.breakdown && f.rnorm > rtol * f.bnorm)) f.phase = FgMember::DONE;
+      }
+    }
+    bool live = false;
+    for (const FgMember& f : F) live = live || f.phase != FgMember::DONE;
+    if (!live) break;
+  }
+  MSP_CUDA(cudaGetLastError());
+  // statuses: an expired bounded wait in a member's staged solves first
+  int worst = MSP_OK;
+  std::string worst_msg;
+  for (int i = 0; i < n; ++i) {
+    FgMember& f = F[i];
+    int e = 0;
+    MSP_CUDA(cudaMemcpyAsync(&e, f.I->ras_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    int rc = f.status;
+    std::string msg = f.msg;
+    if (e) {
+      MSP_CUDA(cudaMemsetAsync(f.I->ras_err, 0, sizeof(int), s));
+      MSP_CUDA(cudaStreamSynchronize(s));
+      rc = MSP_ERR_TIMEOUT;
+      msg = "a bounded wait in the staged RAS solve expired";
+    } else if (rc == MSP_ERR_NOT_CONVERGED && msg.empty()) {
+      msg = "FGMRES did not reach rtol within max_it (or broke down)";
+    }
+    if (st) {
+      std::memset(&st[i], 0, sizeof(msp_stats));
+      st[i].status = rc;
+      st[i].iterations = f.it;
+      st[i].rel_residual = f.bnorm > 0 ? f.rnorm / f.bnorm : 0.0;
+    }
+    if (rc != MSP_OK && worst == MSP_OK) {
+      worst = rc;
+      worst_msg = "member " + std::to_string(i) + ": " + msg;
+    }
+  }
+  if (worst != MSP_OK) return fail(worst, worst_msg);
+  return MSP_OK;
 }
 
 struct Timer {
@@ -1683,6 +2495,77 @@ int msp_instance_copy(const msp_instance* I, int level, int what, int sub, void*
 
 // ---- per-kernel accounting (launch counts, algorithmic bytes/flops, and
 // CUDA-event durations while profiling is on)
+}  // extern "C"
+
+struct msp_batch {
+  msp::BatchState st;
+};
+
+extern "C" {
+
+int msp_batch_create(msp_instance* const* insts, int n, void* stream, msp_batch** out) {
+  msp::g_last_error.clear();
+  if (!insts || !out) return fail(MSP_ERR_INVALID, "NULL argument");
+  std::unique_ptr<msp_batch> b(new (std::nothrow) msp_batch());
+  if (!b) return fail(MSP_ERR_OOM, "host allocation failed");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : (n > 0 && insts[0] ? insts[0]->stream : nullptr);
+  const int rc = msp::batch_build(b->st, insts, n, s);
+  if (rc) {
+    msp::batch_release(b->st);
+    return rc;
+  }
+  *out = b.release();
+  return MSP_OK;
+}
+
+void msp_batch_free(msp_batch* b) {
+  if (!b) return;
+  msp::batch_release(b->st);
+  delete b;
+}
+
+int msp_batch_assemble(msp_batch* bt, const double* mu, int n_mu) {
+  msp::g_last_error.clear();
+  if (!bt) return fail(MSP_ERR_INVALID, "NULL batch");
+  return msp::batch_assemble(bt->st, mu, n_mu);
+}
+
+int msp_batch_factor(msp_batch* bt) {
+  msp::g_last_error.clear();
+  if (!bt) return fail(MSP_ERR_INVALID, "NULL batch");
+  return msp::batch_factor(bt->st);
+}
+
+int msp_solve_batch(msp_batch* bt, const double* const* b_dev, double* const* x_dev, double rtol, msp_stats* st) {
+  msp::g_last_error.clear();
+  if (!bt || !x_dev) return fail(MSP_ERR_INVALID, "NULL argument");
+  msp::BatchState& B = bt->st;
+  const int n = (int)B.m.size();
+  if (st) std::memset(st, 0, sizeof(msp_stats) * n);
+  if (!(rtol > 0.0) || !std::isfinite(rtol)) return fail(MSP_ERR_INVALID, "rtol must be > 0");
+  for (int i = 0; i < n; ++i) {
+    if (!x_dev[i]) return fail(MSP_ERR_INVALID, "NULL solution pointer");
+    if (!B.m[i]->factored) return fail(MSP_ERR_INVALID, "batch member " + std::to_string(i) + " not factored");
+  }
+  // the batch stream after every member's own stream, and back
+  for (msp_instance* I : B.m) {
+    if (I->stream == B.stream) continue;
+    MSP_CUDA(cudaEventRecord(B.ev, I->stream));
+    MSP_CUDA(cudaStreamWaitEvent(B.stream, B.ev, 0));
+  }
+  Timer tm;
+  const int rc = msp::fgmres_batch(B, b_dev, x_dev, rtol, st);
+  const double ms = tm.ms();
+  if (st)
+    for (int i = 0; i < n; ++i) st[i].ms_solve = ms;
+  for (msp_instance* I : B.m) {
+    if (I->stream == B.stream) continue;
+    MSP_CUDA(cudaEventRecord(B.ev, B.stream));
+    MSP_CUDA(cudaStreamWaitEvent(I->stream, B.ev, 0));
+  }
+  return rc;
+}
+
 int msp_debug_expire_waits(msp_instance* I, int count) {
   msp::g_last_error.clear();
   if (!I || count < 0) return fail(MSP_ERR_INVALID, "NULL instance or negative count");

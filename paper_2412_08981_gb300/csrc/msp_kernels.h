@@ -110,14 +110,6 @@ void launch_ldlt_blocks_batch(const BlockItem* items, const int32_t* cta_ptr, co
                               cudaStream_t s);
 template <typename T>
 int ldlt_blocks_batch_per_sm();
-// y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level),
-// on a cluster of 8 CTAs that split every tile row of both sweeps and
-// exchange partial results through distributed shared memory; Dirichlet
-// nodes get t.  Written (add = 0) or added (add = 1) to z.
-template <typename T>
-void launch_block_solve_cluster(const T* fac, const EnvDev& E, const int32_t* sub_ptr,
-                                const int32_t* dofs, int max_nt, const int32_t* dir_list,
-                                int ndir, const double* t, double* z, int add, cudaStream_t s);
 // Persistent factorisation of the blocks of a level whose factors are stored
 // in BF16: FP32 diagonal tiles and panels, trailing updates on the tensor
 // cores (BF16 operands, FP32 accumulation), fac = the FP32 working envelope.
@@ -155,30 +147,113 @@ void launch_ilu_solve(const T* fac, int64_t nnz, int64_t rows, int nsub, const i
 // BF16 storage of factors computed in FP32: dst = bf16(src) to nearest even,
 // n a multiple of 4.
 void launch_round_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);
+// ---- triangular solves with the tiled factors (k_ras.cu)
+// One level of one instance as the solves see it: its factors (T*), their
+// envelope, the subdomains (DoF lists, owned flags), the Dirichlet DoFs and
+// the error word of the staged solve.  A launch takes an array of views (the
+// same level of several instances of a batch, or a single one) and, per view,
+// its input t and output z (z == NULL: the view sits the launch out).
+constexpr int kMaxBatch = 32;
+constexpr int kViewShift = 20;  // CTA-list entries (view << kViewShift) | block, block < 2^20
+struct RasView {
+  const void* fac;
+  EnvDev E;
+  const int32_t* sub_ptr;
+  const int32_t* dofs;
+  const uint8_t* own;
+  const int32_t* dir_list;
+  int ndir;
+  int* err;
+};
+struct RasVecs {
+  const double* t[kMaxBatch];
+  double* z[kMaxBatch];
+};
 // z = B^{-1} t on one level: per subdomain y = (L D L^T)^{-1} t[dofs], owned
 // entries written (add = 0) or added (add = 1) to z; Dirichlet nodes get t.
-// CTA b solves the subdomains cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
+// CTA b solves the items cta_list[cta_ptr[b] .. cta_ptr[b+1]) (a
 // longest-first balanced assignment built on the host); a bounded mbarrier
-// wait that expires sets bit 4 of *err.  The factor tiles stream through
-// ras_slots<T>(max_nt) shared-memory slots; each sweep holds one tile at a
+// wait that expires sets bit 4 of the item's view's err.  The factor tiles
+// stream through ras_slots<T>(max_nt) shared-memory slots (max_nt: the most
+// tiles per side of any block of any view); each sweep holds one tile at a
 // time (the backward sweep takes a row's column tiles, then its diagonal
 // tile), so two slots are enough to make progress (checked on the host at
 // set-up); deeper rings let the producer run further ahead.
 // `wide`: one CTA of 16 consumer warps per SM (always the FP64 form); else
 // FP32 / BF16 run 2 / 3 smaller CTAs per SM, each with fewer ring slots.
 // `inject` != 0 (failure-injection tests only): no tile copy is issued, every
-// wait on a full slot runs out after a short limit and bit 4 of *err is set.
+// wait on a full slot runs out after a short limit and bit 4 of err is set.
 template <typename T>
 int ras_slots(int max_nt, bool wide);
 // CTAs of k_ras_solve that share an SM (the persistent grid is this x SMs)
 template <typename T>
 int ras_ctas_per_sm(bool wide);
 template <typename T>
-void launch_ras_solve(const T* fac, const EnvDev& E, const int32_t* cta_ptr,
-                      const int32_t* cta_list, int grid, const int32_t* sub_ptr,
-                      const int32_t* dofs, const uint8_t* own, int max_nt,
-                      const int32_t* dir_list, int ndir, const double* t, double* z, int add,
-                      int* err, bool wide, cudaStream_t s, int inject = 0);
+void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
+                      const int32_t* cta_list, int grid, int max_nt, int add, bool wide, cudaStream_t s,
+                      int inject = 0);
+// y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level) for
+// each of `nviews` views, each on a cluster of 8 CTAs that split every tile
+// row of both sweeps and exchange partial results through distributed shared
+// memory; Dirichlet nodes get t.  Written (add = 0) or added (add = 1) to z.
+template <typename T>
+void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
+                                cudaStream_t s);
+
+// ---- batched launches: one launch for several instances of a batch, each
+// member's arithmetic exactly that of its own one-member launch.  Members are
+// described in parameter arrays of kMaxBatch entries; a member whose output
+// pointer is NULL sits the launch out.
+constexpr int kMaxMembers = 32;
+// One SpMV family over the members' stacked rows (row blocks for lpr == 1):
+// member b owns start[b] .. start[b+1]; every member uses the schedule lpr.
+struct SpmvBatch {
+  int nb = 0, lpr = 8, mode = 0;
+  int64_t start[kMaxMembers + 1] = {};
+  const int32_t* rowptr[kMaxMembers] = {};
+  const int32_t* col[kMaxMembers] = {};
+  const double* val[kMaxMembers] = {};
+  const int32_t* row_blk[kMaxMembers] = {};  // lpr == 1: nblk + 1 row offsets, then their first nonzeros
+  int nblk[kMaxMembers] = {};
+  const int4* ell_col[kMaxMembers] = {};
+  const double2* ell_val[kMaxMembers] = {};
+  const double* x[kMaxMembers] = {};
+  double* y[kMaxMembers] = {};
+  const double* r[kMaxMembers] = {};
+};
+void launch_spmv_batch(const SpmvBatch& B, cudaStream_t s);
+// out_b[i] = V_b[i] . w_b, i < nv[b], partials in part_b (nv[b] x kDotBlocks)
+struct DotBatch {
+  int nb = 0;
+  const double* V[kMaxMembers] = {};
+  int64_t ld[kMaxMembers] = {};
+  int nv[kMaxMembers] = {};
+  const double* w[kMaxMembers] = {};
+  int64_t n[kMaxMembers] = {};
+  double* part[kMaxMembers] = {};
+  double* out[kMaxMembers] = {};
+};
+void launch_multidot_batch(const DotBatch& B, int nv_max, cudaStream_t s);
+// w_b -= / += sum_i h_b[i] V_b[i], i < nv[b] (h on the device)
+struct AxpyBatch {
+  int nb = 0;
+  const double* V[kMaxMembers] = {};
+  int64_t ld[kMaxMembers] = {};
+  int nv[kMaxMembers] = {};
+  const double* h[kMaxMembers] = {};
+  double* w[kMaxMembers] = {};
+  int64_t n[kMaxMembers] = {};
+};
+void launch_multi_axpy_batch(const AxpyBatch& B, int64_t n_max, double sign, cudaStream_t s);
+enum VecOp { VEC_SCALE = 0, VEC_COPY = 1, VEC_FILL = 2 };
+struct VecBatch {
+  int nb = 0;
+  const double* x[kMaxMembers] = {};
+  double* y[kMaxMembers] = {};
+  double a[kMaxMembers] = {};
+  int64_t n[kMaxMembers] = {};
+};
+void launch_vec_batch(const VecBatch& B, int op, int64_t n_max, cudaStream_t s);
 
 // ---- Krylov helpers (deterministic two-stage reductions)
 // out[i] = sum_k V[i*ld + k] * w[k], i < nv; part: scratch of nv * kDotBlocks doubles

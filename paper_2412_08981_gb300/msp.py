@@ -126,6 +126,12 @@ EXPORTS = {
     "msp_profile_reset": (C.c_int, [C.c_void_p]),
     "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
     "msp_debug_expire_waits": (C.c_int, [C.c_void_p, C.c_int]),
+    "msp_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "msp_batch_free": (None, [C.c_void_p]),
+    "msp_batch_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "msp_batch_factor": (C.c_int, [C.c_void_p]),
+    "msp_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double,
+                                  C.POINTER(msp_stats)]),
     "msp_multidot_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                        C.c_void_p, C.c_void_p]),
     "msp_instance_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -440,6 +446,53 @@ class Server:
         if getattr(self, "srv", None):
             load().msp_server_free(self.srv)
             self.srv = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """msp_batch_create / msp_solve_batch / msp_batch_free: lockstep FGMRES of
+    several factored instances with their launches fused."""
+
+    def __init__(self, instances, stream=None):
+        self._insts = list(instances)
+        arr = (C.c_void_p * len(self._insts))(*[i.inst.value for i in self._insts])
+        b = C.c_void_p()
+        _check(load().msp_batch_create(arr, len(self._insts),
+                                       _stream_ptr(stream) if stream is not None else None, C.byref(b)))
+        self.b = b
+
+    def assemble(self, mus):
+        """msp_batch_assemble: re-assemble every member for its parameter
+        vector (mus: one 8-vector per member)."""
+        m = np.ascontiguousarray(np.asarray(mus, np.float64).reshape(len(self._insts), -1))
+        self._mus = m
+        _check(load().msp_batch_assemble(self.b, _ptr(m), int(m.shape[1])))
+
+    def factor(self):
+        """msp_batch_factor: factor every member, persistent levels batched."""
+        _check(load().msp_batch_factor(self.b))
+
+    def solve(self, xs, bs=None, rtol=1e-8, raise_on_fail=True):
+        """xs: device tensors (one per member); bs: None or a list of device
+        tensors / None (None: the member's load vector).  Returns the
+        per-member stats dicts."""
+        n = len(self._insts)
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ba = None
+        if bs is not None:
+            ba = (C.c_void_p * n)(*[(b.data_ptr() if b is not None else None) for b in bs])
+        st = (msp_stats * n)()
+        rc = load().msp_solve_batch(self.b, ba, xa, float(rtol), st)
+        if rc not in (MSP_OK, MSP_ERR_NOT_CONVERGED) or (raise_on_fail and rc != MSP_OK):
+            _check(rc)
+        return [{k: getattr(st[i], k) for k, _ in msp_stats._fields_} for i in range(n)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().msp_batch_free(self.b)
+            self.b = None
 
     def __del__(self):
         self.close()

@@ -31,14 +31,20 @@
 //   * with several fields, DoF 3v + c is field c at vertex v; a Dirichlet
 //     vertex fixes all its fields; the transfers are split by field (the
 //     field-splitting interpolation I = sum_f R_f^T I_f R~_f of Section 2.1
-//     with the scalar P for every field: P (x) I_3).
+//     with the scalar P for every field: P (x) I_3);
+//   * with quadratic (P2) elements for the scalar problem, DoFs sit at the
+//     vertices and at the edge midpoints (the DoF distribution N = (1,1,0,0)
+//     of Section 2.1); see "P2 elements" below for their numbering, the
+//     Dirichlet edges, the subdomains and the transfer between levels.
 // Compiled with -O2 -ffp-contract=off, OpenMP over subdomains and rows only.
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <set>
 #include <string>
 #include <vector>
@@ -59,8 +65,14 @@ struct Subdomain {
 };
 
 struct Level {
-  int n = 0, m = 0;  // DoFs (fields x vertices) and tets
+  int n = 0, m = 0;  // DoFs (fields x vertices, or vertices + edges with P2) and tets
   int nv = 0;        // vertices
+  // P2 only: the edges (vertex pairs a < b, ascending), the global DoF of the
+  // 10 local DoFs of every tet, the point of every DoF, the vertex owners
+  std::vector<int> edges;
+  std::vector<int> tdof;
+  std::vector<double> dofx;
+  std::vector<int> vowner;
   std::vector<double> xyz;
   std::vector<int> tets;
   std::vector<unsigned char> vdir;  // per vertex
@@ -78,6 +90,7 @@ struct Level {
 struct Oracle {
   std::vector<Level> lv;
   int fields = 1;                     // DoFs per vertex: 1 (scalar) or 3 (elasticity)
+  int p2 = 0;                         // 1: quadratic elements (DoFs on vertices and edges)
   double lame_l = 0.0, lame_m = 0.0;  // Lame parameters of the unit-modulus material
   int delta = 1, nu_pre = 2, nu_post = 2;
   int coef_kind = 0;  // 0: k = 1; 1: exp(s * sum_j mu_j * 0.5 * cos(pi a_j . x))
@@ -179,6 +192,151 @@ void elastic_element(const double g[4][3], double vol, double lam, double mu, do
         }
 }
 
+// ------------------------------------------------------------ P2 elements
+// Quadratic Lagrange elements for the scalar problem.  Local DoFs of a tet:
+// its vertices 0..3, then its edges 01, 02, 03, 12, 13, 23.  Basis functions
+// in barycentric coordinates: vertex a, lambda_a (2 lambda_a - 1); edge ab,
+// 4 lambda_a lambda_b.  Element integrals by the 4-point rule that is exact
+// for polynomials of degree 2 (the integrands grad phi_i . grad phi_j are of
+// degree 2, phi_i of degree 2): barycentric points (A,B,B,B) and their
+// permutations, A = (5 + 3 sqrt 5)/20, B = (5 - sqrt 5)/20, weights |T|/4.
+const int kP2Edge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+double p2_phi(int i, const double lam[4]) {
+  if (i < 4) return lam[i] * (2.0 * lam[i] - 1.0);
+  const int a = kP2Edge[i - 4][0], b = kP2Edge[i - 4][1];
+  return 4.0 * lam[a] * lam[b];
+}
+
+void p2_grad(int i, const double lam[4], const double g[4][3], double out[3]) {
+  for (int d = 0; d < 3; ++d) {
+    if (i < 4) {
+      out[d] = (4.0 * lam[i] - 1.0) * g[i][d];
+    } else {
+      const int a = kP2Edge[i - 4][0], b = kP2Edge[i - 4][1];
+      out[d] = 4.0 * (lam[a] * g[b][d] + lam[b] * g[a][d]);
+    }
+  }
+}
+
+// K10[i][j] = int_T grad phi_i . grad phi_j, m1[i] = int_T phi_i.
+void p2_element(const double g[4][3], double vol, double* K10, double* m1) {
+  const double A = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, B = (5.0 - std::sqrt(5.0)) / 20.0;
+  for (int k = 0; k < 100; ++k) K10[k] = 0.0;
+  for (int i = 0; i < 10; ++i) m1[i] = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    double lam[4] = {B, B, B, B};
+    lam[q] = A;
+    double gr[10][3];
+    for (int i = 0; i < 10; ++i) p2_grad(i, lam, g, gr[i]);
+    for (int i = 0; i < 10; ++i) {
+      m1[i] += vol / 4.0 * p2_phi(i, lam);
+      for (int j = 0; j < 10; ++j) K10[i * 10 + j] += vol / 4.0 * dot3(gr[i], gr[j]);
+    }
+  }
+}
+
+// The P2 DoFs of a level.  Edges: the distinct vertex pairs (a, b), a < b, of
+// the tets, ascending.  Numbering: vertex 0, then the edges (0, b) in
+// ascending b, then vertex 1 and its edges (1, b), b > 1, and so on (a DoF
+// next to the DoFs of its neighbourhood, so subdomain blocks stay banded).
+// An edge DoF sits at the edge's midpoint.  Dirichlet: a vertex as given; an
+// edge when it lies on a boundary face (a face of exactly one tet) whose three
+// vertices are Dirichlet.  Owner: a vertex's own; an edge takes the owner of
+// its lower vertex if that id owns a non-Dirichlet vertex, else the owner of
+// its upper vertex.  Returns false if an edge gets no owner.
+bool p2_number(Level& L, const int* vowner) {
+  std::vector<std::pair<int, int>> E;
+  for (int e = 0; e < L.m; ++e)
+    for (int k = 0; k < 6; ++k) {
+      int a = L.tets[4 * e + kP2Edge[k][0]], b = L.tets[4 * e + kP2Edge[k][1]];
+      E.push_back({std::min(a, b), std::max(a, b)});
+    }
+  std::sort(E.begin(), E.end());
+  E.erase(std::unique(E.begin(), E.end()), E.end());
+  const int ne = (int)E.size();
+  L.edges.assign(2 * (size_t)ne, 0);
+  for (int k = 0; k < ne; ++k) {
+    L.edges[2 * k] = E[k].first;
+    L.edges[2 * k + 1] = E[k].second;
+  }
+  std::vector<int> vdof(L.nv), edof(ne);
+  int cnt = 0, k = 0;
+  for (int v = 0; v < L.nv; ++v) {
+    vdof[v] = cnt++;
+    while (k < ne && E[k].first == v) edof[k++] = cnt++;
+  }
+  L.n = cnt;
+  L.tdof.assign(10 * (size_t)L.m, 0);
+  for (int e = 0; e < L.m; ++e) {
+    const int* t = &L.tets[4 * e];
+    for (int a = 0; a < 4; ++a) L.tdof[10 * e + a] = vdof[t[a]];
+    for (int q = 0; q < 6; ++q) {
+      std::pair<int, int> key{std::min(t[kP2Edge[q][0]], t[kP2Edge[q][1]]),
+                              std::max(t[kP2Edge[q][0]], t[kP2Edge[q][1]])};
+      L.tdof[10 * e + 4 + q] = edof[std::lower_bound(E.begin(), E.end(), key) - E.begin()];
+    }
+  }
+  L.dofx.assign(3 * (size_t)L.n, 0.0);
+  L.dir.assign(L.n, 0);
+  for (int v = 0; v < L.nv; ++v) {
+    for (int d = 0; d < 3; ++d) L.dofx[3 * vdof[v] + d] = L.xyz[3 * v + d];
+    L.dir[vdof[v]] = L.vdir[v];
+  }
+  for (int q = 0; q < ne; ++q)
+    for (int d = 0; d < 3; ++d)
+      L.dofx[3 * edof[q] + d] = 0.5 * (L.xyz[3 * E[q].first + d] + L.xyz[3 * E[q].second + d]);
+  std::map<std::array<int, 3>, int> faces;
+  for (int e = 0; e < L.m; ++e)
+    for (int skip = 0; skip < 4; ++skip) {
+      std::array<int, 3> f;
+      int c = 0;
+      for (int a = 0; a < 4; ++a)
+        if (a != skip) f[c++] = L.tets[4 * e + a];
+      std::sort(f.begin(), f.end());
+      faces[f]++;
+    }
+  for (const auto& fc : faces) {
+    if (fc.second != 1) continue;
+    const auto& f = fc.first;
+    if (!(L.vdir[f[0]] && L.vdir[f[1]] && L.vdir[f[2]])) continue;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a + 1; b < 3; ++b) {
+        std::pair<int, int> key{std::min(f[a], f[b]), std::max(f[a], f[b])};
+        L.dir[edof[std::lower_bound(E.begin(), E.end(), key) - E.begin()]] = 1;
+      }
+  }
+  if (vowner) {
+    L.vowner.assign(vowner, vowner + L.nv);
+    std::set<int> ids;
+    for (int v = 0; v < L.nv; ++v)
+      if (!L.vdir[v]) ids.insert(vowner[v]);
+    L.owner.assign(L.n, -1);
+    for (int v = 0; v < L.nv; ++v) L.owner[vdof[v]] = vowner[v];
+    for (int q = 0; q < ne; ++q) {
+      const int oa = vowner[E[q].first], ob = vowner[E[q].second];
+      L.owner[edof[q]] = ids.count(oa) ? oa : (ids.count(ob) ? ob : -1);
+      if (L.owner[edof[q]] < 0 && !L.dir[edof[q]]) return false;
+    }
+  }
+  return true;
+}
+
+// Row i of the P2 pattern: the DoFs of the tets that hold DoF i, sorted.
+void build_pattern_p2(Level& L) {
+  std::vector<std::set<int>> nb(L.n);
+  for (int e = 0; e < L.m; ++e)
+    for (int i = 0; i < 10; ++i)
+      for (int j = 0; j < 10; ++j) nb[L.tdof[10 * e + i]].insert(L.tdof[10 * e + j]);
+  L.A.rowptr.assign(L.n + 1, 0);
+  L.A.col.clear();
+  for (int i = 0; i < L.n; ++i) {
+    for (int j : nb[i]) L.A.col.push_back(j);
+    L.A.rowptr[i + 1] = (int)L.A.col.size();
+  }
+  L.A.val.assign(L.A.col.size(), 0.0);
+}
+
 // ------------------------------------------------------------- CSR pattern
 // Row i: the sorted distinct vertices that share a tet with i (i included);
 // with F fields, row F v + c holds the F DoFs of each of those vertices.
@@ -225,6 +383,19 @@ int assemble_level(const Oracle& o, Level& L) {
     double xc[3];
     for (int d = 0; d < 3; ++d) xc[d] = (x[0][d] + x[1][d] + x[2][d] + x[3][d]) / 4.0;
     double k = coefficient(o, xc);
+    if (o.p2) {  // quadratic elements: DoFs at the vertices and edge midpoints
+      double K10[100], m1[10];
+      p2_element(g, vol, K10, m1);
+      const int* td = &L.tdof[10 * e];
+      for (int i = 0; i < 10; ++i) {
+        for (int j = 0; j < 10; ++j) {
+          long nz = csr_find(L.A, td[i], td[j]);
+          L.A.val[nz] += k * K10[i * 10 + j];
+        }
+        L.b[td[i]] += m1[i];  // f = 1: b_i = int phi_i
+      }
+      continue;
+    }
     if (o.fields == 3) {  // linear elasticity, three displacement fields
       double K12[144];
       elastic_element(g, vol, o.lame_l, o.lame_m, K12);
@@ -291,6 +462,49 @@ void build_subdomains(const Oracle& o, Level& L) {
     Subdomain S;
     for (int i = 0; i < L.n; ++i)
       if (in[i] && !L.dir[i]) {
+        S.dofs.push_back(i);
+        S.own.push_back(L.owner[i] == id ? 1 : 0);
+      }
+    L.subs.push_back(std::move(S));
+  }
+}
+
+// P2 subdomains: the vertex sets grow as for P1 (V^0 = the vertices with
+// owner id, Dirichlet ones included; V^{k+1} = the vertices of the tets
+// touching V^k, delta times); the subdomain holds the non-Dirichlet vertex
+// DoFs of V^delta and the non-Dirichlet edge DoFs with both ends in V^delta,
+// ascending; a DoF is owned where its owner is the subdomain's id.
+void build_subdomains_p2(const Oracle& o, Level& L) {
+  L.subs.clear();
+  std::set<int> ids;
+  for (int v = 0; v < L.nv; ++v)
+    if (!L.vdir[v]) ids.insert(L.vowner[v]);
+  std::vector<std::vector<int>> vt(L.nv);
+  for (int e = 0; e < L.m; ++e)
+    for (int a = 0; a < 4; ++a) vt[L.tets[4 * e + a]].push_back(e);
+  for (int id : ids) {
+    std::vector<unsigned char> in(L.nv, 0);
+    for (int v = 0; v < L.nv; ++v)
+      if (L.vowner[v] == id) in[v] = 1;
+    for (int layer = 0; layer < o.delta; ++layer) {
+      std::vector<unsigned char> nxt = in;
+      for (int v = 0; v < L.nv; ++v)
+        if (in[v])
+          for (int e : vt[v])
+            for (int a = 0; a < 4; ++a) nxt[L.tets[4 * e + a]] = 1;
+      in.swap(nxt);
+    }
+    std::vector<unsigned char> take(L.n, 0);
+    for (int e = 0; e < L.m; ++e) {
+      const int* t = &L.tets[4 * e];
+      for (int a = 0; a < 4; ++a)
+        if (in[t[a]]) take[L.tdof[10 * e + a]] = 1;
+      for (int q = 0; q < 6; ++q)
+        if (in[t[kP2Edge[q][0]]] && in[t[kP2Edge[q][1]]]) take[L.tdof[10 * e + 4 + q]] = 1;
+    }
+    Subdomain S;
+    for (int i = 0; i < L.n; ++i)
+      if (take[i] && !L.dir[i]) {
         S.dofs.push_back(i);
         S.own.push_back(L.owner[i] == id ? 1 : 0);
       }
@@ -622,6 +836,54 @@ void transpose(const Csr& P, int ncols, Csr& T) {
     }
 }
 
+// P2 interpolation between non-nested levels: each non-Dirichlet fine DoF's
+// point (a vertex or an edge midpoint) is located in the coarse mesh exactly
+// as a P1 node is (build_interp's rule, run on the DoF points); its row holds
+// the ten coarse P2 basis functions of that tet evaluated there, on the
+// tet's non-Dirichlet coarse DoFs, columns ascending (zero weights kept).
+void build_interp_p2(const Level& C, const Level& F, Csr& P) {
+  // the containing tet and barycentric coordinates of every fine DoF point:
+  // build_interp on the DoF points with every coarse vertex kept returns the
+  // four raw weights in ascending vertex order, from which the tet follows
+  std::vector<unsigned char> keep(C.nv, 0);
+  Csr loc;
+  build_interp(C.nv, C.xyz.data(), C.m, C.tets.data(), keep.data(), F.n, F.dofx.data(), F.dir.data(), 1, loc);
+  // vertex set -> tet: the coarse tet with exactly those vertices, lowest id
+  std::map<std::array<int, 4>, int> tet_of;
+  for (int e = C.m - 1; e >= 0; --e) {
+    std::array<int, 4> key{C.tets[4 * e], C.tets[4 * e + 1], C.tets[4 * e + 2], C.tets[4 * e + 3]};
+    std::sort(key.begin(), key.end());
+    tet_of[key] = e;
+  }
+  P.rowptr.assign(F.n + 1, 0);
+  P.col.clear();
+  P.val.clear();
+  for (int f = 0; f < F.n; ++f) {
+    if (loc.rowptr[f + 1] > loc.rowptr[f]) {
+      std::array<int, 4> key;
+      for (int a = 0; a < 4; ++a) key[a] = loc.col[loc.rowptr[f] + a];
+      const int e = tet_of.at(key);
+      const int* t = &C.tets[4 * e];
+      double lam[4];
+      for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q)
+          if (loc.col[loc.rowptr[f] + q] == t[a]) lam[a] = loc.val[loc.rowptr[f] + q];
+      std::vector<std::pair<int, double>> row;
+      for (int i = 0; i < 10; ++i) {
+        const int c = C.tdof[10 * e + i];
+        if (C.dir[c]) continue;
+        row.push_back({c, p2_phi(i, lam)});
+      }
+      std::sort(row.begin(), row.end());
+      for (auto& pr : row) {
+        P.col.push_back(pr.first);
+        P.val.push_back(pr.second);
+      }
+    }
+    P.rowptr[f + 1] = (int)P.col.size();
+  }
+}
+
 // ------------------------------------- MLS transfer (Section 3.2, Eq. 13-15, 24)
 // Overlapping moving-least-squares interpolation from a source mesh S to the
 // nodes of a target mesh T.  For a target node x* with partition id q:
@@ -937,14 +1199,18 @@ typedef struct {
 } orc_level;
 
 // pde: 0 scalar P1 (one field), 1 linear elasticity (three fields, Poisson
-// ratio `poisson` in (0, 0.5), unit Young's modulus scaled by k(x;mu)).
+// ratio `poisson` in (0, 0.5), unit Young's modulus scaled by k(x;mu)), 2
+// scalar P2 (DoFs on vertices and edges; barycentric transfers, f = 1, and
+// delta >= 1 where a level is partitioned).
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
                  int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
                  int restrict_scaling, int coarse_ras, int ilu_fine, int ilu_coarse, int pde,
                  double poisson) {
-  if (nlevels < 1 || transfer < 0 || transfer > 1 || pde < 0 || pde > 1) return nullptr;
+  if (nlevels < 1 || transfer < 0 || transfer > 1 || pde < 0 || pde > 2) return nullptr;
   if (pde == 1 && (transfer != 0 || !(poisson > 0.0 && poisson < 0.5))) return nullptr;
+  if (pde == 2 && (transfer != 0 || load_kind != 0 || delta < 1)) return nullptr;
   Oracle* o = new Oracle();
+  o->p2 = pde == 2 ? 1 : 0;
   if (pde == 1) {
     o->fields = 3;
     o->lame_l = poisson / ((1.0 + poisson) * (1.0 - 2.0 * poisson));
@@ -973,6 +1239,23 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
     L.vdir.assign(lv[l].dirichlet, lv[l].dirichlet + L.nv);
     L.dir.resize(L.n);
     for (int i = 0; i < L.n; ++i) L.dir[i] = L.vdir[i / NF];
+    if (o->p2) {
+      if (!p2_number(L, lv[l].owner)) {
+        delete o;
+        return nullptr;
+      }
+      build_pattern_p2(L);
+      if (l + 1 < nlevels || o->coarse_ras) {
+        if (!lv[l].owner) {
+          delete o;
+          return nullptr;
+        }
+        build_subdomains_p2(*o, L);
+      } else {
+        build_coarse(L);
+      }
+      continue;
+    }
     if (lv[l].owner) {
       L.owner.resize(L.n);
       for (int i = 0; i < L.n; ++i) L.owner[i] = lv[l].owner[i / NF];
@@ -997,6 +1280,9 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
         delete o;
         return nullptr;
       }
+    } else if (o->p2) {
+      build_interp_p2(C, F, F.P);
+      transpose(F.P, C.n, F.PT);
     } else {
       Csr Pv;  // the scalar interpolation between the vertex sets
       build_interp(C.nv, C.xyz.data(), C.m, C.tets.data(), C.vdir.data(), F.nv, F.xyz.data(),
@@ -1145,6 +1431,8 @@ long orc_get(void* h, const char* what, int level, int sub, const void** ptr) {
   if (w == "PT_rowptr") return ret(L.PT.rowptr);
   if (w == "PT_col") return ret(L.PT.col);
   if (w == "PT_val") return ret(L.PT.val);
+  if (w == "dofdir") return ret(L.dir);
+  if (w == "dofx") return ret(L.dofx);
   if (w == "n_subs") {
     *ptr = nullptr;
     return (long)L.subs.size();
@@ -1162,7 +1450,25 @@ long orc_get(void* h, const char* what, int level, int sub, const void** ptr) {
   return -1;
 }
 
+// DoFs of a level.
+int orc_ndofs(void* h, int level) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (level < 0 || level >= (int)o->lv.size()) return -1;
+  return o->lv[level].n;
+}
+
 // ---- standalone pieces used by the pins ----
+// The P2 element of a tet (local DoFs: vertices 0..3, edges 01 02 03 12 13 23):
+// K100 row-major = k int grad phi_i . grad phi_j, m10 = int phi_i; returns |T|.
+double orc_tet_p2(const double* x4, double k, double* K100, double* m10) {
+  double g[4][3];
+  double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);
+  double vol = std::fabs(det) / 6.0;
+  p2_element(g, vol, K100, m10);
+  for (int i = 0; i < 100; ++i) K100[i] *= k;
+  return vol;
+}
+
 double orc_tet_stiffness(const double* x4, double k, double* K16) {
   double g[4][3];
   double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);

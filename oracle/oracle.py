@@ -60,6 +60,10 @@ def lib():
             L.orc_tet_stiffness.argtypes = [vp, dp, vp]
             L.orc_tet_elasticity.restype = dp
             L.orc_tet_elasticity.argtypes = [vp, dp, dp, dp, vp]
+            L.orc_tet_p2.restype = dp
+            L.orc_tet_p2.argtypes = [vp, dp, vp, vp]
+            L.orc_ndofs.restype = ip
+            L.orc_ndofs.argtypes = [vp, ip]
             L.orc_lu_factor.argtypes = [ip, vp]
             L.orc_lu_solve.argtypes = [ip, vp, vp]
             L.orc_build_interp.restype = C.c_long
@@ -90,7 +94,7 @@ def _p(a):
 _COEF = {"const": 0, "cosexp": 1}
 _LOAD = {"one": 0, "sines": 1}
 _TRANSFER = {"bary": 0, "mls": 1}
-_PDE = {"poisson": 0, "elasticity": 1}
+_PDE = {"poisson": 0, "elasticity": 1, "poisson_p2": 2}
 
 
 def lame(poisson):
@@ -137,7 +141,8 @@ class Oracle:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels
         self.fields = 3 if pde == "elasticity" else 1
-        self.n = [self.fields * lv.n_nodes for lv in levels]  # DoFs per level
+        self.pde = pde
+        self.n = [int(L.orc_ndofs(self.h, l)) for l in range(len(levels))]  # DoFs per level
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -155,7 +160,7 @@ class Oracle:
         if dtype is None:
             dtype = {"val": np.float64, "b": np.float64, "P_val": np.float64,
                      "PT_val": np.float64, "sub_lu": np.float64, "sub_ilu_val": np.float64,
-                     "sub_own": np.uint8}.get(what, np.int32)
+                     "sub_own": np.uint8, "dofdir": np.uint8, "dofx": np.float64}.get(what, np.int32)
         if cnt == 0:
             return np.zeros(0, dtype)
         buf = (C.c_char * (cnt * np.dtype(dtype).itemsize)).from_address(ptr.value)
@@ -246,6 +251,17 @@ class Oracle:
         st = lib().orc_fgmres(self.h, _p(b), _p(x), float(rtol), int(restart), int(maxit),
                               1 if precond else 0, C.byref(it), C.byref(rr))
         return x, dict(status=int(st), iters=int(it.value), relres=float(rr.value))
+
+
+def tet_p2(x4, k=1.0):
+    """P2 element of a tet: 10 x 10 stiffness k int grad phi_i . grad phi_j
+    (local DoFs: vertices 0..3, then edges 01 02 03 12 13 23), the integrals
+    int phi_i, and the volume."""
+    x4 = np.ascontiguousarray(x4, np.float64).reshape(4, 3)
+    K = np.zeros((10, 10))
+    m = np.zeros(10)
+    vol = lib().orc_tet_p2(_p(x4), float(k), _p(K), _p(m))
+    return K, m, vol
 
 
 def tet_stiffness(x4, k=1.0):

@@ -23,7 +23,9 @@ def workload(name, hierarchy_id=0):
 
 
 def _pde(w):
-    return dict(pde=w["pde"], poisson=w["poisson"]) if "pde" in w else {}
+    if "pde" not in w:
+        return {}
+    return dict(pde=w["pde"], poisson=w.get("poisson", 0.3))
 
 
 def make_oracle(levels, w, orc, **kw):
@@ -41,7 +43,9 @@ def make_hierarchy(levels, w, P, **kw):
 
 
 def n_dofs(levels, w, level=0):
-    """Vector length of a level of a workload."""
+    """Vector length of a level of a workload (P1 DoF distributions only; with
+    P2 elements take the oracle's count)."""
+    assert w.get("pde") != "poisson_p2"
     return (3 if w.get("pde") == "elasticity" else 1) * levels[level].n_nodes
 
 

@@ -39,6 +39,9 @@ DESCR = {
                    "one mu per step (16 sequential)",
     "cube16_3lvl": "16^3/8^3/4^3 jittered Kuhn meshes, 64/8 subdomains, overlap 2",
     "cube8_2lvl": "8^3/4^3 jittered Kuhn meshes, k=1, 8 subdomains, overlap 1",
+    "p2cube32_3lvl": "quadratic (P2) elements, DoFs on the vertices and edge midpoints (N = (1,1,0,0)), on "
+                     "32^3/16^3/8^3 jittered Kuhn meshes: 274,625 fine DoFs, 512 + 64 subdomains, overlap 1, "
+                     "nu=2, P2 interpolation between the non-nested levels, coarsest direct, FGMRES(30) rtol 1e-8",
     "elast32_3lvl": "linear elasticity (three P1 displacement fields per vertex, Poisson ratio 0.3, "
                     "Young's modulus k(x;mu), unit body force along -z) on 32^3/16^3/8^3 jittered "
                     "Kuhn meshes: 107,811 fine DoFs, 64 + 8 subdomains, overlap 1, nu=2, field-split "
@@ -92,6 +95,8 @@ def parse():
                     help="skip the 96^3 L-shaped precision study (FP64 / FP32 / BF16 factors)")
     ap.add_argument("--no-elastic", action="store_true",
                     help="skip the linear-elasticity (three fields per vertex) object")
+    ap.add_argument("--no-p2", action="store_true",
+                    help="skip the quadratic-element (DoFs on vertices and edges) object")
     ap.add_argument("--no-ilu", action="store_true",
                     help="skip the ILU(2)/ILU(0) subdomain-solver variant (Section 4.4)")
     ap.add_argument("--no-literal", action="store_true",
@@ -883,6 +888,28 @@ def run_msp(args):
             else:
                 e["rel_diff_vs_f64_solution"] = float(np.linalg.norm(r["x"] - x64) / np.linalg.norm(x64))
             elastic[prec] = e
+    p2 = None
+    if not args.no_p2 and args.precision == "f64":
+        # quadratic elements: DoFs on the vertices and the edge midpoints
+        lv_q, w_q = syn.workload("p2cube32_3lvl")
+        kw_q = dict(delta=w_q["delta"], nu_pre=w_q["nu"], nu_post=w_q["nu"], restart=w_q["restart"],
+                    coef=w_q["coef"], wave=syn.wave_vectors(), scale=w_q["scale"], load=w_q["load"],
+                    pde="poisson_p2")
+        k = max(2, min(args.steps, 8))
+        p2 = {"workload": "p2cube32_3lvl", "description": DESCR["p2cube32_3lvl"]}
+        x64 = None
+        for prec in ("f64", "f32"):
+            r = measure(prec, k, args.warmup, lv=lv_q, opts=kw_q, time_dominant=False)
+            e = {"value": k / (r["ms"] / 1e3), "unit": UNIT, "steps": k,
+                 "iterations_mean": float(np.mean(r["iters"])),
+                 "final_rel_residual_max": float(np.max(r["relres"])),
+                 "stage_ms_host": r["stage_ms"], "kernel_ms_per_solve": r["kernel_ms"]}
+            p2["dofs"] = int(r["x"].size)
+            if x64 is None:
+                x64 = r["x"]
+            else:
+                e["rel_diff_vs_f64_solution"] = float(np.linalg.norm(r["x"] - x64) / np.linalg.norm(x64))
+            p2[prec] = e
     ilu = None
     if not args.no_ilu and args.precision == "f64":
         ilu = {"subdomain_solver": "ILU(2) on level 0, ILU(0) on level 1 (Section 4.4); coarsest direct (FP64)"}
@@ -970,6 +997,8 @@ def run_msp(args):
         line["mls"] = mls
     if ilu:
         line["ilu"] = ilu
+    if p2:
+        line["p2"] = p2
     if hbm:
         line["hbm_kernels"] = hbm
     if elastic:

@@ -101,8 +101,23 @@ typedef enum msp_load { MSP_F_ONE = 0, MSP_F_SINES = 1 } msp_load;
  *       N = (3,0,0,0), DoF 3v + c for field c of vertex v.  A Dirichlet vertex
  *       fixes its three fields.  The transfers are split by field: P (x) I_3,
  *       the field-splitting interpolation I = sum_f R_f^T I_f R~_f of
- *       Section 2.1 with the scalar barycentric P for every field. */
-typedef enum msp_pde { MSP_PDE_POISSON = 0, MSP_PDE_ELASTICITY = 1 } msp_pde;
+ *       Section 2.1 with the scalar barycentric P for every field.
+ *   MSP_PDE_POISSON_P2: -div(k grad u) = f with continuous piecewise-quadratic
+ *       (P2) Lagrange elements: one DoF at every vertex and one at the midpoint
+ *       of every edge, N = (1,1,0,0).  DoF order: vertex 0, then its edges
+ *       (0, b) to higher-numbered vertices b in ascending b, then vertex 1 and
+ *       its edges (1, b), b > 1, and so on (the edges are the distinct vertex
+ *       pairs of the tets).  A vertex DoF is Dirichlet as its vertex; an edge
+ *       DoF when the edge lies on a boundary face (a face of one tet only)
+ *       whose three vertices are Dirichlet.  An edge DoF belongs to the
+ *       partition id of its lower vertex if that id owns a non-Dirichlet
+ *       vertex, else to that of its upper vertex.  Subdomains grow by delta
+ *       (>= 1) element layers over the vertices as for P1 and hold the vertex
+ *       DoFs and the edge DoFs with both ends inside.  The transfers are the
+ *       P2 interpolation (the coarse P2 basis evaluated at the fine DoF
+ *       points; restriction by its transpose).  Loads: MSP_F_ONE only
+ *       (b_i = integral of phi_i). */
+typedef enum msp_pde { MSP_PDE_POISSON = 0, MSP_PDE_ELASTICITY = 1, MSP_PDE_POISSON_P2 = 2 } msp_pde;
 
 /* One mesh level (Section 2.1: the mesh perspective M = (K, N); the DoFs
  * per vertex follow msp_options.pde).  All arrays are host memory, copied. */

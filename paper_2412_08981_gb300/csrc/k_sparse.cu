@@ -28,10 +28,25 @@ constexpr double kPi = 3.14159265358979323846;
 //   |T| (lam g_a[i] g_b[j] + mu g_a[j] g_b[i] + [i == j] mu g_a . g_b),
 // the unit-k element matrix of int 2 mu eps(u):eps(v) + lam div u div v,
 // upper triangle row-major.
-template <bool Elastic>
+// P2 (Kind 2): S[e*55 + slot(i, j)] = int_T grad phi_i . grad phi_j for the
+// local DoFs vertices 0..3, edges 01 02 03 12 13 23, phi_a = l_a (2 l_a - 1),
+// phi_ab = 4 l_a l_b, in closed form from G_ab = grad l_a . grad l_b and the
+// moments int l_a = |T|/4, int l_a l_b = |T| (1 + [a == b]) / 20:
+//   vertex a, vertex b: G_ab |T| (0.8 (1 + [a == b]) - 1);
+//   vertex a, edge bc : 4 (G_ac m_ab + G_ab m_ac), m_ab = int (4 l_a - 1) l_b
+//                       = |T| ((1 + [a == b]) / 5 - 1/4);
+//   edge ab, edge cd  : 16 (G_bd M_ac + G_bc M_ad + G_ad M_bc + G_ac M_bd),
+//                       M_ij = int l_i l_j.
+__device__ __forceinline__ int p2_local_slot(int r, int c) {
+  if (r > c) { const int t = r; r = c; c = t; }
+  return 10 * r - r * (r - 1) / 2 + (c - r);
+}
+
+template <int Kind>
 __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                                int m, double lam, double mu, double* __restrict__ S,
                                double* __restrict__ vol, double* __restrict__ cen, int* bad) {
+  constexpr bool Elastic = Kind == 1;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   int4 t = reinterpret_cast<const int4*>(tets)[e];
@@ -77,6 +92,29 @@ __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __
         if (i == j) v += mu * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
         S[(int64_t)e * 78 + s] = vv * v;
         ++s;
+      }
+  } else if (Kind == 2) {
+    constexpr int ea[6] = {0, 0, 0, 1, 1, 2}, eb[6] = {1, 2, 3, 2, 3, 3};
+    double G[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) G[a][b] = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+    auto M2 = [&](int i, int j) { return vv * (i == j ? 2.0 : 1.0) / 20.0; };
+    auto mv = [&](int a, int b) { return vv * ((a == b ? 2.0 : 1.0) / 5.0 - 0.25); };
+    double* Se = S + (int64_t)e * 55;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a; b < 4; ++b) Se[p2_local_slot(a, b)] = G[a][b] * vv * (a == b ? 0.6 : -0.2);
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 6; ++k) {
+        const int b = ea[k], c = eb[k];
+        Se[p2_local_slot(a, 4 + k)] = 4.0 * (G[a][c] * mv(a, b) + G[a][b] * mv(a, c));
+      }
+    for (int k = 0; k < 6; ++k)
+      for (int k2 = k; k2 < 6; ++k2) {
+        const int a = ea[k], b = eb[k], c = ea[k2], d = eb[k2];
+        Se[p2_local_slot(4 + k, 4 + k2)] =
+            16.0 * (G[b][d] * M2(a, c) + G[b][c] * M2(a, d) + G[a][d] * M2(b, c) + G[a][c] * M2(b, d));
       }
   } else {
     int s = 0;
@@ -133,10 +171,19 @@ __global__ void k_load_vector(const double* __restrict__ xyz, const uint8_t* __r
     b[i] = 0.0;
     return;
   }
-  const double* x = xyz + 3 * (int64_t)(i / fields);
-  double f = fields == 1 ? load_f(kind, x[0], x[1], x[2]) : load_elastic(kind, i % fields, x, lam, mu);
   int q = diag[i];
   double s = 0.0;
+  if (ns == 55) {  // P2, f = 1: the diagonal slot names the local DoF (vertex slots < 34)
+    for (int c = cptr[q]; c < cptr[q + 1]; ++c) {
+      const int id = contrib[c];
+      const double v = vol[id / 55];
+      s += (id % 55) < 34 ? -v / 20.0 : v / 5.0;
+    }
+    b[i] = s;
+    return;
+  }
+  const double* x = xyz + 3 * (int64_t)(i / fields);
+  double f = fields == 1 ? load_f(kind, x[0], x[1], x[2]) : load_elastic(kind, i % fields, x, lam, mu);
   for (int c = cptr[q]; c < cptr[q + 1]; ++c) s += f * vol[contrib[c] / ns] / 4.0;
   b[i] = s;
 }
@@ -526,13 +573,15 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, bool elastic, double lam, double mu,
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, int kind, double lam, double mu,
                          double* S, double* vol, double* cen, int* bad, cudaStream_t s) {
   if (m <= 0) return;
-  if (elastic)
-    k_tet_geometry<true><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
+  if (kind == 1)
+    k_tet_geometry<1><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
+  else if (kind == 2)
+    k_tet_geometry<2><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
   else
-    k_tet_geometry<false><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
+    k_tet_geometry<0><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
 }
 
 void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,

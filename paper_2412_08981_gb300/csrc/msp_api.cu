@@ -314,7 +314,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.cptr = A.upload(H.cptr);
   D.contrib = A.upload(H.contrib);
   D.nzflag = A.upload(H.nzflag);
-  D.S = A.alloc<double>((size_t)H.m * (H.fields == 3 ? kElasticSlots : 10));
+  D.S = A.alloc<double>((size_t)H.m * H.nslot);
   D.vol = A.alloc<double>(H.m);
   D.cen = A.alloc<double>((size_t)H.m * 3);
   D.b = A.alloc<double>(H.n);
@@ -474,10 +474,10 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   // Lame parameters of a unit Young's modulus (linear elasticity only)
   const double nu = h->opt.poisson_ratio;
   const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
-  const bool elastic = H.fields == 3;
-  launch_tet_geometry(D.xyz, D.tets, D.m, elastic, lam, mu, D.S, D.vol, D.cen, bad, s);
+  const int kind = H.fields == 3 ? 1 : (H.p2 ? 2 : 0);  // element: P1, elasticity, P2
+  launch_tet_geometry(D.xyz, D.tets, D.m, kind, lam, mu, D.S, D.vol, D.cen, bad, s);
   launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, H.fields,
-                     elastic ? kElasticSlots : 10, lam, mu, D.b, s);
+                     H.nslot, lam, mu, D.b, s);
   int hbad = 0;
   MSP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   MSP_CUDA(cudaStreamSynchronize(s));
@@ -520,7 +520,12 @@ int check_options(const msp_options& o) {
   if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
     return fail(MSP_ERR_INVALID, "unknown load");
   if (!std::isfinite(o.coef_scale)) return fail(MSP_ERR_INVALID, "non-finite coef_scale");
-  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY) return fail(MSP_ERR_INVALID, "unknown pde");
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2)
+    return fail(MSP_ERR_INVALID, "unknown pde");
+  if (o.pde == MSP_PDE_POISSON_P2 && o.transfer != MSP_TRANSFER_BARY)
+    return fail(MSP_ERR_INVALID, "P2 elements take the P2 interpolation between levels, not MLS");
+  if (o.pde == MSP_PDE_POISSON_P2 && o.load_kind != MSP_F_ONE)
+    return fail(MSP_ERR_INVALID, "P2 elements support the load f = 1 only");
   if (o.pde == MSP_PDE_ELASTICITY && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
     return fail(MSP_ERR_INVALID, "linear elasticity needs a Poisson ratio in (0, 0.5)");
   if (o.pde == MSP_PDE_ELASTICITY && o.transfer != MSP_TRANSFER_BARY)
@@ -539,7 +544,7 @@ int assemble_all(msp_instance* I) {
     ProfScope ps(I->prof, PK_ASSEMBLE, s, 2);
     launch_coefficient(D.cen, D.m, h->opt.coef_kind, I->mu, h->wave, h->opt.coef_scale, I->k[l], s);
     launch_assemble(D.cptr, D.contrib, D.nzflag, I->k[l], D.S, D.nnz,
-                    h->host[l].fields == 3 ? kElasticSlots : 10, I->val[l], s);
+                    h->host[l].nslot, I->val[l], s);
     ps.account((double)D.nnz * 8 + (double)D.nnz * 5 + (double)h->host[l].contrib.size() * 12 +
                    (double)D.m * 32,
                (double)h->host[l].contrib.size() * 2);

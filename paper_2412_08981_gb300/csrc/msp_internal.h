@@ -33,12 +33,28 @@ inline int elastic_slot(int r, int s) {
 }
 constexpr int kElasticSlots = 78;
 
+// Quadratic (P2) elements: local DoFs of a tet are its vertices 0..3, then
+// its edges 01, 02, 03, 12, 13, 23; the symmetric 10 x 10 element matrix is
+// stored by its upper triangle, row-major: 55 slots.
+constexpr int kP2Slots = 55;
+inline int p2_slot(int r, int s) {
+  if (r > s) { int t = r; r = s; s = t; }
+  return 10 * r - r * (r - 1) / 2 + (s - r);
+}
+constexpr int kP2EdgeEnd[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
 // Host-side structures of one level, built once per hierarchy.
 struct HostLevel {
   // n: DoFs = fields x nv; xyz / tets are per vertex; dir, owner and dir_list
   // are per DoF (field c of vertex v is DoF fields*v + c)
   int n = 0, m = 0;
   int nv = 0, fields = 1;
+  int nslot = 10;  // element-matrix slots per tet: 10 (P1), 78 (elasticity), 55 (P2)
+  // P2 only: the global DoF of each of the 10 local DoFs of every tet, and
+  // the point of every DoF (a vertex, or an edge's midpoint)
+  bool p2 = false;
+  std::vector<int32_t> tdof;
+  std::vector<double> dofx;
   std::vector<double> xyz;
   std::vector<int32_t> tets;
   std::vector<uint8_t> dir;

@@ -9,13 +9,16 @@
 namespace msp {
 
 // ---- per-tet geometry (set-up) and per-parameter coefficient / assembly
-// S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b), or with `elastic` the 78
-// upper-triangle slots of the unit-k 12 x 12 elasticity matrix (Lame lam, mu);
-// vol[e] = |T|; cen[e*3] centroid
-void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, bool elastic, double lam, double mu,
+// kind 0 (P1): S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b); kind 1
+// (elasticity): the 78 upper-triangle slots of the unit-k 12 x 12 elasticity
+// matrix (Lame lam, mu); kind 2 (P2): the 55 upper-triangle slots of the
+// unit-k 10 x 10 quadratic-element matrix; vol[e] = |T|; cen[e*3] centroid
+void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, int kind, double lam, double mu,
                          double* S, double* vol, double* cen, int* bad, cudaStream_t s);
 // b_i = f_c(x_v) * sum_{e containing v} |T_e| / 4 (ascending e) for DoF i =
-// fields*v + c, 0 on Dirichlet DoFs; ns slots per tet in the contributions
+// fields*v + c, 0 on Dirichlet DoFs; ns slots per tet in the contributions.
+// With P2 elements (ns == 55, f = 1): b_i = sum_e int_e phi_i, -|T|/20 for a
+// vertex DoF and |T|/5 for an edge DoF.
 void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* diag,
                         const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
                         int load_kind, int fields, int ns, double lam, double mu, double* b,

@@ -1017,6 +1017,342 @@ void expand_fields(HostLevel& L) {
   L.sub_own.swap(so);
 }
 
+// ------------------------------------------------ quadratic (P2) elements
+// One DoF per vertex and one per edge (the DoF distribution N = (1,1,0,0) of
+// the mesh perspective, Section 2.1).  The edges are the distinct vertex
+// pairs of the tets.  Numbering: each vertex is followed by its edges to
+// higher-numbered vertices, ascending, so that the DoF of vertex v is
+// v + (edges of the vertices before v) and a block's DoFs stay banded.  A
+// vertex DoF is Dirichlet as its vertex; an edge DoF when the edge lies on a
+// boundary face (a face of exactly one tet) with three Dirichlet vertices.
+// The pattern couples the DoFs of each tet; contribution e*55 + slot(li, lj)
+// of tet e (ascending e) feeds the nonzero of its local DoFs li, lj.
+std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool smoothed) {
+  const int nv = L.nv;
+  std::vector<int32_t> vptr, vadj;
+  vertex_tets(L, vptr, vadj);
+  // upper neighbours of every vertex through the edges of its tets
+  std::vector<int32_t> uptr(nv + 1, 0), ucol;
+  {
+    std::vector<std::vector<int32_t>> up(nv);
+    for (int e = 0; e < L.m; ++e)
+      for (int k = 0; k < 6; ++k) {
+        int a = L.tets[4 * (int64_t)e + kP2EdgeEnd[k][0]], b = L.tets[4 * (int64_t)e + kP2EdgeEnd[k][1]];
+        if (a > b) std::swap(a, b);
+        up[a].push_back(b);
+      }
+    for (int v = 0; v < nv; ++v) {
+      std::sort(up[v].begin(), up[v].end());
+      up[v].erase(std::unique(up[v].begin(), up[v].end()), up[v].end());
+      uptr[v + 1] = uptr[v] + (int32_t)up[v].size();
+    }
+    ucol.reserve(uptr[nv]);
+    for (int v = 0; v < nv; ++v) ucol.insert(ucol.end(), up[v].begin(), up[v].end());
+  }
+  const int64_t ne = uptr[nv];
+  if (nv + ne > INT32_MAX / 2) return "too many P2 DoFs";
+  auto vdof = [&](int v) { return v + uptr[v]; };
+  auto edof = [&](int a, int b) {  // a != b
+    if (a > b) std::swap(a, b);
+    const int32_t* lo = ucol.data() + uptr[a];
+    const int32_t* hi = ucol.data() + uptr[a + 1];
+    const int32_t* it = std::lower_bound(lo, hi, b);
+    return (int32_t)(a + 1 + (it - ucol.data()));
+  };
+  const int n = (int)(nv + ne);
+  std::vector<uint8_t> vdir = L.dir;
+  L.p2 = true;
+  L.nslot = kP2Slots;
+  L.n = n;
+  L.tdof.assign(10 * (size_t)L.m, 0);
+  for (int e = 0; e < L.m; ++e) {
+    const int32_t* t = &L.tets[4 * (int64_t)e];
+    for (int a = 0; a < 4; ++a) L.tdof[10 * (size_t)e + a] = vdof(t[a]);
+    for (int k = 0; k < 6; ++k) L.tdof[10 * (size_t)e + 4 + k] = edof(t[kP2EdgeEnd[k][0]], t[kP2EdgeEnd[k][1]]);
+  }
+  L.dofx.assign(3 * (size_t)n, 0.0);
+  L.dir.assign(n, 0);
+  for (int v = 0; v < nv; ++v) {
+    for (int d = 0; d < 3; ++d) L.dofx[3 * (size_t)vdof(v) + d] = L.xyz[3 * (size_t)v + d];
+    L.dir[vdof(v)] = vdir[v];
+    for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k)
+      for (int d = 0; d < 3; ++d)
+        L.dofx[3 * (size_t)(v + 1 + k) + d] = 0.5 * (L.xyz[3 * (size_t)v + d] + L.xyz[3 * (size_t)ucol[k] + d]);
+  }
+  // boundary faces: faces that no other tet shares
+  for (int e = 0; e < L.m; ++e) {
+    const int32_t* t = &L.tets[4 * (int64_t)e];
+    for (int skip = 0; skip < 4; ++skip) {
+      int f[3], c = 0;
+      for (int a = 0; a < 4; ++a)
+        if (a != skip) f[c++] = t[a];
+      if (!(vdir[f[0]] && vdir[f[1]] && vdir[f[2]])) continue;
+      int shared = 0;
+      for (int k = vptr[f[0]]; k < vptr[f[0] + 1] && !shared; ++k) {
+        const int e2 = vadj[k];
+        if (e2 == e) continue;
+        const int32_t* t2 = &L.tets[4 * (int64_t)e2];
+        int hit = 0;
+        for (int a = 0; a < 4; ++a) hit += (t2[a] == f[1]) + (t2[a] == f[2]);
+        shared = hit == 2;
+      }
+      if (shared) continue;
+      L.dir[edof(f[0], f[1])] = 1;
+      L.dir[edof(f[0], f[2])] = 1;
+      L.dir[edof(f[1], f[2])] = 1;
+    }
+  }
+  L.dir_list.clear();
+  for (int i = 0; i < n; ++i)
+    if (L.dir[i]) L.dir_list.push_back(i);
+  // pattern: the DoFs of the tets holding each DoF (found among the tets of
+  // the DoF's vertex, or of its edge's lower vertex)
+  std::vector<int32_t> ent_a(n), ent_b(n, -1);  // DoF -> its vertex (a) or edge (a, b)
+  for (int v = 0; v < nv; ++v) {
+    ent_a[vdof(v)] = v;
+    for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k) {
+      ent_a[v + 1 + k] = v;
+      ent_b[v + 1 + k] = ucol[k];
+    }
+  }
+  auto holds = [&](int e, int i) {  // local index of DoF i in tet e, or -1
+    for (int li = 0; li < 10; ++li)
+      if (L.tdof[10 * (size_t)e + li] == i) return li;
+    return -1;
+  };
+  L.rowptr.assign(n + 1, 0);
+  std::vector<std::vector<int32_t>> rows(n);
+  std::vector<int32_t> buf;
+  for (int i = 0; i < n; ++i) {
+    buf.clear();
+    const int a = ent_a[i];
+    for (int k = vptr[a]; k < vptr[a + 1]; ++k) {
+      const int e = vadj[k];
+      if (holds(e, i) < 0) continue;
+      buf.insert(buf.end(), &L.tdof[10 * (size_t)e], &L.tdof[10 * (size_t)e] + 10);
+    }
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    rows[i] = buf;
+    L.rowptr[i + 1] = L.rowptr[i] + (int32_t)buf.size();
+  }
+  L.col.resize(L.rowptr[n]);
+  L.diag.assign(n, -1);
+  for (int i = 0; i < n; ++i) {
+    std::copy(rows[i].begin(), rows[i].end(), L.col.begin() + L.rowptr[i]);
+    L.diag[i] = find_in_row(L, i, i);
+  }
+  rows.clear();
+  rows.shrink_to_fit();
+  const int64_t nnz = L.col.size();
+  L.nzflag.assign(nnz, 0);
+  for (int i = 0; i < n; ++i)
+    for (int q = L.rowptr[i]; q < L.rowptr[i + 1]; ++q) {
+      const int j = L.col[q];
+      if (L.dir[i]) L.nzflag[q] = (i == j) ? 1 : 2;
+      else if (L.dir[j]) L.nzflag[q] = 2;
+    }
+  std::vector<int32_t> cnt(nnz + 1, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int32_t> fill;
+    if (pass == 1) {
+      L.cptr.assign(nnz + 1, 0);
+      for (int64_t q = 0; q < nnz; ++q) L.cptr[q + 1] = L.cptr[q] + cnt[q];
+      L.contrib.assign(L.cptr[nnz], 0);
+      fill.assign(L.cptr.begin(), L.cptr.end() - 1);
+    }
+    for (int i = 0; i < n; ++i) {
+      if (L.dir[i]) continue;
+      const int a = ent_a[i];
+      for (int k = vptr[a]; k < vptr[a + 1]; ++k) {  // ascending tet id
+        const int e = vadj[k];
+        const int li = holds(e, i);
+        if (li < 0) continue;
+        for (int lj = 0; lj < 10; ++lj) {
+          const int32_t q = find_in_row(L, i, L.tdof[10 * (size_t)e + lj]);
+          if (L.nzflag[q] != 0) continue;
+          if (pass == 0) cnt[q]++;
+          else L.contrib[fill[q]++] = e * kP2Slots + p2_slot(li, lj);
+        }
+      }
+    }
+  }
+  if (!smoothed) return "";
+  // owners: a vertex's own; an edge's lower vertex's, if that id owns a
+  // non-Dirichlet vertex, else its upper vertex's
+  std::vector<char> is_id;
+  {
+    int32_t mx = 0;
+    for (int v = 0; v < nv; ++v) mx = std::max(mx, vowner[v]);
+    is_id.assign((size_t)mx + 1, 0);
+    for (int v = 0; v < nv; ++v)
+      if (!vdir[v] && vowner[v] >= 0) is_id[vowner[v]] = 1;
+  }
+  L.owner.assign(n, -1);
+  for (int i = 0; i < n; ++i) {
+    if (ent_b[i] < 0) {
+      L.owner[i] = vowner[ent_a[i]];
+    } else {
+      const int32_t oa = vowner[ent_a[i]], ob = vowner[ent_b[i]];
+      L.owner[i] = (oa >= 0 && is_id[oa]) ? oa : ((ob >= 0 && is_id[ob]) ? ob : -1);
+      if (L.owner[i] < 0 && !L.dir[i]) return "an edge DoF has no owning subdomain";
+    }
+  }
+  if (delta < 1) return "P2 subdomains need delta >= 1";
+  // subdomains: vertex layers over the tets from the vertices of each id,
+  // then the vertex DoFs and the DoFs of edges with both ends inside
+  std::vector<int32_t> ids;
+  for (int v = 0; v < nv; ++v)
+    if (!vdir[v]) ids.push_back(vowner[v]);
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  L.nsub = (int)ids.size();
+  std::vector<std::vector<int32_t>> by_id(L.nsub);
+  for (int v = 0; v < nv; ++v) {
+    auto it = std::lower_bound(ids.begin(), ids.end(), vowner[v]);
+    if (it != ids.end() && *it == vowner[v]) by_id[it - ids.begin()].push_back(v);
+  }
+  std::vector<std::vector<int32_t>> dofs(L.nsub);
+  std::vector<std::vector<uint8_t>> own(L.nsub);
+  auto work = [&](int p0, int p1) {
+    std::vector<int32_t> stamp(nv, -1), frontier, next, members;
+    for (int p = p0; p < p1; ++p) {
+      members = by_id[p];
+      frontier = members;
+      for (int v : members) stamp[v] = p;
+      for (int layer = 0; layer < delta; ++layer) {
+        next.clear();
+        for (int v : frontier)
+          for (int k = vptr[v]; k < vptr[v + 1]; ++k)
+            for (int a = 0; a < 4; ++a) {
+              const int w = L.tets[4 * (int64_t)vadj[k] + a];
+              if (stamp[w] != p) {
+                stamp[w] = p;
+                members.push_back(w);
+                next.push_back(w);
+              }
+            }
+        frontier.swap(next);
+      }
+      std::vector<int32_t> d;
+      for (int v : members) {
+        if (!L.dir[vdof(v)]) d.push_back(vdof(v));
+        for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k)
+          if (stamp[ucol[k]] == p && !L.dir[v + 1 + k]) d.push_back(v + 1 + k);
+      }
+      std::sort(d.begin(), d.end());
+      std::vector<uint8_t> o(d.size());
+      for (size_t k = 0; k < d.size(); ++k) o[k] = (L.owner[d[k]] == ids[p]) ? 1 : 0;
+      dofs[p] = std::move(d);
+      own[p] = std::move(o);
+    }
+  };
+  int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+  nth = std::min(nth, std::max(1, L.nsub));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back(work, (int)((int64_t)L.nsub * t / nth), (int)((int64_t)L.nsub * (t + 1) / nth));
+  for (auto& t : th) t.join();
+  L.sub_ptr.assign(L.nsub + 1, 0);
+  for (int p = 0; p < L.nsub; ++p) L.sub_ptr[p + 1] = L.sub_ptr[p] + (int32_t)dofs[p].size();
+  L.sub_dofs.resize(L.sub_ptr[L.nsub]);
+  L.sub_own.resize(L.sub_ptr[L.nsub]);
+  for (int p = 0; p < L.nsub; ++p) {
+    std::copy(dofs[p].begin(), dofs[p].end(), L.sub_dofs.begin() + L.sub_ptr[p]);
+    std::copy(own[p].begin(), own[p].end(), L.sub_own.begin() + L.sub_ptr[p]);
+  }
+  // every non-Dirichlet DoF owned exactly once
+  std::vector<int> owned(n, 0);
+  for (size_t k = 0; k < L.sub_dofs.size(); ++k) owned[L.sub_dofs[k]] += L.sub_own[k];
+  for (int i = 0; i < n; ++i)
+    if (!L.dir[i] && owned[i] != 1) return "internal: a P2 DoF is not owned exactly once";
+  return "";
+}
+
+// P2 interpolation from C (coarse) to the DoFs of F: every non-Dirichlet
+// fine DoF point is located in the coarse mesh by the rule of build_interp
+// (the lowest containing tet id, else the tet whose smallest barycentric
+// weight is largest) and its row holds the coarse tet's ten P2 basis
+// functions there -- vertex a: l_a (2 l_a - 1), edge ab: 4 l_a l_b -- on the
+// non-Dirichlet coarse DoFs, columns ascending, zero weights kept.
+void build_interp_p2(const HostLevel& F, const HostLevel& C, HostLevel& out) {
+  TetGrid g;
+  build_grid(C, g);
+  const int n = F.n;
+  std::vector<int32_t> tet_of(n, -1);
+  std::vector<double> lam_of(4 * (size_t)n, 0.0);
+  auto work = [&](int f0, int f1) {
+    for (int f = f0; f < f1; ++f) {
+      if (F.dir[f]) continue;
+      const double* x = &F.dofx[3 * (size_t)f];
+      size_t c = (size_t)g.cell(x[0], 0) + (size_t)g.G * ((size_t)g.cell(x[1], 1) + (size_t)g.G * g.cell(x[2], 2));
+      int best = -1;
+      double lam[4];
+      for (int k = g.ptr[c]; k < g.ptr[c + 1]; ++k) {
+        bary(C, g.ids[k], x, lam);
+        if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) {
+          best = g.ids[k];
+          break;
+        }
+      }
+      if (best < 0) {
+        double bm = -1e300, l2[4];
+        for (int e = 0; e < C.m; ++e) {
+          bary(C, e, x, l2);
+          const double mn = std::min(std::min(l2[0], l2[1]), std::min(l2[2], l2[3]));
+          if (mn > bm) {
+            bm = mn;
+            best = e;
+            std::copy(l2, l2 + 4, lam);
+          }
+        }
+      }
+      tet_of[f] = best;
+      std::copy(lam, lam + 4, &lam_of[4 * (size_t)f]);
+    }
+  };
+  int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back(work, (int)((int64_t)n * t / nth), (int)((int64_t)n * (t + 1) / nth));
+  for (auto& t : th) t.join();
+  out.P_rowptr.assign(n + 1, 0);
+  out.P_col.clear();
+  out.P_val.clear();
+  std::vector<std::pair<int32_t, double>> row;
+  for (int f = 0; f < n; ++f) {
+    if (tet_of[f] >= 0) {
+      const double* l = &lam_of[4 * (size_t)f];
+      const int32_t* td = &C.tdof[10 * (size_t)tet_of[f]];
+      row.clear();
+      for (int i = 0; i < 10; ++i) {
+        if (C.dir[td[i]]) continue;
+        const double w = i < 4 ? l[i] * (2.0 * l[i] - 1.0)
+                               : 4.0 * l[kP2EdgeEnd[i - 4][0]] * l[kP2EdgeEnd[i - 4][1]];
+        row.push_back({td[i], w});
+      }
+      std::sort(row.begin(), row.end());
+      for (auto& pr : row) {
+        out.P_col.push_back(pr.first);
+        out.P_val.push_back(pr.second);
+      }
+    }
+    out.P_rowptr[f + 1] = (int32_t)out.P_col.size();
+  }
+  out.PT_rowptr.assign(C.n + 1, 0);
+  for (int32_t c : out.P_col) out.PT_rowptr[c + 1]++;
+  for (int i = 0; i < C.n; ++i) out.PT_rowptr[i + 1] += out.PT_rowptr[i];
+  out.PT_col.resize(out.P_col.size());
+  out.PT_val.resize(out.P_col.size());
+  std::vector<int32_t> fill(out.PT_rowptr.begin(), out.PT_rowptr.end() - 1);
+  for (int f = 0; f < n; ++f)
+    for (int q = out.P_rowptr[f]; q < out.P_rowptr[f + 1]; ++q) {
+      const int32_t d = fill[out.P_col[q]]++;
+      out.PT_col[d] = f;
+      out.PT_val[d] = out.P_val[q];
+    }
+}
+
 std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
   if (d.n_nodes <= 0 || d.n_tets <= 0 || !d.xyz || !d.tets || !d.dirichlet)
     return "level " + std::to_string(l) + ": empty mesh or NULL array";
@@ -1046,8 +1382,12 @@ std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
 std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_options& o,
                               std::vector<HostLevel>& out) {
   if (nlevels < 1) return "nlevels must be >= 1";
-  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY) return "unknown pde";
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2)
+    return "unknown pde";
   const bool elastic = o.pde == MSP_PDE_ELASTICITY;
+  const bool p2 = o.pde == MSP_PDE_POISSON_P2;
+  if (p2 && o.transfer != MSP_TRANSFER_BARY) return "P2 elements take the barycentric-rule transfers (P2 interpolation)";
+  if (p2 && o.load_kind != MSP_F_ONE) return "P2 elements support the load f = 1 only";
   if (elastic && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
     return "linear elasticity needs a Poisson ratio in (0, 0.5)";
   if (elastic && o.transfer != MSP_TRANSFER_BARY)
@@ -1067,6 +1407,13 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     for (int i = 0; i < L.n; ++i)
       if (L.dir[i]) L.dir_list.push_back(i);
     if (need_owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
+    L.direct = (l + 1 == nlevels) && o.coarse_solver == MSP_COARSE_DIRECT;
+    if (p2) {
+      std::string e2 = build_p2_level(L, lv[l].owner, o.delta, !L.direct);
+      if (!e2.empty()) return "level " + std::to_string(l) + ": " + e2;
+      if (L.direct) build_coarsest_block(L);
+      continue;
+    }
     build_pattern_and_contribs(L);
     for (int i = 0; i < L.n; ++i)
       if (L.diag[i] < 0) return "level " + std::to_string(l) + ": node " + std::to_string(i) + " belongs to no tet";
@@ -1079,7 +1426,9 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
   for (int l = 0; l + 1 < nlevels; ++l) {
     HostLevel& F = out[l];
     const HostLevel& C = out[l + 1];
-    if (o.transfer == MSP_TRANSFER_MLS) {
+    if (p2) {
+      build_interp_p2(F, C, F);
+    } else if (o.transfer == MSP_TRANSFER_MLS) {
       const double h = mls_unit(C);
       std::string e = build_mls(C, F, h, o.delta, false, F.P_rowptr, F.P_col, F.P_val);
       if (e.empty()) e = build_mls(F, C, h, o.delta, o.restrict_scaling != 0, F.PT_rowptr, F.PT_col, F.PT_val);
@@ -1093,6 +1442,7 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
   for (int l = 0; l < nlevels; ++l) {
     HostLevel& L = out[l];
     if (elastic) {
+      L.nslot = kElasticSlots;
       expand_fields(L);
       if (l + 1 < nlevels) {
         std::vector<int32_t> rp, cl;

@@ -24,7 +24,7 @@ MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
 MSP_COARSE_DIRECT, MSP_COARSE_RAS = 0, 1
-MSP_PDE_POISSON, MSP_PDE_ELASTICITY = 0, 1
+MSP_PDE_POISSON, MSP_PDE_ELASTICITY, MSP_PDE_POISSON_P2 = 0, 1, 2
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
@@ -231,8 +231,9 @@ class Hierarchy:
     levels: sequence of objects with xyz [n,3] f64, tets [m,4] i32,
     dirichlet [n] u8 and owner [n] i32 (or None on the coarsest level).
     pde: "poisson" (one DoF per vertex) or "elasticity" (three displacement
-    fields per vertex, DoF 3v + c; Poisson ratio `poisson`); vectors of a
-    level hold n_dofs(level) entries.
+    fields per vertex, DoF 3v + c; Poisson ratio `poisson`) or "poisson_p2"
+    (quadratic elements: DoFs on the vertices and the edge midpoints, in the
+    order msp.h states); vectors of a level hold n_dofs(level) entries.
     """
 
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
@@ -263,7 +264,8 @@ class Hierarchy:
                             coarse_solver={"direct": MSP_COARSE_DIRECT, "ras": MSP_COARSE_RAS}[coarse],
                             ilu_fill_fine=-1 if ilu is None else int(ilu[0]),
                             ilu_fill_coarse=-1 if ilu is None else int(ilu[1]),
-                            pde={"poisson": MSP_PDE_POISSON, "elasticity": MSP_PDE_ELASTICITY}[pde],
+                            pde={"poisson": MSP_PDE_POISSON, "elasticity": MSP_PDE_ELASTICITY,
+                                 "poisson_p2": MSP_PDE_POISSON_P2}[pde],
                             poisson_ratio=float(poisson),
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))

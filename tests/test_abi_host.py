@@ -262,3 +262,31 @@ def test_noalloc_binding_checks_its_tensors(P):
     cpu = torch.zeros(8, dtype=torch.float64)
     with pytest.raises(ValueError, match="CUDA"):
         m.multidot_noalloc(cpu, cpu, cpu)
+
+
+@pytest.mark.parametrize("name", ["p2cube6_3lvl", "p2cube12_3lvl"])
+def test_host_p2_structures_match_oracle(P, orc, name):
+    """Quadratic elements (DoFs on vertices and edges): the DoF-level pattern,
+    subdomains and the P2 transfers of the library's host set-up against the
+    oracle's, bit for bit (values of P to 1e-13)."""
+    levels, w = workload(name)
+    h = make_hierarchy(levels, w, P, host_only=True)
+    o = make_oracle(levels, w, orc)
+    L = len(levels)
+    for l in range(L):
+        assert h.n_dofs(l) == o.n[l]
+        np.testing.assert_array_equal(h.array(l, "rowptr"), o.get("rowptr", l))
+        np.testing.assert_array_equal(h.array(l, "col"), o.get("col", l))
+    for l in range(L - 1):
+        subs = o.subdomains(l)
+        sp, sd, so = h.array(l, "sub_ptr"), h.array(l, "sub_dofs"), h.array(l, "sub_own")
+        assert sp.size - 1 == len(subs)
+        for p, (d, ow) in enumerate(subs):
+            np.testing.assert_array_equal(sd[sp[p]:sp[p + 1]], d)
+            np.testing.assert_array_equal(so[sp[p]:sp[p + 1]], ow)
+        for a in ("P_rowptr", "P_col", "PT_rowptr", "PT_col"):
+            np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+        np.testing.assert_allclose(h.array(l, "P_val"), o.get("P_val", l), atol=1e-13)
+        np.testing.assert_allclose(h.array(l, "PT_val"), o.get("PT_val", l), atol=1e-13)
+    dirc = o.get("dofdir", L - 1)
+    np.testing.assert_array_equal(h.array(L - 1, "sub_dofs"), np.where(dirc == 0)[0])

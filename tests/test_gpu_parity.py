@@ -48,8 +48,8 @@ class Case:
         self.inst = self.h.assemble(self.mu, stream=torch.cuda.current_stream())
         self.inst.factor()
         self.torch = torch
-        self.n = list(self.o.n)  # DoFs per level (fields x vertices)
-        self.dir0 = np.repeat(self.levels[0].dirichlet, self.o.fields)
+        self.n = list(self.o.n)  # DoFs per level (fields x vertices, or vertices + edges)
+        self.dir0 = self.o.get("dofdir", 0)
 
     def dev(self, x):
         return self.torch.tensor(np.asarray(x, np.float64), device="cuda")
@@ -63,10 +63,11 @@ class Case:
 
 
 # every parity workload with P / P^T, two with the MLS transfers of Section
-# 3.2 (cube20m pairs the subdomains of the two RAS levels), and the
-# multi-field case: linear elasticity, three fields per vertex, field-split P
+# 3.2 (cube20m pairs the subdomains of the two RAS levels), the multi-field
+# case (linear elasticity, three fields per vertex, field-split P) and the
+# quadratic elements (DoFs on vertices and edges, the P2 interpolation)
 CASES = ([(n, "bary") for n in PARITY] + [("cube16_3lvl", "mls"), ("cube20m_3lvl", "mls")] +
-         [("elast12_3lvl", "bary")])
+         [("elast12_3lvl", "bary"), ("p2cube12_3lvl", "bary")])
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-{c[1]}")
@@ -210,6 +211,25 @@ def test_elasticity_fp32_factors(P, orc, torch):
 
 
 # ------------------------------------------------------------- edge cases
+def test_p2_fp32_factors(P, orc, torch):
+    """Quadratic elements with FP32 subdomain factors under the FP64 outer
+    loop: the FP64 oracle's solution at rtol 1e-10, at most 3 more iterations."""
+    levels, w = workload("p2cube12_3lvl")
+    mu = syn.mu_draw(6)
+    o = make_oracle(levels, w, orc)
+    o.assemble(mu)
+    o.factor()
+    xo, so = o.fgmres(rtol=1e-10, restart=w["restart"])
+    h = make_hierarchy(levels, w, P, precision="f32")
+    assert h.n_dofs(0) == o.n[0] == (2 * levels[0].n + 1) ** 3
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    x = torch.zeros(o.n[0], dtype=torch.float64, device="cuda")
+    st = inst.solve(x, rtol=1e-10)
+    assert st["status"] == 0 and st["iterations"] <= so["iters"] + 3
+    assert close(x.cpu().numpy(), xo, 1e-7)
+
+
 def test_single_level_is_a_direct_solve(P, orc, torch):
     lv = syn.cube_level(6, 9)
     w = dict(delta=1, nu=2, coef="cosexp", scale=1.0, load="one", restart=30)

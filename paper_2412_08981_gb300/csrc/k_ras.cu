@@ -42,6 +42,7 @@ namespace {
 // Levels whose tile band needs more ring slots than that leaves per CTA use
 // the wide form (one CTA of 16 consumers per SM) in every precision.
 template <typename T, bool Wide> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
+template <> struct RasCfg<double, false> { static constexpr int NCW = 8, CTAS = 2; };
 template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 2; };
 template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 3; };
 constexpr long kWaitLimit = 1L << 20;

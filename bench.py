@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--serve", type=int, default=400,
                     help="requests served from the start of the three-hierarchy trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16"],
+                    help="subdomain factors of the served solves (FP64 outer loop)")
     ap.add_argument("--serve-trace", action="store_true",
                     help="also serve the full trace: 2000 requests at 200/s over 32^3, 64^3 and 128^3 hierarchies "
                          "(probabilities 0.5/0.35/0.15), 120 GB budget")
@@ -678,7 +680,7 @@ def run_msp(args):
         And the plain FP64 path on the same mix: the first `fp64_sample`
         requests solved one after another with FP64 factors (no concurrency),
         whose solutions are compared with the served ones."""
-        hs = serve_hierarchies("f32")
+        hs = serve_hierarchies(args.serve_precision)
         hs_n.clear()
         hs_n.extend(h.n_dofs(0) for h in hs)
         srv = P.Server(slots_per_hierarchy=4, budget_bytes=120 << 30)
@@ -698,7 +700,7 @@ def run_msp(args):
         out = {"hierarchies": {nm: int((which == k).sum()) for k, nm in enumerate(SERVE_NAMES)},
                "dofs": {nm: hs_n[k] for k, nm in enumerate(SERVE_NAMES)},
                "requests": nreq, "of_trace": 2000, "arrival_rate_per_s": rate,
-               "factor_precision": "f32 (FP64 outer loop, SpMV, transfers, coarsest level)",
+               "factor_precision": args.serve_precision + " (FP64 outer loop, SpMV, transfers, coarsest level)",
                "slots_per_hierarchy": 4, "mem_budget_bytes": 120 << 30,
                "value": thr, "unit": UNIT,
                "latency_ms": {"p50": float(np.percentile(tr["lat"], 50)),

@@ -36,8 +36,8 @@ Parity status per function (what pins it, tests/test_oracle_pins.py):
 Iteration counts of the preconditioned solver: parity unpinned (the paper
 reports counts only for other PDEs and meshes).
 """
-from .oracle import (Oracle, build, lib, tet_stiffness, tet_elasticity, tet_p2, lame, lu_factor, lu_solve,
+from .oracle import (Oracle, build, lib, tet_stiffness, tet_elasticity, tet_p2, tet_p2p1, lame, lu_factor, lu_solve,
                      build_interp, build_mls, mesh_h, ilu_factor)
 
-__all__ = ["Oracle", "build", "lib", "tet_stiffness", "tet_elasticity", "tet_p2", "lame", "lu_factor", "lu_solve",
+__all__ = ["Oracle", "build", "lib", "tet_stiffness", "tet_elasticity", "tet_p2", "tet_p2p1", "lame", "lu_factor", "lu_solve",
            "build_interp", "build_mls", "mesh_h", "ilu_factor"]

@@ -73,6 +73,8 @@ struct Level {
   std::vector<int> tdof;
   std::vector<double> dofx;
   std::vector<int> vowner;
+  int nloc = 10;                // local DoFs per tet: 10 (P2), 14 (P2 u and P1 p)
+  std::vector<unsigned char> pdof;  // P2-P1 only: 1 for the DoFs of the P1 field p
   std::vector<double> xyz;
   std::vector<int> tets;
   std::vector<unsigned char> vdir;  // per vertex
@@ -91,6 +93,8 @@ struct Oracle {
   std::vector<Level> lv;
   int fields = 1;                     // DoFs per vertex: 1 (scalar) or 3 (elasticity)
   int p2 = 0;                         // 1: quadratic elements (DoFs on vertices and edges)
+  int twofield = 0;                   // 1: the coupled system of a P2 field u and a P1 field p
+  double sigma = 1.0;                 // its coupling coefficient
   double lame_l = 0.0, lame_m = 0.0;  // Lame parameters of the unit-modulus material
   int delta = 1, nu_pre = 2, nu_post = 2;
   int coef_kind = 0;  // 0: k = 1; 1: exp(s * sum_j mu_j * 0.5 * cos(pi a_j . x))
@@ -236,6 +240,48 @@ void p2_element(const double g[4][3], double vol, double* K10, double* m1) {
   }
 }
 
+// The coupled two-field element (u in P2, p in P1; unit k):
+//   K_uu = int grad phi_i . grad phi_j + sigma int phi_i phi_j,
+//   K_up = -sigma int phi_i lambda_b,
+//   K_pp = int grad lambda_a . grad lambda_b + sigma int lambda_a lambda_b,
+// local DoFs 0..9 the P2 ones (as p2_element), 10..13 the P1 ones; m1 = the
+// integrals of the 14 basis functions.  Integrals by the collapsed (Duffy)
+// map of the reference tet from the unit cube with 4 Gauss-Legendre points
+// per direction, exact for these integrands (degree <= 4).
+void coupled_element(const double g[4][3], double vol, double sigma, double* K14, double* m1) {
+  const double gx[4] = {0.5 - 0.5 * 0.8611363115940526, 0.5 - 0.5 * 0.3399810435848563,
+                        0.5 + 0.5 * 0.3399810435848563, 0.5 + 0.5 * 0.8611363115940526};
+  const double gw[4] = {0.5 * 0.3478548451374538, 0.5 * 0.6521451548625461, 0.5 * 0.6521451548625461,
+                        0.5 * 0.3478548451374538};
+  for (int k = 0; k < 196; ++k) K14[k] = 0.0;
+  for (int i = 0; i < 14; ++i) m1[i] = 0.0;
+  for (int ia = 0; ia < 4; ++ia)
+    for (int ib = 0; ib < 4; ++ib)
+      for (int ic = 0; ic < 4; ++ic) {
+        const double a = gx[ia], b = gx[ib], c = gx[ic];
+        const double xi = a, eta = b * (1.0 - a), zeta = c * (1.0 - a) * (1.0 - b);
+        const double w = 6.0 * vol * gw[ia] * gw[ib] * gw[ic] * (1.0 - a) * (1.0 - a) * (1.0 - b);
+        const double lam[4] = {1.0 - xi - eta - zeta, xi, eta, zeta};
+        double val[14], gr[14][3];
+        for (int i = 0; i < 10; ++i) {
+          val[i] = p2_phi(i, lam);
+          p2_grad(i, lam, g, gr[i]);
+        }
+        for (int q = 0; q < 4; ++q) {
+          val[10 + q] = lam[q];
+          for (int d = 0; d < 3; ++d) gr[10 + q][d] = g[q][d];
+        }
+        for (int i = 0; i < 14; ++i) {
+          m1[i] += w * val[i];
+          for (int j = 0; j < 14; ++j) {
+            const bool same = (i < 10) == (j < 10);
+            const double v = same ? dot3(gr[i], gr[j]) + sigma * val[i] * val[j] : -sigma * val[i] * val[j];
+            K14[i * 14 + j] += w * v;
+          }
+        }
+      }
+}
+
 // The P2 DoFs of a level.  Edges: the distinct vertex pairs (a, b), a < b, of
 // the tets, ascending.  Numbering: vertex 0, then the edges (0, b) in
 // ascending b, then vertex 1 and its edges (1, b), b > 1, and so on (a DoF
@@ -245,7 +291,11 @@ void p2_element(const double g[4][3], double vol, double* K10, double* m1) {
 // vertices are Dirichlet.  Owner: a vertex's own; an edge takes the owner of
 // its lower vertex if that id owns a non-Dirichlet vertex, else the owner of
 // its upper vertex.  Returns false if an edge gets no owner.
-bool p2_number(Level& L, const int* vowner) {
+// With the coupled system (twofield), each vertex also carries the DoF of the
+// P1 field p, right after its P2 (u) DoF: vertex 0's u, vertex 0's p, the
+// edges (0, b), vertex 1's u, ...; local DoFs 10..13 of a tet are the p DoFs
+// of its vertices; a p DoF is Dirichlet and owned as its vertex.
+bool p2_number(Level& L, const int* vowner, bool twofield = false) {
   std::vector<std::pair<int, int>> E;
   for (int e = 0; e < L.m; ++e)
     for (int k = 0; k < 6; ++k) {
@@ -260,28 +310,39 @@ bool p2_number(Level& L, const int* vowner) {
     L.edges[2 * k] = E[k].first;
     L.edges[2 * k + 1] = E[k].second;
   }
-  std::vector<int> vdof(L.nv), edof(ne);
+  std::vector<int> vdof(L.nv), pdof(L.nv, -1), edof(ne);
   int cnt = 0, k = 0;
   for (int v = 0; v < L.nv; ++v) {
     vdof[v] = cnt++;
+    if (twofield) pdof[v] = cnt++;
     while (k < ne && E[k].first == v) edof[k++] = cnt++;
   }
   L.n = cnt;
-  L.tdof.assign(10 * (size_t)L.m, 0);
+  const int NL = twofield ? 14 : 10;
+  L.nloc = NL;
+  L.tdof.assign(NL * (size_t)L.m, 0);
   for (int e = 0; e < L.m; ++e) {
     const int* t = &L.tets[4 * e];
-    for (int a = 0; a < 4; ++a) L.tdof[10 * e + a] = vdof[t[a]];
+    for (int a = 0; a < 4; ++a) L.tdof[NL * e + a] = vdof[t[a]];
     for (int q = 0; q < 6; ++q) {
       std::pair<int, int> key{std::min(t[kP2Edge[q][0]], t[kP2Edge[q][1]]),
                               std::max(t[kP2Edge[q][0]], t[kP2Edge[q][1]])};
-      L.tdof[10 * e + 4 + q] = edof[std::lower_bound(E.begin(), E.end(), key) - E.begin()];
+      L.tdof[NL * e + 4 + q] = edof[std::lower_bound(E.begin(), E.end(), key) - E.begin()];
     }
+    if (twofield)
+      for (int a = 0; a < 4; ++a) L.tdof[NL * e + 10 + a] = pdof[t[a]];
   }
   L.dofx.assign(3 * (size_t)L.n, 0.0);
   L.dir.assign(L.n, 0);
+  L.pdof.assign(L.n, 0);
   for (int v = 0; v < L.nv; ++v) {
     for (int d = 0; d < 3; ++d) L.dofx[3 * vdof[v] + d] = L.xyz[3 * v + d];
     L.dir[vdof[v]] = L.vdir[v];
+    if (twofield) {
+      for (int d = 0; d < 3; ++d) L.dofx[3 * pdof[v] + d] = L.xyz[3 * v + d];
+      L.dir[pdof[v]] = L.vdir[v];
+      L.pdof[pdof[v]] = 1;
+    }
   }
   for (int q = 0; q < ne; ++q)
     for (int d = 0; d < 3; ++d)
@@ -312,7 +373,10 @@ bool p2_number(Level& L, const int* vowner) {
     for (int v = 0; v < L.nv; ++v)
       if (!L.vdir[v]) ids.insert(vowner[v]);
     L.owner.assign(L.n, -1);
-    for (int v = 0; v < L.nv; ++v) L.owner[vdof[v]] = vowner[v];
+    for (int v = 0; v < L.nv; ++v) {
+      L.owner[vdof[v]] = vowner[v];
+      if (twofield) L.owner[pdof[v]] = vowner[v];
+    }
     for (int q = 0; q < ne; ++q) {
       const int oa = vowner[E[q].first], ob = vowner[E[q].second];
       L.owner[edof[q]] = ids.count(oa) ? oa : (ids.count(ob) ? ob : -1);
@@ -324,10 +388,11 @@ bool p2_number(Level& L, const int* vowner) {
 
 // Row i of the P2 pattern: the DoFs of the tets that hold DoF i, sorted.
 void build_pattern_p2(Level& L) {
+  const int NL = L.nloc;
   std::vector<std::set<int>> nb(L.n);
   for (int e = 0; e < L.m; ++e)
-    for (int i = 0; i < 10; ++i)
-      for (int j = 0; j < 10; ++j) nb[L.tdof[10 * e + i]].insert(L.tdof[10 * e + j]);
+    for (int i = 0; i < NL; ++i)
+      for (int j = 0; j < NL; ++j) nb[L.tdof[NL * e + i]].insert(L.tdof[NL * e + j]);
   L.A.rowptr.assign(L.n + 1, 0);
   L.A.col.clear();
   for (int i = 0; i < L.n; ++i) {
@@ -384,15 +449,17 @@ int assemble_level(const Oracle& o, Level& L) {
     for (int d = 0; d < 3; ++d) xc[d] = (x[0][d] + x[1][d] + x[2][d] + x[3][d]) / 4.0;
     double k = coefficient(o, xc);
     if (o.p2) {  // quadratic elements: DoFs at the vertices and edge midpoints
-      double K10[100], m1[10];
-      p2_element(g, vol, K10, m1);
-      const int* td = &L.tdof[10 * e];
-      for (int i = 0; i < 10; ++i) {
-        for (int j = 0; j < 10; ++j) {
+      const int NL = L.nloc;
+      double Ke[196], m1[14];
+      if (o.twofield) coupled_element(g, vol, o.sigma, Ke, m1);
+      else p2_element(g, vol, Ke, m1);
+      const int* td = &L.tdof[NL * e];
+      for (int i = 0; i < NL; ++i) {
+        for (int j = 0; j < NL; ++j) {
           long nz = csr_find(L.A, td[i], td[j]);
-          L.A.val[nz] += k * K10[i * 10 + j];
+          L.A.val[nz] += k * Ke[i * NL + j];
         }
-        L.b[td[i]] += m1[i];  // f = 1: b_i = int phi_i
+        L.b[td[i]] += m1[i];  // f = 1 (for every field): b_i = int phi_i
       }
       continue;
     }
@@ -495,12 +562,16 @@ void build_subdomains_p2(const Oracle& o, Level& L) {
       in.swap(nxt);
     }
     std::vector<unsigned char> take(L.n, 0);
+    const int NL = L.nloc;
     for (int e = 0; e < L.m; ++e) {
       const int* t = &L.tets[4 * e];
       for (int a = 0; a < 4; ++a)
-        if (in[t[a]]) take[L.tdof[10 * e + a]] = 1;
+        if (in[t[a]]) {
+          take[L.tdof[NL * e + a]] = 1;
+          if (NL == 14) take[L.tdof[NL * e + 10 + a]] = 1;
+        }
       for (int q = 0; q < 6; ++q)
-        if (in[t[kP2Edge[q][0]]] && in[t[kP2Edge[q][1]]]) take[L.tdof[10 * e + 4 + q]] = 1;
+        if (in[t[kP2Edge[q][0]]] && in[t[kP2Edge[q][1]]]) take[L.tdof[NL * e + 4 + q]] = 1;
     }
     Subdomain S;
     for (int i = 0; i < L.n; ++i)
@@ -841,6 +912,9 @@ void transpose(const Csr& P, int ncols, Csr& T) {
 // as a P1 node is (build_interp's rule, run on the DoF points); its row holds
 // the ten coarse P2 basis functions of that tet evaluated there, on the
 // tet's non-Dirichlet coarse DoFs, columns ascending (zero weights kept).
+// With the coupled system the interpolation is split by field (Section 2.1,
+// I = sum_f R_f^T I_f R~_f): rows of the P2 field u as above, on the coarse u
+// DoFs; rows of the P1 field p the barycentric weights on the coarse p DoFs.
 void build_interp_p2(const Level& C, const Level& F, Csr& P) {
   // the containing tet and barycentric coordinates of every fine DoF point:
   // build_interp on the DoF points with every coarse vertex kept returns the
@@ -869,10 +943,19 @@ void build_interp_p2(const Level& C, const Level& F, Csr& P) {
         for (int q = 0; q < 4; ++q)
           if (loc.col[loc.rowptr[f] + q] == t[a]) lam[a] = loc.val[loc.rowptr[f] + q];
       std::vector<std::pair<int, double>> row;
-      for (int i = 0; i < 10; ++i) {
-        const int c = C.tdof[10 * e + i];
-        if (C.dir[c]) continue;
-        row.push_back({c, p2_phi(i, lam)});
+      const int NL = C.nloc;
+      if (!F.pdof.empty() && F.pdof[f]) {  // the P1 field: barycentric weights on the coarse p DoFs
+        for (int a = 0; a < 4; ++a) {
+          const int c = C.tdof[NL * e + 10 + a];
+          if (C.dir[c]) continue;
+          row.push_back({c, lam[a]});
+        }
+      } else {
+        for (int i = 0; i < 10; ++i) {
+          const int c = C.tdof[NL * e + i];
+          if (C.dir[c]) continue;
+          row.push_back({c, p2_phi(i, lam)});
+        }
       }
       std::sort(row.begin(), row.end());
       for (auto& pr : row) {
@@ -1201,16 +1284,21 @@ typedef struct {
 // pde: 0 scalar P1 (one field), 1 linear elasticity (three fields, Poisson
 // ratio `poisson` in (0, 0.5), unit Young's modulus scaled by k(x;mu)), 2
 // scalar P2 (DoFs on vertices and edges; barycentric transfers, f = 1, and
-// delta >= 1 where a level is partitioned).
+// delta >= 1 where a level is partitioned), 3 the coupled system of a P2
+// field u and a P1 field p, -div(k grad u) + sigma k (u - p) = 1,
+// -div(k grad p) + sigma k (p - u) = 1, sigma = `poisson` (> 0).
 void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu_post,
                  int coef_kind, const int* wave, double coef_scale, int load_kind, int transfer,
                  int restrict_scaling, int coarse_ras, int ilu_fine, int ilu_coarse, int pde,
                  double poisson) {
-  if (nlevels < 1 || transfer < 0 || transfer > 1 || pde < 0 || pde > 2) return nullptr;
+  if (nlevels < 1 || transfer < 0 || transfer > 1 || pde < 0 || pde > 3) return nullptr;
   if (pde == 1 && (transfer != 0 || !(poisson > 0.0 && poisson < 0.5))) return nullptr;
-  if (pde == 2 && (transfer != 0 || load_kind != 0 || delta < 1)) return nullptr;
+  if (pde >= 2 && (transfer != 0 || load_kind != 0 || delta < 1)) return nullptr;
+  if (pde == 3 && !(poisson > 0.0)) return nullptr;
   Oracle* o = new Oracle();
-  o->p2 = pde == 2 ? 1 : 0;
+  o->p2 = pde >= 2 ? 1 : 0;
+  o->twofield = pde == 3 ? 1 : 0;
+  if (pde == 3) o->sigma = poisson;  // the coupling coefficient of the two-field system
   if (pde == 1) {
     o->fields = 3;
     o->lame_l = poisson / ((1.0 + poisson) * (1.0 - 2.0 * poisson));
@@ -1240,7 +1328,7 @@ void* orc_create(const orc_level* lv, int nlevels, int delta, int nu_pre, int nu
     L.dir.resize(L.n);
     for (int i = 0; i < L.n; ++i) L.dir[i] = L.vdir[i / NF];
     if (o->p2) {
-      if (!p2_number(L, lv[l].owner)) {
+      if (!p2_number(L, lv[l].owner, o->twofield != 0)) {
         delete o;
         return nullptr;
       }
@@ -1432,6 +1520,7 @@ long orc_get(void* h, const char* what, int level, int sub, const void** ptr) {
   if (w == "PT_col") return ret(L.PT.col);
   if (w == "PT_val") return ret(L.PT.val);
   if (w == "dofdir") return ret(L.dir);
+  if (w == "pdof") return ret(L.pdof);
   if (w == "dofx") return ret(L.dofx);
   if (w == "n_subs") {
     *ptr = nullptr;
@@ -1460,6 +1549,17 @@ int orc_ndofs(void* h, int level) {
 // ---- standalone pieces used by the pins ----
 // The P2 element of a tet (local DoFs: vertices 0..3, edges 01 02 03 12 13 23):
 // K100 row-major = k int grad phi_i . grad phi_j, m10 = int phi_i; returns |T|.
+// The coupled two-field element (P2 u, P1 p): K196 row-major 14 x 14 times k,
+// m14 = int of the 14 basis functions; returns |T|.
+double orc_tet_p2p1(const double* x4, double k, double sigma, double* K196, double* m14) {
+  double g[4][3];
+  double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);
+  double vol = std::fabs(det) / 6.0;
+  coupled_element(g, vol, sigma, K196, m14);
+  for (int i = 0; i < 196; ++i) K196[i] *= k;
+  return vol;
+}
+
 double orc_tet_p2(const double* x4, double k, double* K100, double* m10) {
   double g[4][3];
   double det = tet_gradients(&x4[0], &x4[3], &x4[6], &x4[9], g);

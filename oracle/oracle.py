@@ -62,6 +62,8 @@ def lib():
             L.orc_tet_elasticity.argtypes = [vp, dp, dp, dp, vp]
             L.orc_tet_p2.restype = dp
             L.orc_tet_p2.argtypes = [vp, dp, vp, vp]
+            L.orc_tet_p2p1.restype = dp
+            L.orc_tet_p2p1.argtypes = [vp, dp, dp, vp, vp]
             L.orc_ndofs.restype = ip
             L.orc_ndofs.argtypes = [vp, ip]
             L.orc_lu_factor.argtypes = [ip, vp]
@@ -94,7 +96,7 @@ def _p(a):
 _COEF = {"const": 0, "cosexp": 1}
 _LOAD = {"one": 0, "sines": 1}
 _TRANSFER = {"bary": 0, "mls": 1}
-_PDE = {"poisson": 0, "elasticity": 1, "poisson_p2": 2}
+_PDE = {"poisson": 0, "elasticity": 1, "poisson_p2": 2, "p2p1": 3}
 
 
 def lame(poisson):
@@ -160,7 +162,7 @@ class Oracle:
         if dtype is None:
             dtype = {"val": np.float64, "b": np.float64, "P_val": np.float64,
                      "PT_val": np.float64, "sub_lu": np.float64, "sub_ilu_val": np.float64,
-                     "sub_own": np.uint8, "dofdir": np.uint8, "dofx": np.float64}.get(what, np.int32)
+                     "sub_own": np.uint8, "dofdir": np.uint8, "pdof": np.uint8, "dofx": np.float64}.get(what, np.int32)
         if cnt == 0:
             return np.zeros(0, dtype)
         buf = (C.c_char * (cnt * np.dtype(dtype).itemsize)).from_address(ptr.value)
@@ -261,6 +263,18 @@ def tet_p2(x4, k=1.0):
     K = np.zeros((10, 10))
     m = np.zeros(10)
     vol = lib().orc_tet_p2(_p(x4), float(k), _p(K), _p(m))
+    return K, m, vol
+
+
+def tet_p2p1(x4, k=1.0, sigma=1.0):
+    """The coupled two-field element (u in P2: local DoFs 0..9 as tet_p2; p in
+    P1: local DoFs 10..13): the 14 x 14 matrix k [[Ku + s Muu, -s Mup], [-s Mpu,
+    Kp + s Mpp]] with s = sigma, the integrals of the 14 basis functions and
+    the volume."""
+    x4 = np.ascontiguousarray(x4, np.float64).reshape(4, 3)
+    K = np.zeros((14, 14))
+    m = np.zeros(14)
+    vol = lib().orc_tet_p2p1(_p(x4), float(k), float(sigma), _p(K), _p(m))
     return K, m, vol
 
 

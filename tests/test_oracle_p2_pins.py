@@ -194,3 +194,122 @@ def test_p2_solves(orc):
     xd = spla.spsolve(A, o.get("b", 0))
     assert st["status"] == 0 and st["iters"] <= 8
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+# ---------------------------------------------------------------------------
+# The coupled two-field system: a P2 field u and a P1 field p (DoFs of u on
+# the vertices and edges, of p on the vertices), -div(k grad u) + s k (u - p)
+# = 1, -div(k grad p) + s k (p - u) = 1; the transfers split by field (the
+# P2 interpolation for u, the P1 one for p).
+
+def test_p2p1_element_against_exact_integration(orc):
+    sp = pytest.importorskip("sympy")
+    X = [sp.Matrix([0, 0, 0]), sp.Matrix([sp.Rational(5, 4), sp.Rational(1, 3), 0]),
+         sp.Matrix([sp.Rational(1, 5), sp.Rational(4, 3), sp.Rational(1, 6)]),
+         sp.Matrix([sp.Rational(-1, 3), sp.Rational(1, 4), sp.Rational(7, 5)])]
+    x, y, z = sp.symbols("x y z")
+    M = sp.Matrix([[1, *X[a]] for a in range(4)])
+    coef = M.inv()
+    lam = [coef[0, a] + coef[1, a] * x + coef[2, a] * y + coef[3, a] * z for a in range(4)]
+    phi = [lam[a] * (2 * lam[a] - 1) for a in range(4)] + [4 * lam[a] * lam[b] for a, b in EDGES] + lam
+    s_, t_, u_ = sp.symbols("s t u")
+    J = sp.Matrix.hstack(X[1] - X[0], X[2] - X[0], X[3] - X[0])
+    detJ = abs(J.det())
+    mp = X[0] + J * sp.Matrix([s_, t_, u_])
+
+    def integrate(expr):
+        e = sp.expand(expr.subs({x: mp[0], y: mp[1], z: mp[2]}))
+        return detJ * sp.integrate(e, (u_, 0, 1 - s_ - t_), (t_, 0, 1 - s_), (s_, 0, 1))
+
+    sigma, k = sp.Rational(7, 10), 1.3
+    grads = [[sp.diff(f, v) for v in (x, y, z)] for f in phi]
+    K_exact = np.zeros((14, 14))
+    for i in range(14):
+        for j in range(i, 14):
+            mass = integrate(phi[i] * phi[j])
+            if (i < 10) == (j < 10):
+                val = integrate(sum(grads[i][d] * grads[j][d] for d in range(3))) + sigma * mass
+            else:
+                val = -sigma * mass
+            K_exact[i, j] = K_exact[j, i] = float(val)
+    m_exact = np.array([float(integrate(f)) for f in phi])
+    x4 = np.array([[float(c) for c in p] for p in X])
+    K, m, vol = orc.tet_p2p1(x4, k=k, sigma=0.7)
+    assert np.max(np.abs(K - k * K_exact)) <= 1e-13 * np.max(np.abs(K))
+    assert np.max(np.abs(m - m_exact)) <= 1e-15
+    # positive semi-definite with one zero mode: u = p = constant (no gradient, no coupling)
+    ev = np.linalg.eigvalsh(K)
+    assert ev[0] >= -1e-14 * ev[-1] and abs(ev[0]) <= 1e-14 * ev[-1] and ev[1] > 1e-3 * ev[-1]
+    assert np.max(np.abs(K @ np.ones(14))) <= 1e-14 * ev[-1]
+
+
+def _p2p1(orc, name="p2p1cube6_3lvl", **kw):
+    levels, w = workload(name)
+    return levels, w, make_oracle(levels, w, orc, **kw)
+
+
+def test_p2p1_numbering_and_equal_fields(orc):
+    """DoFs: every vertex's u, then its p, then its edges' u; u = p = an affine
+    field makes the coupling vanish, so rows away from the boundary of J x are
+    zero (k = 1)."""
+    levels, w, o = _p2p1(orc, coef="const")
+    lv = levels[0]
+    E = _edges_of(lv)
+    assert o.n[0] == 2 * lv.n_nodes + len(E)
+    pd = o.get("pdof", 0)
+    X = o.get("dofx", 0).reshape(-1, 3)
+    order = sorted([(v, -2) for v in range(lv.n_nodes)] + [(v, -1) for v in range(lv.n_nodes)] +
+                   [(int(a), int(b)) for a, b in E])
+    np.testing.assert_array_equal(pd, np.array([1 if b == -1 else 0 for _, b in order], np.uint8))
+    o.assemble(np.zeros(8))
+    A = o.csr(0).tocsr()
+    dirv = o.get("dofdir", 0)
+    aff = 0.3 + X[:, 0] - 2 * X[:, 1] + 0.7 * X[:, 2]
+    Ax = A @ aff
+    away = np.array([not dirv[i] and not np.any(dirv[A.indices[A.indptr[i]:A.indptr[i + 1]]])
+                     for i in range(A.shape[0])])
+    assert away.sum() > 50
+    assert np.max(np.abs(Ax[away])) <= 1e-13 * abs(A).max()
+    assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+
+
+def test_p2p1_transfer_splits_by_field(orc):
+    levels, w = workload("p2p1cube6_3lvl")
+    coarse = levels[1]
+    levels = [levels[0], syn.Level(n=coarse.n, xyz=coarse.xyz, tets=coarse.tets,
+                                   dirichlet=np.zeros_like(coarse.dirichlet), owner=coarse.owner,
+                                   lattice=coarse.lattice), levels[2]]
+    o = make_oracle(levels, w, orc)
+    P = o.csr(0, "P").tocsr()
+    Xf, Xc = o.get("dofx", 0).reshape(-1, 3), o.get("dofx", 1).reshape(-1, 3)
+    pf, pc = o.get("pdof", 0).astype(bool), o.get("pdof", 1).astype(bool)
+    dirf = o.get("dofdir", 0)
+    # rows of u only reference coarse u DoFs, rows of p only coarse p DoFs
+    for f in range(P.shape[0]):
+        cols = P.indices[P.indptr[f]:P.indptr[f + 1]]
+        assert np.all(pc[cols] == pf[f])
+    # u reproduces quadratics (P2), p reproduces affine fields (P1) exactly
+    q = 1 + Xc[:, 0] - Xc[:, 1] * Xc[:, 2] + 2 * Xc[:, 2] ** 2
+    a = 0.5 - Xc[:, 0] + 3 * Xc[:, 1] + Xc[:, 2]
+    xc = np.where(pc, a, q)
+    y = P @ xc
+    qf = 1 + Xf[:, 0] - Xf[:, 1] * Xf[:, 2] + 2 * Xf[:, 2] ** 2
+    af = 0.5 - Xf[:, 0] + 3 * Xf[:, 1] + Xf[:, 2]
+    want = np.where(pf, af, qf)
+    fine = dirf == 0
+    assert np.max(np.abs(y[fine] - want[fine])) <= 1e-12
+
+
+def test_p2p1_subdomains_and_solve(orc):
+    levels, w, o = _p2p1(orc)
+    dirv = o.get("dofdir", 0)
+    owned = np.zeros(o.n[0], int)
+    for dofs, own in o.subdomains(0):
+        owned[dofs[own == 1]] += 1
+    assert np.all(owned[dirv == 0] == 1) and np.all(owned[dirv == 1] == 0)
+    o.assemble(syn.mu_draw(4))
+    o.factor()
+    x, st = o.fgmres(rtol=1e-11)
+    xd = spla.spsolve(o.csr(0).tocsc(), o.get("b", 0))
+    assert st["status"] == 0 and st["iters"] <= 8
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)

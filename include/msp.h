@@ -116,8 +116,21 @@ typedef enum msp_load { MSP_F_ONE = 0, MSP_F_SINES = 1 } msp_load;
  *       DoFs and the edge DoFs with both ends inside.  The transfers are the
  *       P2 interpolation (the coarse P2 basis evaluated at the fine DoF
  *       points; restriction by its transpose).  Loads: MSP_F_ONE only
- *       (b_i = integral of phi_i). */
-typedef enum msp_pde { MSP_PDE_POISSON = 0, MSP_PDE_ELASTICITY = 1, MSP_PDE_POISSON_P2 = 2 } msp_pde;
+ *       (b_i = integral of phi_i).
+ *   MSP_PDE_P2P1: two fields of different element order on one mesh, a P2
+ *       field u (vertices and edges) and a P1 field p (vertices), coupled:
+ *       -div(k grad u) + sigma k (u - p) = 1, -div(k grad p) + sigma k (p - u) = 1,
+ *       sigma = msp_options.coupling > 0 (symmetric positive definite with the
+ *       Dirichlet rows); N = (2,1,0,0).  DoF order: vertex 0's u, vertex 0's p,
+ *       the u DoFs of its edges (0, b), b > 0 ascending, vertex 1's u, its p,
+ *       ...; a p DoF is Dirichlet and belongs to a partition as its vertex;
+ *       subdomains hold both fields of their vertices.  The transfers are split
+ *       by field (Section 2.1, I = sum_f R_f^T I_f R~_f): the P2 interpolation
+ *       on the u DoFs, the P1 barycentric one on the p DoFs.  Loads: MSP_F_ONE
+ *       (f = 1 for both fields). */
+typedef enum msp_pde {
+  MSP_PDE_POISSON = 0, MSP_PDE_ELASTICITY = 1, MSP_PDE_POISSON_P2 = 2, MSP_PDE_P2P1 = 3
+} msp_pde;
 
 /* One mesh level (Section 2.1: the mesh perspective M = (K, N); the DoFs
  * per vertex follow msp_options.pde).  All arrays are host memory, copied. */
@@ -179,6 +192,7 @@ typedef struct msp_options {
   int32_t pde;                /* msp_pde (default MSP_PDE_POISSON) */
   double poisson_ratio;       /* MSP_PDE_ELASTICITY: in (0, 0.5), default 0.3; the transfers
                                  must then be MSP_TRANSFER_BARY */
+  double coupling;            /* MSP_PDE_P2P1: the coupling coefficient sigma > 0, default 1 */
   int32_t host_only;          /* 1: build the host-side structures only (no device use);
                                  only msp_hierarchy_copy / info work on such a handle */
   size_t mem_budget_bytes;    /* 0 = unlimited; instances beyond it get MSP_ERR_OOM */

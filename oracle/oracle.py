@@ -120,7 +120,7 @@ class Oracle:
 
     def __init__(self, levels, delta=1, nu_pre=2, nu_post=2, coef="const", wave=None,
                  scale=1.0, load="one", transfer="bary", restrict_scaling=True, coarse="direct",
-                 ilu=None, pde="poisson", poisson=0.3):
+                 ilu=None, pde="poisson", poisson=0.3, coupling=1.0):
         L = lib()
         self._keep = []
         arr = (_Level * len(levels))()
@@ -138,7 +138,7 @@ class Oracle:
                               _TRANSFER[transfer], 1 if restrict_scaling else 0,
                               {"direct": 0, "ras": 1}[coarse],
                               -1 if ilu is None else int(ilu[0]), -1 if ilu is None else int(ilu[1]),
-                              _PDE[pde], float(poisson))
+                              _PDE[pde], float(coupling if pde == "p2p1" else poisson))
         if not self.h:
             raise ValueError("oracle: invalid hierarchy")
         self.levels = levels

@@ -37,9 +37,49 @@ constexpr double kPi = 3.14159265358979323846;
 //                       = |T| ((1 + [a == b]) / 5 - 1/4);
 //   edge ab, edge cd  : 16 (G_bd M_ac + G_bc M_ad + G_ad M_bc + G_ac M_bd),
 //                       M_ij = int l_i l_j.
-__device__ __forceinline__ int p2_local_slot(int r, int c) {
-  if (r > c) { const int t = r; r = c; c = t; }
-  return 10 * r - r * (r - 1) / 2 + (c - r);
+
+// The P2-P1 pair (Kind 3, coupling sigma passed as `lam`): S[e*105 + slot]
+// over the 14 local DoFs (P2 0..9 as above, P1 10..13 at the vertices) of
+//   [[K2 + sigma M22, -sigma M21], [-sigma M12, K1 + sigma M11]]
+// (unit k), the mass blocks in closed form from the moments
+// int l0^a l1^b l2^c l3^d = 6 |T| a! b! c! d! / (a + b + c + d + 3)!, the P2
+// basis written in the l: vertex a, 2 l_a^2 - l_a; edge ab, 4 l_a l_b.
+__device__ __forceinline__ double lam_moment(const int ex[4], double vv) {
+  constexpr double fact[8] = {1, 1, 2, 6, 24, 120, 720, 5040};
+  const int s = ex[0] + ex[1] + ex[2] + ex[3];
+  return 6.0 * vv * fact[ex[0]] * fact[ex[1]] * fact[ex[2]] * fact[ex[3]] / fact[s + 3];
+}
+
+// int of the product of basis functions i and j (P2: 0..9; P1: 10..13) as a
+// sum of monomials: basis i = sum_t c_t prod l^e_t, at most two terms each
+__device__ inline double p2p1_mass(int i, int j, double vv) {
+  constexpr int ea[6] = {0, 0, 0, 1, 1, 2}, eb[6] = {1, 2, 3, 2, 3, 3};
+  double ci[2], cj[2];
+  int ei[2][4] = {{0}}, ej[2][4] = {{0}};
+  int ni = 0, nj = 0;
+  auto expand = [&](int k, double* c, int (*e)[4], int& n) {
+    if (k < 4) {  // 2 l_k^2 - l_k
+      c[0] = 2.0; e[0][k] = 2;
+      c[1] = -1.0; e[1][k] = 1;
+      n = 2;
+    } else if (k < 10) {  // 4 l_a l_b
+      c[0] = 4.0; e[0][ea[k - 4]] = 1; e[0][eb[k - 4]] = 1;
+      n = 1;
+    } else {  // l_a
+      c[0] = 1.0; e[0][k - 10] = 1;
+      n = 1;
+    }
+  };
+  expand(i, ci, ei, ni);
+  expand(j, cj, ej, nj);
+  double s = 0.0;
+  for (int a = 0; a < ni; ++a)
+    for (int b = 0; b < nj; ++b) {
+      int ex[4];
+      for (int d = 0; d < 4; ++d) ex[d] = ei[a][d] + ej[b][d];
+      s += ci[a] * cj[b] * lam_moment(ex, vv);
+    }
+  return s;
 }
 
 template <int Kind>
@@ -93,8 +133,13 @@ __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __
         S[(int64_t)e * 78 + s] = vv * v;
         ++s;
       }
-  } else if (Kind == 2) {
+  } else if (Kind == 2 || Kind == 3) {
     constexpr int ea[6] = {0, 0, 0, 1, 1, 2}, eb[6] = {1, 2, 3, 2, 3, 3};
+    constexpr int NL = Kind == 3 ? 14 : 10, NS = Kind == 3 ? 105 : 55;
+    auto slot = [&](int r, int c) {
+      if (r > c) { const int t = r; r = c; c = t; }
+      return NL * r - r * (r - 1) / 2 + (c - r);
+    };
     double G[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -102,20 +147,29 @@ __global__ void k_tet_geometry(const double* __restrict__ xyz, const int32_t* __
       for (int b = 0; b < 4; ++b) G[a][b] = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
     auto M2 = [&](int i, int j) { return vv * (i == j ? 2.0 : 1.0) / 20.0; };
     auto mv = [&](int a, int b) { return vv * ((a == b ? 2.0 : 1.0) / 5.0 - 0.25); };
-    double* Se = S + (int64_t)e * 55;
+    double* Se = S + (int64_t)e * NS;
     for (int a = 0; a < 4; ++a)
-      for (int b = a; b < 4; ++b) Se[p2_local_slot(a, b)] = G[a][b] * vv * (a == b ? 0.6 : -0.2);
+      for (int b = a; b < 4; ++b) Se[slot(a, b)] = G[a][b] * vv * (a == b ? 0.6 : -0.2);
     for (int a = 0; a < 4; ++a)
       for (int k = 0; k < 6; ++k) {
         const int b = ea[k], c = eb[k];
-        Se[p2_local_slot(a, 4 + k)] = 4.0 * (G[a][c] * mv(a, b) + G[a][b] * mv(a, c));
+        Se[slot(a, 4 + k)] = 4.0 * (G[a][c] * mv(a, b) + G[a][b] * mv(a, c));
       }
     for (int k = 0; k < 6; ++k)
       for (int k2 = k; k2 < 6; ++k2) {
         const int a = ea[k], b = eb[k], c = ea[k2], d = eb[k2];
-        Se[p2_local_slot(4 + k, 4 + k2)] =
+        Se[slot(4 + k, 4 + k2)] =
             16.0 * (G[b][d] * M2(a, c) + G[b][c] * M2(a, d) + G[a][d] * M2(b, c) + G[a][c] * M2(b, d));
       }
+    if (Kind == 3) {  // the coupled pair: sigma (= lam here) times the mass blocks, and K1 on the P1 field
+      const double sg = lam;
+      for (int i = 0; i < 10; ++i)
+        for (int j = i; j < 10; ++j) Se[slot(i, j)] += sg * p2p1_mass(i, j, vv);
+      for (int i = 0; i < 10; ++i)
+        for (int a = 0; a < 4; ++a) Se[slot(i, 10 + a)] = -sg * p2p1_mass(i, 10 + a, vv);
+      for (int a = 0; a < 4; ++a)
+        for (int b = a; b < 4; ++b) Se[slot(10 + a, 10 + b)] = vv * G[a][b] + sg * p2p1_mass(10 + a, 10 + b, vv);
+    }
   } else {
     int s = 0;
 #pragma unroll
@@ -173,11 +227,14 @@ __global__ void k_load_vector(const double* __restrict__ xyz, const uint8_t* __r
   }
   int q = diag[i];
   double s = 0.0;
-  if (ns == 55) {  // P2, f = 1: the diagonal slot names the local DoF (vertex slots < 34)
+  if (ns == 55 || ns == 105) {  // P2 (and P2-P1), f = 1: the diagonal slot names the local DoF
+    const int NL = ns == 55 ? 10 : 14;
     for (int c = cptr[q]; c < cptr[q + 1]; ++c) {
-      const int id = contrib[c];
-      const double v = vol[id / 55];
-      s += (id % 55) < 34 ? -v / 20.0 : v / 5.0;
+      const int id = contrib[c], sl = id % ns;
+      const double v = vol[id / ns];
+      int li = 0;  // slot of (li, li) is NL li - li (li - 1) / 2
+      while (li + 1 < NL && NL * (li + 1) - (li + 1) * li / 2 <= sl) ++li;
+      s += li < 4 ? -v / 20.0 : (li < 10 ? v / 5.0 : v / 4.0);  // int phi: P2 vertex, P2 edge, P1 vertex
     }
     b[i] = s;
     return;
@@ -580,6 +637,8 @@ void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, int kind
     k_tet_geometry<1><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
   else if (kind == 2)
     k_tet_geometry<2><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
+  else if (kind == 3)
+    k_tet_geometry<3><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
   else
     k_tet_geometry<0><<<nblk(m, 128), 128, 0, s>>>(xyz, tets, m, lam, mu, S, vol, cen, bad);
 }

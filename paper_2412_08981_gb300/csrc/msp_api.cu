@@ -478,8 +478,9 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   // Lame parameters of a unit Young's modulus (linear elasticity only)
   const double nu = h->opt.poisson_ratio;
   const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
-  const int kind = H.fields == 3 ? 1 : (H.p2 ? 2 : 0);  // element: P1, elasticity, P2
-  launch_tet_geometry(D.xyz, D.tets, D.m, kind, lam, mu, D.S, D.vol, D.cen, bad, s);
+  // element: P1, elasticity, P2, or the P2-P1 pair (whose coupling rides in `lam`)
+  const int kind = H.fields == 3 ? 1 : (H.p2 ? (H.nloc == 14 ? 3 : 2) : 0);
+  launch_tet_geometry(D.xyz, D.tets, D.m, kind, kind == 3 ? h->opt.coupling : lam, mu, D.S, D.vol, D.cen, bad, s);
   launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, H.fields,
                      H.nslot, lam, mu, D.b, s);
   int hbad = 0;
@@ -524,12 +525,15 @@ int check_options(const msp_options& o) {
   if (o.load_kind != MSP_F_ONE && o.load_kind != MSP_F_SINES)
     return fail(MSP_ERR_INVALID, "unknown load");
   if (!std::isfinite(o.coef_scale)) return fail(MSP_ERR_INVALID, "non-finite coef_scale");
-  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2)
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2 &&
+      o.pde != MSP_PDE_P2P1)
     return fail(MSP_ERR_INVALID, "unknown pde");
-  if (o.pde == MSP_PDE_POISSON_P2 && o.transfer != MSP_TRANSFER_BARY)
+  const bool p2 = o.pde == MSP_PDE_POISSON_P2 || o.pde == MSP_PDE_P2P1;
+  if (p2 && o.transfer != MSP_TRANSFER_BARY)
     return fail(MSP_ERR_INVALID, "P2 elements take the P2 interpolation between levels, not MLS");
-  if (o.pde == MSP_PDE_POISSON_P2 && o.load_kind != MSP_F_ONE)
-    return fail(MSP_ERR_INVALID, "P2 elements support the load f = 1 only");
+  if (p2 && o.load_kind != MSP_F_ONE) return fail(MSP_ERR_INVALID, "P2 elements support the load f = 1 only");
+  if (o.pde == MSP_PDE_P2P1 && !(o.coupling > 0.0 && std::isfinite(o.coupling)))
+    return fail(MSP_ERR_INVALID, "the P2-P1 system needs a coupling coefficient > 0");
   if (o.pde == MSP_PDE_ELASTICITY && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
     return fail(MSP_ERR_INVALID, "linear elasticity needs a Poisson ratio in (0, 0.5)");
   if (o.pde == MSP_PDE_ELASTICITY && o.transfer != MSP_TRANSFER_BARY)
@@ -2036,6 +2040,7 @@ void msp_default_options(msp_options* o) {
   o->ilu_fill_coarse = -1;
   o->pde = MSP_PDE_POISSON;
   o->poisson_ratio = 0.3;
+  o->coupling = 1.0;
 }
 
 const char* msp_last_error(void) { return msp::g_last_error.c_str(); }

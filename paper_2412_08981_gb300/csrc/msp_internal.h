@@ -37,9 +37,13 @@ constexpr int kElasticSlots = 78;
 // its edges 01, 02, 03, 12, 13, 23; the symmetric 10 x 10 element matrix is
 // stored by its upper triangle, row-major: 55 slots.
 constexpr int kP2Slots = 55;
-inline int p2_slot(int r, int s) {
+// The coupled two-field element (a P2 field u, local DoFs 0..9 as above, and
+// a P1 field p, local DoFs 10..13 at the vertices): 14 x 14, 105 slots.
+constexpr int kP2P1Slots = 105;
+// slot of (r, s) in the upper triangle, row-major, of an n x n symmetric matrix
+inline int sym_slot(int n, int r, int s) {
   if (r > s) { int t = r; r = s; s = t; }
-  return 10 * r - r * (r - 1) / 2 + (s - r);
+  return n * r - r * (r - 1) / 2 + (s - r);
 }
 constexpr int kP2EdgeEnd[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 
@@ -49,12 +53,14 @@ struct HostLevel {
   // are per DoF (field c of vertex v is DoF fields*v + c)
   int n = 0, m = 0;
   int nv = 0, fields = 1;
-  int nslot = 10;  // element-matrix slots per tet: 10 (P1), 78 (elasticity), 55 (P2)
+  int nslot = 10;  // element-matrix slots per tet: 10 (P1), 78 (elasticity), 55 (P2), 105 (P2-P1)
   // P2 only: the global DoF of each of the 10 local DoFs of every tet, and
   // the point of every DoF (a vertex, or an edge's midpoint)
   bool p2 = false;
+  int nloc = 10;                 // local DoFs per tet of the P2 forms: 10, or 14 with the P1 field p
   std::vector<int32_t> tdof;
   std::vector<double> dofx;
+  std::vector<uint8_t> pdof;     // P2-P1: 1 for the DoFs of the P1 field
   std::vector<double> xyz;
   std::vector<int32_t> tets;
   std::vector<uint8_t> dir;

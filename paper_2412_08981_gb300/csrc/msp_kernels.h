@@ -12,7 +12,9 @@ namespace msp {
 // kind 0 (P1): S[e*10+slot] = |T| grad(lambda_a).grad(lambda_b); kind 1
 // (elasticity): the 78 upper-triangle slots of the unit-k 12 x 12 elasticity
 // matrix (Lame lam, mu); kind 2 (P2): the 55 upper-triangle slots of the
-// unit-k 10 x 10 quadratic-element matrix; vol[e] = |T|; cen[e*3] centroid
+// unit-k 10 x 10 quadratic-element matrix; kind 3 (P2-P1 pair): the 105
+// slots of the 14 x 14 coupled element with coupling sigma = lam; vol[e] =
+// |T|; cen[e*3] centroid
 void launch_tet_geometry(const double* xyz, const int32_t* tets, int m, int kind, double lam, double mu,
                          double* S, double* vol, double* cen, int* bad, cudaStream_t s);
 // b_i = f_c(x_v) * sum_{e containing v} |T_e| / 4 (ascending e) for DoF i =

@@ -1027,8 +1027,16 @@ void expand_fields(HostLevel& L) {
 // boundary face (a face of exactly one tet) with three Dirichlet vertices.
 // The pattern couples the DoFs of each tet; contribution e*55 + slot(li, lj)
 // of tet e (ascending e) feeds the nonzero of its local DoFs li, lj.
-std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool smoothed) {
+// With `twofield` (the coupled P2-P1 system) every vertex also carries the
+// DoF of the P1 field p, right after its u DoF (vertex 0's u, its p, its
+// edges, vertex 1's u, ...); local DoFs 10..13 of a tet are its vertices' p
+// DoFs, Dirichlet and owned as their vertex; contributions address the
+// 105-slot element matrix.
+std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool smoothed, bool twofield) {
   const int nv = L.nv;
+  const int nb = twofield ? 2 : 1;        // vertex DoFs per vertex
+  const int NL = twofield ? 14 : 10;      // local DoFs per tet
+  const int NS = twofield ? kP2P1Slots : kP2Slots;
   std::vector<int32_t> vptr, vadj;
   vertex_tets(L, vptr, vadj);
   // upper neighbours of every vertex through the edges of its tets
@@ -1051,33 +1059,41 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
   }
   const int64_t ne = uptr[nv];
   if (nv + ne > INT32_MAX / 2) return "too many P2 DoFs";
-  auto vdof = [&](int v) { return v + uptr[v]; };
+  auto vdof = [&](int v) { return nb * v + uptr[v]; };
+  auto edof_at = [&](int v, int32_t k) { return (int32_t)(nb * v + nb + k); };  // CSR position k of v's edges
   auto edof = [&](int a, int b) {  // a != b
     if (a > b) std::swap(a, b);
     const int32_t* lo = ucol.data() + uptr[a];
     const int32_t* hi = ucol.data() + uptr[a + 1];
     const int32_t* it = std::lower_bound(lo, hi, b);
-    return (int32_t)(a + 1 + (it - ucol.data()));
+    return edof_at(a, (int32_t)(it - ucol.data()));
   };
-  const int n = (int)(nv + ne);
+  const int n = (int)(nb * (int64_t)nv + ne);
   std::vector<uint8_t> vdir = L.dir;
   L.p2 = true;
-  L.nslot = kP2Slots;
+  L.nloc = NL;
+  L.nslot = NS;
   L.n = n;
-  L.tdof.assign(10 * (size_t)L.m, 0);
+  L.tdof.assign(NL * (size_t)L.m, 0);
   for (int e = 0; e < L.m; ++e) {
     const int32_t* t = &L.tets[4 * (int64_t)e];
-    for (int a = 0; a < 4; ++a) L.tdof[10 * (size_t)e + a] = vdof(t[a]);
-    for (int k = 0; k < 6; ++k) L.tdof[10 * (size_t)e + 4 + k] = edof(t[kP2EdgeEnd[k][0]], t[kP2EdgeEnd[k][1]]);
+    for (int a = 0; a < 4; ++a) L.tdof[NL * (size_t)e + a] = vdof(t[a]);
+    for (int k = 0; k < 6; ++k) L.tdof[NL * (size_t)e + 4 + k] = edof(t[kP2EdgeEnd[k][0]], t[kP2EdgeEnd[k][1]]);
+    if (twofield)
+      for (int a = 0; a < 4; ++a) L.tdof[NL * (size_t)e + 10 + a] = vdof(t[a]) + 1;
   }
   L.dofx.assign(3 * (size_t)n, 0.0);
   L.dir.assign(n, 0);
+  L.pdof.assign(twofield ? n : 0, 0);
   for (int v = 0; v < nv; ++v) {
-    for (int d = 0; d < 3; ++d) L.dofx[3 * (size_t)vdof(v) + d] = L.xyz[3 * (size_t)v + d];
-    L.dir[vdof(v)] = vdir[v];
+    for (int f = 0; f < nb; ++f) {
+      for (int d = 0; d < 3; ++d) L.dofx[3 * (size_t)(vdof(v) + f) + d] = L.xyz[3 * (size_t)v + d];
+      L.dir[vdof(v) + f] = vdir[v];
+    }
+    if (twofield) L.pdof[vdof(v) + 1] = 1;
     for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k)
       for (int d = 0; d < 3; ++d)
-        L.dofx[3 * (size_t)(v + 1 + k) + d] = 0.5 * (L.xyz[3 * (size_t)v + d] + L.xyz[3 * (size_t)ucol[k] + d]);
+        L.dofx[3 * (size_t)edof_at(v, k) + d] = 0.5 * (L.xyz[3 * (size_t)v + d] + L.xyz[3 * (size_t)ucol[k] + d]);
   }
   // boundary faces: faces that no other tet shares
   for (int e = 0; e < L.m; ++e) {
@@ -1109,15 +1125,15 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
   // the DoF's vertex, or of its edge's lower vertex)
   std::vector<int32_t> ent_a(n), ent_b(n, -1);  // DoF -> its vertex (a) or edge (a, b)
   for (int v = 0; v < nv; ++v) {
-    ent_a[vdof(v)] = v;
+    for (int f = 0; f < nb; ++f) ent_a[vdof(v) + f] = v;
     for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k) {
-      ent_a[v + 1 + k] = v;
-      ent_b[v + 1 + k] = ucol[k];
+      ent_a[edof_at(v, k)] = v;
+      ent_b[edof_at(v, k)] = ucol[k];
     }
   }
   auto holds = [&](int e, int i) {  // local index of DoF i in tet e, or -1
-    for (int li = 0; li < 10; ++li)
-      if (L.tdof[10 * (size_t)e + li] == i) return li;
+    for (int li = 0; li < NL; ++li)
+      if (L.tdof[NL * (size_t)e + li] == i) return li;
     return -1;
   };
   L.rowptr.assign(n + 1, 0);
@@ -1129,7 +1145,7 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
     for (int k = vptr[a]; k < vptr[a + 1]; ++k) {
       const int e = vadj[k];
       if (holds(e, i) < 0) continue;
-      buf.insert(buf.end(), &L.tdof[10 * (size_t)e], &L.tdof[10 * (size_t)e] + 10);
+      buf.insert(buf.end(), &L.tdof[NL * (size_t)e], &L.tdof[NL * (size_t)e] + NL);
     }
     std::sort(buf.begin(), buf.end());
     buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
@@ -1168,11 +1184,11 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
         const int e = vadj[k];
         const int li = holds(e, i);
         if (li < 0) continue;
-        for (int lj = 0; lj < 10; ++lj) {
-          const int32_t q = find_in_row(L, i, L.tdof[10 * (size_t)e + lj]);
+        for (int lj = 0; lj < NL; ++lj) {
+          const int32_t q = find_in_row(L, i, L.tdof[NL * (size_t)e + lj]);
           if (L.nzflag[q] != 0) continue;
           if (pass == 0) cnt[q]++;
-          else L.contrib[fill[q]++] = e * kP2Slots + p2_slot(li, lj);
+          else L.contrib[fill[q]++] = e * NS + sym_slot(NL, li, lj);
         }
       }
     }
@@ -1236,9 +1252,10 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
       }
       std::vector<int32_t> d;
       for (int v : members) {
-        if (!L.dir[vdof(v)]) d.push_back(vdof(v));
+        for (int f = 0; f < nb; ++f)
+          if (!L.dir[vdof(v) + f]) d.push_back(vdof(v) + f);
         for (int32_t k = uptr[v]; k < uptr[v + 1]; ++k)
-          if (stamp[ucol[k]] == p && !L.dir[v + 1 + k]) d.push_back(v + 1 + k);
+          if (stamp[ucol[k]] == p && !L.dir[edof_at(v, k)]) d.push_back(edof_at(v, k));
       }
       std::sort(d.begin(), d.end());
       std::vector<uint8_t> o(d.size());
@@ -1274,7 +1291,9 @@ std::string build_p2_level(HostLevel& L, const int32_t* vowner, int delta, bool 
 // (the lowest containing tet id, else the tet whose smallest barycentric
 // weight is largest) and its row holds the coarse tet's ten P2 basis
 // functions there -- vertex a: l_a (2 l_a - 1), edge ab: 4 l_a l_b -- on the
-// non-Dirichlet coarse DoFs, columns ascending, zero weights kept.
+// non-Dirichlet coarse DoFs, columns ascending, zero weights kept.  With the
+// P2-P1 system the transfer is split by field (Section 2.1): rows of the P1
+// field p hold the barycentric weights on the coarse p DoFs.
 void build_interp_p2(const HostLevel& F, const HostLevel& C, HostLevel& out) {
   TetGrid g;
   build_grid(C, g);
@@ -1323,13 +1342,18 @@ void build_interp_p2(const HostLevel& F, const HostLevel& C, HostLevel& out) {
   for (int f = 0; f < n; ++f) {
     if (tet_of[f] >= 0) {
       const double* l = &lam_of[4 * (size_t)f];
-      const int32_t* td = &C.tdof[10 * (size_t)tet_of[f]];
+      const int32_t* td = &C.tdof[C.nloc * (size_t)tet_of[f]];
       row.clear();
-      for (int i = 0; i < 10; ++i) {
-        if (C.dir[td[i]]) continue;
-        const double w = i < 4 ? l[i] * (2.0 * l[i] - 1.0)
-                               : 4.0 * l[kP2EdgeEnd[i - 4][0]] * l[kP2EdgeEnd[i - 4][1]];
-        row.push_back({td[i], w});
+      if (!F.pdof.empty() && F.pdof[f]) {  // the P1 field: its barycentric weights on the coarse p DoFs
+        for (int a = 0; a < 4; ++a)
+          if (!C.dir[td[10 + a]]) row.push_back({td[10 + a], l[a]});
+      } else {
+        for (int i = 0; i < 10; ++i) {
+          if (C.dir[td[i]]) continue;
+          const double w = i < 4 ? l[i] * (2.0 * l[i] - 1.0)
+                                 : 4.0 * l[kP2EdgeEnd[i - 4][0]] * l[kP2EdgeEnd[i - 4][1]];
+          row.push_back({td[i], w});
+        }
       }
       std::sort(row.begin(), row.end());
       for (auto& pr : row) {
@@ -1382,10 +1406,13 @@ std::string check_level(const msp_level_desc& d, int l, bool need_owner) {
 std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_options& o,
                               std::vector<HostLevel>& out) {
   if (nlevels < 1) return "nlevels must be >= 1";
-  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2)
+  if (o.pde != MSP_PDE_POISSON && o.pde != MSP_PDE_ELASTICITY && o.pde != MSP_PDE_POISSON_P2 &&
+      o.pde != MSP_PDE_P2P1)
     return "unknown pde";
   const bool elastic = o.pde == MSP_PDE_ELASTICITY;
-  const bool p2 = o.pde == MSP_PDE_POISSON_P2;
+  const bool p2 = o.pde == MSP_PDE_POISSON_P2 || o.pde == MSP_PDE_P2P1;
+  if (o.pde == MSP_PDE_P2P1 && !(o.coupling > 0.0 && std::isfinite(o.coupling)))
+    return "the P2-P1 system needs a coupling coefficient > 0";
   if (p2 && o.transfer != MSP_TRANSFER_BARY) return "P2 elements take the barycentric-rule transfers (P2 interpolation)";
   if (p2 && o.load_kind != MSP_F_ONE) return "P2 elements support the load f = 1 only";
   if (elastic && !(o.poisson_ratio > 0.0 && o.poisson_ratio < 0.5))
@@ -1409,7 +1436,7 @@ std::string build_host_levels(const msp_level_desc* lv, int nlevels, const msp_o
     if (need_owner) L.owner.assign(lv[l].owner, lv[l].owner + L.n);
     L.direct = (l + 1 == nlevels) && o.coarse_solver == MSP_COARSE_DIRECT;
     if (p2) {
-      std::string e2 = build_p2_level(L, lv[l].owner, o.delta, !L.direct);
+      std::string e2 = build_p2_level(L, lv[l].owner, o.delta, !L.direct, o.pde == MSP_PDE_P2P1);
       if (!e2.empty()) return "level " + std::to_string(l) + ": " + e2;
       if (L.direct) build_coarsest_block(L);
       continue;

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -24,7 +25,7 @@ MSP_K_CONST, MSP_K_COSEXP = 0, 1
 MSP_F_ONE, MSP_F_SINES = 0, 1
 MSP_TRANSFER_BARY, MSP_TRANSFER_MLS = 0, 1
 MSP_COARSE_DIRECT, MSP_COARSE_RAS = 0, 1
-MSP_PDE_POISSON, MSP_PDE_ELASTICITY, MSP_PDE_POISSON_P2 = 0, 1, 2
+MSP_PDE_POISSON, MSP_PDE_ELASTICITY, MSP_PDE_POISSON_P2, MSP_PDE_P2P1 = 0, 1, 2, 3
 MSP_OP_SPMV, MSP_OP_RESIDUAL, MSP_OP_INTERP, MSP_OP_RESTRICT, MSP_OP_RAS, MSP_OP_COARSE = range(6)
 ARRAYS = {"rowptr": 0, "col": 1, "sub_ptr": 2, "sub_dofs": 3, "sub_own": 4, "P_rowptr": 5,
           "P_col": 6, "P_val": 7, "PT_rowptr": 8, "PT_col": 9, "PT_val": 10, "load": 11,
@@ -67,7 +68,7 @@ class msp_options(C.Structure):
                 ("coef_scale", C.c_double), ("load_kind", C.c_int32), ("transfer", C.c_int32),
                 ("restrict_scaling", C.c_int32), ("coarse_solver", C.c_int32),
                 ("ilu_fill_fine", C.c_int32), ("ilu_fill_coarse", C.c_int32),
-                ("pde", C.c_int32), ("poisson_ratio", C.c_double),
+                ("pde", C.c_int32), ("poisson_ratio", C.c_double), ("coupling", C.c_double),
                 ("host_only", C.c_int32),
                 ("mem_budget_bytes", C.c_size_t), ("alloc", msp_alloc_fn),
                 ("free", msp_free_fn), ("alloc_ctx", C.c_void_p)]
@@ -225,7 +226,50 @@ def default_options(**kw) -> msp_options:
     return o
 
 
-class Hierarchy:
+class _Shared:
+    """Release order of library objects that others are built on.
+
+    The C library wants an object freed after everything built on it (a
+    hierarchy after its instances and servers, an instance after its
+    batches).  A user of an object takes a reference (_acquire) and gives it
+    back when it is freed (_release); close() frees the object at once when
+    it has no users, else marks it and the last user's release frees it.  So
+    the order holds whatever order the garbage collector finalises a
+    reference cycle in (it clears weak references before it runs
+    finalisers, so a list of weak references alone cannot give the order).
+    An explicit close() also closes the users still alive first."""
+
+    def _init_shared(self):
+        self._users = 0
+        self._closing = False
+        self._deps = weakref.WeakSet()
+
+    def _acquire(self, user):
+        self._users += 1
+        self._deps.add(user)
+
+    def _release(self):
+        self._users -= 1
+        if self._closing and self._users <= 0:
+            self._free_now()
+
+    def _handle(self):
+        raise NotImplementedError
+
+    def close(self):
+        if not self._handle() or getattr(self, "_closing", True):
+            return
+        for d in list(self._deps):
+            d.close()
+        self._closing = True
+        if self._users <= 0:
+            self._free_now()
+
+    def __del__(self):
+        self.close()
+
+
+class Hierarchy(_Shared):
     """msp_load_hierarchy / msp_free_hierarchy.
 
     levels: sequence of objects with xyz [n,3] f64, tets [m,4] i32,
@@ -233,16 +277,18 @@ class Hierarchy:
     pde: "poisson" (one DoF per vertex) or "elasticity" (three displacement
     fields per vertex, DoF 3v + c; Poisson ratio `poisson`) or "poisson_p2"
     (quadratic elements: DoFs on the vertices and the edge midpoints, in the
-    order msp.h states); vectors of a level hold n_dofs(level) entries.
+    order msp.h states) or "p2p1" (a P2 field and a P1 field coupled with the
+    coefficient `coupling`); vectors of a level hold n_dofs(level) entries.
     """
 
     def __init__(self, levels: Sequence, delta=1, nu_pre=2, nu_post=2, restart=30,
                  max_it=1000, precision="f64", coef="const", wave=None, scale=1.0,
                  load="one", host_only=False, budget_bytes=0, torch_alloc=True,
                  transfer="bary", restrict_scaling=True, coarse="direct", ilu=None,
-                 pde="poisson", poisson=0.3):
+                 pde="poisson", poisson=0.3, coupling=1.0):
         lib = _load_library()
         self._keep = []
+        self._init_shared()  # instances and servers built on it are freed first
         arr = (msp_level_desc * len(levels))()
         for i, lv in enumerate(levels):
             xyz = np.ascontiguousarray(lv.xyz, np.float64)
@@ -265,8 +311,8 @@ class Hierarchy:
                             ilu_fill_fine=-1 if ilu is None else int(ilu[0]),
                             ilu_fill_coarse=-1 if ilu is None else int(ilu[1]),
                             pde={"poisson": MSP_PDE_POISSON, "elasticity": MSP_PDE_ELASTICITY,
-                                 "poisson_p2": MSP_PDE_POISSON_P2}[pde],
-                            poisson_ratio=float(poisson),
+                                 "poisson_p2": MSP_PDE_POISSON_P2, "p2p1": MSP_PDE_P2P1}[pde],
+                            poisson_ratio=float(poisson), coupling=float(coupling),
                             host_only=1 if host_only else 0,
                             mem_budget_bytes=int(budget_bytes))
         if wave is not None:
@@ -290,13 +336,12 @@ class Hierarchy:
         """Length of the vectors of a level."""
         return int(self.info(level)["n_dofs"])
 
-    def close(self):
-        if getattr(self, "h", None):
-            load().msp_free_hierarchy(self.h)
-            self.h = None
+    def _handle(self):
+        return getattr(self, "h", None)
 
-    def __del__(self):
-        self.close()
+    def _free_now(self):
+        load().msp_free_hierarchy(self.h)
+        self.h = None
 
     def info(self, level=0) -> dict:
         inf = msp_level_info()
@@ -322,24 +367,26 @@ class Hierarchy:
         return int(b.value)
 
 
-class Instance:
+class Instance(_Shared):
     """msp_assemble ... msp_free_instance for one parameter vector."""
 
     def __init__(self, h: Hierarchy, mu=None, stream=None):
         self.hier = h
+        self._init_shared()  # batches holding this instance are freed first
         self._mu = np.zeros(8) if mu is None else np.ascontiguousarray(mu, np.float64)
         self.stream = _stream_ptr(stream)
         inst = C.c_void_p()
         _check(load().msp_assemble(h.h, _ptr(self._mu), 8, self.stream, C.byref(inst)))
         self.inst = inst
+        h._acquire(self)
 
-    def close(self):
-        if getattr(self, "inst", None):
-            load().msp_free_instance(self.inst)
-            self.inst = None
+    def _handle(self):
+        return getattr(self, "inst", None)
 
-    def __del__(self):
-        self.close()
+    def _free_now(self):
+        load().msp_free_instance(self.inst)
+        self.inst = None
+        self.hier._release()
 
     def reassemble(self, mu):
         self._mu = np.ascontiguousarray(mu, np.float64)
@@ -427,6 +474,7 @@ class Server:
         i = C.c_int(0)
         _check(load().msp_server_add_hierarchy(self.srv, h.h, C.byref(i)))
         self._hier.append(h)
+        h._acquire(self)  # the server's slot instances go before the hierarchy
         return int(i.value)
 
     def submit(self, hid, mu, rtol=0.0) -> int:
@@ -448,6 +496,8 @@ class Server:
         if getattr(self, "srv", None):
             load().msp_server_free(self.srv)
             self.srv = None
+            for h in self._hier:
+                h._release()
 
     def __del__(self):
         self.close()
@@ -464,6 +514,8 @@ class Batch:
         _check(load().msp_batch_create(arr, len(self._insts),
                                        _stream_ptr(stream) if stream is not None else None, C.byref(b)))
         self.b = b
+        for i in self._insts:
+            i._acquire(self)
 
     def assemble(self, mus):
         """msp_batch_assemble: re-assemble every member for its parameter
@@ -495,6 +547,8 @@ class Batch:
         if getattr(self, "b", None):
             load().msp_batch_free(self.b)
             self.b = None
+            for i in self._insts:
+                i._release()
 
     def __del__(self):
         self.close()

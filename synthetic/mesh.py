@@ -151,7 +151,7 @@ def mu_draw(request: int) -> np.ndarray:
 #   pde: "poisson" (default), "elasticity" (with its Poisson ratio "poisson"),
 #        "poisson_p2" (quadratic elements: DoFs on the vertices and the edges) or
 #        "p2p1" (a quadratic field u and a linear field p coupled with the
-#        coefficient given as "poisson")
+#        coefficient "coupling")
 WORKLOADS = {
     # two-level plain FP64, 8^3 -> 4^3, 2x2x2 boxes, overlap 1
     "cube8_2lvl": dict(ns=(8, 4), parts=((2, 2, 2),), delta=1, nu=2, coef="const",
@@ -205,11 +205,11 @@ WORKLOADS = {
     # two fields of different element order (u quadratic, p linear) coupled by
     # sigma k (u - p): field-split transfers, P2 interpolation for u, P1 for p
     "p2p1cube6_3lvl": dict(ns=(6, 3, 2), parts=((2, 2, 2), (1, 1, 1)), delta=1, nu=2, coef="cosexp",
-                           scale=1.0, load="one", rtol=1e-10, restart=30, pde="p2p1", poisson=1.0),
+                           scale=1.0, load="one", rtol=1e-10, restart=30, pde="p2p1", coupling=1.0),
     "p2p1cube12_3lvl": dict(ns=(12, 6, 3), parts=((3, 3, 3), (2, 2, 2)), delta=1, nu=2, coef="cosexp",
-                            scale=1.0, load="one", rtol=1e-10, restart=30, pde="p2p1", poisson=1.0),
+                            scale=1.0, load="one", rtol=1e-10, restart=30, pde="p2p1", coupling=1.0),
     "p2p1cube32_3lvl": dict(ns=(32, 16, 8), parts=((8, 8, 8), (4, 4, 4)), delta=1, nu=2, coef="cosexp",
-                            scale=1.0, load="one", rtol=1e-8, restart=30, pde="p2p1", poisson=1.0),
+                            scale=1.0, load="one", rtol=1e-8, restart=30, pde="p2p1", coupling=1.0),
     # and the measured case: 107,811 DoFs on 32^3, 64 + 8 blocks of ~3000 DoFs
     "elast32_3lvl": dict(ns=(32, 16, 8), parts=((4, 4, 4), (2, 2, 2)), delta=1, nu=2,
                          coef="cosexp", scale=1.0, load="one", rtol=1e-8, restart=30,

@@ -25,7 +25,7 @@ def workload(name, hierarchy_id=0):
 def _pde(w):
     if "pde" not in w:
         return {}
-    return dict(pde=w["pde"], poisson=w.get("poisson", 0.3))
+    return dict(pde=w["pde"], poisson=w.get("poisson", 0.3), coupling=w.get("coupling", 1.0))
 
 
 def make_oracle(levels, w, orc, **kw):

@@ -264,7 +264,7 @@ def test_noalloc_binding_checks_its_tensors(P):
         m.multidot_noalloc(cpu, cpu, cpu)
 
 
-@pytest.mark.parametrize("name", ["p2cube6_3lvl", "p2cube12_3lvl"])
+@pytest.mark.parametrize("name", ["p2cube6_3lvl", "p2cube12_3lvl", "p2p1cube6_3lvl", "p2p1cube12_3lvl"])
 def test_host_p2_structures_match_oracle(P, orc, name):
     """Quadratic elements (DoFs on vertices and edges): the DoF-level pattern,
     subdomains and the P2 transfers of the library's host set-up against the
@@ -290,3 +290,66 @@ def test_host_p2_structures_match_oracle(P, orc, name):
         np.testing.assert_allclose(h.array(l, "PT_val"), o.get("PT_val", l), atol=1e-13)
     dirc = o.get("dofdir", L - 1)
     np.testing.assert_array_equal(h.array(L - 1, "sub_dofs"), np.where(dirc == 0)[0])
+
+
+def test_binding_frees_dependents_before_their_hierarchy(P, monkeypatch):
+    """The binding frees an instance before its hierarchy (and a batch before
+    its instances) in either finalisation order of a reference cycle, and an
+    explicit close() of a hierarchy closes its live instances first.  The
+    library calls are replaced by a log: only the order is checked."""
+    msp = P.msp
+    log = []
+
+    class Lib:
+        def msp_free_hierarchy(self, h):
+            log.append(("hierarchy", h))
+
+        def msp_free_instance(self, i):
+            log.append(("instance", i))
+
+        def msp_batch_free(self, b):
+            log.append(("batch", b))
+    monkeypatch.setattr(msp, "load", lambda: Lib())
+
+    def make():
+        h = object.__new__(msp.Hierarchy)
+        h._init_shared()
+        h.h = "H"
+        insts = []
+        for k in range(2):
+            i = object.__new__(msp.Instance)
+            i.hier = h
+            i._init_shared()
+            i.inst = f"I{k}"
+            h._acquire(i)
+            insts.append(i)
+        b = object.__new__(msp.Batch)
+        b._insts = list(insts)
+        b.b = "B"
+        for i in insts:
+            i._acquire(b)
+        return h, insts, b
+
+    def check(order):
+        pos = {name: k for k, (_, name) in enumerate(log)}
+        assert sorted(pos) == ["B", "H", "I0", "I1"]
+        assert pos["B"] < pos["I0"] and pos["B"] < pos["I1"]
+        assert pos["I0"] < pos["H"] and pos["I1"] < pos["H"], order
+
+    # garbage-collector orders: finalisers in any order, no weak references left
+    import itertools
+    for perm in itertools.permutations(range(4)):
+        log.clear()
+        h, insts, b = make()
+        objs = [h, insts[0], insts[1], b]
+        for o in objs[:3]:
+            o._deps.clear()
+        for k in perm:
+            objs[k].__del__()
+        check(perm)
+    # explicit close of the hierarchy with everything alive
+    log.clear()
+    h, insts, b = make()
+    h.close()
+    check("explicit")
+    assert h.h is None and all(i.inst is None for i in insts) and b.b is None

@@ -64,10 +64,12 @@ class Case:
 
 # every parity workload with P / P^T, two with the MLS transfers of Section
 # 3.2 (cube20m pairs the subdomains of the two RAS levels), the multi-field
-# case (linear elasticity, three fields per vertex, field-split P) and the
-# quadratic elements (DoFs on vertices and edges, the P2 interpolation)
+# case (linear elasticity, three fields per vertex, field-split P), the
+# quadratic elements (DoFs on vertices and edges, the P2 interpolation) and
+# the coupled pair of a P2 and a P1 field (the transfer split by field with a
+# different interpolation per field)
 CASES = ([(n, "bary") for n in PARITY] + [("cube16_3lvl", "mls"), ("cube20m_3lvl", "mls")] +
-         [("elast12_3lvl", "bary"), ("p2cube12_3lvl", "bary")])
+         [("elast12_3lvl", "bary"), ("p2cube12_3lvl", "bary"), ("p2p1cube12_3lvl", "bary")])
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-{c[1]}")

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "msp_dense.cuh"
 #include "msp_kernels.h"
@@ -34,25 +35,15 @@ namespace msp {
 namespace {
 
 
-// 1/d by Newton's method for the reciprocal (x <- x + x (1 - d x), which
-// doubles the correct bits per step) from a single-precision seed: two steps
-// take the seed's ~23 bits past double precision.  Shorter dependent chain
-// than a full-precision division on the pivot chain of the factorisation.
-// The seed needs d and 1/d inside the normal single-precision range; outside
-// [1e-37, 1e37] (where the float seed would be zero, infinite or subnormal)
-// the reciprocal is the full-precision division instead.  The factor parity
-// tests bound the agreement with 1/d, and a test on meshes scaled by 2^+-133
-// (pivots near 1e40 and 1e-40) runs the division branch.
-__device__ inline double rcp_newton(double d) {
-  const double a = fabs(d);
-  if (!(a >= 1e-37 && a <= 1e37)) return 1.0 / d;
-  double x = (double)__frcp_rn((float)d);
-  double e = fma(-d, x, 1.0);
-  x = fma(x, e, x);
-  e = fma(-d, x, 1.0);
-  return fma(x, e, x);
-}
-__device__ inline float rcp_newton(float d) { return 1.0f / d; }
+// 1/d of a pivot, correctly rounded.  Every reciprocal sits on the
+// sequential pivot chain of a factorisation.  On GB300 the dependent latency
+// of __drcp_rn (about 440 cycles for one warp, against 63 for one FP64 FMA)
+// is shorter than that of Newton steps from a single-precision seed, whose
+// conversions cost more than the steps (about 640 cycles), and it is exact
+// over the whole double range (a test on meshes scaled by 2^+-133 puts
+// pivots near 1e40 and 1e-40).
+__device__ inline double pivot_rcp(double d) { return __drcp_rn(d); }
+__device__ inline float pivot_rcp(float d) { return 1.0f / d; }
 
 // element offset of tile (I, J), J >= F_I, of subdomain p
 __device__ inline int64_t tile_at(const EnvDev& E, int p, int I, int J) {
@@ -105,7 +96,7 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);  // X starts as the identity (zeros above)
   }
   __syncthreads();
-  if (tid == 0) dinv[0] = rcp_newton(A[0]);
+  if (tid == 0) dinv[0] = pivot_rcp(A[0]);
   __syncthreads();
   for (int c = 0; c < T64 - 1; ++c) {
     if (tid > c && tid < T64) lcol[tid] = A[tid * 65 + c] * dinv[c];
@@ -122,7 +113,7 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
         const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
         const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
         A[r * 65 + s2] = v;
-        if (e == 0) dinv[c + 1] = rcp_newton(v);  // entry (c+1, c+1): the next pivot is final
+        if (e == 0) dinv[c + 1] = pivot_rcp(v);  // entry (c+1, c+1): the next pivot is final
       } else {
         const int x = e - nA;  // x = rr (c+1) + j
         int rr = (int)((float)x * inv_w);
@@ -150,21 +141,28 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
 // Blocked form for a lone CTA (the tile steps of the coarsest block, whose
 // diagonal tiles form the critical path): four 16-column blocks K, each
 //   (a) its 16 x 16 diagonal block as above (one entry per thread per step),
-//       with the inverse X_KK built in the same sweep;
+//       with the inverse X_KK built in the same sweep.  A step reads column
+//       c and writes only columns > c, so one barrier per column suffices:
+//       every thread forms its own l_rc = A_rc / d_c (the same bits as a
+//       shared scaled column).  The step's critical path is the next pivot
+//       and its reciprocal; on GB300 an FP64 warp instruction holds its SM
+//       sub-partition's FP64 unit for ~64 cycles, so the pivot has a warp to
+//       itself (warp 7, whose sub-partition no other entry of (a) uses:
+//       the entries go to warps 0-2 and 4-5);
 //   (b) the panel W_rK = A_rK X_KK^T below it (W = L D), and L_rK = W_rK D_K^{-1};
 //   (c) the trailing update A_rs -= W_rK L_sK^T, c1 <= s <= r (16-long dot
 //       products in registers, one output entry each);
 // then L = W D^{-1}, and the off-diagonal blocks of X = L^{-1} block row by
 // block row: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.  Per column only the
 // short steps of (a) are sequential; everything else is a few wide phases.
-// smem: (64*65 + 128 + 48*17 + 16*49) elements of AT.
-constexpr int kDiagBlockedElems = 64 * 65 + 128 + 48 * 17 + 16 * 49;
+// smem: (64*65 + 64 + 48*17 + 16*49) elements of AT.
+constexpr int kDiagBlockedElems = 64 * 65 + 64 + 48 * 17 + 16 * 49;
 
 template <typename T, typename AT>
 __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
   constexpr int NB = 16;
-  AT* lcol = A + 64 * 65;  // [64] scaled column of the current step of (a)
-  AT* dinv = lcol + 64;    // [64] 1/d_c
+  static_assert(kDiagThreads == 256, "the entry-to-thread map of (a) assumes 8 warps");
+  AT* dinv = A + 64 * 65;  // [64] 1/d_c
   AT* Lp = dinv + 64;      // [48][17] L of the current panel
   AT* Tb = Lp + 48 * 17;   // [16][49] sum_K L_IK X_KJ of the current X block row
   const int tid = threadIdx.x;
@@ -174,34 +172,43 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
     A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
   }
   __syncthreads();
-  if (tid == 0) dinv[0] = rcp_newton(A[0]);
+  if (tid == 0) dinv[0] = pivot_rcp(A[0]);
   __syncthreads();
+  // (a)'s entry of this thread: 0 (the next pivot) on warp 7, 1..96 on
+  // warps 0-2, 97..136 on warps 4-5 (a step has at most 120 + 15 entries)
+  const int ea = tid == 224 ? 0 : (tid < 96 ? tid + 1 : (tid >= 128 && tid < 168 ? tid - 31 : -1));
   for (int K = 0; K < 4; ++K) {
     const int c0 = K * NB, c1 = c0 + NB;
     // (a) diagonal block: Schur complement inside the block and X_KK
     for (int c = c0; c < c1; ++c) {
-      if (tid > c && tid < c1) lcol[tid] = A[tid * 65 + c] * dinv[c];
-      __syncthreads();
       const int m = c1 - 1 - c, w = c - c0 + 1;
-      const int nA = m * (m + 1) / 2, nX = m * w;  // at most 120 + 15 entries
-      for (int e = tid; e < nA + nX; e += blockDim.x) {
-        if (e < nA) {
-          int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-          rr += ((rr + 1) * (rr + 2) / 2 <= e);
-          rr -= (rr * (rr + 1) / 2 > e);
-          const int r = c + 1 + rr, s2 = c + 1 + (e - rr * (rr + 1) / 2);
-          const AT v = fma(-lcol[r], A[s2 * 65 + c], A[r * 65 + s2]);
-          A[r * 65 + s2] = v;
-          if (e == 0) dinv[c + 1] = rcp_newton(v);
-        } else {
-          const int x = e - nA, rr = x / w;
-          const int j = c0 + (x - rr * w), r = c + 1 + rr;
-          const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
-          A[j * 65 + r] = fma(-lcol[r], xcj, A[j * 65 + r]);
-        }
+      const int nA = m * (m + 1) / 2, nX = m * w;
+      const int e = ea;
+      int r = 0, s2 = 0, j = 0;
+      if (e >= 0 && e < nA) {
+        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        rr += ((rr + 1) * (rr + 2) / 2 <= e);
+        rr -= (rr * (rr + 1) / 2 > e);
+        r = c + 1 + rr;
+        s2 = c + 1 + (e - rr * (rr + 1) / 2);
+      } else if (e >= nA && e < nA + nX) {
+        const int x = e - nA, rr = x / w;
+        j = c0 + (x - rr * w);
+        r = c + 1 + rr;
       }
-      __syncthreads();
+      __syncthreads();  // column c and d_c are final
+      if (e >= 0 && e < nA) {
+        const AT l = A[r * 65 + c] * dinv[c];
+        const AT v = fma(-l, A[s2 * 65 + c], A[r * 65 + s2]);
+        A[r * 65 + s2] = v;
+        if (e == 0) dinv[c + 1] = pivot_rcp(v);  // entry (c+1, c+1): the next pivot is final
+      } else if (e >= nA && e < nA + nX) {
+        const AT l = A[r * 65 + c] * dinv[c];
+        const AT xcj = (j == c) ? AT(1) : A[j * 65 + c];
+        A[j * 65 + r] = fma(-l, xcj, A[j * 65 + r]);
+      }
     }
+    __syncthreads();
     if (K == 3) break;
     // (b) panel below the block: W_rc = A_rc + sum_{c0 <= m < c} A_rm X_cm
     const int nr = 64 - c1;
@@ -255,7 +262,7 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
         }
         const AT v = A[r * 65 + s2] - ((a0 + a1) + (a2 + a3));
         A[r * 65 + s2] = v;
-        if (e == 0) dinv[c1] = rcp_newton(v);  // the next block's first pivot
+        if (e == 0) dinv[c1] = pivot_rcp(v);  // the next block's first pivot
       }
     }
     __syncthreads();
@@ -523,7 +530,10 @@ __device__ void factor_block(T* __restrict__ fac, const EnvDev& E, int p, AT* sm
   for (int k = 0; k < NT; ++k) {
     const int R = E.last[E.trow[p] + k];
     T* dt = fac + tile_at(E, p, k, k);
-    diag_tile<T, AT>(dt, sm, info);
+    // FP32 arithmetic: the blocked form (few index decodes, short sequential
+    // steps); FP64: the unblocked one, whose every step fills all the lanes
+    if constexpr (std::is_same<AT, float>::value) diag_tile_blocked<T, AT>(dt, sm, info);
+    else diag_tile<T, AT>(dt, sm, info);
     for (int i = k + 1; i <= R; ++i) panel_tile<T, AT>(dt, fac + tile_at(E, p, i, k), sm);
     for (int i = k + 1; i <= R; ++i)
       for (int j = k + 1; j <= i; ++j)
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(256, 4) k_ldlt_blocks_tc(float* __restrict__ f
     for (int k = 0; k < NT; ++k) {
       const int R = E.last[E.trow[p] + k];
       float* dt = fac + tile_at(E, p, k, k);
-      diag_tile<float, float>(dt, sm, info);
+      diag_tile_blocked<float, float>(dt, sm, info);
       for (int i = k + 1; i <= R; ++i) panel_tile<float, float>(dt, fac + tile_at(E, p, i, k), sm);
       if (R == k) continue;
       __syncthreads();
@@ -728,7 +738,7 @@ __device__ void diag_tiles2(double* __restrict__ t0, double* __restrict__ t1, do
   __syncthreads();
   if (tid < ntile) {
     double* A = tid ? S1 : S0;
-    A[64 * 65 + 128] = rcp_newton(A[0]);  // dinv[0]
+    A[64 * 65 + 128] = pivot_rcp(A[0]);  // dinv[0]
   }
   __syncthreads();
   for (int c = 0; c < T64; c += 2) {
@@ -749,7 +759,7 @@ __device__ void diag_tiles2(double* __restrict__ t0, double* __restrict__ t1, do
             // pivot d_c+1 after step c, formed by every thread the same way
             const double lp = A[c1 * 65 + c] * dinv[c];
             const double d1 = fma(-lp, A[c1 * 65 + c], A[c1 * 65 + c1]);
-            const double di1 = rcp_newton(d1);
+            const double di1 = pivot_rcp(d1);
             if (r > c1) {
               const double a1 = fma(-lc, A[c1 * 65 + c], A[r * 65 + c1]);
               A[r * 65 + c1] = a1;
@@ -821,7 +831,7 @@ __device__ void diag_tiles2(double* __restrict__ t0, double* __restrict__ t1, do
         const double v = fma(-f1[q], b1[q], fma(-f0[q], b0[q], av[q]));
         double* A = ((tsel >> q) & 1u) ? S1 : S0;
         A[idx[q]] = v;
-        if (idx[q] == (c + 2) * 65 + (c + 2)) A[64 * 65 + 128 + c + 2] = rcp_newton(v);  // next first pivot
+        if (idx[q] == (c + 2) * 65 + (c + 2)) A[64 * 65 + 128 + c + 2] = pivot_rcp(v);  // next first pivot
       }
     }
     __syncthreads();

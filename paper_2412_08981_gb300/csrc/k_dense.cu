@@ -138,6 +138,40 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
+// The off-diagonal 16 x 16 blocks of X = L^{-1} of a 64 x 64 diagonal tile in
+// shared memory (L strictly below the diagonal, the diagonal blocks X_KK^T
+// above it), block row by block row: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ,
+// as T_ij = L_ij + sum_{j < m < i0} L_im X_mj, then
+// X_ij = -(T_ij + sum_{i0 <= m < i} X_im T_mj).  X_ij is stored at A[j][i].
+// Tb: [16][49] elements.  Every thread of the block takes part.
+template <typename AT>
+__device__ void x_offdiag_blocks(AT* __restrict__ A, AT* __restrict__ Tb) {
+  constexpr int NB = 16;
+  const int tid = threadIdx.x;
+  for (int I = 1; I < 4; ++I) {
+    const int i0 = I * NB;
+    for (int e = tid; e < NB * i0; e += blockDim.x) {
+      const int i = i0 + e / i0, j = e % i0;
+      AT v = A[i * 65 + j], v2 = 0;
+      int mm = j + 1;
+      for (; mm + 1 < i0; mm += 2) {
+        v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
+        v2 = fma(A[i * 65 + mm + 1], A[j * 65 + mm + 1], v2);
+      }
+      if (mm < i0) v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
+      Tb[(i - i0) * 49 + j] = v + v2;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * i0; e += blockDim.x) {
+      const int i = i0 + e / i0, j = e % i0;
+      AT v = Tb[(i - i0) * 49 + j];
+      for (int mm = i0; mm < i; ++mm) v = fma(A[mm * 65 + i], Tb[(mm - i0) * 49 + j], v);
+      A[j * 65 + i] = -v;
+    }
+    __syncthreads();
+  }
+}
+
 // Blocked form for a lone CTA (the tile steps of the coarsest block, whose
 // diagonal tiles form the critical path): four 16-column blocks K, each
 //   (a) its 16 x 16 diagonal block as above (one entry per thread per step),
@@ -152,13 +186,16 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
 //   (b) the panel W_rK = A_rK X_KK^T below it (W = L D), and L_rK = W_rK D_K^{-1};
 //   (c) the trailing update A_rs -= W_rK L_sK^T, c1 <= s <= r (16-long dot
 //       products in registers, one output entry each);
-// then L = W D^{-1}, and the off-diagonal blocks of X = L^{-1} block row by
-// block row: X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.  Per column only the
-// short steps of (a) are sequential; everything else is a few wide phases.
+// then L = W D^{-1}, and (kXFull) the off-diagonal blocks of X = L^{-1}.
+// Without them the tile holds X's diagonal blocks only, which is all that
+// the blocked panel solve of the tile steps needs; k_ldlt_xfill adds the
+// rest once the level is factored, off the chain of diagonal tiles.  Per
+// column only the short steps of (a) are sequential; everything else is a
+// few wide phases.
 // smem: (64*65 + 64 + 48*17 + 16*49) elements of AT.
 constexpr int kDiagBlockedElems = 64 * 65 + 64 + 48 * 17 + 16 * 49;
 
-template <typename T, typename AT>
+template <typename T, typename AT, bool kXFull = true>
 __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int* __restrict__ info) {
   constexpr int NB = 16;
   static_assert(kDiagThreads == 256, "the entry-to-thread map of (a) assumes 8 warps");
@@ -276,29 +313,7 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
     if (c < r) A[r * 65 + c] *= dinv[c];
   }
   __syncthreads();
-  // off-diagonal blocks of X, block row I (X_ij stored at A[j][i])
-  for (int I = 1; I < 4; ++I) {
-    const int i0 = I * NB;
-    for (int e = tid; e < NB * i0; e += blockDim.x) {  // T_ij = L_ij + sum_{j < m < i0} L_im X_mj
-      const int i = i0 + e / i0, j = e % i0;
-      AT v = A[i * 65 + j], v2 = 0;
-      int mm = j + 1;
-      for (; mm + 1 < i0; mm += 2) {
-        v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
-        v2 = fma(A[i * 65 + mm + 1], A[j * 65 + mm + 1], v2);
-      }
-      if (mm < i0) v = fma(A[i * 65 + mm], A[j * 65 + mm], v);
-      Tb[(i - i0) * 49 + j] = v + v2;
-    }
-    __syncthreads();
-    for (int e = tid; e < NB * i0; e += blockDim.x) {  // X_ij = -(T_ij + sum_{i0 <= m < i} X_im T_mj)
-      const int i = i0 + e / i0, j = e % i0;
-      AT v = Tb[(i - i0) * 49 + j];
-      for (int mm = i0; mm < i; ++mm) v = fma(A[mm * 65 + i], Tb[(mm - i0) * 49 + j], v);
-      A[j * 65 + i] = -v;
-    }
-    __syncthreads();
-  }
+  if (kXFull) x_offdiag_blocks(A, Tb);
   for (int e = tid; e < TE; e += blockDim.x) tile[e] = (T)A[(e >> 6) * 65 + (e & 63)];
 }
 
@@ -309,7 +324,28 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   const int p = order[blockIdx.x];
-  diag_tile_blocked<T, AT>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
+  diag_tile_blocked<T, AT, false>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
+}
+
+// The off-diagonal blocks of X in every diagonal tile (block order[y], tile
+// x) of a level factored by the tile steps; only those entries are written.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_xfill(T* __restrict__ fac, EnvDev E,
+                                                    const int32_t* __restrict__ order) {
+  using AT = typename Acc<T>::type;
+  const int p = order[blockIdx.y], k = blockIdx.x;
+  if (k >= E.nt[p]) return;
+  extern __shared__ unsigned char smraw[];
+  AT* A = reinterpret_cast<AT*>(smraw);  // [64][65]
+  AT* Tb = A + 64 * 65;                   // [16][49]
+  T* tile = fac + tile_at(E, p, k, k);
+  for (int e = threadIdx.x; e < TE; e += blockDim.x) A[(e >> 6) * 65 + (e & 63)] = (AT)tile[e];
+  __syncthreads();
+  x_offdiag_blocks(A, Tb);
+  for (int e = threadIdx.x; e < TE; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    if ((r >> 4) < (c >> 4)) tile[e] = (T)A[r * 65 + c];
+  }
 }
 
 // ----------------------------------------------------------- panel solve
@@ -359,46 +395,60 @@ __device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, A
 
 // Multi-launch form (levels with few, large blocks, the coarsest chain):
 // every panel tile is split into kStepSplit CTAs of kStepRows rows, so that
-// a step spreads over more SMs.  Thread t owns row kStepRows*q + (t %
-// kStepRows) and the columns g and 63 - g, g = t / kStepRows (column c needs
-// the products over m <= c: the pair has 65 in all, the same for every
-// thread); the loop runs over [0, g] with both columns and (g, 63 - g] with
-// the second only, so no FMA is issued for an entry of X^T that is zero.
+// a step spreads over more SMs.  The diagonal tile holds X's diagonal
+// blocks only (its off-diagonal blocks come after the level is factored), so
+// W = A X^T is formed as the blocked solve W L^T = A, block column by block
+// column: W_J = (A_J - sum_{K<J} W_K L_JK^T) X_JJ^T.  A thread pair shares
+// one output (r, c) of block column J: each sums half of the products (the
+// two halves of n < 16J, then the even and odd m of X_JJ) and the pair adds
+// its halves with a shuffle.  Then L_ik = W D^{-1}.
 constexpr int kStepSplit = 8, kStepRows = 64 / kStepSplit;
+constexpr int kPanelElems = kStepRows * 65 + 64 * 65 + 64 + kStepRows * 17 + kStepRows * 65;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev E,
                                                     const int32_t* __restrict__ order, int k, int off) {
   using AT = typename Acc<T>::type;
+  static_assert(kStepRows * 16 * 2 == 256, "a thread pair per output of a block column");
   const int p = order[blockIdx.y];
   const int i = k + 1 + off + blockIdx.x / kStepSplit, q = blockIdx.x % kStepSplit;
   if (i > E.last[E.trow[p] + k]) return;
   extern __shared__ unsigned char smraw[];
-  AT* A = reinterpret_cast<AT*>(smraw);   // [kStepRows][65] rows of the panel tile
-  AT* Xt = A + kStepRows * 65;            // [64][64] X^T (upper, unit diagonal)
-  AT* Dinv = Xt + 64 * 64;                // [64]
+  AT* A = reinterpret_cast<AT*>(smraw);  // [kStepRows][65] rows of the panel tile
+  AT* Lk = A + kStepRows * 65;           // [64][65] diagonal tile k: L below, X_JJ^T in the blocks above
+  AT* Dinv = Lk + 64 * 65;               // [64]
+  AT* Tt = Dinv + 64;                    // [kStepRows][17] T of the current block column
+  AT* Wb = Tt + kStepRows * 17;          // [kStepRows][65] W, block column by block column
   const T* dtile = fac + tile_at(E, p, k, k);
   T* ptile = fac + tile_at(E, p, i, k) + q * kStepRows * 64;
   const int tid = threadIdx.x;
   for (int e = tid; e < TE; e += blockDim.x) {
     const int r = e >> 6, c = e & 63;
-    Xt[e] = (r < c) ? (AT)dtile[e] : (r == c ? AT(1) : AT(0));
+    Lk[r * 65 + c] = (AT)dtile[e];
     if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
     if (e < kStepRows * 64) A[r * 65 + c] = (AT)ptile[e];
   }
   __syncthreads();
-  const int r = tid % kStepRows, g = tid / kStepRows;  // g = 0 .. 31
-  const int c1 = 63 - g;
-  AT w0 = 0, w1 = 0;
-  int m = 0;
-  for (; m <= g; ++m) {
-    const AT a = A[r * 65 + m];
-    w0 = fma(a, Xt[m * 64 + g], w0);
-    w1 = fma(a, Xt[m * 64 + c1], w1);
+  const int o = tid >> 1, h = tid & 1;  // output o of the block column, half h of its sums
+  const int r = o >> 4, cc = o & 15;
+  for (int J = 0; J < 4; ++J) {
+    const int c = 16 * J + cc;
+    AT t = 0;  // sum_{n < 16J} W_rn L_cn, half h
+    for (int n = 8 * J * h; n < 8 * J * (h + 1); ++n) t = fma(Wb[r * 65 + n], Lk[c * 65 + n], t);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    if (h == 0) Tt[r * 17 + cc] = A[r * 65 + c] - t;
+    __syncthreads();
+    AT w = 0;  // sum_{16J <= m <= c} T_rm X_cm (X_cc = 1, X_cm at Lk[m][c]), the m of parity h
+    for (int mm = h; mm <= cc; mm += 2)
+      w = fma(Tt[r * 17 + mm], mm == cc ? AT(1) : Lk[(16 * J + mm) * 65 + c], w);
+    w += __shfl_xor_sync(0xffffffffu, w, 1);
+    if (h == 0) Wb[r * 65 + c] = w;
+    __syncthreads();
   }
-  for (; m <= c1; ++m) w1 = fma(A[r * 65 + m], Xt[m * 64 + c1], w1);
-  ptile[r * 64 + g] = (T)(w0 * Dinv[g]);
-  ptile[r * 64 + c1] = (T)(w1 * Dinv[c1]);
+  for (int e = tid; e < kStepRows * 64; e += blockDim.x) {
+    const int rr = e >> 6, c = e & 63;
+    ptile[e] = (T)(Wb[rr * 65 + c] * Dinv[c]);
+  }
 }
 
 // -------------------------------------------------------- trailing update
@@ -1277,7 +1327,7 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
                        int off, int max_rows, cudaStream_t s) {
   if (nactive <= 0 || max_rows <= 0) return;
   using AT = typename Acc<T>::type;
-  size_t smem = (kStepRows * 65 + 64 * 64 + 64) * sizeof(AT);
+  size_t smem = (size_t)kPanelElems * sizeof(AT);
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1298,6 +1348,18 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   k_ldlt_trail<T><<<dim3(kStepSplit * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k, pair0);
 }
 
+
+template <typename T>
+void launch_ldlt_xfill(T* fac, const EnvDev& E, const int32_t* order, int nblocks, int max_nt, cudaStream_t s) {
+  if (nblocks <= 0 || max_nt <= 0) return;
+  using AT = typename Acc<T>::type;
+  size_t smem = (size_t)(64 * 65 + 16 * 49) * sizeof(AT);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_ldlt_xfill<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  k_ldlt_xfill<T><<<dim3(max_nt, nblocks), 256, smem, s>>>(fac, E, order);
+}
 
 // CTAs of a 256-thread persistent kernel resident per SM at once: limited by
 // its shared memory (with the carveout set to the maximum) and its registers.
@@ -1392,6 +1454,7 @@ int ldlt_blocks_tc_per_sm() {
                                      cudaStream_t);                                              \
   template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int, int,      \
                                      cudaStream_t);                                              \
+  template void launch_ldlt_xfill<T>(T*, const EnvDev&, const int32_t*, int, int, cudaStream_t); \
   template void launch_ldlt_blocks_batch<T>(const BlockItem*, const int32_t*, const int32_t*, int,    \
                                             cudaStream_t);                                        \
   template int ldlt_blocks_batch_per_sm<T>();                                                     \

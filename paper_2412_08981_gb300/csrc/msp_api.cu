@@ -642,6 +642,11 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
   }
   cudaEventRecord(ev_bulk, sb);  // join the bulk stream back (always: graph capture needs it)
   cudaStreamWaitEvent(s, ev_bulk, 0);
+  {
+    ProfScope ps(I->prof, PK_LDLT_DIAG, s);
+    launch_ldlt_xfill<T>(fac, D.env, D.sub_order, D.active[0], D.max_nt, s);
+    ps.account(0, 0);
+  }
 }
 
 // ILU(p) factors of level l in T: A's lower triangle into [L | D], the

@@ -94,6 +94,11 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
 template <typename T>
 void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                        int pair0, int max_pairs, cudaStream_t s);
+// after the tile steps of a level: the off-diagonal blocks of X in every
+// diagonal tile (the diagonal kernel of the steps forms X's diagonal blocks
+// only), over the first nblocks blocks of `order`
+template <typename T>
+void launch_ldlt_xfill(T* fac, const EnvDev& E, const int32_t* order, int nblocks, int max_nt, cudaStream_t s);
 // The whole L D L^T of many blocks in one persistent launch: CTA b factors
 // cta_list[cta_ptr[b] .. cta_ptr[b+1]) through every tile step.
 template <typename T>

@@ -68,6 +68,41 @@ __global__ void k_scatter(const int64_t* __restrict__ pos, const int32_t* __rest
   fac[pos[e]] = (T)(q >= 0 ? val[q] : 1.0);
 }
 
+// Reads N elements of T (N a multiple of 16 bytes' worth; src 16-byte
+// aligned) with 16-byte loads, up to four of a thread's loads in flight
+// together, and hands each element to f(e, value), e = 0 .. N-1.  The tile
+// loops of the factorisation otherwise wait out one L2 round trip per
+// element in turn.  Every thread of the 256-thread block takes part.  Plain
+// (coherent) loads: the factors are rewritten within the same launch.
+template <typename T, int N, typename F>
+__device__ __forceinline__ void read_elems(const T* src, F&& f) {
+  constexpr int V = 16 / sizeof(T);
+  constexpr int NVEC = N / V;
+  constexpr int PER = (NVEC + 255) / 256;
+  constexpr int R = PER < 4 ? PER : 4;
+  static_assert(N % V == 0, "whole 16-byte vectors");
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const Vec* sv = reinterpret_cast<const Vec*>(src);
+#pragma unroll
+  for (int r0 = 0; r0 < PER; r0 += R) {
+    Vec v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = threadIdx.x + 256 * (r0 + q);
+      if (NVEC % 256 == 0 || i < NVEC) v[q] = sv[i];
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = threadIdx.x + 256 * (r0 + q);
+      if (NVEC % 256 == 0 || i < NVEC) {
+        const T* x = reinterpret_cast<const T*>(&v[q]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) f(i * V + k, x[k]);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------- diagonal tile LDL^T
 // Factors one diagonal tile in shared memory, computing in the factor's
 // precision: unblocked right-looking elimination of the lower triangle with
@@ -91,10 +126,10 @@ __device__ void diag_tile(T* __restrict__ tile, AT* __restrict__ A, int* __restr
   AT* dinv = lcol + 64;    // [64] 1/d_c, formed once each, by the thread finishing d_c
   const int tid = threadIdx.x;
   __syncthreads();  // the shared buffer may still be read by a previous phase
-  for (int e = tid; e < TE; e += blockDim.x) {
-    int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);  // X starts as the identity (zeros above)
-  }
+  read_elems<T, TE>(tile, [&](int e, T v) {
+    const int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (c <= r) ? (AT)v : AT(0);  // X starts as the identity (zeros above)
+  });
   __syncthreads();
   if (tid == 0) dinv[0] = pivot_rcp(A[0]);
   __syncthreads();
@@ -204,10 +239,10 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
   AT* Tb = Lp + 48 * 17;   // [16][49] sum_K L_IK X_KJ of the current X block row
   const int tid = threadIdx.x;
   __syncthreads();
-  for (int e = tid; e < TE; e += blockDim.x) {
-    int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (c <= r) ? (AT)tile[e] : AT(0);
-  }
+  read_elems<T, TE>(tile, [&](int e, T v) {
+    const int r = e >> 6, c = e & 63;
+    A[r * 65 + c] = (c <= r) ? (AT)v : AT(0);
+  });
   __syncthreads();
   if (tid == 0) dinv[0] = pivot_rcp(A[0]);
   __syncthreads();
@@ -339,7 +374,7 @@ __global__ void __launch_bounds__(256) k_ldlt_xfill(T* __restrict__ fac, EnvDev 
   AT* A = reinterpret_cast<AT*>(smraw);  // [64][65]
   AT* Tb = A + 64 * 65;                   // [16][49]
   T* tile = fac + tile_at(E, p, k, k);
-  for (int e = threadIdx.x; e < TE; e += blockDim.x) A[(e >> 6) * 65 + (e & 63)] = (AT)tile[e];
+  read_elems<T, TE>(tile, [&](int e, T v) { A[(e >> 6) * 65 + (e & 63)] = (AT)v; });
   __syncthreads();
   x_offdiag_blocks(A, Tb);
   for (int e = threadIdx.x; e < TE; e += blockDim.x) {
@@ -359,13 +394,12 @@ __device__ void panel_tile(const T* __restrict__ dtile, T* __restrict__ ptile, A
   AT* Dinv = Xt + 64 * 64;  // [64]
   const int tid = threadIdx.x;
   __syncthreads();
-  for (int e = tid; e < TE; e += blockDim.x) {
-    int r = e >> 6, c = e & 63;
-    A[r * 65 + c] = (AT)ptile[e];
-    AT xv = (r < c) ? (AT)dtile[e] : (r == c ? AT(1) : AT(0));
-    Xt[e] = xv;
-    if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
-  }
+  read_elems<T, TE>(ptile, [&](int e, T v) { A[(e >> 6) * 65 + (e & 63)] = (AT)v; });
+  read_elems<T, TE>(dtile, [&](int e, T v) {
+    const int r = e >> 6, c = e & 63;
+    Xt[e] = (r < c) ? (AT)v : (r == c ? AT(1) : AT(0));
+    if (r == c) Dinv[r] = AT(1) / (AT)v;
+  });
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
   const int r0 = lane, r1 = lane + 32;
@@ -422,12 +456,12 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
   const T* dtile = fac + tile_at(E, p, k, k);
   T* ptile = fac + tile_at(E, p, i, k) + q * kStepRows * 64;
   const int tid = threadIdx.x;
-  for (int e = tid; e < TE; e += blockDim.x) {
+  read_elems<T, TE>(dtile, [&](int e, T v) {
     const int r = e >> 6, c = e & 63;
-    Lk[r * 65 + c] = (AT)dtile[e];
-    if (r == c) Dinv[r] = AT(1) / (AT)dtile[e];
-    if (e < kStepRows * 64) A[r * 65 + c] = (AT)ptile[e];
-  }
+    Lk[r * 65 + c] = (AT)v;
+    if (r == c) Dinv[r] = AT(1) / (AT)v;
+  });
+  read_elems<T, kStepRows * 64>(ptile, [&](int e, T v) { A[(e >> 6) * 65 + (e & 63)] = (AT)v; });
   __syncthreads();
   const int o = tid >> 1, h = tid & 1;  // output o of the block column, half h of its sums
   const int r = o >> 4, cc = o & 15;
@@ -471,12 +505,11 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
   AT* Lt = Wt + 64 * LD; // [64 m][LD] = L_jk[c][m]
   const int tid = threadIdx.x;
   __syncthreads();
-  for (int e = tid; e < TE; e += blockDim.x) {
-    int r = e >> 6, m = e & 63;
-    AT d = (AT)dt[m * 65];
-    Wt[m * LD + r] = (AT)li[e] * d;
-    Lt[m * LD + r] = (AT)lj[e];
-  }
+  read_elems<T, TE>(li, [&](int e, T v) {
+    const int r = e >> 6, m = e & 63;
+    Wt[m * LD + r] = (AT)v * (AT)dt[m * 65];
+  });
+  read_elems<T, TE>(lj, [&](int e, T v) { Lt[(e & 63) * LD + (e >> 6)] = (AT)v; });
   __syncthreads();
   // 4x4 output blocks: all 256 of a general pair; for a diagonal pair only the
   // 136 blocks on or below the diagonal, numbered densely so that they fill
@@ -545,11 +578,11 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
   const T* lj = fac + tile_at(E, p, j, k);
   T* out = fac + tile_at(E, p, i, j) + q * kStepRows * 64;
   const int tid = threadIdx.x;
-  for (int e = tid; e < TE; e += blockDim.x) {
+  read_elems<T, TE>(lj, [&](int e, T v) { Lt[(e & 63) * LD + (e >> 6)] = (AT)v; });
+  read_elems<T, kStepRows * 64>(li, [&](int e, T v) {
     const int r = e >> 6, m = e & 63;
-    Lt[m * LD + r] = (AT)lj[e];
-    if (e < kStepRows * 64) Wt[m * kStepRows + r] = (AT)li[e] * (AT)dt[m * 65];
-  }
+    Wt[m * kStepRows + r] = (AT)v * (AT)dt[m * 65];
+  });
   __syncthreads();
   const int r = tid >> 5, c0 = (tid & 31) * 2;
   const int rg = kStepRows * q + r;  // row inside the tile
@@ -592,8 +625,15 @@ __device__ void factor_block(T* __restrict__ fac, const EnvDev& E, int p, AT* sm
   }
 }
 
+// CTAs per SM the whole-block kernels are built for (their registers are
+// capped to fit): FP32 arithmetic four, FP64 three.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev E,
+struct LevelCtas {
+  static constexpr int value = sizeof(T) == 4 ? 4 : 3;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, LevelCtas<T>::value) k_ldlt_blocks(T* __restrict__ fac, EnvDev E,
                                                      const int32_t* __restrict__ cta_ptr,
                                                      const int32_t* __restrict__ cta_list,
                                                      int* __restrict__ info) {
@@ -608,7 +648,7 @@ __global__ void __launch_bounds__(256) k_ldlt_blocks(T* __restrict__ fac, EnvDev
 // the instance's status word.  Each block's arithmetic is exactly that of
 // k_ldlt_blocks.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ldlt_blocks_batch(const BlockItem* __restrict__ items,
+__global__ void __launch_bounds__(256, LevelCtas<T>::value) k_ldlt_blocks_batch(const BlockItem* __restrict__ items,
                                                            const int32_t* __restrict__ cta_ptr,
                                                            const int32_t* __restrict__ cta_list) {
   using AT = typename Acc<T>::type;
@@ -645,18 +685,24 @@ constexpr int kTcBarOff = kTcSmem - 64;       // mbarrier + TMEM base address sl
 // lane / 4, column pair lane % 4): 32 distinct banks.
 __device__ void stage_bf16(unsigned char* slab, int row0, const float* __restrict__ tile,
                            const float* __restrict__ scale) {
-  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
-    const int lane = e & 31, blk = e >> 5;
+  constexpr int kIt = 64 * 32 / 256;  // 256 threads; all of a thread's loads in flight together
+  float2 v[kIt];
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int e = threadIdx.x + 256 * it, lane = e & 31, blk = e >> 5;
     const int r = (blk >> 3) * 8 + (lane >> 2), k = (blk & 7) * 8 + (lane & 3) * 2;
-    float2 v = make_float2(0.f, 0.f);
-    if (tile) {
-      v = *reinterpret_cast<const float2*>(tile + r * 64 + k);
-      if (scale) {
-        v.x *= scale[k];
-        v.y *= scale[k + 1];
-      }
+    v[it] = tile ? *reinterpret_cast<const float2*>(tile + r * 64 + k) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int e = threadIdx.x + 256 * it, lane = e & 31, blk = e >> 5;
+    const int r = (blk >> 3) * 8 + (lane >> 2), k = (blk & 7) * 8 + (lane & 3) * 2;
+    if (tile && scale) {
+      v[it].x *= scale[k];
+      v[it].y *= scale[k + 1];
     }
-    *reinterpret_cast<__nv_bfloat162*>(slab + tc::kmajor_offset(row0 + r, k)) = __floats2bfloat162_rn(v.x, v.y);
+    *reinterpret_cast<__nv_bfloat162*>(slab + tc::kmajor_offset(row0 + r, k)) =
+        __floats2bfloat162_rn(v[it].x, v[it].y);
   }
 }
 

@@ -245,22 +245,39 @@ __global__ void k_load_vector(const double* __restrict__ xyz, const uint8_t* __r
   b[i] = s;
 }
 
-__global__ void k_coefficient(const double* __restrict__ cen, int m, int kind,
-                              const double* __restrict__ mu, const int32_t* __restrict__ wave,
-                              double scale, double* __restrict__ k) {
+// The parameter-independent part of the coefficient, once per hierarchy:
+// cw[8e + j] = cos(pi a_j . c_e) at the centroid c_e of tet e.  Per
+// parameter vector only the eight products with mu and one exp remain (FP64
+// cos is ~35 FP64-pipe instructions, so eight per tet per solve cost more
+// than the rest of the assembly).
+__global__ void k_coefficient_basis(const double* __restrict__ cen, int m, const int32_t* __restrict__ wave,
+                                    double* __restrict__ cw) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  double x = cen[3 * (int64_t)e], y = cen[3 * (int64_t)e + 1], z = cen[3 * (int64_t)e + 2];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    double ax = wave[3 * j] * x + wave[3 * j + 1] * y + wave[3 * j + 2] * z;
+    cw[8 * (int64_t)e + j] = cos(kPi * ax);
+  }
+}
+
+// k_e = exp(scale sum_j (mu_j / 2) cos(pi a_j . c_e)), the sum in ascending j
+// (or 1).  (mu_j * 0.5) is exact, so this is the direct evaluation bit for bit.
+__global__ void k_coefficient(const double* __restrict__ cw, int m, int kind,
+                              const double* __restrict__ mu, double scale, double* __restrict__ k) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   if (kind == 0) {
     k[e] = 1.0;
     return;
   }
-  double x = cen[3 * (int64_t)e], y = cen[3 * (int64_t)e + 1], z = cen[3 * (int64_t)e + 2];
+  const double2* c2 = reinterpret_cast<const double2*>(cw + 8 * (int64_t)e);
+  const double2 a = c2[0], b = c2[1], c = c2[2], d = c2[3];
+  const double cj[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
   double s = 0.0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    double ax = wave[3 * j] * x + wave[3 * j + 1] * y + wave[3 * j + 2] * z;
-    s += mu[j] * 0.5 * cos(kPi * ax);
-  }
+  for (int j = 0; j < 8; ++j) s += mu[j] * 0.5 * cj[j];
   k[e] = exp(scale * s);
 }
 
@@ -652,9 +669,13 @@ void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* di
                                                lam, mu, b);
 }
 
-void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
-                        const int32_t* wave24, double scale, double* k, cudaStream_t s) {
-  if (m > 0) k_coefficient<<<nblk(m, 256), 256, 0, s>>>(cen, m, coef_kind, mu8, wave24, scale, k);
+void launch_coefficient_basis(const double* cen, int m, const int32_t* wave24, double* cw, cudaStream_t s) {
+  if (m > 0) k_coefficient_basis<<<nblk(m, 256), 256, 0, s>>>(cen, m, wave24, cw);
+}
+
+void launch_coefficient(const double* cw, int m, int coef_kind, const double* mu8, double scale, double* k,
+                        cudaStream_t s) {
+  if (m > 0) k_coefficient<<<nblk(m, 256), 256, 0, s>>>(cw, m, coef_kind, mu8, scale, k);
 }
 
 void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,

@@ -117,6 +117,7 @@ struct DevLevel {
   int32_t* dir_list = nullptr;
   int ndir = 0;
   double *xyz = nullptr, *S = nullptr, *vol = nullptr, *cen = nullptr;
+  double* cwave = nullptr;  // [m][8] cos(pi a_j . c_e) of the cosine coefficient (set-up)
   int32_t* tets = nullptr;
   double* b = nullptr;  // load vector
   // subdomains
@@ -317,6 +318,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   D.S = A.alloc<double>((size_t)H.m * H.nslot);
   D.vol = A.alloc<double>(H.m);
   D.cen = A.alloc<double>((size_t)H.m * 3);
+  if (h->opt.coef_kind == MSP_K_COSEXP) D.cwave = A.alloc<double>((size_t)H.m * 8);
   D.b = A.alloc<double>(H.n);
   D.nsub = H.nsub;
   D.sub_ptr = A.upload(H.sub_ptr);
@@ -481,6 +483,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
   // element: P1, elasticity, P2, or the P2-P1 pair (whose coupling rides in `lam`)
   const int kind = H.fields == 3 ? 1 : (H.p2 ? (H.nloc == 14 ? 3 : 2) : 0);
   launch_tet_geometry(D.xyz, D.tets, D.m, kind, kind == 3 ? h->opt.coupling : lam, mu, D.S, D.vol, D.cen, bad, s);
+  if (D.cwave) launch_coefficient_basis(D.cen, D.m, h->wave, D.cwave, s);
   launch_load_vector(D.xyz, D.dir, D.diag, D.cptr, D.contrib, D.vol, D.n, h->opt.load_kind, H.fields,
                      H.nslot, lam, mu, D.b, s);
   int hbad = 0;
@@ -550,11 +553,11 @@ int assemble_all(msp_instance* I) {
   for (size_t l = 0; l < h->dev.size(); ++l) {
     DevLevel& D = h->dev[l];
     ProfScope ps(I->prof, PK_ASSEMBLE, s, 2);
-    launch_coefficient(D.cen, D.m, h->opt.coef_kind, I->mu, h->wave, h->opt.coef_scale, I->k[l], s);
+    launch_coefficient(D.cwave, D.m, h->opt.coef_kind, I->mu, h->opt.coef_scale, I->k[l], s);
     launch_assemble(D.cptr, D.contrib, D.nzflag, I->k[l], D.S, D.nnz,
                     h->host[l].nslot, I->val[l], s);
     ps.account((double)D.nnz * 8 + (double)D.nnz * 5 + (double)h->host[l].contrib.size() * 12 +
-                   (double)D.m * 32,
+                   (double)D.m * (D.cwave ? 72 : 8),
                (double)h->host[l].contrib.size() * 2);
   }
   MSP_CUDA(cudaGetLastError());

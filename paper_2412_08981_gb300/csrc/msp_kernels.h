@@ -25,9 +25,11 @@ void launch_load_vector(const double* xyz, const uint8_t* dir, const int32_t* di
                         const int32_t* cptr, const int32_t* contrib, const double* vol, int n,
                         int load_kind, int fields, int ns, double lam, double mu, double* b,
                         cudaStream_t s);
-// k_e = exp(s * sum_j mu_j 0.5 cos(pi a_j . c_e))  (or 1)
-void launch_coefficient(const double* cen, int m, int coef_kind, const double* mu8,
-                        const int32_t* wave24, double scale, double* k, cudaStream_t s);
+// cw[8e + j] = cos(pi a_j . c_e), once per hierarchy (cosine coefficient)
+void launch_coefficient_basis(const double* cen, int m, const int32_t* wave24, double* cw, cudaStream_t s);
+// k_e = exp(s * sum_j mu_j 0.5 cw[8e + j])  (or 1; cw unused)
+void launch_coefficient(const double* cw, int m, int coef_kind, const double* mu8, double scale, double* k,
+                        cudaStream_t s);
 // val[q] = sum_{c in contrib(q)} k[c/ns] * S[c]  (ascending e), Dirichlet flags
 void launch_assemble(const int32_t* cptr, const int32_t* contrib, const uint8_t* nzflag,
                      const double* k, const double* S, int64_t nnz, int ns, double* val, cudaStream_t s);

@@ -263,7 +263,7 @@ __global__ void k_coefficient_basis(const double* __restrict__ cen, int m, const
 }
 
 // k_e = exp(scale sum_j (mu_j / 2) cos(pi a_j . c_e)), the sum in ascending j
-// (or 1).  (mu_j * 0.5) is exact, so this is the direct evaluation bit for bit.
+// (or 1): the terms and their order of evaluating the cosines in place.
 __global__ void k_coefficient(const double* __restrict__ cw, int m, int kind,
                               const double* __restrict__ mu, double scale, double* __restrict__ k) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;

@@ -177,6 +177,31 @@ def make_oracle(levels, w):
                          wave=syn.wave_vectors(), scale=w["scale"], load=w["load"])
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or on Arm the
+    implementer and part numbers), with the machine type."""
+    import platform
+    name, impl, part = None, None, None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and name is None:
+                    name = v
+                elif k == "CPU implementer" and impl is None:
+                    impl = v
+                elif k == "CPU part" and part is None:
+                    part = v
+    except OSError:
+        pass
+    if name:
+        return f"{name} ({platform.machine()})"
+    if impl or part:
+        return f"{platform.machine()}, CPU implementer {impl}, part {part}"
+    return platform.machine()
+
+
 def cpu_baseline(o, levels, w, mu, iters, sample, slice_index=0):
     """The oracle, as it stands, on a bounded sample of one solve of the workload.
 
@@ -247,7 +272,7 @@ def cpu_baseline(o, levels, w, mu, iters, sample, slice_index=0):
     if omp:
         cores = int(omp)
     return {"value": 1.0 / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "seconds_per_solve": t_solve,
+            "cpu_model": cpu_model(), "seconds_per_solve": t_solve,
             "extrapolated": {"fine_subdomains_timed": hi - lo, "fine_subdomains": nsub0,
                              "scale": round(scale, 3), "slice": [lo, hi]},
             "sample": (f"one solve of the workload: assembly + coarser-level and coarsest LU in "

@@ -103,6 +103,15 @@ __device__ __forceinline__ void read_elems(const T* src, F&& f) {
   }
 }
 
+// Programmatic dependent launch between the tile-step kernels of a chain
+// (launched with the programmatic-serialisation attribute on one stream):
+// a kernel lets its successor launch at once (step_release) and waits for
+// its predecessor's completion and memory before its first read
+// (step_acquire; a no-op without such a predecessor), so that a launch's
+// set-up overlaps the previous step instead of following it.
+__device__ __forceinline__ void step_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void step_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------- diagonal tile LDL^T
 // Factors one diagonal tile in shared memory, computing in the factor's
 // precision: unblocked right-looking elimination of the lower triangle with
@@ -358,6 +367,8 @@ __global__ void __launch_bounds__(256) k_ldlt_diag(T* __restrict__ fac, EnvDev E
                                                    int* __restrict__ info) {
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
+  step_release();
+  step_acquire();
   const int p = order[blockIdx.x];
   diag_tile_blocked<T, AT, false>(fac + tile_at(E, p, k, k), reinterpret_cast<AT*>(smraw), info);
 }
@@ -444,6 +455,8 @@ __global__ void __launch_bounds__(256) k_ldlt_panel(T* __restrict__ fac, EnvDev 
                                                     const int32_t* __restrict__ order, int k, int off) {
   using AT = typename Acc<T>::type;
   static_assert(kStepRows * 16 * 2 == 256, "a thread pair per output of a block column");
+  step_release();
+  step_acquire();
   const int p = order[blockIdx.y];
   const int i = k + 1 + off + blockIdx.x / kStepSplit, q = blockIdx.x % kStepSplit;
   if (i > E.last[E.trow[p] + k]) return;
@@ -561,6 +574,8 @@ __global__ void __launch_bounds__(256) k_ldlt_trail(T* __restrict__ fac, EnvDev 
                                                     const int32_t* __restrict__ order, int k, int pair0) {
   using AT = typename Acc<T>::type;
   static_assert(kStepRows * 32 == 256, "one warp per output row");
+  step_release();
+  step_acquire();
   const int p = order[blockIdx.y];
   const int rem = E.last[E.trow[p] + k] - k;
   const int pair = pair0 + blockIdx.x / kStepSplit, q = blockIdx.x % kStepSplit;
@@ -1355,6 +1370,23 @@ void launch_extract(const int64_t* ext_pos, const int32_t* ext_nz, int64_t nent,
   if (nent > 0) k_scatter<T><<<nblk(nent, 256), 256, 0, s>>>(ext_pos, ext_nz, val, nent, fac);
 }
 
+// Launch with programmatic stream serialisation (the kernels order their
+// reads behind their predecessor with step_acquire).
+template <typename... KArgs, typename... Args>
+void launch_step(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T>
 void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive, int k,
                       int* info, cudaStream_t s) {
@@ -1365,7 +1397,7 @@ void launch_ldlt_diag(T* fac, const EnvDev& E, const int32_t* order, int nactive
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_diag<T><<<nactive, 256, smem, s>>>(fac, E, order, k, info);
+  launch_step(k_ldlt_diag<T>, dim3(nactive), smem, s, fac, E, order, k, info);
 }
 
 template <typename T>
@@ -1378,7 +1410,7 @@ void launch_ldlt_panel(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_panel<T><<<dim3(kStepSplit * max_rows, nactive), 256, smem, s>>>(fac, E, order, k, off);
+  launch_step(k_ldlt_panel<T>, dim3(kStepSplit * max_rows, nactive), smem, s, fac, E, order, k, off);
 }
 
 template <typename T>
@@ -1391,7 +1423,7 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_ldlt_trail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  k_ldlt_trail<T><<<dim3(kStepSplit * max_pairs, nactive), 256, smem, s>>>(fac, E, order, k, pair0);
+  launch_step(k_ldlt_trail<T>, dim3(kStepSplit * max_pairs, nactive), smem, s, fac, E, order, k, pair0);
 }
 
 

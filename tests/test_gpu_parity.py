@@ -132,6 +132,32 @@ def test_subdomain_factors(case, P):
             assert np.linalg.norm(Lg @ np.diag(dg) @ Lg.T - A) <= 1e-13 * np.linalg.norm(A)
 
 
+def test_diagonal_tiles_hold_the_inverse(case, P):
+    """Every diagonal tile of sampled blocks of every level stores X^T above
+    its diagonal, X the inverse of the tile's unit lower factor (the solves
+    multiply by it): X L_II = I.  On the tile-step levels (the coarsest
+    block, and levels with few blocks) X's diagonal 16 x 16 blocks come from
+    the diagonal kernel and the rest from the fill launch after the steps."""
+    T = P.msp.MSP_TILE
+    for l in range(len(case.levels)):
+        coarse = l == len(case.levels) - 1
+        ns = 1 if coarse else case.o.get("n_subs", l)
+        for p in sorted(set([0, ns - 1])):
+            sub = -1 if coarse else p
+            flat = case.inst.array(l, "factor", sub)
+            first = P.msp.tile_first_of(case.h, l, sub)
+            t = 0
+            for I in range(len(first)):
+                t += I - int(first[I])  # the tiles left of the diagonal
+                tile = flat[t * T * T:(t + 1) * T * T].reshape(T, T)
+                t += 1
+                Lii = np.tril(tile, -1) + np.eye(T)
+                X = np.triu(tile, 1).T + np.eye(T)
+                err = np.max(np.abs(X @ Lii - np.eye(T)))
+                assert err <= 1e-12 * max(1.0, np.max(np.abs(X))) * max(1.0, np.max(np.abs(Lii))), (l, p, I, err)
+            assert t * T * T == flat.size
+
+
 def test_ras_and_coarse_solve(case, P):
     rng = np.random.default_rng(2)
     m = P.msp

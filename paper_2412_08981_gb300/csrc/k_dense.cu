@@ -256,8 +256,22 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
   if (tid == 0) dinv[0] = pivot_rcp(A[0]);
   __syncthreads();
   // (a)'s entry of this thread: 0 (the next pivot) on warp 7, 1..96 on
-  // warps 0-2, 97..136 on warps 4-5 (a step has at most 120 + 15 entries)
+  // warps 0-2, 97..136 on warps 4-5 (a step has at most 120 + 15 entries).
+  // A triangle entry e of step c is (c + 1 + rr, c + 1 + off) with (rr, off)
+  // a function of e alone, so it is decoded once; likewise (c)'s entries
+  // e = tid + 256 k (at most 1176 of them: five per thread), packed rr << 8 | off.
   const int ea = tid == 224 ? 0 : (tid < 96 ? tid + 1 : (tid >= 128 && tid < 168 ? tid - 31 : -1));
+  auto tri = [](int e) {
+    int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    rr += ((rr + 1) * (rr + 2) / 2 <= e);
+    rr -= (rr * (rr + 1) / 2 > e);
+    return (rr << 8) | (e - rr * (rr + 1) / 2);
+  };
+  const int ea_tri = ea >= 0 ? tri(ea) : 0;
+  constexpr int kTrailPer = (48 * 49 / 2 + kDiagThreads - 1) / kDiagThreads;
+  int tc_tri[kTrailPer];
+#pragma unroll
+  for (int k = 0; k < kTrailPer; ++k) tc_tri[k] = tri(tid + kDiagThreads * k);
   for (int K = 0; K < 4; ++K) {
     const int c0 = K * NB, c1 = c0 + NB;
     // (a) diagonal block: Schur complement inside the block and X_KK
@@ -267,11 +281,8 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
       const int e = ea;
       int r = 0, s2 = 0, j = 0;
       if (e >= 0 && e < nA) {
-        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-        rr += ((rr + 1) * (rr + 2) / 2 <= e);
-        rr -= (rr * (rr + 1) / 2 > e);
-        r = c + 1 + rr;
-        s2 = c + 1 + (e - rr * (rr + 1) / 2);
+        r = c + 1 + (ea_tri >> 8);
+        s2 = c + 1 + (ea_tri & 255);
       } else if (e >= nA && e < nA + nX) {
         const int x = e - nA, rr = x / w;
         j = c0 + (x - rr * w);
@@ -326,11 +337,11 @@ __device__ void diag_tile_blocked(T* __restrict__ tile, AT* __restrict__ A, int*
     // (c) trailing update of the rows and columns >= c1
     {
       const int n2 = nr * (nr + 1) / 2;  // at most 1176 entries
-      for (int e = tid; e < n2; e += blockDim.x) {
-        int rr = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-        rr += ((rr + 1) * (rr + 2) / 2 <= e);
-        rr -= (rr * (rr + 1) / 2 > e);
-        const int r = c1 + rr, s2 = c1 + (e - rr * (rr + 1) / 2);
+#pragma unroll
+      for (int kk = 0; kk < kTrailPer; ++kk) {
+        const int e = tid + kDiagThreads * kk;
+        if (e >= n2) break;
+        const int r = c1 + (tc_tri[kk] >> 8), s2 = c1 + (tc_tri[kk] & 255);
         const AT* wr = A + r * 65 + c0;
         const AT* ls = Lp + (s2 - c1) * 17;
         AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;

@@ -44,7 +44,7 @@ namespace {
 template <typename T, bool Wide> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
 template <> struct RasCfg<double, false> { static constexpr int NCW = 8, CTAS = 2; };
 template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 2; };
-template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 3; };
+template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 4; };
 constexpr long kWaitLimit = 1L << 20;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -89,6 +89,26 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
 }
 template <int NCW>
 __device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCW * 32) : "memory"); }
+
+// FP32 / BF16 tiles: a lane takes contiguous entries of a tile row, so that
+// one shared-memory load brings several (16 bytes: 8 BF16 or 4 FP32 entries),
+// where one entry per load left these sweeps bound by load instructions.
+__device__ __forceinline__ void load8(const float* p, float (&e)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  e[0] = a.x; e[1] = a.y; e[2] = a.z; e[3] = a.w; e[4] = b.x; e[5] = b.y; e[6] = b.z; e[7] = b.w;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&e)[8]) {
+  const uint4 w = *reinterpret_cast<const uint4*>(p);
+  e[0] = bf16_lo(w.x); e[1] = bf16_hi(w.x); e[2] = bf16_lo(w.y); e[3] = bf16_hi(w.y);
+  e[4] = bf16_lo(w.z); e[5] = bf16_hi(w.z); e[6] = bf16_lo(w.w); e[7] = bf16_hi(w.w);
+}
+__device__ __forceinline__ float2 load2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 load2(const __nv_bfloat16* p) {
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+  return make_float2(bf16_lo(w), bf16_hi(w));
+}
 
 // Per-subdomain envelope metadata staged in shared memory (one copy for the
 // producer, which runs ahead, one for the consumers): F_I, R_I and the tile
@@ -255,11 +275,26 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
 #pragma unroll
         for (int ps = 0; ps < NPASS; ++ps) {
           const T* trow = tl + (warp * RW + 4 * ps + rl) * 64;
+          if constexpr (sizeof(T) < sizeof(double)) {  // columns 8g .. 8g + 7
+            AT e[8];
+            load8(trow + 8 * g, e);
+            const float4 ya = *reinterpret_cast<const float4*>(yJ + 8 * g);
+            const float4 yb = *reinterpret_cast<const float4*>(yJ + 8 * g + 4);
+            se[ps] = fma(e[0], ya.x, se[ps]);
+            so[ps] = fma(e[1], ya.y, so[ps]);
+            se[ps] = fma(e[2], ya.z, se[ps]);
+            so[ps] = fma(e[3], ya.w, so[ps]);
+            se[ps] = fma(e[4], yb.x, se[ps]);
+            so[ps] = fma(e[5], yb.y, so[ps]);
+            se[ps] = fma(e[6], yb.z, se[ps]);
+            so[ps] = fma(e[7], yb.w, so[ps]);
+          } else {
 #pragma unroll
-          for (int c = 0; c < 8; c += 2) {
-            const int c0 = 8 * ((c + rl) & 7) + g, c1 = 8 * ((c + 1 + rl) & 7) + g;
-            se[ps] = fma((AT)trow[c0], yJ[c0], se[ps]);
-            so[ps] = fma((AT)trow[c1], yJ[c1], so[ps]);
+            for (int c = 0; c < 8; c += 2) {
+              const int c0 = 8 * ((c + rl) & 7) + g, c1 = 8 * ((c + 1 + rl) & 7) + g;
+              se[ps] = fma((AT)trow[c0], yJ[c0], se[ps]);
+              so[ps] = fma((AT)trow[c1], yJ[c1], so[ps]);
+            }
           }
         }
         release();
@@ -279,23 +314,38 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
          // a = 8 rb .. 8 rb + 7 and its columns b; (row, column set) pairs with
          // no a < b are skipped by the whole warp
         const T* dt = acquire();
-        AT v[NB];
+        if constexpr (sizeof(T) < sizeof(double) && CH == 1) {  // columns 2 lane, 2 lane + 1
+          const int b = 2 * lane;
+          AT v0 = 0, v1 = 0;
 #pragma unroll
-        for (int q = 0; q < NB; ++q) v[q] = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int a = rb * 8 + k;
-#pragma unroll
-          for (int q = 0; q < NB; ++q) {
-            const int b0 = (CH == 2 ? 32 * hh : 32 * q);
-            if (a < b0 + 31) {
-              const int b = b0 + lane;
-              if (a < b) v[q] = fma((AT)dt[a * 64 + b], acc[a], v[q]);
+          for (int k = 0; k < 8; ++k) {
+            const int a = rb * 8 + k;
+            if (a < b + 1) {
+              const float2 x = load2(dt + a * 64 + b);
+              if (a < b) v0 = fma(x.x, acc[a], v0);
+              v1 = fma(x.y, acc[a], v1);
             }
           }
-        }
+          *reinterpret_cast<float2*>(part + rb * 64 + b) = make_float2(v0, v1);
+        } else {
+          AT v[NB];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = v[q];
+          for (int q = 0; q < NB; ++q) v[q] = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int a = rb * 8 + k;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+              const int b0 = (CH == 2 ? 32 * hh : 32 * q);
+              if (a < b0 + 31) {
+                const int b = b0 + lane;
+                if (a < b) v[q] = fma((AT)dt[a * 64 + b], acc[a], v[q]);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = v[q];
+        }
         release();
       }
       consumers_sync<kConsumers>();
@@ -320,14 +370,24 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
         for (int k = 0; k < 8; ++k) {
           const int r = rb * 8 + k;
           const AT xr = y[J * 64 + r];
+          if constexpr (sizeof(T) < sizeof(double) && CH == 1) {  // columns 2 lane, 2 lane + 1
+            const float2 x = load2(tl + r * 64 + 2 * lane);
+            s[0][k & 1] = fma(x.x, xr, s[0][k & 1]);
+            s[1][k & 1] = fma(x.y, xr, s[1][k & 1]);
+          } else {
 #pragma unroll
-          for (int q = 0; q < NB; ++q)
-            s[q][k & 1] = fma((AT)tl[r * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane], xr, s[q][k & 1]);
+            for (int q = 0; q < NB; ++q)
+              s[q][k & 1] = fma((AT)tl[r * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane], xr, s[q][k & 1]);
+          }
         }
         release();
       }
+      if constexpr (sizeof(T) < sizeof(double) && CH == 1) {
+        *reinterpret_cast<float2*>(part + rb * 64 + 2 * lane) = make_float2(s[0][0] + s[0][1], s[1][0] + s[1][1]);
+      } else {
 #pragma unroll
-      for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = s[q][0] + s[q][1];
+        for (int q = 0; q < NB; ++q) part[rb * 64 + (CH == 2 ? 32 * hh : 32 * q) + lane] = s[q][0] + s[q][1];
+      }
       consumers_sync<kConsumers>();
       const T* dt = acquire();  // the diagonal tile, released after its product
       if (tid < 64) {
@@ -343,15 +403,32 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       for (int ps = 0; ps < NPASS; ++ps) {
         const int amin = warp * RW + 4 * ps, a = amin + rl;
         AT e0 = 0, e1 = 0;
+        if constexpr (sizeof(T) < sizeof(double)) {  // columns 8g .. 8g + 7
+          if (8 * g + 7 > a) {
+            AT e[8], av[8];
+            load8(dt + a * 64 + 8 * g, e);
+            load8(acc + 8 * g, av);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (8 * c + 7 > amin) {
-            const int b = 8 * c + g;
-            if (b > a) {
-              if (c & 1)
-                e1 = fma((AT)dt[a * 64 + b], acc[b], e1);
-              else
-                e0 = fma((AT)dt[a * 64 + b], acc[b], e0);
+            for (int u = 0; u < 8; ++u) {
+              if (8 * g + u > a) {
+                if (u & 1)
+                  e1 = fma(e[u], av[u], e1);
+                else
+                  e0 = fma(e[u], av[u], e0);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (8 * c + 7 > amin) {
+              const int b = 8 * c + g;
+              if (b > a) {
+                if (c & 1)
+                  e1 = fma((AT)dt[a * 64 + b], acc[b], e1);
+                else
+                  e0 = fma((AT)dt[a * 64 + b], acc[b], e0);
+              }
             }
           }
         }

@@ -35,15 +35,17 @@ namespace {
 // records an error bit and goes on (the results are then garbage and the
 // host reports MSP_ERR_TIMEOUT); the producer finally waits, bounded, for its
 // own copies, so none is in flight when the CTA exits.
-// Consumer warps per CTA and CTAs per SM.  FP64 sweeps are ALU-bound: one
-// CTA per SM with 16 consumers.  FP32 and BF16 sweeps are bound by the
-// latency of the per-row barriers: two CTAs per SM with 8 consumers each run
-// two subdomains at once on every SM.
+// Consumer warps per CTA and CTAs per SM.  FP64 sweeps are ALU-bound: two
+// CTAs of 8 consumers, so that one CTA's row sums and barriers overlap the
+// other's FMAs on the SM's FP64 pipe.  FP32 and BF16 sweeps are bound by
+// latency and HBM: four CTAs of 8 consumers, so that a level's blocks (512 at
+// 64^3) take one CTA each rather than leaving CTAs with two to set the time
+// (FP32 then runs two ring slots a CTA, enough with four CTAs streaming).
 // Levels whose tile band needs more ring slots than that leaves per CTA use
 // the wide form (one CTA of 16 consumers per SM) in every precision.
 template <typename T, bool Wide> struct RasCfg { static constexpr int NCW = 16, CTAS = 1; };
 template <> struct RasCfg<double, false> { static constexpr int NCW = 8, CTAS = 2; };
-template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 2; };
+template <> struct RasCfg<float, false> { static constexpr int NCW = 8, CTAS = 4; };
 template <> struct RasCfg<__nv_bfloat16, false> { static constexpr int NCW = 8, CTAS = 4; };
 constexpr long kWaitLimit = 1L << 20;
 
@@ -161,8 +163,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   AT* y = reinterpret_cast<AT*>(empty + nslot);                                 // [max_nt*64]
   AT* acc = y + max_nt * 64;                                                    // [64]
   AT* part = acc + 64;                                                          // [kConsumers][64]
-  AT* red = part + kConsumers * 64;                                             // [64][33] row partials
-  int32_t* meta = reinterpret_cast<int32_t*>(red + 64 * 33);                    // [2][3][max_nt]
+  AT* red = part + kConsumers * 64;                                             // [64][9] row partials (8 a row)
+  int32_t* meta = reinterpret_cast<int32_t*>(red + 64 * 9);                     // [2][3][max_nt]
   const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
   const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
   __shared__ int sflag;
@@ -597,7 +599,7 @@ size_t ras_smem_budget() {
 template <typename T, bool W>
 size_t ras_fixed_bytes(int max_nt) {
   using AT = typename Acc<T>::type;
-  return ((size_t)max_nt * 64 + 64 + RasCfg<T, W>::NCW * 64 + 64 * 33) * sizeof(AT) + 6 * (size_t)max_nt * 4;
+  return ((size_t)max_nt * 64 + 64 + RasCfg<T, W>::NCW * 64 + 64 * 9) * sizeof(AT) + 6 * (size_t)max_nt * 4;
 }
 
 template <typename T, bool W>

@@ -386,10 +386,9 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     std::vector<int32_t> cptr, clist;
     {
       const Store st = level_store(h, l);
-      // FP64: two CTAs per SM whenever two ring slots fit (one CTA's sums and
-      // barriers overlap with the other's FMAs on the SM's FP64 pipe); FP32 and
-      // BF16: the smaller form when its slots cover the tile band
-      const int need = st == Store::F64 ? 2 : std::max(2, D.max_band);
+      // FP64 and FP32: the smaller form (two / four CTAs per SM) whenever two
+      // ring slots fit; BF16 (four CTAs per SM): when its slots cover the tile band
+      const int need = st == Store::BF16 ? std::max(2, D.max_band) : 2;
       D.ras_wide = !direct_level(h, l) && ras_slots_of(h, l, false) < need;
       const int per_sm = st == Store::F64   ? ras_ctas_per_sm<double>(D.ras_wide)
                          : st == Store::F32 ? ras_ctas_per_sm<float>(D.ras_wide)

@@ -329,6 +329,46 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
             }
           }
           *reinterpret_cast<float2*>(part + rb * 64 + b) = make_float2(v0, v1);
+        } else if constexpr (CH == 1) {
+          // FP64, 8 warps: the 2016 products of the strict triangle in 64 warp
+          // instructions with every lane busy (an FP64 warp instruction costs
+          // the same with idle lanes).  Column halves 0..31 and 32..63:
+          //  * rows a < 32 of the right half are full: lane l, column 32 + l;
+          //  * the triangles (rows 0..30 of the left half, 32..62 of the right)
+          //    pair row p with row 30 - p of the same half: lane l takes column
+          //    l of row p when l > p, else column 31 - l of row 30 - p, which
+          //    are exactly the columns above the diagonal; row 15 (47) goes alone.
+          // Warp w: left pairs 2w, 2w + 1 (15: the single row), right full rows
+          // 4w .. 4w + 3, right pairs 2w, 2w + 1.  A lane keeps its own column's
+          // sums (d) and its mirror column's (m); the mirror sums reach their
+          // column's lane by a shuffle.
+          AT d0 = 0, m0 = 0, d1 = 0, m1 = 0;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int pr = 2 * rb + k;  // pair index 0..15
+            const bool dir = lane > pr, on = dir || pr < 15;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              // one FMA for the whole warp: the operands and the accumulator are
+              // selected per lane, not branched on
+              const int c = 32 * half;
+              const int row = dir ? c + pr : c + 30 - pr;
+              const int col = dir ? c + lane : c + 31 - lane;
+              const AT x = on ? (AT)dt[row * 64 + col] : AT(0);
+              AT& dh = half == 0 ? d0 : d1;
+              AT& mh = half == 0 ? m0 : m1;
+              const AT t = fma(x, acc[row], dir ? dh : mh);
+              dh = dir ? t : dh;
+              mh = dir ? mh : t;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = 4 * rb + k;
+            d1 = fma((AT)dt[a * 64 + 32 + lane], acc[a], d1);
+          }
+          part[rb * 64 + lane] = d0 + __shfl_sync(0xffffffffu, m0, 31 - lane);
+          part[rb * 64 + 32 + lane] = d1 + __shfl_sync(0xffffffffu, m1, 31 - lane);
         } else {
           AT v[NB];
 #pragma unroll

@@ -1,14 +1,15 @@
-"""Failure paths that run on the GPU without faulting it, and the range
-guard of the pivot reciprocal.
+"""Failure paths that run on the GPU without faulting it, and pivots over
+the whole double range.
 
 * A bounded wait that runs out: msp_debug_expire_waits makes the next staged
   RAS application issue no tile copies, so its waits on the shared-memory
   ring expire after a short limit (no copy is ever in flight).  msp_solve must
   report MSP_ERR_TIMEOUT, and the same instance and a fresh one must then
   solve normally, bit for bit as before.
-* Pivots outside the single-precision range: the factorisation's Newton
-  reciprocal starts from a single-precision seed and takes the full division
-  outside [1e-37, 1e37].  The meshes scaled by 2^133 and 2^-133 give pivots
+* Pivots outside the single-precision range: the factorisation's pivot
+  reciprocals (correctly rounded, __drcp_rn) must hold there as anywhere,
+  which an earlier single-precision-seeded form needed a guard for.  The
+  meshes scaled by 2^133 and 2^-133 give pivots
   near 1e40 and 1e-40; since the scaling is by a power of two, the oracle's
   solution of the unscaled problem times 2^(2 * 133 * sign) is the exact
   solution of the scaled one (stiffness scales like the length, the load like

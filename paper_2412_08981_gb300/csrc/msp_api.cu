@@ -682,9 +682,13 @@ int enqueue_factor(msp_instance* I, cudaStream_t s0, bool defer = false) {
   MSP_CUDA(cudaEventRecord(I->fork, s0));
   for (int a = 0; a < 2; ++a) MSP_CUDA(cudaStreamWaitEvent(I->aux[a], I->fork, 0));
   for (int l = L - 1; l >= 0; --l) {
-    cudaStream_t s = (l == 0) ? s0 : (l == L - 1 ? I->aux[0] : I->aux[1]);
     const Store st = level_store(h, l);
     const DevLevel& D = h->dev[l];
+    // FP32 / BF16 persistent levels one after another on the instance stream:
+    // their one-CTA-per-block grids then never hold every slot of the GPU,
+    // and the coarsest block's tile steps always find room beside them
+    const bool serial = l > 0 && l < L - 1 && st != Store::F64 && D.fac_blocks && !D.ilu;
+    cudaStream_t s = (l == 0 || serial) ? s0 : (l == L - 1 ? I->aux[0] : I->aux[1]);
     if (D.ilu) {
       if (st == Store::F64)
         factor_ilu<double>(I, l, static_cast<double*>(I->fac[l]), s);

@@ -506,7 +506,22 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
 // rows 8c..8c+7 of X_II^T, with the same two exchanges.  Cluster v of the
 // grid solves view v (the coarsest block of one instance of a batch); a
 // cluster whose vecs.z[v] is NULL leaves at once, all its CTAs together.
+//
+// The sweep is a chain of 4 NT exchanges, so only the work that needs the
+// newest tile of the solution stays on it.  A cluster barrier is split into
+// its arrive and its wait, and between the two a CTA prepares the next tile
+// row: the sum over every tile but the one next to the diagonal (its
+// operands are final), and loads of that tile's entries and of the next
+// diagonal tile's into registers.  After the wait only that last tile's two
+// products (and the diagonal tile's) remain, operands already in registers.
 constexpr int kCl = 8;
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* __restrict__ views,
@@ -540,52 +555,105 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* _
   }
   for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
   cl.sync();
-  const int r8 = 8 * me;  // this CTA's 8 rows (columns)
+  const int r8 = 8 * me;    // this CTA's 8 rows (columns)
+  const int r = r8 + warp;  // this warp's row of the off-diagonal tiles and of X_II (X_II^T backward)
+  // tile (I, J) of the envelope, F_I <= J <= I
+  auto tile = [&](int I, int J) { return base + (int64_t)(E.toff[rb + I] + (J - E.first[rb + I])) * TE; };
   // sends v (this CTA's row/column r8 + k) to every CTA's array `dst`
   auto send8 = [&](AT* dst, int k, AT v) {
     for (int c = 0; c < kCl; ++c) cl.map_shared_rank(dst, c)[r8 + k] = v;
   };
   // ---- forward
-  for (int I = 0; I < NT; ++I) {
+  // Prepared for row I: the lane sums s0 / s1 over the tiles F_I <= J < I - 1
+  // (they need y_J, J < I - 1 only), row r of tile (I, I - 1) and this lane's
+  // entries of X_II's row r (X[r][a] = dt[a][r], a < r).
+  AT f_s0 = 0, f_s1 = 0, f_l0 = 0, f_l1 = 0, f_x0 = 0, f_x1 = 0;
+  bool f_has = false;
+  auto prep_fwd = [&](int I) {
     const int F = E.first[rb + I];
-    const T* rowt = base + (int64_t)E.toff[rb + I] * TE;
-    {  // warp w: row r8 + w of the off-diagonal tiles
-      const int r = r8 + warp;
-      AT s0 = 0, s1 = 0;
-      for (int J = F; J < I; ++J) {
-        const T* tl = rowt + (int64_t)(J - F) * TE;
-        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
-        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+    AT s0 = 0, s1 = 0;
+#pragma unroll 4
+    for (int J = F; J < I - 1; ++J) {
+      const T* tl = tile(I, J);
+      s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
+      s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+    }
+    f_s0 = s0;
+    f_s1 = s1;
+    f_has = I - 1 >= F;
+    if (f_has) {
+      const T* tl = tile(I, I - 1);
+      f_l0 = (AT)tl[r * 64 + lane];
+      f_l1 = (AT)tl[r * 64 + lane + 32];
+    }
+    const T* dt = tile(I, I);
+    f_x0 = lane < r ? (AT)dt[lane * 64 + r] : AT(0);
+    f_x1 = lane + 32 < r ? (AT)dt[(lane + 32) * 64 + r] : AT(0);
+  };
+  prep_fwd(0);
+  for (int I = 0; I < NT; ++I) {
+    {  // acc_I[r] = y_I[r] - sum_J L_IJ[r][:] y_J
+      AT s0 = f_s0, s1 = f_s1;
+      if (f_has) {
+        s0 = fma(f_l0, y[(I - 1) * 64 + lane], s0);
+        s1 = fma(f_l1, y[(I - 1) * 64 + lane + 32], s1);
       }
       AT v = s0 + s1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane < kCl) cl.map_shared_rank(acc, lane)[r] = y[I * 64 + r] - v;
     }
-    cl.sync();
-    {  // warp w: y_I[b], b = r8 + w: acc[b] + sum_{a<b} X[b][a] acc[a], X[b][a] = dt[a][b]
-      const T* dt = rowt + (int64_t)(I - F) * TE;
-      const int b = r8 + warp;
+    cluster_arrive();
+    const AT x0 = f_x0, x1 = f_x1;
+    if (I + 1 < NT) prep_fwd(I + 1);  // reads y_J, J < I: final; the exchange writes y_I only
+    cluster_wait();
+    {  // y_I[r] = acc[r] + sum_{a<r} X[r][a] acc[a]
       AT v = 0;
-      if (lane < b) v = fma((AT)dt[lane * 64 + b], acc[lane], v);
-      if (lane + 32 < b) v = fma((AT)dt[(lane + 32) * 64 + b], acc[lane + 32], v);
+      if (lane < r) v = fma(x0, acc[lane], v);
+      if (lane + 32 < r) v = fma(x1, acc[lane + 32], v);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + b] = acc[b] + v;
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + r] = acc[r] + v;
     }
-    cl.sync();
+    cluster_arrive();
+    cluster_wait();
   }
   // ---- backward
-  for (int I = NT - 1; I >= 0; --I) {
+  // Prepared for row I: this thread's column sum over the tiles I + 2 <= J <=
+  // R_I (x_J final), its two entries of tile (I + 1, I), this lane's entries
+  // of row r of X_II^T's factor (dt[r][b], b > r), and (threads < 8) the
+  // forward y_I[c] / d_c of column c = r8 + tid.
+  const int col = r8 + (tid & 7), rg = tid >> 3;  // column; rows 2 rg, 2 rg + 1
+  AT b_s = 0, b_l0 = 0, b_l1 = 0, b_x0 = 0, b_x1 = 0, b_q = 0;
+  bool b_has = false;
+  auto prep_bwd = [&](int I) {
     const int R = E.last[rb + I];
-    const T* dt = base + (int64_t)(E.toff[rb + I] + (I - E.first[rb + I])) * TE;
-    {  // column col = r8 + (tid & 7); rows split over 32 groups of 2
-      const int col = r8 + (tid & 7), rg = tid >> 3;
-      AT v = 0;
-      for (int J = I + 1; J <= R; ++J) {
-        const T* tl = base + (int64_t)(E.toff[rb + J] + (I - E.first[rb + J])) * TE;
-        v = fma((AT)tl[(2 * rg) * 64 + col], y[J * 64 + 2 * rg], v);
-        v = fma((AT)tl[(2 * rg + 1) * 64 + col], y[J * 64 + 2 * rg + 1], v);
+    AT v = 0;
+#pragma unroll 4
+    for (int J = I + 2; J <= R; ++J) {
+      const T* tl = tile(J, I);
+      v = fma((AT)tl[(2 * rg) * 64 + col], y[J * 64 + 2 * rg], v);
+      v = fma((AT)tl[(2 * rg + 1) * 64 + col], y[J * 64 + 2 * rg + 1], v);
+    }
+    b_s = v;
+    b_has = I + 1 <= R;
+    if (b_has) {
+      const T* tl = tile(I + 1, I);
+      b_l0 = (AT)tl[(2 * rg) * 64 + col];
+      b_l1 = (AT)tl[(2 * rg + 1) * 64 + col];
+    }
+    const T* dt = tile(I, I);
+    b_x0 = lane > r ? (AT)dt[r * 64 + lane] : AT(0);
+    b_x1 = lane + 32 > r ? (AT)dt[r * 64 + lane + 32] : AT(0);
+    if (tid < 8) b_q = y[I * 64 + col] / (AT)dt[col * 65];
+  };
+  prep_bwd(NT - 1);
+  for (int I = NT - 1; I >= 0; --I) {
+    {  // acc_I[c] = y_I[c] / d_c - sum_J L_JI[:][c] x_J
+      AT v = b_s;
+      if (b_has) {
+        v = fma(b_l0, y[(I + 1) * 64 + 2 * rg], v);
+        v = fma(b_l1, y[(I + 1) * 64 + 2 * rg + 1], v);
       }
       // the 4 row groups inside a warp share a column: lanes l, l^8, l^16, l^24
       v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -596,21 +664,23 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* _
         AT sum = 0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) sum += red[w * 8 + tid];
-        const int c = r8 + tid;
-        send8(acc, tid, y[I * 64 + c] / (AT)dt[c * 65] - sum);
+        send8(acc, tid, b_q - sum);
       }
     }
-    cl.sync();
-    {  // warp w: x_I[a], a = r8 + w: acc[a] + sum_{b>a} dt[a][b] acc[b]
-      const int a2 = r8 + warp;
+    cluster_arrive();
+    const AT x0 = b_x0, x1 = b_x1;
+    if (I > 0) prep_bwd(I - 1);  // reads x_J, J > I, and the forward y_{I-1}: neither changes now
+    cluster_wait();
+    {  // x_I[r] = acc[r] + sum_{b>r} dt[r][b] acc[b]
       AT v = 0;
-      if (lane > a2) v = fma((AT)dt[a2 * 64 + lane], acc[lane], v);
-      if (lane + 32 > a2) v = fma((AT)dt[a2 * 64 + lane + 32], acc[lane + 32], v);
+      if (lane > r) v = fma(x0, acc[lane], v);
+      if (lane + 32 > r) v = fma(x1, acc[lane + 32], v);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + a2] = acc[a2] + v;
+      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + r] = acc[r] + v;
     }
-    cl.sync();
+    cluster_arrive();
+    cluster_wait();
   }
   for (int li = me * 256 + tid; li < np_; li += kCl * 256) {
     const int g = dofs[off + li];

@@ -405,6 +405,81 @@ __global__ void __launch_bounds__(256) k_ldlt_xfill(T* __restrict__ fac, EnvDev 
   }
 }
 
+// ------------------------------------------ coupling tiles of a block solve
+// For a level solved as one block (p = 0) on a cluster: per tile row I the
+// tiles that carry one tile row's solution into the next row's sums, so that
+// each row of a sweep needs only the previous row's right-hand side acc
+// (y_J = X_J acc_J forward, x_J = X_J^T acc_J backward, X_J = L_JJ^{-1}):
+//   M_I = L_{I,I-1} X_{I-1}   (L_{I,I-1} y_{I-1} = M_I acc_{I-1}),
+//   N_I = X_{I+1} L_{I+1,I}   (L_{I+1,I}^T x_{I+1} = N_I^T acc_{I+1}),
+// and the reciprocals 1/d of D.  They follow the block's envelope: M_I at
+// tile I, N_I^T at tile NT + I, then NT * 64 reciprocals.  CTA (I, 0) forms
+// M_I and row I's reciprocals, CTA (I, 1) N_I^T; a tile outside the envelope
+// (no L_{I,I-1} / L_{I+1,I}) is not formed, and the solve never reads it.
+// The diagonal tile holds X above its diagonal: X[a][c] at dt[c][a], a > c.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ldlt_mnfill(T* __restrict__ fac, EnvDev E) {
+  using AT = typename Acc<T>::type;
+  const int NT = E.nt[0], I = blockIdx.x, kind = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  T* mn = fac + E.fac_off[1];
+  if (kind == 0 && tid < 64) {
+    const T* dt = fac + tile_at(E, 0, I, I);
+    mn[(int64_t)2 * NT * TE + I * 64 + tid] = (T)(AT(1) / (AT)dt[tid * 65]);
+  }
+  const int Ir = kind == 0 ? I : I + 1;  // the tile row of L_{I,I-1} / L_{I+1,I}
+  const int Jd = kind == 0 ? I - 1 : I + 1;  // the diagonal tile whose X is applied
+  if (Ir >= NT || Ir - 1 < E.first[E.trow[0] + Ir] || Ir < 1) return;
+  extern __shared__ unsigned char smraw[];
+  AT* Ls = reinterpret_cast<AT*>(smraw);  // [64][65] L_{Ir,Ir-1}, then the result
+  AT* Xs = Ls + 64 * 65;                  // [64][65] the diagonal tile of Jd
+  read_elems<T, TE>(fac + tile_at(E, 0, Ir, Ir - 1), [&](int e, T v) { Ls[(e >> 6) * 65 + (e & 63)] = (AT)v; });
+  read_elems<T, TE>(fac + tile_at(E, 0, Jd, Jd), [&](int e, T v) { Xs[(e >> 6) * 65 + (e & 63)] = (AT)v; });
+  __syncthreads();
+  AT o[2][8];
+  if (kind == 0) {
+    // M[r][c] = L[r][c] + sum_{a>c} L[r][a] X[a][c]; lane: rows lane, lane + 32; warp: columns warp + 8 j
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = warp + 8 * j;
+      AT v0 = Ls[lane * 65 + c], v1 = Ls[(lane + 32) * 65 + c];
+      for (int a = c + 1; a < 64; ++a) {
+        const AT x = Xs[c * 65 + a];
+        v0 = fma(Ls[lane * 65 + a], x, v0);
+        v1 = fma(Ls[(lane + 32) * 65 + a], x, v1);
+      }
+      o[0][j] = v0;
+      o[1][j] = v1;
+    }
+  } else {
+    // N[a][c] = L[a][c] + sum_{b<a} X[a][b] L[b][c]; lane: columns lane, lane + 32; warp: rows warp + 8 j
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int a = warp + 8 * j;
+      AT v0 = Ls[a * 65 + lane], v1 = Ls[a * 65 + lane + 32];
+      for (int b = 0; b < a; ++b) {
+        const AT x = Xs[b * 65 + a];
+        v0 = fma(x, Ls[b * 65 + lane], v0);
+        v1 = fma(x, Ls[b * 65 + lane + 32], v1);
+      }
+      o[0][j] = v0;
+      o[1][j] = v1;
+    }
+  }
+  __syncthreads();
+  // the result in [row of the stored tile][column] order: M_I as is, N_I transposed
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int u = warp + 8 * j, w = lane + 32 * k;  // M: column u, row w; N: row u, column w
+      Ls[w * 65 + u] = o[k][j];
+    }
+  __syncthreads();
+  T* dst = mn + (int64_t)(kind == 0 ? I : NT + I) * TE;
+  for (int e = tid; e < TE; e += blockDim.x) dst[e] = (T)Ls[(e >> 6) * 65 + (e & 63)];
+}
+
 // ----------------------------------------------------------- panel solve
 // L_ik = A_ik X^T D^{-1} for a tile below the diagonal tile of step k.
 // Column c needs the products over m <= c (X^T is upper triangular), so warp
@@ -1450,6 +1525,18 @@ void launch_ldlt_xfill(T* fac, const EnvDev& E, const int32_t* order, int nblock
   k_ldlt_xfill<T><<<dim3(max_nt, nblocks), 256, smem, s>>>(fac, E, order);
 }
 
+template <typename T>
+void launch_ldlt_mnfill(T* fac, const EnvDev& E, int nt, cudaStream_t s) {
+  if (nt <= 0) return;
+  using AT = typename Acc<T>::type;
+  const size_t smem = (size_t)2 * 64 * 65 * sizeof(AT);
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
+    cudaFuncSetAttribute(k_ldlt_mnfill<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  k_ldlt_mnfill<T><<<dim3(nt, 2), 256, smem, s>>>(fac, E);
+}
+
 // CTAs of a 256-thread persistent kernel resident per SM at once: limited by
 // its shared memory (with the carveout set to the maximum) and its registers.
 int resident_per_sm(const void* fn, size_t smem) {
@@ -1544,6 +1631,7 @@ int ldlt_blocks_tc_per_sm() {
   template void launch_ldlt_trail<T>(T*, const EnvDev&, const int32_t*, int, int, int, int,      \
                                      cudaStream_t);                                              \
   template void launch_ldlt_xfill<T>(T*, const EnvDev&, const int32_t*, int, int, cudaStream_t); \
+  template void launch_ldlt_mnfill<T>(T*, const EnvDev&, int, cudaStream_t);                      \
   template void launch_ldlt_blocks_batch<T>(const BlockItem*, const int32_t*, const int32_t*, int,    \
                                             cudaStream_t);                                        \
   template int ldlt_blocks_batch_per_sm<T>();                                                     \

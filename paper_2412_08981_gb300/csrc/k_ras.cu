@@ -497,40 +497,56 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
 
 // ------------------------------------------- single-block solve on a cluster
 // The coarsest level is one block (one CTA would use one SM's FP64 pipe), so
-// its sweeps run on a cluster of kCl CTAs.  Every CTA keeps the whole
-// right-hand side / solution vector in its shared memory.  Forward, tile row
-// I: CTA c owns rows 8c..8c+7; it sums its rows of the off-diagonal tiles,
-// sends its 8 results to every CTA (distributed shared memory), the cluster
-// synchronises, each CTA applies its rows of X_II, sends them, synchronises.
-// Backward, tile row I: CTA c owns the columns 8c..8c+7 of L_JI^T x_J and the
-// rows 8c..8c+7 of X_II^T, with the same two exchanges.  Cluster v of the
-// grid solves view v (the coarsest block of one instance of a batch); a
-// cluster whose vecs.z[v] is NULL leaves at once, all its CTAs together.
+// its sweeps run on a cluster of CL CTAs of NW = 64 / CL warps.  Every CTA
+// keeps the whole right-hand side / solution vector in its shared memory;
+// CTA c owns the rows r0 .. r0 + NW - 1 (r0 = NW c) of every tile row, one
+// per warp, and sends what it computes for them to every CTA (distributed
+// shared memory) before a cluster barrier.
 //
-// The sweep is a chain of 4 NT exchanges, so only the work that needs the
-// newest tile of the solution stays on it.  A cluster barrier is split into
-// its arrive and its wait, and between the two a CTA prepares the next tile
-// row: the sum over every tile but the one next to the diagonal (its
-// operands are final), and loads of that tile's entries and of the next
-// diagonal tile's into registers.  After the wait only that last tile's two
-// products (and the diagonal tile's) remain, operands already in registers.
+// Forward sweep of L y = t by tile rows, acc_I = t_I - sum_{J<I} L_IJ y_J and
+// y_I = X_I acc_I (X_I = L_II^{-1}, kept in the diagonal tile).  With the
+// coupling tile M_I = L_{I,I-1} X_{I-1}, the term of the newest row is
+// L_{I,I-1} y_{I-1} = M_I acc_{I-1}, so step I forms acc_I from acc_{I-1}
+// and y_J, J <= I - 2, and in the same pass y_{I-1} = X_{I-1} acc_{I-1}: one
+// exchange per tile row.  Backward (L^T x = D^{-1} y), with N_I = X_{I+1}
+// L_{I+1,I}: acc_I = y_I / d - sum_{J>I} L_JI^T x_J, the newest term
+// L_{I+1,I}^T x_{I+1} = N_I^T acc_{I+1}, and x_{I+1} = X_{I+1}^T acc_{I+1}.
+// Every step keeps on its critical path only the two newest tiles' products
+// (in registers, loaded the step before) and one reduction of two sums over
+// the warp: the older tiles' sums are formed between the arrive and the wait
+// of the previous step's cluster barrier.  Cluster v of the grid solves view
+// v (the coarsest block of one instance of a batch); a cluster whose
+// vecs.z[v] is NULL leaves at once, all its CTAs together.
 constexpr int kCl = 8;
 
+// The non-aligned forms: a warp may reach the barrier still diverged from
+// its sends (lanes 0..CL-1 and 16..16+CL-1 store), and every lane's stores
+// must be ordered before its own arrival.
 __device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* __restrict__ views,
-                                                              const __grid_constant__ RasVecs vecs, int add) {
+// Shared memory of one CTA: the vector, acc double-buffered, the backward
+// column partials double-buffered.
+template <int CL>
+size_t block_solve_smem_cl(int max_nt) {
+  return ((size_t)max_nt * 64 + 128 + 2 * 32 * (64 / CL)) * sizeof(double);
+}
+
+template <typename T, int CL>
+__global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const RasView* __restrict__ views,
+                                                                        const __grid_constant__ RasVecs vecs,
+                                                                        int add) {
+  constexpr int NW = 64 / CL, NTH = 32 * NW;
+  static_assert(CL >= 4 && CL <= 16, "lanes 0..CL-1 and 16..16+CL-1 send the two sums");
   using AT = typename Acc<T>::type;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int me = (int)cl.block_rank();
-  const int vw = blockIdx.x / kCl;
+  const int vw = blockIdx.x / CL;
   const double* __restrict__ t = vecs.t[vw];
   double* __restrict__ z = vecs.z[vw];
   if (z == nullptr) return;
@@ -546,143 +562,157 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cluster(const RasView* _
   const int off = sub_ptr[p], np_ = sub_ptr[p + 1] - off;
   extern __shared__ unsigned char smraw[];
   AT* y = reinterpret_cast<AT*>(smraw);  // [NT*64] the whole vector, in every CTA
-  AT* acc = y + NT * 64;                 // [64] exchanged partial results
-  AT* red = acc + 64;                    // [8][32] backward column partials
+  AT* acc = y + NT * 64;                 // [2][64] acc of the newest tile row, by parity
+  AT* redp = acc + 128;                  // [2][32][NW] backward partials: row pair, column
   const T* base = fac + E.fac_off[p];
-  for (int d = me * 256 + tid; d < ndir; d += kCl * 256) {
+  const T* Mt = fac + E.fac_off[p + 1];      // M_I at tile I
+  const T* Nt = Mt + (int64_t)NT * TE;       // N_I^T at tile I
+  const T* Dinv = Nt + (int64_t)NT * TE;     // 1/d, 64 per tile row
+  for (int d = me * NTH + tid; d < ndir; d += CL * NTH) {
     const int g = dir_list[d];
     z[g] = add ? z[g] + t[g] : t[g];
   }
-  for (int li = tid; li < NT * 64; li += 256) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+  for (int li = tid; li < NT * 64; li += NTH) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
   cl.sync();
-  const int r8 = 8 * me;    // this CTA's 8 rows (columns)
-  const int r = r8 + warp;  // this warp's row of the off-diagonal tiles and of X_II (X_II^T backward)
-  // tile (I, J) of the envelope, F_I <= J <= I
+  const int r = NW * me + warp;  // this warp's row (forward), column of acc and row of x (backward)
   auto tile = [&](int I, int J) { return base + (int64_t)(E.toff[rb + I] + (J - E.first[rb + I])) * TE; };
-  // sends v (this CTA's row/column r8 + k) to every CTA's array `dst`
-  auto send8 = [&](AT* dst, int k, AT v) {
-    for (int c = 0; c < kCl; ++c) cl.map_shared_rank(dst, c)[r8 + k] = v;
+  // Sum over the warp of a (lanes < 16 end with it) and of b (lanes >= 16):
+  // the first level halves the lanes of each, so the two take 5 adds.
+  auto reduce2 = [&](AT a, AT b) {
+    const bool hi = lane & 16;
+    AT v = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
   };
-  // ---- forward
-  // Prepared for row I: the lane sums s0 / s1 over the tiles F_I <= J < I - 1
-  // (they need y_J, J < I - 1 only), row r of tile (I, I - 1) and this lane's
-  // entries of X_II's row r (X[r][a] = dt[a][r], a < r).
-  AT f_s0 = 0, f_s1 = 0, f_l0 = 0, f_l1 = 0, f_x0 = 0, f_x1 = 0;
-  bool f_has = false;
-  auto prep_fwd = [&](int I) {
-    const int F = E.first[rb + I];
-    AT s0 = 0, s1 = 0;
+  // ---- forward: step I = 0 .. NT forms acc_I (I < NT) and y_{I-1} (I >= 1)
+  // Prepared for step I: the lane sums over the tiles F_I <= J < I - 2, row r
+  // of tile (I, I - 2) and of M_I (where they exist), this lane's entries of
+  // row r of X_{I-1} (X[r][a] = dt[a][r], a < r).
+  AT f0 = 0, f1 = 0, l20 = 0, l21 = 0, m0 = 0, m1 = 0, x0 = 0, x1 = 0;
+  bool h2 = false, h1 = false;
+  auto prep_fwd = [&](int I) {  // reads y_J, J < I - 2
+    h2 = h1 = false;
+    f0 = f1 = x0 = x1 = AT(0);
+    if (I < NT) {
+      const int F = E.first[rb + I];
+      AT s0 = 0, s1 = 0;
 #pragma unroll 4
-    for (int J = F; J < I - 1; ++J) {
-      const T* tl = tile(I, J);
-      s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
-      s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+      for (int J = F; J < I - 2; ++J) {
+        const T* tl = tile(I, J);
+        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
+        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+      }
+      f0 = s0;
+      f1 = s1;
+      h2 = I - 2 >= F;
+      if (h2) {
+        const T* tl = tile(I, I - 2);
+        l20 = (AT)tl[r * 64 + lane];
+        l21 = (AT)tl[r * 64 + lane + 32];
+      }
+      h1 = I - 1 >= F;
+      if (h1) {
+        const T* mt = Mt + (int64_t)I * TE;
+        m0 = (AT)mt[r * 64 + lane];
+        m1 = (AT)mt[r * 64 + lane + 32];
+      }
     }
-    f_s0 = s0;
-    f_s1 = s1;
-    f_has = I - 1 >= F;
-    if (f_has) {
-      const T* tl = tile(I, I - 1);
-      f_l0 = (AT)tl[r * 64 + lane];
-      f_l1 = (AT)tl[r * 64 + lane + 32];
+    if (I >= 1) {
+      const T* dt = tile(I - 1, I - 1);
+      x0 = lane < r ? (AT)dt[lane * 64 + r] : AT(0);
+      x1 = lane + 32 < r ? (AT)dt[(lane + 32) * 64 + r] : AT(0);
     }
-    const T* dt = tile(I, I);
-    f_x0 = lane < r ? (AT)dt[lane * 64 + r] : AT(0);
-    f_x1 = lane + 32 < r ? (AT)dt[(lane + 32) * 64 + r] : AT(0);
   };
   prep_fwd(0);
-  for (int I = 0; I < NT; ++I) {
-    {  // acc_I[r] = y_I[r] - sum_J L_IJ[r][:] y_J
-      AT s0 = f_s0, s1 = f_s1;
-      if (f_has) {
-        s0 = fma(f_l0, y[(I - 1) * 64 + lane], s0);
-        s1 = fma(f_l1, y[(I - 1) * 64 + lane + 32], s1);
-      }
-      AT v = s0 + s1;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane < kCl) cl.map_shared_rank(acc, lane)[r] = y[I * 64 + r] - v;
+  for (int I = 0; I <= NT; ++I) {
+    const AT* ap = acc + ((I + 1) & 1) * 64;  // acc_{I-1}
+    AT* an = acc + (I & 1) * 64;              // acc_I
+    AT a0 = f0, a1 = f1;
+    if (h2) {
+      a0 = fma(l20, y[(I - 2) * 64 + lane], a0);
+      a1 = fma(l21, y[(I - 2) * 64 + lane + 32], a1);
     }
-    cluster_arrive();
-    const AT x0 = f_x0, x1 = f_x1;
-    if (I + 1 < NT) prep_fwd(I + 1);  // reads y_J, J < I: final; the exchange writes y_I only
-    cluster_wait();
-    {  // y_I[r] = acc[r] + sum_{a<r} X[r][a] acc[a]
-      AT v = 0;
-      if (lane < r) v = fma(x0, acc[lane], v);
-      if (lane + 32 < r) v = fma(x1, acc[lane + 32], v);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + r] = acc[r] + v;
+    if (h1) {
+      a0 = fma(m0, ap[lane], a0);
+      a1 = fma(m1, ap[lane + 32], a1);
     }
+    const AT yv = I >= 1 ? fma(x1, ap[lane + 32], x0 * ap[lane]) : AT(0);
+    const AT v = reduce2(a0 + a1, yv);
+    if (I < NT && lane < CL) cl.map_shared_rank(an, lane)[r] = y[I * 64 + r] - v;
+    if (I >= 1 && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I - 1) * 64 + r] = ap[r] + v;
     cluster_arrive();
+    if (I < NT) prep_fwd(I + 1);  // reads y_J, J < I - 1: final; the exchange writes y_{I-1} and acc_I
     cluster_wait();
   }
-  // ---- backward
-  // Prepared for row I: this thread's column sum over the tiles I + 2 <= J <=
-  // R_I (x_J final), its two entries of tile (I + 1, I), this lane's entries
-  // of row r of X_II^T's factor (dt[r][b], b > r), and (threads < 8) the
-  // forward y_I[c] / d_c of column c = r8 + tid.
-  const int col = r8 + (tid & 7), rg = tid >> 3;  // column; rows 2 rg, 2 rg + 1
-  AT b_s = 0, b_l0 = 0, b_l1 = 0, b_x0 = 0, b_x1 = 0, b_q = 0;
-  bool b_has = false;
-  auto prep_bwd = [&](int I) {
-    const int R = E.last[rb + I];
-    AT v = 0;
+  // ---- backward: step I = NT - 1 .. -1 forms acc_I (I >= 0) and x_{I+1} (I + 1 < NT)
+  // Prepared for step I: this thread's partial of column r0 + (tid % NW) over
+  // rows 2 (tid / NW), 2 (tid / NW) + 1 of the tiles I + 3 <= J <= R_I (into
+  // redp), this lane's entries of column r of tile (I + 2, I) and of N_I^T's
+  // row r, of row r of X_{I+1}^T (dt[r][b], b > r), and y_I[r] / d_r.
+  const int pc = tid % NW, prg = tid / NW, pcol = NW * me + pc;
+  AT bl0 = 0, bl1 = 0, bn0 = 0, bn1 = 0, bx0 = 0, bx1 = 0, bq = 0;
+  bool bh2 = false, bh1 = false;
+  auto prep_bwd = [&](int I) {  // reads x_J, J >= I + 3, and the forward y_I
+    bh2 = bh1 = false;
+    bx0 = bx1 = AT(0);
+    if (I >= 0) {
+      const int R = E.last[rb + I];
+      AT v = 0;
 #pragma unroll 4
-    for (int J = I + 2; J <= R; ++J) {
-      const T* tl = tile(J, I);
-      v = fma((AT)tl[(2 * rg) * 64 + col], y[J * 64 + 2 * rg], v);
-      v = fma((AT)tl[(2 * rg + 1) * 64 + col], y[J * 64 + 2 * rg + 1], v);
+      for (int J = I + 3; J <= R; ++J) {
+        const T* tl = tile(J, I);
+        v = fma((AT)tl[(2 * prg) * 64 + pcol], y[J * 64 + 2 * prg], v);
+        v = fma((AT)tl[(2 * prg + 1) * 64 + pcol], y[J * 64 + 2 * prg + 1], v);
+      }
+      redp[(I & 1) * 32 * NW + prg * NW + pc] = v;
+      bh2 = I + 2 <= R;
+      if (bh2) {
+        const T* tl = tile(I + 2, I);
+        bl0 = (AT)tl[lane * 64 + r];
+        bl1 = (AT)tl[(lane + 32) * 64 + r];
+      }
+      bh1 = I + 1 <= R;
+      if (bh1) {
+        const T* nt = Nt + (int64_t)I * TE;
+        bn0 = (AT)nt[r * 64 + lane];
+        bn1 = (AT)nt[r * 64 + lane + 32];
+      }
+      bq = y[I * 64 + r] * (AT)Dinv[I * 64 + r];
     }
-    b_s = v;
-    b_has = I + 1 <= R;
-    if (b_has) {
-      const T* tl = tile(I + 1, I);
-      b_l0 = (AT)tl[(2 * rg) * 64 + col];
-      b_l1 = (AT)tl[(2 * rg + 1) * 64 + col];
+    if (I + 1 < NT) {
+      const T* dt = tile(I + 1, I + 1);
+      bx0 = lane > r ? (AT)dt[r * 64 + lane] : AT(0);
+      bx1 = lane + 32 > r ? (AT)dt[r * 64 + lane + 32] : AT(0);
     }
-    const T* dt = tile(I, I);
-    b_x0 = lane > r ? (AT)dt[r * 64 + lane] : AT(0);
-    b_x1 = lane + 32 > r ? (AT)dt[r * 64 + lane + 32] : AT(0);
-    if (tid < 8) b_q = y[I * 64 + col] / (AT)dt[col * 65];
   };
   prep_bwd(NT - 1);
-  for (int I = NT - 1; I >= 0; --I) {
-    {  // acc_I[c] = y_I[c] / d_c - sum_J L_JI[:][c] x_J
-      AT v = b_s;
-      if (b_has) {
-        v = fma(b_l0, y[(I + 1) * 64 + 2 * rg], v);
-        v = fma(b_l1, y[(I + 1) * 64 + 2 * rg + 1], v);
+  __syncthreads();  // its partials in redp
+  for (int I = NT - 1; I >= -1; --I) {
+    const AT* ap = acc + ((I + 1) & 1) * 64;  // acc_{I+1}
+    AT* an = acc + (I & 1) * 64;              // acc_I
+    AT a = 0;
+    if (I >= 0) {
+      a = redp[(I & 1) * 32 * NW + lane * NW + warp];  // rows 2 lane, 2 lane + 1 of the older tiles
+      if (bh2) {
+        a = fma(bl0, y[(I + 2) * 64 + lane], a);
+        a = fma(bl1, y[(I + 2) * 64 + lane + 32], a);
       }
-      // the 4 row groups inside a warp share a column: lanes l, l^8, l^16, l^24
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (lane < 8) red[warp * 8 + lane] = v;
-      __syncthreads();
-      if (tid < 8) {
-        AT sum = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) sum += red[w * 8 + tid];
-        send8(acc, tid, b_q - sum);
+      if (bh1) {
+        a = fma(bn0, ap[lane], a);
+        a = fma(bn1, ap[lane + 32], a);
       }
     }
+    const AT xv = I + 1 < NT ? fma(bx1, ap[lane + 32], bx0 * ap[lane]) : AT(0);
+    const AT v = reduce2(a, xv);
+    if (I >= 0 && lane < CL) cl.map_shared_rank(an, lane)[r] = bq - v;
+    if (I + 1 < NT && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I + 1) * 64 + r] = ap[r] + v;
     cluster_arrive();
-    const AT x0 = b_x0, x1 = b_x1;
-    if (I > 0) prep_bwd(I - 1);  // reads x_J, J > I, and the forward y_{I-1}: neither changes now
+    if (I >= 0) prep_bwd(I - 1);  // reads x_J, J >= I + 2, and y_{I-1}: final; the exchange writes x_{I+1}, acc_I
     cluster_wait();
-    {  // x_I[r] = acc[r] + sum_{b>r} dt[r][b] acc[b]
-      AT v = 0;
-      if (lane > r) v = fma(x0, acc[lane], v);
-      if (lane + 32 > r) v = fma(x1, acc[lane + 32], v);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane < kCl) cl.map_shared_rank(y, lane)[I * 64 + r] = acc[r] + v;
-    }
-    cluster_arrive();
-    cluster_wait();
+    __syncthreads();  // redp is written after the arrive, which orders only what came before it
   }
-  for (int li = me * 256 + tid; li < np_; li += kCl * 256) {
+  for (int li = me * NTH + tid; li < np_; li += CL * NTH) {
     const int g = dofs[off + li];
     z[g] = add ? z[g] + (double)y[li] : (double)y[li];
   }
@@ -757,30 +787,56 @@ void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, con
     launch_ras_cfg<T, false>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s);
 }
 
-template <typename T>
-void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
-                                cudaStream_t s) {
-  using AT = typename Acc<T>::type;
-  if (nviews < 1) return;
-  const size_t smem = ((size_t)max_nt * 64 + 64 + 64) * sizeof(AT);
+size_t block_solve_cluster_smem(int max_nt) { return block_solve_smem_cl<kCl>(max_nt); }
+
+// One launch of the cluster solve with CL CTAs a cluster.
+template <typename T, int CL>
+cudaError_t launch_block_solve_cl(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
+                                  cudaStream_t s, bool query_only = false) {
+  auto kern = k_block_solve_cluster<T, CL>;
+  const size_t smem = block_solve_smem_cl<CL>(max_nt);
   static std::once_flag attr;
   std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_block_solve_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         limits().smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limits().smem);
+    if (CL > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   });
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCl * nviews, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.gridDim = dim3(CL * std::max(nviews, 1), 1, 1);
+  cfg.blockDim = dim3(32 * (64 / CL), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr1[1];
   attr1[0].id = cudaLaunchAttributeClusterDimension;
-  attr1[0].val.clusterDim.x = kCl;
+  attr1[0].val.clusterDim.x = CL;
   attr1[0].val.clusterDim.y = 1;
   attr1[0].val.clusterDim.z = 1;
   cfg.attrs = attr1;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_block_solve_cluster<T>, views, vecs, add);
+  if (query_only) {  // can one cluster of CL CTAs be resident at all?
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    return (e == cudaSuccess && n >= 1) ? cudaSuccess : cudaErrorNotSupported;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, views, vecs, add);
+}
+
+// Clusters of 16 CTAs (a non-portable size) where the GPU can place one:
+// four warps a CTA, so each SM sub-partition's FP64 unit serves one warp of
+// the critical path; else 8 CTAs of eight warps.
+template <typename T>
+void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
+                                cudaStream_t s) {
+  if (nviews < 1) return;
+  static std::once_flag pick;
+  static bool wide = false;
+  std::call_once(pick, [&] {
+    wide = launch_block_solve_cl<T, 16>(views, nviews, vecs, max_nt, add, s, true) == cudaSuccess;
+    cudaGetLastError();
+  });
+  if (wide)
+    launch_block_solve_cl<T, 16>(views, nviews, vecs, max_nt, add, s);
+  else
+    launch_block_solve_cl<T, kCl>(views, nviews, vecs, max_nt, add, s);
 }
 
 #define MSP_RAS_INST(T)                                                                          \

@@ -433,7 +433,7 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
     // the sweeps hold one tile at a time, so two ring slots keep the producer
     // ahead; deeper rings (up to the tile band) prefetch more
     const bool direct = direct_level(h, l);
-    if (direct && ((size_t)D.max_nt * 64 + 128) * sizeof(double) > 220u * 1024u)
+    if (direct && block_solve_cluster_smem(D.max_nt) > 220u * 1024u)
       return fail(MSP_ERR_INVALID, "coarsest level too large for the cluster block solve (" +
                                        std::to_string(D.max_nt) + " tiles)");
     if (!direct && slots < 2)
@@ -647,6 +647,7 @@ void factor_level(msp_instance* I, int l, T* fac, cudaStream_t s, bool tensor = 
   {
     ProfScope ps(I->prof, PK_LDLT_DIAG, s);
     launch_ldlt_xfill<T>(fac, D.env, D.sub_order, D.active[0], D.max_nt, s);
+    if (direct_level(h, l)) launch_ldlt_mnfill<T>(fac, D.env, D.max_nt, s);  // for the cluster solve
     ps.account(0, 0);
   }
 }
@@ -1093,7 +1094,8 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     I->t[l] = A.alloc<double>(D.n);
     const Store st = level_store(h, l);
     if (st == Store::F64) {
-      I->fac[l] = A.alloc<double>(D.fac_elems);
+      // the level solved as one block keeps its cluster solve's coupling tiles after the envelope
+      I->fac[l] = A.alloc<double>(D.fac_elems + (direct_level(h, l) ? kBlockSolveExtra(D.max_nt) : 0));
     } else if (st == Store::F32) {
       I->fac[l] = A.alloc<float>(D.fac_elems);
     } else {
@@ -1210,6 +1212,7 @@ size_t instance_need(const msp_hierarchy* h) {
     const DevLevel& D = h->dev[l];
     need += (size_t)D.m * 8 + (size_t)D.nnz * 8 + (size_t)D.n * 24 +
             (size_t)D.fac_elems * (level_store(h, (int)l) == Store::BF16 ? 6 : store_bytes(level_store(h, (int)l)));
+    if (direct_level(h, (int)l)) need += (size_t)kBlockSolveExtra(D.max_nt) * 8;
   }
   need += (size_t)(2 * h->opt.restart + 5) * h->dev[0].n * 8;
   return need;

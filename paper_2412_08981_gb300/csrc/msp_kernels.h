@@ -101,6 +101,13 @@ void launch_ldlt_trail(T* fac, const EnvDev& E, const int32_t* order, int nactiv
 // only), over the first nblocks blocks of `order`
 template <typename T>
 void launch_ldlt_xfill(T* fac, const EnvDev& E, const int32_t* order, int nblocks, int max_nt, cudaStream_t s);
+// after the factorisation of a level solved as one block on a cluster (block
+// 0, nt tile rows): the coupling tiles M_I = L_{I,I-1} X_{I-1} and
+// N_I^T = (X_{I+1} L_{I+1,I})^T and the reciprocals of D, written after the
+// block's envelope (kBlockSolveExtra(nt) elements of T)
+template <typename T>
+void launch_ldlt_mnfill(T* fac, const EnvDev& E, int nt, cudaStream_t s);
+constexpr int64_t kBlockSolveExtra(int nt) { return (int64_t)nt * (2 * 4096 + 64); }
 // The whole L D L^T of many blocks in one persistent launch: CTA b factors
 // cta_list[cta_ptr[b] .. cta_ptr[b+1]) through every tile step.
 template <typename T>
@@ -207,7 +214,10 @@ void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, con
 // y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level) for
 // each of `nviews` views, each on a cluster of 8 CTAs that split every tile
 // row of both sweeps and exchange partial results through distributed shared
-// memory; Dirichlet nodes get t.  Written (add = 0) or added (add = 1) to z.
+// memory, one exchange per tile row; the factor must carry the coupling
+// tiles of launch_ldlt_mnfill after its envelope.  Dirichlet nodes get t.
+// Written (add = 0) or added (add = 1) to z.
+size_t block_solve_cluster_smem(int max_nt);  // dynamic shared memory of one CTA
 template <typename T>
 void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
                                 cudaStream_t s);

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
-from _common import make_hierarchy, make_oracle, rel, workload
+from _common import make_hierarchy, make_oracle, rel, relmax, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -141,11 +141,19 @@ def test_full_coarsest_solve_residual(full, P, orc, torch):
     oc = make_oracle([levels[2]], w, orc)
     oc.assemble(full["mu"])
     Ac = oc.csr(0)
-    r = np.random.default_rng(5).normal(size=Ac.shape[0])
-    z = torch.zeros(Ac.shape[0], dtype=torch.float64, device="cuda")
-    inst.apply_op(P.msp.MSP_OP_COARSE, 2, _dev(torch, r), z)
-    torch.cuda.synchronize()
-    assert rel(Ac @ z.cpu().numpy(), r) <= 1e-11
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(Ac.tocsc())
+    rng = np.random.default_rng(5)
+    # repeated applications: the cluster sweeps exchange every tile row, so an
+    # ordering fault would show as an occasional wrong row, not a constant one
+    for _ in range(12):
+        r = rng.normal(size=Ac.shape[0])
+        z = torch.zeros(Ac.shape[0], dtype=torch.float64, device="cuda")
+        inst.apply_op(P.msp.MSP_OP_COARSE, 2, _dev(torch, r), z)
+        torch.cuda.synchronize()
+        zg = z.cpu().numpy()
+        assert rel(Ac @ zg, r) <= 1e-11
+        assert relmax(zg, lu.solve(r)) <= 1e-11
 
 
 def test_full_solution_meets_rtol_in_fp64_and_fp32(full, P, torch):

@@ -543,6 +543,7 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   constexpr int NW = 64 / CL, NTH = 32 * NW;
   static_assert(CL >= 4 && CL <= 16, "lanes 0..CL-1 and 16..16+CL-1 send the two sums");
   using AT = typename Acc<T>::type;
+  constexpr int kPre = 4;  // older tiles of a prep held in registers at once
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int me = (int)cl.block_rank();
@@ -592,19 +593,22 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   AT f0 = 0, f1 = 0, l20 = 0, l21 = 0, m0 = 0, m1 = 0, x0 = 0, x1 = 0;
   bool h2 = false, h1 = false;
   auto prep_fwd = [&](int I) {  // reads y_J, J < I - 2
+    // every load first (the older tiles' entries up to kPre of them, the
+    // newest tiles', X's), so that they share one round trip, then the FMAs
     h2 = h1 = false;
     f0 = f1 = x0 = x1 = AT(0);
+    AT q0[kPre], q1[kPre];
+    int F = 0, nJ = 0;
     if (I < NT) {
-      const int F = E.first[rb + I];
-      AT s0 = 0, s1 = 0;
-#pragma unroll 4
-      for (int J = F; J < I - 2; ++J) {
-        const T* tl = tile(I, J);
-        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
-        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
-      }
-      f0 = s0;
-      f1 = s1;
+      F = E.first[rb + I];
+      nJ = I - 2 - F;
+#pragma unroll
+      for (int q = 0; q < kPre; ++q)
+        if (q < nJ) {
+          const T* tl = tile(I, F + q);
+          q0[q] = (AT)tl[r * 64 + lane];
+          q1[q] = (AT)tl[r * 64 + lane + 32];
+        }
       h2 = I - 2 >= F;
       if (h2) {
         const T* tl = tile(I, I - 2);
@@ -622,6 +626,22 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
       const T* dt = tile(I - 1, I - 1);
       x0 = lane < r ? (AT)dt[lane * 64 + r] : AT(0);
       x1 = lane + 32 < r ? (AT)dt[(lane + 32) * 64 + r] : AT(0);
+    }
+    if (I < NT) {  // step NT forms y_{NT-1} only
+      AT s0 = 0, s1 = 0;
+#pragma unroll
+      for (int q = 0; q < kPre; ++q)
+        if (q < nJ) {
+          s0 = fma(q0[q], y[(F + q) * 64 + lane], s0);
+          s1 = fma(q1[q], y[(F + q) * 64 + lane + 32], s1);
+        }
+      for (int J = F + kPre; J < I - 2; ++J) {  // bands wider than kPre + 2 tiles
+        const T* tl = tile(I, J);
+        s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
+        s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
+      }
+      f0 = s0;
+      f1 = s1;
     }
   };
   prep_fwd(0);
@@ -656,16 +676,18 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   auto prep_bwd = [&](int I) {  // reads x_J, J >= I + 3, and the forward y_I
     bh2 = bh1 = false;
     bx0 = bx1 = AT(0);
+    AT q0[kPre], q1[kPre];
+    int R = -1, nJ = 0;
     if (I >= 0) {
-      const int R = E.last[rb + I];
-      AT v = 0;
-#pragma unroll 4
-      for (int J = I + 3; J <= R; ++J) {
-        const T* tl = tile(J, I);
-        v = fma((AT)tl[(2 * prg) * 64 + pcol], y[J * 64 + 2 * prg], v);
-        v = fma((AT)tl[(2 * prg + 1) * 64 + pcol], y[J * 64 + 2 * prg + 1], v);
-      }
-      redp[(I & 1) * 32 * NW + prg * NW + pc] = v;
+      R = E.last[rb + I];
+      nJ = R - (I + 2);
+#pragma unroll
+      for (int q = 0; q < kPre; ++q)
+        if (q < nJ) {
+          const T* tl = tile(I + 3 + q, I);
+          q0[q] = (AT)tl[(2 * prg) * 64 + pcol];
+          q1[q] = (AT)tl[(2 * prg + 1) * 64 + pcol];
+        }
       bh2 = I + 2 <= R;
       if (bh2) {
         const T* tl = tile(I + 2, I);
@@ -678,12 +700,29 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
         bn0 = (AT)nt[r * 64 + lane];
         bn1 = (AT)nt[r * 64 + lane + 32];
       }
-      bq = y[I * 64 + r] * (AT)Dinv[I * 64 + r];
+      bq = (AT)Dinv[I * 64 + r];
     }
     if (I + 1 < NT) {
       const T* dt = tile(I + 1, I + 1);
       bx0 = lane > r ? (AT)dt[r * 64 + lane] : AT(0);
       bx1 = lane + 32 > r ? (AT)dt[r * 64 + lane + 32] : AT(0);
+    }
+    if (I >= 0) {
+      AT v = 0;
+#pragma unroll
+      for (int q = 0; q < kPre; ++q)
+        if (q < nJ) {
+          const int J = I + 3 + q;
+          v = fma(q0[q], y[J * 64 + 2 * prg], v);
+          v = fma(q1[q], y[J * 64 + 2 * prg + 1], v);
+        }
+      for (int J = I + 3 + kPre; J <= R; ++J) {  // bands wider than kPre + 2 tiles
+        const T* tl = tile(J, I);
+        v = fma((AT)tl[(2 * prg) * 64 + pcol], y[J * 64 + 2 * prg], v);
+        v = fma((AT)tl[(2 * prg + 1) * 64 + pcol], y[J * 64 + 2 * prg + 1], v);
+      }
+      redp[(I & 1) * 32 * NW + prg * NW + pc] = v;
+      bq *= y[I * 64 + r];
     }
   };
   prep_bwd(NT - 1);

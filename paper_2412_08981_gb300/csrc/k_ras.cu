@@ -533,8 +533,25 @@ __device__ __forceinline__ void cluster_wait() {
 // column partials double-buffered.
 template <int CL>
 size_t block_solve_smem_cl(int max_nt) {
-  return ((size_t)max_nt * 64 + 128 + 2 * 32 * (64 / CL)) * sizeof(double);
+  constexpr int NW = 64 / CL, NTH = 32 * NW;
+  const size_t dbl = (size_t)max_nt * 64 + 128 + 2 * 32 * NW + 2 * 16 * NTH;
+  return dbl * sizeof(double) + ((size_t)3 * max_nt * sizeof(int) + 15) / 16 * 16;
 }
+
+// One element copied global -> shared without passing through registers, so
+// that no later release (the cluster barrier's arrive) has to wait for it;
+// cp_stage_wait makes this thread's copies visible to it.
+template <typename T>
+__device__ __forceinline__ void cp_stage(T* dst, const T* src) {
+  static_assert(sizeof(T) == 8 || sizeof(T) == 4, "4- or 8-byte elements");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_stage_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_stage_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <typename T, int CL>
 __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const RasView* __restrict__ views,
@@ -565,6 +582,11 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   AT* y = reinterpret_cast<AT*>(smraw);  // [NT*64] the whole vector, in every CTA
   AT* acc = y + NT * 64;                 // [2][64] acc of the newest tile row, by parity
   AT* redp = acc + 128;                  // [2][32][NW] backward partials: row pair, column
+  AT* stg = redp + 2 * 32 * NW;          // [2][16][NTH] this thread's staged loads, by step parity
+  int* efirst = reinterpret_cast<int*>(stg + 2 * 16 * NTH);  // [NT] F_I, R_I, tile offsets
+  int* elast = efirst + NT;
+  int* etoff = elast + NT;
+  static_assert(sizeof(T) == sizeof(AT), "staged copies keep the factor's element type");
   const T* base = fac + E.fac_off[p];
   const T* Mt = fac + E.fac_off[p + 1];      // M_I at tile I
   const T* Nt = Mt + (int64_t)NT * TE;       // N_I^T at tile I
@@ -574,9 +596,15 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
     z[g] = add ? z[g] + t[g] : t[g];
   }
   for (int li = tid; li < NT * 64; li += NTH) y[li] = (li < np_) ? (AT)t[dofs[off + li]] : AT(0);
+  for (int i = tid; i < NT; i += NTH) {
+    efirst[i] = E.first[rb + i];
+    elast[i] = E.last[rb + i];
+    etoff[i] = E.toff[rb + i];
+  }
   cl.sync();
   const int r = NW * me + warp;  // this warp's row (forward), column of acc and row of x (backward)
-  auto tile = [&](int I, int J) { return base + (int64_t)(E.toff[rb + I] + (J - E.first[rb + I])) * TE; };
+  auto tile = [&](int I, int J) { return base + (int64_t)(etoff[I] + (J - efirst[I])) * TE; };
+  auto S = [&](int b, int slot) -> AT& { return stg[(b * 16 + slot) * NTH + tid]; };
   // Sum over the warp of a (lanes < 16 end with it) and of b (lanes >= 16):
   // the first level halves the lanes of each, so the two take 5 adds.
   auto reduce2 = [&](AT a, AT b) {
@@ -592,50 +620,69 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   // row r of X_{I-1} (X[r][a] = dt[a][r], a < r).
   AT f0 = 0, f1 = 0, l20 = 0, l21 = 0, m0 = 0, m1 = 0, x0 = 0, x1 = 0;
   bool h2 = false, h1 = false;
-  auto prep_fwd = [&](int I) {  // reads y_J, J < I - 2
-    // every load first (the older tiles' entries up to kPre of them, the
-    // newest tiles', X's), so that they share one round trip, then the FMAs
-    h2 = h1 = false;
-    f0 = f1 = x0 = x1 = AT(0);
-    AT q0[kPre], q1[kPre];
-    int F = 0, nJ = 0;
+  // Loads run two steps ahead of their use, as asynchronous copies into this
+  // thread's staging slots (buffer = step parity): step I's gap finishes step
+  // I + 1 from its slots and starts the copies of step I + 2, and no cluster
+  // barrier's release waits on a copy in flight.  Slots: 2q, 2q + 1 the older
+  // tiles, 8-9 tile (I, I - 2), 10-11 M_I, 12-13 X_{I-1}.
+  int qF = 0, qnJ = 0;
+  bool qh2 = false, qh1 = false;
+  auto load_fwd = [&](int I) {  // the copies of step I (0 <= I <= NT)
+    const int b = I & 1;
+    qh2 = qh1 = false;
+    qF = 0;
+    qnJ = 0;
     if (I < NT) {
-      F = E.first[rb + I];
-      nJ = I - 2 - F;
+      qF = efirst[I];
+      qnJ = I - 2 - qF;
 #pragma unroll
       for (int q = 0; q < kPre; ++q)
-        if (q < nJ) {
-          const T* tl = tile(I, F + q);
-          q0[q] = (AT)tl[r * 64 + lane];
-          q1[q] = (AT)tl[r * 64 + lane + 32];
+        if (q < qnJ) {
+          const T* tl = tile(I, qF + q);
+          cp_stage(&S(b, 2 * q), tl + r * 64 + lane);
+          cp_stage(&S(b, 2 * q + 1), tl + r * 64 + lane + 32);
         }
-      h2 = I - 2 >= F;
-      if (h2) {
+      qh2 = I - 2 >= qF;
+      if (qh2) {
         const T* tl = tile(I, I - 2);
-        l20 = (AT)tl[r * 64 + lane];
-        l21 = (AT)tl[r * 64 + lane + 32];
+        cp_stage(&S(b, 8), tl + r * 64 + lane);
+        cp_stage(&S(b, 9), tl + r * 64 + lane + 32);
       }
-      h1 = I - 1 >= F;
-      if (h1) {
+      qh1 = I - 1 >= qF;
+      if (qh1) {
         const T* mt = Mt + (int64_t)I * TE;
-        m0 = (AT)mt[r * 64 + lane];
-        m1 = (AT)mt[r * 64 + lane + 32];
+        cp_stage(&S(b, 10), mt + r * 64 + lane);
+        cp_stage(&S(b, 11), mt + r * 64 + lane + 32);
       }
     }
     if (I >= 1) {
       const T* dt = tile(I - 1, I - 1);
-      x0 = lane < r ? (AT)dt[lane * 64 + r] : AT(0);
-      x1 = lane + 32 < r ? (AT)dt[(lane + 32) * 64 + r] : AT(0);
+      if (lane < r) cp_stage(&S(b, 12), dt + lane * 64 + r);
+      if (lane + 32 < r) cp_stage(&S(b, 13), dt + (lane + 32) * 64 + r);
     }
+    cp_stage_commit();
+  };
+  auto finish_fwd = [&](int I) {  // step I's operands from its copies; reads y_J, J < I - 2
+    const int b = I & 1;
+    cp_stage_wait();
+    h2 = qh2;
+    h1 = qh1;
+    l20 = h2 ? S(b, 8) : AT(0);
+    l21 = h2 ? S(b, 9) : AT(0);
+    m0 = h1 ? S(b, 10) : AT(0);
+    m1 = h1 ? S(b, 11) : AT(0);
+    x0 = (I >= 1 && lane < r) ? S(b, 12) : AT(0);
+    x1 = (I >= 1 && lane + 32 < r) ? S(b, 13) : AT(0);
+    f0 = f1 = AT(0);
     if (I < NT) {  // step NT forms y_{NT-1} only
       AT s0 = 0, s1 = 0;
 #pragma unroll
       for (int q = 0; q < kPre; ++q)
-        if (q < nJ) {
-          s0 = fma(q0[q], y[(F + q) * 64 + lane], s0);
-          s1 = fma(q1[q], y[(F + q) * 64 + lane + 32], s1);
+        if (q < qnJ) {
+          s0 = fma(S(b, 2 * q), y[(qF + q) * 64 + lane], s0);
+          s1 = fma(S(b, 2 * q + 1), y[(qF + q) * 64 + lane + 32], s1);
         }
-      for (int J = F + kPre; J < I - 2; ++J) {  // bands wider than kPre + 2 tiles
+      for (int J = qF + kPre; J < I - 2; ++J) {  // bands wider than kPre + 2 tiles
         const T* tl = tile(I, J);
         s0 = fma((AT)tl[r * 64 + lane], y[J * 64 + lane], s0);
         s1 = fma((AT)tl[r * 64 + lane + 32], y[J * 64 + lane + 32], s1);
@@ -644,7 +691,9 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
       f1 = s1;
     }
   };
-  prep_fwd(0);
+  load_fwd(0);
+  finish_fwd(0);
+  if (NT >= 1) load_fwd(1);
   for (int I = 0; I <= NT; ++I) {
     const AT* ap = acc + ((I + 1) & 1) * 64;  // acc_{I-1}
     AT* an = acc + (I & 1) * 64;              // acc_I
@@ -662,7 +711,10 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
     if (I < NT && lane < CL) cl.map_shared_rank(an, lane)[r] = y[I * 64 + r] - v;
     if (I >= 1 && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I - 1) * 64 + r] = ap[r] + v;
     cluster_arrive();
-    if (I < NT) prep_fwd(I + 1);  // reads y_J, J < I - 1: final; the exchange writes y_{I-1} and acc_I
+    if (I < NT) {  // reads y_J, J < I - 1: final; the exchange writes y_{I-1} and acc_I
+      finish_fwd(I + 1);
+      if (I + 2 <= NT) load_fwd(I + 2);
+    }
     cluster_wait();
   }
   // ---- backward: step I = NT - 1 .. -1 forms acc_I (I >= 0) and x_{I+1} (I + 1 < NT)
@@ -673,59 +725,78 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
   const int pc = tid % NW, prg = tid / NW, pcol = NW * me + pc;
   AT bl0 = 0, bl1 = 0, bn0 = 0, bn1 = 0, bx0 = 0, bx1 = 0, bq = 0;
   bool bh2 = false, bh1 = false;
-  auto prep_bwd = [&](int I) {  // reads x_J, J >= I + 3, and the forward y_I
-    bh2 = bh1 = false;
-    bx0 = bx1 = AT(0);
-    AT q0[kPre], q1[kPre];
-    int R = -1, nJ = 0;
+  // as forward: copies two steps ahead.  Slots: 2q, 2q + 1 the older tiles'
+  // column entries, 8-9 tile (I + 2, I), 10-11 N_I^T, 12-13 X_{I+1}^T, 14 1/d.
+  int qR = -1, qbnJ = 0;
+  bool qbh2 = false, qbh1 = false;
+  auto load_bwd = [&](int I) {  // the copies of step I (-1 <= I <= NT - 1)
+    const int b = I & 1;
+    qbh2 = qbh1 = false;
+    qR = -1;
+    qbnJ = 0;
     if (I >= 0) {
-      R = E.last[rb + I];
-      nJ = R - (I + 2);
+      qR = elast[I];
+      qbnJ = qR - (I + 2);
 #pragma unroll
       for (int q = 0; q < kPre; ++q)
-        if (q < nJ) {
+        if (q < qbnJ) {
           const T* tl = tile(I + 3 + q, I);
-          q0[q] = (AT)tl[(2 * prg) * 64 + pcol];
-          q1[q] = (AT)tl[(2 * prg + 1) * 64 + pcol];
+          cp_stage(&S(b, 2 * q), tl + (2 * prg) * 64 + pcol);
+          cp_stage(&S(b, 2 * q + 1), tl + (2 * prg + 1) * 64 + pcol);
         }
-      bh2 = I + 2 <= R;
-      if (bh2) {
+      qbh2 = I + 2 <= qR;
+      if (qbh2) {
         const T* tl = tile(I + 2, I);
-        bl0 = (AT)tl[lane * 64 + r];
-        bl1 = (AT)tl[(lane + 32) * 64 + r];
+        cp_stage(&S(b, 8), tl + lane * 64 + r);
+        cp_stage(&S(b, 9), tl + (lane + 32) * 64 + r);
       }
-      bh1 = I + 1 <= R;
-      if (bh1) {
+      qbh1 = I + 1 <= qR;
+      if (qbh1) {
         const T* nt = Nt + (int64_t)I * TE;
-        bn0 = (AT)nt[r * 64 + lane];
-        bn1 = (AT)nt[r * 64 + lane + 32];
+        cp_stage(&S(b, 10), nt + r * 64 + lane);
+        cp_stage(&S(b, 11), nt + r * 64 + lane + 32);
       }
-      bq = (AT)Dinv[I * 64 + r];
+      cp_stage(&S(b, 14), Dinv + I * 64 + r);
     }
     if (I + 1 < NT) {
       const T* dt = tile(I + 1, I + 1);
-      bx0 = lane > r ? (AT)dt[r * 64 + lane] : AT(0);
-      bx1 = lane + 32 > r ? (AT)dt[r * 64 + lane + 32] : AT(0);
+      if (lane > r) cp_stage(&S(b, 12), dt + r * 64 + lane);
+      if (lane + 32 > r) cp_stage(&S(b, 13), dt + r * 64 + lane + 32);
     }
+    cp_stage_commit();
+  };
+  auto finish_bwd = [&](int I) {  // step I's operands; reads x_J, J >= I + 3, and the forward y_I
+    const int b = I & 1;
+    cp_stage_wait();
+    bh2 = qbh2;
+    bh1 = qbh1;
+    bl0 = bh2 ? S(b, 8) : AT(0);
+    bl1 = bh2 ? S(b, 9) : AT(0);
+    bn0 = bh1 ? S(b, 10) : AT(0);
+    bn1 = bh1 ? S(b, 11) : AT(0);
+    bx0 = (I + 1 < NT && lane > r) ? S(b, 12) : AT(0);
+    bx1 = (I + 1 < NT && lane + 32 > r) ? S(b, 13) : AT(0);
     if (I >= 0) {
       AT v = 0;
 #pragma unroll
       for (int q = 0; q < kPre; ++q)
-        if (q < nJ) {
+        if (q < qbnJ) {
           const int J = I + 3 + q;
-          v = fma(q0[q], y[J * 64 + 2 * prg], v);
-          v = fma(q1[q], y[J * 64 + 2 * prg + 1], v);
+          v = fma(S(b, 2 * q), y[J * 64 + 2 * prg], v);
+          v = fma(S(b, 2 * q + 1), y[J * 64 + 2 * prg + 1], v);
         }
-      for (int J = I + 3 + kPre; J <= R; ++J) {  // bands wider than kPre + 2 tiles
+      for (int J = I + 3 + kPre; J <= qR; ++J) {  // bands wider than kPre + 2 tiles
         const T* tl = tile(J, I);
         v = fma((AT)tl[(2 * prg) * 64 + pcol], y[J * 64 + 2 * prg], v);
         v = fma((AT)tl[(2 * prg + 1) * 64 + pcol], y[J * 64 + 2 * prg + 1], v);
       }
       redp[(I & 1) * 32 * NW + prg * NW + pc] = v;
-      bq *= y[I * 64 + r];
+      bq = S(b, 14) * y[I * 64 + r];
     }
   };
-  prep_bwd(NT - 1);
+  load_bwd(NT - 1);
+  finish_bwd(NT - 1);
+  if (NT - 2 >= -1) load_bwd(NT - 2);
   __syncthreads();  // its partials in redp
   for (int I = NT - 1; I >= -1; --I) {
     const AT* ap = acc + ((I + 1) & 1) * 64;  // acc_{I+1}
@@ -747,7 +818,10 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
     if (I >= 0 && lane < CL) cl.map_shared_rank(an, lane)[r] = bq - v;
     if (I + 1 < NT && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I + 1) * 64 + r] = ap[r] + v;
     cluster_arrive();
-    if (I >= 0) prep_bwd(I - 1);  // reads x_J, J >= I + 2, and y_{I-1}: final; the exchange writes x_{I+1}, acc_I
+    if (I >= 0) {  // reads x_J, J >= I + 2, and y_{I-1}: final; the exchange writes x_{I+1}, acc_I
+      finish_bwd(I - 1);
+      if (I - 2 >= -1) load_bwd(I - 2);
+    }
     cluster_wait();
     __syncthreads();  // redp is written after the arrive, which orders only what came before it
   }

@@ -710,11 +710,11 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
     const AT v = reduce2(a0 + a1, yv);
     if (I < NT && lane < CL) cl.map_shared_rank(an, lane)[r] = y[I * 64 + r] - v;
     if (I >= 1 && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I - 1) * 64 + r] = ap[r] + v;
+    // the next step's sums while the sends travel (the arrive's release
+    // waits for them); then the copies two steps ahead, after the arrive
+    if (I < NT) finish_fwd(I + 1);  // reads y_J, J < I - 1: final; the exchange writes y_{I-1} and acc_I
     cluster_arrive();
-    if (I < NT) {  // reads y_J, J < I - 1: final; the exchange writes y_{I-1} and acc_I
-      finish_fwd(I + 1);
-      if (I + 2 <= NT) load_fwd(I + 2);
-    }
+    if (I + 2 <= NT) load_fwd(I + 2);
     cluster_wait();
   }
   // ---- backward: step I = NT - 1 .. -1 forms acc_I (I >= 0) and x_{I+1} (I + 1 < NT)
@@ -817,11 +817,9 @@ __global__ void __launch_bounds__(32 * (64 / CL), 1) k_block_solve_cluster(const
     const AT v = reduce2(a, xv);
     if (I >= 0 && lane < CL) cl.map_shared_rank(an, lane)[r] = bq - v;
     if (I + 1 < NT && lane >= 16 && lane < 16 + CL) cl.map_shared_rank(y, lane - 16)[(I + 1) * 64 + r] = ap[r] + v;
+    if (I >= 0) finish_bwd(I - 1);  // reads x_J, J >= I + 2, and y_{I-1}: final; the exchange writes x_{I+1}, acc_I
     cluster_arrive();
-    if (I >= 0) {  // reads x_J, J >= I + 2, and y_{I-1}: final; the exchange writes x_{I+1}, acc_I
-      finish_bwd(I - 1);
-      if (I - 2 >= -1) load_bwd(I - 2);
-    }
+    if (I - 2 >= -1) load_bwd(I - 2);
     cluster_wait();
     __syncthreads();  // redp is written after the arrive, which orders only what came before it
   }

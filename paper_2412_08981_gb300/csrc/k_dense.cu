@@ -751,15 +751,61 @@ __global__ void __launch_bounds__(256, LevelCtas<T>::value) k_ldlt_blocks(T* __r
 template <typename T>
 __global__ void __launch_bounds__(256, LevelCtas<T>::value) k_ldlt_blocks_batch(const BlockItem* __restrict__ items,
                                                            const int32_t* __restrict__ cta_ptr,
-                                                           const int32_t* __restrict__ cta_list) {
+                                                           const int32_t* __restrict__ cta_list,
+                                                           int* __restrict__ ctr, int nbins) {
   using AT = typename Acc<T>::type;
   extern __shared__ unsigned char smraw[];
   AT* sm = reinterpret_cast<AT*>(smraw);
   __shared__ BlockItem it;  // the current item, read from shared memory where it is used
-  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+  if (ctr == nullptr) {  // one static list per CTA
+    for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+      __syncthreads();  // the previous item is finished with
+      if (threadIdx.x == 0) it = items[cta_list[q]];
+      __syncthreads();
+      factor_block<T, AT>(static_cast<T*>(it.fac), it.E, it.p, sm, it.info);
+    }
+    return;
+  }
+  // One list per SM (the CTAs resident on an SM share its FP64 pipe, so it is
+  // the SMs' loads that are balanced): a CTA takes the next item of its own
+  // SM's list.  Once that is exhausted it takes items only from lists that no
+  // CTA of their own SM works on (an SM this launch did not reach, or left),
+  // and leaves when there are none: a CTA that took another SM's items would
+  // keep sharing its own SM's pipe with the block still running there, which
+  // is often the list's largest.  ctr[b] counts the items taken from list b,
+  // ctr[nbins + b] the CTAs of SM b still on it (both zeroed before the launch).
+  __shared__ int got;
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  const int home = (int)(smid % (unsigned)nbins);
+  int* active = ctr + nbins;
+  int bin = home, tried = 0;
+  bool own = true;
+  if (threadIdx.x == 0) atomicAdd(&active[home], 1);
+  for (;;) {
     __syncthreads();  // the previous item is finished with
-    if (threadIdx.x == 0) it = items[cta_list[q]];
+    if (threadIdx.x == 0) {
+      int g = -1;
+      while (tried < nbins) {
+        if (own || atomicAdd(&active[bin], 0) == 0) {
+          const int q = atomicAdd(&ctr[bin], 1);
+          if (q < cta_ptr[bin + 1] - cta_ptr[bin]) {
+            g = cta_list[cta_ptr[bin] + q];
+            break;
+          }
+          if (own) {  // the home list is exhausted
+            atomicSub(&active[home], 1);
+            own = false;
+          }
+        }
+        bin = bin + 1 == nbins ? 0 : bin + 1;
+        ++tried;
+      }
+      if (g >= 0) it = items[g];
+      got = g;
+    }
     __syncthreads();
+    if (got < 0) break;
     factor_block<T, AT>(static_cast<T*>(it.fac), it.E, it.p, sm, it.info);
   }
 }
@@ -1569,13 +1615,13 @@ void launch_ldlt_blocks(T* fac, const EnvDev& E, const int32_t* cta_ptr, const i
 
 template <typename T>
 void launch_ldlt_blocks_batch(const BlockItem* items, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
-                              cudaStream_t s) {
+                              cudaStream_t s, int* sm_ctr, int nbins) {
   using AT = typename Acc<T>::type;
   if (grid < 1) return;
   const size_t smem = (size_t)(2 * 64 * 65) * sizeof(AT);  // the largest phase (trailing pair)
   static std::once_flag attr;
   std::call_once(attr, [&] { resident_per_sm(reinterpret_cast<const void*>(k_ldlt_blocks_batch<T>), smem); });
-  k_ldlt_blocks_batch<T><<<grid, 256, smem, s>>>(items, cta_ptr, cta_list);
+  k_ldlt_blocks_batch<T><<<grid, 256, smem, s>>>(items, cta_ptr, cta_list, sm_ctr, nbins);
 }
 
 template <typename T>
@@ -1633,7 +1679,7 @@ int ldlt_blocks_tc_per_sm() {
   template void launch_ldlt_xfill<T>(T*, const EnvDev&, const int32_t*, int, int, cudaStream_t); \
   template void launch_ldlt_mnfill<T>(T*, const EnvDev&, int, cudaStream_t);                      \
   template void launch_ldlt_blocks_batch<T>(const BlockItem*, const int32_t*, const int32_t*, int,    \
-                                            cudaStream_t);                                        \
+                                            cudaStream_t, int*, int);                             \
   template int ldlt_blocks_batch_per_sm<T>();                                                     \
   template void launch_ldlt_blocks<T>(T*, const EnvDev&, const int32_t*, const int32_t*, int,     \
                                       int*, cudaStream_t);                                       \

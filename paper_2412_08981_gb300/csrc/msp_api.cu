@@ -191,6 +191,8 @@ struct msp_instance {
   BlockItem* fz_items = nullptr;
   int32_t *fz_ptr = nullptr, *fz_list = nullptr;
   int fz_grid = 0;
+  int* fz_ctr = nullptr;  // [2 fz_bins] items taken from, and CTAs on, each SM's list (zeroed before every launch)
+  int fz_bins = 0;
   bool fz_f32 = false;
   double fz_flops = 0;
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
@@ -711,8 +713,11 @@ int enqueue_factor(msp_instance* I, cudaStream_t s0, bool defer = false) {
     for (int l = 1; l < L; ++l)
       if (h->dev[l].fac_blocks && !h->dev[l].ilu) MSP_CUDA(cudaStreamWaitEvent(s0, I->bev[l][0], 0));
     ProfScope ps(I->prof, PK_LDLT_BLOCKS, s0);
-    if (I->fz_f32) launch_ldlt_blocks_batch<float>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0);
-    else launch_ldlt_blocks_batch<double>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0);
+    MSP_CUDA(cudaMemsetAsync(I->fz_ctr, 0, sizeof(int) * 2 * I->fz_bins, s0));
+    if (I->fz_f32)
+      launch_ldlt_blocks_batch<float>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0, I->fz_ctr, I->fz_bins);
+    else
+      launch_ldlt_blocks_batch<double>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0, I->fz_ctr, I->fz_bins);
     ps.account(0, I->fz_flops);
   }
   for (int a = 0; a < 2; ++a) {
@@ -1137,10 +1142,10 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
       I->fz_flops += D.fac_flops;
       for (int p = 0; p < H.nsub; ++p) {
         const int32_t* R = &H.tile_last[H.sub_trow[p]];
-        int64_t c = 0;
+        int64_t c = 0;  // the block's FP64 flops over 64 (the FP64 pipe is the bound)
         for (int k = 0; k < H.sub_nt[p]; ++k) {
           const int64_t rem = R[k] - k;
-          c += 1 + rem + rem * (rem - 1) + rem;
+          c += rem * (rem - 1) / 2 * 2 * 64 * 64 + rem * 64 * 65 + rem * 64 * 65 + 2 * 64 * 64 / 3;
         }
         items.push_back(BlockItem{I->fac[l], D.env, p, I->info});
         cost.push_back(c);
@@ -1151,12 +1156,21 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
       MSP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
       I->fz_f32 = h->opt.factor_precision == MSP_F32;
       const int per_sm = I->fz_f32 ? ldlt_blocks_batch_per_sm<float>() : ldlt_blocks_batch_per_sm<double>();
+      // One longest-first list per SM: the CTAs an SM holds share its FP64
+      // pipe, so it is the SMs' sums that must come out even (balancing the
+      // CTAs' lists left the busiest SM 11 % above the median, as the CTAs
+      // land on SMs in an order of the hardware's).  The per_sm CTAs of an SM
+      // take its items in turn; a list whose SM the launch did not reach is
+      // taken by the CTAs that have finished their own.
       std::vector<int32_t> cptr, clist;
-      lpt_lists(cost, std::max(1, std::min((int)items.size(), nsm * per_sm)), cptr, clist);
+      const int bins = std::max(1, std::min((int)items.size(), nsm));
+      lpt_lists(cost, bins, cptr, clist);
       I->fz_items = A.upload(items);
       I->fz_ptr = A.upload(cptr);
       I->fz_list = A.upload(clist);
-      I->fz_grid = (int)cptr.size() - 1;
+      I->fz_bins = bins;
+      I->fz_ctr = A.alloc<int>(2 * (size_t)bins);
+      I->fz_grid = bins * per_sm;
       if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
     }
   }

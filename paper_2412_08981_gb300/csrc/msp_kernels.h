@@ -124,9 +124,13 @@ struct BlockItem {
   int32_t p;
   int* info;
 };
+// sm_ctr == nullptr: CTA b factors the items cta_list[cta_ptr[b] .. cta_ptr[b+1]).
+// Else the lists are per SM (nbins of them): a CTA takes items from its own
+// SM's list, then from lists no CTA of their SM works on; sm_ctr[2 nbins]
+// must be zero at launch.
 template <typename T>
 void launch_ldlt_blocks_batch(const BlockItem* items, const int32_t* cta_ptr, const int32_t* cta_list, int grid,
-                              cudaStream_t s);
+                              cudaStream_t s, int* sm_ctr = nullptr, int nbins = 0);
 template <typename T>
 int ldlt_blocks_batch_per_sm();
 // Persistent factorisation of the blocks of a level whose factors are stored

@@ -142,7 +142,7 @@ template <typename T, int NCW, int CTAS>
 __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     const RasView* __restrict__ views, int nviews, const __grid_constant__ RasVecs vecs,
     const int32_t* __restrict__ cta_ptr, const int32_t* __restrict__ cta_list, int add, int max_nt,
-    int nslot, int inject) {
+    int nslot, int inject, int* __restrict__ claim, int nbins) {
   using AT = typename Acc<T>::type;
   constexpr int kConsumers = NCW;
   // inject != 0 (failure-injection tests only): the producer issues no copies,
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
   const MetaSm pm{meta, meta + max_nt, meta + 2 * max_nt};                      // producer's
   const MetaSm cm{meta + 3 * max_nt, meta + 4 * max_nt, meta + 5 * max_nt};    // consumers'
   __shared__ int sflag;
+  __shared__ int slist;  // the work list this CTA takes
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int rl = lane >> 3, g = lane & 7;            // row within a 4-row pass, lane within the row
@@ -180,8 +181,27 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       mbar_init(&empty[s], kConsumers);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // claim == nullptr: list blockIdx.x.  Else the lists come per_sm to an SM
+    // (the host balanced the SMs' sums, then split each over its CTAs): a
+    // CTA takes list (its SM, its arrival rank there); one whose list is
+    // taken, or whose SM holds more CTAs than that, takes the first list no
+    // one has.  There are as many lists as CTAs, so each is taken once.
+    // claim[0, nbins): arrivals per SM, claim[nbins, nbins + G): list taken.
+    int lid = blockIdx.x;
+    if (claim != nullptr) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      const int b = (int)(smid % (unsigned)nbins), per = gridDim.x / nbins;
+      const int rank = atomicAdd(&claim[b], 1);
+      lid = -1;
+      if (rank < per && atomicExch(&claim[nbins + b * per + rank], 1) == 0) lid = b * per + rank;
+      for (int i = 0; lid < 0 && i < (int)gridDim.x; ++i)
+        if (atomicExch(&claim[nbins + i], 1) == 0) lid = i;
+    }
+    slist = lid;
   }
   __syncthreads();
+  const int mylist = slist;
 
   int* err = views[0].err;  // the error word of the item in hand
   if (warp == kConsumers) {  // ------------------------------------ producer
@@ -195,7 +215,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
       }
       ++seq;
     };
-    for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+    for (int q = cta_ptr[mylist]; q < cta_ptr[mylist + 1]; ++q) {
       const int vw = cta_list[q] >> kViewShift, p = cta_list[q] & ((1 << kViewShift) - 1);
       if (vecs.z[vw] == nullptr) continue;
       const EnvDev& E = views[vw].E;
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), CTAS) k_ras_solve(
     if (lane == 0) mbar_arrive(&empty[seq % nslot]);
     ++seq;
   };
-  for (int q = cta_ptr[blockIdx.x]; q < cta_ptr[blockIdx.x + 1]; ++q) {
+  for (int q = cta_ptr[mylist]; q < cta_ptr[mylist + 1]; ++q) {
     const int vw = cta_list[q] >> kViewShift, p = cta_list[q] & ((1 << kViewShift) - 1);
     const double* __restrict__ t = vecs.t[vw];
     double* __restrict__ z = vecs.z[vw];
@@ -874,7 +894,8 @@ int ras_slots(int max_nt, bool wide) {
 
 template <typename T, bool W>
 void launch_ras_cfg(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
-                    const int32_t* cta_list, int grid, int max_nt, int add, int inject, cudaStream_t s) {
+                    const int32_t* cta_list, int grid, int max_nt, int add, int inject, cudaStream_t s,
+                    int* claim, int nbins) {
   constexpr int NCW = RasCfg<T, W>::NCW, CTAS = RasCfg<T, W>::CTAS;
   auto kern = k_ras_solve<T, NCW, CTAS>;
   static std::once_flag attr;
@@ -885,17 +906,18 @@ void launch_ras_cfg(const RasView* views, int nviews, const RasVecs& vecs, const
   const int nslot = ras_slots_cfg<T, W>(max_nt);  // the host checked at set-up that this is enough
   const size_t smem = (size_t)nslot * ((size_t)TE * sizeof(T) + 2 * sizeof(uint64_t)) + ras_fixed_bytes<T, W>(max_nt);
   if (grid < 1 || nviews < 1) return;
-  kern<<<grid, 32 * (NCW + 1), smem, s>>>(views, nviews, vecs, cta_ptr, cta_list, add, max_nt, nslot, inject);
+  kern<<<grid, 32 * (NCW + 1), smem, s>>>(views, nviews, vecs, cta_ptr, cta_list, add, max_nt, nslot, inject, claim,
+                                          nbins);
 }
 
 template <typename T>
 void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, int max_nt, int add, bool wide, cudaStream_t s,
-                      int inject) {
+                      int inject, int* claim, int nbins) {
   if (wide)
-    launch_ras_cfg<T, true>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s);
+    launch_ras_cfg<T, true>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s, claim, nbins);
   else
-    launch_ras_cfg<T, false>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s);
+    launch_ras_cfg<T, false>(views, nviews, vecs, cta_ptr, cta_list, grid, max_nt, add, inject, s, claim, nbins);
 }
 
 size_t block_solve_cluster_smem(int max_nt) { return block_solve_smem_cl<kCl>(max_nt); }
@@ -952,7 +974,7 @@ void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs&
 
 #define MSP_RAS_INST(T)                                                                          \
   template void launch_ras_solve<T>(const RasView*, int, const RasVecs&, const int32_t*, const int32_t*, \
-                                    int, int, int, bool, cudaStream_t, int);                     \
+                                    int, int, int, bool, cudaStream_t, int, int*, int);          \
   template int ras_slots<T>(int, bool);                                                          \
   template int ras_ctas_per_sm<T>(bool);
 MSP_RAS_INST(double)

@@ -138,6 +138,7 @@ struct DevLevel {
   int max_band = 0;               // max over tile rows of 1 + (R_I - I)
   bool ras_wide = false;          // the staged solve in its one-CTA-per-SM form
   int ras_grid = 0;               // CTAs of the RAS solve and their subdomain lists
+  int ras_bins = 0;               // > 0: the lists come ras_grid / ras_bins to an SM (taken by SM on the device)
   int32_t *ras_cta_ptr = nullptr, *ras_cta_list = nullptr;
   bool fac_blocks = false;        // whole-block persistent factorisation on this level
   int fac_grid = 0;               // its CTAs and their block lists
@@ -179,6 +180,7 @@ struct msp_instance {
   int* info = nullptr;
   int* ras_err = nullptr;  // bit 4: a bounded wait of the staged RAS solve expired
   RasView* rview = nullptr;  // device: this instance's view of every level for the triangular solves
+  int* ras_claim = nullptr;  // device: the RAS launch's per-SM arrivals and taken lists (zeroed per launch)
   int expire_ras = 0;      // msp_debug_expire_waits: staged RAS launches left to starve of copies
   int m = 30;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *res = nullptr, *part = nullptr, *hdev = nullptr;
@@ -395,7 +397,29 @@ int upload_level(msp_hierarchy* h, int l, cudaStream_t s) {
       const int per_sm = st == Store::F64   ? ras_ctas_per_sm<double>(D.ras_wide)
                          : st == Store::F32 ? ras_ctas_per_sm<float>(D.ras_wide)
                                             : ras_ctas_per_sm<__nv_bfloat16>(D.ras_wide);
-      lpt_lists(cost, std::max(1, std::min(H.nsub, nsm * per_sm)), cptr, clist);
+      const int G = nsm * per_sm;
+      if (H.nsub >= G && per_sm > 1) {
+        // the CTAs an SM holds share its FP64 / FP32 issue, so the SMs' sums
+        // are balanced first, then each SM's share over its CTAs
+        std::vector<int32_t> bptr, blist;
+        lpt_lists(cost, nsm, bptr, blist);
+        cptr.assign(1, 0);
+        clist.clear();
+        for (int b = 0; b < nsm; ++b) {
+          std::vector<int64_t> sub;
+          for (int k = bptr[b]; k < bptr[b + 1]; ++k) sub.push_back(cost[blist[k]]);
+          std::vector<int32_t> sptr, slist;
+          lpt_lists(sub, per_sm, sptr, slist);
+          for (int r = 0; r < per_sm; ++r) {
+            for (int k = sptr[r]; k < sptr[r + 1]; ++k) clist.push_back(blist[bptr[b] + slist[k]]);
+            cptr.push_back((int32_t)clist.size());
+          }
+        }
+        D.ras_bins = nsm;
+      } else {
+        lpt_lists(cost, std::max(1, std::min(H.nsub, G)), cptr, clist);
+        D.ras_bins = 0;
+      }
     }
     D.ras_grid = (int)cptr.size() - 1;
     D.ras_cta_ptr = A.upload(cptr);
@@ -816,15 +840,17 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   } else {
     const int inj = I->expire_ras > 0 ? 1 : 0;
     if (inj) --I->expire_ras;
+    int* claim = D.ras_bins > 0 ? I->ras_claim : nullptr;
+    if (claim) cudaMemsetAsync(claim, 0, sizeof(int) * ((size_t)D.ras_bins + D.ras_grid), s);
     if (st == Store::BF16)
       launch_ras_solve<__nv_bfloat16>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt,
-                                      add, D.ras_wide, s, inj);
+                                      add, D.ras_wide, s, inj, claim, D.ras_bins);
     else if (st == Store::F32)
       launch_ras_solve<float>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
-                              D.ras_wide, s, inj);
+                              D.ras_wide, s, inj, claim, D.ras_bins);
     else
       launch_ras_solve<double>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
-                               D.ras_wide, s, inj);
+                               D.ras_wide, s, inj, claim, D.ras_bins);
   }
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
@@ -1124,6 +1150,10 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
       rv[l] = RasView{I->fac[l], D.env, D.sub_ptr, D.sub_dofs, D.sub_own, D.dir_list, D.ndir, I->ras_err};
     }
     I->rview = A.upload(rv);
+    size_t claim = 0;
+    for (int l = 0; l < L; ++l)
+      if (h->dev[l].ras_bins > 0) claim = std::max(claim, (size_t)h->dev[l].ras_bins + h->dev[l].ras_grid);
+    if (claim) I->ras_claim = A.alloc<int>(claim);
   }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
   // FP64 factors: one work list over the blocks of every persistent level

@@ -211,10 +211,13 @@ int ras_slots(int max_nt, bool wide);
 // CTAs of k_ras_solve that share an SM (the persistent grid is this x SMs)
 template <typename T>
 int ras_ctas_per_sm(bool wide);
+// claim != nullptr: the grid's lists come per_sm to each of nbins SMs and a
+// CTA takes its SM's (claim[nbins + grid] ints, zero at launch); else CTA b
+// takes list b.
 template <typename T>
 void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, const int32_t* cta_ptr,
                       const int32_t* cta_list, int grid, int max_nt, int add, bool wide, cudaStream_t s,
-                      int inject = 0);
+                      int inject = 0, int* claim = nullptr, int nbins = 0);
 // y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level) for
 // each of `nviews` views, each on a cluster of 8 CTAs that split every tile
 // row of both sweeps and exchange partial results through distributed shared

@@ -610,16 +610,41 @@ __device__ void trail_pair(const T* __restrict__ dt, const T* __restrict__ li,
   });
   read_elems<T, TE>(lj, [&](int e, T v) { Lt[(e & 63) * LD + (e >> 6)] = (AT)v; });
   __syncthreads();
-  // 4x4 output blocks: all 256 of a general pair; for a diagonal pair only the
-  // 136 blocks on or below the diagonal, numbered densely so that they fill
-  // whole warps (an idle lane costs as much FP64 issue time as a busy one)
+  // 4x4 output blocks: all 256 of a general pair.  A diagonal pair needs the
+  // 2080 entries on or below the diagonal (an idle lane costs as much FP64
+  // issue time as a busy one): its 120 blocks strictly below the diagonal go
+  // to warps 0-3, one block a thread, and the 160 entries of the 16 diagonal
+  // blocks to warps 4-7, one entry a thread (a second pass for the last 32);
+  // 69 warp instructions a step of m where 4x4 blocks for all 136 took 80.
+  // (FP32 arithmetic keeps the 136 blocks: its issue is cheap, and the split
+  // would cost the FP32 kernels registers)
   int rb, cb;
   if (!diagonal) {
     rb = tid >> 4;
     cb = tid & 15;
-  } else {
+  } else if (sizeof(AT) == 4) {
     if (tid >= 136) return;
     pair_of(tid, rb, cb);  // rb >= cb
+  } else if (tid < 128) {
+    if (tid >= 120) return;
+    pair_of(tid, rb, cb);  // cb <= rb < 15
+    ++rb;
+  } else {
+#pragma unroll 1
+    for (int u = tid - 128; u < 160; u += 128) {
+      int x, y;
+      pair_of(u % 10, x, y);  // y <= x < 4
+      const int r = (u / 10) * 4 + x, c = (u / 10) * 4 + y;
+      AT a0 = 0, a1 = 0;
+#pragma unroll 8
+      for (int m = 0; m < T64; m += 2) {
+        a0 = fma(Wt[m * LD + r], Lt[m * LD + c], a0);
+        a1 = fma(Wt[(m + 1) * LD + r], Lt[(m + 1) * LD + c], a1);
+      }
+      T* o = out + r * 64 + c;
+      *o = (T)((AT)*o - (a0 + a1));
+    }
+    return;
   }
   const int r0 = rb * 4, c0 = cb * 4;
   AT acc[4][4];

@@ -524,6 +524,19 @@ MSP_API int msp_profile_read(msp_instance* inst, int kclass, msp_kernel_profile*
  * Errors: MSP_ERR_INVALID (NULL instance, count < 0). */
 MSP_API int msp_debug_expire_waits(msp_instance* inst, int count);
 
+/* ---- work placement, for tests (no counterpart in the paper) ----
+ * The persistent FP64 factorisation and the staged RAS solves split their
+ * blocks into work lists per SM, and a CTA takes the list of the SM it runs
+ * on (read on the device); lists that no CTA of their SM takes (an SM the
+ * launch does not reach, or a CTA beyond its SM's share) are taken by other
+ * CTAs.  With on != 0 this instance's launches use twice as many lists as
+ * SMs, so that half of the lists are always taken that way; the blocks'
+ * arithmetic does not depend on which CTA takes them, so factors and
+ * solutions are bitwise those of on == 0.  A factorisation graph captured
+ * before the switch is dropped (the call waits for the instance's stream).
+ * Errors: MSP_ERR_INVALID (NULL instance), MSP_ERR_CUDA. */
+MSP_API int msp_debug_spread_work(msp_instance* inst, int on);
+
 /* ---- tensor-core self-check (no counterpart in the paper) ----
  * Multiplies two fixed 128 x 64 BF16 matrices with integer entries on the
  * current device through the library's tcgen05 path (operands in shared

@@ -193,8 +193,10 @@ struct msp_instance {
   BlockItem* fz_items = nullptr;
   int32_t *fz_ptr = nullptr, *fz_list = nullptr;
   int fz_grid = 0;
-  int* fz_ctr = nullptr;  // [2 fz_bins] items taken from, and CTAs on, each SM's list (zeroed before every launch)
+  int* fz_ctr = nullptr;  // [4 fz_bins] items taken from, and CTAs on, each list (zeroed before every launch)
   int fz_bins = 0;
+  int32_t *fz_ptr2 = nullptr, *fz_list2 = nullptr;  // the same items over 2 fz_bins lists (msp_debug_spread_work)
+  bool spread_work = false;  // msp_debug_spread_work: twice as many work lists as SMs
   bool fz_f32 = false;
   double fz_flops = 0;
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
@@ -737,11 +739,14 @@ int enqueue_factor(msp_instance* I, cudaStream_t s0, bool defer = false) {
     for (int l = 1; l < L; ++l)
       if (h->dev[l].fac_blocks && !h->dev[l].ilu) MSP_CUDA(cudaStreamWaitEvent(s0, I->bev[l][0], 0));
     ProfScope ps(I->prof, PK_LDLT_BLOCKS, s0);
-    MSP_CUDA(cudaMemsetAsync(I->fz_ctr, 0, sizeof(int) * 2 * I->fz_bins, s0));
+    const int nb = I->spread_work ? 2 * I->fz_bins : I->fz_bins;
+    const int32_t* ptr = I->spread_work ? I->fz_ptr2 : I->fz_ptr;
+    const int32_t* list = I->spread_work ? I->fz_list2 : I->fz_list;
+    MSP_CUDA(cudaMemsetAsync(I->fz_ctr, 0, sizeof(int) * 2 * nb, s0));
     if (I->fz_f32)
-      launch_ldlt_blocks_batch<float>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0, I->fz_ctr, I->fz_bins);
+      launch_ldlt_blocks_batch<float>(I->fz_items, ptr, list, I->fz_grid, s0, I->fz_ctr, nb);
     else
-      launch_ldlt_blocks_batch<double>(I->fz_items, I->fz_ptr, I->fz_list, I->fz_grid, s0, I->fz_ctr, I->fz_bins);
+      launch_ldlt_blocks_batch<double>(I->fz_items, ptr, list, I->fz_grid, s0, I->fz_ctr, nb);
     ps.account(0, I->fz_flops);
   }
   for (int a = 0; a < 2; ++a) {
@@ -841,16 +846,19 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
     const int inj = I->expire_ras > 0 ? 1 : 0;
     if (inj) --I->expire_ras;
     int* claim = D.ras_bins > 0 ? I->ras_claim : nullptr;
-    if (claim) cudaMemsetAsync(claim, 0, sizeof(int) * ((size_t)D.ras_bins + D.ras_grid), s);
+    // msp_debug_spread_work: twice as many bins as SMs, so half of each SM's
+    // CTAs find their rank beyond its share and claim a list no SM owns
+    const int nb = (I->spread_work && D.ras_grid % (2 * std::max(1, D.ras_bins)) == 0) ? 2 * D.ras_bins : D.ras_bins;
+    if (claim) cudaMemsetAsync(claim, 0, sizeof(int) * ((size_t)nb + D.ras_grid), s);
     if (st == Store::BF16)
       launch_ras_solve<__nv_bfloat16>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt,
-                                      add, D.ras_wide, s, inj, claim, D.ras_bins);
+                                      add, D.ras_wide, s, inj, claim, nb);
     else if (st == Store::F32)
       launch_ras_solve<float>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
-                              D.ras_wide, s, inj, claim, D.ras_bins);
+                              D.ras_wide, s, inj, claim, nb);
     else
       launch_ras_solve<double>(I->rview + l, 1, vv, D.ras_cta_ptr, D.ras_cta_list, D.ras_grid, D.max_nt, add,
-                               D.ras_wide, s, inj, claim, D.ras_bins);
+                               D.ras_wide, s, inj, claim, nb);
   }
   // algorithmic: the stored envelope of L read by each of the two sweeps
   // (the element count of an L and U pair), gather + scatter of the vectors
@@ -1152,7 +1160,7 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
     I->rview = A.upload(rv);
     size_t claim = 0;
     for (int l = 0; l < L; ++l)
-      if (h->dev[l].ras_bins > 0) claim = std::max(claim, (size_t)h->dev[l].ras_bins + h->dev[l].ras_grid);
+      if (h->dev[l].ras_bins > 0) claim = std::max(claim, (size_t)2 * h->dev[l].ras_bins + h->dev[l].ras_grid);
     if (claim) I->ras_claim = A.alloc<int>(claim);
   }
   if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
@@ -1192,14 +1200,17 @@ int alloc_instance(msp_hierarchy* h, msp_instance* I) {
       // land on SMs in an order of the hardware's).  The per_sm CTAs of an SM
       // take its items in turn; a list whose SM the launch did not reach is
       // taken by the CTAs that have finished their own.
-      std::vector<int32_t> cptr, clist;
+      std::vector<int32_t> cptr, clist, sptr, slist;
       const int bins = std::max(1, std::min((int)items.size(), nsm));
       lpt_lists(cost, bins, cptr, clist);
+      lpt_lists(cost, 2 * bins, sptr, slist);  // half of them no SM's own (msp_debug_spread_work)
       I->fz_items = A.upload(items);
       I->fz_ptr = A.upload(cptr);
       I->fz_list = A.upload(clist);
+      I->fz_ptr2 = A.upload(sptr);
+      I->fz_list2 = A.upload(slist);
       I->fz_bins = bins;
-      I->fz_ctr = A.alloc<int>(2 * (size_t)bins);
+      I->fz_ctr = A.alloc<int>(4 * (size_t)bins);
       I->fz_grid = bins * per_sm;
       if (!A.ok) return fail(MSP_ERR_OOM, "device allocation failed for an instance");
     }
@@ -2642,6 +2653,20 @@ int msp_debug_expire_waits(msp_instance* I, int count) {
   msp::g_last_error.clear();
   if (!I || count < 0) return fail(MSP_ERR_INVALID, "NULL instance or negative count");
   I->expire_ras = count;
+  return MSP_OK;
+}
+
+int msp_debug_spread_work(msp_instance* I, int on) {
+  msp::g_last_error.clear();
+  if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
+  if (I->spread_work != (on != 0)) {
+    I->spread_work = on != 0;
+    if (I->fac_graph) {  // the captured factorisation holds the lists it was captured with
+      MSP_CUDA(cudaStreamSynchronize(I->stream));
+      cudaGraphExecDestroy(I->fac_graph);
+      I->fac_graph = nullptr;
+    }
+  }
   return MSP_OK;
 }
 

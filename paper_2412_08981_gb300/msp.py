@@ -127,6 +127,7 @@ EXPORTS = {
     "msp_profile_reset": (C.c_int, [C.c_void_p]),
     "msp_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(msp_kernel_profile)]),
     "msp_debug_expire_waits": (C.c_int, [C.c_void_p, C.c_int]),
+    "msp_debug_spread_work": (C.c_int, [C.c_void_p, C.c_int]),
     "msp_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
     "msp_batch_free": (None, [C.c_void_p]),
     "msp_batch_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -437,6 +438,11 @@ class Instance(_Shared):
         """msp_debug_expire_waits: starve the next `count` staged RAS
         applications of their tile copies (failure-injection tests)."""
         _check(load().msp_debug_expire_waits(self.inst, int(count)))
+
+    def spread_work(self, on=True):
+        """msp_debug_spread_work: twice as many per-SM work lists as SMs, so
+        that the lists no SM owns are exercised (results bitwise unchanged)."""
+        _check(load().msp_debug_spread_work(self.inst, int(bool(on))))
 
     def profile_enable(self, classes=()):
         mask = 0

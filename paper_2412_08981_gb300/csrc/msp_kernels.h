@@ -219,9 +219,9 @@ void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, con
                       const int32_t* cta_list, int grid, int max_nt, int add, bool wide, cudaStream_t s,
                       int inject = 0, int* claim = nullptr, int nbins = 0);
 // y = (L D L^T)^{-1} t of a level made of ONE block (the coarsest level) for
-// each of `nviews` views, each on a cluster of 8 CTAs that split every tile
-// row of both sweeps and exchange partial results through distributed shared
-// memory, one exchange per tile row; the factor must carry the coupling
+// each of `nviews` views, each on a cluster of 16 CTAs (8 where the GPU cannot
+// place 16) that split every tile row of both sweeps and exchange partial
+// results through distributed shared memory, one exchange per tile row; the factor must carry the coupling
 // tiles of launch_ldlt_mnfill after its envelope.  Dirichlet nodes get t.
 // Written (add = 0) or added (add = 1) to z.
 size_t block_solve_cluster_smem(int max_nt);  // dynamic shared memory of one CTA

@@ -529,11 +529,14 @@ MSP_API int msp_debug_expire_waits(msp_instance* inst, int count);
  * blocks into work lists per SM, and a CTA takes the list of the SM it runs
  * on (read on the device); lists that no CTA of their SM takes (an SM the
  * launch does not reach, or a CTA beyond its SM's share) are taken by other
- * CTAs.  With on != 0 this instance's launches use twice as many lists as
- * SMs, so that half of the lists are always taken that way; the blocks'
- * arithmetic does not depend on which CTA takes them, so factors and
+ * CTAs.  With bit 0 of `on` set this instance's launches use twice as many
+ * lists as SMs, so that half of the lists are always taken that way; the
+ * blocks' arithmetic does not depend on which CTA takes them, so factors and
  * solutions are bitwise those of on == 0.  A factorisation graph captured
  * before the switch is dropped (the call waits for the instance's stream).
+ * Bit 1: the coarsest level's cluster solve takes its 8-CTA form, the one it
+ * falls back to where the GPU cannot place a cluster of 16 (the same sweeps
+ * over 8 rows a CTA; sums in another order, so equal to rounding).
  * Errors: MSP_ERR_INVALID (NULL instance), MSP_ERR_CUDA. */
 MSP_API int msp_debug_spread_work(msp_instance* inst, int on);
 

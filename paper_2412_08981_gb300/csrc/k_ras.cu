@@ -958,7 +958,7 @@ cudaError_t launch_block_solve_cl(const RasView* views, int nviews, const RasVec
 // the critical path; else 8 CTAs of eight warps.
 template <typename T>
 void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool narrow) {
   if (nviews < 1) return;
   static std::once_flag pick;
   static bool wide = false;
@@ -966,7 +966,7 @@ void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs&
     wide = launch_block_solve_cl<T, 16>(views, nviews, vecs, max_nt, add, s, true) == cudaSuccess;
     cudaGetLastError();
   });
-  if (wide)
+  if (wide && !narrow)
     launch_block_solve_cl<T, 16>(views, nviews, vecs, max_nt, add, s);
   else
     launch_block_solve_cl<T, kCl>(views, nviews, vecs, max_nt, add, s);
@@ -981,7 +981,7 @@ MSP_RAS_INST(double)
 MSP_RAS_INST(float)
 // BF16 factors: only the solve reads them (they are factored in FP32)
 MSP_RAS_INST(__nv_bfloat16)
-template void launch_block_solve_cluster<double>(const RasView*, int, const RasVecs&, int, int, cudaStream_t);
-template void launch_block_solve_cluster<float>(const RasView*, int, const RasVecs&, int, int, cudaStream_t);
+template void launch_block_solve_cluster<double>(const RasView*, int, const RasVecs&, int, int, cudaStream_t, bool);
+template void launch_block_solve_cluster<float>(const RasView*, int, const RasVecs&, int, int, cudaStream_t, bool);
 
 }  // namespace msp

@@ -197,6 +197,7 @@ struct msp_instance {
   int fz_bins = 0;
   int32_t *fz_ptr2 = nullptr, *fz_list2 = nullptr;  // the same items over 2 fz_bins lists (msp_debug_spread_work)
   bool spread_work = false;  // msp_debug_spread_work: twice as many work lists as SMs
+  bool narrow_cluster = false;  // msp_debug_spread_work(2): the coarsest solve's 8-CTA form
   bool fz_f32 = false;
   double fz_flops = 0;
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
@@ -841,7 +842,7 @@ void ras(msp_instance* I, int l, const double* t, double* z, int add, cudaStream
   vv.t[0] = t;
   vv.z[0] = z;
   if (coarse) {  // one block: both sweeps split over a cluster of CTAs
-    launch_block_solve_cluster<double>(I->rview + l, 1, vv, D.max_nt, add, s);
+    launch_block_solve_cluster<double>(I->rview + l, 1, vv, D.max_nt, add, s, I->narrow_cluster);
   } else {
     const int inj = I->expire_ras > 0 ? 1 : 0;
     if (inj) --I->expire_ras;
@@ -2659,8 +2660,9 @@ int msp_debug_expire_waits(msp_instance* I, int count) {
 int msp_debug_spread_work(msp_instance* I, int on) {
   msp::g_last_error.clear();
   if (!I) return fail(MSP_ERR_INVALID, "NULL instance");
-  if (I->spread_work != (on != 0)) {
-    I->spread_work = on != 0;
+  I->narrow_cluster = (on & 2) != 0;
+  if (I->spread_work != ((on & 1) != 0)) {
+    I->spread_work = (on & 1) != 0;
     if (I->fac_graph) {  // the captured factorisation holds the lists it was captured with
       MSP_CUDA(cudaStreamSynchronize(I->stream));
       cudaGraphExecDestroy(I->fac_graph);

@@ -227,7 +227,7 @@ void launch_ras_solve(const RasView* views, int nviews, const RasVecs& vecs, con
 size_t block_solve_cluster_smem(int max_nt);  // dynamic shared memory of one CTA
 template <typename T>
 void launch_block_solve_cluster(const RasView* views, int nviews, const RasVecs& vecs, int max_nt, int add,
-                                cudaStream_t s);
+                                cudaStream_t s, bool narrow = false);  // narrow: always the 8-CTA form
 
 // ---- batched launches: one launch for several instances of a batch, each
 // member's arithmetic exactly that of its own one-member launch.  Members are

@@ -439,10 +439,11 @@ class Instance(_Shared):
         applications of their tile copies (failure-injection tests)."""
         _check(load().msp_debug_expire_waits(self.inst, int(count)))
 
-    def spread_work(self, on=True):
+    def spread_work(self, on=True, narrow_cluster=False):
         """msp_debug_spread_work: twice as many per-SM work lists as SMs, so
-        that the lists no SM owns are exercised (results bitwise unchanged)."""
-        _check(load().msp_debug_spread_work(self.inst, int(bool(on))))
+        that the lists no SM owns are exercised (results bitwise unchanged);
+        narrow_cluster: the coarsest solve's 8-CTA cluster form."""
+        _check(load().msp_debug_spread_work(self.inst, int(bool(on)) | (2 if narrow_cluster else 0)))
 
     def profile_enable(self, classes=()):
         mask = 0

@@ -69,3 +69,31 @@ def test_spread_work_lists_are_bitwise_the_same(P, torch):
     np.testing.assert_array_equal(x0, x2)
     for a, b in zip(f0, f1):
         np.testing.assert_array_equal(a, b)
+
+
+def test_narrow_cluster_form_of_the_coarsest_solve(P, torch, orc):
+    # the coarsest solve takes clusters of 16 CTAs where the GPU places them,
+    # else 8; both forms against a sparse LU of the oracle's coarsest matrix,
+    # on a coarsest block of 21 tile rows whose band reaches three tiles back
+    import scipy.sparse.linalg as spla
+    from _common import make_oracle, relmax
+    levels, w = workload("cube48_3lvl")
+    h = make_hierarchy(levels, w, P)
+    mu = syn.mu_draw(11)
+    inst = h.assemble(mu, stream=torch.cuda.current_stream())
+    inst.factor()
+    L = len(levels) - 1
+    oc = make_oracle([levels[L]], w, orc)
+    oc.assemble(mu)
+    Ac = oc.csr(0)
+    lu = spla.splu(Ac.tocsc())
+    rng = np.random.default_rng(13)
+    for narrow in (False, True, False):
+        inst.spread_work(False, narrow_cluster=narrow)
+        for _ in range(4):
+            r = rng.normal(size=Ac.shape[0])
+            z = torch.zeros(Ac.shape[0], dtype=torch.float64, device="cuda")
+            inst.apply_op(P.msp.MSP_OP_COARSE, L, torch.tensor(r, device="cuda"), z)
+            torch.cuda.synchronize()
+            assert relmax(z.cpu().numpy(), lu.solve(r)) <= 1e-11
+    inst.spread_work(False)

@@ -1026,13 +1026,13 @@ def run_msp(args):
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "derived: 152 SMs x FMA/clk x 2 x 2.07 GHz (FP64 SIMT, no fast "
                                "FP64 tensor path on GB300); probe measured 1.19 TFLOP/s FP64",
-                "traffic": traffic_for(res["dominant"], prof)}
+                "traffic": traffic_for(res["dominant"], args.workload, args.precision)}
     else:
         peak = measured_peak("hbm_gbs", 6755.1)
         achieved = prof["bytes"] / max(1, prof["launches"]) / (dom_ms / 1e3) / 1e9
         roof = {"kernel": res["dominant"], "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": "MEASURED_PEAKS hbm_gbs",
-                "traffic": traffic_for(res["dominant"], prof)}
+                "traffic": traffic_for(res["dominant"], args.workload, args.precision)}
     roof["avg_launch_ms"] = dom_ms
     roof["grids"] = res["grids"]
     roof["time_shares_warmup"] = res["shares"]
@@ -1099,9 +1099,10 @@ def kernel_source_hash(name):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel, prof):
-    """DRAM bytes per launch from the committed ncu summary, if the source
-    file of the kernel is unchanged since it was taken (else null)."""
+def traffic_for(kernel, workload, precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    this workload and factor precision and the source file of the kernel is
+    unchanged since (else null)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
             t = json.load(fh)
@@ -1109,6 +1110,8 @@ def traffic_for(kernel, prof):
         return None
     e = t.get(kernel)
     if not e or "kernel_file" not in e:
+        return None
+    if e.get("workload") != workload or e.get("precision") != precision:
         return None
     try:
         if e.get("source_hash") != kernel_source_hash(e["kernel_file"]):

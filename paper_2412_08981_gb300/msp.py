@@ -180,6 +180,37 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data)
 
 
+def _vec(a, n, name, where):
+    """Checks a vector argument before its raw pointer goes to the C side,
+    which sees the pointer only and cannot check it: float64, contiguous, at
+    least n entries, and on the device (where == "cuda") or in host memory
+    (where == "host").  None passes (the C side treats NULL itself)."""
+    if a is None:
+        return
+    if hasattr(a, "data_ptr"):  # a torch tensor
+        on_cuda = bool(a.is_cuda)
+        if str(a.dtype) != "torch.float64":
+            raise ValueError(f"{name} must be float64")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        size = int(a.numel())
+    else:
+        if not isinstance(a, np.ndarray):
+            raise ValueError(f"{name} must be a torch tensor or a numpy array")
+        on_cuda = False
+        if a.dtype != np.float64:
+            raise ValueError(f"{name} must be float64")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{name} must be contiguous")
+        size = int(a.size)
+    if where == "cuda" and not on_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if where == "host" and on_cuda:
+        raise ValueError(f"{name} must be in host memory")
+    if size < n:
+        raise ValueError(f"{name} holds {size} entries; the level's vectors have {n}")
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -335,7 +366,10 @@ class Hierarchy(_Shared):
 
     def n_dofs(self, level=0) -> int:
         """Length of the vectors of a level."""
-        return int(self.info(level)["n_dofs"])
+        cache = self.__dict__.setdefault("_n_dofs", {})
+        if level not in cache:
+            cache[level] = int(self.info(level)["n_dofs"])
+        return cache[level]
 
     def _handle(self):
         return getattr(self, "h", None)
@@ -397,14 +431,26 @@ class Instance(_Shared):
         _check(load().msp_factor(self.inst))
 
     def apply(self, r, z, stream=None):
+        n = self.hier.n_dofs(0)
+        _vec(r, n, "r", "cuda")
+        _vec(z, n, "z", "cuda")
         _check(load().msp_apply(self.inst, _ptr(r), _ptr(z),
                                 self.stream if stream is None else _stream_ptr(stream)))
 
     def apply_op(self, op, level, x, y, stream=None):
-        _check(load().msp_apply_op(self.inst, int(op), int(level), _ptr(x), _ptr(y),
+        op, level = int(op), int(level)
+        if 0 <= level < self.hier.nlevels:  # other levels: the C side refuses them
+            n = self.hier.n_dofs(level)
+            nc = self.hier.n_dofs(level + 1) if level + 1 < self.hier.nlevels else n
+            _vec(x, nc if op == MSP_OP_INTERP else n, "x", "cuda")
+            _vec(y, nc if op == MSP_OP_RESTRICT else n, "y", "cuda")
+        _check(load().msp_apply_op(self.inst, op, level, _ptr(x), _ptr(y),
                                    self.stream if stream is None else _stream_ptr(stream)))
 
     def solve(self, x, b=None, rtol=1e-8, raise_on_fail=True) -> dict:
+        n = self.hier.n_dofs(0)
+        _vec(x, n, "x", "cuda")
+        _vec(b, n, "b", "cuda")
         st = msp_stats()
         rc = load().msp_solve(self.inst, _ptr(b), _ptr(x), float(rtol), C.byref(st))
         if rc not in (MSP_OK, MSP_ERR_NOT_CONVERGED) or (raise_on_fail and rc != MSP_OK):
@@ -412,6 +458,9 @@ class Instance(_Shared):
         return {k: getattr(st, k) for k, _ in msp_stats._fields_}
 
     def solve_host(self, mu, x_host, b_host=None, rtol=1e-8, raise_on_fail=True) -> dict:
+        n = self.hier.n_dofs(0)
+        _vec(x_host, n, "x_host", "host")
+        _vec(b_host, n, "b_host", "host")
         st = msp_stats()
         mu = np.ascontiguousarray(mu, np.float64)
         rc = load().msp_solve_host(self.inst, _ptr(mu), 8, _ptr(b_host), _ptr(x_host),
@@ -476,11 +525,14 @@ class Server:
         _check(load().msp_server_create(C.byref(o), C.byref(srv)))
         self.srv = srv
         self._hier = []
+        self._by_id = {}    # hierarchy id -> Hierarchy
+        self._rid_n = {}    # request id -> length of its solution, until collected
 
     def add(self, h: Hierarchy) -> int:
         i = C.c_int(0)
         _check(load().msp_server_add_hierarchy(self.srv, h.h, C.byref(i)))
         self._hier.append(h)
+        self._by_id[int(i.value)] = h
         h._acquire(self)  # the server's slot instances go before the hierarchy
         return int(i.value)
 
@@ -489,14 +541,21 @@ class Server:
         rid = C.c_uint64(0)
         _check(load().msp_submit(self.srv, int(hid), _ptr(mu), int(mu.size), float(rtol),
                                  C.byref(rid)))
+        if int(hid) in self._by_id:
+            self._rid_n[int(rid.value)] = self._by_id[int(hid)].n_dofs(0)
         return int(rid.value)
 
     def poll(self, rid, x_host=None, timeout_ms=-1):
-        """Returns (status, stats dict); status MSP_PENDING if not finished."""
+        """Returns (status, stats dict); status MSP_PENDING if not finished.
+        x_host: host memory for the solution (at least the request's level-0
+        length), or None."""
+        _vec(x_host, self._rid_n.get(int(rid), 0), "x_host", "host")
         st = msp_stats()
         rc = load().msp_poll(self.srv, C.c_uint64(rid), _ptr(x_host), C.byref(st), int(timeout_ms))
         if rc == MSP_ERR_INVALID:
             _check(rc)
+        if rc != MSP_PENDING:
+            self._rid_n.pop(int(rid), None)
         return rc, {k: getattr(st, k) for k, _ in msp_stats._fields_}
 
     def close(self):
@@ -540,6 +599,15 @@ class Batch:
         tensors / None (None: the member's load vector).  Returns the
         per-member stats dicts."""
         n = len(self._insts)
+        if len(xs) != n or (bs is not None and len(bs) != n):
+            raise ValueError(f"one x (and b, if given) per member: {n} members")
+        for i, inst in enumerate(self._insts):
+            m = inst.hier.n_dofs(0)
+            _vec(xs[i], m, f"xs[{i}]", "cuda")
+            if xs[i] is None:
+                raise ValueError(f"xs[{i}] must be a CUDA tensor")
+            if bs is not None:
+                _vec(bs[i], m, f"bs[{i}]", "cuda")
         xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
         ba = None
         if bs is not None:

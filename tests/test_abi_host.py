@@ -264,6 +264,38 @@ def test_noalloc_binding_checks_its_tensors(P):
         m.multidot_noalloc(cpu, cpu, cpu)
 
 
+def test_binding_checks_vector_arguments(P):
+    """Vectors handed to apply, apply_op, solve, solve_host, poll and a batch's
+    solve reach the C side as raw pointers, so the binding checks them first:
+    float64, contiguous, long enough for the level, and in the memory the call
+    reads (device or host)."""
+    m = P.msp
+    m._vec(None, 10, "x", "cuda")  # NULL: the C side decides
+    m._vec(np.zeros(10), 10, "x", "host")
+    m._vec(np.zeros(12), 10, "x", "host")
+    with pytest.raises(ValueError, match="entries"):
+        m._vec(np.zeros(9), 10, "x", "host")
+    with pytest.raises(ValueError, match="float64"):
+        m._vec(np.zeros(10, np.float32), 10, "x", "host")
+    with pytest.raises(ValueError, match="contiguous"):
+        m._vec(np.zeros(20)[::2], 10, "x", "host")
+    with pytest.raises(ValueError, match="CUDA"):
+        m._vec(np.zeros(10), 10, "x", "cuda")
+    with pytest.raises(ValueError, match="numpy"):
+        m._vec([0.0] * 10, 10, "x", "host")
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(10, dtype=torch.float64)
+    m._vec(t, 10, "x", "host")
+    with pytest.raises(ValueError, match="CUDA"):
+        m._vec(t, 10, "x", "cuda")
+    with pytest.raises(ValueError, match="float64"):
+        m._vec(t.float(), 10, "x", "host")
+    with pytest.raises(ValueError, match="contiguous"):
+        m._vec(torch.zeros(20, dtype=torch.float64)[::2], 10, "x", "host")
+    with pytest.raises(ValueError, match="entries"):
+        m._vec(torch.zeros(9, dtype=torch.float64), 10, "x", "host")
+
+
 @pytest.mark.parametrize("name", ["p2cube6_3lvl", "p2cube12_3lvl", "p2p1cube6_3lvl", "p2p1cube12_3lvl"])
 def test_host_p2_structures_match_oracle(P, orc, name):
     """Quadratic elements (DoFs on vertices and edges): the DoF-level pattern,

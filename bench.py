@@ -145,6 +145,8 @@ class Clocks:
 
     def stop(self):
         if self.p is None:
+            self.f.close()
+            os.unlink(self.f.name)
             return None
         self.p.terminate()
         try:

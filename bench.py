@@ -160,6 +160,7 @@ class Clocks:
                 parts = [x.strip() for x in line.split(",")]
                 if len(parts) >= 9:
                     rows.append(parts)
+        self.f.close()
         os.unlink(self.f.name)
         if not rows:
             return None

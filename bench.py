@@ -496,18 +496,21 @@ def run_msp(args):
         h.close()
         return out
 
-    def measure_batched_uneven(total=64, group=16):
+    def measure_batched_uneven(total=128, group=16, reps=3):
         """Batched uneven solves: `total` parameters, half on a 32^3 and half on a
         48^3 hierarchy (FP32 factors, FP64 outer loop), `group` instances
-        resident at once (half of each).  Two ways, timed on the host wall
-        clock over the same parameters:
+        resident at once (half of each).  Three ways, each warmed up and then
+        timed `reps` times on the host wall clock over the same parameters
+        (the median is reported):
           streams: every instance on its own stream and host thread, each
             re-assembling, factoring and solving its share in turn;
           batch: rounds of `group` parameters through one msp_batch: one
             msp_batch_assemble, one msp_batch_factor (the persistent-level
             blocks of all of them in one launch), one msp_solve_batch (FGMRES
             of all of them in lockstep, each V-cycle and Krylov step one
-            launch per kernel for the whole round)."""
+            launch per kernel for the whole round);
+          batch_pipelined: the same as four msp_batch groups, each on its own
+            stream and host thread."""
         import threading
         hs = []
         for name in ("cube32b_3lvl", "cube48_3lvl"):
@@ -581,11 +584,13 @@ def run_msp(args):
                 pbatches = [P.msp.Batch(insts[g * per:(g + 1) * per], stream=pstreams[g]) for g in range(npipe)]
             fn(5000, 5000 + group)  # warm-up
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            fn(0, total)
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-            out[name] = {"value": total / wall, "unit": UNIT, "wall_s": round(wall, 3)}
+            rates = []
+            for _ in range(reps):  # each way timed `reps` times over the same parameters: the median
+                t0 = time.perf_counter()
+                fn(0, total)
+                torch.cuda.synchronize()
+                rates.append(total / (time.perf_counter() - t0))
+            out[name] = {"value": float(np.median(rates)), "unit": UNIT, "reps": [round(v, 1) for v in rates]}
         out["batch"]["how"] = ("rounds of 16 parameters through one msp_batch: msp_batch_assemble, msp_batch_factor "
                                "(the persistent levels' blocks of all 16 in one launch, replayed from a CUDA graph), "
                                "msp_solve_batch (the 16 FGMRES solves in lockstep, every V-cycle and Krylov launch "

@@ -180,11 +180,12 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data)
 
 
-def _vec(a, n, name, where):
+def _vec(a, n, name, where, out=False):
     """Checks a vector argument before its raw pointer goes to the C side,
     which sees the pointer only and cannot check it: float64, contiguous, at
-    least n entries, and on the device (where == "cuda") or in host memory
-    (where == "host").  None passes (the C side treats NULL itself)."""
+    least n entries, on the device (where == "cuda") or in host memory
+    (where == "host"), and writable if the call writes it (out).  None passes
+    (the C side treats NULL itself)."""
     if a is None:
         return
     if hasattr(a, "data_ptr"):  # a torch tensor
@@ -200,6 +201,8 @@ def _vec(a, n, name, where):
         on_cuda = False
         if a.dtype != np.float64:
             raise ValueError(f"{name} must be float64")
+        if out and not a.flags.writeable:
+            raise ValueError(f"{name} must be writable")
         if not a.flags.c_contiguous:
             raise ValueError(f"{name} must be contiguous")
         size = int(a.size)
@@ -433,7 +436,7 @@ class Instance(_Shared):
     def apply(self, r, z, stream=None):
         n = self.hier.n_dofs(0)
         _vec(r, n, "r", "cuda")
-        _vec(z, n, "z", "cuda")
+        _vec(z, n, "z", "cuda", out=True)
         _check(load().msp_apply(self.inst, _ptr(r), _ptr(z),
                                 self.stream if stream is None else _stream_ptr(stream)))
 
@@ -443,13 +446,13 @@ class Instance(_Shared):
             n = self.hier.n_dofs(level)
             nc = self.hier.n_dofs(level + 1) if level + 1 < self.hier.nlevels else n
             _vec(x, nc if op == MSP_OP_INTERP else n, "x", "cuda")
-            _vec(y, nc if op == MSP_OP_RESTRICT else n, "y", "cuda")
+            _vec(y, nc if op == MSP_OP_RESTRICT else n, "y", "cuda", out=True)
         _check(load().msp_apply_op(self.inst, op, level, _ptr(x), _ptr(y),
                                    self.stream if stream is None else _stream_ptr(stream)))
 
     def solve(self, x, b=None, rtol=1e-8, raise_on_fail=True) -> dict:
         n = self.hier.n_dofs(0)
-        _vec(x, n, "x", "cuda")
+        _vec(x, n, "x", "cuda", out=True)
         _vec(b, n, "b", "cuda")
         st = msp_stats()
         rc = load().msp_solve(self.inst, _ptr(b), _ptr(x), float(rtol), C.byref(st))
@@ -459,7 +462,7 @@ class Instance(_Shared):
 
     def solve_host(self, mu, x_host, b_host=None, rtol=1e-8, raise_on_fail=True) -> dict:
         n = self.hier.n_dofs(0)
-        _vec(x_host, n, "x_host", "host")
+        _vec(x_host, n, "x_host", "host", out=True)
         _vec(b_host, n, "b_host", "host")
         st = msp_stats()
         mu = np.ascontiguousarray(mu, np.float64)
@@ -549,7 +552,7 @@ class Server:
         """Returns (status, stats dict); status MSP_PENDING if not finished.
         x_host: host memory for the solution (at least the request's level-0
         length), or None."""
-        _vec(x_host, self._rid_n.get(int(rid), 0), "x_host", "host")
+        _vec(x_host, self._rid_n.get(int(rid), 0), "x_host", "host", out=True)
         st = msp_stats()
         rc = load().msp_poll(self.srv, C.c_uint64(rid), _ptr(x_host), C.byref(st), int(timeout_ms))
         if rc == MSP_ERR_INVALID:
@@ -603,7 +606,7 @@ class Batch:
             raise ValueError(f"one x (and b, if given) per member: {n} members")
         for i, inst in enumerate(self._insts):
             m = inst.hier.n_dofs(0)
-            _vec(xs[i], m, f"xs[{i}]", "cuda")
+            _vec(xs[i], m, f"xs[{i}]", "cuda", out=True)
             if xs[i] is None:
                 raise ValueError(f"xs[{i}] must be a CUDA tensor")
             if bs is not None:

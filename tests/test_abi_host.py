@@ -283,6 +283,11 @@ def test_binding_checks_vector_arguments(P):
         m._vec(np.zeros(10), 10, "x", "cuda")
     with pytest.raises(ValueError, match="numpy"):
         m._vec([0.0] * 10, 10, "x", "host")
+    ro = np.zeros(10)
+    ro.flags.writeable = False
+    m._vec(ro, 10, "b_host", "host")  # read only: fine for an input
+    with pytest.raises(ValueError, match="writable"):
+        m._vec(ro, 10, "x_host", "host", out=True)
     torch = pytest.importorskip("torch")
     t = torch.zeros(10, dtype=torch.float64)
     m._vec(t, 10, "x", "host")

@@ -308,7 +308,9 @@ struct TetGrid {
 void build_grid(const HostLevel& C, TetGrid& g) {
   double hi[3] = {-1e300, -1e300, -1e300};
   for (int d = 0; d < 3; ++d) g.lo[d] = 1e300;
-  for (int i = 0; i < C.n; ++i)
+  // the mesh's vertices (xyz holds nv points; with P2 elements n also counts
+  // the edge DoFs)
+  for (int i = 0; i < C.nv; ++i)
     for (int d = 0; d < 3; ++d) {
       g.lo[d] = std::min(g.lo[d], C.xyz[3 * (int64_t)i + d]);
       hi[d] = std::max(hi[d], C.xyz[3 * (int64_t)i + d]);

@@ -265,11 +265,12 @@ def test_noalloc_binding_checks_its_tensors(P):
 
 
 def test_random_small_setups_match_oracle(P, orc):
-    """Seeded random small P1 set-ups (2-3 levels of 4^3..12^3 cells, every
+    """Seeded random small set-ups: P1 (2-3 levels of 4^3..12^3 cells, every
     box split of 1-3 a side, overlap 1-3, jitter 0-0.2, barycentric or MLS
-    transfers): the library's host structures equal the oracle's, pattern,
-    subdomains, owners and transfer structure bit for bit, transfer weights to
-    rounding.  Partitions here include boxes that hold few or no vertices."""
+    transfers), then P2, P2-P1 and three fields per vertex.  The library's
+    host structures equal the oracle's: pattern, subdomains, owners and
+    transfer structure bit for bit, transfer weights to rounding.  Partitions
+    here include boxes that hold few or no vertices."""
     import random
     rng = random.Random(20261204)
     for _ in range(12):
@@ -301,6 +302,36 @@ def test_random_small_setups_match_oracle(P, orc):
                 ref = o.get(a, l)
                 np.testing.assert_allclose(h.array(l, a), ref, rtol=1e-12, atol=1e-13 * max(1.0, abs(ref).max()))
         np.testing.assert_array_equal(h.array(L - 1, "sub_dofs"), np.where(levels[-1].dirichlet == 0)[0])
+        h.close()
+    # and the other DoF distributions: P2, P2-P1, three fields per vertex
+    for _ in range(9):
+        nl = rng.choice([2, 3])
+        ns = [rng.choice([4, 5, 6, 7, 8])]
+        for _ in range(nl - 1):
+            ns.append(max(2, ns[-1] // 2 + rng.choice([0, 0, 1])))
+        parts = tuple(tuple(rng.choice([1, 2]) for _ in range(3)) for _ in range(nl - 1))
+        pde = rng.choice(["poisson_p2", "p2p1", "elasticity"])
+        levels = syn.hierarchy(tuple(ns), parts, hierarchy_id=rng.randrange(5), jitter=rng.choice([0.0, 0.1, 0.2]))
+        w = dict(delta=rng.choice([1, 2]), nu=2, restart=30, coef="cosexp", scale=1.0, load="one", pde=pde,
+                 poisson=0.3, coupling=1.0)
+        h = make_hierarchy(levels, w, P, host_only=True)
+        o = make_oracle(levels, w, orc)
+        L = len(levels)
+        for l in range(L):
+            assert h.n_dofs(l) == o.n[l]
+            np.testing.assert_array_equal(h.array(l, "rowptr"), o.get("rowptr", l))
+            np.testing.assert_array_equal(h.array(l, "col"), o.get("col", l))
+        for l in range(L - 1):
+            subs = o.subdomains(l)
+            sp, sd, so = h.array(l, "sub_ptr"), h.array(l, "sub_dofs"), h.array(l, "sub_own")
+            assert sp.size - 1 == len(subs)
+            for p, (d, ow) in enumerate(subs):
+                np.testing.assert_array_equal(sd[sp[p]:sp[p + 1]], d)
+                np.testing.assert_array_equal(so[sp[p]:sp[p + 1]], ow)
+            for a in ("P_rowptr", "P_col", "PT_rowptr", "PT_col"):
+                np.testing.assert_array_equal(h.array(l, a), o.get(a, l))
+            np.testing.assert_allclose(h.array(l, "P_val"), o.get("P_val", l), atol=1e-13)
+            np.testing.assert_allclose(h.array(l, "PT_val"), o.get("PT_val", l), atol=1e-13)
         h.close()
 
 
